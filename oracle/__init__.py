@@ -1,0 +1,347 @@
+"""CPU oracle of the UGKS + adaptive-velocity-space hot path (arXiv 2212.05645).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  It is
+a plain FP64 C implementation (``avs_oracle.c``, built with gcc and
+``-ffp-contract=off``) wrapped with ctypes, plus :mod:`oracle.mlp` (numpy
+FP64).  It shares no code with the CUDA library; the only common module is
+the input generator :mod:`paper_2212_05645_gb300.workloads`.
+
+Parity status of each routine (what pins it) is listed in the tests under
+``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libavs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OM_COPY, OM_MERGE = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP over cells, no FMA contraction)."""
+    src = os.path.join(_HERE, "avs_oracle.c")
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "avs_oracle.h"))):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-std=c11",
+           "-o", tmp, src, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_SO)
+            dp = C.POINTER(C.c_double)
+            ip = C.POINTER(C.c_int)
+            up = C.POINTER(C.c_uint)
+            L.om_mu_ref_from_Kn.restype = C.c_double
+            L.om_mu_ref_from_Kn.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.om_shakhov_field.restype = None
+            L.om_shakhov_field.argtypes = [C.c_int, C.c_int, dp, C.c_double, C.c_double, dp, C.c_double,
+                                           dp, dp, dp]
+            L.om_forest_base.restype = C.c_int
+            L.om_forest_base.argtypes = [C.c_int, ip, ip, ip, up]
+            L.om_forest_geom.restype = None
+            L.om_forest_geom.argtypes = [C.c_int, ip, dp, dp, C.c_int, ip, ip, up, dp, dp]
+            L.om_maxwell_init.restype = None
+            L.om_maxwell_init.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_double, C.c_double,
+                                          C.c_ulonglong, dp]
+            L.om_normal_field.restype = None
+            L.om_normal_field.argtypes = [C.c_ulonglong, C.c_int, C.c_int, dp]
+            L.om_moments.restype = None
+            L.om_moments.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+            L.om_dt_unit.restype = C.c_double
+            L.om_dt_unit.argtypes = [C.c_void_p, C.c_int, dp]
+            L.om_step.restype = C.c_int
+            L.om_step.argtypes = [C.c_void_p, C.c_void_p, C.c_int, dp, dp, C.c_double, dp, dp, dp]
+            L.om_criterion.restype = None
+            L.om_criterion.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+            L.om_adapt_tree.restype = C.c_int
+            L.om_adapt_tree.argtypes = [C.c_int, C.c_int, ip, ip, up, dp, C.c_double, C.c_double,
+                                        C.c_double, C.c_int, C.c_int, ip, ip, up, ip, ip]
+            L.om_remap.restype = None
+            L.om_remap.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, ip, dp]
+            L.om_correct.restype = C.c_double
+            L.om_correct.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_double, C.c_int, dp, dp]
+            _lib = L
+    return _lib
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("D", C.c_int), ("Nc", C.c_int), ("Nf", C.c_int), ("nbc", C.c_int),
+                ("faceL", C.POINTER(C.c_int)), ("faceR", C.POINTER(C.c_int)),
+                ("An", C.POINTER(C.c_double)), ("rL", C.POINTER(C.c_double)),
+                ("rR", C.POINTER(C.c_double)), ("vol", C.POINTER(C.c_double)),
+                ("bc", C.POINTER(C.c_double))]
+
+
+class _Gas(C.Structure):
+    _fields_ = [("R", C.c_double), ("Pr", C.c_double), ("omega", C.c_double),
+                ("mu_ref", C.c_double), ("T_ref", C.c_double), ("lim_K", C.c_double),
+                ("limiter", C.c_int)]
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _up(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def n_arrays(D: int) -> int:
+    """Reduced distributions per node: G and H in 2D, G alone in 3D (Eq. 6)."""
+    return 2 if D == 2 else 1
+
+
+# ---------------------------------------------------------------------------
+# thin wrappers (numpy in, numpy out)
+# ---------------------------------------------------------------------------
+def mu_ref_from_Kn(Kn, omega, R=0.5):
+    return lib().om_mu_ref_from_Kn(Kn, omega, R)
+
+
+def shakhov_field(D, xi, Pr, rho, U, RT, q):
+    """Shakhov equilibrium G (and H in 2D) of one state at the nodes (Eqs. 14-17)."""
+    xi = _f64(xi); U = _f64(U); q = _f64(q)
+    Nv = xi.shape[0]
+    gG = np.zeros(Nv); gH = np.zeros(Nv)
+    lib().om_shakhov_field(D, Nv, _dp(xi), Pr, rho, _dp(U), RT, _dp(q), _dp(gG), _dp(gH))
+    return gG, gH
+
+
+def forest_base(D, nb):
+    nb = np.ascontiguousarray(nb, dtype=np.int32)
+    n = int(np.prod(nb))
+    level = np.zeros(n, np.int32)
+    base = np.zeros(n, np.int32)
+    key = np.zeros(n, np.uint32)
+    lib().om_forest_base(D, _ip(nb), _ip(level), _ip(base), _up(key))
+    return level, base, key
+
+
+def forest_geom(D, nb, vlo, vhi, level, base, key):
+    nb = np.ascontiguousarray(nb, dtype=np.int32)
+    vlo = _f64(vlo); vhi = _f64(vhi)
+    level = np.ascontiguousarray(level, np.int32)
+    base = np.ascontiguousarray(base, np.int32)
+    key = np.ascontiguousarray(key, np.uint32)
+    Nv = len(level)
+    xi = np.zeros((Nv, D)); w = np.zeros(Nv)
+    lib().om_forest_geom(D, _ip(nb), _dp(vlo), _dp(vhi), Nv, _ip(level), _ip(base), _up(key), _dp(xi), _dp(w))
+    return xi, w
+
+
+def maxwell_init(D, xi, Wp, R=0.5, amp=0.0, seed=12345):
+    xi = _f64(xi); Wp = _f64(Wp)
+    Nc, Nv = Wp.shape[0], xi.shape[0]
+    f = np.zeros((Nc, n_arrays(D), Nv))
+    lib().om_maxwell_init(D, Nc, Nv, _dp(xi), _dp(Wp), R, amp, seed, _dp(f))
+    return f
+
+
+def normal_field(seed, Nc, Nv):
+    z = np.zeros((Nc, Nv))
+    lib().om_normal_field(seed, Nc, Nv, _dp(z))
+    return z
+
+
+def moments(D, xi, w, f):
+    """Conserved W (rho, rho U, rho E) and heat flux q of every cell (Eqs. 7-8)."""
+    xi = _f64(xi); w = _f64(w); f = _f64(f)
+    Nc, Nv = f.shape[0], f.shape[-1]
+    Wc = np.zeros((Nc, D + 2)); q = np.zeros((Nc, D))
+    lib().om_moments(D, Nc, Nv, _dp(xi), _dp(w), _dp(f), _dp(Wc), _dp(q))
+    return Wc, q
+
+
+class MeshHandle:
+    """Keeps the numpy arrays alive behind the C struct."""
+
+    def __init__(self, mesh):
+        self.mesh = mesh
+        self._keep = [mesh.faceL, mesh.faceR, mesh.An, mesh.rL, mesh.rR, mesh.vol, mesh.bc]
+        self.s = _Mesh(mesh.D, mesh.Nc, mesh.Nf, mesh.bc.shape[0], _ip(mesh.faceL), _ip(mesh.faceR),
+                       _dp(mesh.An), _dp(mesh.rL), _dp(mesh.rR), _dp(mesh.vol), _dp(mesh.bc))
+
+    @property
+    def ptr(self):
+        return C.byref(self.s)
+
+
+def gas(R=0.5, Pr=2.0 / 3.0, omega=0.81, mu_ref=None, Kn=None, T_ref=1.0, lim_K=0.3, limiter=1):
+    if mu_ref is None:
+        mu_ref = mu_ref_from_Kn(Kn, omega, R)
+    return _Gas(R, Pr, omega, mu_ref, T_ref, lim_K, limiter)
+
+
+def dt_unit(mh: MeshHandle, xi):
+    xi = _f64(xi)
+    return lib().om_dt_unit(mh.ptr, xi.shape[0], _dp(xi))
+
+
+def step(mh: MeshHandle, g: _Gas, xi, w, dt, f_in, Wc):
+    """One explicit step; returns f_out and updates Wc in place."""
+    xi = _f64(xi); w = _f64(w); f_in = _f64(f_in)
+    assert Wc.dtype == np.float64 and Wc.flags.c_contiguous
+    f_out = np.empty_like(f_in)
+    rc = lib().om_step(mh.ptr, C.byref(g), xi.shape[0], _dp(xi), _dp(w), float(dt), _dp(f_in), _dp(f_out), _dp(Wc))
+    if rc != 0:
+        raise FloatingPointError(f"oracle step: non-positive density or temperature (status {rc})")
+    return f_out
+
+
+def criterion(D, xi, w, f, Wc):
+    xi = _f64(xi); w = _f64(w); f = _f64(f); Wc = _f64(Wc)
+    Nc, Nv = f.shape[0], f.shape[-1]
+    M = np.zeros(Nv)
+    lib().om_criterion(D, Nc, Nv, _dp(xi), _dp(w), _dp(f), _dp(Wc), _dp(M))
+    return M
+
+
+def adapt_tree(D, level, base, key, M, s, C1, C2, max_refine, cap=None):
+    level = np.ascontiguousarray(level, np.int32)
+    base = np.ascontiguousarray(base, np.int32)
+    key = np.ascontiguousarray(key, np.uint32)
+    M = _f64(M)
+    Nv = len(level)
+    cap = cap or Nv * (1 << D)
+    nl = np.zeros(cap, np.int32); nb = np.zeros(cap, np.int32); nk = np.zeros(cap, np.uint32)
+    src = np.zeros(cap, np.int32); kind = np.zeros(cap, np.int32)
+    n = lib().om_adapt_tree(D, Nv, _ip(level), _ip(base), _up(key), _dp(M), float(s), float(C1), float(C2),
+                            int(max_refine), int(cap), _ip(nl), _ip(nb), _up(nk), _ip(src), _ip(kind))
+    if n < 0:
+        raise MemoryError("adapted tree exceeds the node capacity")
+    return nl[:n].copy(), nb[:n].copy(), nk[:n].copy(), src[:n].copy(), kind[:n].copy()
+
+
+def remap(D, f_old, src, kind):
+    f_old = _f64(f_old)
+    Nc, nA, Nv_old = f_old.shape
+    src = np.ascontiguousarray(src, np.int32); kind = np.ascontiguousarray(kind, np.int32)
+    f_new = np.zeros((Nc, nA, len(src)))
+    lib().om_remap(D, Nc, Nv_old, _dp(f_old), len(src), _ip(src), _ip(kind), _dp(f_new))
+    return f_new
+
+
+def correct(D, xi, w, Wc_target, f, iters=3, R=0.5):
+    """Conservation correction in place; returns the remaining relative gap."""
+    xi = _f64(xi); w = _f64(w); Wc_target = _f64(Wc_target)
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    Nc, Nv = f.shape[0], f.shape[-1]
+    return lib().om_correct(D, Nc, Nv, _dp(xi), _dp(w), R, iters, _dp(Wc_target), _dp(f))
+
+
+def conserved_from_primitive(D, Wp, R=0.5):
+    """rho, rho U, rho E with rho E = rho U^2 / 2 + (3/2) rho R T (monatomic)."""
+    Wp = _f64(Wp)
+    Wc = np.zeros_like(Wp)
+    rho = Wp[..., 0]
+    U = Wp[..., 1:1 + D]
+    Wc[..., 0] = rho
+    Wc[..., 1:1 + D] = rho[..., None] * U
+    Wc[..., D + 1] = 0.5 * rho * (U * U).sum(-1) + 1.5 * rho * R * Wp[..., D + 1]
+    return Wc
+
+
+# ---------------------------------------------------------------------------
+# whole-run driver
+# ---------------------------------------------------------------------------
+class Run:
+    """Oracle state for one workload: velocity forest, f, carried W."""
+
+    def __init__(self, wl, limiter=None, corr_iters=3, build_tree=True):
+        self.wl = wl
+        self.D = wl.D
+        self.mh = MeshHandle(wl.mesh)
+        self.g = gas(R=0.5, Pr=wl.Pr, omega=wl.omega, Kn=wl.Kn,
+                     limiter=wl.limiter if limiter is None else limiter)
+        self.corr_iters = corr_iters
+        self.nb = np.array(wl.base, np.int32)
+        self.s = float(np.prod(wl.base))            # uniform-share normalisation (R10)
+        self.level, self.base, self.key = forest_base(self.D, self.nb)
+        self._geom()
+        if build_tree:
+            self.initial_tree()
+        self.f = None
+        self.Wc = None
+
+    def _geom(self):
+        self.xi, self.w = forest_geom(self.D, self.nb, self.wl.vlo, self.wl.vhi, self.level, self.base, self.key)
+
+    @property
+    def Nv(self):
+        return len(self.level)
+
+    def initial_tree(self):
+        """Step-0 AVS (Sec. 3.5, steps 1-3; reading R13): adapt on the two
+        pseudo cells g^eq(W_inf) and g^eq(rho_inf, 0, T_inf) until stable."""
+        D = self.D
+        Winf = np.array(self.wl.W_inf, dtype=np.float64)
+        W0 = Winf.copy(); W0[1:1 + D] = 0.0
+        Wp = np.stack([Winf, W0])
+        Wc = conserved_from_primitive(D, Wp)
+        for _ in range(max(1, self.wl.max_refine)):
+            f = maxwell_init(D, self.xi, Wp)
+            M = criterion(D, self.xi, self.w, f, Wc)
+            nl, nb, nk, src, kind = adapt_tree(D, self.level, self.base, self.key, M, self.s,
+                                               self.wl.C1, self.wl.C2, self.wl.max_refine)
+            changed = len(nl) != self.Nv or np.any(nl != self.level) or np.any(nk != self.key)
+            self.level, self.base, self.key = nl, nb, nk
+            self._geom()
+            if not changed:
+                break
+
+    def init_field(self, Wp=None, amp=0.0, seed=12345):
+        Wp = self.wl.W_init if Wp is None else Wp
+        self.f = maxwell_init(self.D, self.xi, Wp, amp=amp, seed=seed)
+        self.Wc, _ = moments(self.D, self.xi, self.w, self.f)
+
+    def dt(self, cfl=None):
+        return (self.wl.cfl if cfl is None else cfl) * dt_unit(self.mh, self.xi)
+
+    def step(self, dt):
+        self.f = step(self.mh, self.g, self.xi, self.w, dt, self.f, self.Wc)
+
+    def adapt(self, Wc_override=None, correct_f=True):
+        """One adaptation: criterion on the moments of f (Eq. 7), marks, new
+        tree, consanguinity remap, conservation correction."""
+        D = self.D
+        Wf, _ = moments(D, self.xi, self.w, self.f)
+        Wcrit = Wf if Wc_override is None else Wc_override
+        M = criterion(D, self.xi, self.w, self.f, Wcrit)
+        nl, nb, nk, src, kind = adapt_tree(D, self.level, self.base, self.key, M, self.s,
+                                           self.wl.C1, self.wl.C2, self.wl.max_refine)
+        f_new = remap(D, self.f, src, kind)
+        self.level, self.base, self.key = nl, nb, nk
+        self._geom()
+        gap = 0.0
+        if correct_f:
+            gap = correct(D, self.xi, self.w, Wf, f_new, iters=self.corr_iters)
+        self.f = f_new
+        return dict(M=M, src=src, kind=kind, gap=gap, Nv=self.Nv)

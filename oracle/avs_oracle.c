@@ -1,0 +1,725 @@
+/*
+ * Plain FP64 CPU oracle of the explicit UGKS step on a global adaptive
+ * velocity space (arXiv 2212.05645).  TEST INFRASTRUCTURE: only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg use it.
+ *
+ * Every routine follows the paper's definitions in the paper's order, with
+ * plain loops (cells, then arrays, then nodes; faces in list order) and no
+ * blocking or fusion.  Where the paper is silent the reading used is named
+ * in the comment (R1..R14 are the readings listed in the design notes).
+ * Build with -ffp-contract=off so that no multiply-add is fused.
+ */
+#include "avs_oracle.h"
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXS 8            /* face slots per cell */
+#define PI 3.14159265358979323846
+
+static int nArr(int D) { return D == 2 ? 2 : 1; }
+
+/* ---- gas model ----------------------------------------------------------- */
+
+/* Eq. (4)-(5) with rho = T = L_ref = 1:  Kn = 2 mu (5-2w)(7-2w) / (15 sqrt(2 pi R)) */
+double om_mu_ref_from_Kn(double Kn, double omega, double R)
+{
+    return 15.0 * sqrt(2.0 * PI * R) * Kn / (2.0 * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega));
+}
+
+/* Eq. (3): tau = mu / (rho R T), VHS mu = mu_ref (T / T_ref)^omega */
+static double tau_of(const om_gas *g, double rho, double RT)
+{
+    double T = RT / g->R;
+    double mu = g->mu_ref * pow(T / g->T_ref, g->omega);
+    return mu / (rho * RT);
+}
+
+/* conserved -> rho, U, RT.  Monatomic gas: rho E = rho U^2 / 2 + (3/2) rho R T
+ * (three translational degrees of freedom, K = 0; Eq. 7). */
+static void prim_of(int D, const double *Wc, double *rho, double *U, double *RT)
+{
+    double r = Wc[0];
+    double m2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        U[d] = Wc[1 + d] / r;
+        m2 += Wc[1 + d] * Wc[1 + d];
+    }
+    *rho = r;
+    *RT = (Wc[D + 1] - 0.5 * m2 / r) / (1.5 * r);
+}
+
+/* Eq. (Maxwell_df): g = rho / (2 pi R T)^(D/2) exp(-|xi-U|^2 / (2 R T)) */
+static double maxwell(int D, double rho, const double *U, double RT, const double *xi)
+{
+    double c2 = 0.0;
+    for (int d = 0; d < D; ++d) c2 += (xi[d] - U[d]) * (xi[d] - U[d]);
+    return rho / pow(2.0 * PI * RT, 0.5 * D) * exp(-c2 / (2.0 * RT));
+}
+
+/* Eqs. (14)-(17), monatomic (K = 0): Shakhov equilibrium of the reduced
+ * distributions.  The second line of Eq. (14) is read as g^H. */
+static void shakhov(int D, double Pr, double rho, const double *U, double RT, const double *q,
+                    const double *xi, double *gG, double *gH)
+{
+    double c[3], c2 = 0.0, cq = 0.0;
+    for (int d = 0; d < D; ++d) {
+        c[d] = xi[d] - U[d];
+        c2 += c[d] * c[d];
+        cq += c[d] * q[d];
+    }
+    double geq = rho / pow(2.0 * PI * RT, 0.5 * D) * exp(-c2 / (2.0 * RT));
+    double p = rho * RT;
+    double a = (1.0 - Pr) * cq / (5.0 * p * RT);
+    *gG = geq + a * (c2 / RT - D - 2.0) * geq;                       /* g^eq + G_Pr */
+    double Heq = (3.0 - D) * RT * geq;                               /* Eq. 16      */
+    *gH = Heq + a * ((c2 / RT - D) * (3.0 - D)) * RT * geq;          /* + H_Pr      */
+}
+
+/* Shakhov equilibrium (G, H) of one state at every node; exported for tests. */
+void om_shakhov_field(int D, int Nv, const double *xi, double Pr, double rho, const double *U,
+                      double RT, const double *q, double *gG, double *gH)
+{
+    for (int k = 0; k < Nv; ++k) {
+        double h;
+        shakhov(D, Pr, rho, U, RT, q, xi + (size_t)k * D, gG + k, gH ? gH + k : &h);
+    }
+}
+
+/* ---- velocity forest (Sec. 3.1) ---------------------------------------- */
+
+/* Level-0 base forest, base cells in row-major order (axis 0 fastest). */
+int om_forest_base(int D, const int *nb, int *level, int *base, unsigned *key)
+{
+    int n = 1;
+    for (int d = 0; d < D; ++d) n *= nb[d];
+    for (int b = 0; b < n; ++b) {
+        level[b] = 0;
+        base[b] = b;
+        key[b] = 0u;
+    }
+    return n;
+}
+
+/* Mid-point quadrature (Sec. 3): node = element centre, weight = element
+ * area/volume.  Path digits c = o0 | o1 << 1 | o2 << 2, most significant
+ * digit = first refinement.  xi = vlo + hb * (b + (2 o + 1) / 2^(l+1)). */
+void om_forest_geom(int D, const int *nb, const double *vlo, const double *vhi, int Nv,
+                    const int *level, const int *base, const unsigned *key,
+                    double *xi, double *w)
+{
+    double hb[3];
+    for (int d = 0; d < D; ++d) hb[d] = (vhi[d] - vlo[d]) / (double)nb[d];
+    for (int k = 0; k < Nv; ++k) {
+        int l = level[k];
+        int b = base[k];
+        int bi[3];
+        for (int d = 0; d < D; ++d) {
+            bi[d] = b % nb[d];
+            b /= nb[d];
+        }
+        double wk = 1.0;
+        for (int d = 0; d < D; ++d) {
+            unsigned o = 0;
+            for (int m = 0; m < l; ++m) {
+                unsigned digit = (key[k] >> (D * (l - 1 - m))) & ((1u << D) - 1u);
+                o = 2u * o + ((digit >> d) & 1u);
+            }
+            double frac = (double)(2u * o + 1u) / (double)(1u << (l + 1));
+            xi[k * D + d] = vlo[d] + hb[d] * ((double)bi[d] + frac);
+            wk *= hb[d];
+        }
+        w[k] = ldexp(wk, -D * l);
+    }
+}
+
+/* ---- synthetic initial field -------------------------------------------- */
+
+static uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double normal_ik(uint64_t seed, uint64_t i, uint64_t k)
+{
+    uint64_t key = (i << 32) | k;
+    uint64_t u1 = splitmix64(seed ^ splitmix64(2u * key));
+    uint64_t u2 = splitmix64(seed ^ splitmix64(2u * key + 1u));
+    double U1 = ((double)(u1 >> 11) + 1.0) * 0x1p-53;
+    double U2 = (double)(u2 >> 11) * 0x1p-53;
+    return sqrt(-2.0 * log(U1)) * cos(2.0 * PI * U2);
+}
+
+void om_normal_field(unsigned long long seed, int Nc, int Nv, double *z)
+{
+    for (int i = 0; i < Nc; ++i)
+        for (int k = 0; k < Nv; ++k) z[(size_t)i * Nv + k] = normal_ik(seed, (uint64_t)i, (uint64_t)k);
+}
+
+/* G = g^eq(W_i)(xi_k) (1 + amp z_ik), H = (3 - D) R T G  (Eq. 16, K = 0). */
+void om_maxwell_init(int D, int Nc, int Nv, const double *xi, const double *Wp, double R,
+                     double amp, unsigned long long seed, double *f)
+{
+    int nA = nArr(D);
+    for (int i = 0; i < Nc; ++i) {
+        const double *P = Wp + (size_t)i * (D + 2);
+        double RT = R * P[D + 1];
+        for (int k = 0; k < Nv; ++k) {
+            double G = maxwell(D, P[0], P + 1, RT, xi + (size_t)k * D);
+            if (amp != 0.0) G *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
+            f[((size_t)i * nA + 0) * Nv + k] = G;
+            if (nA == 2) f[((size_t)i * nA + 1) * Nv + k] = (3.0 - D) * RT * G;
+        }
+    }
+}
+
+/* ---- moments (Eq. 7, Eq. 8) --------------------------------------------- */
+
+static void cell_moments(int D, int Nv, const double *xi, const double *w, const double *fi,
+                         double *Wc, double *q)
+{
+    int nA = nArr(D);
+    const double *G = fi;
+    const double *H = nA == 2 ? fi + Nv : NULL;
+    double rho = 0.0, m[3] = {0, 0, 0}, E = 0.0;
+    for (int k = 0; k < Nv; ++k) {
+        const double *x = xi + (size_t)k * D;
+        double x2 = 0.0;
+        for (int d = 0; d < D; ++d) x2 += x[d] * x[d];
+        rho += w[k] * G[k];
+        for (int d = 0; d < D; ++d) m[d] += w[k] * x[d] * G[k];
+        E += 0.5 * w[k] * (x2 * G[k] + (H ? H[k] : 0.0));
+    }
+    Wc[0] = rho;
+    for (int d = 0; d < D; ++d) Wc[1 + d] = m[d];
+    Wc[D + 1] = E;
+    if (q) {
+        double U[3];
+        for (int d = 0; d < D; ++d) U[d] = m[d] / rho;
+        double qq[3] = {0, 0, 0};
+        for (int k = 0; k < Nv; ++k) {
+            const double *x = xi + (size_t)k * D;
+            double c[3], c2 = 0.0;
+            for (int d = 0; d < D; ++d) {
+                c[d] = x[d] - U[d];
+                c2 += c[d] * c[d];
+            }
+            for (int d = 0; d < D; ++d) qq[d] += 0.5 * w[k] * c[d] * (c2 * G[k] + (H ? H[k] : 0.0));
+        }
+        for (int d = 0; d < D; ++d) q[d] = qq[d];
+    }
+}
+
+void om_moments(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
+                double *Wc, double *q)
+{
+    int nA = nArr(D);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < Nc; ++i)
+        cell_moments(D, Nv, xi, w, f + (size_t)i * nA * Nv, Wc + (size_t)i * (D + 2),
+                     q ? q + (size_t)i * D : NULL);
+}
+
+/* ---- cell -> face slots ------------------------------------------------- */
+
+typedef struct {
+    int n;
+    int face[MAXS];
+    int sgn[MAXS];   /* +1: cell is L (An points outward), -1: cell is R */
+} slots_t;
+
+static slots_t *build_slots(const om_mesh *m)
+{
+    slots_t *S = (slots_t *)calloc((size_t)m->Nc, sizeof(slots_t));
+    for (int f = 0; f < m->Nf; ++f) {
+        int L = m->faceL[f], R = m->faceR[f];
+        slots_t *s = &S[L];
+        s->face[s->n] = f;
+        s->sgn[s->n] = +1;
+        s->n++;
+        if (R >= 0) {
+            s = &S[R];
+            s->face[s->n] = f;
+            s->sgn[s->n] = -1;
+            s->n++;
+        }
+    }
+    return S;
+}
+
+/* offset from the centre of cell i to the centre of its face in slot s */
+static const double *slot_r(const om_mesh *m, const slots_t *S, int i, int s)
+{
+    int f = S[i].face[s];
+    return S[i].sgn[s] > 0 ? m->rL + (size_t)f * m->D : m->rR + (size_t)f * m->D;
+}
+
+static int slot_nb(const om_mesh *m, const slots_t *S, int i, int s)
+{
+    int f = S[i].face[s];
+    return S[i].sgn[s] > 0 ? m->faceR[f] : m->faceL[f];
+}
+
+/* Δt from the CFL number (reading R5): min over cells and nodes of
+ * |V_i| / sum_faces max(xi_k . An_out, 0).  Returns that minimum (Δt / CFL). */
+double om_dt_unit(const om_mesh *m, int Nv, const double *xi)
+{
+    int D = m->D;
+    slots_t *S = build_slots(m);
+    double best = INFINITY;
+    for (int i = 0; i < m->Nc; ++i) {
+        for (int k = 0; k < Nv; ++k) {
+            const double *x = xi + (size_t)k * D;
+            double sum = 0.0;
+            for (int s = 0; s < S[i].n; ++s) {
+                const double *a = m->An + (size_t)S[i].face[s] * D;
+                double sn = 0.0;
+                for (int d = 0; d < D; ++d) sn += x[d] * a[d];
+                sn *= S[i].sgn[s];
+                if (sn > 0.0) sum += sn;
+            }
+            if (sum > 0.0) {
+                double t = m->vol[i] / sum;
+                if (t < best) best = t;
+            }
+        }
+    }
+    free(S);
+    return best;
+}
+
+/* ---- least-squares gradient + Venkatakrishnan limiter (Sec. 2.3.3) ---- */
+
+/* Inverse of the LSQ normal matrix sum w d d^T with weights 1/|d|^2 (R6).
+ * Returns 0 when the matrix is singular (gradient taken as zero). */
+static int lsq_inverse(const om_mesh *m, const slots_t *S, int i, double *Minv)
+{
+    int D = m->D;
+    double M[9] = {0};
+    for (int s = 0; s < S[i].n; ++s) {
+        int nb = slot_nb(m, S, i, s);
+        if (nb < 0) continue;
+        int f = S[i].face[s];
+        const double *rs = S[i].sgn[s] > 0 ? m->rL + (size_t)f * D : m->rR + (size_t)f * D;
+        const double *ro = S[i].sgn[s] > 0 ? m->rR + (size_t)f * D : m->rL + (size_t)f * D;
+        double d[3], n2 = 0.0;
+        for (int a = 0; a < D; ++a) {
+            d[a] = rs[a] - ro[a];          /* x_nb - x_i */
+            n2 += d[a] * d[a];
+        }
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) M[a * D + b] += d[a] * d[b] / n2;
+    }
+    double tr = 0.0;
+    for (int a = 0; a < D; ++a) tr += M[a * D + a];
+    if (D == 2) {
+        double det = M[0] * M[3] - M[1] * M[2];
+        if (!(det > 1e-12 * tr * tr)) return 0;
+        Minv[0] = M[3] / det;
+        Minv[1] = -M[1] / det;
+        Minv[2] = -M[2] / det;
+        Minv[3] = M[0] / det;
+    } else {
+        double c00 = M[4] * M[8] - M[5] * M[7];
+        double c01 = M[5] * M[6] - M[3] * M[8];
+        double c02 = M[3] * M[7] - M[4] * M[6];
+        double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+        if (!(det > 1e-12 * tr * tr * tr)) return 0;
+        Minv[0] = c00 / det;
+        Minv[1] = (M[2] * M[7] - M[1] * M[8]) / det;
+        Minv[2] = (M[1] * M[5] - M[2] * M[4]) / det;
+        Minv[3] = c01 / det;
+        Minv[4] = (M[0] * M[8] - M[2] * M[6]) / det;
+        Minv[5] = (M[2] * M[3] - M[0] * M[5]) / det;
+        Minv[6] = c02 / det;
+        Minv[7] = (M[1] * M[6] - M[0] * M[7]) / det;
+        Minv[8] = (M[0] * M[4] - M[1] * M[3]) / det;
+    }
+    return 1;
+}
+
+/* Venkatakrishnan's limiter function, capped at 1 (R6). */
+static double venkat(double d1, double d2, double eps2)
+{
+    double num = d1 * d1 + eps2 + 2.0 * d1 * d2;
+    double den = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2;
+    double v = num / den;
+    return v < 1.0 ? v : 1.0;
+}
+
+/* ---- one explicit step (Sec. 2.3, explicit reading R1/R2) --------------- */
+
+int om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
+            double dt, const double *f_in, double *f_out, double *Wc)
+{
+    const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
+    const double h = 0.5 * dt;
+    slots_t *S = build_slots(m);
+    double *Minv = (double *)calloc((size_t)Nc * 9, sizeof(double));
+    int *lsq_ok = (int *)calloc((size_t)Nc, sizeof(int));
+    double *eps2 = (double *)malloc((size_t)Nc * sizeof(double));
+    double *grad = (double *)malloc((size_t)Nc * nA * Nv * D * sizeof(double));
+    double *lim = (double *)malloc((size_t)Nc * nA * Nv * sizeof(double));
+    double *phi = (double *)malloc((size_t)Nf * nA * Nv * sizeof(double));
+    double *F = (double *)calloc((size_t)Nf * NW, sizeof(double));
+    int bad = 0;
+
+    for (int i = 0; i < Nc; ++i) {
+        lsq_ok[i] = lsq_inverse(m, S, i, Minv + (size_t)i * 9);
+        double dx = pow(m->vol[i], 1.0 / D);
+        eps2[i] = pow(g->lim_K * dx, 3.0);
+    }
+
+    /* 1. gradient and limiter of every cell, array and node */
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < Nc; ++i) {
+        for (int a = 0; a < nA; ++a) {
+            for (int k = 0; k < Nv; ++k) {
+                double phi_i = f_in[((size_t)i * nA + a) * Nv + k];
+                double b[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+                double dmax = 0.0, dmin = 0.0;
+                for (int s = 0; s < S[i].n; ++s) {
+                    int nb = slot_nb(m, S, i, s);
+                    if (nb < 0) continue;
+                    int f = S[i].face[s];
+                    const double *rs = S[i].sgn[s] > 0 ? m->rL + (size_t)f * D : m->rR + (size_t)f * D;
+                    const double *ro = S[i].sgn[s] > 0 ? m->rR + (size_t)f * D : m->rL + (size_t)f * D;
+                    double d[3], n2 = 0.0;
+                    for (int c = 0; c < D; ++c) {
+                        d[c] = rs[c] - ro[c];
+                        n2 += d[c] * d[c];
+                    }
+                    double dphi = f_in[((size_t)nb * nA + a) * Nv + k] - phi_i;
+                    for (int c = 0; c < D; ++c) b[c] += d[c] * dphi / n2;
+                    if (dphi > dmax) dmax = dphi;
+                    if (dphi < dmin) dmin = dphi;
+                }
+                double L = 1.0;
+                if (g->limiter != 0 && lsq_ok[i]) {
+                    const double *Mi = Minv + (size_t)i * 9;
+                    for (int r = 0; r < D; ++r)
+                        for (int c = 0; c < D; ++c) gr[r] += Mi[r * D + c] * b[c];
+                    if (g->limiter == 1) {
+                        for (int s = 0; s < S[i].n; ++s) {
+                            const double *r = slot_r(m, S, i, s);
+                            double d2 = 0.0;
+                            for (int c = 0; c < D; ++c) d2 += gr[c] * r[c];
+                            double psi = 1.0;
+                            if (d2 > 0.0) psi = venkat(dmax, d2, eps2[i]);
+                            else if (d2 < 0.0) psi = venkat(dmin, d2, eps2[i]);
+                            if (psi < L) L = psi;
+                        }
+                    }
+                }
+                size_t o = ((size_t)i * nA + a) * Nv + k;
+                for (int c = 0; c < D; ++c) grad[o * D + c] = gr[c];
+                lim[o] = L;
+            }
+        }
+    }
+
+    /* 2. interface distribution and flux of every face */
+#pragma omp parallel for schedule(static) reduction(|:bad)
+    for (int f = 0; f < Nf; ++f) {
+        const int L = m->faceL[f], R = m->faceR[f];
+        const double *An = m->An + (size_t)f * D;
+        double *pf = phi + (size_t)f * nA * Nv;
+        /* foot value at x_f - xi h from the upwind cell (C = L if xi.n >= 0) */
+        for (int k = 0; k < Nv; ++k) {
+            const double *x = xi + (size_t)k * D;
+            double sn = 0.0;
+            for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+            int C;
+            const double *r;
+            if (sn >= 0.0) { C = L; r = m->rL + (size_t)f * D; }
+            else if (R >= 0) { C = R; r = m->rR + (size_t)f * D; }
+            else { for (int a = 0; a < nA; ++a) pf[a * Nv + k] = 0.0; continue; }
+            for (int a = 0; a < nA; ++a) {
+                size_t o = ((size_t)C * nA + a) * Nv + k;
+                double dot = 0.0;
+                for (int d = 0; d < D; ++d) dot += grad[o * D + d] * (r[d] - x[d] * h);
+                pf[a * Nv + k] = f_in[o] + lim[o] * dot;
+            }
+        }
+        if (R >= 0) {
+            /* interface macroscopic state: Eq. (w_interface) */
+            double Wf[5];
+            cell_moments(D, Nv, xi, w, pf, Wf, NULL);
+            double rho, U[3], RT, qbar[3];
+            prim_of(D, Wf, &rho, U, &RT);
+            {   /* heat flux of the foot distribution, Eq. (8) about U_ij */
+                double qq[3] = {0, 0, 0};
+                for (int k = 0; k < Nv; ++k) {
+                    const double *x = xi + (size_t)k * D;
+                    double c[3], c2 = 0.0;
+                    for (int d = 0; d < D; ++d) { c[d] = x[d] - U[d]; c2 += c[d] * c[d]; }
+                    double Hk = nA == 2 ? pf[Nv + k] : 0.0;
+                    for (int d = 0; d < D; ++d) qq[d] += 0.5 * w[k] * c[d] * (c2 * pf[k] + Hk);
+                }
+                for (int d = 0; d < D; ++d) qbar[d] = qq[d];
+            }
+            if (!(rho > 0.0) || !(RT > 0.0)) bad = 1;
+            double tau = tau_of(g, rho, RT);
+            double qf[3];
+            for (int d = 0; d < D; ++d) qf[d] = tau * qbar[d] / (tau + h * g->Pr);   /* R4 */
+            double wa = tau / (tau + h), wb = h / (tau + h);                        /* Eq. equ28 */
+            for (int k = 0; k < Nv; ++k) {
+                double gG, gH;
+                shakhov(D, g->Pr, rho, U, RT, qf, xi + (size_t)k * D, &gG, &gH);
+                pf[k] = wa * pf[k] + wb * gG;
+                if (nA == 2) pf[Nv + k] = wa * pf[Nv + k] + wb * gH;
+            }
+        } else {
+            /* boundary face (R8) */
+            const double *B = m->bc + (size_t)(-1 - R) * 6;
+            int type = (int)B[0];
+            double Ub[3] = {B[2], B[3], B[4]};
+            double RTb = g->R * B[5];
+            double rb = B[1];
+            if (type == 1) {   /* isothermal diffuse wall, zero net mass flux */
+                double out = 0.0, in = 0.0;
+                for (int k = 0; k < Nv; ++k) {
+                    const double *x = xi + (size_t)k * D;
+                    double sn = 0.0;
+                    for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                    if (sn >= 0.0) out += w[k] * sn * pf[k];
+                    else in += w[k] * (-sn) * maxwell(D, 1.0, Ub, RTb, x);
+                }
+                rb = in > 0.0 ? out / in : 0.0;
+            }
+            for (int k = 0; k < Nv; ++k) {
+                const double *x = xi + (size_t)k * D;
+                double sn = 0.0;
+                for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                if (sn >= 0.0) continue;
+                double gk = maxwell(D, rb, Ub, RTb, x);
+                pf[k] = gk;
+                if (nA == 2) pf[Nv + k] = (3.0 - D) * RTb * gk;
+            }
+        }
+        /* area-weighted flux  A F = sum_k w (xi . An) psi phi */
+        double *Ff = F + (size_t)f * NW;
+        for (int k = 0; k < Nv; ++k) {
+            const double *x = xi + (size_t)k * D;
+            double sn = 0.0, x2 = 0.0;
+            for (int d = 0; d < D; ++d) { sn += x[d] * An[d]; x2 += x[d] * x[d]; }
+            double G = pf[k], H = nA == 2 ? pf[Nv + k] : 0.0;
+            Ff[0] += w[k] * sn * G;
+            for (int d = 0; d < D; ++d) Ff[1 + d] += w[k] * sn * x[d] * G;
+            Ff[D + 1] += w[k] * sn * 0.5 * (x2 * G + H);
+        }
+    }
+
+    /* 3. macroscopic predictor and collision update of every cell */
+#pragma omp parallel for schedule(static) reduction(|:bad)
+    for (int i = 0; i < Nc; ++i) {
+        double *Wi = Wc + (size_t)i * NW;
+        const double *fi = f_in + (size_t)i * nA * Nv;
+        double *fo = f_out + (size_t)i * nA * Nv;
+        double Wt[5];
+        /* explicit conservative update, R2 */
+        for (int c = 0; c < NW; ++c) {
+            double s = 0.0;
+            for (int sl = 0; sl < S[i].n; ++sl) s += S[i].sgn[sl] * F[(size_t)S[i].face[sl] * NW + c];
+            Wt[c] = Wi[c] - dt / m->vol[i] * s;
+        }
+        /* lagged heat flux of f^n (R3) */
+        double Wn[5], qn[3];
+        cell_moments(D, Nv, xi, w, fi, Wn, qn);
+        double rho, U[3], RT;
+        prim_of(D, Wt, &rho, U, &RT);
+        if (!(rho > 0.0) || !(RT > 0.0)) bad = 1;
+        double tau = tau_of(g, rho, RT);
+        for (int k = 0; k < Nv; ++k) {
+            const double *x = xi + (size_t)k * D;
+            double gG, gH;
+            shakhov(D, g->Pr, rho, U, RT, qn, x, &gG, &gH);
+            for (int a = 0; a < nA; ++a) {
+                double N = 0.0;
+                for (int sl = 0; sl < S[i].n; ++sl) {
+                    int f = S[i].face[sl];
+                    const double *An = m->An + (size_t)f * D;
+                    double sn = 0.0;
+                    for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                    N += S[i].sgn[sl] * sn * phi[((size_t)f * nA + a) * Nv + k];
+                }
+                double ge = a == 0 ? gG : gH;
+                /* diagonal of Eq. (SGS_phi): explicit transport, implicit collision (R1) */
+                fo[a * Nv + k] = (fi[a * Nv + k] / dt + ge / tau - N / m->vol[i]) / (1.0 / dt + 1.0 / tau);
+            }
+        }
+        for (int c = 0; c < NW; ++c) Wi[c] = Wt[c];
+    }
+
+    free(S); free(Minv); free(lsq_ok); free(eps2); free(grad); free(lim); free(phi); free(F);
+    return bad ? -5 : 0;
+}
+
+/* ---- adaptive criterion (Sec. 3.4) ------------------------------------- */
+
+/* M_k = max over cells of max(M1, M2) (Eqs. criterion_rho/_e/_mk), with the
+ * cell's rho, U and internal energy from the given conserved W.  The
+ * operation order is fixed: wg = w G; M1 = wg / rho;
+ * c2 = sum_d (xi_d - U_d)^2 left to right; M2 = ((0.5 wg) c2) / e_int,
+ * e_int = rho E - 0.5 (sum_d m_d m_d) / rho.  M2 uses G only (R9). */
+void om_criterion(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
+                  const double *Wc, double *M)
+{
+    int nA = nArr(D);
+    for (int k = 0; k < Nv; ++k) M[k] = -INFINITY;
+    for (int i = 0; i < Nc; ++i) {
+        const double *W = Wc + (size_t)i * (D + 2);
+        double rho = W[0];
+        double U[3], mm = 0.0;
+        for (int d = 0; d < D; ++d) {
+            U[d] = W[1 + d] / rho;
+            mm = mm + W[1 + d] * W[1 + d];
+        }
+        double eint = W[D + 1] - 0.5 * mm / rho;
+        const double *G = f + (size_t)i * nA * Nv;
+        for (int k = 0; k < Nv; ++k) {
+            double wg = w[k] * G[k];
+            double m1 = wg / rho;
+            double c2 = 0.0;
+            for (int d = 0; d < D; ++d) {
+                double c = xi[(size_t)k * D + d] - U[d];
+                c2 = c2 + c * c;
+            }
+            double m2 = ((0.5 * wg) * c2) / eint;
+            double mk = m1 > m2 ? m1 : m2;
+            if (mk > M[k]) M[k] = mk;
+        }
+    }
+}
+
+/* ---- marks and the new tree (Sec. 3.1, 3.4; readings R10, R11, R14) ---- */
+/* Split a leaf when s*M_k > C1 and its level < max_refine.  Merge 2^D
+ * sibling leaves into their parent when all of them satisfy s*M < C2 (their
+ * level >= 1).  New order is depth first: a kept leaf emits itself, a split
+ * leaf its children in digit order, a merged group its parent.  src/kind
+ * give, per new node, the old node it copies or the first of the 2^D old
+ * siblings it averages.  Returns the new count, or -1 if it exceeds cap. */
+int om_adapt_tree(int D, int Nv, const int *level, const int *base, const unsigned *key,
+                  const double *M, double s, double C1, double C2, int max_refine, int cap,
+                  int *nlevel, int *nbase, unsigned *nkey, int *src, int *kind)
+{
+    const int nch = 1 << D;
+    int n = 0;
+    int k = 0;
+    while (k < Nv) {
+        int group = 0;
+        if (level[k] >= 1 && (key[k] & (unsigned)(nch - 1)) == 0u && k + nch <= Nv) {
+            group = 1;
+            for (int c = 0; c < nch; ++c) {
+                int kk = k + c;
+                if (level[kk] != level[k] || base[kk] != base[k] || key[kk] != key[k] + (unsigned)c ||
+                    !(s * M[kk] < C2))
+                    group = 0;
+            }
+        }
+        if (group) {
+            if (n + 1 > cap) return -1;
+            nlevel[n] = level[k] - 1;
+            nbase[n] = base[k];
+            nkey[n] = key[k] >> D;
+            src[n] = k;
+            kind[n] = OM_MERGE;
+            n++;
+            k += nch;
+            continue;
+        }
+        if (s * M[k] > C1 && level[k] < max_refine) {
+            if (n + nch > cap) return -1;
+            for (int c = 0; c < nch; ++c) {
+                nlevel[n] = level[k] + 1;
+                nbase[n] = base[k];
+                nkey[n] = (key[k] << D) | (unsigned)c;
+                src[n] = k;
+                kind[n] = OM_COPY;
+                n++;
+            }
+        } else {
+            if (n + 1 > cap) return -1;
+            nlevel[n] = level[k];
+            nbase[n] = base[k];
+            nkey[n] = key[k];
+            src[n] = k;
+            kind[n] = OM_COPY;
+            n++;
+        }
+        k++;
+    }
+    return n;
+}
+
+/* Consanguinity reconstruction (Sec. 3.2): a child copies its parent, a
+ * merged parent takes the mean of its children, summed pairwise
+ * ((c0 + c1) + (c2 + c3)) / 4 in 2D and the three-level pairwise sum / 8 in 3D. */
+void om_remap(int D, int Nc, int Nv_old, const double *f_old, int Nv_new,
+              const int *src, const int *kind, double *f_new)
+{
+    int nA = nArr(D);
+    for (int i = 0; i < Nc; ++i) {
+        for (int a = 0; a < nA; ++a) {
+            const double *fo = f_old + ((size_t)i * nA + a) * Nv_old;
+            double *fn = f_new + ((size_t)i * nA + a) * Nv_new;
+            for (int k = 0; k < Nv_new; ++k) {
+                const double *c = fo + src[k];
+                if (kind[k] == OM_COPY) fn[k] = c[0];
+                else if (D == 2) fn[k] = ((c[0] + c[1]) + (c[2] + c[3])) * 0.25;
+                else fn[k] = (((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]))) * 0.125;
+            }
+        }
+    }
+}
+
+/* Conservation correction (Sec. 3.3): f = f' + g^eq(W) - g^eq(W'), with
+ * W' the discrete moments of f'; repeated `iters` times (R12).  Returns the
+ * largest remaining relative gap |M[f] - W| over cells and components
+ * (density relative to rho, momentum to rho sqrt(2 R T) + |rho U|, energy
+ * relative to rho E). */
+double om_correct(int D, int Nc, int Nv, const double *xi, const double *w, double R,
+                  int iters, const double *Wc_target, double *f)
+{
+    int nA = nArr(D);
+    double worst = 0.0;
+    (void)R;
+    for (int i = 0; i < Nc; ++i) {
+        const double *Wt = Wc_target + (size_t)i * (D + 2);
+        double *fi = f + (size_t)i * nA * Nv;
+        double rho, U[3], RT;
+        prim_of(D, Wt, &rho, U, &RT);
+        for (int it = 0; it < iters; ++it) {
+            double Wp[5];
+            cell_moments(D, Nv, xi, w, fi, Wp, NULL);
+            double rp, Up[3], RTp;
+            prim_of(D, Wp, &rp, Up, &RTp);
+            for (int k = 0; k < Nv; ++k) {
+                const double *x = xi + (size_t)k * D;
+                double ga = maxwell(D, rho, U, RT, x);
+                double gb = maxwell(D, rp, Up, RTp, x);
+                fi[k] += ga - gb;
+                if (nA == 2) fi[Nv + k] += (3.0 - D) * (RT * ga - RTp * gb);
+            }
+        }
+        double Wp[5];
+        cell_moments(D, Nv, xi, w, fi, Wp, NULL);
+        double mref = 0.0;
+        for (int d = 0; d < D; ++d) mref += Wt[1 + d] * Wt[1 + d];
+        mref = sqrt(mref) + rho * sqrt(2.0 * RT);
+        double e = fabs(Wp[0] - Wt[0]) / fabs(Wt[0]);
+        for (int d = 0; d < D; ++d) {
+            double t = fabs(Wp[1 + d] - Wt[1 + d]) / mref;
+            if (t > e) e = t;
+        }
+        double t = fabs(Wp[D + 1] - Wt[D + 1]) / fabs(Wt[D + 1]);
+        if (t > e) e = t;
+        if (e > worst || e != e) worst = e;
+    }
+    return worst;
+}

@@ -1,0 +1,361 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed-form
+Gaussian integrals, exact limits of the scheme (free transport, continuum),
+conservation laws, exact dyadic arithmetic of the tree, and printed values.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2212_05645_gb300 import workloads as wl
+
+R = 0.5
+
+
+def uniform_forest(D, n, lo, hi):
+    nb = np.array([n] * D, np.int32)
+    level, base, key = O.forest_base(D, nb)
+    xi, w = O.forest_geom(D, nb, [lo] * D, [hi] * D, level, base, key)
+    return nb, level, base, key, xi, w
+
+
+# ---------------------------------------------------------------- velocity tree
+def test_forest_weights_dyadic_and_dfs_order():
+    """Sec. 3 mid-point quadrature: children tile their parent exactly, node =
+    element centre, and the leaf order is depth first."""
+    D = 2
+    nb = np.array([3, 2], np.int32)
+    vlo, vhi = np.array([-1.5, -0.7]), np.array([2.5, 1.3])
+    level, base, key = O.forest_base(D, nb)
+    xi0, w0 = O.forest_geom(D, nb, vlo, vhi, level, base, key)
+    assert w0.sum() == pytest.approx((vhi - vlo).prod(), rel=0, abs=1e-15)
+    # split node 4 twice (child 3 of it again): M chosen so exactly those split
+    M = np.zeros(len(level)); M[4] = 10.0
+    l1, b1, k1, src, kind = O.adapt_tree(D, level, base, key, M, 1.0, 1.0, 1e-9, 5)
+    assert len(l1) == 6 - 1 + 4
+    xi1, w1 = O.forest_geom(D, nb, vlo, vhi, l1, b1, k1)
+    ch = np.where(l1 == 1)[0]
+    assert np.all(b1[ch] == 4) and list(k1[ch]) == [0, 1, 2, 3]
+    assert w1[ch].sum() == w0[4]                      # exact: dyadic pieces
+    assert np.allclose(xi1[ch].mean(0), xi0[4], rtol=0, atol=4e-16)   # children centroid = parent centre
+    # child digit c = o0 | o1 << 1: child 1 is to the right of child 0, child 2 above it
+    assert xi1[ch[1], 0] > xi1[ch[0], 0] and xi1[ch[1], 1] == xi1[ch[0], 1]
+    assert xi1[ch[2], 1] > xi1[ch[0], 1] and xi1[ch[2], 0] == xi1[ch[0], 0]
+    M2 = np.zeros(len(l1)); M2[ch[3]] = 10.0
+    l2, b2, k2, _, _ = O.adapt_tree(D, l1, b1, k1, M2, 1.0, 1.0, 1e-9, 5)
+    xi2, w2 = O.forest_geom(D, nb, vlo, vhi, l2, b2, k2)
+    assert w2.sum() == pytest.approx((vhi - vlo).prod(), rel=1e-15)
+    # depth-first order: keys left-aligned to depth 2 increase within a base cell
+    Lmax = 2
+    aligned = k2.astype(np.int64) << (D * (Lmax - l2.astype(np.int64)))
+    for b in np.unique(b2):
+        sel = b2 == b
+        assert np.all(np.diff(aligned[sel]) > 0)
+    assert np.all(np.diff(b2) >= 0)
+
+
+def test_split_then_merge_is_identity_bitwise():
+    """Consanguinity (Sec. 3.2): a split copies the parent, a merge averages
+    the children, so split followed by merge returns f bit for bit; mass is
+    unchanged by either (to round-off)."""
+    for D in (2, 3):
+        nb, level, base, key, xi, w = uniform_forest(D, 4, -3.0, 3.0)
+        rng = np.random.default_rng(0)
+        Nc = 3
+        f = rng.uniform(0.1, 1.0, size=(Nc, O.n_arrays(D), len(level)))
+        M = np.full(len(level), 10.0)
+        l1, b1, k1, s1, kd1 = O.adapt_tree(D, level, base, key, M, 1.0, 1.0, 1e-6, 3)
+        assert len(l1) == len(level) << D
+        f1 = O.remap(D, f, s1, kd1)
+        _, w1 = O.forest_geom(D, nb, [-3.0] * D, [3.0] * D, l1, b1, k1)
+        M1 = np.zeros(len(l1))
+        l2, b2, k2, s2, kd2 = O.adapt_tree(D, l1, b1, k1, M1, 1.0, 1.0, 1e-6, 3)
+        assert np.array_equal(l2, level) and np.array_equal(k2, key) and np.array_equal(b2, base)
+        f2 = O.remap(D, f1, s2, kd2)
+        assert np.array_equal(f2, f)
+        m0 = (f[:, 0] * w).sum(-1)
+        m1 = (f1[:, 0] * w1).sum(-1)
+        assert np.allclose(m1, m0, rtol=4e-16 * len(level), atol=0)
+
+
+def test_merge_rules_root_and_incomplete_groups():
+    """Sec. 3.1: level-0 nodes never merge, and only complete sibling groups of
+    leaves with M < C2 merge (one sibling above C2 blocks the group)."""
+    D = 2
+    nb, level, base, key, xi, w = uniform_forest(D, 2, -1.0, 1.0)
+    M = np.zeros(len(level)); M[0] = 10.0; M[3] = 10.0
+    l1, b1, k1, _, _ = O.adapt_tree(D, level, base, key, M, 1.0, 1.0, 0.5, 4)
+    assert len(l1) == 4 + 3 + 3
+    M1 = np.zeros(len(l1))
+    first = np.where(b1 == 0)[0]
+    last = np.where(b1 == 3)[0]
+    M1[first[2]] = 0.7                      # blocks the merge of base cell 0's children
+    l2, b2, k2, _, kind = O.adapt_tree(D, l1, b1, k1, M1, 1.0, 1.0, 0.5, 4)
+    assert list(l2[b2 == 0]) == [1, 1, 1, 1]      # kept
+    assert list(l2[b2 == 3]) == [0]               # merged
+    assert list(l2[b2 == 1]) == [0] and list(l2[b2 == 2]) == [0]   # roots stay
+    assert kind[np.where(b2 == 3)[0][0]] == O.OM_MERGE
+
+
+# ---------------------------------------------------------------- equilibria
+@pytest.mark.parametrize("D", [2, 3])
+def test_discrete_maxwellian_reproduces_moments(D):
+    """Eq. (Maxwell_df) with Eq. (7): on a uniform mesh with h = sigma/4 over
+    +-9 sigma, the mid-point moments equal the closed-form Gaussian integrals
+    rho, rho U, rho U^2/2 + (3/2) rho R T to 1e-10 (the rule is spectrally
+    accurate for a Gaussian), and the heat flux (Eq. 8) vanishes."""
+    rho, U, T = 1.3, np.array([0.31, -0.17, 0.05])[:D], 1.7
+    sig = math.sqrt(R * T)
+    n = 72 if D == 2 else 40
+    lo, hi = -9 * sig, 9 * sig
+    if D == 3:
+        lo, hi = -7 * sig, 7 * sig
+    _, _, _, _, xi, w = uniform_forest(D, n, lo, hi)
+    f = O.maxwell_init(D, xi, np.concatenate([[rho], U, [T]])[None, :])
+    Wc, q = O.moments(D, xi, w, f)
+    E = 0.5 * rho * (U @ U) + 1.5 * rho * R * T
+    tol = 1e-10 if D == 2 else 5e-8
+    assert Wc[0, 0] == pytest.approx(rho, rel=tol)
+    assert np.allclose(Wc[0, 1:1 + D], rho * U, rtol=0, atol=tol * rho * sig)
+    assert Wc[0, D + 1] == pytest.approx(E, rel=tol)
+    assert np.allclose(q[0], 0.0, atol=tol * rho * sig ** 3)
+
+
+def test_shakhov_moments():
+    """Eqs. (14)-(17), 2D reduced G/H: the Shakhov correction adds no mass,
+    momentum or energy, and the heat flux of (g^G, g^H) is (1 - Pr) q."""
+    D, Pr = 2, 2.0 / 3.0
+    rho, U, T = 0.9, np.array([0.2, -0.4]), 1.4
+    q = np.array([0.05, -0.03])
+    sig = math.sqrt(R * T)
+    _, _, _, _, xi, w = uniform_forest(D, 96, -10 * sig, 10 * sig)
+    gG, gH = O.shakhov_field(D, xi, Pr, rho, U, R * T, q)
+    f = np.stack([gG, gH])[None]
+    Wc, qq = O.moments(D, xi, w, f)
+    assert Wc[0, 0] == pytest.approx(rho, rel=1e-11)
+    assert np.allclose(Wc[0, 1:3], rho * U, atol=1e-11)
+    assert Wc[0, 3] == pytest.approx(0.5 * rho * U @ U + 1.5 * rho * R * T, rel=1e-11)
+    assert np.allclose(qq[0], (1 - Pr) * q, rtol=1e-9, atol=1e-13)
+    # H part alone carries the out-of-plane energy rho R T (Eq. 16, L = 1)
+    assert (w * gH).sum() == pytest.approx(rho * R * T, rel=1e-11)
+
+
+def test_mu_from_Kn():
+    """Eq. (4)-(5) with rho = T = L = 1, R = 1/2: the mean free path of the
+    reference state equals Kn."""
+    for Kn, om in [(0.075, 0.81), (1.0, 0.5), (0.0169, 0.74)]:
+        mu = O.mu_ref_from_Kn(Kn, om, R)
+        lam = 2 * mu * (5 - 2 * om) * (7 - 2 * om) / (15 * math.sqrt(2 * math.pi * R))
+        assert lam == pytest.approx(Kn, rel=1e-15)
+    # hard-sphere value: mu = 5 sqrt(pi) Kn / 16 when R = 1/2, omega = 1/2
+    assert O.mu_ref_from_Kn(1.0, 0.5, R) == pytest.approx(5 * math.sqrt(math.pi) / 16, rel=1e-15)
+
+
+# ---------------------------------------------------------------- time step
+def test_dt_unit_cartesian_closed_form():
+    """R5 on a uniform Cartesian mesh: min dx dy / (|xi_x| dy + |xi_y| dx)."""
+    m = wl.cartesian_mesh((4, 3), (1.0, 0.6), periodic=(True, True))
+    _, _, _, _, xi, w = uniform_forest(2, 6, -2.0, 2.0)
+    mh = O.MeshHandle(m)
+    dx, dy = 0.25, 0.2
+    ref = min(dx * dy / (abs(x) * dy + abs(y) * dx) for x, y in xi)
+    assert O.dt_unit(mh, xi) == pytest.approx(ref, rel=1e-15)
+
+
+# ---------------------------------------------------------------- step limits
+def _box(n, D=2, periodic=True):
+    return wl.cartesian_mesh((n,) * D, (1.0,) * D, periodic=(periodic,) * D)
+
+
+def test_free_transport_limit_first_order():
+    """tau -> infinity (Kn = 1e14), first-order reconstruction: the step is the
+    first-order upwind update of free transport,
+    f_i - dt/dx (xi_x^+ (f_i - f_W) + xi_x^- (f_E - f_i) + same in y)."""
+    n = 4
+    m = _box(n)
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=1e14, limiter=0)
+    _, _, _, _, xi, w = uniform_forest(2, 2, -1.0, 1.0)   # 4 nodes at (+-0.5, +-0.5)
+    rng = np.random.default_rng(3)
+    Wp = np.column_stack([1 + 0.2 * rng.random(n * n), 0.1 * rng.standard_normal((n * n, 2)),
+                          1 + 0.2 * rng.random(n * n)])
+    f = O.maxwell_init(2, xi, Wp) * (1 + 0.3 * rng.random((n * n, 2, 4)))
+    Wc, _ = O.moments(2, xi, w, f)
+    dt = 0.05
+    fo = O.step(mh, g, xi, w, dt, f, Wc)
+    F = f.reshape(n, n, 2, 4)                 # [y][x][array][node]
+    exp = np.empty_like(F)
+    dx = 1.0 / n
+    for k, (ux, uy) in enumerate(xi):
+        for a in range(2):
+            u = F[:, :, a, k]
+            Wn = np.roll(u, 1, axis=1); En = np.roll(u, -1, axis=1)
+            Sn = np.roll(u, 1, axis=0); Nn = np.roll(u, -1, axis=0)
+            exp[:, :, a, k] = u - dt / dx * (max(ux, 0) * (u - Wn) + min(ux, 0) * (En - u)
+                                             + max(uy, 0) * (u - Sn) + min(uy, 0) * (Nn - u))
+    assert np.allclose(fo.reshape(n, n, 2, 4), exp, rtol=1e-13, atol=1e-15)
+
+
+def _advect_error(n, limiter, T_end=0.25, profile="smooth"):
+    """Collisionless transport of a scalar profile with one velocity node."""
+    m = _box(n)
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=1e14, limiter=limiter)
+    v = np.array([0.5, 0.25])
+    xi, w = O.forest_geom(2, np.array([1, 1], np.int32), v - 0.5, v + 0.5,
+                          np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros(1, np.uint32))
+    x, y = m.xc[:, 0], m.xc[:, 1]
+
+    def prof(x, y):
+        if profile == "smooth":
+            return 1.0 + 0.5 * np.sin(2 * math.pi * x) * np.sin(2 * math.pi * y)
+        return 1.0 + 1.0 * ((np.mod(x, 1.0) > 0.25) & (np.mod(x, 1.0) < 0.75))
+
+    G = prof(x, y)
+    f = np.stack([G, 0.5 * G], axis=1)[:, :, None].copy()
+    Wc, _ = O.moments(2, xi, w, f)
+    nsteps = int(round(T_end / (0.4 / n / (abs(v).sum()))))
+    dt = T_end / nsteps
+    for _ in range(nsteps):
+        f = O.step(mh, g, xi, w, dt, f, Wc)
+    exact = prof(x - v[0] * T_end, y - v[1] * T_end)
+    return f[:, 0, 0], exact
+
+
+def test_second_order_unlimited_transport():
+    """Sec. 2.3.3 reconstruction phi_C + grad phi_C . (x_ij - xi h - x_C): with
+    the unlimited least-squares gradient, free transport of a smooth profile
+    converges at second order (observed rate > 1.8)."""
+    errs = []
+    for n in (16, 32):
+        num, ex = _advect_error(n, limiter=2)
+        errs.append(np.abs(num - ex).max())
+    rate = math.log2(errs[0] / errs[1])
+    assert rate > 1.8, (errs, rate)
+
+
+def test_limiter_bounds_a_step():
+    """Venkatakrishnan limiter: a square wave stays within 5% of its initial
+    range, while the unlimited reconstruction overshoots by more."""
+    num_l, _ = _advect_error(32, limiter=1, T_end=0.1, profile="step")
+    num_u, _ = _advect_error(32, limiter=2, T_end=0.1, profile="step")
+    over_l = max(num_l.max() - 2.0, 1.0 - num_l.min())
+    over_u = max(num_u.max() - 2.0, 1.0 - num_u.min())
+    assert over_l < 0.05 and over_u > 2 * over_l, (over_l, over_u)
+
+
+def test_continuum_limit_gives_shakhov_of_predicted_state():
+    """tau -> 0 (Kn = 1e-10): f^{n+1} equals the Shakhov equilibrium of the
+    predicted W~ with the lagged heat flux of f^n (Eq. SGS_phi diagonal, R3)."""
+    n = 4
+    m = _box(n)
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=1e-10, limiter=1)
+    _, _, _, _, xi, w = uniform_forest(2, 12, -3.0, 3.0)
+    W = wl.sweep_W(m)
+    f = O.maxwell_init(2, xi, W, amp=1e-2, seed=5)
+    Wc, _ = O.moments(2, xi, w, f)
+    _, qn = O.moments(2, xi, w, f)
+    dt = 0.5 * O.dt_unit(mh, xi)
+    fo = O.step(mh, g, xi, w, dt, f, Wc)
+    for i in range(m.Nc):
+        rho = Wc[i, 0]; U = Wc[i, 1:3] / rho
+        RT = (Wc[i, 3] - 0.5 * rho * U @ U) / (1.5 * rho)
+        gG, gH = O.shakhov_field(2, xi, g.Pr, rho, U, RT, qn[i])
+        assert np.allclose(fo[i, 0], gG, rtol=0, atol=1e-7 * gG.max())
+        assert np.allclose(fo[i, 1], gH, rtol=0, atol=1e-7 * gH.max())
+
+
+# ---------------------------------------------------------------- conservation
+def test_uniform_stream_stays_uniform():
+    """Periodic box, f = discrete Maxwellian on a symmetric uniform velocity
+    mesh: W is unchanged bit for bit (face fluxes cancel exactly) and f to
+    1e-13 (its discrete moments equal W to round-off)."""
+    m = _box(6)
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=0.05)
+    sig = math.sqrt(R)
+    _, _, _, _, xi, w = uniform_forest(2, 40, -10 * sig, 10 * sig)
+    Wp = np.tile([1.0, 0.0, 0.0, 1.0], (m.Nc, 1))
+    f = O.maxwell_init(2, xi, Wp)
+    Wc, _ = O.moments(2, xi, w, f)
+    W0 = Wc.copy()
+    fo = O.step(mh, g, xi, w, 0.5 * O.dt_unit(mh, xi), f, Wc)
+    assert np.array_equal(Wc, W0)
+    assert np.allclose(fo, f, rtol=0, atol=1e-13 * f.max())
+
+
+def test_conservation_periodic_and_walls():
+    """Conservative update (R2): periodic box conserves sum |V| W to 1e-14
+    per step; the closed cavity with diffuse walls (zero net mass flux, R8)
+    conserves mass to 1e-12 over 60 steps."""
+    wb = wl.sweep_box((8, 8), base=(10, 10), max_refine=1)
+    rb = O.Run(wb)
+    rb.init_field(amp=1e-3)
+    tot0 = (rb.Wc * wb.mesh.vol[:, None]).sum(0)
+    dt = rb.dt()
+    for _ in range(3):
+        rb.step(dt)
+    tot = (rb.Wc * wb.mesh.vol[:, None]).sum(0)
+    assert np.allclose(tot, tot0, rtol=1e-14, atol=1e-14)
+
+    wc = wl.cavity(n=8)
+    rc = O.Run(wc)
+    rc.init_field()
+    m0 = (rc.Wc[:, 0] * wc.mesh.vol).sum()
+    dt = rc.dt()
+    for _ in range(60):
+        rc.step(dt)
+    m1 = (rc.Wc[:, 0] * wc.mesh.vol).sum()
+    assert abs(m1 - m0) / m0 < 1e-12
+
+
+def test_correction_restores_moments():
+    """Sec. 3.3: after a consanguinity remap the moments drift (energy on a
+    split, momentum on a merge); f' + g^eq(W) - g^eq(W') iterated restores
+    them, the gap shrinking every pass, below 1e-13 after 8 passes."""
+    D = 2
+    nb, level, base, key, xi, w = uniform_forest(D, 12, -3.0, 3.0)
+    Wp = np.array([[1.0, 0.2, -0.1, 1.0], [0.8, -0.3, 0.4, 1.3]])
+    f = O.maxwell_init(D, xi, Wp, amp=1e-2, seed=7)
+    Wc, _ = O.moments(D, xi, w, f)
+    M = np.zeros(len(level)); M[::3] = 10.0
+    l1, b1, k1, s1, kd1 = O.adapt_tree(D, level, base, key, M, 1.0, 1.0, 1e-6, 3)
+    xi1, w1 = O.forest_geom(D, nb, [-3.0] * D, [3.0] * D, l1, b1, k1)
+    f1 = O.remap(D, f, s1, kd1)
+    W1, _ = O.moments(D, xi1, w1, f1)
+    assert np.allclose(W1[:, 0], Wc[:, 0], rtol=1e-14)            # mass kept by consanguinity
+    assert np.abs(W1[:, 3] - Wc[:, 3]).max() > 1e-5               # energy is not
+    gaps = []
+    for it in range(0, 4):
+        g = f1.copy()
+        gaps.append(O.correct(D, xi1, w1, Wc, g, iters=it))
+    assert all(gaps[i + 1] < gaps[i] for i in range(3)), gaps
+    g = f1.copy()
+    assert O.correct(D, xi1, w1, Wc, g, iters=8) < 1e-13
+
+
+# ---------------------------------------------------------------- criterion
+def test_criterion_maxwellian_closed_form_and_max_over_cells():
+    """Eqs. (criterion_rho/_e/_mk): for a Maxwellian cell M1 = w g / rho and
+    M2 = w g c^2 / (3 rho R T) (e_int = 3/2 rho R T); M_k is the max over cells,
+    so the criterion of a union of cells is the elementwise max of the parts."""
+    D = 2
+    _, _, _, _, xi, w = uniform_forest(D, 8, -3.0, 3.0)
+    Wp = np.array([[1.0, 0.3, 0.0, 1.0], [2.0, -0.5, 0.2, 0.7], [0.5, 0.0, 0.0, 2.0]])
+    f = O.maxwell_init(D, xi, Wp)
+    Wc = O.conserved_from_primitive(D, Wp)
+    M = O.criterion(D, xi, w, f, Wc)
+    ref = np.full(len(w), -np.inf)
+    for (rho, ux, uy, T) in Wp:
+        c2 = (xi[:, 0] - ux) ** 2 + (xi[:, 1] - uy) ** 2
+        g = rho / (2 * math.pi * R * T) * np.exp(-c2 / (2 * R * T))
+        m1 = w * g / rho
+        m2 = w * g * c2 / (3 * rho * R * T)
+        ref = np.maximum(ref, np.maximum(m1, m2))
+    assert np.allclose(M, ref, rtol=1e-13, atol=0)
+    parts = np.maximum(O.criterion(D, xi, w, f[:1], Wc[:1]), O.criterion(D, xi, w, f[1:], Wc[1:]))
+    assert np.array_equal(parts, M)
