@@ -1,0 +1,365 @@
+"""Benchmark of the UGKS + adaptive-velocity-space hot path on GB300.
+
+Workload (default): supersonic cylinder, O-mesh 128 radial x 96
+circumferential cells, Ma 5, Kn 0.1, isothermal wall, global quadtree over
+[-15, 15]^2 sqrt(R T_inf) with base 24x24 and up to 4 levels, mixed precision
+(f in FP32, moment sums, wall balance and correction in FP64).
+
+One benchmark step = one pass of the whole hot path: `nu` (= 50, the
+adaptation interval) explicit UGKS steps followed by one adaptation of the
+velocity mesh (moments, criterion, marks + scan compaction, consanguinity
+remap, conservation correction).  Metric: cell-velocity-node updates per
+second, sum over the UGKS steps of Nc * Nv divided by the time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs its own replica (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-velocity-node updates/s"
+UNIT = "cell-node updates/s"
+NU = 50
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--nu", type=int, default=NU)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
+    ap.add_argument("--workload", default="cylinder", choices=sorted(WORKLOADS),
+                    help="cylinder (the benchmark case) or a smaller case for profiling")
+    return ap.parse_args()
+
+
+WORKLOADS = {
+    # supersonic cylinder, O-mesh 128 radial x 96 circumferential (the benchmark case)
+    "cylinder": dict(),
+    # same flow and velocity mesh on the inner 64 radial rows (profiling case, f > L2)
+    "cylinder-r64": dict(n_r=64),
+}
+_WL = "cylinder"
+
+
+def _workload(precision="mixed"):
+    from paper_2212_05645_gb300 import workloads as wl
+    return wl.cylinder(precision=precision, **WORKLOADS[_WL])
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- peaks
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic(kind, Nc, Nv):
+    """dram bytes per launch of the step kernel from the committed ncu
+    summary, scaled to this launch by cell-nodes; None when the kernel source
+    changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "step_kernel_dram.json")
+    src = os.path.join(ROOT, "paper_2212_05645_gb300", "csrc", "avs_step.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(kind)
+    if not e or e.get("src_sha") != sha:
+        return None
+    return e["dram_bytes"] * (Nc * Nv) / (e["Nc"] * e["Nv"])
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(seconds=12.0, nu=NU):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload: the first 12 radial rows (1152 cells) of the O-mesh with the
+    full velocity tree; UGKS steps until about `seconds` of CPU time."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    import oracle as O
+    from paper_2212_05645_gb300 import workloads as wl
+    w = wl.cylinder(n_r=12, precision="fp64")
+    r = O.Run(w)
+    r.init_field()
+    dt = r.dt()
+    r.step(dt)                                     # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        r.step(dt)
+        n += 1
+        if time.perf_counter() - t0 > seconds or n >= nu:
+            break
+    el = time.perf_counter() - t0
+    val = w.mesh.Nc * r.Nv * n / el
+    return {"value": val, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+            "sample": f"{n} UGKS steps of the first 12 radial rows ({w.mesh.Nc} cells) x {r.Nv} velocity nodes, FP64",
+            "seconds": el}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(seconds=1.0, nu=2)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(seconds=8.0, nu=args.nu))
+    el = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    w = _workload()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "oracle_sample": vals[0]["sample"]},
+            "cpu_baseline": {"kind": "oracle", "cores": vals[0]["cores"], "sample": vals[0]["sample"], "value": v,
+                             "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2212_05645_gb300 import avs as A
+    from paper_2212_05645_gb300 import build as B
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    B.build()
+    stream = torch.cuda.current_stream()
+    w = _workload("mixed")
+    g = A.AVS(w, precision="mixed", stream=stream.cuda_stream)
+    g.init_field()
+    Nc = g.Nc
+    nu = args.nu
+
+    def bench_step(ctx, updates):
+        ctx.step(nu)
+        updates.append(Nc * ctx.Nv * nu)
+        ctx.adapt()
+
+    upd = []
+    for _ in range(args.warmup):
+        bench_step(g, upd)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    upd = []
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    step_cells = []
+    barrier()
+    torch.cuda.synchronize()
+    l0 = g.launches
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for j in range(args.steps):
+        ev_s[j].record(stream)
+        g.step(nu)
+        ev_e[j].record(stream)
+        upd.append(Nc * g.Nv * nu)
+        step_cells.append(Nc * g.Nv)
+        g.adapt()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = g.launches - l0
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
+    my_updates = float(sum(upd))
+    t_max = ms
+    tot_updates = my_updates
+    if ws > 1:
+        tt = torch.tensor([ms, my_updates], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = tt.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        t_max, tot_updates = float(mx[0]), float(sm[1])
+    value = tot_updates / (t_max * 1e-3)
+
+    # roofline of the step kernel (dominant): 1 read + 1 write of G and H in FP32
+    bytes_per_cn = 2 * g.NA * 4
+    kern_ms = sum(step_ms) / (args.steps * nu)
+    cn_per_launch = statistics.mean(step_cells)
+    achieved = bytes_per_cn * cn_per_launch / (kern_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    traffic = _traffic("mixed", Nc, cn_per_launch / Nc)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_step<2,float>", "peak_source": peak_kind,
+            "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
+            "peak_spec_gbs": 8000.0, "frac_of_spec": achieved / 8000.0}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 or ws > 1:
+        Wp = torch.from_numpy(np.ascontiguousarray(w.W_init)).pin_memory()
+        Wout = torch.zeros((Nc, w.D + 2), dtype=torch.float64).pin_memory()
+        ke = max(2, args.steps // 2)
+        torch.cuda.synchronize()
+        e_upd = []
+        te0 = time.perf_counter()
+        for _ in range(ke):
+            g.init_field(Wp)          # h2d of the step's input W
+            g.step(nu)
+            e_upd.append(Nc * g.Nv * nu)
+            g.adapt()
+            g.moments(out_W=Wout)     # d2h of the step's result
+        torch.cuda.synchronize()
+        te = time.perf_counter() - te0
+        e2e = {"value": sum(e_upd) / te, "unit": UNIT, "h2d_bytes_per_step": int(Wp.numel() * 8),
+               "d2h_bytes_per_step": int(Wout.numel() * 8)}
+
+    # plain FP64 GPU form on the same workload (same definition of a step)
+    fp64 = None
+    if not args.no_fp64:
+        gd = A.AVS(w, precision="fp64", stream=stream.cuda_stream)
+        gd.init_field()
+        u = []
+        bench_step(gd, u)
+        torch.cuda.synchronize()
+        u = []
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kd = 2
+        for _ in range(kd):
+            bench_step(gd, u)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fms = a.elapsed_time(b)
+        fp64 = {"value": sum(u) / (fms * 1e-3), "ms_per_step": fms / kd, "steps": kd}
+        gd.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        f_mb = Nc * g.NA * g.Nv * 4 / 1e6
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": w.name, "cells": Nc, "velocity_nodes": g.Nv,
+                           "ugks_steps_per_step": nu, "precision": "mixed (f FP32, sums FP64)",
+                           "l2": f"inputs larger than L2 (f = {f_mb:.0f} MB per buffer)",
+                           "parallelism": f"replicas x{ws}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "fp64_form": fp64,
+                "speedup_vs_fp64_form": (value / ws / fp64["value"]) if fp64 else None}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    global _WL
+    args = _args()
+    _WL = args.workload
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * avs.h — C ABI of the GB300 (sm_103a) library for the unified gas-kinetic
+ * scheme (UGKS) on one global adaptive velocity space (AVS), following
+ * Chen, Liu, Zhang, Zhong, Yang, Zhuo, arXiv 2212.05645.
+ *
+ * One context owns one problem on one GPU: the physical mesh, the global
+ * quadtree/octree velocity mesh, the reduced distributions f (G and H in 2D,
+ * G in 3D; Eq. 6) and the carried conserved variables W (Eq. 7).  Every call
+ * enqueues its work on the context's CUDA stream.  Calls return an
+ * avs_status and never throw; on error avs_last_error() describes it.  After
+ * AVS_ECUDA the context must be destroyed; after any other error it stays
+ * valid.  A context is not thread-safe.
+ *
+ * Pointers marked "host or device" are read or written on the host when the
+ * accompanying is_device flag is 0 and on the device (same device as the
+ * context, ordered on its stream) when it is 1.  Input pointers are borrowed
+ * for the duration of the call only.  Output buffers are owned by the caller.
+ *
+ * Layouts
+ *   f    [cell][array][node]  (array 0 = G, array 1 = H in 2D), FP64 on the ABI
+ *   Wc   [cell][D+2]          conserved: rho, rho*U (D), rho*E
+ *   Wp   [cell][D+2]          primitive: rho, U (D), T
+ *   q    [cell][D]            heat flux (Eq. 8)
+ *   xi   [node][D], w [node]  velocity node (element centre) and weight (Sec. 3)
+ */
+#ifndef AVS_H
+#define AVS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct avs_ctx avs_ctx;
+
+typedef enum {
+    AVS_OK = 0,
+    AVS_EINVAL = -1,      /* bad argument, configuration or mesh           */
+    AVS_ENOMEM = -2,      /* device or host allocation failed              */
+    AVS_ECUDA = -3,       /* CUDA runtime error; the context is unusable   */
+    AVS_ETIMEOUT = -4,    /* a bounded device wait gave up                 */
+    AVS_ENUMERIC = -5,    /* non-positive density or temperature met       */
+    AVS_ENOTCONV = -6,    /* conservation correction gap grew              */
+    AVS_ECAPACITY = -7    /* adapted velocity mesh exceeds max_nodes       */
+} avs_status;
+
+enum { AVS_FP64 = 0, AVS_MIXED = 1 };
+enum { AVS_BC_WALL = 1, AVS_BC_FARFIELD = 2 };
+enum { AVS_LIM_FIRST_ORDER = 0, AVS_LIM_VENKAT = 1, AVS_LIM_NONE = 2 };
+
+/* Run configuration.  Units: rho_inf = T_inf = L_ref = 1 and velocity unit
+ * sqrt(2 R T_inf), so R = 1/2 (paper Sec. 4.5 tables). */
+typedef struct {
+    int dim;              /* 2 or 3 (physical = velocity dimension)                        */
+    int base[3];          /* base-forest elements per velocity axis (level 0, Sec. 3.5 step 2) */
+    int max_refine;       /* largest tree level                                             */
+    double vlo[3], vhi[3];/* velocity domain                                                */
+    int precision;        /* AVS_FP64: f and all arithmetic in FP64.
+                             AVS_MIXED: f, reconstruction, flux and collision in FP32;
+                             moment sums, wall balance and correction in FP64              */
+    int learned;          /* 1: the MLP proposer restricts the criterion to a check set      */
+    double R, Pr, omega;  /* gas constant, Prandtl number (2/3), VHS exponent (Eq. 3)       */
+    double Kn;            /* Knudsen number of the reference state (Eq. 5)                  */
+    double T_ref;         /* reference temperature of the viscosity law                    */
+    double C1, C2;        /* split / merge thresholds (Sec. 3.4) on s*M_k, s = base nodes   */
+    double W_inf[5];      /* primitive free stream rho, U (dim), T for the step-0 AVS        */
+    int limiter;          /* AVS_LIM_*; Venkatakrishnan with eps^2 = (lim_K dx)^3           */
+    double lim_K;
+    int corr_iters;       /* passes of the conservation correction (Sec. 3.3)               */
+    int max_nodes;        /* velocity-node capacity; 0 = 8x the step-0 count                */
+    int learned_full_every; /* learned form: run the full criterion every n-th adaptation   */
+} avs_config;
+
+/* Physical mesh as a face list (finite-volume form of Eq. 18).
+ * faceR[f] < 0 marks a boundary face with condition -1 - faceR[f]; for those
+ * faceL[f] is the interior cell and An points out of the domain.
+ * bc[b*6 .. b*6+5] = type (AVS_BC_*), rho, U0, U1, U2, T: a wall uses U, T
+ * (diffuse reflection, density from zero net mass flux); a far field imposes
+ * the Maxwellian of (rho, U, T) on incoming velocities.  All host pointers. */
+typedef struct {
+    int dim, Nc, Nf, nbc;
+    const int *faceL, *faceR;     /* [Nf]                                   */
+    const double *An;             /* [Nf][dim] area * unit normal, L -> R   */
+    const double *rL, *rR;        /* [Nf][dim] face centre - cell centre    */
+    const double *vol;            /* [Nc]                                   */
+    const double *bc;             /* [nbc][6]                               */
+} avs_mesh;
+
+typedef struct {
+    int Nv_old, Nv, splits, merges;
+    double gap;           /* largest relative |M[f] - W| after the correction */
+    int checked_cells;    /* cells on which the criterion ran                 */
+    int missed_nodes;     /* learned form: decisions the check set got wrong (full steps only) */
+    int full;             /* 1 if the full criterion ran                      */
+} avs_adapt_stats;
+
+typedef struct {
+    const double *W_override; /* nullable: conserved W [Nc][D+2] used by the criterion and as
+                                 the correction target instead of the moments of f           */
+    int W_is_device;
+    int skip_correction;      /* 1: remap only (Sec. 3.2), no Sec. 3.3 correction             */
+    int force_full;           /* learned form: run the full criterion on this call            */
+} avs_adapt_opts;
+
+/* Creates a context, uploads the mesh, builds the step-0 velocity mesh
+ * (Sec. 3.5 steps 1-3: base forest, then adaptation on g^eq(W_inf) and
+ * g^eq(rho_inf, 0, T_inf) repeated until it stops changing, at most
+ * max_refine passes) and allocates f.  cuda_stream: cudaStream_t or NULL
+ * for the default stream.  Errors: EINVAL (config/mesh), ENOMEM, ECUDA. */
+avs_status avs_create(const avs_config *cfg, const avs_mesh *mesh, void *cuda_stream, avs_ctx **out);
+void       avs_destroy(avs_ctx *ctx);
+const char *avs_last_error(const avs_ctx *ctx);
+int        avs_num_nodes(const avs_ctx *ctx);
+int        avs_num_cells(const avs_ctx *ctx);
+
+/* f = g^eq(Wp_i)(xi_k) (1 + amp z_ik), H = (3-D) R T G (Eq. 16), with z_ik a
+ * standard normal from SplitMix64 (key (i << 32) | k, Box-Muller); then the
+ * carried W = moments of f (Eq. 7).  Wp: primitive, host or device. */
+avs_status avs_init_field(avs_ctx *ctx, const double *Wp, int is_device, double amp, uint64_t seed);
+
+/* dt = cfl * min over cells i and nodes k of |V_i| / sum_j A_ij max(xi_k . n_ij, 0). */
+avs_status avs_dt(avs_ctx *ctx, double cfl, double *dt_out);
+
+/* nsteps explicit UGKS steps (Sec. 2.3 with zero SGS sweeps): foot
+ * reconstruction, interface moments and Shakhov state, simplified
+ * multiscale flux (Eq. equ28), conservative W update, implicit-collision
+ * update of f (diagonal of Eq. SGS_phi).  dt from cfl (avs_dt); dt_out
+ * nullable.  Does not synchronise; numeric failures surface at the next
+ * blocking call as AVS_ENUMERIC. */
+avs_status ugks_step(avs_ctx *ctx, int nsteps, double cfl, double *dt_out);
+avs_status ugks_step_dt(avs_ctx *ctx, int nsteps, double dt);
+
+/* One AVS adaptation (Sec. 3): moments of f (Eq. 7), criterion M_k
+ * (Eqs. criterion_rho/_e/_mk), split/merge marks, new depth-first tree,
+ * consanguinity remap (Sec. 3.2), conservation correction (Sec. 3.3).
+ * Blocks until the new node count is known.  opts and stats nullable.
+ * Errors: ECAPACITY (tree would exceed max_nodes; state unchanged), ENUMERIC. */
+avs_status avs_adapt(avs_ctx *ctx, const avs_adapt_opts *opts, avs_adapt_stats *stats);
+
+/* Carried conserved W (FP64) and heat flux q of f (Eq. 8), host or device.
+ * Either output may be NULL.  Blocks when writing to the host. */
+avs_status avs_moments(avs_ctx *ctx, double *Wc_out, double *q_out, int is_device);
+/* Conserved moments of f itself (Eq. 7). */
+avs_status avs_f_moments(avs_ctx *ctx, double *Wc_out, int is_device);
+avs_status avs_set_W(avs_ctx *ctx, const double *Wc, int is_device);
+
+/* Criterion values M_k (unscaled) for the current f; Wc nullable (NULL: the
+ * moments of f).  M_out: [Nv] host or device. */
+avs_status avs_criterion(avs_ctx *ctx, const double *Wc, int W_is_device, double *M_out, int M_is_device);
+
+/* Tree copy-out (host): level, base index, path key, xi [Nv][D], w [Nv].
+ * Any output may be NULL. */
+avs_status avs_get_tree(avs_ctx *ctx, int *level, int *base, uint32_t *key, double *xi, double *w);
+
+/* f copy-out / copy-in in FP64 [Nc][nA][Nv] (parity and checkpoints). */
+avs_status avs_get_f(avs_ctx *ctx, double *f, int is_device);
+avs_status avs_set_f(avs_ctx *ctx, const double *f, int is_device);
+
+/* Number of kernels this context has launched so far (all entry points). */
+uint64_t   avs_kernel_launches(const avs_ctx *ctx);
+
+/* Waits for the context's stream and reports a pending device error. */
+avs_status avs_sync(avs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

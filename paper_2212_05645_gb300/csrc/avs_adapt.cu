@@ -1,0 +1,627 @@
+// Velocity-mesh kernels: node geometry, time-step bound, initial field,
+// moments, adaptive criterion, split/merge marks with prefix-scan compaction,
+// consanguinity remap and conservation correction (paper Sec. 3).
+//
+// The criterion, the marks and the new tree are computed with the same
+// operation order as a plain sequential code, without fused multiply-adds,
+// so that for the same f and W the adapted topology is bit-identical.
+#include <string.h>
+
+#include "avs_dev.cuh"
+#include "avs_internal.h"
+
+namespace avs {
+
+int round_up(int n, int m) { return (n + m - 1) / m * m; }
+
+// ------------------------------------------------------------------ geometry
+// Mid-point quadrature on the tree (Sec. 3): node = element centre,
+// weight = element area/volume; xi = vlo + hb (b + (2o+1)/2^(l+1)).
+__global__ void k_geom(int D, int Nv, int Nvp, const int* __restrict__ level, const int* __restrict__ base,
+                       const uint32_t* __restrict__ key, int nb0, int nb1, int nb2, double vlo0, double vlo1,
+                       double vlo2, double hb0, double hb1, double hb2, double* xi_d, double* w_d, float* xi_f,
+                       float* w_f)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nvp) return;
+    if (k >= Nv) {
+        for (int d = 0; d < D; ++d) {
+            xi_d[(size_t)k * D + d] = 0.0;
+            xi_f[(size_t)k * D + d] = 0.0f;
+        }
+        w_d[k] = 0.0;
+        w_f[k] = 0.0f;
+        return;
+    }
+    const int nb[3] = {nb0, nb1, nb2};
+    const double vlo[3] = {vlo0, vlo1, vlo2};
+    const double hb[3] = {hb0, hb1, hb2};
+    const int l = level[k];
+    int b = base[k];
+    const uint32_t kk = key[k];
+    double wk = 1.0;
+    for (int d = 0; d < D; ++d) {
+        const int bi = b % nb[d];
+        b /= nb[d];
+        uint32_t o = 0;
+        for (int m = 0; m < l; ++m) {
+            const uint32_t digit = (kk >> (D * (l - 1 - m))) & ((1u << D) - 1u);
+            o = 2u * o + ((digit >> d) & 1u);
+        }
+        const double frac = (double)(2u * o + 1u) / (double)(1u << (l + 1));
+        const double x = __dadd_rn(vlo[d], __dmul_rn(hb[d], __dadd_rn((double)bi, frac)));
+        xi_d[(size_t)k * D + d] = x;
+        xi_f[(size_t)k * D + d] = (float)x;
+        wk = __dmul_rn(wk, hb[d]);
+    }
+    const double wv = ldexp(wk, -D * l);
+    w_d[k] = wv;
+    w_f[k] = (float)wv;
+}
+
+cudaError_t launch_geom(avs_ctx* c)
+{
+    const int n = c->Nvp;
+    k_geom<<<(n + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nv, c->Nvp, c->level, c->base, c->key, c->cfg.base[0],
+                                                   c->cfg.base[1], c->cfg.base[2], c->cfg.vlo[0], c->cfg.vlo[1],
+                                                   c->cfg.vlo[2], c->hb[0], c->hb[1], c->hb[2], c->xi_d, c->w_d,
+                                                   c->xi_f, c->w_f);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ dt bound
+// min over cells and nodes of |V_i| / sum_faces max(xi . An_out, 0)  (R5)
+__global__ void k_dt_unit(int D, int Nv, const double* __restrict__ xi, const int* __restrict__ slot,
+                          const unsigned char* __restrict__ nslot, const double* __restrict__ An,
+                          const double* __restrict__ vol, unsigned long long* out)
+{
+    const int i = blockIdx.x;
+    const int ns = nslot[i];
+    double best = INFINITY;
+    for (int k = threadIdx.x; k < Nv; k += blockDim.x) {
+        const double* x = xi + (size_t)k * D;
+        double sum = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            const int sl = slot[i * AVS_MAXS + s];
+            const double* a = An + (size_t)(sl >> 1) * D;
+            double sn = __dmul_rn(x[0], a[0]);
+            for (int d = 1; d < D; ++d) sn = __dadd_rn(sn, __dmul_rn(x[d], a[d]));
+            if (sl & 1) sn = -sn;
+            if (sn > 0.0) sum = __dadd_rn(sum, sn);
+        }
+        if (sum > 0.0) {
+            const double t = __ddiv_rn(vol[i], sum);
+            best = t < best ? t : best;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_down_sync(0xffffffffu, best, o);
+        best = v < best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best < INFINITY) atomicMin(out, dkey(best));
+}
+
+cudaError_t launch_dt_unit(avs_ctx* c)
+{
+    const unsigned long long init = ~0ull;
+    cudaError_t e = cudaMemcpyAsync(c->dt_key, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    k_dt_unit<<<c->Nc, 128, 0, c->stream>>>(c->D, c->Nv, c->xi_d, c->slot, c->nslot, c->An_d, c->vol, c->dt_key);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ initial field
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// standard normal from SplitMix64 (Steele, Lea, Flood 2014) and Box-Muller
+__device__ __forceinline__ double normal_ik(uint64_t seed, uint64_t i, uint64_t k)
+{
+    const uint64_t key = (i << 32) | k;
+    const uint64_t u1 = splitmix64(seed ^ splitmix64(2u * key));
+    const uint64_t u2 = splitmix64(seed ^ splitmix64(2u * key + 1u));
+    const double U1 = ((double)(u1 >> 11) + 1.0) * 0x1p-53;
+    const double U2 = (double)(u2 >> 11) * 0x1p-53;
+    return sqrt(-2.0 * log(U1)) * cos(2.0 * AVS_PI * U2);
+}
+
+template <typename T>
+__global__ void k_maxwell(int D, int NA, int Nv, int Nvp, const double* __restrict__ xi, const double* __restrict__ Wp,
+                          double R, double amp, uint64_t seed, T* f)
+{
+    const int i = blockIdx.x;
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= Nvp) return;
+    T* fi = f + (size_t)i * NA * Nvp;
+    if (k >= Nv) {
+        for (int a = 0; a < NA; ++a) fi[(size_t)a * Nvp + k] = T(0);
+        return;
+    }
+    const double* P = Wp + (size_t)i * (D + 2);
+    const double rho = P[0], RT = R * P[D + 1];
+    double c2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        const double c = __dsub_rn(xi[(size_t)k * D + d], P[1 + d]);
+        c2 = __dadd_rn(c2, __dmul_rn(c, c));
+    }
+    double G = rho / pow(2.0 * AVS_PI * RT, 0.5 * D) * exp(-c2 / (2.0 * RT));
+    if (amp != 0.0) G *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
+    fi[k] = (T)G;
+    if (NA == 2) fi[Nvp + k] = (T)((3.0 - D) * RT * G);
+}
+
+cudaError_t launch_maxwell(avs_ctx* c, const double* Wp, int Ncells, double amp, uint64_t seed, void* fout,
+                           int f_is_double, int Nvp)
+{
+    dim3 g(Ncells, (Nvp + 255) / 256);
+    if (f_is_double || !c->mixed)
+        k_maxwell<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp, seed,
+                                                    (double*)fout);
+    else
+        k_maxwell<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp, seed,
+                                                   (float*)fout);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ moments
+// Conserved moments (Eq. 7) and heat flux (Eq. 8) of every cell, summed about
+// the cell's carried velocity (when given) to limit cancellation.
+template <int D, typename T, int NT>
+__global__ void __launch_bounds__(NT) k_cell_moments(int Nv, int Nvp, const T* __restrict__ f,
+                                                     const T* __restrict__ xi, const T* __restrict__ w,
+                                                     const double* __restrict__ Wref, double* Wc, double* q)
+{
+    constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
+    constexpr int CH = (sizeof(T) == 4) ? 8 : (1 << 20);
+    __shared__ double sred[(NT / 32) * NM];
+    __shared__ double mom[NM];
+    const int i = blockIdx.x;
+    double V[3] = {0, 0, 0};
+    if (Wref && Wref[(size_t)i * NW] > 0.0) {
+        for (int d = 0; d < D; ++d) V[d] = (double)(T)(Wref[(size_t)i * NW + 1 + d] / Wref[(size_t)i * NW]);
+    }
+    T Vt[D];
+    for (int d = 0; d < D; ++d) Vt[d] = (T)V[d];
+    const T* fi = f + (size_t)i * NA * Nvp;
+    double acc[NM];
+    for (int m = 0; m < NM; ++m) acc[m] = 0.0;
+    for (int k0 = threadIdx.x; k0 < Nv; k0 += NT * CH) {
+        T part[NM];
+        for (int m = 0; m < NM; ++m) part[m] = T(0);
+        for (int c = 0, k = k0; c < CH && k < Nv; ++c, k += NT) {
+            T xs[D];
+            for (int d = 0; d < D; ++d) xs[d] = xi[(size_t)k * D + d] - Vt[d];
+            const T wk = w[k];
+            raw_acc<D>(part, xs, wk * fi[k], NA == 2 ? wk * fi[Nvp + k] : T(0));
+        }
+        for (int m = 0; m < NM; ++m) acc[m] += (double)part[m];
+    }
+    block_sum<NM, NT>(acc, sred, mom);
+    if (threadIdx.x == 0) {
+        double W[5], qq[3];
+        moments_from_raw<D>(mom, V, W, qq, nullptr, nullptr);
+        if (Wc)
+            for (int m = 0; m < NW; ++m) Wc[(size_t)i * NW + m] = W[m];
+        if (q)
+            for (int d = 0; d < D; ++d) q[(size_t)i * D + d] = qq[d];
+    }
+}
+
+cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wc_out,
+                                double* q_out)
+{
+    const bool dbl = f_is_double || !c->mixed;
+    const double* Wref = (Ncells == c->Nc) ? c->W[c->wcur] : nullptr;
+    if (c->D == 2) {
+        if (dbl)
+            k_cell_moments<2, double, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
+                c->Nv, Nvp, (const double*)f, c->xi_d, c->w_d, Wref, Wc_out, q_out);
+        else
+            k_cell_moments<2, float, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
+                c->Nv, Nvp, (const float*)f, c->xi_f, c->w_f, Wref, Wc_out, q_out);
+    } else {
+        if (dbl)
+            k_cell_moments<3, double, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
+                c->Nv, Nvp, (const double*)f, c->xi_d, c->w_d, Wref, Wc_out, q_out);
+        else
+            k_cell_moments<3, float, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
+                c->Nv, Nvp, (const float*)f, c->xi_f, c->w_f, Wref, Wc_out, q_out);
+    }
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ criterion
+// Per-cell inputs of the criterion, in the fixed order of the definition:
+// rho, U_d = m_d / rho, e_int = rho E - 0.5 (sum m_d m_d) / rho.
+__global__ void k_crit_cells(int D, int Ncells, const double* __restrict__ Wc, double* cp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ncells) return;
+    const double* W = Wc + (size_t)i * (D + 2);
+    const double rho = W[0];
+    double mm = 0.0;
+    for (int d = 0; d < D; ++d) {
+        cp[(size_t)i * 5 + 1 + d] = __ddiv_rn(W[1 + d], rho);
+        mm = __dadd_rn(mm, __dmul_rn(W[1 + d], W[1 + d]));
+    }
+    cp[(size_t)i * 5 + 0] = rho;
+    cp[(size_t)i * 5 + 4] = __dsub_rn(W[D + 1], __ddiv_rn(__dmul_rn(0.5, mm), rho));
+}
+
+__global__ void k_fill_key(unsigned long long* k, int n, unsigned long long v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) k[i] = v;
+}
+
+// M_k = max over cells of max(M1, M2): M1 = (w G) / rho,
+// M2 = ((0.5 (w G)) c^2) / e_int, c^2 summed left to right (Sec. 3.4, R9).
+template <typename T>
+__global__ void k_criterion(int D, int NA, int Nv, int Nvp, int ncells, int cells_per_block, const T* __restrict__ f,
+                            const double* __restrict__ xi, const double* __restrict__ w, const double* __restrict__ cp,
+                            const int* __restrict__ cells, unsigned long long* Mkey)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nv) return;
+    const int j0 = blockIdx.y * cells_per_block;
+    const int j1 = min(ncells, j0 + cells_per_block);
+    double x[3];
+    for (int d = 0; d < D; ++d) x[d] = xi[(size_t)k * D + d];
+    const double wk = w[k];
+    double best = -INFINITY;
+    for (int j = j0; j < j1; ++j) {
+        const int i = cells ? cells[j] : j;
+        const double* p = cp + (size_t)i * 5;
+        const double G = (double)f[(size_t)i * NA * Nvp + k];
+        const double wg = __dmul_rn(wk, G);
+        const double m1 = __ddiv_rn(wg, p[0]);
+        double c2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double cc = __dsub_rn(x[d], p[1 + d]);
+            c2 = __dadd_rn(c2, __dmul_rn(cc, cc));
+        }
+        const double m2 = __ddiv_rn(__dmul_rn(__dmul_rn(0.5, wg), c2), p[4]);
+        const double mk = m1 > m2 ? m1 : m2;
+        best = mk > best ? mk : best;
+    }
+    if (best > -INFINITY) atomicMax(Mkey + k, dkey(best));
+}
+
+__global__ void k_decode_M(const unsigned long long* __restrict__ Mkey, double* M, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) M[i] = dkey_inv(Mkey[i]);
+}
+
+cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, const double* Wc,
+                             const int* cells, int ncells_list)
+{
+    double* cp = c->crit_cp;
+    k_crit_cells<<<(Ncells + 255) / 256, 256, 0, c->stream>>>(c->D, Ncells, Wc, cp);
+    const unsigned long long ninf = dkey(-INFINITY);
+    k_fill_key<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->Nv, ninf);
+    const int n = cells ? ncells_list : Ncells;
+    const int cpb = 64;
+    dim3 g((c->Nv + 255) / 256, (n + cpb - 1) / cpb);
+    if (n > 0) {
+        if (f_is_double || !c->mixed)
+            k_criterion<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const double*)f, c->xi_d,
+                                                          c->w_d, cp, cells, c->Mkey);
+        else
+            k_criterion<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const float*)f, c->xi_d,
+                                                         c->w_d, cp, cells, c->Mkey);
+    }
+    k_decode_M<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->M, c->Nv);
+    c->launches += (n > 0) ? 4 : 3;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ marks, scan, new tree
+// emit[k] = number of new leaves produced by old leaf k; kind of the first:
+// a group start (2^D sibling leaves, all s*M < C2, level >= 1) emits the
+// parent; the other members of its group emit nothing; a leaf with
+// s*M > C1 below the level cap emits its 2^D children; others emit themselves.
+__global__ void k_group_start(int D, int Nv, const int* __restrict__ level, const int* __restrict__ base,
+                              const uint32_t* __restrict__ key, const double* __restrict__ M, double s, double C2,
+                              int* gs)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nv) return;
+    const int nch = 1 << D;
+    int g = 0;
+    if (level[k] >= 1 && (key[k] & (uint32_t)(nch - 1)) == 0u && k + nch <= Nv) {
+        g = 1;
+        for (int c = 0; c < nch; ++c) {
+            const int kk = k + c;
+            if (level[kk] != level[k] || base[kk] != base[k] || key[kk] != key[k] + (uint32_t)c ||
+                !(__dmul_rn(s, M[kk]) < C2))
+                g = 0;
+        }
+    }
+    gs[k] = g;
+}
+
+__global__ void k_emit(int D, int Nv, const int* __restrict__ level, const uint32_t* __restrict__ key,
+                       const double* __restrict__ M, const int* __restrict__ gs, double s, double C1, int max_refine,
+                       int* emit)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nv) return;
+    const int nch = 1 << D;
+    int e;
+    if (gs[k]) {
+        e = 1;
+    } else {
+        const int dig = (int)(key[k] & (uint32_t)(nch - 1));
+        const int st = k - dig;
+        if (level[k] >= 1 && dig != 0 && st >= 0 && gs[st]) e = 0;
+        else if (__dmul_rn(s, M[k]) > C1 && level[k] < max_refine) e = nch;
+        else e = 1;
+    }
+    emit[k] = e;
+}
+
+// Single-block exclusive scan (1024 threads, contiguous segments per thread,
+// warp-shuffle scans); writes the total to *count.
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int* out, int n, int* count)
+{
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int per = (n + 1023) / 1024;
+    const int b = min(n, t * per), e = min(n, b + per);
+    int local = 0;
+    for (int k = b; k < e; ++k) local += in[k];
+    int x = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int v = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        wsum[lane] = v;
+    }
+    __syncthreads();
+    int run = x - local + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int k = b; k < e; ++k) {
+        out[k] = run;
+        run += in[k];
+    }
+    if (t == 1023) *count = run;
+}
+
+__global__ void k_build(int D, int Nv, const int* __restrict__ level, const int* __restrict__ base,
+                        const uint32_t* __restrict__ key, const int* __restrict__ gs, const int* __restrict__ emit,
+                        const int* __restrict__ idx, int cap, int* nl, int* nb, uint32_t* nk, int* src, int* kind,
+                        int* counters)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nv) return;
+    const int e = emit[k];
+    const int n = idx[k];
+    if (e == 0 || n + e > cap) return;
+    const int nch = 1 << D;
+    if (gs[k]) {
+        nl[n] = level[k] - 1;
+        nb[n] = base[k];
+        nk[n] = key[k] >> D;
+        src[n] = k;
+        kind[n] = 1;
+        atomicAdd(counters + 1, 1);
+    } else if (e == nch) {
+        for (int c = 0; c < nch; ++c) {
+            nl[n + c] = level[k] + 1;
+            nb[n + c] = base[k];
+            nk[n + c] = (key[k] << D) | (uint32_t)c;
+            src[n + c] = k;
+            kind[n + c] = 0;
+        }
+        atomicAdd(counters + 0, 1);
+    } else {
+        nl[n] = level[k];
+        nb[n] = base[k];
+        nk[n] = key[k];
+        src[n] = k;
+        kind[n] = 0;
+    }
+}
+
+cudaError_t launch_adapt_tree(avs_ctx* c, double C1, double C2)
+{
+    const int n = c->Nv;
+    const int g = (n + 255) / 256;
+    int* gs = c->newidx + c->cap;    // second half of the index scratch
+    k_group_start<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->base, c->key, c->M, c->s_norm, C2, gs);
+    k_emit<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->key, c->M, gs, c->s_norm, C1, c->cfg.max_refine, c->emit);
+    k_scan<<<1, 1024, 0, c->stream>>>(c->emit, c->newidx, n, c->d_count);
+    cudaMemsetAsync(c->d_count + 1, 0, 2 * sizeof(int), c->stream);
+    k_build<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->base, c->key, gs, c->emit, c->newidx, c->cap, c->level2,
+                                      c->base2, c->key2, c->src, c->kind, c->d_count + 1);
+    c->launches += 4;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ remap
+// Consanguinity (Sec. 3.2): child = parent; merged parent = pairwise mean.
+template <typename T>
+__global__ void k_remap(int D, int NA, int Nv_new, int Nvp_old, int Nvp_new, const int* __restrict__ src,
+                        const int* __restrict__ kind, const T* __restrict__ fo, T* fn)
+{
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    const int ia = blockIdx.x;              // cell * NA + array
+    if (k >= Nvp_new) return;
+    T* out = fn + (size_t)ia * Nvp_new;
+    if (k >= Nv_new) {
+        out[k] = T(0);
+        return;
+    }
+    const T* in = fo + (size_t)ia * Nvp_old + src[k];
+    T v;
+    if (kind[k] == 0) v = in[0];
+    else if (D == 2) v = ((in[0] + in[1]) + (in[2] + in[3])) * T(0.25);
+    else v = (((in[0] + in[1]) + (in[2] + in[3])) + ((in[4] + in[5]) + (in[6] + in[7]))) * T(0.125);
+    out[k] = v;
+}
+
+cudaError_t launch_remap(avs_ctx* c, const void* fold, int Nvp_old, void* fnew, int Nvp_new, int Nv_new)
+{
+    dim3 g(c->Nc * c->NA, (Nvp_new + 255) / 256);
+    if (c->mixed)
+        k_remap<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, Nv_new, Nvp_old, Nvp_new, c->src, c->kind,
+                                                 (const float*)fold, (float*)fnew);
+    else
+        k_remap<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, Nv_new, Nvp_old, Nvp_new, c->src, c->kind,
+                                                  (const double*)fold, (double*)fnew);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ correction
+// f <- f + g^eq(W) - g^eq(W'), W' = moments of f, `iters` passes (Sec. 3.3,
+// R12); then the remaining relative gap, max over cells, into *gap_key.
+template <int D, typename T, int NT>
+__global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* __restrict__ xi,
+                                                const T* __restrict__ w, const double* __restrict__ Wt, double R,
+                                                int iters, unsigned long long* gap_key)
+{
+    constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
+    constexpr int CH = (sizeof(T) == 4) ? 8 : (1 << 20);
+    __shared__ double sred[(NT / 32) * NM];
+    __shared__ double mom[NM];
+    __shared__ EqPar<T> ea, eb;
+    const int i = blockIdx.x;
+    T* fi = f + (size_t)i * NA * Nvp;
+    const double* Wi = Wt + (size_t)i * NW;
+    double rho, U[3], RT;
+    prim<D>(Wi, rho, U, RT);
+    double V[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) V[d] = (double)(T)U[d];
+    T Vt[D];
+    for (int d = 0; d < D; ++d) Vt[d] = (T)V[d];
+    for (int it = 0; it <= iters; ++it) {
+        double acc[NM];
+        for (int m = 0; m < NM; ++m) acc[m] = 0.0;
+        for (int k0 = threadIdx.x; k0 < Nv; k0 += NT * CH) {
+            T part[NM];
+            for (int m = 0; m < NM; ++m) part[m] = T(0);
+            for (int c = 0, k = k0; c < CH && k < Nv; ++c, k += NT) {
+                T xs[D];
+                for (int d = 0; d < D; ++d) xs[d] = xi[(size_t)k * D + d] - Vt[d];
+                const T wk = w[k];
+                raw_acc<D>(part, xs, wk * fi[k], NA == 2 ? wk * fi[Nvp + k] : T(0));
+            }
+            for (int m = 0; m < NM; ++m) acc[m] += (double)part[m];
+        }
+        block_sum<NM, NT>(acc, sred, mom);
+        if (it == iters) {
+            if (threadIdx.x == 0) {
+                double Wp[5];
+                moments_from_raw<D>(mom, V, Wp, nullptr, nullptr, nullptr);
+                double mref = 0.0;
+                for (int d = 0; d < D; ++d) mref += Wi[1 + d] * Wi[1 + d];
+                mref = sqrt(mref) + rho * sqrt(2.0 * RT);
+                double e = fabs(Wp[0] - Wi[0]) / fabs(Wi[0]);
+                for (int d = 0; d < D; ++d) e = fmax(e, fabs(Wp[1 + d] - Wi[1 + d]) / mref);
+                e = fmax(e, fabs(Wp[D + 1] - Wi[D + 1]) / fabs(Wi[D + 1]));
+                if (e != e) e = INFINITY;
+                atomicMax(gap_key, dkey(e));
+            }
+            break;
+        }
+        if (threadIdx.x == 0) {
+            double Wp[5], rp, Up[3], RTp;
+            moments_from_raw<D>(mom, V, Wp, nullptr, nullptr, nullptr);
+            prim<D>(Wp, rp, Up, RTp);
+            ea = make_eq<D, T>(rho, U, RT, nullptr, 0.0);
+            eb = make_eq<D, T>(rp, Up, RTp, nullptr, 0.0);
+        }
+        __syncthreads();
+        const EqPar<T> A = ea, B = eb;
+        for (int k = threadIdx.x; k < Nv; k += NT) {
+            T x[D];
+            for (int d = 0; d < D; ++d) x[d] = xi[(size_t)k * D + d];
+            T ga, gah, gb, gbh;
+            eq_eval<D>(A, x, ga, gah);
+            eq_eval<D>(B, x, gb, gbh);
+            fi[k] += ga - gb;
+            if (NA == 2) fi[Nvp + k] += gah - gbh;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters)
+{
+    const unsigned long long zero = dkey(0.0);
+    cudaError_t e = cudaMemcpyAsync(c->gap_d, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    unsigned long long* gk = (unsigned long long*)c->gap_d;
+    if (c->D == 2) {
+        if (c->mixed)
+            k_correct<2, float, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_f, c->w_f,
+                                                                         Wtarget, c->cfg.R, iters, gk);
+        else
+            k_correct<2, double, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d,
+                                                                          c->w_d, Wtarget, c->cfg.R, iters, gk);
+    } else {
+        if (c->mixed)
+            k_correct<3, float, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_f, c->w_f,
+                                                                         Wtarget, c->cfg.R, iters, gk);
+        else
+            k_correct<3, double, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d,
+                                                                          c->w_d, Wtarget, c->cfg.R, iters, gk);
+    }
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ conversions
+template <typename T>
+__global__ void k_to_double(int Nv, int Nvp, const T* __restrict__ f, double* out)
+{
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    const int ia = blockIdx.x;
+    if (k < Nv) out[(size_t)ia * Nv + k] = (double)f[(size_t)ia * Nvp + k];
+}
+
+template <typename T>
+__global__ void k_from_double(int Nv, int Nvp, const double* __restrict__ in, T* f)
+{
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    const int ia = blockIdx.x;
+    if (k < Nvp) f[(size_t)ia * Nvp + k] = k < Nv ? (T)in[(size_t)ia * Nv + k] : T(0);
+}
+
+cudaError_t launch_to_double(avs_ctx* c, const void* f, double* out, int Nvp)
+{
+    dim3 g(c->Nc * c->NA, (c->Nv + 255) / 256);
+    if (c->mixed) k_to_double<float><<<g, 256, 0, c->stream>>>(c->Nv, Nvp, (const float*)f, out);
+    else k_to_double<double><<<g, 256, 0, c->stream>>>(c->Nv, Nvp, (const double*)f, out);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_double(avs_ctx* c, const double* in, void* f, int Nvp)
+{
+    dim3 g(c->Nc * c->NA, (Nvp + 255) / 256);
+    if (c->mixed) k_from_double<float><<<g, 256, 0, c->stream>>>(c->Nv, Nvp, in, (float*)f);
+    else k_from_double<double><<<g, 256, 0, c->stream>>>(c->Nv, Nvp, in, (double*)f);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace avs

@@ -1,0 +1,669 @@
+// C ABI of the library (include/avs.h): validation, mesh preprocessing,
+// the step-0 velocity mesh, state management and every entry point.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "avs_dev.cuh"
+#include "avs_internal.h"
+
+using namespace avs;
+
+namespace {
+
+avs_status fail(avs_ctx* c, avs_status s, const char* what, cudaError_t e = cudaSuccess)
+{
+    if (c) {
+        c->err = what;
+        if (e != cudaSuccess) {
+            c->err += ": ";
+            c->err += cudaGetErrorString(e);
+        }
+    }
+    return s;
+}
+
+#define CK(x)                                                              \
+    do {                                                                   \
+        cudaError_t e_ = (x);                                              \
+        if (e_ != cudaSuccess) return fail(c, AVS_ECUDA, #x, e_);          \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n)
+{
+    if (n == 0) n = 1;
+    return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+template <typename T>
+cudaError_t up(T* dst, const std::vector<T>& v, cudaStream_t s)
+{
+    return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+size_t elem_size(const avs_ctx* c) { return c->mixed ? sizeof(float) : sizeof(double); }
+
+void free_all(avs_ctx* c)
+{
+    void* ptrs[] = {c->faceL, c->faceR, c->An_d, c->rL_d, c->rR_d, c->An_f, c->rL_f, c->rR_f, c->vol, c->bc,
+                    c->slot, c->nslot, c->nbr, c->cg_d, c->r_d, c->eps2_d, c->cg_f, c->r_f, c->eps2_f,
+                    c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
+                    c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
+                    c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->stage, c->dev_err,
+                    c->dt_key, c->gap_d};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+// conserved from primitive (monatomic): rho E = rho U^2 / 2 + 3/2 rho R T
+void cons_host(int D, const double* Wp, double R, double* Wc)
+{
+    const double rho = Wp[0];
+    double u2 = 0.0;
+    Wc[0] = rho;
+    for (int d = 0; d < D; ++d) {
+        Wc[1 + d] = rho * Wp[1 + d];
+        u2 += Wp[1 + d] * Wp[1 + d];
+    }
+    Wc[D + 1] = 0.5 * rho * u2 + 1.5 * rho * R * Wp[D + 1];
+}
+
+__global__ void k_prim_to_cons(int D, int Nc, const double* __restrict__ Wp, double R, double* Wc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nc) return;
+    const double* P = Wp + (size_t)i * (D + 2);
+    double* C = Wc + (size_t)i * (D + 2);
+    double u2 = 0.0;
+    C[0] = P[0];
+    for (int d = 0; d < D; ++d) {
+        C[1 + d] = P[0] * P[1 + d];
+        u2 += P[1 + d] * P[1 + d];
+    }
+    C[D + 1] = 0.5 * P[0] * u2 + 1.5 * P[0] * R * P[D + 1];
+}
+
+avs_status read_err(avs_ctx* c)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e & 1) {
+        CK(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+        return fail(c, AVS_ENUMERIC, "non-positive density or temperature in a step");
+    }
+    return AVS_OK;
+}
+
+avs_status refresh_dt(avs_ctx* c)
+{
+    CK(launch_dt_unit(c));
+    unsigned long long k = 0;
+    CK(cudaMemcpyAsync(&k, c->dt_key, sizeof(k), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->dt_unit = (k == ~0ull) ? INFINITY : dkey_inv(k);
+    return AVS_OK;
+}
+
+// One pass of marks + compaction on criterion values already in c->M;
+// swaps in the new tree.  Returns counts through out pointers.
+avs_status apply_marks(avs_ctx* c, int* Nv_new, int* splits, int* merges)
+{
+    CK(launch_adapt_tree(c, c->cfg.C1, c->cfg.C2));
+    int cnt[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *Nv_new = cnt[0];
+    *splits = cnt[1];
+    *merges = cnt[2];
+    if (cnt[0] > c->cap) return fail(c, AVS_ECAPACITY, "adapted velocity tree exceeds its capacity");
+    return AVS_OK;
+}
+
+void swap_tree(avs_ctx* c, int Nv_new)
+{
+    std::swap(c->level, c->level2);
+    std::swap(c->base, c->base2);
+    std::swap(c->key, c->key2);
+    c->Nv = Nv_new;
+    c->Nvp = round_up(Nv_new, 32);
+}
+
+avs_status ensure_stage(avs_ctx* c)
+{
+    const size_t need = (size_t)c->Nc * c->NA * std::max(c->Nv, 1);
+    if (c->stage_elems >= need) return AVS_OK;
+    if (c->stage) CK(cudaFree(c->stage));
+    c->stage = nullptr;
+    c->stage_elems = 0;
+    if (dalloc(&c->stage, need) != cudaSuccess) return fail(c, AVS_ENOMEM, "staging buffer");
+    c->stage_elems = need;
+    return AVS_OK;
+}
+
+avs_status alloc_f(avs_ctx* c, int nodes, void** f0, void** f1)
+{
+    const size_t bytes = (size_t)c->Nc * c->NA * (size_t)round_up(nodes, 32) * elem_size(c);
+    if (cudaMalloc(f0, bytes) != cudaSuccess) return fail(c, AVS_ENOMEM, "f buffer");
+    if (cudaMalloc(f1, bytes) != cudaSuccess) {
+        cudaFree(*f0);
+        return fail(c, AVS_ENOMEM, "f buffer");
+    }
+    CK(cudaMemsetAsync(*f0, 0, bytes, c->stream));
+    CK(cudaMemsetAsync(*f1, 0, bytes, c->stream));
+    return AVS_OK;
+}
+
+avs_status validate(const avs_config* cfg, const avs_mesh* m, std::string& why)
+{
+    if (!cfg || !m) { why = "null config or mesh"; return AVS_EINVAL; }
+    const int D = cfg->dim;
+    if (D != 2 && D != 3) { why = "dim must be 2 or 3"; return AVS_EINVAL; }
+    if (m->dim != D) { why = "mesh dim differs from config dim"; return AVS_EINVAL; }
+    if (cfg->max_refine < 0 || D * cfg->max_refine > 30) { why = "max_refine out of range"; return AVS_EINVAL; }
+    long long nbase = 1;
+    for (int d = 0; d < D; ++d) {
+        if (cfg->base[d] < 1 || !(cfg->vhi[d] > cfg->vlo[d])) { why = "bad velocity base/bounds"; return AVS_EINVAL; }
+        nbase *= cfg->base[d];
+    }
+    if (nbase > (1 << 24)) { why = "base forest too large"; return AVS_EINVAL; }
+    if (cfg->precision != AVS_FP64 && cfg->precision != AVS_MIXED) { why = "bad precision"; return AVS_EINVAL; }
+    if (!(cfg->R > 0) || !(cfg->Kn > 0) || !(cfg->T_ref > 0) || !(cfg->Pr > 0)) { why = "bad gas constants"; return AVS_EINVAL; }
+    if (!(cfg->C1 > cfg->C2)) { why = "C1 must exceed C2"; return AVS_EINVAL; }
+    if (cfg->limiter < 0 || cfg->limiter > 2) { why = "bad limiter"; return AVS_EINVAL; }
+    if (cfg->corr_iters < 0 || cfg->corr_iters > 64) { why = "bad corr_iters"; return AVS_EINVAL; }
+    if (m->Nc <= 0 || m->Nf <= 0 || m->nbc < 0) { why = "empty mesh"; return AVS_EINVAL; }
+    if (!m->faceL || !m->faceR || !m->An || !m->rL || !m->rR || !m->vol || (m->nbc > 0 && !m->bc)) {
+        why = "null mesh array";
+        return AVS_EINVAL;
+    }
+    for (int b = 0; b < m->nbc; ++b) {
+        const int t = (int)m->bc[b * 6];
+        if (t != AVS_BC_WALL && t != AVS_BC_FARFIELD) { why = "bad boundary type"; return AVS_EINVAL; }
+        if (!(m->bc[b * 6 + 5] > 0)) { why = "boundary temperature must be positive"; return AVS_EINVAL; }
+    }
+    std::vector<int> cnt(m->Nc, 0);
+    for (int f = 0; f < m->Nf; ++f) {
+        const int L = m->faceL[f], R = m->faceR[f];
+        if (L < 0 || L >= m->Nc) { why = "faceL out of range"; return AVS_EINVAL; }
+        if (R >= m->Nc || (R < 0 && -1 - R >= m->nbc)) { why = "faceR out of range"; return AVS_EINVAL; }
+        if (R == L) { why = "face joins a cell to itself"; return AVS_EINVAL; }
+        if (++cnt[L] > AVS_MAXS) { why = "more than 6 faces on a cell"; return AVS_EINVAL; }
+        if (R >= 0 && ++cnt[R] > AVS_MAXS) { why = "more than 6 faces on a cell"; return AVS_EINVAL; }
+    }
+    for (int i = 0; i < m->Nc; ++i)
+        if (!(m->vol[i] > 0)) { why = "non-positive cell volume"; return AVS_EINVAL; }
+    return AVS_OK;
+}
+
+// Cell -> face slots in face order; least-squares weights (inverse-distance
+// squared, R6) and limiter eps^2 = (K vol^(1/D))^3.
+avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
+{
+    const int D = c->D, Nc = c->Nc, Nf = c->Nf;
+    std::vector<int> slot((size_t)Nc * AVS_MAXS, -1), nbr((size_t)Nc * AVS_MAXS, -1);
+    std::vector<unsigned char> ns(Nc, 0);
+    for (int f = 0; f < Nf; ++f) {
+        const int L = m->faceL[f], R = m->faceR[f];
+        slot[(size_t)L * AVS_MAXS + ns[L]] = 2 * f;
+        nbr[(size_t)L * AVS_MAXS + ns[L]] = R >= 0 ? R : -1;
+        ns[L]++;
+        if (R >= 0) {
+            slot[(size_t)R * AVS_MAXS + ns[R]] = 2 * f + 1;
+            nbr[(size_t)R * AVS_MAXS + ns[R]] = L;
+            ns[R]++;
+        }
+    }
+    std::vector<double> cg((size_t)Nc * AVS_MAXS * D, 0.0), r((size_t)Nc * AVS_MAXS * D, 0.0), eps2(Nc);
+    for (int i = 0; i < Nc; ++i) {
+        double M[9] = {0}, dv[AVS_MAXS][3], n2[AVS_MAXS];
+        for (int s = 0; s < ns[i]; ++s) {
+            const int sl = slot[(size_t)i * AVS_MAXS + s];
+            const int f = sl >> 1;
+            const bool isR = sl & 1;
+            const double* rs = (isR ? m->rR : m->rL) + (size_t)f * D;
+            const double* ro = (isR ? m->rL : m->rR) + (size_t)f * D;
+            for (int a = 0; a < D; ++a) r[((size_t)i * AVS_MAXS + s) * D + a] = rs[a];
+            n2[s] = 0.0;
+            if (nbr[(size_t)i * AVS_MAXS + s] < 0) continue;
+            for (int a = 0; a < D; ++a) {
+                dv[s][a] = rs[a] - ro[a];
+                n2[s] += dv[s][a] * dv[s][a];
+            }
+            for (int a = 0; a < D; ++a)
+                for (int b = 0; b < D; ++b) M[a * D + b] += dv[s][a] * dv[s][b] / n2[s];
+        }
+        double tr = 0.0;
+        for (int a = 0; a < D; ++a) tr += M[a * D + a];
+        double Mi[9] = {0};
+        bool ok = false;
+        if (D == 2) {
+            const double det = M[0] * M[3] - M[1] * M[2];
+            if (det > 1e-12 * tr * tr) {
+                ok = true;
+                Mi[0] = M[3] / det; Mi[1] = -M[1] / det; Mi[2] = -M[2] / det; Mi[3] = M[0] / det;
+            }
+        } else {
+            const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8],
+                         c02 = M[3] * M[7] - M[4] * M[6];
+            const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+            if (det > 1e-12 * tr * tr * tr) {
+                ok = true;
+                Mi[0] = c00 / det; Mi[1] = (M[2] * M[7] - M[1] * M[8]) / det; Mi[2] = (M[1] * M[5] - M[2] * M[4]) / det;
+                Mi[3] = c01 / det; Mi[4] = (M[0] * M[8] - M[2] * M[6]) / det; Mi[5] = (M[2] * M[3] - M[0] * M[5]) / det;
+                Mi[6] = c02 / det; Mi[7] = (M[1] * M[6] - M[0] * M[7]) / det; Mi[8] = (M[0] * M[4] - M[1] * M[3]) / det;
+            }
+        }
+        if (ok) {
+            for (int s = 0; s < ns[i]; ++s) {
+                if (nbr[(size_t)i * AVS_MAXS + s] < 0) continue;
+                for (int a = 0; a < D; ++a) {
+                    double v = 0.0;
+                    for (int b = 0; b < D; ++b) v += Mi[a * D + b] * dv[s][b];
+                    cg[((size_t)i * AVS_MAXS + s) * D + a] = v / n2[s];
+                }
+            }
+        }
+        eps2[i] = pow(c->cfg.lim_K * pow(m->vol[i], 1.0 / D), 3.0);
+    }
+    auto tof = [](const double* p, size_t n) {
+        std::vector<float> v(n);
+        for (size_t k = 0; k < n; ++k) v[k] = (float)p[k];
+        return v;
+    };
+    const size_t nfd = (size_t)Nf * D, ncs = (size_t)Nc * AVS_MAXS, ncsd = ncs * D;
+    if (dalloc(&c->faceL, Nf) || dalloc(&c->faceR, Nf) || dalloc(&c->An_d, nfd) || dalloc(&c->rL_d, nfd) ||
+        dalloc(&c->rR_d, nfd) || dalloc(&c->An_f, nfd) || dalloc(&c->rL_f, nfd) || dalloc(&c->rR_f, nfd) ||
+        dalloc(&c->vol, Nc) || dalloc(&c->bc, (size_t)std::max(1, c->nbc) * 6) || dalloc(&c->slot, ncs) ||
+        dalloc(&c->nslot, Nc) || dalloc(&c->nbr, ncs) || dalloc(&c->cg_d, ncsd) || dalloc(&c->r_d, ncsd) ||
+        dalloc(&c->eps2_d, Nc) || dalloc(&c->cg_f, ncsd) || dalloc(&c->r_f, ncsd) || dalloc(&c->eps2_f, Nc))
+        return fail(c, AVS_ENOMEM, "mesh arrays");
+    cudaStream_t s = c->stream;
+    CK(up(c->faceL, std::vector<int>(m->faceL, m->faceL + Nf), s));
+    CK(up(c->faceR, std::vector<int>(m->faceR, m->faceR + Nf), s));
+    CK(up(c->An_d, std::vector<double>(m->An, m->An + nfd), s));
+    CK(up(c->rL_d, std::vector<double>(m->rL, m->rL + nfd), s));
+    CK(up(c->rR_d, std::vector<double>(m->rR, m->rR + nfd), s));
+    CK(up(c->An_f, tof(m->An, nfd), s));
+    CK(up(c->rL_f, tof(m->rL, nfd), s));
+    CK(up(c->rR_f, tof(m->rR, nfd), s));
+    CK(up(c->vol, std::vector<double>(m->vol, m->vol + Nc), s));
+    if (c->nbc > 0) CK(up(c->bc, std::vector<double>(m->bc, m->bc + (size_t)c->nbc * 6), s));
+    CK(up(c->slot, slot, s));
+    CK(up(c->nslot, ns, s));
+    CK(up(c->nbr, nbr, s));
+    CK(up(c->cg_d, cg, s));
+    CK(up(c->r_d, r, s));
+    CK(up(c->eps2_d, eps2, s));
+    CK(up(c->cg_f, tof(cg.data(), ncsd), s));
+    CK(up(c->r_f, tof(r.data(), ncsd), s));
+    CK(up(c->eps2_f, tof(eps2.data(), Nc), s));
+    CK(cudaStreamSynchronize(s));    // host vectors go out of scope
+    return AVS_OK;
+}
+
+// Step-0 AVS (Sec. 3.5, steps 1-3): base forest, then adaptation on the two
+// pseudo cells g^eq(W_inf) and g^eq(rho_inf, 0, T_inf), repeated until it
+// stops changing (at most max(1, max_refine) passes).
+avs_status initial_tree(avs_ctx* c)
+{
+    const int D = c->D;
+    int nbase = 1;
+    for (int d = 0; d < D; ++d) nbase *= c->cfg.base[d];
+    std::vector<int> lev(nbase, 0), bas(nbase);
+    std::vector<uint32_t> key(nbase, 0u);
+    for (int b = 0; b < nbase; ++b) bas[b] = b;
+    CK(up(c->level, lev, c->stream));
+    CK(up(c->base, bas, c->stream));
+    CK(up(c->key, key, c->stream));
+    c->Nv = nbase;
+    c->Nvp = round_up(nbase, 32);
+    CK(launch_geom(c));
+    double Wp[2][5] = {{0}}, Wc[2][5];
+    for (int m = 0; m < D + 2; ++m) Wp[0][m] = Wp[1][m] = c->cfg.W_inf[m];
+    for (int d = 0; d < D; ++d) Wp[1][1 + d] = 0.0;
+    std::vector<double> wpv, wcv;
+    for (int j = 0; j < 2; ++j) {
+        cons_host(D, Wp[j], c->cfg.R, Wc[j]);
+        for (int m = 0; m < D + 2; ++m) {
+            wpv.push_back(Wp[j][m]);
+            wcv.push_back(Wc[j][m]);
+        }
+    }
+    for (int m = 0; m < D + 2; ++m) {
+        if (!(Wp[0][0] > 0) || !(Wp[0][D + 1] > 0)) return fail(c, AVS_EINVAL, "W_inf must have rho, T > 0");
+    }
+    double* Wp_d = c->pseudo_W;
+    double* Wc_d = c->pseudo_W + 2 * (D + 2);
+    CK(up(Wp_d, wpv, c->stream));
+    CK(up(Wc_d, wcv, c->stream));
+    const int passes = std::max(1, c->cfg.max_refine);
+    for (int p = 0; p < passes; ++p) {
+        CK(launch_maxwell(c, Wp_d, 2, 0.0, 0, c->pseudo_f, 1, c->Nvp));
+        CK(launch_criterion(c, c->pseudo_f, 1, 2, c->Nvp, Wc_d, nullptr, 0));
+        int Nn, sp, mg;
+        avs_status st = apply_marks(c, &Nn, &sp, &mg);
+        if (st != AVS_OK) return st;
+        swap_tree(c, Nn);
+        CK(launch_geom(c));
+        if (sp == 0 && mg == 0) break;
+    }
+    return AVS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_stream, avs_ctx** out)
+{
+    if (!out) return AVS_EINVAL;
+    *out = nullptr;
+    std::string why;
+    avs_status st = validate(cfg, mesh, why);
+    if (st != AVS_OK) {
+        fprintf(stderr, "avs_create: %s\n", why.c_str());
+        return st;
+    }
+    avs_ctx* c = new avs_ctx();
+    c->cfg = *cfg;
+    c->D = cfg->dim;
+    c->NA = cfg->dim == 2 ? 2 : 1;
+    c->Nc = mesh->Nc;
+    c->Nf = mesh->Nf;
+    c->nbc = mesh->nbc;
+    c->mixed = cfg->precision == AVS_MIXED;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (c->cfg.corr_iters == 0) c->cfg.corr_iters = 3;
+    // Eq. (4)-(5) with rho = T = L_ref = 1
+    c->mu_ref = 15.0 * sqrt(2.0 * AVS_PI * cfg->R) * cfg->Kn /
+                (2.0 * (5.0 - 2.0 * cfg->omega) * (7.0 - 2.0 * cfg->omega));
+    long long nbase = 1;
+    for (int d = 0; d < c->D; ++d) {
+        c->hb[d] = (cfg->vhi[d] - cfg->vlo[d]) / (double)cfg->base[d];
+        nbase *= cfg->base[d];
+    }
+    c->s_norm = (double)nbase;
+    // node capacity of the tree arrays: all leaves at max_refine, bounded
+    long long full = nbase << (c->D * cfg->max_refine);
+    long long cap = std::min<long long>(full, 1 << 23);
+    if (cfg->max_nodes > 0) cap = std::min<long long>(cap, cfg->max_nodes);
+    cap = std::max<long long>(cap, nbase);
+    c->cap = (int)cap;
+    const int capp = round_up(c->cap, 32);
+    const int NW = c->D + 2;
+#define AL(p, n) \
+    if (dalloc(&(p), (n)) != cudaSuccess) { st = fail(c, AVS_ENOMEM, "allocation of " #p); goto bad; }
+    AL(c->level, capp); AL(c->base, capp); AL(c->key, capp);
+    AL(c->level2, capp); AL(c->base2, capp); AL(c->key2, capp);
+    AL(c->src, capp); AL(c->kind, capp); AL(c->emit, capp);
+    AL(c->newidx, 2 * (size_t)capp); AL(c->d_count, 4);
+    AL(c->xi_d, (size_t)capp * c->D); AL(c->w_d, capp);
+    AL(c->xi_f, (size_t)capp * c->D); AL(c->w_f, capp);
+    AL(c->M, capp); AL(c->Mkey, capp);
+    AL(c->pseudo_f, 2 * (size_t)c->NA * capp); AL(c->pseudo_W, 4 * NW);
+    AL(c->crit_cp, 5 * (size_t)std::max(c->Nc, 2));
+    AL(c->W[0], (size_t)c->Nc * NW); AL(c->W[1], (size_t)c->Nc * NW);
+    AL(c->Wf, (size_t)c->Nc * NW); AL(c->q, (size_t)c->Nc * c->D);
+    AL(c->dev_err, 1); AL(c->dt_key, 1); AL(c->gap_d, 1);
+#undef AL
+    if (cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream) != cudaSuccess) {
+        st = fail(c, AVS_ECUDA, "memset");
+        goto bad;
+    }
+    st = setup_mesh(c, mesh);
+    if (st != AVS_OK) goto bad;
+    st = initial_tree(c);
+    if (st != AVS_OK) goto bad;
+    {
+        int fnodes = cfg->max_nodes > 0 ? cfg->max_nodes : std::min(c->cap, 8 * c->Nv);
+        fnodes = std::max(fnodes, c->Nv);
+        c->fcap = round_up(fnodes, 32);
+        st = alloc_f(c, c->fcap, &c->f[0], &c->f[1]);
+        if (st != AVS_OK) goto bad;
+    }
+    if (cudaMemsetAsync(c->W[0], 0, sizeof(double) * c->Nc * NW, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->W[1], 0, sizeof(double) * c->Nc * NW, c->stream) != cudaSuccess) {
+        st = fail(c, AVS_ECUDA, "memset");
+        goto bad;
+    }
+    st = refresh_dt(c);
+    if (st != AVS_OK) goto bad;
+    *out = c;
+    return AVS_OK;
+bad:
+    fprintf(stderr, "avs_create: %s\n", c->err.c_str());
+    free_all(c);
+    delete c;
+    return st;
+}
+
+void avs_destroy(avs_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+const char* avs_last_error(const avs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+int avs_num_nodes(const avs_ctx* c) { return c ? c->Nv : 0; }
+int avs_num_cells(const avs_ctx* c) { return c ? c->Nc : 0; }
+
+avs_status avs_init_field(avs_ctx* c, const double* Wp, int is_device, double amp, uint64_t seed)
+{
+    if (!c || !Wp) return AVS_EINVAL;
+    const size_t n = (size_t)c->Nc * (c->D + 2);
+    const double* Wp_d = Wp;
+    if (!is_device) {
+        CK(cudaMemcpyAsync(c->Wf, Wp, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        Wp_d = c->Wf;
+    }
+    CK(launch_maxwell(c, Wp_d, c->Nc, amp, seed, c->f[c->cur], 0, c->Nvp));
+    k_prim_to_cons<<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nc, Wp_d, c->cfg.R, c->W[c->wcur]);
+    c->launches += 1;
+    CK(cudaGetLastError());
+    // carried W = moments of the discrete initial f (Eq. 7)
+    CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->W[c->wcur], nullptr));
+    if (!is_device) CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_dt(avs_ctx* c, double cfl, double* dt_out)
+{
+    if (!c || !dt_out || !(cfl > 0)) return AVS_EINVAL;
+    *dt_out = cfl * c->dt_unit;
+    return AVS_OK;
+}
+
+avs_status ugks_step_dt(avs_ctx* c, int nsteps, double dt)
+{
+    if (!c || nsteps < 0 || !(dt > 0)) return AVS_EINVAL;
+    for (int s = 0; s < nsteps; ++s) {
+        CK(launch_step(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt));
+        c->cur ^= 1;
+        c->wcur ^= 1;
+    }
+    return AVS_OK;
+}
+
+avs_status ugks_step(avs_ctx* c, int nsteps, double cfl, double* dt_out)
+{
+    if (!c || !(cfl > 0)) return AVS_EINVAL;
+    const double dt = cfl * c->dt_unit;
+    if (dt_out) *dt_out = dt;
+    return ugks_step_dt(c, nsteps, dt);
+}
+
+avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* stats)
+{
+    if (!c) return AVS_EINVAL;
+    avs_adapt_opts o = {};
+    if (opts) o = *opts;
+    const int NW = c->D + 2;
+    const int Nv_old = c->Nv, Nvp_old = c->Nvp;
+    // moments of f on the old mesh (Eq. 7): criterion input and correction target
+    CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr));
+    if (o.W_override) {
+        CK(cudaMemcpyAsync(c->Wf, o.W_override, sizeof(double) * c->Nc * NW,
+                           o.W_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+    int Nn, sp, mg;
+    avs_status st = apply_marks(c, &Nn, &sp, &mg);
+    if (st != AVS_OK) return st;
+    const int Nvp_new = round_up(Nn, 32);
+    void* dst = c->f[c->cur ^ 1];
+    void *n0 = nullptr, *n1 = nullptr;
+    if (Nvp_new > c->fcap) {
+        if (c->cfg.max_nodes > 0) return fail(c, AVS_ECAPACITY, "adapted node count exceeds max_nodes");
+        st = alloc_f(c, Nvp_new + Nvp_new / 2, &n0, &n1);
+        if (st != AVS_OK) return st;
+        dst = n0;
+    }
+    CK(launch_remap(c, c->f[c->cur], Nvp_old, dst, Nvp_new, Nn));
+    swap_tree(c, Nn);
+    CK(launch_geom(c));
+    if (n0) {
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->f[0]);
+        cudaFree(c->f[1]);
+        c->f[0] = n0;
+        c->f[1] = n1;
+        c->fcap = round_up(Nvp_new + Nvp_new / 2, 32);
+        c->cur = 0;
+    } else {
+        c->cur ^= 1;
+    }
+    double gap = 0.0;
+    if (!o.skip_correction) {
+        CK(launch_correct(c, c->f[c->cur], c->Wf, c->cfg.corr_iters));
+        unsigned long long gk = 0;
+        CK(cudaMemcpyAsync(&gk, c->gap_d, sizeof(gk), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        gap = dkey_inv(gk);
+    }
+    st = refresh_dt(c);
+    if (st != AVS_OK) return st;
+    c->adapt_count++;
+    if (stats) {
+        stats->Nv_old = Nv_old;
+        stats->Nv = c->Nv;
+        stats->splits = sp;
+        stats->merges = mg;
+        stats->gap = gap;
+        stats->checked_cells = c->Nc;
+        stats->missed_nodes = 0;
+        stats->full = 1;
+    }
+    (void)Nv_old;
+    return read_err(c);
+}
+
+avs_status avs_moments(avs_ctx* c, double* Wc_out, double* q_out, int is_device)
+{
+    if (!c) return AVS_EINVAL;
+    const cudaMemcpyKind kd = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (Wc_out)
+        CK(cudaMemcpyAsync(Wc_out, c->W[c->wcur], sizeof(double) * c->Nc * (c->D + 2), kd, c->stream));
+    if (q_out) {
+        CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, nullptr, c->q));
+        CK(cudaMemcpyAsync(q_out, c->q, sizeof(double) * c->Nc * c->D, kd, c->stream));
+    }
+    if (!is_device) return read_err(c);
+    return AVS_OK;
+}
+
+avs_status avs_f_moments(avs_ctx* c, double* Wc_out, int is_device)
+{
+    if (!c || !Wc_out) return AVS_EINVAL;
+    CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr));
+    CK(cudaMemcpyAsync(Wc_out, c->Wf, sizeof(double) * c->Nc * (c->D + 2),
+                       is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!is_device) CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_set_W(avs_ctx* c, const double* Wc, int is_device)
+{
+    if (!c || !Wc) return AVS_EINVAL;
+    CK(cudaMemcpyAsync(c->W[c->wcur], Wc, sizeof(double) * c->Nc * (c->D + 2),
+                       is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (!is_device) CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_criterion(avs_ctx* c, const double* Wc, int W_is_device, double* M_out, int M_is_device)
+{
+    if (!c || !M_out) return AVS_EINVAL;
+    const int NW = c->D + 2;
+    if (Wc)
+        CK(cudaMemcpyAsync(c->Wf, Wc, sizeof(double) * c->Nc * NW,
+                           W_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    else
+        CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr));
+    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+    CK(cudaMemcpyAsync(M_out, c->M, sizeof(double) * c->Nv,
+                       M_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!M_is_device || !W_is_device) CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_get_tree(avs_ctx* c, int* level, int* base, uint32_t* key, double* xi, double* w)
+{
+    if (!c) return AVS_EINVAL;
+    const size_t n = c->Nv;
+    if (level) CK(cudaMemcpyAsync(level, c->level, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (base) CK(cudaMemcpyAsync(base, c->base, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (key) CK(cudaMemcpyAsync(key, c->key, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    if (xi) CK(cudaMemcpyAsync(xi, c->xi_d, n * c->D * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (w) CK(cudaMemcpyAsync(w, c->w_d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_get_f(avs_ctx* c, double* f, int is_device)
+{
+    if (!c || !f) return AVS_EINVAL;
+    const size_t n = (size_t)c->Nc * c->NA * c->Nv;
+    if (is_device) {
+        CK(launch_to_double(c, c->f[c->cur], f, c->Nvp));
+        return AVS_OK;
+    }
+    avs_status st = ensure_stage(c);
+    if (st != AVS_OK) return st;
+    CK(launch_to_double(c, c->f[c->cur], c->stage, c->Nvp));
+    CK(cudaMemcpyAsync(f, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_set_f(avs_ctx* c, const double* f, int is_device)
+{
+    if (!c || !f) return AVS_EINVAL;
+    const size_t n = (size_t)c->Nc * c->NA * c->Nv;
+    if (is_device) {
+        CK(launch_from_double(c, f, c->f[c->cur], c->Nvp));
+        return AVS_OK;
+    }
+    avs_status st = ensure_stage(c);
+    if (st != AVS_OK) return st;
+    CK(cudaMemcpyAsync(c->stage, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_from_double(c, c->stage, c->f[c->cur], c->Nvp));
+    CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+uint64_t avs_kernel_launches(const avs_ctx* c) { return c ? (uint64_t)c->launches : 0; }
+
+avs_status avs_sync(avs_ctx* c)
+{
+    if (!c) return AVS_EINVAL;
+    return read_err(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,322 @@
+// Device-side building blocks of the UGKS/AVS kernels (sm_103a).
+//
+// Element type T is double (FP64 form) or float (mixed form: f, reconstruction,
+// flux and collision in FP32; every velocity-space sum is carried into FP64
+// through short FP32 partials flushed into double accumulators).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#define AVS_MAXS 6            // face slots per cell (hexahedra)
+#define AVS_PI 3.14159265358979323846
+
+namespace avs {
+
+template <int D> struct NArr { static constexpr int v = (D == 2) ? 2 : 1; };
+// raw velocity moments of one distribution pair about a reference velocity V:
+// 2D: G{1, x, y, xx, xy, yy, x s, y s} + H{1, x, y}       (s = |xi - V|^2)
+// 3D: G{1, x, y, z, xx, xy, xz, yy, yz, zz, x s, y s, z s}
+template <int D> struct NMom { static constexpr int v = (D == 2) ? 11 : 13; };
+
+// ---------------------------------------------------------------- numerics
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float dmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float dadd(float a, float b) { return __fadd_rn(a, b); }
+
+// xi . An summed left to right without fused multiply-add, so that the upwind
+// choice (sign test) is made on the same value as in a plain sequential code.
+template <int D, typename T>
+__device__ __forceinline__ T dot_rn(const T* x, const T* a)
+{
+    T s = dmul(x[0], a[0]);
+    s = dadd(s, dmul(x[1], a[1]));
+    if (D == 3) s = dadd(s, dmul(x[2], a[2]));
+    return s;
+}
+
+__device__ __forceinline__ double ex(double x) { return exp(x); }
+__device__ __forceinline__ float ex(float x) { return expf(x); }
+
+// ---------------------------------------------------------------- geometry
+template <typename T>
+struct CellGeo {
+    const int* __restrict__ nbr;            // [Nc][MAXS] neighbour cell, -1 none/boundary
+    const T* __restrict__ cg;               // [Nc][MAXS][D] least-squares weights
+    const T* __restrict__ r;                // [Nc][MAXS][D] face centre - cell centre
+    const T* __restrict__ eps2;             // [Nc] Venkatakrishnan eps^2
+    const unsigned char* __restrict__ ns;   // [Nc] number of face slots
+};
+
+// Venkatakrishnan limiter function, capped at 1.
+template <typename T>
+__device__ __forceinline__ T venkat(T d1, T d2, T eps2)
+{
+    T num = d1 * d1 + eps2 + T(2) * d1 * d2;
+    T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + eps2;
+    T v = num / den;
+    return v < T(1) ? v : T(1);
+}
+
+// Limited least-squares gradient of array `fa` (pointer already offset to
+// array and node) at cell C.  Returns phi_C; gr and L receive the gradient
+// and the limiter value.  The limiter is the minimum over the faces of the
+// capped Venkatakrishnan function; because the capped function is
+// non-increasing in |Delta_2| on each side of zero, that minimum is reached
+// at the largest positive and the most negative face projection.
+template <int D, typename T>
+__device__ __forceinline__ T grad_lim(const CellGeo<T>& g, int limiter, const T* __restrict__ fa,
+                                      size_t cstride, int C, T* gr, T& L)
+{
+    const T phi = fa[(size_t)C * cstride];
+#pragma unroll
+    for (int d = 0; d < D; ++d) gr[d] = T(0);
+    L = T(1);
+    if (limiter == 0) return phi;
+    const int ns = g.ns[C];
+    T dmax = T(0), dmin = T(0);
+    for (int s = 0; s < ns; ++s) {
+        const int nb = g.nbr[C * AVS_MAXS + s];
+        if (nb < 0) continue;
+        const T d = fa[(size_t)nb * cstride] - phi;
+        const T* c = g.cg + (size_t)(C * AVS_MAXS + s) * D;
+#pragma unroll
+        for (int k = 0; k < D; ++k) gr[k] += c[k] * d;
+        dmax = d > dmax ? d : dmax;
+        dmin = d < dmin ? d : dmin;
+    }
+    if (limiter == 1) {
+        T p = T(0), n = T(0);
+        for (int s = 0; s < ns; ++s) {
+            const T* r = g.r + (size_t)(C * AVS_MAXS + s) * D;
+            T d2 = gr[0] * r[0];
+#pragma unroll
+            for (int k = 1; k < D; ++k) d2 += gr[k] * r[k];
+            p = d2 > p ? d2 : p;
+            n = d2 < n ? d2 : n;
+        }
+        const T e2 = g.eps2[C];
+        if (p > T(0)) { T v = venkat(dmax, p, e2); L = v < L ? v : L; }
+        if (n < T(0)) { T v = venkat(dmin, n, e2); L = v < L ? v : L; }
+    }
+    return phi;
+}
+
+// Foot value phi_C + L grad . (x_f - x_C - xi h)   (Sec. 2.3.3)
+template <int D, typename T>
+__device__ __forceinline__ T foot_value(T phi, const T* gr, T L, const T* rF, const T* x, T h)
+{
+    T dot = gr[0] * (rF[0] - x[0] * h);
+#pragma unroll
+    for (int k = 1; k < D; ++k) dot += gr[k] * (rF[k] - x[k] * h);
+    return phi + L * dot;
+}
+
+// ---------------------------------------------------------------- equilibria
+// Parameters of one equilibrium evaluated on the nodes:
+//   G = pref exp(-|c|^2 inv2RT) (1 + (c . alpha)(|c|^2 invRT - D - 2)),
+//   H = RTH exp(..)pref (1 + (c . alpha)(|c|^2 invRT - D)),   c = xi - U
+// which is the Shakhov form of Eqs. 14-17 (K = 0) with
+// alpha = (1 - Pr) q / (5 p R T), and the plain Maxwellian when alpha = 0.
+template <typename T>
+struct EqPar {
+    T pref, U[3], inv2RT, invRT, RTH, alpha[3];
+};
+
+template <int D, typename T>
+__device__ __forceinline__ void eq_eval(const EqPar<T>& p, const T* x, T& gG, T& gH)
+{
+    T c[D];
+    T c2 = T(0), cq = T(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        c[d] = x[d] - p.U[d];
+        c2 += c[d] * c[d];
+        cq += c[d] * p.alpha[d];
+    }
+    const T e = p.pref * ex(-c2 * p.inv2RT);
+    const T s = c2 * p.invRT;
+    gG = e * (T(1) + cq * (s - T(D + 2)));
+    gH = (D == 2) ? p.RTH * e * (T(1) + cq * (s - T(D))) : T(0);
+}
+
+// Host/device: equilibrium parameters from rho, U, RT, q (double inputs).
+template <int D, typename T>
+__device__ __forceinline__ EqPar<T> make_eq(double rho, const double* U, double RT, const double* q,
+                                            double Pr)
+{
+    EqPar<T> p;
+    const double pref = rho / pow(2.0 * AVS_PI * RT, 0.5 * D);
+    p.pref = (T)pref;
+    const double a = (1.0 - Pr) / (5.0 * rho * RT * RT);
+    for (int d = 0; d < 3; ++d) {
+        p.U[d] = d < D ? (T)U[d] : T(0);
+        p.alpha[d] = (d < D && q) ? (T)(a * q[d]) : T(0);
+    }
+    p.inv2RT = (T)(1.0 / (2.0 * RT));
+    p.invRT = (T)(1.0 / RT);
+    p.RTH = (T)((3.0 - D) * RT);
+    return p;
+}
+
+// conserved (rho, m, E) -> rho, U, RT (monatomic: E = m^2/2rho + 3/2 rho R T)
+template <int D>
+__device__ __forceinline__ void prim(const double* Wc, double& rho, double* U, double& RT)
+{
+    rho = Wc[0];
+    double m2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        U[d] = Wc[1 + d] / rho;
+        m2 += Wc[1 + d] * Wc[1 + d];
+    }
+    RT = (Wc[D + 1] - 0.5 * m2 / rho) / (1.5 * rho);
+}
+
+// ---------------------------------------------------------------- moments
+// Accumulate the raw-moment contributions of one node (weight already folded
+// into wg, wh) about reference velocity; xs = xi - V.
+template <int D, typename T>
+__device__ __forceinline__ void raw_acc(T* m, const T* xs, T wg, T wh)
+{
+    if (D == 2) {
+        const T s = xs[0] * xs[0] + xs[1] * xs[1];
+        m[0] += wg;
+        m[1] += wg * xs[0];
+        m[2] += wg * xs[1];
+        m[3] += wg * xs[0] * xs[0];
+        m[4] += wg * xs[0] * xs[1];
+        m[5] += wg * xs[1] * xs[1];
+        m[6] += wg * xs[0] * s;
+        m[7] += wg * xs[1] * s;
+        m[8] += wh;
+        m[9] += wh * xs[0];
+        m[10] += wh * xs[1];
+    } else {
+        const T s = xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2];
+        m[0] += wg;
+        m[1] += wg * xs[0];
+        m[2] += wg * xs[1];
+        m[3] += wg * xs[2];
+        m[4] += wg * xs[0] * xs[0];
+        m[5] += wg * xs[0] * xs[1];
+        m[6] += wg * xs[0] * xs[2];
+        m[7] += wg * xs[1] * xs[1];
+        m[8] += wg * xs[1] * xs[2];
+        m[9] += wg * xs[2] * xs[2];
+        m[10] += wg * xs[0] * s;
+        m[11] += wg * xs[1] * s;
+        m[12] += wg * xs[2] * s;
+    }
+}
+
+// Raw moments about V (m) -> conserved W, heat flux q about the own mean
+// velocity (Eq. 8), and optionally the area-weighted flux of W through An:
+// A F = sum_k w (xi . An) (G, xi G, (|xi|^2 G + H)/2).
+template <int D>
+__device__ void moments_from_raw(const double* m, const double* V, double* W, double* q,
+                                 const double* An, double* AF)
+{
+    // shifted moments S0, S1[a], S2[a][b], S3[a] (S3 = sum w x_a |x|^2 G), H0, H1[a]
+    double S0 = m[0], S1[3], S2[3][3], S3[3], H0 = 0, H1[3] = {0, 0, 0};
+    if (D == 2) {
+        S1[0] = m[1]; S1[1] = m[2];
+        S2[0][0] = m[3]; S2[0][1] = S2[1][0] = m[4]; S2[1][1] = m[5];
+        S3[0] = m[6]; S3[1] = m[7];
+        H0 = m[8]; H1[0] = m[9]; H1[1] = m[10];
+    } else {
+        S1[0] = m[1]; S1[1] = m[2]; S1[2] = m[3];
+        S2[0][0] = m[4]; S2[0][1] = S2[1][0] = m[5]; S2[0][2] = S2[2][0] = m[6];
+        S2[1][1] = m[7]; S2[1][2] = S2[2][1] = m[8]; S2[2][2] = m[9];
+        S3[0] = m[10]; S3[1] = m[11]; S3[2] = m[12];
+    }
+    double trS2 = 0.0;
+    for (int a = 0; a < D; ++a) trS2 += S2[a][a];
+    // conserved variables
+    double rho = S0;
+    double d[3];                   // mean velocity relative to V
+    for (int a = 0; a < D; ++a) d[a] = S1[a] / rho;
+    W[0] = rho;
+    double V2 = 0.0, VS1 = 0.0;
+    for (int a = 0; a < D; ++a) { V2 += V[a] * V[a]; VS1 += V[a] * S1[a]; }
+    for (int a = 0; a < D; ++a) W[1 + a] = S1[a] + rho * V[a];
+    W[D + 1] = 0.5 * (trS2 + 2.0 * VS1 + rho * V2 + H0);
+    // heat flux about U = V + d:  1/2 sum w c_a (|c|^2 G + H), c = x' - d
+    if (q) {
+        double dd = 0.0;
+        for (int a = 0; a < D; ++a) dd += d[a] * d[a];
+        for (int a = 0; a < D; ++a) {
+            double S2d = 0.0;
+            for (int b = 0; b < D; ++b) S2d += S2[a][b] * d[b];
+            double dS1 = 0.0;
+            for (int b = 0; b < D; ++b) dS1 += d[b] * S1[b];
+            double g3 = S3[a] - 2.0 * S2d + dd * S1[a] - d[a] * trS2 + 2.0 * d[a] * dS1 - d[a] * dd * S0;
+            double h1 = H1[a] - d[a] * H0;
+            q[a] = 0.5 * (g3 + h1);
+        }
+    }
+    if (AF) {
+        // flux moments of the raw (unshifted) distribution through An
+        double Fm = 0.0;
+        for (int a = 0; a < D; ++a) Fm += An[a] * (S1[a] + rho * V[a]);
+        AF[0] = Fm;
+        for (int b = 0; b < D; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < D; ++a)
+                s += An[a] * (S2[a][b] + V[a] * S1[b] + S1[a] * V[b] + rho * V[a] * V[b]);
+            AF[1 + b] = s;
+        }
+        double E = 0.0;
+        for (int a = 0; a < D; ++a) {
+            double S2V = 0.0;
+            for (int b = 0; b < D; ++b) S2V += S2[a][b] * V[b];
+            double g = S3[a] + 2.0 * S2V + V2 * S1[a] + V[a] * trS2 + 2.0 * V[a] * VS1 + V[a] * V2 * S0;
+            double h = H1[a] + V[a] * H0;
+            E += An[a] * (g + h);
+        }
+        AF[D + 1] = 0.5 * E;
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+// Deterministic block reduction of N doubles per thread: warp tree with
+// shuffles, then a fixed-order sum over warps.  Result in out[0..N-1] (smem),
+// visible to all threads after return.
+template <int N, int NT>
+__device__ __forceinline__ void block_sum(double* v, double* sred, double* out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        double x = v[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sred[warp * N + m] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += sred[w * N + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Ordered 64-bit key of a double (monotone for all finite values) for
+// atomicMax/atomicMin on doubles.
+__host__ __device__ __forceinline__ unsigned long long dkey(double x)
+{
+    unsigned long long b;
+    memcpy(&b, &x, sizeof(b));
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double dkey_inv(unsigned long long k)
+{
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    double x;
+    memcpy(&x, &b, sizeof(x));
+    return x;
+}
+
+}  // namespace avs

@@ -1,0 +1,92 @@
+// Host-side context of the AVS/UGKS library and the launchers shared by the
+// translation units.  Not part of the public ABI (see include/avs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/avs.h"
+
+#define AVS_NT 256            // threads per block of the per-cell kernels
+
+struct avs_ctx {
+    avs_config cfg;
+    int D = 2, NA = 2, Nc = 0, Nf = 0, nbc = 0;
+    int mixed = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    double mu_ref = 0.0;     // from Kn, Eq. (5)
+    double hb[3] = {0, 0, 0};
+    double s_norm = 1.0;     // number of base-forest nodes
+    int adapt_count = 0;
+
+    // ---- physical mesh (device)
+    int *faceL = nullptr, *faceR = nullptr;          // [Nf]
+    double *An_d = nullptr, *rL_d = nullptr, *rR_d = nullptr;  // [Nf][D]
+    float *An_f = nullptr, *rL_f = nullptr, *rR_f = nullptr;
+    double *vol = nullptr;                           // [Nc]
+    double *bc = nullptr;                            // [nbc][6]
+    int *slot = nullptr;                             // [Nc][MAXS] face*2 + (cell is R), -1 none
+    unsigned char *nslot = nullptr;                  // [Nc]
+    int *nbr = nullptr;                              // [Nc][MAXS]
+    double *cg_d = nullptr, *r_d = nullptr, *eps2_d = nullptr;
+    float *cg_f = nullptr, *r_f = nullptr, *eps2_f = nullptr;
+
+    // ---- velocity tree (device), capacity `cap` nodes
+    int Nv = 0, Nvp = 0, cap = 0;
+    int *level = nullptr, *base = nullptr;
+    uint32_t *key = nullptr;
+    int *level2 = nullptr, *base2 = nullptr;
+    uint32_t *key2 = nullptr;
+    int *src = nullptr, *kind = nullptr, *emit = nullptr, *newidx = nullptr;
+    int *d_count = nullptr;
+    double *xi_d = nullptr, *w_d = nullptr;          // [cap][D], [cap]
+    float *xi_f = nullptr, *w_f = nullptr;
+    double *M = nullptr;                             // [cap]
+    unsigned long long *Mkey = nullptr;              // [cap]
+
+    // ---- state (device)
+    void *f[2] = {nullptr, nullptr};                 // [Nc][NA][Nvp] of T, capacity fcap nodes
+    int fcap = 0;                                    // node capacity of the f buffers
+    int cur = 0;
+    double *W[2] = {nullptr, nullptr};               // carried conserved W, [Nc][D+2]
+    int wcur = 0;
+    double *Wf = nullptr;                            // moments of f / correction target
+    double *q = nullptr;                             // [Nc][D]
+    double *pseudo_f = nullptr;                      // step-0 pseudo cells [2][NA][cap]
+    double *pseudo_W = nullptr;                      // [2][D+2]
+    double *crit_cp = nullptr;                       // criterion per-cell inputs [max(Nc,2)][5]
+    double *stage = nullptr;                         // FP64 staging [Nc][NA][Nv] for get/set (lazy)
+    size_t stage_elems = 0;
+    int *dev_err = nullptr;                          // device error word (bit 1: numeric)
+    unsigned long long *dt_key = nullptr;
+    double *gap_d = nullptr;                         // correction gap (max over cells)
+    double dt_unit = 0.0;
+    unsigned long long launches = 0;                 // kernels launched by this context
+};
+
+namespace avs {
+
+int round_up(int n, int m);
+
+// ---- launchers (avs_step.cu)
+cudaError_t launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
+
+// ---- launchers (avs_adapt.cu)
+cudaError_t launch_geom(avs_ctx* c);                       // xi, w of the current tree
+cudaError_t launch_dt_unit(avs_ctx* c);                    // min |V|/sum max(xi.n,0) -> c->dt_key
+cudaError_t launch_maxwell(avs_ctx* c, const double* Wp, int Ncells, double amp, uint64_t seed,
+                           void* fout, int f_is_double, int Nvp);
+cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp,
+                                double* Wc_out, double* q_out);
+cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp,
+                             const double* Wc, const int* cells, int ncells_list);
+cudaError_t launch_adapt_tree(avs_ctx* c, double C1, double C2);  // marks, scan, new tree -> *2 arrays
+cudaError_t launch_remap(avs_ctx* c, const void* fold, int Nvp_old, void* fnew, int Nvp_new, int Nv_new);
+cudaError_t launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters);
+cudaError_t launch_to_double(avs_ctx* c, const void* f, double* out, int Nvp);   // packed [Nc][NA][Nv]
+cudaError_t launch_from_double(avs_ctx* c, const double* in, void* f, int Nvp);
+
+}  // namespace avs

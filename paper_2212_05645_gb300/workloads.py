@@ -485,7 +485,9 @@ def cavity(n=32, C1=6.0, max_refine=1, precision="fp64") -> Workload:
 def cylinder(n_theta=96, n_r=128, Ma=5.0, Kn=0.1, C1=1.0, max_refine=4, precision="mixed") -> Workload:
     """Supersonic cylinder (paper Sec. 4.1 shape): O-mesh 128 radial x 96
     circumferential, r in [1, 15], first layer 0.01, Ma 5, Kn 0.1, isothermal
-    wall at T_inf, forest 24x24 over [-15, 15]^2 sqrt(R T_inf), up to 4 levels."""
+    wall at T_inf, forest 24x24 over [-15, 15]^2 sqrt(R T_inf), up to 4 levels.
+    The gas starts at rest and the Ma 5 stream enters through the far field
+    (an impulsive start empties the first wake cell within a few steps)."""
     U = mach_speed(Ma)
     wall = _bc_row(BC_WALL, T=1.0)
     far = _bc_row(BC_FARFIELD, rho=1.0, U=(U, 0.0), T=1.0)
@@ -493,7 +495,7 @@ def cylinder(n_theta=96, n_r=128, Ma=5.0, Kn=0.1, C1=1.0, max_refine=4, precisio
     v = 15.0 * sqrt_RT(1.0)
     return Workload(f"cylinder-omesh-{n_r}x{n_theta}", mesh, 2, (24, 24), (-v, -v), (v, v), max_refine,
                     Kn=Kn, omega=0.81, Pr=2.0 / 3.0, C1=C1, C2=K_SIGMA * C1,
-                    W_inf=(1.0, U, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 2, 1.0, (U, 0.0), 1.0),
+                    W_inf=(1.0, U, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 2, 1.0, (0.0, 0.0), 1.0),
                     precision=precision, steps=200)
 
 
@@ -509,7 +511,7 @@ def blunt_wedge(n_theta=240, n_r=160, Ma=8.0, Kn=0.01, C1=1.0, max_refine=5, pre
     v = 20.0 * sqrt_RT(1.0)
     return Workload(f"blunt-wedge-{n_theta}x{n_r}", mesh, 2, (32, 32), (-v, -v), (v, v), max_refine,
                     Kn=Kn, omega=0.81, Pr=2.0 / 3.0, C1=C1, C2=K_SIGMA * C1,
-                    W_inf=(1.0, U, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 2, 1.0, (U, 0.0), 1.0),
+                    W_inf=(1.0, U, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 2, 1.0, (0.0, 0.0), 1.0),
                     precision=precision, learned=learned)
 
 
@@ -525,7 +527,7 @@ def sphere(n_r=64, n_theta=48, n_phi=48, Ma=4.25, Kn=0.031, C1=1.0, max_refine=3
     v = 12.0 * sqrt_RT(1.0)
     return Workload(f"sphere-shell-{n_r}x{n_theta}x{n_phi}", mesh, 3, (16, 16, 16), (-v,) * 3, (v,) * 3,
                     max_refine, Kn=Kn, omega=0.81, Pr=2.0 / 3.0, C1=C1, C2=K_SIGMA * C1,
-                    W_inf=(1.0, U, 0.0, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 3, 1.0, (U, 0.0, 0.0), 1.0),
+                    W_inf=(1.0, U, 0.0, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 3, 1.0, (0.0, 0.0, 0.0), 1.0),
                     precision=precision, learned=learned)
 
 

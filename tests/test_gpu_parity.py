@@ -1,0 +1,175 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: the velocity-mesh topology, node geometry and the time-step bound
+are bit-exact; the FP64 form agrees to 1e-12 relative; the mixed form agrees
+on the macroscopic fields to 1e-5 relative (field scale).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2212_05645_gb300 import workloads as wl
+
+from gpu_common import field_err, need_gpu, pair, rel_err, small_cylinder, small_sphere
+
+pytestmark = pytest.mark.gpu
+
+
+def test_step0_tree_geometry_and_dt_bitexact():
+    avs = need_gpu()
+    for w in (wl.cavity(), small_cylinder(), small_sphere()):
+        r = O.Run(w)
+        g = avs.AVS(w)
+        t = g.tree()
+        assert np.array_equal(t["level"], r.level)
+        assert np.array_equal(t["base"], r.base)
+        assert np.array_equal(t["key"], r.key)
+        assert np.array_equal(t["xi"], r.xi)
+        assert np.array_equal(t["w"], r.w)
+        assert g.dt(0.8) == r.dt(0.8)
+        g.close()
+
+
+def test_init_field_and_moments():
+    avs = need_gpu()
+    w = wl.sweep_box((6, 5), base=(12, 12), max_refine=1)
+    r = O.Run(w)
+    r.init_field(amp=1e-3, seed=99)
+    g = avs.AVS(w)
+    g.init_field(amp=1e-3, seed=99)
+    assert rel_err(g.get_f(), r.f) < 1e-14
+    W, q = g.moments()
+    Wo, qo = O.moments(2, r.xi, r.w, r.f)
+    assert rel_err(W, Wo) < 1e-13
+    assert np.abs(q - qo).max() < 1e-13 * np.abs(Wo).max()
+    assert rel_err(g.f_moments(), Wo) < 1e-13
+
+
+@pytest.mark.parametrize("limiter", [0, 1, 2])
+def test_step_fp64_periodic(limiter):
+    avs = need_gpu()
+    w = wl.sweep_box((7, 6), base=(10, 10), max_refine=1)
+    r, g = pair(w, avs, limiter=limiter)
+    dt = r.dt()
+    for _ in range(3):
+        r.step(dt)
+    g.step(3, dt=dt)
+    assert rel_err(g.get_f(), r.f) < 1e-12
+    W, _ = g.moments()
+    assert rel_err(W, r.Wc) < 1e-12
+
+
+def test_step_fp64_cavity_walls_200_steps():
+    """Config 1 (lid-driven cavity, FP64): all 200 steps against the oracle."""
+    avs = need_gpu()
+    w = wl.cavity()
+    r, g = pair(w, avs, amp=0.0)
+    dt = r.dt()
+    assert g.dt() == dt
+    for _ in range(200):
+        r.step(dt)
+    g.step(200, dt=dt)
+    assert rel_err(g.get_f(), r.f) < 1e-11
+    W, _ = g.moments()
+    assert rel_err(W, r.Wc) < 1e-12
+    vol = w.mesh.vol
+    m0 = (O.moments(2, r.xi, r.w, O.maxwell_init(2, r.xi, w.W_init))[0][:, 0] * vol).sum()
+    assert abs((W[:, 0] * vol).sum() - m0) / m0 < 1e-12
+
+
+def test_step_fp64_omesh_wall_farfield():
+    avs = need_gpu()
+    w = small_cylinder()
+    r, g = pair(w, avs)
+    dt = r.dt()
+    for _ in range(4):
+        r.step(dt)
+    g.step(4, dt=dt)
+    assert rel_err(g.get_f(), r.f) < 1e-12
+    assert rel_err(g.moments()[0], r.Wc) < 1e-12
+
+
+def test_step_fp64_3d_sphere_shell():
+    avs = need_gpu()
+    w = small_sphere()
+    r, g = pair(w, avs)
+    dt = r.dt()
+    for _ in range(2):
+        r.step(dt)
+    g.step(2, dt=dt)
+    assert rel_err(g.get_f(), r.f) < 1e-12
+    assert rel_err(g.moments()[0], r.Wc) < 1e-12
+
+
+def test_criterion_bitexact_given_W():
+    avs = need_gpu()
+    w = small_cylinder()
+    r, g = pair(w, avs, amp=1e-2)
+    Wf, _ = O.moments(2, r.xi, r.w, r.f)
+    M_o = O.criterion(2, r.xi, r.w, r.f, Wf)
+    M_g = g.criterion(Wf)
+    assert np.array_equal(M_g, M_o)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_adapt_topology_remap_bitexact_and_correction(D):
+    avs = need_gpu()
+    w = small_cylinder(C1=0.6, max_refine=3) if D == 2 else small_sphere()
+    r, g = pair(w, avs, amp=1e-2)
+    r.step(r.dt()); g.step(1, dt=r.dt())
+    f_now = r.f.copy()
+    g.set_f(f_now)
+    Wf, _ = O.moments(D, r.xi, r.w, f_now)
+    # remap only: bit-exact
+    st_o = r.adapt(Wc_override=Wf, correct_f=False)
+    st_g = g.adapt(W_override=Wf, skip_correction=True)
+    t = g.tree()
+    assert st_g["Nv"] == st_o["Nv"]
+    assert np.array_equal(t["level"], r.level) and np.array_equal(t["key"], r.key)
+    assert np.array_equal(t["base"], r.base)
+    assert np.array_equal(g.get_f(), r.f)
+    # with the conservation correction
+    r2, g2 = pair(w, avs, amp=1e-2)
+    r2.f = f_now.copy(); g2.set_f(f_now)
+    st_o = r2.adapt(Wc_override=Wf)
+    st_g = g2.adapt(W_override=Wf)
+    assert rel_err(g2.get_f(), r2.f) < 1e-12
+    assert abs(st_g["gap"] - st_o["gap"]) <= 1e-12 + 1e-6 * st_o["gap"]
+
+
+def test_adapt_learned_off_counts_and_stats():
+    avs = need_gpu()
+    w = small_cylinder(C1=0.6, max_refine=3)
+    r, g = pair(w, avs, amp=1e-2)
+    st = g.adapt()
+    o = r.adapt()
+    assert st["Nv"] == o["Nv"]
+    assert st["Nv"] == g.Nv
+    assert st["splits"] * 3 - st["merges"] * 3 == st["Nv"] - st["Nv_old"]
+
+
+def test_mixed_precision_fields_within_1e5():
+    """Mixed form (FP32 f, FP64 sums): macroscopic fields within 1e-5 of the
+    FP64 oracle after 20 steps on the O-mesh with wall and far field."""
+    avs = need_gpu()
+    w = small_cylinder(precision="mixed")
+    r, g = pair(w, avs, precision="mixed")
+    dt = r.dt()
+    for _ in range(20):
+        r.step(dt)
+    g.step(20, dt=dt)
+    W, q = g.moments()
+    e = field_err(W, r.Wc, 2)
+    assert max(e.values()) < 1e-5, e
+    assert rel_err(g.get_f(), r.f) < 1e-4
+
+
+def test_edge_cases_zero_steps_single_cell_row():
+    avs = need_gpu()
+    w = wl.sweep_box((3, 2), base=(5, 3), max_refine=0)
+    r, g = pair(w, avs)
+    g.step(0, dt=1e-3)
+    assert np.array_equal(g.get_f(), r.f)
+    dt = r.dt()
+    r.step(dt); g.step(1, dt=dt)
+    assert rel_err(g.get_f(), r.f) < 1e-12

@@ -1,0 +1,71 @@
+"""Pins of the FP64 MLP oracle: central finite differences of the loss pin
+every gradient; the BCE form matches its definition -[y log s + (1-y) log(1-s)];
+features of a uniform state take their closed-form values."""
+import math
+
+import numpy as np
+
+import oracle as O
+from oracle import mlp
+from paper_2212_05645_gb300 import workloads as wl
+
+
+def test_gradients_match_central_differences():
+    rng = np.random.default_rng(0)
+    p = mlp.init_params(3)
+    X = rng.standard_normal((37, mlp.NF))
+    Y = (rng.random((37, mlp.NO)) > 0.6).astype(float)
+    g = mlp.backward(p, X, Y)
+    h = 1e-6
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        flat = p[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(12, flat.size), replace=False):
+            q = {k: v.copy() for k, v in p.items()}
+            q[name].reshape(-1)[idx] += h
+            lp = mlp.loss(q, X, Y)
+            q[name].reshape(-1)[idx] -= 2 * h
+            lm = mlp.loss(q, X, Y)
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[name].reshape(-1)[idx]) < 1e-7 + 1e-5 * abs(fd), (name, idx)
+
+
+def test_bce_definition_and_sgd_descends():
+    rng = np.random.default_rng(1)
+    p = mlp.init_params(4)
+    X = rng.standard_normal((50, mlp.NF))
+    Y = (rng.random((50, mlp.NO)) > 0.5).astype(float)
+    Z, _ = mlp.forward(p, X)
+    s = 1 / (1 + np.exp(-Z))
+    ref = -np.mean(Y * np.log(s) + (1 - Y) * np.log(1 - s))
+    assert math.isclose(mlp.loss(p, X, Y), ref, rel_tol=1e-12)
+    l0 = mlp.loss(p, X, Y)
+    for _ in range(20):
+        p = mlp.sgd(p, mlp.backward(p, X, Y), 0.5)
+    assert mlp.loss(p, X, Y) < l0
+
+
+def test_features_uniform_state_closed_form():
+    """A uniform state at rest: log rho, 0, log T, log(Kn dx^-1) with the
+    reference mean free path equal to Kn, and zero neighbour jumps."""
+    w = wl.sweep_box((4, 4))
+    m = w.mesh
+    rho, T = 1.0, 1.0
+    Wc = np.tile([rho, 0.0, 0.0, 1.5 * rho * 0.5 * T], (m.Nc, 1))
+    q = np.zeros((m.Nc, 2))
+    Kn = 0.05
+    mu = O.mu_ref_from_Kn(Kn, 0.81)
+    X = mlp.features(2, Wc, q, m.vol, m.faceL, m.faceR, mu_ref=mu)
+    assert np.allclose(X[:, 0], 0.0) and np.allclose(X[:, 1], 0.0) and np.allclose(X[:, 2], 0.0)
+    assert np.allclose(X[:, 3], math.log(Kn / 0.25), rtol=1e-13)
+    assert np.all(X[:, 4:] == 0.0)
+
+
+def test_labels_small_case_by_hand():
+    m = np.array([[5.0, 0.1, 0.0], [1.0, 0.2, 3e-4], [1.0, 0.05, 1e-5]])
+    M = m.max(0)
+    level = np.array([0, 1, 1])
+    y = mlp.labels(m, M, level, C1=2.0, C2=1e-3, max_refine=2)
+    assert y[:, 0].tolist() == [1, 0, 0]          # only cell 0 exceeds C1
+    assert y[:, 1].tolist() == [1, 1, 0]          # argmax of node 0 and node 1 (node 2 inactive)
+    assert y[:, 2].tolist() == [1, 1, 0]          # 0.1 >= 0.2/2, 0.2; 0.05 < 0.1
+    assert y[:, 3].tolist() == [1, 1, 1]          # level-1 nodes with m >= C2
