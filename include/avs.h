@@ -157,6 +157,26 @@ avs_status avs_get_tree(avs_ctx *ctx, int *level, int *base, uint32_t *key, doub
 avs_status avs_get_f(avs_ctx *ctx, double *f, int is_device);
 avs_status avs_set_f(avs_ctx *ctx, const double *f, int is_device);
 
+/* Criterion values M_k, as avs_criterion, for caller-owned device arrays and
+ * without allocating any device memory.  The paper has no counterpart: this is
+ * a library service for callers that cannot allocate on demand, such as an
+ * embedder whose device memory belongs to another allocator (a caching pool, a
+ * fixed budget) or a latency-sensitive loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  It needs no context.
+ *   f [Nc][nA][Nv] (packed, nA = 2 in 2D, 1 in 3D), xi [Nv][dim], w [Nv],
+ *   Wc [Nc][dim+2] conserved, M_out [Nv]: all device pointers on the current
+ *   device; work is enqueued on cuda_stream (NULL: default stream).
+ * Scratch lives in fixed device arrays of the library: at most 262144 cells
+ * and 131072 nodes (about 11 MiB, held by every GPU that loads the library
+ * until exit); larger inputs return AVS_ECAPACITY with a message on stderr.
+ * All calls share that scratch and it keeps the last call's contents (each call
+ * resets what it needs); calls that overlap on the GPU race and must be
+ * ordered.  The first call on each device looks up the scratch address
+ * (cudaGetSymbolAddress) and should come before any stream capture.
+ * Errors: EINVAL (bad argument), ECAPACITY, ECUDA. */
+avs_status avs_criterion_noalloc(int dim, int Nc, int Nv, const double *f, const double *xi, const double *w,
+                                 const double *Wc, double *M_out, void *cuda_stream);
+
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t   avs_kernel_launches(const avs_ctx *ctx);
 
