@@ -177,6 +177,34 @@ avs_status avs_set_f(avs_ctx *ctx, const double *f, int is_device);
 avs_status avs_criterion_noalloc(int dim, int Nc, int Nv, const double *f, const double *xi, const double *w,
                                  const double *Wc, double *M_out, void *cuda_stream);
 
+/* ---- learned proposer (not in the paper) ------------------------------------
+ * An MLP 8 -> 64 -> 64 -> 4 (ReLU, ReLU, logits), BF16 tensor-core forward and
+ * backward passes with FP32 accumulation and FP32 master weights.  From eight
+ * per-cell features (log rho, |U|/sqrt(RT), log T, log of the mean free path
+ * of Eq. 4 over the cell size, the largest relative jumps of rho, T and U to
+ * the face neighbours, |q|/(rho (RT)^1.5)) it predicts four per-cell labels of
+ * the Sec. 3.4 criterion (split witness, dominant, near-dominant, merge
+ * blocker).  With cfg.learned = 1, avs_adapt evaluates the criterion only on
+ * the cells whose first three logits exceed the threshold (the check set);
+ * every learned_full_every-th adaptation it also runs the full criterion,
+ * counts the nodes whose decision the check set got wrong, takes labels from
+ * it and trains.  Parameters: AVS_MLP_NPARAM floats laid out
+ * W1[64][8], b1[64], W2[64][64], b2[64], W3[4][64], b3[4] (weights [out][in]). */
+#define AVS_MLP_NPARAM 4996
+avs_status avs_mlp_set_params(avs_ctx *ctx, const float *params);     /* host */
+avs_status avs_mlp_get_params(avs_ctx *ctx, float *params);           /* host */
+/* logits [n][4] of features X [n][8]; host buffers. */
+avs_status avs_mlp_forward(avs_ctx *ctx, const float *X, int n, float *logits);
+/* Mean binary cross-entropy over n x 4 outputs and its gradient (host
+ * buffers, grad_out [AVS_MLP_NPARAM] nullable); lr > 0 also applies one SGD
+ * step to the master weights. */
+avs_status avs_mlp_grad(avs_ctx *ctx, const float *X, const float *Y, int n, float lr, float *grad_out,
+                        float *loss_out);
+/* Features [Nc][8] and criterion labels [Nc][4] of the current state (host, nullable). */
+avs_status avs_features(avs_ctx *ctx, float *X_out, float *Y_out);
+/* iters SGD steps on the current state's features and labels; last loss out. */
+avs_status avs_mlp_train(avs_ctx *ctx, int iters, float lr, float *loss_out);
+
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t   avs_kernel_launches(const avs_ctx *ctx);
 

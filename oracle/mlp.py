@@ -59,6 +59,25 @@ def features(D, Wc, q, vol, faceL, faceR, R=0.5, mu_ref=1.0, omega=0.81, T_ref=1
     return X
 
 
+def criterion_values(D, xi, w, f, Wc, s):
+    """Scaled criterion values m[i, k] = s * max(M1_ik, M2_ik) (Eqs.
+    criterion_rho, criterion_e) in the oracle's operation order."""
+    rho = Wc[:, 0]
+    U = Wc[:, 1:1 + D] / rho[:, None]
+    mm = np.zeros_like(rho)
+    for d in range(D):
+        mm = mm + Wc[:, 1 + d] * Wc[:, 1 + d]
+    eint = Wc[:, D + 1] - 0.5 * mm / rho
+    wg = w[None, :] * f[:, 0, :]
+    m1 = wg / rho[:, None]
+    c2 = np.zeros_like(wg)
+    for d in range(D):
+        c = xi[None, :, d] - U[:, d:d + 1]
+        c2 = c2 + c * c
+    m2 = ((0.5 * wg) * c2) / eint[:, None]
+    return s * np.maximum(m1, m2)
+
+
 def labels(m, M, level, C1, C2, max_refine):
     """Per-cell labels from the scaled criterion values m[i, k] and their max M[k]."""
     act = M >= C2

@@ -25,7 +25,10 @@ FP64, MIXED = 0, 1
 
 EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs_num_cells", "avs_init_field",
             "avs_dt", "ugks_step", "ugks_step_dt", "avs_adapt", "avs_moments", "avs_f_moments", "avs_set_W",
-            "avs_criterion", "avs_get_tree", "avs_get_f", "avs_set_f", "avs_sync", "avs_kernel_launches"]
+            "avs_criterion", "avs_get_tree", "avs_get_f", "avs_set_f", "avs_sync", "avs_kernel_launches",
+            "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
+            "avs_mlp_train"]
+MLP_NPARAM = 4996
 
 
 class AVSError(RuntimeError):
@@ -90,6 +93,12 @@ def load():
         "avs_set_f": (C.c_int, [vp, dp, C.c_int]),
         "avs_sync": (C.c_int, [vp]),
         "avs_kernel_launches": (C.c_uint64, [vp]),
+        "avs_mlp_set_params": (C.c_int, [vp, dp]),
+        "avs_mlp_get_params": (C.c_int, [vp, dp]),
+        "avs_mlp_forward": (C.c_int, [vp, dp, C.c_int, dp]),
+        "avs_mlp_grad": (C.c_int, [vp, dp, dp, C.c_int, C.c_float, dp, C.POINTER(C.c_float)]),
+        "avs_features": (C.c_int, [vp, dp, dp]),
+        "avs_mlp_train": (C.c_int, [vp, C.c_int, C.c_float, C.POINTER(C.c_float)]),
     }
     for name, (rt, args) in sig.items():
         fn = getattr(L, name)
@@ -283,6 +292,43 @@ class AVS:
     @property
     def launches(self):
         return int(self.L.avs_kernel_launches(self.h))
+
+    # ------------------------------------------------------------------ learned proposer
+    def mlp_set_params(self, P):
+        P = np.ascontiguousarray(P, np.float32).reshape(-1)
+        assert P.size == MLP_NPARAM
+        self._ck(self.L.avs_mlp_set_params(self.h, P.ctypes.data))
+
+    def mlp_get_params(self):
+        P = np.zeros(MLP_NPARAM, np.float32)
+        self._ck(self.L.avs_mlp_get_params(self.h, P.ctypes.data))
+        return P
+
+    def mlp_forward(self, X):
+        X = np.ascontiguousarray(X, np.float32)
+        out = np.zeros((X.shape[0], 4), np.float32)
+        self._ck(self.L.avs_mlp_forward(self.h, X.ctypes.data, X.shape[0], out.ctypes.data))
+        return out
+
+    def mlp_grad(self, X, Y, lr=0.0):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = C.c_float()
+        self._ck(self.L.avs_mlp_grad(self.h, X.ctypes.data, Y.ctypes.data, X.shape[0], float(lr), g.ctypes.data,
+                                     C.byref(loss)))
+        return g, loss.value
+
+    def features(self):
+        X = np.zeros((self.Nc, 8), np.float32)
+        Y = np.zeros((self.Nc, 4), np.float32)
+        self._ck(self.L.avs_features(self.h, X.ctypes.data, Y.ctypes.data))
+        return X, Y
+
+    def mlp_train(self, iters, lr=0.1):
+        loss = C.c_float()
+        self._ck(self.L.avs_mlp_train(self.h, int(iters), float(lr), C.byref(loss)))
+        return loss.value
 
 
 def _is_torch(a):

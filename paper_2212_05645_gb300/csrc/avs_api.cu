@@ -9,6 +9,7 @@
 
 #include "avs_dev.cuh"
 #include "avs_internal.h"
+#include "avs_mlp.h"
 
 using namespace avs;
 
@@ -54,7 +55,8 @@ void free_all(avs_ctx* c)
                     c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
                     c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
                     c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->stage, c->dev_err,
-                    c->dt_key, c->gap_d};
+                    c->dt_key, c->gap_d, c->grad, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
+                    c->mlp_X, c->mlp_Y, c->mlp_logits, c->mlp_list, c->mlp_count, c->M_alt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -155,6 +157,54 @@ avs_status alloc_f(avs_ctx* c, int nodes, void** f0, void** f1)
     }
     CK(cudaMemsetAsync(*f0, 0, bytes, c->stream));
     CK(cudaMemsetAsync(*f1, 0, bytes, c->stream));
+    return AVS_OK;
+}
+
+// He-uniform initial MLP weights from SplitMix64 (deterministic), zero biases.
+void mlp_default_params(std::vector<float>& P)
+{
+    P.assign(AVS_MLP_NPARAM, 0.0f);
+    uint64_t st = 0x5EED2212ull;
+    auto uni = [&st]() {
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * 0x1p-53;
+    };
+    auto fill = [&](int off, int n, int fan_in) {
+        const double b = sqrt(6.0 / fan_in);
+        for (int k = 0; k < n; ++k) P[off + k] = (float)((2.0 * uni() - 1.0) * b);
+    };
+    fill(0, 64 * 8, 8);
+    fill(64 * 8 + 64, 64 * 64, 64);
+    fill(64 * 8 + 64 + 64 * 64 + 64, 4 * 64, 64);
+}
+
+avs_status ensure_mlp(avs_ctx* c, int rows)
+{
+    if (c->mlp_P && rows <= c->mlp_rows) return AVS_OK;
+    const int nrows = std::max(rows, std::max(c->Nc, 1024));
+    if (!c->mlp_P) {
+        if (dalloc(&c->mlp_P, AVS_MLP_NPARAM) || cudaMalloc(&c->mlp_Wb, AVS_MLP_BF16_ELEMS * 2) ||
+            dalloc(&c->mlp_part, (size_t)AVS_MLP_MAXBLK * (AVS_MLP_NPARAM + 1)) ||
+            dalloc(&c->mlp_grad, AVS_MLP_NPARAM + 1) || dalloc(&c->mlp_count, 2) ||
+            dalloc(&c->M_alt, round_up(c->cap, 32)))
+            return fail(c, AVS_ENOMEM, "MLP buffers");
+        std::vector<float> P;
+        mlp_default_params(P);
+        CK(cudaMemcpyAsync(c->mlp_P, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(mlp_prep(c));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (c->mlp_X) { cudaFree(c->mlp_X); cudaFree(c->mlp_Y); cudaFree(c->mlp_logits); cudaFree(c->mlp_list); }
+    c->mlp_X = c->mlp_Y = c->mlp_logits = nullptr;
+    c->mlp_list = nullptr;
+    if (dalloc(&c->mlp_X, (size_t)nrows * 8) || dalloc(&c->mlp_Y, (size_t)nrows * 4) ||
+        dalloc(&c->mlp_logits, (size_t)nrows * 4) || dalloc(&c->mlp_list, nrows))
+        return fail(c, AVS_ENOMEM, "MLP buffers");
+    c->mlp_rows = nrows;
     return AVS_OK;
 }
 
@@ -512,7 +562,41 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
         CK(cudaMemcpyAsync(c->Wf, o.W_override, sizeof(double) * c->Nc * NW,
                            o.W_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     }
-    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+    int checked = c->Nc, missed = 0, full = 1;
+    if (c->cfg.learned) {
+        avs_status s2 = ensure_mlp(c, c->Nc);
+        if (s2 != AVS_OK) return s2;
+        const int every = std::max(1, c->cfg.learned_full_every);
+        full = o.force_full || c->mlp_trained == 0 || (c->adapt_count % every) == 0;
+        // features of the current state: moments and heat flux of f
+        CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, nullptr, c->q));
+        CK(mlp_features(c, c->Wf, c->q, c->mlp_X));
+        if (c->mlp_trained > 0) {
+            // the proposer's check set and the criterion restricted to it
+            CK(mlp_forward(c, c->Nc, c->mlp_X, c->mlp_logits));
+            CK(mlp_checkset(c, c->mlp_logits, c->mlp_zthr, c->mlp_list, c->mlp_count));
+            CK(cudaMemcpyAsync(&checked, c->mlp_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, c->mlp_list, checked));
+        }
+        if (full) {
+            if (c->mlp_trained > 0)
+                CK(cudaMemcpyAsync(c->M_alt, c->M, sizeof(double) * c->Nv, cudaMemcpyDeviceToDevice, c->stream));
+            // the plain criterion: fallback, judge of the misses and source of the labels
+            CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+            if (c->mlp_trained > 0) {
+                CK(mlp_misses(c, c->M, c->M_alt, c->mlp_count + 1));
+                CK(cudaMemcpyAsync(&missed, c->mlp_count + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            }
+            CK(mlp_labels(c, c->f[c->cur], c->mlp_Y));
+            for (int it = 0; it < c->mlp_train_iters; ++it)
+                CK(mlp_grad_step(c, c->Nc, c->mlp_X, c->mlp_Y, c->mlp_lr, c->mlp_grad));
+            c->mlp_trained += c->mlp_train_iters;
+            checked = c->Nc;
+        }
+    } else {
+        CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+    }
     int Nn, sp, mg;
     avs_status st = apply_marks(c, &Nn, &sp, &mg);
     if (st != AVS_OK) return st;
@@ -556,9 +640,9 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
         stats->splits = sp;
         stats->merges = mg;
         stats->gap = gap;
-        stats->checked_cells = c->Nc;
-        stats->missed_nodes = 0;
-        stats->full = 1;
+        stats->checked_cells = checked;
+        stats->missed_nodes = missed;
+        stats->full = full;
     }
     (void)Nv_old;
     return read_err(c);
@@ -659,6 +743,86 @@ avs_status avs_set_f(avs_ctx* c, const double* f, int is_device)
 }
 
 uint64_t avs_kernel_launches(const avs_ctx* c) { return c ? (uint64_t)c->launches : 0; }
+
+avs_status avs_mlp_set_params(avs_ctx* c, const float* params)
+{
+    if (!c || !params) return AVS_EINVAL;
+    avs_status st = ensure_mlp(c, c->Nc);
+    if (st != AVS_OK) return st;
+    CK(cudaMemcpyAsync(c->mlp_P, params, sizeof(float) * AVS_MLP_NPARAM, cudaMemcpyHostToDevice, c->stream));
+    CK(mlp_prep(c));
+    CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_mlp_get_params(avs_ctx* c, float* params)
+{
+    if (!c || !params) return AVS_EINVAL;
+    avs_status st = ensure_mlp(c, c->Nc);
+    if (st != AVS_OK) return st;
+    CK(cudaMemcpyAsync(params, c->mlp_P, sizeof(float) * AVS_MLP_NPARAM, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_mlp_forward(avs_ctx* c, const float* X, int n, float* logits)
+{
+    if (!c || !X || !logits || n < 0) return AVS_EINVAL;
+    avs_status st = ensure_mlp(c, n);
+    if (st != AVS_OK) return st;
+    CK(cudaMemcpyAsync(c->mlp_X, X, sizeof(float) * 8 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(mlp_forward(c, n, c->mlp_X, c->mlp_logits));
+    CK(cudaMemcpyAsync(logits, c->mlp_logits, sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_mlp_grad(avs_ctx* c, const float* X, const float* Y, int n, float lr, float* grad_out, float* loss_out)
+{
+    if (!c || !X || !Y || n <= 0) return AVS_EINVAL;
+    avs_status st = ensure_mlp(c, n);
+    if (st != AVS_OK) return st;
+    CK(cudaMemcpyAsync(c->mlp_X, X, sizeof(float) * 8 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->mlp_Y, Y, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(mlp_grad_step(c, n, c->mlp_X, c->mlp_Y, lr, c->mlp_grad));
+    std::vector<float> g(AVS_MLP_NPARAM + 1);
+    CK(cudaMemcpyAsync(g.data(), c->mlp_grad, sizeof(float) * g.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (grad_out) memcpy(grad_out, g.data(), sizeof(float) * AVS_MLP_NPARAM);
+    if (loss_out) *loss_out = g[AVS_MLP_NPARAM];
+    return AVS_OK;
+}
+
+avs_status avs_features(avs_ctx* c, float* X_out, float* Y_out)
+{
+    if (!c) return AVS_EINVAL;
+    avs_status st = ensure_mlp(c, c->Nc);
+    if (st != AVS_OK) return st;
+    CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, c->q));
+    CK(mlp_features(c, c->Wf, c->q, c->mlp_X));
+    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+    CK(mlp_labels(c, c->f[c->cur], c->mlp_Y));
+    if (X_out) CK(cudaMemcpyAsync(X_out, c->mlp_X, sizeof(float) * 8 * c->Nc, cudaMemcpyDeviceToHost, c->stream));
+    if (Y_out) CK(cudaMemcpyAsync(Y_out, c->mlp_Y, sizeof(float) * 4 * c->Nc, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return AVS_OK;
+}
+
+avs_status avs_mlp_train(avs_ctx* c, int iters, float lr, float* loss_out)
+{
+    if (!c || iters < 0) return AVS_EINVAL;
+    avs_status st = avs_features(c, nullptr, nullptr);
+    if (st != AVS_OK) return st;
+    for (int it = 0; it < iters; ++it) CK(mlp_grad_step(c, c->Nc, c->mlp_X, c->mlp_Y, lr, c->mlp_grad));
+    c->mlp_trained += iters;
+    if (loss_out) {
+        float g = 0.f;
+        CK(cudaMemcpyAsync(&g, c->mlp_grad + AVS_MLP_NPARAM, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        *loss_out = g;
+    }
+    return AVS_OK;
+}
 
 avs_status avs_sync(avs_ctx* c)
 {

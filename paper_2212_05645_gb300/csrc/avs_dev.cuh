@@ -37,8 +37,12 @@ __device__ __forceinline__ T dot_rn(const T* x, const T* a)
     return s;
 }
 
+// exp: correctly rounded library exp in FP64; the hardware ex2 path in the
+// FP32 form (relative error a few ulp, far below the FP32 storage of f).
 __device__ __forceinline__ double ex(double x) { return exp(x); }
-__device__ __forceinline__ float ex(float x) { return expf(x); }
+__device__ __forceinline__ float ex(float x) { return __expf(x); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 
 // ---------------------------------------------------------------- geometry
 template <typename T>
@@ -56,7 +60,7 @@ __device__ __forceinline__ T venkat(T d1, T d2, T eps2)
 {
     T num = d1 * d1 + eps2 + T(2) * d1 * d2;
     T den = d1 * d1 + T(2) * d2 * d2 + d1 * d2 + eps2;
-    T v = num / den;
+    T v = fdiv(num, den);
     return v < T(1) ? v : T(1);
 }
 
@@ -148,7 +152,8 @@ __device__ __forceinline__ EqPar<T> make_eq(double rho, const double* U, double 
                                             double Pr)
 {
     EqPar<T> p;
-    const double pref = rho / pow(2.0 * AVS_PI * RT, 0.5 * D);
+    const double t = 2.0 * AVS_PI * RT;
+    const double pref = rho / (D == 2 ? t : t * sqrt(t));
     p.pref = (T)pref;
     const double a = (1.0 - Pr) / (5.0 * rho * RT * RT);
     for (int d = 0; d < 3; ++d) {
@@ -279,6 +284,68 @@ __device__ void moments_from_raw(const double* m, const double* V, double* W, do
     }
 }
 
+// Raw moments about V (m, FP64 sums) -> rho, U, RT and heat flux q about the
+// own mean velocity, evaluated in type A.  With V close to the mean velocity
+// the shifted moments are nearly central, so no large terms cancel:
+// e_int = (tr S2 + H0)/2 - rho |d|^2 / 2, d = S1 / rho (3/2 rho R T, monatomic).
+template <int D, typename A>
+__device__ __forceinline__ void state_from_raw(const double* m, const double* V, A& rho, A* U, A& RT, A* q)
+{
+    A S1[3], S2[3][3], S3[3], H0 = A(0), H1[3] = {A(0), A(0), A(0)};
+    const A S0 = (A)m[0];
+    if (D == 2) {
+        S1[0] = (A)m[1]; S1[1] = (A)m[2];
+        S2[0][0] = (A)m[3]; S2[0][1] = S2[1][0] = (A)m[4]; S2[1][1] = (A)m[5];
+        S3[0] = (A)m[6]; S3[1] = (A)m[7];
+        H0 = (A)m[8]; H1[0] = (A)m[9]; H1[1] = (A)m[10];
+    } else {
+        S1[0] = (A)m[1]; S1[1] = (A)m[2]; S1[2] = (A)m[3];
+        S2[0][0] = (A)m[4]; S2[0][1] = S2[1][0] = (A)m[5]; S2[0][2] = S2[2][0] = (A)m[6];
+        S2[1][1] = (A)m[7]; S2[1][2] = S2[2][1] = (A)m[8]; S2[2][2] = (A)m[9];
+        S3[0] = (A)m[10]; S3[1] = (A)m[11]; S3[2] = (A)m[12];
+    }
+    rho = S0;
+    const A ir = A(1) / S0;
+    A d[3], dd = A(0), trS2 = A(0), dS1 = A(0);
+    for (int a = 0; a < D; ++a) {
+        d[a] = S1[a] * ir;
+        U[a] = (A)V[a] + d[a];
+        dd += d[a] * d[a];
+        trS2 += S2[a][a];
+        dS1 += d[a] * S1[a];
+    }
+    RT = (A(0.5) * (trS2 + H0) - A(0.5) * S0 * dd) / (A(1.5) * S0);
+    if (q) {
+        for (int a = 0; a < D; ++a) {
+            A S2d = A(0);
+            for (int b = 0; b < D; ++b) S2d += S2[a][b] * d[b];
+            const A g3 = S3[a] - A(2) * S2d + dd * S1[a] - d[a] * trS2 + A(2) * d[a] * dS1 - d[a] * dd * S0;
+            q[a] = A(0.5) * (g3 + H1[a] - d[a] * H0);
+        }
+    }
+}
+
+// Equilibrium parameters from rho, U, RT, q given in type A.
+template <int D, typename T, typename A>
+__device__ __forceinline__ EqPar<T> make_eq_a(A rho, const A* U, A RT, const A* q, A Pr)
+{
+    EqPar<T> p;
+    const A t = A(2.0 * AVS_PI) * RT;
+    p.pref = (T)(rho / (D == 2 ? t : t * sqrt(t)));
+    const A a = (A(1) - Pr) / (A(5) * rho * RT * RT);
+    for (int d = 0; d < 3; ++d) {
+        p.U[d] = d < D ? (T)U[d] : T(0);
+        p.alpha[d] = (d < D && q) ? (T)(a * q[d]) : T(0);
+    }
+    p.inv2RT = (T)(A(1) / (A(2) * RT));
+    p.invRT = (T)(A(1) / RT);
+    p.RTH = (T)(A(3 - D) * RT);
+    return p;
+}
+
+__device__ __forceinline__ double powa(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float powa(float x, float y) { return exp2f(y * __log2f(x)); }
+
 // ---------------------------------------------------------------- reductions
 // Deterministic block reduction of N doubles per thread: warp tree with
 // shuffles, then a fixed-order sum over warps.  Result in out[0..N-1] (smem),
@@ -299,6 +366,30 @@ __device__ __forceinline__ void block_sum(double* v, double* sred, double* out)
         double s = 0.0;
         for (int w = 0; w < NT / 32; ++w) s += sred[w * N + threadIdx.x];
         out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Block reduction of N values per thread kept in the element type: warp tree
+// with shuffles in T, then a fixed-order FP64 sum of the per-warp results.
+// Deterministic.  out[0..N-1] (smem, double) is visible to all threads after
+// return.  sw must hold (NT/32)*N doubles.
+template <int N, int NT, typename T>
+__device__ __forceinline__ void block_sum_t(T* v, double* sw, double* out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        T x = v[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sw[warp * N + m] = (double)x;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < N; m += NT) {
+        double s = 0.0;
+        for (int w = 0; w < NT / 32; ++w) s += sw[w * N + m];
+        out[m] = s;
     }
     __syncthreads();
 }

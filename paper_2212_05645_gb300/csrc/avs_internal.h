@@ -65,6 +65,23 @@ struct avs_ctx {
     double *gap_d = nullptr;                         // correction gap (max over cells)
     double dt_unit = 0.0;
     unsigned long long launches = 0;                 // kernels launched by this context
+    void *grad = nullptr;                            // limited gradients [Nc][NA][D][Nvp] of T
+    size_t grad_bytes = 0;
+
+    // ---- learned proposer (MLP 8-64-64-4)
+    float *mlp_P = nullptr;                          // FP32 master parameters
+    void *mlp_Wb = nullptr;                          // BF16 operand copies
+    float *mlp_part = nullptr;                       // per-block gradient partials
+    float *mlp_grad = nullptr;                       // gradient (+ loss) of the last step
+    float *mlp_X = nullptr, *mlp_Y = nullptr;        // features / labels [Nc][8], [Nc][4]
+    float *mlp_logits = nullptr;                     // [Nc][4]
+    int *mlp_list = nullptr, *mlp_count = nullptr;   // check set
+    int mlp_rows = 0;                                // row capacity of the MLP buffers
+    double *M_alt = nullptr;                         // criterion over the check set
+    int mlp_trained = 0;                             // training steps so far
+    float mlp_lr = 0.1f;
+    int mlp_train_iters = 50;
+    float mlp_zthr = -1.0f;                          // logit threshold of the check set
 };
 
 namespace avs {

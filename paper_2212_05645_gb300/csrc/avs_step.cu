@@ -1,36 +1,126 @@
 // One explicit UGKS step on the global velocity mesh (paper Sec. 2.3, with
-// the explicit readings R1-R4): one thread block per physical cell.
+// the explicit readings R1-R4), as two kernels.
 //
-//   pass 1a  for every face of the cell: foot values phi_C + L grad.(x_f - xi h - x_C)
-//            from the upwind cell (Sec. 2.3.3), summed into raw velocity
-//            moments (interface W of Eq. w_interface, heat flux, flux moments)
-//   pass 1b  raw moments of the cell's own f^n (lagged heat flux, R3)
-//   state    interface Shakhov state per face: tau (Eq. 3), q_ij (R4), blend
-//            weights tau/(tau+h), h/(tau+h) (Eq. equ28); wall density from
-//            zero net mass flux (R8)
-//   pass 1c  discrete flux moments of the interface equilibrium
-//   update   W~ = W - dt/|V| sum_j A F_ij (R2), cell Shakhov state
-//   pass 2   phi_ij per node and face, net flux, collision update (Eq. SGS_phi
-//            diagonal, R1), written to the second f buffer.
+// k_grad: the limited least-squares gradient L grad phi of every cell, array
+//   and node (Sec. 2.3.3: least squares with weights 1/|d|^2, Venkatakrishnan
+//   limiter), computed once and stored next to f.  Elementwise stencil over
+//   the face neighbours.
 //
-// Faces shared by two cells are evaluated by both blocks with identical
-// arithmetic (same inputs, same node-to-thread map, same reduction order), so
-// the two flux copies agree bit for bit and W telescopes.  f^n and W^n are
-// read-only during the step (double buffers), so blocks never wait on each
-// other.
+// k_step: one thread block per physical cell, three passes over the nodes
+// (thread t owns nodes k = t, t + NT, ...):
+//   A  foot values phi_C + (L grad phi)_C . (x_f - xi h - x_C) of every face
+//      from the upwind cell, summed into raw velocity moments per face
+//      (interface W of Eq. w_interface, heat flux, flux moments).
+//   -  interface Shakhov state per face: tau (Eq. 3), q_ij (R4), blend weights
+//      tau/(tau+h), h/(tau+h) (Eq. equ28); incoming Maxwellians of boundaries.
+//   B  interface equilibria: their discrete flux moments; the interface
+//      distribution phi_ij = wa phi_bar + wb g_ij (foot values recomputed)
+//      and the per-node net flux sum_j A (xi . n) phi_ij, parked in the
+//      f^{n+1} slot of the node; raw moments of the cell's own f^n (lagged
+//      heat flux, R3).  Wall density from zero net mass flux (R8).
+//   -  W~ = W - dt/|V| sum_j A F_ij (R2) and the cell's Shakhov state.
+//   C  collision update (diagonal of Eq. SGS_phi, R1), overwriting the slot.
+//
+// Faces shared by two cells are evaluated by both blocks from the same inputs
+// with the same node-to-thread map and reduction order, so both copies of a
+// face flux agree and W telescopes.  f^n, its gradient and W^n are read-only
+// during the step, so blocks never wait on each other.  Sums: per-thread and
+// warp sums in the element type, FP64 across warps and in every per-cell /
+// per-face formula.
+#include <algorithm>
+
 #include "avs_dev.cuh"
 #include "avs_internal.h"
 
 namespace avs {
 
+// ------------------------------------------------------------------ k_grad
+// G[i][a][d][k] = L * (grad phi)_d of array a of cell i at node k.  Each
+// thread handles VG consecutive nodes (rows are padded to 32 nodes, so the
+// vector stays inside the row) to keep more loads in flight.
+template <int D, typename T, int VG>
+__global__ void __launch_bounds__(256) k_grad(int Nv, int Nvp, int limiter, const T* __restrict__ f,
+                                              T* __restrict__ G, CellGeo<T> geo)
+{
+    constexpr int NA = NArr<D>::v;
+    const int i = blockIdx.x;
+    const int k0 = (blockIdx.y * blockDim.x + threadIdx.x) * VG;
+    if (k0 >= Nv) return;
+    const size_t cstride = (size_t)NA * Nvp;
+    const int ns = geo.ns[i];
+    int nb[AVS_MAXS];
+    T cg[AVS_MAXS][D], rr[AVS_MAXS][D];
+#pragma unroll
+    for (int s = 0; s < AVS_MAXS; ++s) {
+        nb[s] = s < ns ? geo.nbr[i * AVS_MAXS + s] : -1;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            cg[s][d] = s < ns ? geo.cg[(size_t)(i * AVS_MAXS + s) * D + d] : T(0);
+            rr[s][d] = s < ns ? geo.r[(size_t)(i * AVS_MAXS + s) * D + d] : T(0);
+        }
+    }
+    const T e2 = geo.eps2[i];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const T* fa = f + (size_t)a * Nvp + k0;
+        T phi[VG], nv[AVS_MAXS][VG];
+#pragma unroll
+        for (int v = 0; v < VG; ++v) phi[v] = fa[(size_t)i * cstride + v];
+#pragma unroll
+        for (int s = 0; s < AVS_MAXS; ++s)
+#pragma unroll
+            for (int v = 0; v < VG; ++v) nv[s][v] = nb[s] >= 0 ? fa[(size_t)nb[s] * cstride + v] : phi[v];
+        T* o = G + ((size_t)i * NA + a) * D * Nvp + k0;
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            T g[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) g[d] = T(0);
+            T L = T(1);
+            if (limiter != 0) {
+                T dmax = T(0), dmin = T(0);
+#pragma unroll
+                for (int s = 0; s < AVS_MAXS; ++s) {
+                    if (nb[s] < 0) continue;
+                    const T dd = nv[s][v] - phi[v];
+#pragma unroll
+                    for (int d = 0; d < D; ++d) g[d] += cg[s][d] * dd;
+                    dmax = dd > dmax ? dd : dmax;
+                    dmin = dd < dmin ? dd : dmin;
+                }
+                if (limiter == 1) {
+                    T p = T(0), n = T(0);
+#pragma unroll
+                    for (int s = 0; s < AVS_MAXS; ++s) {
+                        if (s >= ns) break;
+                        T d2 = g[0] * rr[s][0];
+#pragma unroll
+                        for (int d = 1; d < D; ++d) d2 += g[d] * rr[s][d];
+                        p = d2 > p ? d2 : p;
+                        n = d2 < n ? d2 : n;
+                    }
+                    if (p > T(0)) { const T t = venkat(dmax, p, e2); L = t < L ? t : L; }
+                    if (n < T(0)) { const T t = venkat(dmin, n, e2); L = t < L ? t : L; }
+                }
+            }
+            if (k0 + v < Nvp) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) o[(size_t)d * Nvp + v] = L * g[d];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ k_step
 template <int D, typename T>
 struct StepP {
-    int Nv, Nvp, limiter;
-    size_t cstride;
+    int Nc, Nv, Nvp;
+    size_t cstride;          // elements per cell in f: NA * Nvp
     T h;
     double dt, hd;
     double R, Pr, omega, mu_ref, T_ref;
     const T* __restrict__ fin;
+    const T* __restrict__ G;   // [cell][array][dim][Nvp], null for first order
     T* __restrict__ fout;
     const double* __restrict__ Win;
     double* __restrict__ Wout;
@@ -44,250 +134,268 @@ struct StepP {
     const T* __restrict__ rR;
     const double* __restrict__ bc;
     const int* __restrict__ slot;
+    const unsigned char* __restrict__ nslot;
     const double* __restrict__ vol;
-    CellGeo<T> geo;
     int* err;
 };
 
 template <typename T>
 struct SlotSt {
-    int kind, f, L, R;       // kind: 0 interior, 1 wall, 2 far field
+    int kind, L, R;          // kind: 0 interior, 1 wall, 2 far field
     T sgn;                   // +1: the cell is L (An points out of it), -1: it is R
     T An[3], rL[3], rR[3];
     double And[3];
     double V[3];             // reference velocity of the moment sums
+    T Vt[3];                 // the same in the element type
     EqPar<T> eq;             // interface equilibrium / incoming Maxwellian
     T wa, wb;
     double wad, wbd;
-    double mom[13];          // raw moments of the foot distribution / outgoing flux
-    double AFphi[5];
-    double AFg[6];
     double AF[5];            // area-weighted interface flux
 };
 
-__device__ __forceinline__ double tau_vhs(double rho, double RT, double R, double mu_ref, double T_ref,
-                                          double omega)
+template <typename A>
+__device__ __forceinline__ A tau_vhs(A rho, A RT, A R, A mu_ref, A T_ref, A omega)
 {
-    const double T = RT / R;
-    return mu_ref * pow(T / T_ref, omega) / (rho * RT);
+    const A T = RT / R;
+    return mu_ref * powa(T / T_ref, omega) / (rho * RT);
 }
 
+// foot value of array a at node k from upwind cell C, offset rF of the face
+template <int D, int NA, typename T>
+__device__ __forceinline__ T foot(const StepP<D, T>& P, int C, int a, int k, const T* rF, const T* x, T h)
+{
+    T v = P.fin[(size_t)C * P.cstride + (size_t)a * P.Nvp + k];
+    if (P.G) {
+        const T* g = P.G + ((size_t)C * NA + a) * D * P.Nvp + k;
+#pragma unroll
+        for (int d = 0; d < D; ++d) v += g[(size_t)d * P.Nvp] * (rF[d] - x[d] * h);
+    }
+    return v;
+}
+
+template <int D> struct FaceGroup { static constexpr int v = (D == 2) ? 4 : 3; };
+
 template <int D, typename T, int NT>
-__global__ void __launch_bounds__(NT) k_step(StepP<D, T> P)
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 3 : 1) k_step(StepP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
-    // FP32 partial sums are flushed into FP64 every CH nodes per thread.
-    constexpr int CH = (sizeof(T) == 4) ? 8 : (1 << 20);
+    constexpr int FG = FaceGroup<D>::v;                  // faces per pass-A sweep
+    constexpr int NB = AVS_MAXS * (NW + 1) + NM;         // values reduced after pass B
+    constexpr int NR = (FG * NM > NB) ? FG * NM : NB;
     __shared__ SlotSt<T> S[AVS_MAXS];
-    __shared__ double sred[(NT / 32) * 14];
-    __shared__ double cmom[NM];
+    __shared__ double sw[(NT / 32) * NR];
+    __shared__ double red[NR];
+    __shared__ double mom[AVS_MAXS][NM];
     __shared__ double Vc[3], qc[3];
     __shared__ EqPar<T> ceq;
     __shared__ T upd[4];
+    __shared__ int wall_slots[AVS_MAXS], n_wall;
 
-    const int i = blockIdx.x, tid = threadIdx.x;
-    const int ns = P.geo.ns[i];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x;
     const T h = P.h;
-
+    const int ns = P.nslot[i];
     if (tid < ns) {
         const int sl = P.slot[i * AVS_MAXS + tid];
+        const int f = sl >> 1;
         SlotSt<T>& s = S[tid];
-        s.f = sl >> 1;
-        s.L = P.faceL[s.f];
-        s.R = P.faceR[s.f];
+        s.L = P.faceL[f];
+        s.R = P.faceR[f];
         s.sgn = (sl & 1) ? T(-1) : T(1);
         s.kind = s.R >= 0 ? 0 : (int)P.bc[(size_t)(-1 - s.R) * 6];
         for (int d = 0; d < 3; ++d) {
-            s.An[d] = d < D ? P.An[(size_t)s.f * D + d] : T(0);
-            s.And[d] = d < D ? P.An_d[(size_t)s.f * D + d] : 0.0;
-            s.rL[d] = d < D ? P.rL[(size_t)s.f * D + d] : T(0);
-            s.rR[d] = d < D ? P.rR[(size_t)s.f * D + d] : T(0);
-            double v = 0.0;
+            s.An[d] = d < D ? P.An[(size_t)f * D + d] : T(0);
+            s.And[d] = d < D ? P.An_d[(size_t)f * D + d] : 0.0;
+            s.rL[d] = d < D ? P.rL[(size_t)f * D + d] : T(0);
+            s.rR[d] = d < D ? P.rR[(size_t)f * D + d] : T(0);
+            T v = T(0);
             if (d < D) {
-                v = P.Win[(size_t)s.L * NW + 1 + d] / P.Win[(size_t)s.L * NW];
-                if (s.R >= 0) v = 0.5 * (v + P.Win[(size_t)s.R * NW + 1 + d] / P.Win[(size_t)s.R * NW]);
+                v = (T)P.Win[(size_t)s.L * NW + 1 + d] / (T)P.Win[(size_t)s.L * NW];
+                if (s.R >= 0) v = T(0.5) * (v + (T)P.Win[(size_t)s.R * NW + 1 + d] / (T)P.Win[(size_t)s.R * NW]);
             }
-            s.V[d] = (double)(T)v;
+            s.V[d] = (double)v;
+            s.Vt[d] = v;
         }
     }
     if (tid == 0) {
         for (int d = 0; d < 3; ++d)
-            Vc[d] = d < D ? (double)(T)(P.Win[(size_t)i * NW + 1 + d] / P.Win[(size_t)i * NW]) : 0.0;
+            Vc[d] = d < D ? (double)((T)P.Win[(size_t)i * NW + 1 + d] / (T)P.Win[(size_t)i * NW]) : 0.0;
+        int nw = 0;
+        for (int s = 0; s < ns; ++s) {
+            const int R = P.faceR[P.slot[i * AVS_MAXS + s] >> 1];
+            if (R < 0 && (int)P.bc[(size_t)(-1 - R) * 6] == AVS_BC_WALL) wall_slots[nw++] = s;
+        }
+        n_wall = nw;
     }
     __syncthreads();
 
-    // ---------------- pass 1a: raw moments of the foot distribution per face
-    for (int s = 0; s < ns; ++s) {
-        const int L = S[s].L, R = S[s].R;
-        const bool inter = S[s].kind == 0;
-        T An[D], rLs[D], rRs[D], Vt[D];
+    // ---------------- pass A: raw moments of the foot distribution, FG faces per sweep
+    for (int s0 = 0; s0 < ns; s0 += FG) {
+        const int s1 = min(ns, s0 + FG);
+        T acc[FG * NM];
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            An[d] = S[s].An[d];
-            rLs[d] = S[s].rL[d];
-            rRs[d] = S[s].rR[d];
-            Vt[d] = (T)S[s].V[d];
-        }
-        double acc[NM];
+        for (int m = 0; m < FG * NM; ++m) acc[m] = T(0);
+        for (int k = tid; k < P.Nv; k += NT) {
+            T x[D];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) acc[m] = 0.0;
-        for (int k0 = tid; k0 < P.Nv; k0 += NT * CH) {
-            T part[NM];
+            for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
+            const T wk = P.w[k];
 #pragma unroll
-            for (int m = 0; m < NM; ++m) part[m] = T(0);
-            for (int c = 0, k = k0; c < CH && k < P.Nv; ++c, k += NT) {
-                T x[D];
+            for (int j = 0; j < FG; ++j) {
+                const int s = s0 + j;
+                if (s >= s1) break;
+                const SlotSt<T>& Sl = S[s];
+                T An[D];
 #pragma unroll
-                for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
+                for (int d = 0; d < D; ++d) An[d] = Sl.An[d];
                 const T sn = dot_rn<D>(x, An);
-                int C;
-                const T* rF;
-                if (sn >= T(0)) { C = L; rF = rLs; }
-                else if (inter) { C = R; rF = rRs; }
-                else continue;
-                T gr[D], Lm;
-                const T phiG = grad_lim<D>(P.geo, P.limiter, P.fin + k, P.cstride, C, gr, Lm);
-                const T fG = foot_value<D>(phiG, gr, Lm, rF, x, h);
-                T fH = T(0);
-                if (NA == 2) {
-                    const T phiH = grad_lim<D>(P.geo, P.limiter, P.fin + P.Nvp + k, P.cstride, C, gr, Lm);
-                    fH = foot_value<D>(phiH, gr, Lm, rF, x, h);
-                }
-                const T wk = P.w[k];
+                const bool inter = Sl.kind == 0;
+                if (!inter && sn < T(0)) continue;      // incoming at a boundary: pass B
+                const int C = sn >= T(0) ? Sl.L : Sl.R;
+                const T* rF = sn >= T(0) ? Sl.rL : Sl.rR;
+                const T fG = foot<D, NA>(P, C, 0, k, rF, x, h);
+                const T fH = NA == 2 ? foot<D, NA>(P, C, NA - 1, k, rF, x, h) : T(0);
+                T* m = acc + j * NM;
                 if (inter) {
                     T xs[D];
 #pragma unroll
-                    for (int d = 0; d < D; ++d) xs[d] = x[d] - Vt[d];
-                    raw_acc<D>(part, xs, wk * fG, wk * fH);
+                    for (int d = 0; d < D; ++d) xs[d] = x[d] - Sl.Vt[d];
+                    raw_acc<D>(m, xs, wk * fG, wk * fH);
                 } else {
                     const T t = wk * sn;
                     T x2 = T(0);
 #pragma unroll
                     for (int d = 0; d < D; ++d) x2 += x[d] * x[d];
-                    part[0] += t * fG;
+                    m[0] += t * fG;
 #pragma unroll
-                    for (int d = 0; d < D; ++d) part[1 + d] += t * fG * x[d];
-                    part[D + 1] += t * T(0.5) * (x2 * fG + fH);
+                    for (int d = 0; d < D; ++d) m[1 + d] += t * fG * x[d];
+                    m[D + 1] += t * T(0.5) * (x2 * fG + fH);
                 }
             }
-#pragma unroll
-            for (int m = 0; m < NM; ++m) acc[m] += (double)part[m];
         }
-        block_sum<NM, NT>(acc, sred, S[s].mom);
+        block_sum_t<FG * NM, NT>(acc, sw, red);
+        for (int v = tid; v < (s1 - s0) * NM; v += NT) mom[s0 + v / NM][v % NM] = red[v];
+        __syncthreads();
     }
 
-    // ---------------- pass 1b: raw moments of the cell's own f^n
-    {
-        double acc[NM];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) acc[m] = 0.0;
-        T Vt[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) Vt[d] = (T)Vc[d];
-        const T* fi = P.fin + (size_t)i * P.cstride;
-        for (int k0 = tid; k0 < P.Nv; k0 += NT * CH) {
-            T part[NM];
-#pragma unroll
-            for (int m = 0; m < NM; ++m) part[m] = T(0);
-            for (int c = 0, k = k0; c < CH && k < P.Nv; ++c, k += NT) {
-                T xs[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) xs[d] = P.xi[(size_t)k * D + d] - Vt[d];
-                const T wk = P.w[k];
-                raw_acc<D>(part, xs, wk * fi[k], NA == 2 ? wk * fi[P.Nvp + k] : T(0));
-            }
-#pragma unroll
-            for (int m = 0; m < NM; ++m) acc[m] += (double)part[m];
-        }
-        block_sum<NM, NT>(acc, sred, cmom);
-    }
-
-    // ---------------- interface states and the cell's lagged heat flux
+    // ---------------- interface states
     if (tid < ns) {
         SlotSt<T>& s = S[tid];
         if (s.kind == 0) {
-            double W[5], qb[3], rho, U[3], RT;
-            moments_from_raw<D>(s.mom, s.V, W, qb, s.And, s.AFphi);
-            prim<D>(W, rho, U, RT);
-            if (!(rho > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
-            const double tau = tau_vhs(rho, RT, P.R, P.mu_ref, P.T_ref, P.omega);
-            double qf[3] = {0, 0, 0};
-            for (int d = 0; d < D; ++d) qf[d] = tau * qb[d] / (tau + P.hd * P.Pr);
-            s.eq = make_eq<D, T>(rho, U, RT, qf, P.Pr);
-            s.wad = tau / (tau + P.hd);
-            s.wbd = P.hd / (tau + P.hd);
+            double Wd[5], AFphi[5];
+            moments_from_raw<D>(mom[tid], s.V, Wd, nullptr, s.And, AFphi);
+            T rho, U[3], RT, qb[3];
+            state_from_raw<D, T>(mom[tid], s.V, rho, U, RT, qb);
+            if (!(rho > T(0)) || !(RT > T(0))) atomicOr(P.err, 1);
+            const T tau = tau_vhs<T>(rho, RT, (T)P.R, (T)P.mu_ref, (T)P.T_ref, (T)P.omega);
+            const T hh = (T)P.hd;
+            T qf[3] = {T(0), T(0), T(0)};
+            for (int d = 0; d < D; ++d) qf[d] = tau * qb[d] / (tau + hh * (T)P.Pr);
+            s.eq = make_eq_a<D, T, T>(rho, U, RT, qf, (T)P.Pr);
+            s.wad = (double)(tau / (tau + hh));
+            s.wbd = (double)(hh / (tau + hh));
+            for (int m = 0; m < NW; ++m) s.AF[m] = s.wad * AFphi[m];
         } else {
-            for (int m = 0; m < NW; ++m) s.AFphi[m] = s.mom[m];
             const double* B = P.bc + (size_t)(-1 - s.R) * 6;
             const double Ub[3] = {B[2], B[3], B[4]};
             s.eq = make_eq<D, T>(s.kind == 1 ? 1.0 : B[1], Ub, P.R * B[5], nullptr, P.Pr);
             s.wad = 1.0;
             s.wbd = 0.0;
+            for (int m = 0; m < NW; ++m) s.AF[m] = mom[tid][m];   // outgoing half
         }
         s.wa = (T)s.wad;
         s.wb = (T)s.wbd;
     }
-    if (tid == 32) {
-        double Wn[5], qn[3];
-        moments_from_raw<D>(cmom, Vc, Wn, qn, nullptr, nullptr);
-        for (int d = 0; d < 3; ++d) qc[d] = d < D ? qn[d] : 0.0;
-    }
     __syncthreads();
 
-    // ---------------- pass 1c: discrete flux moments of the face equilibria
-    for (int s = 0; s < ns; ++s) {
-        const int kind = S[s].kind;
-        const EqPar<T> eq = S[s].eq;
-        T An[D];
+    // ---------------- pass B: face equilibria, interface distribution, net flux, cell moments
+    const T* fi = P.fin + (size_t)i * P.cstride;
+    T* fo = P.fout + (size_t)i * P.cstride;
+    {
+        T acc[NB];
 #pragma unroll
-        for (int d = 0; d < D; ++d) An[d] = S[s].An[d];
-        double acc[NW + 1];
+        for (int m = 0; m < NB; ++m) acc[m] = T(0);
+        T Vct[D];
 #pragma unroll
-        for (int m = 0; m <= NW; ++m) acc[m] = 0.0;
-        for (int k0 = tid; k0 < P.Nv; k0 += NT * CH) {
-            T part[NW + 1];
+        for (int d = 0; d < D; ++d) Vct[d] = (T)Vc[d];
+        for (int k = tid; k < P.Nv; k += NT) {
+            T x[D];
 #pragma unroll
-            for (int m = 0; m <= NW; ++m) part[m] = T(0);
-            for (int c = 0, k = k0; c < CH && k < P.Nv; ++c, k += NT) {
-                T x[D];
+            for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
+            const T wk = P.w[k];
+            T x2 = T(0);
 #pragma unroll
-                for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
+            for (int d = 0; d < D; ++d) x2 += x[d] * x[d];
+            {
+                T xs[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) xs[d] = x[d] - Vct[d];
+                raw_acc<D>(acc + AVS_MAXS * (NW + 1), xs, wk * fi[k], NA == 2 ? wk * fi[P.Nvp + k] : T(0));
+            }
+            T Nn[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) Nn[a] = T(0);
+#pragma unroll
+            for (int s = 0; s < AVS_MAXS; ++s) {
+                if (s >= ns) break;
+                const SlotSt<T>& Sl = S[s];
+                T An[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) An[d] = Sl.An[d];
                 const T sn = dot_rn<D>(x, An);
-                if (kind != 0 && sn >= T(0)) continue;
+                const T ss = Sl.sgn * sn;
+                T* m = acc + s * (NW + 1);
+                if (Sl.kind != 0 && sn >= T(0)) {          // outgoing at a boundary: the foot value
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) Nn[a] += ss * foot<D, NA>(P, Sl.L, a, k, Sl.rL, x, h);
+                    continue;
+                }
                 T gG, gH;
-                eq_eval<D>(eq, x, gG, gH);
-                const T wk = P.w[k];
+                eq_eval<D>(Sl.eq, x, gG, gH);
                 const T t = wk * sn;
-                T x2 = T(0);
+                m[0] += t * gG;
 #pragma unroll
-                for (int d = 0; d < D; ++d) x2 += x[d] * x[d];
-                part[0] += t * gG;
-#pragma unroll
-                for (int d = 0; d < D; ++d) part[1 + d] += t * gG * x[d];
-                part[D + 1] += t * T(0.5) * (x2 * gG + gH);
-                if (kind == 1) part[NW] += wk * (-sn) * gG;
+                for (int d = 0; d < D; ++d) m[1 + d] += t * gG * x[d];
+                m[D + 1] += t * T(0.5) * (x2 * gG + gH);
+                if (Sl.kind == 0) {
+                    const int C = sn >= T(0) ? Sl.L : Sl.R;
+                    const T* rF = sn >= T(0) ? Sl.rL : Sl.rR;
+                    Nn[0] += ss * (Sl.wa * foot<D, NA>(P, C, 0, k, rF, x, h) + Sl.wb * gG);
+                    if (NA == 2) Nn[NA - 1] += ss * (Sl.wa * foot<D, NA>(P, C, NA - 1, k, rF, x, h) + Sl.wb * gH);
+                } else if (Sl.kind == 2) {
+                    Nn[0] += ss * gG;
+                    if (NA == 2) Nn[NA - 1] += ss * gH;
+                } else {
+                    m[NW] += wk * (-sn) * gG;                 // wall: incoming part added in pass C
+                }
             }
 #pragma unroll
-            for (int m = 0; m <= NW; ++m) acc[m] += (double)part[m];
+            for (int a = 0; a < NA; ++a) fo[(size_t)a * P.Nvp + k] = Nn[a];   // parked until pass C
         }
-        block_sum<NW + 1, NT>(acc, sred, S[s].AFg);
+        block_sum_t<NB, NT>(acc, sw, red);
     }
 
-    // ---------------- final interface fluxes
+    // ---------------- final interface fluxes, wall densities, lagged heat flux
     if (tid < ns) {
         SlotSt<T>& s = S[tid];
+        const double* g = red + tid * (NW + 1);
         if (s.kind == 0) {
-            for (int m = 0; m < NW; ++m) s.AF[m] = s.wad * s.AFphi[m] + s.wbd * s.AFg[m];
+            for (int m = 0; m < NW; ++m) s.AF[m] += s.wbd * g[m];
         } else if (s.kind == 1) {
-            const double Sin = s.AFg[NW];
-            const double rw = Sin > 0.0 ? s.AFphi[0] / Sin : 0.0;
-            for (int m = 0; m < NW; ++m) s.AF[m] = s.AFphi[m] + rw * s.AFg[m];
+            const double Sin = g[NW];
+            const double rw = Sin > 0.0 ? s.AF[0] / Sin : 0.0;
+            for (int m = 0; m < NW; ++m) s.AF[m] += rw * g[m];
             const double* B = P.bc + (size_t)(-1 - s.R) * 6;
             const double Ub[3] = {B[2], B[3], B[4]};
             s.eq = make_eq<D, T>(rw, Ub, P.R * B[5], nullptr, P.Pr);
         } else {
-            for (int m = 0; m < NW; ++m) s.AF[m] = s.AFphi[m] + s.AFg[m];
+            for (int m = 0; m < NW; ++m) s.AF[m] += g[m];
         }
+    }
+    if (tid == 32 % NT) {
+        T rn, Un[3], RTn, qn[3];
+        state_from_raw<D, T>(red + AVS_MAXS * (NW + 1), Vc, rn, Un, RTn, qn);
+        for (int d = 0; d < 3; ++d) qc[d] = d < D ? (double)qn[d] : 0.0;
     }
     __syncthreads();
 
@@ -302,70 +410,51 @@ __global__ void __launch_bounds__(NT) k_step(StepP<D, T> P)
             Wt[c] = Wi[c] - dtv * sum;
             P.Wout[(size_t)i * NW + c] = Wt[c];
         }
-        double rho, U[3], RT;
-        prim<D>(Wt, rho, U, RT);
-        if (!(rho > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
-        const double tau = tau_vhs(rho, RT, P.R, P.mu_ref, P.T_ref, P.omega);
-        ceq = make_eq<D, T>(rho, U, RT, qc, P.Pr);
-        upd[0] = (T)(1.0 / P.dt);
-        upd[1] = (T)(1.0 / tau);
+        double rhod, Ud[3], RTd;
+        prim<D>(Wt, rhod, Ud, RTd);
+        if (!(rhod > 0.0) || !(RTd > 0.0)) atomicOr(P.err, 1);
+        const T rho = (T)rhod, RT = (T)RTd;
+        T U[3], q[3];
+        for (int d = 0; d < 3; ++d) {
+            U[d] = (T)Ud[d];
+            q[d] = (T)qc[d];
+        }
+        const T tau = tau_vhs<T>(rho, RT, (T)P.R, (T)P.mu_ref, (T)P.T_ref, (T)P.omega);
+        ceq = make_eq_a<D, T, T>(rho, U, RT, q, (T)P.Pr);
+        const T idt = (T)(1.0 / P.dt), itau = T(1) / tau;
+        upd[0] = idt;
+        upd[1] = itau;
         upd[2] = (T)(1.0 / P.vol[i]);
-        upd[3] = (T)(1.0 / (1.0 / P.dt + 1.0 / tau));
+        upd[3] = T(1) / (idt + itau);
     }
     __syncthreads();
 
-    // ---------------- pass 2: interface distribution, net flux, collision update
-    T* fo = P.fout + (size_t)i * P.cstride;
+    // ---------------- pass C: collision update
+    const int nw = n_wall;
     for (int k = tid; k < P.Nv; k += NT) {
         T x[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
-        T grG[D], LG, grH[D], LH = T(1);
-        const T phiG = grad_lim<D>(P.geo, P.limiter, P.fin + k, P.cstride, i, grG, LG);
-        T phiH = T(0);
-        if (NA == 2) phiH = grad_lim<D>(P.geo, P.limiter, P.fin + P.Nvp + k, P.cstride, i, grH, LH);
-        T NG = T(0), NH = T(0);
-        for (int s = 0; s < ns; ++s) {
-            const SlotSt<T>& Sl = S[s];
+        T Nn[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) Nn[a] = fo[(size_t)a * P.Nvp + k];
+        for (int j = 0; j < nw; ++j) {
+            const SlotSt<T>& Sl = S[wall_slots[j]];
             T An[D];
 #pragma unroll
             for (int d = 0; d < D; ++d) An[d] = Sl.An[d];
             const T sn = dot_rn<D>(x, An);
-            T pG, pH = T(0);
-            if (Sl.kind == 0) {
-                const int C = sn >= T(0) ? Sl.L : Sl.R;
-                const T* rF = sn >= T(0) ? Sl.rL : Sl.rR;
-                T fG, fH = T(0);
-                if (C == i) {
-                    fG = foot_value<D>(phiG, grG, LG, rF, x, h);
-                    if (NA == 2) fH = foot_value<D>(phiH, grH, LH, rF, x, h);
-                } else {
-                    T gr[D], Lm;
-                    const T pg = grad_lim<D>(P.geo, P.limiter, P.fin + k, P.cstride, C, gr, Lm);
-                    fG = foot_value<D>(pg, gr, Lm, rF, x, h);
-                    if (NA == 2) {
-                        const T ph = grad_lim<D>(P.geo, P.limiter, P.fin + P.Nvp + k, P.cstride, C, gr, Lm);
-                        fH = foot_value<D>(ph, gr, Lm, rF, x, h);
-                    }
-                }
-                T gG, gH;
-                eq_eval<D>(Sl.eq, x, gG, gH);
-                pG = Sl.wa * fG + Sl.wb * gG;
-                pH = Sl.wa * fH + Sl.wb * gH;
-            } else if (sn >= T(0)) {
-                pG = foot_value<D>(phiG, grG, LG, Sl.rL, x, h);
-                if (NA == 2) pH = foot_value<D>(phiH, grH, LH, Sl.rL, x, h);
-            } else {
-                eq_eval<D>(Sl.eq, x, pG, pH);
-            }
+            if (sn >= T(0)) continue;
+            T gG, gH;
+            eq_eval<D>(Sl.eq, x, gG, gH);
             const T ss = Sl.sgn * sn;
-            NG += ss * pG;
-            NH += ss * pH;
+            Nn[0] += ss * gG;
+            if (NA == 2) Nn[NA - 1] += ss * gH;
         }
         T gG, gH;
         eq_eval<D>(ceq, x, gG, gH);
-        fo[k] = (phiG * upd[0] + gG * upd[1] - NG * upd[2]) * upd[3];
-        if (NA == 2) fo[P.Nvp + k] = (phiH * upd[0] + gH * upd[1] - NH * upd[2]) * upd[3];
+        fo[k] = (fi[k] * upd[0] + gG * upd[1] - Nn[0] * upd[2]) * upd[3];
+        if (NA == 2) fo[P.Nvp + k] = (fi[P.Nvp + k] * upd[0] + gH * upd[1] - Nn[NA - 1] * upd[2]) * upd[3];
     }
 }
 
@@ -373,12 +462,36 @@ template <int D, typename T>
 static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout,
                                  double dt)
 {
-    StepP<D, T> P;
     const bool f32 = sizeof(T) == 4;
+    const int NA = NArr<D>::v;
+    const bool grad = c->cfg.limiter != 0;
+    if (grad) {
+        // sized for the f capacity so that adaptation does not reallocate it
+        const size_t need = (size_t)c->Nc * NA * D * std::max(c->fcap, c->Nvp) * sizeof(T);
+        if (c->grad_bytes < need) {
+            if (c->grad) cudaFree(c->grad);
+            c->grad = nullptr;
+            c->grad_bytes = 0;
+            cudaError_t e = cudaMalloc(&c->grad, need);
+            if (e != cudaSuccess) return e;
+            c->grad_bytes = need;
+        }
+        CellGeo<T> geo;
+        geo.nbr = c->nbr;
+        geo.cg = f32 ? (const T*)c->cg_f : (const T*)c->cg_d;
+        geo.r = f32 ? (const T*)c->r_f : (const T*)c->r_d;
+        geo.eps2 = f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d;
+        geo.ns = c->nslot;
+        constexpr int VG = 4;
+        dim3 g(c->Nc, (c->Nv + 256 * VG - 1) / (256 * VG));
+        k_grad<D, T, VG><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin, (T*)c->grad, geo);
+        c->launches += 1;
+    }
+    StepP<D, T> P;
+    P.Nc = c->Nc;
     P.Nv = c->Nv;
     P.Nvp = c->Nvp;
-    P.limiter = c->cfg.limiter;
-    P.cstride = (size_t)c->NA * c->Nvp;
+    P.cstride = (size_t)NA * c->Nvp;
     P.dt = dt;
     P.hd = 0.5 * dt;
     P.h = (T)P.hd;
@@ -388,6 +501,7 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     P.mu_ref = c->mu_ref;
     P.T_ref = c->cfg.T_ref;
     P.fin = (const T*)fin;
+    P.G = grad ? (const T*)c->grad : nullptr;
     P.fout = (T*)fout;
     P.Win = Win;
     P.Wout = Wout;
@@ -401,12 +515,8 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     P.rR = f32 ? (const T*)c->rR_f : (const T*)c->rR_d;
     P.bc = c->bc;
     P.slot = c->slot;
+    P.nslot = c->nslot;
     P.vol = c->vol;
-    P.geo.nbr = c->nbr;
-    P.geo.cg = f32 ? (const T*)c->cg_f : (const T*)c->cg_d;
-    P.geo.r = f32 ? (const T*)c->r_f : (const T*)c->r_d;
-    P.geo.eps2 = f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d;
-    P.geo.ns = c->nslot;
     P.err = c->dev_err;
     k_step<D, T, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(P);
     c->launches += 1;
