@@ -127,6 +127,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+def aggregate(ms, updates, ws, device=None):
+    """Whole-job numbers over ranks: the slowest rank's time and the sum of
+    the cell-node updates (replicas, weak scaling).  Uses torch.distributed
+    when ws > 1 (NCCL on the GPU, gloo on the CPU)."""
+    if ws <= 1:
+        return float(ms), float(updates)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms), float(updates)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 # ---------------------------------------------------------------- peaks
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -143,12 +160,14 @@ def _traffic(kind, Nc, Nv):
     changed since the counters were taken."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "step_kernel_dram.json")
-    src = os.path.join(ROOT, "paper_2212_05645_gb300", "csrc", "avs_step.cu")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("avs_step.cu", "avs_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2212_05645_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()[:16]
     e = d.get(kind)
     if not e or e.get("src_sha") != sha:
         return None
@@ -218,7 +237,8 @@ def run_gpu(args):
     B.build()
     stream = torch.cuda.current_stream()
     w = _workload("mixed")
-    g = A.AVS(w, precision="mixed", stream=stream.cuda_stream)
+    # headline form: mixed precision with the learned proposer (full criterion every 4th adaptation)
+    g = A.AVS(w, precision="mixed", stream=stream.cuda_stream, learned=True, full_every=4)
     g.init_field()
     Nc = g.Nc
     nu = args.nu
@@ -250,13 +270,14 @@ def run_gpu(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
+    astats = []
     for j in range(args.steps):
         ev_s[j].record(stream)
         g.step(nu)
         ev_e[j].record(stream)
         upd.append(Nc * g.Nv * nu)
         step_cells.append(Nc * g.Nv)
-        g.adapt()
+        astats.append(g.adapt())
     t1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -264,19 +285,11 @@ def run_gpu(args):
     clocks = sampler.stop()
     ms = t0.elapsed_time(t1)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
-    my_updates = float(sum(upd))
-    t_max = ms
-    tot_updates = my_updates
-    if ws > 1:
-        tt = torch.tensor([ms, my_updates], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = tt.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        t_max, tot_updates = float(mx[0]), float(sm[1])
+    t_max, tot_updates = aggregate(ms, float(sum(upd)), ws, device="cuda")
     value = tot_updates / (t_max * 1e-3)
 
-    # roofline of the step kernel (dominant): 1 read + 1 write of G and H in FP32
+    # roofline of the UGKS step (k_grad + k_step, 90+ % of the time): algorithmic
+    # traffic = 1 read + 1 write of G and H in FP32 per cell-node
     bytes_per_cn = 2 * g.NA * 4
     kern_ms = sum(step_ms) / (args.steps * nu)
     cn_per_launch = statistics.mean(step_cells)
@@ -284,7 +297,7 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     traffic = _traffic("mixed", Nc, cn_per_launch / Nc)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_step<2,float>", "peak_source": peak_kind,
+            "traffic": traffic, "kernel": "UGKS step: k_grad<2,float> + k_step<2,float>", "peak_source": peak_kind,
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
             "peak_spec_gbs": 8000.0, "frac_of_spec": achieved / 8000.0}
 
@@ -311,7 +324,7 @@ def run_gpu(args):
     # plain FP64 GPU form on the same workload (same definition of a step)
     fp64 = None
     if not args.no_fp64:
-        gd = A.AVS(w, precision="fp64", stream=stream.cuda_stream)
+        gd = A.AVS(w, precision="fp64", stream=stream.cuda_stream, learned=False)
         gd.init_field()
         u = []
         bench_step(gd, u)
@@ -340,10 +353,15 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": w.name, "cells": Nc, "velocity_nodes": g.Nv,
                            "ugks_steps_per_step": nu, "precision": "mixed (f FP32, sums FP64)",
+                           "adaptation": "learned proposer, full criterion every 4th adaptation",
                            "l2": f"inputs larger than L2 (f = {f_mb:.0f} MB per buffer)",
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "fp64_form": fp64,
+                "adaptation": {"full": sum(a["full"] for a in astats), "learned": sum(1 - a["full"] for a in astats),
+                               "mean_checked_cells": statistics.mean(a["checked_cells"] for a in astats),
+                               "missed_nodes_on_full_steps": [a["missed_nodes"] for a in astats if a["full"]],
+                               "nodes": [a["Nv"] for a in astats]},
                 "speedup_vs_fp64_form": (value / ws / fp64["value"]) if fp64 else None}
         print(json.dumps(line), flush=True)
     g.close()

@@ -71,14 +71,17 @@ cudaError_t launch_geom(avs_ctx* c)
 }
 
 // ------------------------------------------------------------------ dt bound
-// min over cells and nodes of |V_i| / sum_faces max(xi . An_out, 0)  (R5)
+// min over cells and nodes of |V_i| / sum_faces max(xi . An_out, 0)  (R5).
+// Correctly rounded division is monotone in the divisor, so the minimum over
+// the nodes of a cell equals |V_i| divided by the largest sum: one division per
+// cell, bit-identical to dividing at every node.
 __global__ void k_dt_unit(int D, int Nv, const double* __restrict__ xi, const int* __restrict__ slot,
                           const unsigned char* __restrict__ nslot, const double* __restrict__ An,
                           const double* __restrict__ vol, unsigned long long* out)
 {
     const int i = blockIdx.x;
     const int ns = nslot[i];
-    double best = INFINITY;
+    double big = 0.0;
     for (int k = threadIdx.x; k < Nv; k += blockDim.x) {
         const double* x = xi + (size_t)k * D;
         double sum = 0.0;
@@ -90,16 +93,19 @@ __global__ void k_dt_unit(int D, int Nv, const double* __restrict__ xi, const in
             if (sl & 1) sn = -sn;
             if (sn > 0.0) sum = __dadd_rn(sum, sn);
         }
-        if (sum > 0.0) {
-            const double t = __ddiv_rn(vol[i], sum);
-            best = t < best ? t : best;
-        }
+        big = sum > big ? sum : big;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const double v = __shfl_down_sync(0xffffffffu, best, o);
-        best = v < best ? v : best;
+        const double v = __shfl_down_sync(0xffffffffu, big, o);
+        big = v > big ? v : big;
     }
-    if ((threadIdx.x & 31) == 0 && best < INFINITY) atomicMin(out, dkey(best));
+    __shared__ double wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = big;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) big = wmax[w] > big ? wmax[w] : big;
+        if (big > 0.0) atomicMin(out, dkey(__ddiv_rn(vol[i], big)));
+    }
 }
 
 cudaError_t launch_dt_unit(avs_ctx* c)

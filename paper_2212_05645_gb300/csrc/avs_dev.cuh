@@ -370,6 +370,28 @@ __device__ __forceinline__ void block_sum(double* v, double* sred, double* out)
     __syncthreads();
 }
 
+// float -> double by bit manipulation on the integer pipe (exact for normal
+// numbers; subnormals, far below any partial sum here, become signed zero).
+// On GB300 the FP64 pipe, which executes the usual conversion, is scarce.
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const unsigned sgn = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+    unsigned hi, lo;
+    if (e == 0u) {
+        hi = sgn;
+        lo = 0u;
+    } else if (e == 0xFFu) {
+        hi = sgn | 0x7FF00000u | (m >> 3);
+        lo = m << 29;
+    } else {
+        hi = sgn | ((e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // Block reduction of N values per thread kept in the element type: warp tree
 // with shuffles in T, then a fixed-order FP64 sum of the per-warp results.
 // Deterministic.  out[0..N-1] (smem, double) is visible to all threads after
@@ -383,7 +405,7 @@ __device__ __forceinline__ void block_sum_t(T* v, double* sw, double* out)
         T x = v[m];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sw[warp * N + m] = (double)x;
+        if (lane == 0) sw[warp * N + m] = to_double(x);
     }
     __syncthreads();
     for (int m = threadIdx.x; m < N; m += NT) {

@@ -175,13 +175,113 @@ __device__ __forceinline__ T foot(const StepP<D, T>& P, int C, int a, int k, con
 
 template <int D> struct FaceGroup { static constexpr int v = (D == 2) ? 4 : 3; };
 
+// nodes per thread per iteration: 16-byte vector loads along the node index
+template <typename T> struct VW { static constexpr int v = 16 / sizeof(T); };
+
+template <typename T, int V>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T* o)
+{
+    if constexpr (sizeof(T) == 4 && V == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    } else if constexpr (sizeof(T) == 8 && V == 2) {
+        const double2 q = *reinterpret_cast<const double2*>(p);
+        o[0] = q.x; o[1] = q.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = p[v];
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void stv(T* p, const T* o)
+{
+    if constexpr (sizeof(T) == 4 && V == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(T) == 8 && V == 2) {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = o[v];
+    }
+}
+
+// Foot values of both arrays at the V nodes k0.. from the upwind cells C[v]
+// (vector loads when all V nodes share the upwind cell).
+template <int D, int NA, int V, typename T>
+__device__ __forceinline__ void foot_v(const StepP<D, T>& P, const int* C, int L, const T* rL, const T* rR, int k0,
+                                       const T (*x)[D], T h, T (*out)[NA])
+{
+    bool uni = true;
+#pragma unroll
+    for (int v = 1; v < V; ++v) uni = uni && (C[v] == C[0]);
+    T fv[NA][V], gv[NA][D][V];
+    if (uni) {
+        const size_t base = (size_t)C[0] * P.cstride + k0;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            ldv<T, V>(P.fin + base + (size_t)a * P.Nvp, fv[a]);
+            if (P.G) {
+                const T* g = P.G + ((size_t)C[0] * NA + a) * D * P.Nvp + k0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) ldv<T, V>(g + (size_t)d * P.Nvp, gv[a][d]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                fv[a][v] = P.fin[(size_t)C[v] * P.cstride + (size_t)a * P.Nvp + k0 + v];
+                if (P.G) {
+                    const T* g = P.G + ((size_t)C[v] * NA + a) * D * P.Nvp + k0 + v;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) gv[a][d][v] = g[(size_t)d * P.Nvp];
+                }
+            }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const T* r = C[v] == L ? rL : rR;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            T val = fv[a][v];
+            if (P.G) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) val += gv[a][d][v] * (r[d] - x[v][d] * h);
+            }
+            out[v][a] = val;
+        }
+    }
+}
+
+template <int D, int V, typename T>
+__device__ __forceinline__ void load_nodes(const StepP<D, T>& P, int k0, T (*x)[D], T* w)
+{
+    T xx[V * D];
+    if constexpr ((V * D * sizeof(T)) % 16 == 0) {
+        constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+        for (int j = 0; j < V * D / PER; ++j) ldv<T, PER>(P.xi + (size_t)k0 * D + j * PER, xx + j * PER);
+    } else {
+#pragma unroll
+        for (int j = 0; j < V * D; ++j) xx[j] = P.xi[(size_t)k0 * D + j];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int d = 0; d < D; ++d) x[v][d] = xx[v * D + d];
+    ldv<T, V>(P.w + k0, w);
+}
+
 template <int D, typename T, int NT>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 3 : 1) k_step(StepP<D, T> P)
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 4 : 1) k_step(StepP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
     constexpr int FG = FaceGroup<D>::v;                  // faces per pass-A sweep
     constexpr int NB = AVS_MAXS * (NW + 1) + NM;         // values reduced after pass B
     constexpr int NR = (FG * NM > NB) ? FG * NM : NB;
+    constexpr int V = VW<T>::v;
     __shared__ SlotSt<T> S[AVS_MAXS];
     __shared__ double sw[(NT / 32) * NR];
     __shared__ double red[NR];
@@ -235,11 +335,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 3 : 1) k_step(StepP<D, 
         T acc[FG * NM];
 #pragma unroll
         for (int m = 0; m < FG * NM; ++m) acc[m] = T(0);
-        for (int k = tid; k < P.Nv; k += NT) {
-            T x[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
-            const T wk = P.w[k];
+        for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+            T x[V][D], wv[V];
+            load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
 #pragma unroll
             for (int j = 0; j < FG; ++j) {
                 const int s = s0 + j;
@@ -248,28 +346,37 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 3 : 1) k_step(StepP<D, 
                 T An[D];
 #pragma unroll
                 for (int d = 0; d < D; ++d) An[d] = Sl.An[d];
-                const T sn = dot_rn<D>(x, An);
                 const bool inter = Sl.kind == 0;
-                if (!inter && sn < T(0)) continue;      // incoming at a boundary: pass B
-                const int C = sn >= T(0) ? Sl.L : Sl.R;
-                const T* rF = sn >= T(0) ? Sl.rL : Sl.rR;
-                const T fG = foot<D, NA>(P, C, 0, k, rF, x, h);
-                const T fH = NA == 2 ? foot<D, NA>(P, C, NA - 1, k, rF, x, h) : T(0);
+                T sn[V];
+                int C[V];
+                bool any = false;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    sn[v] = dot_rn<D>(x[v], An);
+                    C[v] = (sn[v] >= T(0) || !inter) ? Sl.L : Sl.R;
+                    any = any || inter || sn[v] >= T(0);
+                }
+                if (!any) continue;                 // all incoming at a boundary: pass B
+                T fv[V][NA];
+                foot_v<D, NA, V>(P, C, Sl.L, Sl.rL, Sl.rR, k0, x, h, fv);
                 T* m = acc + j * NM;
-                if (inter) {
-                    T xs[D];
 #pragma unroll
-                    for (int d = 0; d < D; ++d) xs[d] = x[d] - Sl.Vt[d];
-                    raw_acc<D>(m, xs, wk * fG, wk * fH);
-                } else {
-                    const T t = wk * sn;
-                    T x2 = T(0);
+                for (int v = 0; v < V; ++v) {
+                    if (inter) {
+                        T xs[D];
 #pragma unroll
-                    for (int d = 0; d < D; ++d) x2 += x[d] * x[d];
-                    m[0] += t * fG;
+                        for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Sl.Vt[d];
+                        raw_acc<D>(m, xs, wv[v] * fv[v][0], NA == 2 ? wv[v] * fv[v][NA - 1] : T(0));
+                    } else if (sn[v] >= T(0)) {
+                        const T t = wv[v] * sn[v];
+                        T x2 = T(0);
 #pragma unroll
-                    for (int d = 0; d < D; ++d) m[1 + d] += t * fG * x[d];
-                    m[D + 1] += t * T(0.5) * (x2 * fG + fH);
+                        for (int d = 0; d < D; ++d) x2 += x[v][d] * x[v][d];
+                        m[0] += t * fv[v][0];
+#pragma unroll
+                        for (int d = 0; d < D; ++d) m[1 + d] += t * fv[v][0] * x[v][d];
+                        m[D + 1] += t * T(0.5) * (x2 * fv[v][0] + (NA == 2 ? fv[v][NA - 1] : T(0)));
+                    }
                 }
             }
         }
@@ -318,23 +425,30 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 3 : 1) k_step(StepP<D, 
         T Vct[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) Vct[d] = (T)Vc[d];
-        for (int k = tid; k < P.Nv; k += NT) {
-            T x[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
-            const T wk = P.w[k];
-            T x2 = T(0);
-#pragma unroll
-            for (int d = 0; d < D; ++d) x2 += x[d] * x[d];
+        for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+            T x[V][D], wv[V], x2[V];
+            load_nodes<D, V>(P, k0, x, wv);
             {
-                T xs[D];
+                T f0[V], f1[V];
+                ldv<T, V>(fi + k0, f0);
+                if (NA == 2) ldv<T, V>(fi + P.Nvp + k0, f1);
 #pragma unroll
-                for (int d = 0; d < D; ++d) xs[d] = x[d] - Vct[d];
-                raw_acc<D>(acc + AVS_MAXS * (NW + 1), xs, wk * fi[k], NA == 2 ? wk * fi[P.Nvp + k] : T(0));
+                for (int v = 0; v < V; ++v) {
+                    T xs[D];
+                    x2[v] = T(0);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        xs[d] = x[v][d] - Vct[d];
+                        x2[v] += x[v][d] * x[v][d];
+                    }
+                    raw_acc<D>(acc + AVS_MAXS * (NW + 1), xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
+                }
             }
-            T Nn[NA];
+            T Nn[NA][V];
 #pragma unroll
-            for (int a = 0; a < NA; ++a) Nn[a] = T(0);
+            for (int a = 0; a < NA; ++a)
+#pragma unroll
+                for (int v = 0; v < V; ++v) Nn[a][v] = T(0);
 #pragma unroll
             for (int s = 0; s < AVS_MAXS; ++s) {
                 if (s >= ns) break;
@@ -342,35 +456,46 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 3 : 1) k_step(StepP<D, 
                 T An[D];
 #pragma unroll
                 for (int d = 0; d < D; ++d) An[d] = Sl.An[d];
-                const T sn = dot_rn<D>(x, An);
-                const T ss = Sl.sgn * sn;
-                T* m = acc + s * (NW + 1);
-                if (Sl.kind != 0 && sn >= T(0)) {          // outgoing at a boundary: the foot value
+                T sn[V];
+                int C[V];
+                bool need_foot = false;
 #pragma unroll
-                    for (int a = 0; a < NA; ++a) Nn[a] += ss * foot<D, NA>(P, Sl.L, a, k, Sl.rL, x, h);
-                    continue;
+                for (int v = 0; v < V; ++v) {
+                    sn[v] = dot_rn<D>(x[v], An);
+                    C[v] = (sn[v] >= T(0) || Sl.kind != 0) ? Sl.L : Sl.R;
+                    need_foot = need_foot || Sl.kind == 0 || sn[v] >= T(0);
                 }
-                T gG, gH;
-                eq_eval<D>(Sl.eq, x, gG, gH);
-                const T t = wk * sn;
-                m[0] += t * gG;
+                T fv[V][NA];
+                if (need_foot) foot_v<D, NA, V>(P, C, Sl.L, Sl.rL, Sl.rR, k0, x, h, fv);
+                T* m = acc + s * (NW + 1);
 #pragma unroll
-                for (int d = 0; d < D; ++d) m[1 + d] += t * gG * x[d];
-                m[D + 1] += t * T(0.5) * (x2 * gG + gH);
-                if (Sl.kind == 0) {
-                    const int C = sn >= T(0) ? Sl.L : Sl.R;
-                    const T* rF = sn >= T(0) ? Sl.rL : Sl.rR;
-                    Nn[0] += ss * (Sl.wa * foot<D, NA>(P, C, 0, k, rF, x, h) + Sl.wb * gG);
-                    if (NA == 2) Nn[NA - 1] += ss * (Sl.wa * foot<D, NA>(P, C, NA - 1, k, rF, x, h) + Sl.wb * gH);
-                } else if (Sl.kind == 2) {
-                    Nn[0] += ss * gG;
-                    if (NA == 2) Nn[NA - 1] += ss * gH;
-                } else {
-                    m[NW] += wk * (-sn) * gG;                 // wall: incoming part added in pass C
+                for (int v = 0; v < V; ++v) {
+                    const T ss = Sl.sgn * sn[v];
+                    if (Sl.kind != 0 && sn[v] >= T(0)) {     // outgoing at a boundary: the foot value
+#pragma unroll
+                        for (int a = 0; a < NA; ++a) Nn[a][v] += ss * fv[v][a];
+                        continue;
+                    }
+                    T gG, gH;
+                    eq_eval<D>(Sl.eq, x[v], gG, gH);
+                    const T t = wv[v] * sn[v];
+                    m[0] += t * gG;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) m[1 + d] += t * gG * x[v][d];
+                    m[D + 1] += t * T(0.5) * (x2[v] * gG + gH);
+                    if (Sl.kind == 0) {
+                        Nn[0][v] += ss * (Sl.wa * fv[v][0] + Sl.wb * gG);
+                        if (NA == 2) Nn[NA - 1][v] += ss * (Sl.wa * fv[v][NA - 1] + Sl.wb * gH);
+                    } else if (Sl.kind == 2) {
+                        Nn[0][v] += ss * gG;
+                        if (NA == 2) Nn[NA - 1][v] += ss * gH;
+                    } else {
+                        m[NW] += wv[v] * (-sn[v]) * gG;          // wall: incoming part added in pass C
+                    }
                 }
             }
 #pragma unroll
-            for (int a = 0; a < NA; ++a) fo[(size_t)a * P.Nvp + k] = Nn[a];   // parked until pass C
+            for (int a = 0; a < NA; ++a) stv<T, V>(fo + (size_t)a * P.Nvp + k0, Nn[a]);   // parked until pass C
         }
         block_sum_t<NB, NT>(acc, sw, red);
     }
@@ -429,32 +554,41 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 3 : 1) k_step(StepP<D, 
     }
     __syncthreads();
 
-    // ---------------- pass C: collision update
+    // ---------------- pass C: collision update (pad nodes are written as zero)
     const int nw = n_wall;
-    for (int k = tid; k < P.Nv; k += NT) {
-        T x[D];
+    for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+        T x[V][D], wv[V];
+        load_nodes<D, V>(P, k0, x, wv);
+        T Nn[NA][V], fv[NA][V], out[NA][V];
 #pragma unroll
-        for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
-        T Nn[NA];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) Nn[a] = fo[(size_t)a * P.Nvp + k];
-        for (int j = 0; j < nw; ++j) {
-            const SlotSt<T>& Sl = S[wall_slots[j]];
-            T An[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) An[d] = Sl.An[d];
-            const T sn = dot_rn<D>(x, An);
-            if (sn >= T(0)) continue;
-            T gG, gH;
-            eq_eval<D>(Sl.eq, x, gG, gH);
-            const T ss = Sl.sgn * sn;
-            Nn[0] += ss * gG;
-            if (NA == 2) Nn[NA - 1] += ss * gH;
+        for (int a = 0; a < NA; ++a) {
+            ldv<T, V>(fo + (size_t)a * P.Nvp + k0, Nn[a]);
+            ldv<T, V>(fi + (size_t)a * P.Nvp + k0, fv[a]);
         }
-        T gG, gH;
-        eq_eval<D>(ceq, x, gG, gH);
-        fo[k] = (fi[k] * upd[0] + gG * upd[1] - Nn[0] * upd[2]) * upd[3];
-        if (NA == 2) fo[P.Nvp + k] = (fi[P.Nvp + k] * upd[0] + gH * upd[1] - Nn[NA - 1] * upd[2]) * upd[3];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            for (int j = 0; j < nw; ++j) {
+                const SlotSt<T>& Sl = S[wall_slots[j]];
+                T An[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) An[d] = Sl.An[d];
+                const T sn = dot_rn<D>(x[v], An);
+                if (sn >= T(0)) continue;
+                T gG, gH;
+                eq_eval<D>(Sl.eq, x[v], gG, gH);
+                const T ss = Sl.sgn * sn;
+                Nn[0][v] += ss * gG;
+                if (NA == 2) Nn[NA - 1][v] += ss * gH;
+            }
+            T gG, gH;
+            eq_eval<D>(ceq, x[v], gG, gH);
+            const bool real = k0 + v < P.Nv;
+            out[0][v] = real ? (fv[0][v] * upd[0] + gG * upd[1] - Nn[0][v] * upd[2]) * upd[3] : T(0);
+            if (NA == 2)
+                out[NA - 1][v] = real ? (fv[NA - 1][v] * upd[0] + gH * upd[1] - Nn[NA - 1][v] * upd[2]) * upd[3] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) stv<T, V>(fo + (size_t)a * P.Nvp + k0, out[a]);
     }
 }
 
@@ -518,7 +652,8 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     P.nslot = c->nslot;
     P.vol = c->vol;
     P.err = c->dev_err;
-    k_step<D, T, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(P);
+    constexpr int NT = sizeof(T) == 4 ? 128 : 256;
+    k_step<D, T, NT><<<c->Nc, NT, 0, c->stream>>>(P);
     c->launches += 1;
     return cudaGetLastError();
 }
