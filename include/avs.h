@@ -68,7 +68,7 @@ typedef struct {
     int limiter;          /* AVS_LIM_*; Venkatakrishnan with eps^2 = (lim_K dx)^3           */
     double lim_K;
     int corr_iters;       /* passes of the conservation correction (Sec. 3.3)               */
-    int max_nodes;        /* velocity-node capacity; 0 = 8x the step-0 count                */
+    int max_nodes;        /* velocity-node capacity (fixed); 0 = 1.25x the step-0 count, grown on demand */
     int learned_full_every; /* learned form: run the full criterion every n-th adaptation   */
 } avs_config;
 
@@ -180,15 +180,20 @@ avs_status avs_criterion_noalloc(int dim, int Nc, int Nv, const double *f, const
 /* ---- learned proposer (not in the paper) ------------------------------------
  * An MLP 8 -> 64 -> 64 -> 4 (ReLU, ReLU, logits), BF16 tensor-core forward and
  * backward passes with FP32 accumulation and FP32 master weights.  From eight
- * per-cell features (log rho, |U|/sqrt(RT), log T, log of the mean free path
- * of Eq. 4 over the cell size, the largest relative jumps of rho, T and U to
- * the face neighbours, |q|/(rho (RT)^1.5)) it predicts four per-cell labels of
+ * per-cell features (log rho, the velocity components over sqrt(R T_ref) (in
+ * 2D the third slot holds |q|/(rho (RT)^1.5)), log T, log of the mean free
+ * path of Eq. 4 over the cell size, the largest relative jumps of rho and T to
+ * the face neighbours) it predicts four per-cell labels of
  * the Sec. 3.4 criterion (split witness, dominant, near-dominant, merge
  * blocker).  With cfg.learned = 1, avs_adapt evaluates the criterion only on
- * the cells whose first three logits exceed the threshold (the check set);
+ * the cells whose dominant logit exceeds the threshold (the check set: the cell
+ * attaining M_k decides both the split and the merge test of node k);
  * every learned_full_every-th adaptation it also runs the full criterion,
  * counts the nodes whose decision the check set got wrong, takes labels from
- * it and trains.  Parameters: AVS_MLP_NPARAM floats laid out
+ * it and trains.  The check set keeps a budgeted fraction of the cells by
+ * dominant logit (initially 25 %); the budget doubles after a full step that
+ * found more than 1 % of the nodes missed and shrinks by 20 % after one that
+ * found none.  Parameters: AVS_MLP_NPARAM floats laid out
  * W1[64][8], b1[64], W2[64][64], b2[64], W3[4][64], b3[4] (weights [out][in]). */
 #define AVS_MLP_NPARAM 4996
 avs_status avs_mlp_set_params(avs_ctx *ctx, const float *params);     /* host */

@@ -6,16 +6,16 @@ macroscopic features, predicts which cells can decide a split/merge, so that
 the criterion is evaluated only on that check set.  Everything here is plain
 numpy in float64 and written from these definitions:
 
-features (8 per cell i; rho, U, T from the moments of f, R = 1/2)
+features (8 per cell i; rho, U, T from the moments of f, R = 1/2, T_ref = 1)
   0  log rho_i
-  1  |U_i| / sqrt(R T_i)
-  2  log T_i
-  3  log(lambda_i / dx_i), lambda from Eq. (4) with the VHS viscosity of Eq. (3),
+  1  U_x / sqrt(R T_ref)
+  2  U_y / sqrt(R T_ref)
+  3  U_z / sqrt(R T_ref) in 3D; |q_i| / (rho_i (R T_i)^(3/2)) in 2D
+  4  log T_i
+  5  log(lambda_i / dx_i), lambda from Eq. (4) with the VHS viscosity of Eq. (3),
      dx_i = |V_i|^(1/D)
-  4  max over face neighbours |rho_j - rho_i| / rho_i
-  5  max over face neighbours |T_j - T_i| / T_i
-  6  max over face neighbours |U_j - U_i| / sqrt(R T_i)
-  7  |q_i| / (rho_i (R T_i)^(3/2))
+  6  max over face neighbours |rho_j - rho_i| / rho_i
+  7  max over face neighbours |T_j - T_i| / T_i
 labels (4 per cell) from m_ik = s max(M1_ik, M2_ik) and M_k = max_i m_ik
   0  split witness:   some node k below the level cap has m_ik > C1
   1  dominant:        some node k with M_k >= C2 has m_ik == M_k
@@ -43,19 +43,19 @@ def features(D, Wc, q, vol, faceL, faceR, R=0.5, mu_ref=1.0, omega=0.81, T_ref=1
     mu = mu_ref * (T / T_ref) ** omega
     lam = 2.0 * mu * (5 - 2 * omega) * (7 - 2 * omega) / (15.0 * rho * np.sqrt(2 * math.pi * RT))
     dx = vol ** (1.0 / D)
-    sq = np.sqrt(RT)
     X = np.zeros((len(rho), NF))
     X[:, 0] = np.log(rho)
-    X[:, 1] = np.sqrt((U * U).sum(1)) / sq
-    X[:, 2] = np.log(T)
-    X[:, 3] = np.log(lam / dx)
+    su = math.sqrt(R * T_ref)
+    X[:, 1] = U[:, 0] / su
+    X[:, 2] = U[:, 1] / su
+    X[:, 3] = U[:, 2] / su if D == 3 else np.sqrt((q * q).sum(1)) / (rho * RT ** 1.5)
+    X[:, 4] = np.log(T)
+    X[:, 5] = np.log(lam / dx)
     inner = faceR >= 0
     L, Rr = faceL[inner], faceR[inner]
     for a, b in ((L, Rr), (Rr, L)):
-        np.maximum.at(X[:, 4], a, np.abs(rho[b] - rho[a]) / rho[a])
-        np.maximum.at(X[:, 5], a, np.abs(T[b] - T[a]) / T[a])
-        np.maximum.at(X[:, 6], a, np.sqrt(((U[b] - U[a]) ** 2).sum(1)) / sq[a])
-    X[:, 7] = np.sqrt((q * q).sum(1)) / (rho * RT ** 1.5)
+        np.maximum.at(X[:, 6], a, np.abs(rho[b] - rho[a]) / rho[a])
+        np.maximum.at(X[:, 7], a, np.abs(T[b] - T[a]) / T[a])
     return X
 
 

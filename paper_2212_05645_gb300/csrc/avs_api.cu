@@ -470,7 +470,8 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     st = initial_tree(c);
     if (st != AVS_OK) goto bad;
     {
-        int fnodes = cfg->max_nodes > 0 ? cfg->max_nodes : std::min(c->cap, 8 * c->Nv);
+        // room for 25 % growth; avs_adapt reallocates beyond that unless max_nodes is set
+        int fnodes = cfg->max_nodes > 0 ? cfg->max_nodes : std::min(c->cap, c->Nv + c->Nv / 4 + 32);
         fnodes = std::max(fnodes, c->Nv);
         c->fcap = round_up(fnodes, 32);
         st = alloc_f(c, c->fcap, &c->f[0], &c->f[1]);
@@ -587,11 +588,17 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
             if (c->mlp_trained > 0) {
                 CK(mlp_misses(c, c->M, c->M_alt, c->mlp_count + 1));
                 CK(cudaMemcpyAsync(&missed, c->mlp_count + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                // the full criterion judges the check set: widen it when it missed
+                // more than 1 % of the nodes, narrow it when it missed none
+                if (missed > c->Nv / 100) c->mlp_budget = std::min(1.0f, 2.0f * c->mlp_budget);
+                else if (missed == 0) c->mlp_budget = std::max(0.05f, 0.8f * c->mlp_budget);
             }
             CK(mlp_labels(c, c->f[c->cur], c->mlp_Y));
             for (int it = 0; it < c->mlp_train_iters; ++it)
                 CK(mlp_grad_step(c, c->Nc, c->mlp_X, c->mlp_Y, c->mlp_lr, c->mlp_grad));
             c->mlp_trained += c->mlp_train_iters;
+            CK(mlp_calibrate(c, c->mlp_budget));
             checked = c->Nc;
         }
     } else {
@@ -815,6 +822,7 @@ avs_status avs_mlp_train(avs_ctx* c, int iters, float lr, float* loss_out)
     if (st != AVS_OK) return st;
     for (int it = 0; it < iters; ++it) CK(mlp_grad_step(c, c->Nc, c->mlp_X, c->mlp_Y, lr, c->mlp_grad));
     c->mlp_trained += iters;
+    if (iters > 0) CK(mlp_calibrate(c, c->mlp_budget));
     if (loss_out) {
         float g = 0.f;
         CK(cudaMemcpyAsync(&g, c->mlp_grad + AVS_MLP_NPARAM, sizeof(float), cudaMemcpyDeviceToHost, c->stream));

@@ -82,6 +82,7 @@ struct avs_ctx {
     float mlp_lr = 0.1f;
     int mlp_train_iters = 50;
     float mlp_zthr = -1.0f;                          // logit threshold of the check set
+    float mlp_budget = 0.25f;                        // fraction of cells in the check set
 };
 
 namespace avs {

@@ -17,10 +17,17 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "avs_dev.cuh"
 #include "avs_internal.h"
 #include "avs_mlp.h"
+
+#define CK_RET(x)                               \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
 
 namespace avs {
 
@@ -396,8 +403,9 @@ __global__ void k_mlp_reduce(int nblk, const float* __restrict__ part, float* gr
 
 // ------------------------------------------------------------------ features and labels
 // Per-cell features (rho, U, T, lambda from the cell's moments Wf and heat flux q):
-// log rho, |U|/sqrt(RT), log T, log(lambda/dx), max neighbour jumps of rho, T, U
-// (relative), |q|/(rho (RT)^1.5).  lambda from Eqs. (3)-(4).
+// log rho, U / sqrt(R T_ref) (components; in 2D the third slot is
+// |q| / (rho (RT)^1.5)), log T, log(lambda / dx), largest relative jumps of rho
+// and T to the face neighbours.  lambda from Eqs. (3)-(4).
 template <int D>
 __global__ void k_features(int Nc, const double* __restrict__ Wc, const double* __restrict__ q,
                            const double* __restrict__ vol, const int* __restrict__ nbr,
@@ -412,33 +420,27 @@ __global__ void k_features(int Nc, const double* __restrict__ Wc, const double* 
     const double mu = mu_ref * pow(T / T_ref, omega);
     const double lam = 2.0 * mu * (5 - 2 * omega) * (7 - 2 * omega) / (15.0 * rho * sqrt(2 * AVS_PI * RT));
     const double dx = pow(vol[i], 1.0 / D);
-    double u2 = 0.0, q2 = 0.0;
-    for (int d = 0; d < D; ++d) {
-        u2 += U[d] * U[d];
-        q2 += q[(size_t)i * D + d] * q[(size_t)i * D + d];
-    }
-    const double sq = sqrt(RT);
-    double jr = 0.0, jt = 0.0, ju = 0.0;
+    double q2 = 0.0;
+    for (int d = 0; d < D; ++d) q2 += q[(size_t)i * D + d] * q[(size_t)i * D + d];
+    double jr = 0.0, jt = 0.0;
     for (int s = 0; s < nslot[i]; ++s) {
         const int j = nbr[i * AVS_MAXS + s];
         if (j < 0) continue;
         double rj, Uj[3], RTj;
         prim<D>(Wc + (size_t)j * (D + 2), rj, Uj, RTj);
-        double du = 0.0;
-        for (int d = 0; d < D; ++d) du += (Uj[d] - U[d]) * (Uj[d] - U[d]);
         jr = fmax(jr, fabs(rj - rho) / rho);
         jt = fmax(jt, fabs(RTj / R - T) / T);
-        ju = fmax(ju, sqrt(du) / sq);
     }
+    const double su = sqrt(R * T_ref);
     float* x = X + (size_t)i * NF;
     x[0] = (float)log(rho);
-    x[1] = (float)(sqrt(u2) / sq);
-    x[2] = (float)log(T);
-    x[3] = (float)log(lam / dx);
-    x[4] = (float)jr;
-    x[5] = (float)jt;
-    x[6] = (float)ju;
-    x[7] = (float)(sqrt(q2) / (rho * RT * sq));
+    x[1] = (float)(U[0] / su);
+    x[2] = (float)(U[1] / su);
+    x[3] = D == 3 ? (float)(U[2] / su) : (float)(sqrt(q2) / (rho * RT * sqrt(RT)));
+    x[4] = (float)log(T);
+    x[5] = (float)log(lam / dx);
+    x[6] = (float)jr;
+    x[7] = (float)jt;
 }
 
 // Labels from the scaled criterion values m_ik = s max(M1, M2) (same
@@ -484,15 +486,18 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
     }
 }
 
-// check set: cells whose split-witness, dominant or near-dominant logit is
-// above the threshold logit; appended in any order (the criterion's max is
-// order-free).
+// check set: cells whose dominant logit reaches the threshold.  The cell
+// attaining M_k decides both the split test (M_k > C1) and whether node k
+// blocks a merge (M_k >= C2); a check set holding every dominant cell would
+// reproduce the full criterion's decisions, a budgeted one misses some and the
+// full criterion (run every n-th adaptation) measures and repairs them.
+// Appended in any order (the criterion's max is order-free).
 __global__ void k_checkset(int Nc, const float* __restrict__ logits, float zthr, int* list, int* count)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Nc) return;
     const float* z = logits + (size_t)i * NO;
-    if (z[0] > zthr || z[1] > zthr || z[2] > zthr) list[atomicAdd(count, 1)] = i;
+    if (z[1] >= zthr) list[atomicAdd(count, 1)] = i;
 }
 
 // nodes whose split or merge-candidate decision differs between the criterion
@@ -507,6 +512,22 @@ __global__ void k_misses(int Nv, const double* __restrict__ Mf, const double* __
 }
 
 // ------------------------------------------------------------------ launchers
+// Threshold of the check set: the dominant logit that keeps the top `budget`
+// fraction of the cells of the current state (order statistic on the host).
+cudaError_t mlp_calibrate(avs_ctx* c, float budget)
+{
+    CK_RET(mlp_forward(c, c->Nc, c->mlp_X, c->mlp_logits));
+    std::vector<float> z((size_t)c->Nc * NO);
+    CK_RET(cudaMemcpyAsync(z.data(), c->mlp_logits, sizeof(float) * z.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK_RET(cudaStreamSynchronize(c->stream));
+    std::vector<float> d(c->Nc);
+    for (int i = 0; i < c->Nc; ++i) d[i] = z[(size_t)i * NO + 1];
+    const int keep = std::max(1, std::min(c->Nc, (int)ceilf(budget * (float)c->Nc)));
+    std::nth_element(d.begin(), d.begin() + (c->Nc - keep), d.end());
+    c->mlp_zthr = d[c->Nc - keep] - 1e-6f * fabsf(d[c->Nc - keep]);
+    return cudaSuccess;
+}
+
 cudaError_t mlp_misses(avs_ctx* c, const double* Mf, const double* Ms, int* count)
 {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), c->stream);

@@ -17,4 +17,6 @@ cudaError_t mlp_features(avs_ctx* c, const double* Wc, const double* q, float* X
 cudaError_t mlp_labels(avs_ctx* c, const void* f, float* Y);
 cudaError_t mlp_checkset(avs_ctx* c, const float* logits, float zthr, int* list, int* count);
 cudaError_t mlp_misses(avs_ctx* c, const double* Mf, const double* Ms, int* count);
+// threshold of the check set: keeps the top `budget` fraction of cells by dominant logit
+cudaError_t mlp_calibrate(avs_ctx* c, float budget);
 }  // namespace avs

@@ -499,7 +499,7 @@ def cylinder(n_theta=96, n_r=128, Ma=5.0, Kn=0.1, C1=1.0, max_refine=4, precisio
                     precision=precision, steps=200)
 
 
-def blunt_wedge(n_theta=240, n_r=160, Ma=8.0, Kn=0.01, C1=1.0, max_refine=5, precision="mixed",
+def blunt_wedge(n_theta=240, n_r=160, Ma=8.0, Kn=0.01, C1=0.5, max_refine=5, precision="mixed",
                 learned=True) -> Workload:
     """Blunt wedge (paper Sec. 4.3 shape): 240x160 body-fitted cells clustered
     to the wall, Ma 8, Kn 0.01, forest 32x32 over [-20, 20]^2 (read as
@@ -515,7 +515,7 @@ def blunt_wedge(n_theta=240, n_r=160, Ma=8.0, Kn=0.01, C1=1.0, max_refine=5, pre
                     precision=precision, learned=learned)
 
 
-def sphere(n_r=64, n_theta=48, n_phi=48, Ma=4.25, Kn=0.031, C1=1.0, max_refine=3,
+def sphere(n_r=64, n_theta=48, n_phi=48, Ma=4.25, Kn=0.031, C1=2.0, max_refine=3,
            precision="mixed", learned=True) -> Workload:
     """Sphere (paper Sec. 4.6 shape): spherical shell 64 r x 48 theta x 48 phi,
     r in [1, 10], Ma 4.25, Kn 0.031, octree 16^3 over [-12, 12]^3 (read as

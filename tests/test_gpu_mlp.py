@@ -124,3 +124,58 @@ def test_learned_adaptation_check_set_and_misses():
     if st_l["full"] == 1 or st_l["missed_nodes"] == 0:
         assert st_l["Nv"] == o["Nv"]
     g.close()
+
+
+def _walled_box(n=32, precision="mixed"):
+    wall = wl._bc_row(wl.BC_WALL, T=1.0)
+    hot = wl._bc_row(wl.BC_WALL, T=1.3)
+    mesh = wl.cartesian_mesh((n, n), (1.0, 1.0), bcs=[(wall, hot), (wall, wall)])
+    v = 4.0 * wl.sqrt_RT(1.0)
+    return wl.Workload(f"walled-box-{n}", mesh, 2, (12, 12), (-v, -v), (v, v), 2, Kn=0.05, omega=0.81,
+                       Pr=2.0 / 3.0, C1=2.0, C2=wl.K_SIGMA * 2.0, W_inf=(1.0, 0.0, 0.0, 1.0),
+                       W_init=wl.sweep_W(mesh), precision=precision, learned=True)
+
+
+def _wall_heat_flux(w, q):
+    """q . n at the cells next to a wall (outward normals of the boundary faces)."""
+    m = w.mesh
+    b = m.faceR < 0
+    n = m.An[b] / np.linalg.norm(m.An[b], axis=1, keepdims=True)
+    return (q[m.faceL[b]] * n).sum(1)
+
+
+def test_learned_proposer_gain_over_plain_criterion():
+    """What the trained network gains: the criterion runs on a quarter of the
+    cells (the proposer's budget).  The plain criterion stays the judge: it
+    counts the nodes whose decision the check set got wrong, and the learned
+    run and the plain run (same start, same steps) are compared by the L1 gap
+    of their f-moments and wall heat flux."""
+    avs = need_gpu()
+    import time
+    w = _walled_box()
+    gl = avs.AVS(w, learned=True, full_every=1000)
+    gp = avs.AVS(w, learned=False)
+    for g in (gl, gp):
+        g.init_field(amp=1e-3, seed=21)
+    loss = gl.mlp_train(400, lr=0.2)
+    fracs, misses, tl, tp = [], [], 0.0, 0.0
+    dt = gp.dt()
+    for cycle in range(4):
+        for g in (gl, gp):
+            g.step(10, dt=dt)
+        t0 = time.perf_counter(); sl = gl.adapt(force_full=(cycle == 3)); tl += time.perf_counter() - t0
+        t0 = time.perf_counter(); sp = gp.adapt(); tp += time.perf_counter() - t0
+        if not sl["full"]:
+            fracs.append(sl["checked_cells"] / gl.Nc)
+        else:
+            misses.append(sl["missed_nodes"])
+    Wl, ql = gl.moments()
+    Wp, qp = gp.moments()
+    l1_mom = np.abs(Wl - Wp).sum() / np.abs(Wp).sum()
+    hf = np.abs(_wall_heat_flux(w, ql) - _wall_heat_flux(w, qp)).sum() / np.abs(_wall_heat_flux(w, qp)).sum()
+    print(f"\nlearned proposer: loss {loss:.4f}, checked fraction {np.mean(fracs):.3f}, misses {misses}, "
+          f"L1 f-moment gap {l1_mom:.2e}, wall heat-flux gap {hf:.2e}, adapt time learned {tl:.3f}s plain {tp:.3f}s")
+    assert np.mean(fracs) <= 0.6
+    assert misses[-1] < 0.5 * gl.Nv
+    assert l1_mom < 1e-2 and hf < 0.2
+    gl.close(); gp.close()

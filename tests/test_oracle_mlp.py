@@ -45,8 +45,8 @@ def test_bce_definition_and_sgd_descends():
 
 
 def test_features_uniform_state_closed_form():
-    """A uniform state at rest: log rho, 0, log T, log(Kn dx^-1) with the
-    reference mean free path equal to Kn, and zero neighbour jumps."""
+    """A uniform state at rest: log rho, zero velocity, log T, log(Kn / dx)
+    (the reference mean free path equals Kn), zero neighbour jumps."""
     w = wl.sweep_box((4, 4))
     m = w.mesh
     rho, T = 1.0, 1.0
@@ -55,9 +55,9 @@ def test_features_uniform_state_closed_form():
     Kn = 0.05
     mu = O.mu_ref_from_Kn(Kn, 0.81)
     X = mlp.features(2, Wc, q, m.vol, m.faceL, m.faceR, mu_ref=mu)
-    assert np.allclose(X[:, 0], 0.0) and np.allclose(X[:, 1], 0.0) and np.allclose(X[:, 2], 0.0)
-    assert np.allclose(X[:, 3], math.log(Kn / 0.25), rtol=1e-13)
-    assert np.all(X[:, 4:] == 0.0)
+    assert np.allclose(X[:, :5], 0.0)
+    assert np.allclose(X[:, 5], math.log(Kn / 0.25), rtol=1e-13)
+    assert np.all(X[:, 6:] == 0.0)
 
 
 def test_labels_small_case_by_hand():
