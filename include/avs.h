@@ -210,6 +210,11 @@ avs_status avs_features(avs_ctx *ctx, float *X_out, float *Y_out);
 /* iters SGD steps on the current state's features and labels; last loss out. */
 avs_status avs_mlp_train(avs_ctx *ctx, int iters, float lr, float *loss_out);
 
+/* Measured FMA throughput of the current GPU (GFLOP/s, 2 flops per FMA) in FP64
+ * (fp64 = 1) or FP32: independent multiply-add chains, timed with events.  A
+ * measurement utility for the ALU rooflines; the paper has no counterpart. */
+avs_status avs_measure_fma_peak(int fp64, int iters, double *gflops);
+
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t   avs_kernel_launches(const avs_ctx *ctx);
 

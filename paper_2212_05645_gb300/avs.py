@@ -27,7 +27,7 @@ EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs
             "avs_dt", "ugks_step", "ugks_step_dt", "avs_adapt", "avs_moments", "avs_f_moments", "avs_set_W",
             "avs_criterion", "avs_get_tree", "avs_get_f", "avs_set_f", "avs_sync", "avs_kernel_launches",
             "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
-            "avs_mlp_train"]
+            "avs_mlp_train", "avs_measure_fma_peak"]
 MLP_NPARAM = 4996
 
 
@@ -99,6 +99,7 @@ def load():
         "avs_mlp_grad": (C.c_int, [vp, dp, dp, C.c_int, C.c_float, dp, C.POINTER(C.c_float)]),
         "avs_features": (C.c_int, [vp, dp, dp]),
         "avs_mlp_train": (C.c_int, [vp, C.c_int, C.c_float, C.POINTER(C.c_float)]),
+        "avs_measure_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     }
     for name, (rt, args) in sig.items():
         fn = getattr(L, name)
@@ -329,6 +330,15 @@ class AVS:
         loss = C.c_float()
         self._ck(self.L.avs_mlp_train(self.h, int(iters), float(lr), C.byref(loss)))
         return loss.value
+
+
+def fma_peak_gflops(fp64, iters=20000):
+    """Measured FMA throughput of the current GPU in GFLOP/s."""
+    out = C.c_double()
+    st = load().avs_measure_fma_peak(int(fp64), int(iters), C.byref(out))
+    if st != AVS_OK:
+        raise AVSError(st, "avs_measure_fma_peak")
+    return out.value
 
 
 def _is_torch(a):
