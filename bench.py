@@ -288,8 +288,8 @@ def run_gpu(args):
     t_max, tot_updates = aggregate(ms, float(sum(upd)), ws, device="cuda")
     value = tot_updates / (t_max * 1e-3)
 
-    # roofline of the UGKS step (k_grad + k_step, 90+ % of the time): algorithmic
-    # traffic = 1 read + 1 write of G and H in FP32 per cell-node
+    # roofline of the UGKS step (k_grad + k_face + k_cell, 90+ % of the time):
+    # algorithmic traffic = 1 read + 1 write of G and H in FP32 per cell-node
     bytes_per_cn = 2 * g.NA * 4
     kern_ms = sum(step_ms) / (args.steps * nu)
     cn_per_launch = statistics.mean(step_cells)
@@ -297,7 +297,7 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     traffic = _traffic("mixed", Nc, cn_per_launch / Nc)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "UGKS step: k_grad<2,float> + k_step<2,float>", "peak_source": peak_kind,
+            "traffic": traffic, "kernel": "UGKS step: k_grad + k_face + k_cell <2,float>", "peak_source": peak_kind,
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
             "peak_spec_gbs": 8000.0, "frac_of_spec": achieved / 8000.0}
 
@@ -342,6 +342,8 @@ def run_gpu(args):
         fp64 = {"value": sum(u) / (fms * 1e-3), "ms_per_step": fms / kd, "steps": kd}
         gd.close()
 
+    alu = {"fp32_fma_gflops": A.fma_peak_gflops(False), "fp64_fma_gflops": A.fma_peak_gflops(True),
+           "kind": "measured: independent FMA chains, bench.py start-up"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -356,7 +358,7 @@ def run_gpu(args):
                            "adaptation": "learned proposer, full criterion every 4th adaptation",
                            "l2": f"inputs larger than L2 (f = {f_mb:.0f} MB per buffer)",
                            "parallelism": f"replicas x{ws}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "fp64_form": fp64,
                 "adaptation": {"full": sum(a["full"] for a in astats), "learned": sum(1 - a["full"] for a in astats),
                                "mean_checked_cells": statistics.mean(a["checked_cells"] for a in astats),

@@ -75,35 +75,84 @@ cudaError_t launch_geom(avs_ctx* c)
 // Correctly rounded division is monotone in the divisor, so the minimum over
 // the nodes of a cell equals |V_i| divided by the largest sum: one division per
 // cell, bit-identical to dividing at every node.
-__global__ void k_dt_unit(int D, int Nv, const double* __restrict__ xi, const int* __restrict__ slot,
-                          const unsigned char* __restrict__ nslot, const double* __restrict__ An,
-                          const double* __restrict__ vol, unsigned long long* out)
+//
+// The largest FP64 sum is found without evaluating every node in FP64: an
+// FP32 pass gives each node's sum S32 and a bound B on |S32 - S| (inputs and
+// every operation rounded to FP32: |S32 - S| <= 11 u sum_j sum_d |xi_d A_jd|,
+// u = 2^-24, while the results stay normal; B takes 32 u plus 2^-100).  Only nodes with S32 + B >= max_k (S32 - B), which
+// include the node of the exact maximum, are evaluated in FP64.
+template <int NS>
+__global__ void __launch_bounds__(128) k_dt_unit(int D, int Nv, const double* __restrict__ xi,
+                                                 const float* __restrict__ xi_f, const int* __restrict__ slot,
+                                                 const unsigned char* __restrict__ nslot,
+                                                 const double* __restrict__ An, const float* __restrict__ An_f,
+                                                 const double* __restrict__ vol, unsigned long long* out)
 {
+    __shared__ float wlo[4];
+    __shared__ double wbig[4];
     const int i = blockIdx.x;
     const int ns = nslot[i];
+    float A[NS][3];
+    int fidx[NS];
+    bool isR[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int sl = s < ns ? slot[i * AVS_MAXS + s] : -1;
+        fidx[s] = sl >> 1;
+        isR[s] = sl >= 0 && (sl & 1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float a = (sl >= 0 && d < D) ? An_f[(size_t)fidx[s] * D + d] : 0.0f;
+            A[s][d] = isR[s] ? -a : a;
+        }
+    }
+    auto s32 = [&](int k, float& S, float& B) {
+        float x[3] = {0.0f, 0.0f, 0.0f};
+        for (int d = 0; d < D; ++d) x[d] = xi_f[(size_t)k * D + d];
+        S = 0.0f;
+        B = 0.0f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const float sn = x[0] * A[s][0] + x[1] * A[s][1] + x[2] * A[s][2];
+            S += sn > 0.0f ? sn : 0.0f;
+            B += fabsf(x[0] * A[s][0]) + fabsf(x[1] * A[s][1]) + fabsf(x[2] * A[s][2]);
+        }
+        B = B * 0x1p-19f + 0x1p-100f;
+    };
+    float lo = 0.0f;
+    for (int k = threadIdx.x; k < Nv; k += blockDim.x) {
+        float S, B;
+        s32(k, S, B);
+        lo = fmaxf(lo, S - B);
+    }
+    for (int o = 16; o > 0; o >>= 1) lo = fmaxf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    if ((threadIdx.x & 31) == 0) wlo[threadIdx.x >> 5] = lo;
+    __syncthreads();
+    lo = fmaxf(fmaxf(wlo[0], wlo[1]), fmaxf(wlo[2], wlo[3]));
     double big = 0.0;
     for (int k = threadIdx.x; k < Nv; k += blockDim.x) {
+        float S, B;
+        s32(k, S, B);
+        if (S + B < lo) continue;
         const double* x = xi + (size_t)k * D;
         double sum = 0.0;
         for (int s = 0; s < ns; ++s) {
-            const int sl = slot[i * AVS_MAXS + s];
-            const double* a = An + (size_t)(sl >> 1) * D;
+            const double* a = An + (size_t)fidx[s] * D;
             double sn = __dmul_rn(x[0], a[0]);
             for (int d = 1; d < D; ++d) sn = __dadd_rn(sn, __dmul_rn(x[d], a[d]));
-            if (sl & 1) sn = -sn;
+            if (isR[s]) sn = -sn;
             if (sn > 0.0) sum = __dadd_rn(sum, sn);
         }
         big = sum > big ? sum : big;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        const double v = __shfl_down_sync(0xffffffffu, big, o);
+        const double v = __shfl_xor_sync(0xffffffffu, big, o);
         big = v > big ? v : big;
     }
-    __shared__ double wmax[32];
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = big;
+    if ((threadIdx.x & 31) == 0) wbig[threadIdx.x >> 5] = big;
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) big = wmax[w] > big ? wmax[w] : big;
+        for (int w = 1; w < 4; ++w) big = wbig[w] > big ? wbig[w] : big;
         if (big > 0.0) atomicMin(out, dkey(__ddiv_rn(vol[i], big)));
     }
 }
@@ -113,7 +162,12 @@ cudaError_t launch_dt_unit(avs_ctx* c)
     const unsigned long long init = ~0ull;
     cudaError_t e = cudaMemcpyAsync(c->dt_key, &init, sizeof(init), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;
-    k_dt_unit<<<c->Nc, 128, 0, c->stream>>>(c->D, c->Nv, c->xi_d, c->slot, c->nslot, c->An_d, c->vol, c->dt_key);
+    if (c->max_ns <= 4)
+        k_dt_unit<4><<<c->Nc, 128, 0, c->stream>>>(c->D, c->Nv, c->xi_d, c->xi_f, c->slot, c->nslot, c->An_d,
+                                                   c->An_f, c->vol, c->dt_key);
+    else
+        k_dt_unit<AVS_MAXS><<<c->Nc, 128, 0, c->stream>>>(c->D, c->Nv, c->xi_d, c->xi_f, c->slot, c->nslot,
+                                                          c->An_d, c->An_f, c->vol, c->dt_key);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -138,41 +192,63 @@ __device__ __forceinline__ double normal_ik(uint64_t seed, uint64_t i, uint64_t 
     return sqrt(-2.0 * log(U1)) * cos(2.0 * AVS_PI * U2);
 }
 
+// f = g^eq(W_p) (1 + amp z_ik) per cell and node, pads zero.  One block per
+// cell; the per-cell factors are formed once.  The FP64 form evaluates the
+// exponential in FP64; the mixed form, whose f is stored in FP32, in FP32
+// (correctly rounded expf, a few ulp of FP32 at most).  The noise z is the
+// FP64 SplitMix64/Box-Muller normal in both forms.
 template <typename T>
-__global__ void k_maxwell(int D, int NA, int Nv, int Nvp, const double* __restrict__ xi, const double* __restrict__ Wp,
-                          double R, double amp, uint64_t seed, T* f)
+__global__ void __launch_bounds__(256) k_maxwell(int D, int NA, int Nv, int Nvp, const double* __restrict__ xi,
+                                                 const float* __restrict__ xi32, const double* __restrict__ Wp,
+                                                 double R, double amp, uint64_t seed, T* f)
 {
     const int i = blockIdx.x;
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
-    if (k >= Nvp) return;
     T* fi = f + (size_t)i * NA * Nvp;
-    if (k >= Nv) {
-        for (int a = 0; a < NA; ++a) fi[(size_t)a * Nvp + k] = T(0);
-        return;
-    }
     const double* P = Wp + (size_t)i * (D + 2);
     const double rho = P[0], RT = R * P[D + 1];
-    double c2 = 0.0;
-    for (int d = 0; d < D; ++d) {
-        const double c = __dsub_rn(xi[(size_t)k * D + d], P[1 + d]);
-        c2 = __dadd_rn(c2, __dmul_rn(c, c));
+    const double pref = rho / pow(2.0 * AVS_PI * RT, 0.5 * D);
+    const float pref32 = (float)pref, i2RT32 = (float)(1.0 / (2.0 * RT));
+    float U32[3] = {0.0f, 0.0f, 0.0f};
+    for (int d = 0; d < D; ++d) U32[d] = (float)P[1 + d];
+    for (int k = threadIdx.x; k < Nvp; k += blockDim.x) {
+        if (k >= Nv) {
+            for (int a = 0; a < NA; ++a) fi[(size_t)a * Nvp + k] = T(0);
+            continue;
+        }
+        T G;
+        if (sizeof(T) == 8) {
+            double c2 = 0.0;
+            for (int d = 0; d < D; ++d) {
+                const double c = __dsub_rn(xi[(size_t)k * D + d], P[1 + d]);
+                c2 = __dadd_rn(c2, __dmul_rn(c, c));
+            }
+            double g = pref * exp(-c2 / (2.0 * RT));
+            if (amp != 0.0) g *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
+            G = (T)g;
+        } else {
+            float c2 = 0.0f;
+            for (int d = 0; d < D; ++d) {
+                const float c = xi32[(size_t)k * D + d] - U32[d];
+                c2 += c * c;
+            }
+            float g = pref32 * expf(-c2 * i2RT32);
+            if (amp != 0.0) g *= (float)(1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k));
+            G = (T)g;
+        }
+        fi[k] = G;
+        if (NA == 2) fi[Nvp + k] = (T)((3 - D) * RT) * G;
     }
-    double G = rho / pow(2.0 * AVS_PI * RT, 0.5 * D) * exp(-c2 / (2.0 * RT));
-    if (amp != 0.0) G *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
-    fi[k] = (T)G;
-    if (NA == 2) fi[Nvp + k] = (T)((3.0 - D) * RT * G);
 }
 
 cudaError_t launch_maxwell(avs_ctx* c, const double* Wp, int Ncells, double amp, uint64_t seed, void* fout,
                            int f_is_double, int Nvp)
 {
-    dim3 g(Ncells, (Nvp + 255) / 256);
     if (f_is_double || !c->mixed)
-        k_maxwell<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp, seed,
-                                                    (double*)fout);
+        k_maxwell<double><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, c->xi_f, Wp, c->cfg.R, amp,
+                                                         seed, (double*)fout);
     else
-        k_maxwell<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp, seed,
-                                                   (float*)fout);
+        k_maxwell<float><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, c->xi_f, Wp, c->cfg.R, amp,
+                                                        seed, (float*)fout);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -186,34 +262,38 @@ __global__ void __launch_bounds__(NT) k_cell_moments(int Nv, int Nvp, const T* _
                                                      const double* __restrict__ Wref, double* Wc, double* q)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
-    constexpr int CH = (sizeof(T) == 4) ? 8 : (1 << 20);
-    __shared__ double sred[(NT / 32) * NM];
+    constexpr int V = 16 / sizeof(T);
+    __shared__ double sw[(NT / 32) * NM];
     __shared__ double mom[NM];
     const int i = blockIdx.x;
-    double V[3] = {0, 0, 0};
+    double Vr[3] = {0, 0, 0};
     if (Wref && Wref[(size_t)i * NW] > 0.0) {
-        for (int d = 0; d < D; ++d) V[d] = (double)(T)(Wref[(size_t)i * NW + 1 + d] / Wref[(size_t)i * NW]);
+        for (int d = 0; d < D; ++d) Vr[d] = (double)(T)(Wref[(size_t)i * NW + 1 + d] / Wref[(size_t)i * NW]);
     }
     T Vt[D];
-    for (int d = 0; d < D; ++d) Vt[d] = (T)V[d];
+    for (int d = 0; d < D; ++d) Vt[d] = (T)Vr[d];
     const T* fi = f + (size_t)i * NA * Nvp;
-    double acc[NM];
-    for (int m = 0; m < NM; ++m) acc[m] = 0.0;
-    for (int k0 = threadIdx.x; k0 < Nv; k0 += NT * CH) {
-        T part[NM];
-        for (int m = 0; m < NM; ++m) part[m] = T(0);
-        for (int c = 0, k = k0; c < CH && k < Nv; ++c, k += NT) {
+    T acc[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc[m] = T(0);
+    for (int k0 = threadIdx.x * V; k0 < Nv; k0 += NT * V) {
+        T x[V * D], wv[V], f0[V], f1[V];
+        vload<T, V * D>(xi + (size_t)k0 * D, x);
+        vload<T, V>(w + k0, wv);
+        vload<T, V>(fi + k0, f0);
+        if (NA == 2) vload<T, V>(fi + Nvp + k0, f1);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
             T xs[D];
-            for (int d = 0; d < D; ++d) xs[d] = xi[(size_t)k * D + d] - Vt[d];
-            const T wk = w[k];
-            raw_acc<D>(part, xs, wk * fi[k], NA == 2 ? wk * fi[Nvp + k] : T(0));
+#pragma unroll
+            for (int d = 0; d < D; ++d) xs[d] = x[v * D + d] - Vt[d];
+            raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
         }
-        for (int m = 0; m < NM; ++m) acc[m] += (double)part[m];
     }
-    block_sum<NM, NT>(acc, sred, mom);
+    block_sum_t<NM, NT>(acc, sw, mom);
     if (threadIdx.x == 0) {
         double W[5], qq[3];
-        moments_from_raw<D>(mom, V, W, qq, nullptr, nullptr);
+        moments_from_raw<D>(mom, Vr, W, q ? qq : nullptr, nullptr, nullptr);
         if (Wc)
             for (int m = 0; m < NW; ++m) Wc[(size_t)i * NW + m] = W[m];
         if (q)
@@ -247,20 +327,28 @@ cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int 
 
 // ------------------------------------------------------------------ criterion
 // Per-cell inputs of the criterion, in the fixed order of the definition:
-// rho, U_d = m_d / rho, e_int = rho E - 0.5 (sum m_d m_d) / rho.
-__global__ void k_crit_cells(int D, int Ncells, const double* __restrict__ Wc, double* cp)
+// rho, U_d = m_d / rho, e_int = rho E - 0.5 (sum m_d m_d) / rho.  The FP32
+// screening form holds 1/rho, U_d, 0.5/e_int rounded to FP32.
+__global__ void k_crit_cells(int D, int Ncells, const double* __restrict__ Wc, double* cp, float* cp32)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Ncells) return;
     const double* W = Wc + (size_t)i * (D + 2);
     const double rho = W[0];
     double mm = 0.0;
+    float* c32 = cp32 + (size_t)i * 8;
+    for (int d = 0; d < 3; ++d) c32[1 + d] = 0.0f;
     for (int d = 0; d < D; ++d) {
-        cp[(size_t)i * 5 + 1 + d] = __ddiv_rn(W[1 + d], rho);
+        const double U = __ddiv_rn(W[1 + d], rho);
+        cp[(size_t)i * 5 + 1 + d] = U;
+        c32[1 + d] = (float)U;
         mm = __dadd_rn(mm, __dmul_rn(W[1 + d], W[1 + d]));
     }
+    const double e = __dsub_rn(W[D + 1], __ddiv_rn(__dmul_rn(0.5, mm), rho));
     cp[(size_t)i * 5 + 0] = rho;
-    cp[(size_t)i * 5 + 4] = __dsub_rn(W[D + 1], __ddiv_rn(__dmul_rn(0.5, mm), rho));
+    cp[(size_t)i * 5 + 4] = e;
+    c32[0] = 1.0f / (float)rho;
+    c32[4] = 0.5f / (float)e;
 }
 
 __global__ void k_fill_key(unsigned long long* k, int n, unsigned long long v)
@@ -269,11 +357,58 @@ __global__ void k_fill_key(unsigned long long* k, int n, unsigned long long v)
     if (i < n) k[i] = v;
 }
 
-// M_k = max over cells of max(M1, M2): M1 = (w G) / rho,
-// M2 = ((0.5 (w G)) c^2) / e_int, c^2 summed left to right (Sec. 3.4, R9).
+__global__ void k_fill_u32(unsigned* k, int n, unsigned v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) k[i] = v;
+}
+
+// ordered 32-bit key of a float (monotone for all non-NaN values)
+__device__ __forceinline__ unsigned fkey(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned k) { return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k); }
+
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+__device__ __forceinline__ bool same_bits(double a, double b)
+{
+    return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+// Pass 1: per node, the largest lower bound max_i (m32 - B) over the cells.
+template <typename T>
+__global__ void k_crit_screen(int D, int NA, int Nv, int Nvp, int ncells, int cells_per_block,
+                              const T* __restrict__ f, const float* __restrict__ xi, const float* __restrict__ w,
+                              const float* __restrict__ cp32, const int* __restrict__ cells, unsigned* Mlo)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nv) return;
+    const int j0 = blockIdx.y * cells_per_block;
+    const int j1 = min(ncells, j0 + cells_per_block);
+    float x[3];
+    for (int d = 0; d < D; ++d) x[d] = xi[(size_t)k * D + d];
+    const float wk = w[k];
+    float lo = -INFINITY;
+    for (int j = j0; j < j1; ++j) {
+        const int i = cells ? cells[j] : j;
+        float m, B;
+        crit32(D, (float)f[(size_t)i * NA * Nvp + k], wk, x, cp32 + (size_t)i * 8, m, B);
+        lo = fmaxf(lo, m - B);
+    }
+    if (lo > -INFINITY) atomicMax(Mlo + k, fkey(lo));
+}
+
+// Pass 2: M_k = max over cells of max(M1, M2): M1 = (w G) / rho,
+// M2 = ((0.5 (w G)) c^2) / e_int, c^2 summed left to right (Sec. 3.4, R9),
+// in FP64 at the (cell, node) pairs whose screening interval reaches the
+// node's lower bound: the pair of the exact maximum is always among them.
 template <typename T>
 __global__ void k_criterion(int D, int NA, int Nv, int Nvp, int ncells, int cells_per_block, const T* __restrict__ f,
                             const double* __restrict__ xi, const double* __restrict__ w, const double* __restrict__ cp,
+                            const float* __restrict__ xi32, const float* __restrict__ w32,
+                            const float* __restrict__ cp32, const unsigned* __restrict__ Mlo,
                             const int* __restrict__ cells, unsigned long long* Mkey)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,13 +416,37 @@ __global__ void k_criterion(int D, int NA, int Nv, int Nvp, int ncells, int cell
     const int j0 = blockIdx.y * cells_per_block;
     const int j1 = min(ncells, j0 + cells_per_block);
     double x[3];
-    for (int d = 0; d < D; ++d) x[d] = xi[(size_t)k * D + d];
+    float xf[3];
+    for (int d = 0; d < D; ++d) {
+        x[d] = xi[(size_t)k * D + d];
+        xf[d] = xi32[(size_t)k * D + d];
+    }
     const double wk = w[k];
+    const float wkf = w32[k];
+    const float lo = fkey_inv(Mlo[k]);
     double best = -INFINITY;
+    // a candidate whose inputs (f value and per-cell row) equal, bit for bit,
+    // those of the last one evaluated has the same value: skip it (uniform
+    // regions make many cells identical)
+    int pi = -1;
+    T Gp = T(0);
     for (int j = j0; j < j1; ++j) {
         const int i = cells ? cells[j] : j;
+        const T Gt = f[(size_t)i * NA * Nvp + k];
+        float m32, B;
+        crit32(D, (float)Gt, wkf, xf, cp32 + (size_t)i * 8, m32, B);
+        if (m32 + B < lo) continue;
         const double* p = cp + (size_t)i * 5;
-        const double G = (double)f[(size_t)i * NA * Nvp + k];
+        if (pi >= 0 && same_bits(Gt, Gp)) {
+            const double* q = cp + (size_t)pi * 5;
+            bool same = true;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) same = same && __double_as_longlong(p[c]) == __double_as_longlong(q[c]);
+            if (same) continue;
+        }
+        pi = i;
+        Gp = Gt;
+        const double G = (double)Gt;
         const double wg = __dmul_rn(wk, G);
         const double m1 = __ddiv_rn(wg, p[0]);
         double c2 = 0.0;
@@ -312,22 +471,31 @@ cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Nce
                              const int* cells, int ncells_list)
 {
     double* cp = c->crit_cp;
-    k_crit_cells<<<(Ncells + 255) / 256, 256, 0, c->stream>>>(c->D, Ncells, Wc, cp);
+    k_crit_cells<<<(Ncells + 255) / 256, 256, 0, c->stream>>>(c->D, Ncells, Wc, cp, c->crit_cp32);
     const unsigned long long ninf = dkey(-INFINITY);
     k_fill_key<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->Nv, ninf);
+    k_fill_u32<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mlo, c->Nv, 0x007fffffu);   // key of -inf
     const int n = cells ? ncells_list : Ncells;
     const int cpb = 64;
     dim3 g((c->Nv + 255) / 256, (n + cpb - 1) / cpb);
+    const bool dbl = f_is_double || !c->mixed;
     if (n > 0) {
-        if (f_is_double || !c->mixed)
+        if (dbl) {
+            k_crit_screen<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const double*)f,
+                                                            c->xi_f, c->w_f, c->crit_cp32, cells, c->Mlo);
             k_criterion<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const double*)f, c->xi_d,
-                                                          c->w_d, cp, cells, c->Mkey);
-        else
+                                                          c->w_d, cp, c->xi_f, c->w_f, c->crit_cp32, c->Mlo, cells,
+                                                          c->Mkey);
+        } else {
+            k_crit_screen<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const float*)f,
+                                                           c->xi_f, c->w_f, c->crit_cp32, cells, c->Mlo);
             k_criterion<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const float*)f, c->xi_d,
-                                                         c->w_d, cp, cells, c->Mkey);
+                                                         c->w_d, cp, c->xi_f, c->w_f, c->crit_cp32, c->Mlo, cells,
+                                                         c->Mkey);
+        }
     }
     k_decode_M<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->M, c->Nv);
-    c->launches += (n > 0) ? 4 : 3;
+    c->launches += (n > 0) ? 6 : 4;
     return cudaGetLastError();
 }
 
@@ -505,8 +673,8 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
                                                 int iters, unsigned long long* gap_key)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
-    constexpr int CH = (sizeof(T) == 4) ? 8 : (1 << 20);
-    __shared__ double sred[(NT / 32) * NM];
+    constexpr int V = 16 / sizeof(T);
+    __shared__ double sw[(NT / 32) * NM];
     __shared__ double mom[NM];
     __shared__ EqPar<T> ea, eb;
     const int i = blockIdx.x;
@@ -514,29 +682,35 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
     const double* Wi = Wt + (size_t)i * NW;
     double rho, U[3], RT;
     prim<D>(Wi, rho, U, RT);
-    double V[3] = {0, 0, 0};
-    for (int d = 0; d < D; ++d) V[d] = (double)(T)U[d];
+    double Vr[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) Vr[d] = (double)(T)U[d];
     T Vt[D];
-    for (int d = 0; d < D; ++d) Vt[d] = (T)V[d];
+    for (int d = 0; d < D; ++d) Vt[d] = (T)Vr[d];
+    if (threadIdx.x == 0) ea = make_eq<D, T>(rho, U, RT, nullptr, 0.0);
     for (int it = 0; it <= iters; ++it) {
-        double acc[NM];
-        for (int m = 0; m < NM; ++m) acc[m] = 0.0;
-        for (int k0 = threadIdx.x; k0 < Nv; k0 += NT * CH) {
-            T part[NM];
-            for (int m = 0; m < NM; ++m) part[m] = T(0);
-            for (int c = 0, k = k0; c < CH && k < Nv; ++c, k += NT) {
+        // moments of the current f' (nodes per thread as in the update below)
+        T acc[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[m] = T(0);
+        for (int k0 = threadIdx.x * V; k0 < Nv; k0 += NT * V) {
+            T x[V * D], wv[V], f0[V], f1[V];
+            vload<T, V * D>(xi + (size_t)k0 * D, x);
+            vload<T, V>(w + k0, wv);
+            vload<T, V>(fi + k0, f0);
+            if (NA == 2) vload<T, V>(fi + Nvp + k0, f1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
                 T xs[D];
-                for (int d = 0; d < D; ++d) xs[d] = xi[(size_t)k * D + d] - Vt[d];
-                const T wk = w[k];
-                raw_acc<D>(part, xs, wk * fi[k], NA == 2 ? wk * fi[Nvp + k] : T(0));
+#pragma unroll
+                for (int d = 0; d < D; ++d) xs[d] = x[v * D + d] - Vt[d];
+                raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
             }
-            for (int m = 0; m < NM; ++m) acc[m] += (double)part[m];
         }
-        block_sum<NM, NT>(acc, sred, mom);
+        block_sum_t<NM, NT>(acc, sw, mom);
         if (it == iters) {
             if (threadIdx.x == 0) {
                 double Wp[5];
-                moments_from_raw<D>(mom, V, Wp, nullptr, nullptr, nullptr);
+                moments_from_raw<D>(mom, Vr, Wp, nullptr, nullptr, nullptr);
                 double mref = 0.0;
                 for (int d = 0; d < D; ++d) mref += Wi[1 + d] * Wi[1 + d];
                 mref = sqrt(mref) + rho * sqrt(2.0 * RT);
@@ -550,23 +724,29 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
         }
         if (threadIdx.x == 0) {
             double Wp[5], rp, Up[3], RTp;
-            moments_from_raw<D>(mom, V, Wp, nullptr, nullptr, nullptr);
+            moments_from_raw<D>(mom, Vr, Wp, nullptr, nullptr, nullptr);
             prim<D>(Wp, rp, Up, RTp);
-            ea = make_eq<D, T>(rho, U, RT, nullptr, 0.0);
             eb = make_eq<D, T>(rp, Up, RTp, nullptr, 0.0);
         }
         __syncthreads();
-        const EqPar<T> A = ea, B = eb;
-        for (int k = threadIdx.x; k < Nv; k += NT) {
-            T x[D];
-            for (int d = 0; d < D; ++d) x[d] = xi[(size_t)k * D + d];
-            T ga, gah, gb, gbh;
-            eq_eval<D>(A, x, ga, gah);
-            eq_eval<D>(B, x, gb, gbh);
-            fi[k] += ga - gb;
-            if (NA == 2) fi[Nvp + k] += gah - gbh;
+        // f' <- f' + g(W) - g(W')  (Sec. 3.3)
+        for (int k0 = threadIdx.x * V; k0 < Nv; k0 += NT * V) {
+            T x[V * D], f0[V], f1[V];
+            vload<T, V * D>(xi + (size_t)k0 * D, x);
+            vload<T, V>(fi + k0, f0);
+            if (NA == 2) vload<T, V>(fi + Nvp + k0, f1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                T ga, gah, gb, gbh;
+                eq_eval<D>(ea, x + v * D, ga, gah);
+                eq_eval<D>(eb, x + v * D, gb, gbh);
+                const bool real = k0 + v < Nv;
+                f0[v] = real ? f0[v] + (ga - gb) : f0[v];
+                if (NA == 2) f1[v] = real ? f1[v] + (gah - gbh) : f1[v];
+            }
+            vstore<T, V>(fi + k0, f0);
+            if (NA == 2) vstore<T, V>(fi + Nvp + k0, f1);
         }
-        __syncthreads();
     }
 }
 
@@ -578,17 +758,17 @@ cudaError_t launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters
     unsigned long long* gk = (unsigned long long*)c->gap_d;
     if (c->D == 2) {
         if (c->mixed)
-            k_correct<2, float, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_f, c->w_f,
+            k_correct<2, float, 128><<<c->Nc, 128, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_f, c->w_f,
                                                                          Wtarget, c->cfg.R, iters, gk);
         else
-            k_correct<2, double, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d,
+            k_correct<2, double, 128><<<c->Nc, 128, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d,
                                                                           c->w_d, Wtarget, c->cfg.R, iters, gk);
     } else {
         if (c->mixed)
-            k_correct<3, float, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_f, c->w_f,
+            k_correct<3, float, 128><<<c->Nc, 128, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_f, c->w_f,
                                                                          Wtarget, c->cfg.R, iters, gk);
         else
-            k_correct<3, double, AVS_NT><<<c->Nc, AVS_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d,
+            k_correct<3, double, 128><<<c->Nc, 128, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d,
                                                                           c->w_d, Wtarget, c->cfg.R, iters, gk);
     }
     c->launches += 1;

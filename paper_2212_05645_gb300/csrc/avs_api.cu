@@ -54,8 +54,8 @@ void free_all(avs_ctx* c)
                     c->slot, c->nslot, c->nbr, c->cg_d, c->r_d, c->eps2_d, c->cg_f, c->r_f, c->eps2_f,
                     c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
                     c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
-                    c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->stage, c->dev_err,
-                    c->dt_key, c->gap_d, c->grad, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
+                    c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mthr, c->stage, c->dev_err,
+                    c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->cpar, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
                     c->mlp_X, c->mlp_Y, c->mlp_logits, c->mlp_list, c->mlp_count, c->M_alt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -268,6 +268,8 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
             ns[R]++;
         }
     }
+    c->max_ns = 0;
+    for (int i = 0; i < Nc; ++i) c->max_ns = std::max(c->max_ns, (int)ns[i]);
     std::vector<double> cg((size_t)Nc * AVS_MAXS * D, 0.0), r((size_t)Nc * AVS_MAXS * D, 0.0), eps2(Nc);
     for (int i = 0; i < Nc; ++i) {
         double M[9] = {0}, dv[AVS_MAXS][3], n2[AVS_MAXS];
@@ -330,7 +332,9 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
         dalloc(&c->rR_d, nfd) || dalloc(&c->An_f, nfd) || dalloc(&c->rL_f, nfd) || dalloc(&c->rR_f, nfd) ||
         dalloc(&c->vol, Nc) || dalloc(&c->bc, (size_t)std::max(1, c->nbc) * 6) || dalloc(&c->slot, ncs) ||
         dalloc(&c->nslot, Nc) || dalloc(&c->nbr, ncs) || dalloc(&c->cg_d, ncsd) || dalloc(&c->r_d, ncsd) ||
-        dalloc(&c->eps2_d, Nc) || dalloc(&c->cg_f, ncsd) || dalloc(&c->r_f, ncsd) || dalloc(&c->eps2_f, Nc))
+        dalloc(&c->eps2_d, Nc) || dalloc(&c->cg_f, ncsd) || dalloc(&c->r_f, ncsd) || dalloc(&c->eps2_f, Nc) ||
+        dalloc(&c->AFf, (size_t)Nf * (D + 2)) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * avs::NMom<3>::v) ||
+        dalloc((unsigned char**)&c->cpar, (size_t)Nc * AVS_CELLPAR_BYTES))
         return fail(c, AVS_ENOMEM, "mesh arrays");
     cudaStream_t s = c->stream;
     CK(up(c->faceL, std::vector<int>(m->faceL, m->faceL + Nf), s));
@@ -352,6 +356,13 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
     CK(up(c->cg_f, tof(cg.data(), ncsd), s));
     CK(up(c->r_f, tof(r.data(), ncsd), s));
     CK(up(c->eps2_f, tof(eps2.data(), Nc), s));
+    // faces in the order of their lower cell index, so that the face blocks in
+    // flight together read the f and gradient rows of nearby cells (L2 reuse)
+    std::vector<int> order(Nf);
+    for (int f = 0; f < Nf; ++f) order[f] = f;
+    auto low = [&](int f) { const int R = m->faceR[f]; return R >= 0 ? std::min(m->faceL[f], R) : m->faceL[f]; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return low(a) < low(b); });
+    CK(up(c->forder, order, s));
     CK(cudaStreamSynchronize(s));    // host vectors go out of scope
     return AVS_OK;
 }
@@ -456,7 +467,8 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     AL(c->xi_f, (size_t)capp * c->D); AL(c->w_f, capp);
     AL(c->M, capp); AL(c->Mkey, capp);
     AL(c->pseudo_f, 2 * (size_t)c->NA * capp); AL(c->pseudo_W, 4 * NW);
-    AL(c->crit_cp, 5 * (size_t)std::max(c->Nc, 2));
+    AL(c->crit_cp, 5 * (size_t)std::max(c->Nc, 2)); AL(c->crit_cp32, 8 * (size_t)std::max(c->Nc, 2));
+    AL(c->Mlo, capp); AL(c->Mthr, 4 * (size_t)capp);
     AL(c->W[0], (size_t)c->Nc * NW); AL(c->W[1], (size_t)c->Nc * NW);
     AL(c->Wf, (size_t)c->Nc * NW); AL(c->q, (size_t)c->Nc * c->D);
     AL(c->dev_err, 1); AL(c->dt_key, 1); AL(c->gap_d, 1);
@@ -508,6 +520,7 @@ int avs_num_cells(const avs_ctx* c) { return c ? c->Nc : 0; }
 avs_status avs_init_field(avs_ctx* c, const double* Wp, int is_device, double amp, uint64_t seed)
 {
     if (!c || !Wp) return AVS_EINVAL;
+    c->mom_valid = 0;                 // f or W change outside a step
     const size_t n = (size_t)c->Nc * (c->D + 2);
     const double* Wp_d = Wp;
     if (!is_device) {
@@ -553,12 +566,14 @@ avs_status ugks_step(avs_ctx* c, int nsteps, double cfl, double* dt_out)
 avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* stats)
 {
     if (!c) return AVS_EINVAL;
+    c->mom_valid = 0;                 // f or W change outside a step
     avs_adapt_opts o = {};
     if (opts) o = *opts;
     const int NW = c->D + 2;
     const int Nv_old = c->Nv, Nvp_old = c->Nvp;
-    // moments of f on the old mesh (Eq. 7): criterion input and correction target
-    CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr));
+    // moments of f on the old mesh (Eq. 7): criterion input and correction
+    // target; with the proposer also the heat flux of its features
+    CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, c->cfg.learned ? c->q : nullptr));
     if (o.W_override) {
         CK(cudaMemcpyAsync(c->Wf, o.W_override, sizeof(double) * c->Nc * NW,
                            o.W_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -570,7 +585,6 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
         const int every = std::max(1, c->cfg.learned_full_every);
         full = o.force_full || c->mlp_trained == 0 || (c->adapt_count % every) == 0;
         // features of the current state: moments and heat flux of f
-        CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, nullptr, c->q));
         CK(mlp_features(c, c->Wf, c->q, c->mlp_X));
         if (c->mlp_trained > 0) {
             // the proposer's check set and the criterion restricted to it
@@ -682,6 +696,7 @@ avs_status avs_f_moments(avs_ctx* c, double* Wc_out, int is_device)
 avs_status avs_set_W(avs_ctx* c, const double* Wc, int is_device)
 {
     if (!c || !Wc) return AVS_EINVAL;
+    c->mom_valid = 0;                 // f or W change outside a step
     CK(cudaMemcpyAsync(c->W[c->wcur], Wc, sizeof(double) * c->Nc * (c->D + 2),
                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (!is_device) CK(cudaStreamSynchronize(c->stream));
@@ -736,6 +751,7 @@ avs_status avs_get_f(avs_ctx* c, double* f, int is_device)
 avs_status avs_set_f(avs_ctx* c, const double* f, int is_device)
 {
     if (!c || !f) return AVS_EINVAL;
+    c->mom_valid = 0;                 // f or W change outside a step
     const size_t n = (size_t)c->Nc * c->NA * c->Nv;
     if (is_device) {
         CK(launch_from_double(c, f, c->f[c->cur], c->Nvp));

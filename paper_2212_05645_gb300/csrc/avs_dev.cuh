@@ -305,7 +305,7 @@ __device__ __forceinline__ void state_from_raw(const double* m, const double* V,
         S3[0] = (A)m[10]; S3[1] = (A)m[11]; S3[2] = (A)m[12];
     }
     rho = S0;
-    const A ir = A(1) / S0;
+    const A ir = fdiv(A(1), S0);
     A d[3], dd = A(0), trS2 = A(0), dS1 = A(0);
     for (int a = 0; a < D; ++a) {
         d[a] = S1[a] * ir;
@@ -314,7 +314,7 @@ __device__ __forceinline__ void state_from_raw(const double* m, const double* V,
         trS2 += S2[a][a];
         dS1 += d[a] * S1[a];
     }
-    RT = (A(0.5) * (trS2 + H0) - A(0.5) * S0 * dd) / (A(1.5) * S0);
+    RT = fdiv(A(0.5) * (trS2 + H0) - A(0.5) * S0 * dd, A(1.5) * S0);
     if (q) {
         for (int a = 0; a < D; ++a) {
             A S2d = A(0);
@@ -331,20 +331,80 @@ __device__ __forceinline__ EqPar<T> make_eq_a(A rho, const A* U, A RT, const A* 
 {
     EqPar<T> p;
     const A t = A(2.0 * AVS_PI) * RT;
-    p.pref = (T)(rho / (D == 2 ? t : t * sqrt(t)));
-    const A a = (A(1) - Pr) / (A(5) * rho * RT * RT);
+    p.pref = (T)fdiv(rho, D == 2 ? t : t * sqrt(t));
+    const A a = fdiv(A(1) - Pr, A(5) * rho * RT * RT);
     for (int d = 0; d < 3; ++d) {
         p.U[d] = d < D ? (T)U[d] : T(0);
         p.alpha[d] = (d < D && q) ? (T)(a * q[d]) : T(0);
     }
-    p.inv2RT = (T)(A(1) / (A(2) * RT));
-    p.invRT = (T)(A(1) / RT);
+    p.inv2RT = (T)fdiv(A(1), A(2) * RT);
+    p.invRT = (T)fdiv(A(1), RT);
     p.RTH = (T)(A(3 - D) * RT);
     return p;
 }
 
 __device__ __forceinline__ double powa(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float powa(float x, float y) { return exp2f(y * __log2f(x)); }
+
+// ---------------------------------------------------------------- vector access
+// N consecutive elements starting at a 16-byte aligned address, moved as
+// 16-byte vectors (N * sizeof(T) a multiple of 16).
+template <typename T, int N>
+__device__ __forceinline__ void vload(const T* __restrict__ p, T* o)
+{
+    static_assert((N * sizeof(T)) % 16 == 0, "whole 16-byte vectors");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int j = 0; j < N / 4; ++j) {
+            const float4 q = reinterpret_cast<const float4*>(p)[j];
+            o[4 * j] = q.x; o[4 * j + 1] = q.y; o[4 * j + 2] = q.z; o[4 * j + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) {
+            const double2 q = reinterpret_cast<const double2*>(p)[j];
+            o[2 * j] = q.x; o[2 * j + 1] = q.y;
+        }
+    }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void vstore(T* p, const T* o)
+{
+    static_assert((N * sizeof(T)) % 16 == 0, "whole 16-byte vectors");
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int j = 0; j < N / 4; ++j)
+            reinterpret_cast<float4*>(p)[j] = make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) reinterpret_cast<double2*>(p)[j] = make_double2(o[2 * j], o[2 * j + 1]);
+    }
+}
+
+// ---------------------------------------------------------------- criterion screening
+// FP32 screening value of the criterion at one (cell, node) and a bound on
+// its distance from the exact value.  Inputs and operations rounded to FP32:
+// |M1_32 - M1| <= 6 u |M1|, |M2_32 - M2| <= 24 u |wG 0.5/e| sum_d (|xi_d| + |U_d|)^2
+// (u = 2^-24) while the results stay normal; the bound takes 128 u of the sum
+// of both scales plus 2^-100, far above the absolute error of the few
+// roundings that can fall in the subnormal range (2^-149 each).
+__device__ __forceinline__ void crit32(int D, float G, float wk, const float* x, const float* c32, float& m, float& B)
+{
+    const float wg = wk * G;
+    const float m1 = wg * c32[0];
+    float c2 = 0.0f, a2 = 0.0f;
+    for (int d = 0; d < D; ++d) {
+        const float cc = x[d] - c32[1 + d];
+        const float aa = fabsf(x[d]) + fabsf(c32[1 + d]);
+        c2 += cc * cc;
+        a2 += aa * aa;
+    }
+    const float wh = wg * c32[4];
+    const float m2 = wh * c2;
+    m = m1 > m2 ? m1 : m2;
+    B = 0x1p-17f * (fabsf(m1) + fabsf(wh) * a2) + 0x1p-100f;
+}
 
 // ---------------------------------------------------------------- reductions
 // Deterministic block reduction of N doubles per thread: warp tree with

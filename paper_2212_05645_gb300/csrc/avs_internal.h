@@ -10,6 +10,7 @@
 #include "../../include/avs.h"
 
 #define AVS_NT 256            // threads per block of the per-cell kernels
+#define AVS_CELLPAR_BYTES 256 // bytes per cell of the collision parameters (CellPar)
 
 struct avs_ctx {
     avs_config cfg;
@@ -30,6 +31,7 @@ struct avs_ctx {
     double *bc = nullptr;                            // [nbc][6]
     int *slot = nullptr;                             // [Nc][MAXS] face*2 + (cell is R), -1 none
     unsigned char *nslot = nullptr;                  // [Nc]
+    int max_ns = 0;                                  // largest face count of a cell
     int *nbr = nullptr;                              // [Nc][MAXS]
     double *cg_d = nullptr, *r_d = nullptr, *eps2_d = nullptr;
     float *cg_f = nullptr, *r_f = nullptr, *eps2_f = nullptr;
@@ -58,6 +60,9 @@ struct avs_ctx {
     double *pseudo_f = nullptr;                      // step-0 pseudo cells [2][NA][cap]
     double *pseudo_W = nullptr;                      // [2][D+2]
     double *crit_cp = nullptr;                       // criterion per-cell inputs [max(Nc,2)][5]
+    float *crit_cp32 = nullptr;                      // their FP32 screening form [max(Nc,2)][8]
+    unsigned *Mlo = nullptr;                         // [cap] screening lower bounds of M (ordered keys)
+    float *Mthr = nullptr;                           // [cap][4] label thresholds per node
     double *stage = nullptr;                         // FP64 staging [Nc][NA][Nv] for get/set (lazy)
     size_t stage_elems = 0;
     int *dev_err = nullptr;                          // device error word (bit 1: numeric)
@@ -67,6 +72,13 @@ struct avs_ctx {
     unsigned long long launches = 0;                 // kernels launched by this context
     void *grad = nullptr;                            // limited gradients [Nc][NA][D][Nvp] of T
     size_t grad_bytes = 0;
+    void *flux = nullptr;                            // per-node face flux [Nf][NA][Nvp] of T
+    size_t flux_bytes = 0;
+    double *AFf = nullptr;                           // area-weighted face flux of W [Nf][D+2]
+    int *forder = nullptr;                           // face processing order (by lower cell index)
+    double *cmom = nullptr;                          // raw moments of f about U(W) per cell [Nc][NMom]
+    int mom_valid = 0;                               // cmom matches the current f and W
+    void *cpar = nullptr;                            // per-cell collision parameters (k_cell_state)
 
     // ---- learned proposer (MLP 8-64-64-4)
     float *mlp_P = nullptr;                          // FP32 master parameters

@@ -450,14 +450,48 @@ __global__ void k_features(int Nc, const double* __restrict__ Wc, const double* 
 // (m_ik >= C2 at level >= 1).
 template <typename T>
 __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f, const double* __restrict__ xi,
-                         const double* __restrict__ w, const double* __restrict__ cp, const double* __restrict__ M,
-                         const int* __restrict__ level, double s, double C1, double C2, int max_refine, float* Y)
+                         const double* __restrict__ w, const double* __restrict__ cp, const float* __restrict__ xi32,
+                         const float* __restrict__ w32, const float* __restrict__ cp32, const double* __restrict__ M,
+                         const float4* __restrict__ thr, const int* __restrict__ level, double s, double C1, double C2,
+                         int max_refine, float* Y)
 {
+    // Every test is first decided on the FP32 screening interval of m_ik
+    // (crit32); a test whose threshold lies within 2^-20 relative of the
+    // interval is decided in FP64 as in the definition.
+    constexpr float eps = 0x1p-20f;
     const int i = blockIdx.x;
     const double* p = cp + (size_t)i * 5;
+    const float* p32 = cp32 + (size_t)i * 8;
+    const float s32 = (float)s, C1f = (float)C1, C2f = (float)C2;
     int y0 = 0, y1 = 0, y2 = 0, y3 = 0;
     for (int k = threadIdx.x; k < Nv; k += blockDim.x) {
-        const double wg = __dmul_rn(w[k], (double)f[(size_t)i * NA * Nvp + k]);
+        const T Gt = f[(size_t)i * NA * Nvp + k];
+        float xf[3];
+        for (int d = 0; d < D; ++d) xf[d] = xi32[(size_t)k * D + d];
+        float m32, B;
+        crit32(D, (float)Gt, w32[k], xf, p32, m32, B);
+        const float lo = s32 * (m32 - B), hi = s32 * (m32 + B);
+        const float4 t = thr[k];               // act, M_k, 0.5 s M_k
+        const int lv = level[k];
+        const bool act = t.x != 0.0f;
+        bool amb = false;
+        if (lv < max_refine && !y0) {
+            if (lo > C1f * (1.0f + eps)) y0 = 1;
+            else if (!(hi < C1f * (1.0f - eps))) amb = true;
+        }
+        if (lv >= 1 && !y3) {
+            if (lo > C2f * (1.0f + eps)) y3 = 1;
+            else if (!(hi < C2f * (1.0f - eps))) amb = true;
+        }
+        if (act) {
+            if (!y1 && !(m32 + B < t.y - fabsf(t.y) * eps)) amb = true;
+            if (!y2) {
+                if (lo > t.z + fabsf(t.z) * eps) y2 = 1;
+                else if (!(hi < t.z - fabsf(t.z) * eps)) amb = true;
+            }
+        }
+        if (!amb) continue;
+        const double wg = __dmul_rn(w[k], (double)Gt);
         const double m1 = __ddiv_rn(wg, p[0]);
         double c2 = 0.0;
         for (int d = 0; d < D; ++d) {
@@ -468,11 +502,11 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
         const double mk = m1 > m2 ? m1 : m2;
         const double Mk = M[k];
         const double sm = __dmul_rn(s, mk), sM = __dmul_rn(s, Mk);
-        const bool act = sM >= C2;
-        y0 |= (sm > C1 && level[k] < max_refine);
-        y1 |= (act && mk == Mk);
-        y2 |= (act && sm >= 0.5 * sM);
-        y3 |= (sm >= C2 && level[k] >= 1);
+        const bool actd = sM >= C2;
+        y0 |= (sm > C1 && lv < max_refine);
+        y1 |= (actd && mk == Mk);
+        y2 |= (actd && sm >= 0.5 * sM);
+        y3 |= (sm >= C2 && lv >= 1);
     }
     y0 = __syncthreads_or(y0);
     y1 = __syncthreads_or(y1);
@@ -484,6 +518,15 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
         Y[(size_t)i * NO + 2] = (float)y2;
         Y[(size_t)i * NO + 3] = (float)y3;
     }
+}
+
+// per-node thresholds of the label tests: (s M_k >= C2, M_k, 0.5 s M_k) in FP32
+__global__ void k_label_thr(int Nv, const double* __restrict__ M, double s, double C2, float4* thr)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nv) return;
+    const double sM = __dmul_rn(s, M[k]);
+    thr[k] = make_float4(sM >= C2 ? 1.0f : 0.0f, (float)M[k], (float)(0.5 * sM), 0.0f);
 }
 
 // check set: cells whose dominant logit reaches the threshold.  The cell
@@ -582,15 +625,20 @@ cudaError_t mlp_features(avs_ctx* c, const double* Wc, const double* q, float* X
 
 cudaError_t mlp_labels(avs_ctx* c, const void* f, float* Y)
 {
+    // the criterion's per-cell inputs (crit_cp, crit_cp32) and M are those of
+    // the full criterion evaluated just before
+    float4* thr = (float4*)c->Mthr;
+    k_label_thr<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Nv, c->M, c->s_norm, c->cfg.C2, thr);
     if (c->mixed)
         k_labels<float><<<c->Nc, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, c->Nvp, (const float*)f, c->xi_d, c->w_d,
-                                                      c->crit_cp, c->M, c->level, c->s_norm, c->cfg.C1, c->cfg.C2,
-                                                      c->cfg.max_refine, Y);
+                                                      c->crit_cp, c->xi_f, c->w_f, c->crit_cp32, c->M, thr, c->level,
+                                                      c->s_norm, c->cfg.C1, c->cfg.C2, c->cfg.max_refine, Y);
     else
         k_labels<double><<<c->Nc, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, c->Nvp, (const double*)f, c->xi_d,
-                                                       c->w_d, c->crit_cp, c->M, c->level, c->s_norm, c->cfg.C1,
-                                                       c->cfg.C2, c->cfg.max_refine, Y);
-    c->launches += 1;
+                                                       c->w_d, c->crit_cp, c->xi_f, c->w_f, c->crit_cp32, c->M, thr,
+                                                       c->level, c->s_norm, c->cfg.C1, c->cfg.C2, c->cfg.max_refine,
+                                                       Y);
+    c->launches += 2;
     return cudaGetLastError();
 }
 

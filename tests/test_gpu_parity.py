@@ -45,6 +45,21 @@ def test_init_field_and_moments():
     assert rel_err(g.f_moments(), Wo) < 1e-13
 
 
+def test_init_field_mixed_within_fp32():
+    """Mixed form: the Maxwellian start is evaluated in FP32 (f is stored in
+    FP32); it stays within a few FP32 ulp of the FP64 oracle."""
+    avs = need_gpu()
+    w = wl.sweep_box((6, 5), base=(12, 12), max_refine=1, precision="mixed")
+    r = O.Run(w)
+    r.init_field(amp=1e-3, seed=99)
+    g = avs.AVS(w, precision="mixed")
+    g.init_field(amp=1e-3, seed=99)
+    assert rel_err(g.get_f(), r.f) < 1e-6
+    e = field_err(g.moments()[0], O.moments(2, r.xi, r.w, r.f)[0], 2)
+    assert max(e.values()) < 1e-6, e
+    g.close()
+
+
 @pytest.mark.parametrize("limiter", [0, 1, 2])
 def test_step_fp64_periodic(limiter):
     avs = need_gpu()
@@ -99,6 +114,68 @@ def test_step_fp64_3d_sphere_shell():
     g.step(2, dt=dt)
     assert rel_err(g.get_f(), r.f) < 1e-12
     assert rel_err(g.moments()[0], r.Wc) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_carried_moments_equal_recomputed_bitwise(precision):
+    """The cell kernel sums the raw moments of f^{n+1} while writing it and the
+    next step takes them instead of re-reading f.  Forcing the re-read (set_W
+    with the same W drops the carried moments) gives the same bits."""
+    avs = need_gpu()
+    w = small_cylinder(precision=precision)
+    a = avs.AVS(w, precision=precision)
+    b = avs.AVS(w, precision=precision)
+    for g in (a, b):
+        g.init_field(amp=1e-3, seed=5)
+    dt = a.dt()
+    a.step(3, dt=dt)
+    for _ in range(3):
+        b.step(1, dt=dt)
+        b.set_W(b.moments()[0])
+    assert np.array_equal(a.get_f(), b.get_f())
+    assert np.array_equal(a.moments()[0], b.moments()[0])
+    a.close(); b.close()
+
+
+def test_state_replaced_between_steps_fp64():
+    """f and W replaced between two steps (set_f, set_W): the second step
+    starts from the new state, as in the oracle."""
+    avs = need_gpu()
+    w = small_cylinder()
+    r, g = pair(w, avs)
+    dt = r.dt()
+    r.step(dt)
+    g.step(1, dt=dt)
+    k = np.arange(r.f.shape[2])
+    r.f = np.ascontiguousarray(r.f * (1.0 + 1e-3 * np.cos(0.37 * k))[None, None, :])
+    r.Wc = np.ascontiguousarray(r.Wc * 1.001)
+    g.set_f(r.f)
+    g.set_W(r.Wc)
+    r.step(dt)
+    g.step(1, dt=dt)
+    assert rel_err(g.get_f(), r.f) < 1e-12
+    assert rel_err(g.moments()[0], r.Wc) < 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("amp", [0.0, 1e-2])
+def test_criterion_and_dt_bitexact_mixed_with_ties(amp):
+    """Mixed form: the criterion (FP32 screening, FP64 at the pairs that can
+    hold the maximum) equals the oracle's plain FP64 maximum bit for bit on
+    the same FP32 f values, also when many cells are identical (amp 0: every
+    cell of a uniform region ties at every node); the time-step bound too."""
+    avs = need_gpu()
+    w = wl.sweep_box((9, 7), base=(12, 12), max_refine=2, C1=3.0, precision="mixed")
+    g = avs.AVS(w, precision="mixed")
+    g.init_field(amp=amp, seed=9)
+    r = O.Run(w)
+    t = g.tree()
+    assert np.array_equal(t["level"], r.level) and np.array_equal(t["key"], r.key)
+    f = g.get_f()                                  # the FP32 values, exactly, as float64
+    Wf, _ = O.moments(2, r.xi, r.w, f)
+    assert np.array_equal(g.criterion(Wf), O.criterion(2, r.xi, r.w, f, Wf))
+    assert g.dt() == r.dt()
+    g.close()
 
 
 def test_criterion_bitexact_given_W():
