@@ -255,21 +255,30 @@ cudaError_t launch_maxwell(avs_ctx* c, const double* Wp, int Ncells, double amp,
 
 // ------------------------------------------------------------------ moments
 // Conserved moments (Eq. 7) and heat flux (Eq. 8) of every cell, summed about
-// the cell's carried velocity (when given) to limit cancellation.
+// the cell's carried velocity (when given) to limit cancellation: raw moments
+// by one block per cell (FP32 partials, FP64 across warps), then the FP64
+// conversion by one thread per cell.
+template <typename T>
+__device__ __forceinline__ void ref_velocity(int D, const double* Wref, int i, double* Vr)
+{
+    const int NW = D + 2;
+    for (int d = 0; d < 3; ++d) Vr[d] = 0.0;
+    if (Wref && Wref[(size_t)i * NW] > 0.0)
+        for (int d = 0; d < D; ++d) Vr[d] = (double)(T)(Wref[(size_t)i * NW + 1 + d] / Wref[(size_t)i * NW]);
+}
+
 template <int D, typename T, int NT>
 __global__ void __launch_bounds__(NT) k_cell_moments(int Nv, int Nvp, const T* __restrict__ f,
                                                      const T* __restrict__ xi, const T* __restrict__ w,
-                                                     const double* __restrict__ Wref, double* Wc, double* q)
+                                                     const double* __restrict__ Wref, double* rmom)
 {
-    constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
+    constexpr int NA = NArr<D>::v, NM = NMom<D>::v;
     constexpr int V = 16 / sizeof(T);
     __shared__ double sw[(NT / 32) * NM];
     __shared__ double mom[NM];
     const int i = blockIdx.x;
-    double Vr[3] = {0, 0, 0};
-    if (Wref && Wref[(size_t)i * NW] > 0.0) {
-        for (int d = 0; d < D; ++d) Vr[d] = (double)(T)(Wref[(size_t)i * NW + 1 + d] / Wref[(size_t)i * NW]);
-    }
+    double Vr[3];
+    ref_velocity<T>(D, Wref, i, Vr);
     T Vt[D];
     for (int d = 0; d < D; ++d) Vt[d] = (T)Vr[d];
     const T* fi = f + (size_t)i * NA * Nvp;
@@ -291,14 +300,34 @@ __global__ void __launch_bounds__(NT) k_cell_moments(int Nv, int Nvp, const T* _
         }
     }
     block_sum_t<NM, NT>(acc, sw, mom);
-    if (threadIdx.x == 0) {
-        double W[5], qq[3];
-        moments_from_raw<D>(mom, Vr, W, q ? qq : nullptr, nullptr, nullptr);
-        if (Wc)
-            for (int m = 0; m < NW; ++m) Wc[(size_t)i * NW + m] = W[m];
-        if (q)
-            for (int d = 0; d < D; ++d) q[(size_t)i * D + d] = qq[d];
-    }
+    if (threadIdx.x < NM) rmom[(size_t)i * NM + threadIdx.x] = mom[threadIdx.x];
+}
+
+template <int D, typename T>
+__global__ void k_moments_finish(int Ncells, const double* __restrict__ rmom, const double* __restrict__ Wref,
+                                 double* Wc, double* q)
+{
+    constexpr int NM = NMom<D>::v, NW = D + 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Ncells) return;
+    double Vr[3], m[NM], W[5], qq[3];
+    ref_velocity<T>(D, Wref, i, Vr);
+    for (int k = 0; k < NM; ++k) m[k] = rmom[(size_t)i * NM + k];
+    moments_from_raw<D>(m, Vr, W, q ? qq : nullptr, nullptr, nullptr);
+    if (Wc)
+        for (int k = 0; k < NW; ++k) Wc[(size_t)i * NW + k] = W[k];
+    if (q)
+        for (int d = 0; d < D; ++d) q[(size_t)i * D + d] = qq[d];
+}
+
+template <int D, typename T>
+static cudaError_t cell_moments_t(avs_ctx* c, const T* f, const T* xi, const T* w, int Ncells, int Nvp,
+                                  const double* Wref, double* Wc, double* q)
+{
+    k_cell_moments<D, T, 128><<<Ncells, 128, 0, c->stream>>>(c->Nv, Nvp, f, xi, w, Wref, c->rmom);
+    k_moments_finish<D, T><<<(Ncells + 127) / 128, 128, 0, c->stream>>>(Ncells, c->rmom, Wref, Wc, q);
+    c->launches += 2;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wc_out,
@@ -306,23 +335,11 @@ cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int 
 {
     const bool dbl = f_is_double || !c->mixed;
     const double* Wref = (Ncells == c->Nc) ? c->W[c->wcur] : nullptr;
-    if (c->D == 2) {
-        if (dbl)
-            k_cell_moments<2, double, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
-                c->Nv, Nvp, (const double*)f, c->xi_d, c->w_d, Wref, Wc_out, q_out);
-        else
-            k_cell_moments<2, float, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
-                c->Nv, Nvp, (const float*)f, c->xi_f, c->w_f, Wref, Wc_out, q_out);
-    } else {
-        if (dbl)
-            k_cell_moments<3, double, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
-                c->Nv, Nvp, (const double*)f, c->xi_d, c->w_d, Wref, Wc_out, q_out);
-        else
-            k_cell_moments<3, float, AVS_NT><<<Ncells, AVS_NT, 0, c->stream>>>(
-                c->Nv, Nvp, (const float*)f, c->xi_f, c->w_f, Wref, Wc_out, q_out);
-    }
-    c->launches += 1;
-    return cudaGetLastError();
+    if (c->D == 2)
+        return dbl ? cell_moments_t<2, double>(c, (const double*)f, c->xi_d, c->w_d, Ncells, Nvp, Wref, Wc_out, q_out)
+                   : cell_moments_t<2, float>(c, (const float*)f, c->xi_f, c->w_f, Ncells, Nvp, Wref, Wc_out, q_out);
+    return dbl ? cell_moments_t<3, double>(c, (const double*)f, c->xi_d, c->w_d, Ncells, Nvp, Wref, Wc_out, q_out)
+               : cell_moments_t<3, float>(c, (const float*)f, c->xi_f, c->w_f, Ncells, Nvp, Wref, Wc_out, q_out);
 }
 
 // ------------------------------------------------------------------ criterion
@@ -381,7 +398,8 @@ __device__ __forceinline__ bool same_bits(double a, double b)
 template <typename T>
 __global__ void k_crit_screen(int D, int NA, int Nv, int Nvp, int ncells, int cells_per_block,
                               const T* __restrict__ f, const float* __restrict__ xi, const float* __restrict__ w,
-                              const float* __restrict__ cp32, const int* __restrict__ cells, unsigned* Mlo)
+                              const float* __restrict__ cp32, const int* __restrict__ cells, unsigned* Mlo,
+                              unsigned* Mhi)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nv) return;
@@ -390,29 +408,44 @@ __global__ void k_crit_screen(int D, int NA, int Nv, int Nvp, int ncells, int ce
     float x[3];
     for (int d = 0; d < D; ++d) x[d] = xi[(size_t)k * D + d];
     const float wk = w[k];
-    float lo = -INFINITY;
+    float lo = -INFINITY, hi = -INFINITY;
     for (int j = j0; j < j1; ++j) {
         const int i = cells ? cells[j] : j;
         float m, B;
-        crit32(D, (float)f[(size_t)i * NA * Nvp + k], wk, x, cp32 + (size_t)i * 8, m, B);
+        crit32(D, crit_scaled(f[(size_t)i * NA * Nvp + k]), wk, x, cp32 + (size_t)i * 8, m, B);
         lo = fmaxf(lo, m - B);
+        hi = fmaxf(hi, m + B);
+        if (m != m) hi = INFINITY;         // undecidable pair: force the exact evaluation
     }
     if (lo > -INFINITY) atomicMax(Mlo + k, fkey(lo));
+    if (hi > -INFINITY) atomicMax(Mhi + k, fkey(hi));
 }
 
 // Pass 2: M_k = max over cells of max(M1, M2): M1 = (w G) / rho,
 // M2 = ((0.5 (w G)) c^2) / e_int, c^2 summed left to right (Sec. 3.4, R9),
 // in FP64 at the (cell, node) pairs whose screening interval reaches the
 // node's lower bound: the pair of the exact maximum is always among them.
+// With `decide`, only the split and merge tests of the marks are needed: a
+// node whose interval [lo, hi] of s M_k lies clear of C1 and C2 (by 2^-20
+// relative) is left to k_decode_M, which stores lo as its value; the tests
+// give the same answers for it as for the exact M_k.
 template <typename T>
 __global__ void k_criterion(int D, int NA, int Nv, int Nvp, int ncells, int cells_per_block, const T* __restrict__ f,
                             const double* __restrict__ xi, const double* __restrict__ w, const double* __restrict__ cp,
                             const float* __restrict__ xi32, const float* __restrict__ w32,
                             const float* __restrict__ cp32, const unsigned* __restrict__ Mlo,
+                            const unsigned* __restrict__ Mhi, int decide, float s32, float C1s, float C2s,
                             const int* __restrict__ cells, unsigned long long* Mkey)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nv) return;
+    if (decide) {
+        constexpr float eps = 0x1p-20f;
+        const float slo = s32 * fkey_inv(Mlo[k]), shi = s32 * fkey_inv(Mhi[k]);
+        const bool c1 = slo > C1s * (1.0f + eps) || shi < C1s * (1.0f - eps);
+        const bool c2 = slo > C2s * (1.0f + eps) || shi < C2s * (1.0f - eps);
+        if (c1 && c2) return;
+    }
     const int j0 = blockIdx.y * cells_per_block;
     const int j1 = min(ncells, j0 + cells_per_block);
     double x[3];
@@ -434,8 +467,15 @@ __global__ void k_criterion(int D, int NA, int Nv, int Nvp, int ncells, int cell
         const int i = cells ? cells[j] : j;
         const T Gt = f[(size_t)i * NA * Nvp + k];
         float m32, B;
-        crit32(D, (float)Gt, wkf, xf, cp32 + (size_t)i * 8, m32, B);
+        const float* c32 = cp32 + (size_t)i * 8;
+        crit32(D, crit_scaled(Gt), wkf, xf, c32, m32, B);
         if (m32 + B < lo) continue;
+        if (Gt == T(0) && c32[0] > 0.0f && c32[0] < INFINITY && c32[4] > 0.0f && c32[4] < INFINITY) {
+            // G = +-0 with rho, e_int > 0: M1 = M2 = G exactly
+            const double z = (double)Gt;
+            best = z > best ? z : best;
+            continue;
+        }
         const double* p = cp + (size_t)i * 5;
         if (pi >= 0 && same_bits(Gt, Gp)) {
             const double* q = cp + (size_t)pi * 5;
@@ -461,41 +501,48 @@ __global__ void k_criterion(int D, int NA, int Nv, int Nvp, int ncells, int cell
     if (best > -INFINITY) atomicMax(Mkey + k, dkey(best));
 }
 
-__global__ void k_decode_M(const unsigned long long* __restrict__ Mkey, double* M, int n)
+// M_k from the exact maximum, or, for a node the decisions-only pass left
+// out, the lower end of its screening interval (unscaled)
+__global__ void k_decode_M(const unsigned long long* __restrict__ Mkey, const unsigned* __restrict__ Mlo, int decide,
+                           double* M, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) M[i] = dkey_inv(Mkey[i]);
+    if (i >= n) return;
+    const unsigned long long key = Mkey[i];
+    M[i] = (decide && key == dkey(-INFINITY)) ? (double)fkey_inv(Mlo[i]) * 0x1p-64 : dkey_inv(key);
 }
 
 cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, const double* Wc,
-                             const int* cells, int ncells_list)
+                             const int* cells, int ncells_list, int decide)
 {
     double* cp = c->crit_cp;
     k_crit_cells<<<(Ncells + 255) / 256, 256, 0, c->stream>>>(c->D, Ncells, Wc, cp, c->crit_cp32);
     const unsigned long long ninf = dkey(-INFINITY);
     k_fill_key<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->Nv, ninf);
     k_fill_u32<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mlo, c->Nv, 0x007fffffu);   // key of -inf
+    k_fill_u32<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mhi, c->Nv, 0x007fffffu);
     const int n = cells ? ncells_list : Ncells;
     const int cpb = 64;
     dim3 g((c->Nv + 255) / 256, (n + cpb - 1) / cpb);
     const bool dbl = f_is_double || !c->mixed;
+    const float s32 = (float)c->s_norm, C1s = (float)c->cfg.C1 * kCritScale, C2s = (float)c->cfg.C2 * kCritScale;
     if (n > 0) {
         if (dbl) {
             k_crit_screen<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const double*)f,
-                                                            c->xi_f, c->w_f, c->crit_cp32, cells, c->Mlo);
+                                                            c->xi_f, c->w_f, c->crit_cp32, cells, c->Mlo, c->Mhi);
             k_criterion<double><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const double*)f, c->xi_d,
-                                                          c->w_d, cp, c->xi_f, c->w_f, c->crit_cp32, c->Mlo, cells,
-                                                          c->Mkey);
+                                                          c->w_d, cp, c->xi_f, c->w_f, c->crit_cp32, c->Mlo, c->Mhi,
+                                                          decide, s32, C1s, C2s, cells, c->Mkey);
         } else {
             k_crit_screen<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const float*)f,
-                                                           c->xi_f, c->w_f, c->crit_cp32, cells, c->Mlo);
+                                                           c->xi_f, c->w_f, c->crit_cp32, cells, c->Mlo, c->Mhi);
             k_criterion<float><<<g, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, n, cpb, (const float*)f, c->xi_d,
-                                                         c->w_d, cp, c->xi_f, c->w_f, c->crit_cp32, c->Mlo, cells,
-                                                         c->Mkey);
+                                                         c->w_d, cp, c->xi_f, c->w_f, c->crit_cp32, c->Mlo, c->Mhi,
+                                                         decide, s32, C1s, C2s, cells, c->Mkey);
         }
     }
-    k_decode_M<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->M, c->Nv);
-    c->launches += (n > 0) ? 6 : 4;
+    k_decode_M<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->Mlo, decide && n > 0, c->M, c->Nv);
+    c->launches += (n > 0) ? 7 : 5;
     return cudaGetLastError();
 }
 

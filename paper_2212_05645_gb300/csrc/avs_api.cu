@@ -54,8 +54,8 @@ void free_all(avs_ctx* c)
                     c->slot, c->nslot, c->nbr, c->cg_d, c->r_d, c->eps2_d, c->cg_f, c->r_f, c->eps2_f,
                     c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
                     c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
-                    c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mthr, c->stage, c->dev_err,
-                    c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->cpar, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
+                    c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mhi, c->Mthr, c->stage, c->dev_err,
+                    c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->rmom, c->cpar, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
                     c->mlp_X, c->mlp_Y, c->mlp_logits, c->mlp_list, c->mlp_count, c->M_alt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -405,7 +405,7 @@ avs_status initial_tree(avs_ctx* c)
     const int passes = std::max(1, c->cfg.max_refine);
     for (int p = 0; p < passes; ++p) {
         CK(launch_maxwell(c, Wp_d, 2, 0.0, 0, c->pseudo_f, 1, c->Nvp));
-        CK(launch_criterion(c, c->pseudo_f, 1, 2, c->Nvp, Wc_d, nullptr, 0));
+        CK(launch_criterion(c, c->pseudo_f, 1, 2, c->Nvp, Wc_d, nullptr, 0, 1));
         int Nn, sp, mg;
         avs_status st = apply_marks(c, &Nn, &sp, &mg);
         if (st != AVS_OK) return st;
@@ -468,7 +468,8 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     AL(c->M, capp); AL(c->Mkey, capp);
     AL(c->pseudo_f, 2 * (size_t)c->NA * capp); AL(c->pseudo_W, 4 * NW);
     AL(c->crit_cp, 5 * (size_t)std::max(c->Nc, 2)); AL(c->crit_cp32, 8 * (size_t)std::max(c->Nc, 2));
-    AL(c->Mlo, capp); AL(c->Mthr, 4 * (size_t)capp);
+    AL(c->Mlo, capp); AL(c->Mhi, capp); AL(c->Mthr, 4 * (size_t)capp);
+    AL(c->rmom, 13 * (size_t)std::max(c->Nc, 2));
     AL(c->W[0], (size_t)c->Nc * NW); AL(c->W[1], (size_t)c->Nc * NW);
     AL(c->Wf, (size_t)c->Nc * NW); AL(c->q, (size_t)c->Nc * c->D);
     AL(c->dev_err, 1); AL(c->dt_key, 1); AL(c->gap_d, 1);
@@ -592,13 +593,14 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
             CK(mlp_checkset(c, c->mlp_logits, c->mlp_zthr, c->mlp_list, c->mlp_count));
             CK(cudaMemcpyAsync(&checked, c->mlp_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
-            CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, c->mlp_list, checked));
+            CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, c->mlp_list, checked, 1));
         }
         if (full) {
             if (c->mlp_trained > 0)
                 CK(cudaMemcpyAsync(c->M_alt, c->M, sizeof(double) * c->Nv, cudaMemcpyDeviceToDevice, c->stream));
             // the plain criterion: fallback, judge of the misses and source of the labels
-            CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+            // (exact M: the dominant label compares with it)
+            CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0, 0));
             if (c->mlp_trained > 0) {
                 CK(mlp_misses(c, c->M, c->M_alt, c->mlp_count + 1));
                 CK(cudaMemcpyAsync(&missed, c->mlp_count + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -616,7 +618,7 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
             checked = c->Nc;
         }
     } else {
-        CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+        CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0, 1));
     }
     int Nn, sp, mg;
     avs_status st = apply_marks(c, &Nn, &sp, &mg);
@@ -712,7 +714,7 @@ avs_status avs_criterion(avs_ctx* c, const double* Wc, int W_is_device, double* 
                            W_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     else
         CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr));
-    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0, 0));
     CK(cudaMemcpyAsync(M_out, c->M, sizeof(double) * c->Nv,
                        M_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!M_is_device || !W_is_device) CK(cudaStreamSynchronize(c->stream));
@@ -823,7 +825,7 @@ avs_status avs_features(avs_ctx* c, float* X_out, float* Y_out)
     if (st != AVS_OK) return st;
     CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, c->q));
     CK(mlp_features(c, c->Wf, c->q, c->mlp_X));
-    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0));
+    CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0, 0));
     CK(mlp_labels(c, c->f[c->cur], c->mlp_Y));
     if (X_out) CK(cudaMemcpyAsync(X_out, c->mlp_X, sizeof(float) * 8 * c->Nc, cudaMemcpyDeviceToHost, c->stream));
     if (Y_out) CK(cudaMemcpyAsync(Y_out, c->mlp_Y, sizeof(float) * 4 * c->Nc, cudaMemcpyDeviceToHost, c->stream));

@@ -383,27 +383,42 @@ __device__ __forceinline__ void vstore(T* p, const T* o)
 }
 
 // ---------------------------------------------------------------- criterion screening
-// FP32 screening value of the criterion at one (cell, node) and a bound on
-// its distance from the exact value.  Inputs and operations rounded to FP32:
-// |M1_32 - M1| <= 6 u |M1|, |M2_32 - M2| <= 24 u |wG 0.5/e| sum_d (|xi_d| + |U_d|)^2
-// (u = 2^-24) while the results stay normal; the bound takes 128 u of the sum
-// of both scales plus 2^-100, far above the absolute error of the few
-// roundings that can fall in the subnormal range (2^-149 each).
-__device__ __forceinline__ void crit32(int D, float G, float wk, const float* x, const float* c32, float& m, float& B)
+// FP32 screening value of the criterion at one (cell, node), scaled by 2^64,
+// and a bound on its distance from the exact value times 2^64.  The scaling
+// (exact, a power of two applied to G) keeps the FP32 values of the small f of
+// the distribution tails in the normal range.  With xi, U, w, G, 1/rho,
+// 0.5/e_int and every operation rounded to FP32 (u = 2^-24) and normal results:
+//   |M1_32 - M1| <= 6 u |M1|;
+//   |c_d,32 - c_d| <= delta_d = u a_d + 1.01 u |c_d|,  a_d = |xi_d| + |U_d|,
+//   |c^2_32 - c^2| <= sum_d delta_d (2 |c_d| + delta_d) + 4 u c^2,
+//   |M2_32 - M2| <= |wG 0.5/e| (16 u sum_d a_d |c_d| + 16 u^2 sum_d a_d^2 + 44 u c^2).
+// The bound takes 128 u for the first-order terms and 2^-40 for the
+// second-order one, and adds 2^-126, the smallest normal FP32 number, which
+// covers the absolute error of the roundings that can still fall in the
+// subnormal range (2^-150 each).
+constexpr float kCritScale = 0x1p64f;
+
+// G * 2^64 in FP32 (the scaling done in the type of G, so no extra underflow)
+__device__ __forceinline__ float crit_scaled(float G) { return G * kCritScale; }
+__device__ __forceinline__ float crit_scaled(double G) { return (float)(G * 0x1p64); }
+
+__device__ __forceinline__ void crit32(int D, float Gs, float wk, const float* x, const float* c32, float& m, float& B)
 {
-    const float wg = wk * G;
+    const float wg = wk * Gs;
     const float m1 = wg * c32[0];
-    float c2 = 0.0f, a2 = 0.0f;
+    float c2 = 0.0f, ac = 0.0f, a2 = 0.0f;
     for (int d = 0; d < D; ++d) {
         const float cc = x[d] - c32[1 + d];
         const float aa = fabsf(x[d]) + fabsf(c32[1 + d]);
         c2 += cc * cc;
+        ac += aa * fabsf(cc);
         a2 += aa * aa;
     }
     const float wh = wg * c32[4];
     const float m2 = wh * c2;
     m = m1 > m2 ? m1 : m2;
-    B = 0x1p-17f * (fabsf(m1) + fabsf(wh) * a2) + 0x1p-100f;
+    const float awh = fabsf(wh);
+    B = 0x1p-17f * (fabsf(m1) + awh * (ac + c2)) + 0x1p-40f * awh * a2 + 0x1p-126f;
 }
 
 // ---------------------------------------------------------------- reductions

@@ -62,6 +62,7 @@ struct avs_ctx {
     double *crit_cp = nullptr;                       // criterion per-cell inputs [max(Nc,2)][5]
     float *crit_cp32 = nullptr;                      // their FP32 screening form [max(Nc,2)][8]
     unsigned *Mlo = nullptr;                         // [cap] screening lower bounds of M (ordered keys)
+    unsigned *Mhi = nullptr;                         // [cap] screening upper bounds of M
     float *Mthr = nullptr;                           // [cap][4] label thresholds per node
     double *stage = nullptr;                         // FP64 staging [Nc][NA][Nv] for get/set (lazy)
     size_t stage_elems = 0;
@@ -77,6 +78,7 @@ struct avs_ctx {
     double *AFf = nullptr;                           // area-weighted face flux of W [Nf][D+2]
     int *forder = nullptr;                           // face processing order (by lower cell index)
     double *cmom = nullptr;                          // raw moments of f about U(W) per cell [Nc][NMom]
+    double *rmom = nullptr;                          // scratch raw moments [max(Nc,2)][NMom]
     int mom_valid = 0;                               // cmom matches the current f and W
     void *cpar = nullptr;                            // per-cell collision parameters (k_cell_state)
 
@@ -112,7 +114,8 @@ cudaError_t launch_maxwell(avs_ctx* c, const double* Wp, int Ncells, double amp,
 cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp,
                                 double* Wc_out, double* q_out);
 cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp,
-                             const double* Wc, const int* cells, int ncells_list);
+                             const double* Wc, const int* cells, int ncells_list, int decide);
+// decide = 1: M exact only where the split/merge tests need it (marks); 0: M exact everywhere
 cudaError_t launch_adapt_tree(avs_ctx* c, double C1, double C2);  // marks, scan, new tree -> *2 arrays
 cudaError_t launch_remap(avs_ctx* c, const void* fold, int Nvp_old, void* fnew, int Nvp_new, int Nv_new);
 cudaError_t launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters);

@@ -462,16 +462,16 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
     const int i = blockIdx.x;
     const double* p = cp + (size_t)i * 5;
     const float* p32 = cp32 + (size_t)i * 8;
-    const float s32 = (float)s, C1f = (float)C1, C2f = (float)C2;
+    const float s32 = (float)s, C1f = (float)C1 * kCritScale, C2f = (float)C2 * kCritScale;
     int y0 = 0, y1 = 0, y2 = 0, y3 = 0;
     for (int k = threadIdx.x; k < Nv; k += blockDim.x) {
         const T Gt = f[(size_t)i * NA * Nvp + k];
         float xf[3];
         for (int d = 0; d < D; ++d) xf[d] = xi32[(size_t)k * D + d];
         float m32, B;
-        crit32(D, (float)Gt, w32[k], xf, p32, m32, B);
+        crit32(D, crit_scaled(Gt), w32[k], xf, p32, m32, B);
         const float lo = s32 * (m32 - B), hi = s32 * (m32 + B);
-        const float4 t = thr[k];               // act, M_k, 0.5 s M_k
+        const float4 t = thr[k];               // act, M_k, 0.5 s M_k (scaled like m32)
         const int lv = level[k];
         const bool act = t.x != 0.0f;
         bool amb = false;
@@ -520,13 +520,14 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
     }
 }
 
-// per-node thresholds of the label tests: (s M_k >= C2, M_k, 0.5 s M_k) in FP32
+// per-node thresholds of the label tests: (s M_k >= C2, M_k, 0.5 s M_k) in FP32,
+// the last two scaled by 2^64 like the screening values
 __global__ void k_label_thr(int Nv, const double* __restrict__ M, double s, double C2, float4* thr)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nv) return;
     const double sM = __dmul_rn(s, M[k]);
-    thr[k] = make_float4(sM >= C2 ? 1.0f : 0.0f, (float)M[k], (float)(0.5 * sM), 0.0f);
+    thr[k] = make_float4(sM >= C2 ? 1.0f : 0.0f, (float)(M[k] * 0x1p64), (float)(0.5 * sM * 0x1p64), 0.0f);
 }
 
 // check set: cells whose dominant logit reaches the threshold.  The cell

@@ -39,6 +39,9 @@ __device__ __forceinline__ void ldv(const T* __restrict__ p, T* o)
     if constexpr (sizeof(T) == 4 && V == 4) {
         const float4 q = *reinterpret_cast<const float4*>(p);
         o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    } else if constexpr (sizeof(T) == 4 && V == 2) {
+        const float2 q = *reinterpret_cast<const float2*>(p);
+        o[0] = q.x; o[1] = q.y;
     } else if constexpr (sizeof(T) == 8 && V == 2) {
         const double2 q = *reinterpret_cast<const double2*>(p);
         o[0] = q.x; o[1] = q.y;
@@ -53,6 +56,8 @@ __device__ __forceinline__ void stv(T* p, const T* o)
 {
     if constexpr (sizeof(T) == 4 && V == 4) {
         *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (sizeof(T) == 4 && V == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
     } else if constexpr (sizeof(T) == 8 && V == 2) {
         *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
     } else {
@@ -175,8 +180,8 @@ __device__ __forceinline__ void foot_face(const T* fL, const T* fR, const T* gL,
 #pragma unroll
     for (int v = 1; v < V; ++v) uni = uni && (upL[v] == upL[0]);
     T fv[NA][V], gv[NA][D][V];
-    // one cell's vectors when the V nodes share their upwind cell, else both
-    // cells' vectors and a per-node select (16-byte loads either way)
+    // one cell's vectors when the V nodes share their upwind cell, else a
+    // scalar load per node from its own upwind cell
     if (uni) {
         const T* fb = (upL[0] ? fL : fR) + k0;
         const T* gb = (upL[0] ? gL : gR) + k0;
@@ -190,19 +195,15 @@ __device__ __forceinline__ void foot_face(const T* fL, const T* fR, const T* gL,
         }
     } else {
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            T tr[V];
-            ldv<T, V>(fL + k0 + (size_t)a * Nvp, fv[a]);
-            ldv<T, V>(fR + k0 + (size_t)a * Nvp, tr);
+        for (int v = 0; v < V; ++v) {
+            const T* fb = (upL[v] ? fL : fR) + k0 + v;
+            const T* gb = (upL[v] ? gL : gR) + k0 + v;
 #pragma unroll
-            for (int v = 0; v < V; ++v) fv[a][v] = upL[v] ? fv[a][v] : tr[v];
-            if (gL) {
+            for (int a = 0; a < NA; ++a) {
+                fv[a][v] = fb[(size_t)a * Nvp];
+                if (gL) {
 #pragma unroll
-                for (int d = 0; d < D; ++d) {
-                    ldv<T, V>(gL + k0 + (size_t)(a * D + d) * Nvp, gv[a][d]);
-                    ldv<T, V>(gR + k0 + (size_t)(a * D + d) * Nvp, tr);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) gv[a][d][v] = upL[v] ? gv[a][d][v] : tr[v];
+                    for (int d = 0; d < D; ++d) gv[a][d][v] = gb[(size_t)(a * D + d) * Nvp];
                 }
             }
         }
@@ -279,7 +280,7 @@ struct FaceSt {
 };
 
 // One block per face, two passes over the nodes (thread t owns nodes
-// k = tV.., tV + NT V.., V = 16 bytes of the element type):
+// k = tV.., tV + NT V.., V = VF = 2 nodes):
 //   A  interior: raw moments about V of the foot distribution phi_bar
 //      (upwind cell by the sign of xi . An), the foot values kept in shared
 //      memory when CACHE; boundary: flux moments of the outgoing foot values
@@ -290,12 +291,12 @@ struct FaceSt {
 //   B  interior: phi_ij = wa phi_bar + wb g_ij per node, its flux
 //      (xi . An) phi_ij and the flux moments sum_k w (xi . An) psi phi_ij;
 //      boundary: outgoing foot value / incoming Maxwellian.
-template <int D, typename T, int NT, bool CACHE>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 5 : 4) k_face(FaceP<D, T> P)
+template <int D, typename T, int NT, bool CACHE, int VF>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4) k_face(FaceP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
     constexpr int NR = (NM > 2 * NW) ? NM : 2 * NW;
-    constexpr int V = VW<T>::v;
+    constexpr int V = VF;
     __shared__ FaceSt<T> S;
     __shared__ double sw[(NT / 32) * NR];
     __shared__ double red[NR];
@@ -793,10 +794,14 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     // foot values of pass A kept in shared memory for pass B when they fit in
     // the default dynamic allowance (48 KB); otherwise pass B recomputes them
     const size_t cache_bytes = (size_t)NA * c->Nvp * sizeof(T);
+    // two nodes per thread per iteration (8-byte FP32 / 16-byte FP64 vectors):
+    // fewer registers and more resident warps than 16-byte FP32 vectors, which
+    // the latency-bound face passes prefer
+    constexpr int VF = 2;
     if (cache_bytes <= 48 * 1024)
-        k_face<D, T, NT, true><<<c->Nf, NT, cache_bytes, c->stream>>>(P);
+        k_face<D, T, NT, true, VF><<<c->Nf, NT, cache_bytes, c->stream>>>(P);
     else
-        k_face<D, T, NT, false><<<c->Nf, NT, 0, c->stream>>>(P);
+        k_face<D, T, NT, false, VF><<<c->Nf, NT, 0, c->stream>>>(P);
     c->launches += 1;
 
     CellP<D, T> Q;
