@@ -5,8 +5,9 @@ circumferential cells, Ma 5, Kn 0.1, isothermal wall, global quadtree over
 [-15, 15]^2 sqrt(R T_inf) with base 24x24 and up to 4 levels, mixed precision
 (f in FP32, moment sums, wall balance and correction in FP64).
 
-One benchmark step = one pass of the whole hot path: `nu` (= 50, the
-adaptation interval) explicit UGKS steps followed by one adaptation of the
+One benchmark step = one pass of the whole hot path over one batch: the
+Maxwellian start of the flow from the device-resident initial field, `nu`
+(= 50, the adaptation interval) explicit UGKS steps and one adaptation of the
 velocity mesh (moments, criterion, marks + scan compaction, consanguinity
 remap, conservation correction).  Metric: cell-velocity-node updates per
 second, sum over the UGKS steps of Nc * Nv divided by the time.
@@ -49,22 +50,33 @@ def _args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
     ap.add_argument("--workload", default="cylinder", choices=sorted(WORKLOADS),
-                    help="cylinder (the benchmark case) or a smaller case for profiling")
+                    help="cylinder (the benchmark case) or another configuration")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="host threads of the CPU oracle (default: all cores)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="kernel sweep over cell and node counts (FP32 and FP64 steps), one JSON line per case")
     return ap.parse_args()
 
 
 WORKLOADS = {
     # supersonic cylinder, O-mesh 128 radial x 96 circumferential (the benchmark case)
-    "cylinder": dict(),
+    "cylinder": ("cylinder", dict()),
     # same flow and velocity mesh on the inner 64 radial rows (profiling case, f > L2)
-    "cylinder-r64": dict(n_r=64),
+    "cylinder-r64": ("cylinder", dict(n_r=64)),
+    # lid-driven cavity 32 x 32 (config of the FP64 full-run parity)
+    "cavity": ("cavity", dict()),
+    # blunt wedge 240 x 160, Ma 8, Kn 0.01, 5 levels
+    "wedge": ("blunt_wedge", dict()),
+    # sphere 64 x 48 x 48, Ma 4.25, Kn 0.031, octree 16^3 with 3 levels
+    "sphere": ("sphere", dict()),
 }
 _WL = "cylinder"
 
 
 def _workload(precision="mixed"):
     from paper_2212_05645_gb300 import workloads as wl
-    return wl.cylinder(precision=precision, **WORKLOADS[_WL])
+    fn, kw = WORKLOADS[_WL]
+    return getattr(wl, fn)(precision=precision, **kw)
 
 
 def _dist():
@@ -175,14 +187,25 @@ def _traffic(kind, Nc, Nv):
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
+ORACLE_SAMPLES = {
+    # workload -> (builder, reduced mesh arguments, what the sample is)
+    "cylinder": ("cylinder", dict(n_r=12), "the first 12 radial rows (1152 cells)"),
+    "cylinder-r64": ("cylinder", dict(n_r=12), "the first 12 radial rows (1152 cells)"),
+    "cavity": ("cavity", dict(), "the whole 32 x 32 cavity"),
+    "wedge": ("blunt_wedge", dict(n_r=8, learned=False), "the first 8 wall-normal rows (1920 cells)"),
+    "sphere": ("sphere", dict(n_r=2, learned=False), "the first 2 radial shells (4608 cells)"),
+}
+
+
 def cpu_baseline(seconds=12.0, nu=NU):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same
-    workload: the first 12 radial rows (1152 cells) of the O-mesh with the
-    full velocity tree; UGKS steps until about `seconds` of CPU time."""
+    workload (the rows of cells next to the body, the full velocity tree);
+    UGKS steps until about `seconds` of CPU time, at most `nu`."""
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     import oracle as O
     from paper_2212_05645_gb300 import workloads as wl
-    w = wl.cylinder(n_r=12, precision="fp64")
+    fn, kw, what = ORACLE_SAMPLES[_WL]
+    w = getattr(wl, fn)(precision="fp64", **kw)
     r = O.Run(w)
     r.init_field()
     dt = r.dt()
@@ -196,7 +219,7 @@ def cpu_baseline(seconds=12.0, nu=NU):
     el = time.perf_counter() - t0
     val = w.mesh.Nc * r.Nv * n / el
     return {"value": val, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-            "sample": f"{n} UGKS steps of the first 12 radial rows ({w.mesh.Nc} cells) x {r.Nv} velocity nodes, FP64",
+            "sample": f"{n} UGKS steps of {what} x {r.Nv} velocity nodes, FP64",
             "seconds": el}
 
 
@@ -239,14 +262,18 @@ def run_gpu(args):
     w = _workload("mixed")
     # headline form: mixed precision with the learned proposer (full criterion every 4th adaptation)
     g = A.AVS(w, precision="mixed", stream=stream.cuda_stream, learned=True, full_every=4)
-    g.init_field()
     Nc = g.Nc
     nu = args.nu
+    # every bench step is one batch: a flow started from the resident initial
+    # field W0, nu UGKS steps and one adaptation (the explicit hypersonic runs
+    # are not carried on from step to step; see the design notes on long runs)
+    W0 = torch.from_numpy(np.ascontiguousarray(w.W_init)).to("cuda")
 
     def bench_step(ctx, updates):
+        ctx.init_field(W0)
         ctx.step(nu)
         updates.append(Nc * ctx.Nv * nu)
-        ctx.adapt()
+        return ctx.adapt()
 
     upd = []
     for _ in range(args.warmup):
@@ -272,6 +299,7 @@ def run_gpu(args):
     t0.record(stream)
     astats = []
     for j in range(args.steps):
+        g.init_field(W0)
         ev_s[j].record(stream)
         g.step(nu)
         ev_e[j].record(stream)
@@ -295,9 +323,11 @@ def run_gpu(args):
     cn_per_launch = statistics.mean(step_cells)
     achieved = bytes_per_cn * cn_per_launch / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _traffic("mixed", Nc, cn_per_launch / Nc)
+    # ncu traffic of the step, measured on the cylinder family (2D, mixed)
+    traffic = _traffic("mixed", Nc, cn_per_launch / Nc) if _WL.startswith("cylinder") else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "UGKS step: k_grad + k_face + k_cell <2,float>", "peak_source": peak_kind,
+            "traffic": traffic, "kernel": f"UGKS step: k_grad + k_face + k_cell_state + k_cell <{w.D},float>",
+            "peak_source": peak_kind,
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
             "peak_spec_gbs": 8000.0, "frac_of_spec": achieved / 8000.0}
 
@@ -325,7 +355,6 @@ def run_gpu(args):
     fp64 = None
     if not args.no_fp64:
         gd = A.AVS(w, precision="fp64", stream=stream.cuda_stream, learned=False)
-        gd.init_field()
         u = []
         bench_step(gd, u)
         torch.cuda.synchronize()
@@ -371,12 +400,78 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------- kernel sweep
+SWEEP_CELLS_2D = [(32, 32), (128, 128), (256, 256), (448, 448)]
+SWEEP_CELLS_3D = [(10, 10, 10), (20, 20, 20), (40, 40, 40), (58, 58, 58)]
+SWEEP_BASE_2D = [16, 32, 64, 128, 180]          # 256 .. 32400 nodes (uniform quadtree)
+SWEEP_BASE_3D = [8, 16, 24, 32]                 # 512 .. 32768 nodes (uniform octree)
+SWEEP_MAX_BYTES = 200e9                         # skip states above 200 GB
+
+
+def run_sweep(args):
+    """One JSON line per (cells, nodes, precision): the UGKS step alone on a
+    periodic box with the smooth synthetic field, its cell-node updates/s and
+    the algorithmic HBM fraction (1 read + 1 write of f per cell-node)."""
+    import torch
+    from paper_2212_05645_gb300 import avs as A
+    from paper_2212_05645_gb300 import build as B
+    from paper_2212_05645_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    B.build()
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = _peaks()
+    cases = [(n, b) for n in SWEEP_CELLS_2D for b in SWEEP_BASE_2D] + \
+            [(n, b) for n in SWEEP_CELLS_3D for b in SWEEP_BASE_3D]
+    import dataclasses
+    meshes = {}
+    for n, b in cases:
+        D = len(n)
+        Nc = int(np.prod(n))
+        Nv = b ** D
+        if n not in meshes:
+            meshes[n] = wl.sweep_box(n, base=(b,) * D, max_refine=0)     # mesh and field built once per size
+        for precision in ("mixed", "fp64"):
+            es = 4 if precision == "mixed" else 8
+            NA = 2 if D == 2 else 1
+            # f twice, L grad f, face flux (D faces per cell)
+            state = Nc * Nv * NA * es * (2 + D + D)
+            if state > SWEEP_MAX_BYTES:
+                continue
+            w = dataclasses.replace(meshes[n], base=(b,) * D, precision=precision)
+            g = A.AVS(w, precision=precision, stream=stream.cuda_stream, learned=False)
+            g.init_field()
+            dt = g.dt()
+            g.step(2, dt=dt)
+            torch.cuda.synchronize()
+            work = Nc * g.Nv
+            k = max(3, min(20, int((1e10 if precision == "mixed" else 5e8) / work)))
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.step(k, dt=dt)
+            e.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(e) / k
+            rate = work / (ms * 1e-3)
+            alg = 2 * NA * es
+            print(json.dumps({"sweep": True, "D": D, "cells": Nc, "velocity_nodes": g.Nv, "precision": precision,
+                              "ms_per_step": ms, "value": rate, "unit": UNIT, "steps": k,
+                              "achieved_gbs": alg * rate / 1e9, "peak_gbs": peak, "peak_source": peak_kind,
+                              "frac": alg * rate / 1e9 / peak}), flush=True)
+            g.close()
+            del g
+
+
 def main():
     global _WL
     args = _args()
     _WL = args.workload
+    if args.oracle_threads > 0:
+        os.environ["OMP_NUM_THREADS"] = str(args.oracle_threads)
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_gpu(args)
 

@@ -157,6 +157,13 @@ avs_status avs_get_tree(avs_ctx *ctx, int *level, int *base, uint32_t *key, doub
 avs_status avs_get_f(avs_ctx *ctx, double *f, int is_device);
 avs_status avs_set_f(avs_ctx *ctx, const double *f, int is_device);
 
+/* FP64 copy-out of f for a list of cells only (sampled parity at full size,
+ * where a whole FP64 copy would not fit in host memory).  cells: host array
+ * of ncells indices, each in [0, Nc) (else AVS_EINVAL before any work); out:
+ * host [ncells][nA][Nv].  Allocates and frees a device buffer of
+ * ncells * nA * Nv doubles (AVS_ENOMEM if it cannot); blocking. */
+avs_status avs_get_f_cells(avs_ctx *ctx, const int *cells, int ncells, double *out);
+
 /* Criterion values M_k, as avs_criterion, for caller-owned device arrays and
  * without allocating any device memory.  The paper has no counterpart: this is
  * a library service for callers that cannot allocate on demand, such as an

@@ -25,7 +25,8 @@ FP64, MIXED = 0, 1
 
 EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs_num_cells", "avs_init_field",
             "avs_dt", "ugks_step", "ugks_step_dt", "avs_adapt", "avs_moments", "avs_f_moments", "avs_set_W",
-            "avs_criterion", "avs_get_tree", "avs_get_f", "avs_set_f", "avs_sync", "avs_kernel_launches",
+            "avs_criterion", "avs_get_tree", "avs_get_f", "avs_get_f_cells", "avs_set_f", "avs_sync",
+            "avs_kernel_launches",
             "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
             "avs_mlp_train", "avs_measure_fma_peak"]
 MLP_NPARAM = 4996
@@ -90,6 +91,7 @@ def load():
         "avs_criterion": (C.c_int, [vp, dp, C.c_int, dp, C.c_int]),
         "avs_get_tree": (C.c_int, [vp, ip, ip, ip, dp, dp]),
         "avs_get_f": (C.c_int, [vp, dp, C.c_int]),
+        "avs_get_f_cells": (C.c_int, [vp, C.POINTER(C.c_int), C.c_int, dp]),
         "avs_set_f": (C.c_int, [vp, dp, C.c_int]),
         "avs_sync": (C.c_int, [vp]),
         "avs_kernel_launches": (C.c_uint64, [vp]),
@@ -278,6 +280,14 @@ class AVS:
             out = np.zeros((self.Nc, self.NA, self.Nv))
         p, dev = _ptr(out)
         self._ck(self.L.avs_get_f(self.h, p, dev))
+        return out
+
+    def get_f_cells(self, cells):
+        """FP64 copy of f for the listed cells, [n][nA][Nv] (host)."""
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        out = np.zeros((len(cells), self.NA, self.Nv))
+        self._ck(self.L.avs_get_f_cells(self.h, cells.ctypes.data_as(C.POINTER(C.c_int)), len(cells),
+                                        out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
     def set_f(self, f):

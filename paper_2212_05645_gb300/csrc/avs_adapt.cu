@@ -848,6 +848,30 @@ cudaError_t launch_to_double(avs_ctx* c, const void* f, double* out, int Nvp)
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void k_gather_double(int Nv, int Nvp, int NA, const T* __restrict__ f, const int* __restrict__ cells,
+                                double* out)
+{
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    const int ja = blockIdx.x;                      // (list entry, array)
+    if (k >= Nv) return;
+    const int j = ja / NA, a = ja % NA;
+    out[(size_t)ja * Nv + k] = (double)f[((size_t)cells[j] * NA + a) * Nvp + k];
+}
+
+cudaError_t launch_gather_double(avs_ctx* c, const int* cells_d, int ncells, double* out)
+{
+    dim3 g(ncells * c->NA, (c->Nv + 255) / 256);
+    if (c->mixed)
+        k_gather_double<float><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->NA, (const float*)c->f[c->cur], cells_d,
+                                                         out);
+    else
+        k_gather_double<double><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->NA, (const double*)c->f[c->cur],
+                                                          cells_d, out);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_from_double(avs_ctx* c, const double* in, void* f, int Nvp)
 {
     dim3 g(c->Nc * c->NA, (Nvp + 255) / 256);

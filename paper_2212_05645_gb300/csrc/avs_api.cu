@@ -750,6 +750,30 @@ avs_status avs_get_f(avs_ctx* c, double* f, int is_device)
     return AVS_OK;
 }
 
+avs_status avs_get_f_cells(avs_ctx* c, const int* cells, int ncells, double* out)
+{
+    if (!c || !cells || !out || ncells < 0) return AVS_EINVAL;
+    for (int j = 0; j < ncells; ++j)
+        if (cells[j] < 0 || cells[j] >= c->Nc) return fail(c, AVS_EINVAL, "cell index out of range");
+    if (ncells == 0) return AVS_OK;
+    const size_t n = (size_t)ncells * c->NA * c->Nv;
+    int* cells_d = nullptr;
+    double* buf = nullptr;
+    if (cudaMalloc(&cells_d, sizeof(int) * ncells) != cudaSuccess) return fail(c, AVS_ENOMEM, "cell list");
+    if (cudaMalloc(&buf, sizeof(double) * n) != cudaSuccess) {
+        cudaFree(cells_d);
+        return fail(c, AVS_ENOMEM, "gather buffer");
+    }
+    cudaError_t e = cudaMemcpyAsync(cells_d, cells, sizeof(int) * ncells, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_gather_double(c, cells_d, ncells, buf);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(cells_d);
+    cudaFree(buf);
+    if (e != cudaSuccess) return fail(c, AVS_ECUDA, cudaGetErrorString(e));
+    return read_err(c);
+}
+
 avs_status avs_set_f(avs_ctx* c, const double* f, int is_device)
 {
     if (!c || !f) return AVS_EINVAL;

@@ -121,5 +121,6 @@ cudaError_t launch_remap(avs_ctx* c, const void* fold, int Nvp_old, void* fnew, 
 cudaError_t launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters);
 cudaError_t launch_to_double(avs_ctx* c, const void* f, double* out, int Nvp);   // packed [Nc][NA][Nv]
 cudaError_t launch_from_double(avs_ctx* c, const double* in, void* f, int Nvp);
+cudaError_t launch_gather_double(avs_ctx* c, const int* cells_d, int ncells, double* out);   // [n][NA][Nv]
 
 }  // namespace avs

@@ -563,11 +563,11 @@ struct CellP {
 // Raw moments of the own f^n of every cell about its U(W^n) (one block per
 // cell); used when the previous step did not leave them (after init, set_f,
 // set_W or an adaptation).
-template <int D, typename T, int NT>
+template <int D, typename T, int NT, int VC>
 __global__ void __launch_bounds__(NT) k_raw_moments(CellP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
-    constexpr int V = VW<T>::v;
+    constexpr int V = VC;
     __shared__ double sw[(NT / 32) * NM];
     __shared__ double red[NM];
     const int i = blockIdx.x;
@@ -644,11 +644,11 @@ __global__ void k_cell_state(CellP<D, T> P)
 // update (diagonal of Eq. SGS_phi, R1); pad nodes are written as zero.  The
 // raw moments of the new f about U(W~) are summed on the way for the next
 // step (same nodes per thread and order as k_raw_moments).
-template <int D, typename T, int NT>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? 5 : 4) k_cell(CellP<D, T> P)
+template <int D, typename T, int NT, int VC>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 5 : 7) : 4) k_cell(CellP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v;
-    constexpr int V = VW<T>::v;
+    constexpr int V = VC;
     __shared__ int fs[AVS_MAXS];
     __shared__ T sg[AVS_MAXS];
     __shared__ double sw[(NT / 32) * NM];
@@ -829,12 +829,17 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     Q.nslot = c->nslot;
     Q.vol = c->vol;
     Q.err = c->dev_err;
+    // 16-byte vectors (4 FP32 / 2 FP64 nodes per thread) in the cell kernel: it
+    // streams f and the face fluxes, and more bytes in flight per warp beat the
+    // extra warps of narrower vectors; k_raw_moments uses the same node mapping
+    // so that its sums equal the carried ones bit for bit
+    constexpr int VC = VW<T>::v;
     if (!c->mom_valid) {
-        k_raw_moments<D, T, NT><<<c->Nc, NT, 0, c->stream>>>(Q);
+        k_raw_moments<D, T, NT, VC><<<c->Nc, NT, 0, c->stream>>>(Q);
         c->launches += 1;
     }
     k_cell_state<D, T><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(Q);
-    k_cell<D, T, NT><<<c->Nc, NT, 0, c->stream>>>(Q);
+    k_cell<D, T, NT, VC><<<c->Nc, NT, 0, c->stream>>>(Q);
     c->launches += 2;
     c->mom_valid = 1;          // the raw moments of fout about U(Wout) are in cmom
     return cudaGetLastError();

@@ -58,3 +58,57 @@ def field_err(Wg, Wo, D):
     e_m = np.abs(Wg[:, 1:1 + D] - m).max(1) / mscale
     e_E = np.abs(Wg[:, D + 1] - Wo[:, D + 1]) / np.abs(Wo[:, D + 1])
     return dict(rho=float(e_rho.max()), mom=float(e_m.max()), E=float(e_E.max()))
+
+
+def patch_mesh(mesh, targets, rings=2):
+    """Sub-mesh of the cells within `rings` face-neighbour steps of `targets`.
+
+    Faces are kept, in their original order, when both cells are in the patch
+    or when the face is a boundary face of a patch cell, so every cell within
+    rings - 1 steps keeps all its faces and neighbours.  One explicit step of
+    a target cell depends only on the cells within two steps (its faces'
+    upwind cells and their gradients), so on the patch it computes the same
+    update as on the whole mesh.  Returns (sub-mesh, patch cell indices,
+    positions of the targets in the patch)."""
+    from paper_2212_05645_gb300 import workloads as wl
+    L, R = mesh.faceL, mesh.faceR
+    inner = R >= 0
+    a = np.concatenate([L[inner], R[inner]])
+    b = np.concatenate([R[inner], L[inner]])
+    order = np.argsort(a, kind="stable")
+    a, b = a[order], b[order]
+    start = np.searchsorted(a, np.arange(mesh.Nc + 1))
+    cells = set(int(t) for t in targets)
+    frontier = list(cells)
+    for _ in range(rings):
+        nxt = []
+        for c in frontier:
+            for n in b[start[c]:start[c + 1]]:
+                n = int(n)
+                if n not in cells:
+                    cells.add(n)
+                    nxt.append(n)
+        frontier = nxt
+    cells = np.array(sorted(cells), dtype=np.int64)
+    inv = -np.ones(mesh.Nc, dtype=np.int64)
+    inv[cells] = np.arange(len(cells))
+    keep = (inv[L] >= 0) & ((R < 0) | (inv[np.maximum(R, 0)] >= 0))
+    fL = inv[L[keep]].astype(np.int32)
+    fR = np.where(R[keep] >= 0, inv[np.maximum(R[keep], 0)], R[keep]).astype(np.int32)
+    sub = wl.Mesh(mesh.D, fL, fR, mesh.An[keep], mesh.rL[keep], mesh.rR[keep], mesh.vol[cells], mesh.xc[cells],
+                  mesh.bc, name="patch").contiguous()
+    return sub, cells, inv[np.asarray(targets, dtype=np.int64)]
+
+
+def sample_cells(mesh, n_random=2, seed=7):
+    """Cells to sample at full size: nearest to and farthest from the body
+    centre, the ones closest to the +z / +y axis direction (3D poles), and a
+    few seeded random ones."""
+    x = mesh.xc - mesh.xc.mean(0)
+    r = np.linalg.norm(x, axis=1)
+    pick = [int(np.argmin(r)), int(np.argmax(r))]
+    ax = x[:, -1] / np.maximum(r, 1e-30)
+    pick += [int(np.argmax(ax)), int(np.argmin(ax))]
+    rng = np.random.default_rng(seed)
+    pick += [int(i) for i in rng.integers(0, mesh.Nc, n_random)]
+    return sorted(set(pick))

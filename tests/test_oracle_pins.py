@@ -359,3 +359,29 @@ def test_criterion_maxwellian_closed_form_and_max_over_cells():
     assert np.allclose(M, ref, rtol=1e-13, atol=0)
     parts = np.maximum(O.criterion(D, xi, w, f[:1], Wc[:1]), O.criterion(D, xi, w, f[1:], Wc[1:]))
     assert np.array_equal(parts, M)
+
+
+def test_step_locality_two_face_rings():
+    """One explicit step of a cell uses only the cells within two face steps
+    (its faces' upwind cells and their limited gradients, Sec. 2.3.3): the
+    oracle's step on a patch of those cells reproduces the whole-mesh step of
+    the patch's centre cells bit for bit, in 2D and 3D.  The sampled parity
+    of the full-size GPU runs rests on this."""
+    from gpu_common import patch_mesh, sample_cells
+    for w in (wl.cylinder(n_theta=24, n_r=8, precision="fp64"),
+              wl.sphere(n_r=4, n_theta=6, n_phi=6, C1=1.0, max_refine=1, precision="fp64", learned=False)):
+        r = O.Run(w)
+        r.init_field(amp=1e-2, seed=3)
+        dt = r.dt()
+        for _ in range(2):
+            r.step(dt)
+        f0, W0 = r.f.copy(), r.Wc.copy()
+        r.step(dt)
+        t = sample_cells(w.mesh)
+        sub, cells, pos = patch_mesh(w.mesh, t)
+        assert len(cells) < w.mesh.Nc
+        Wp = np.ascontiguousarray(W0[cells])
+        fo = O.step(O.MeshHandle(sub), O.gas(R=0.5, Pr=w.Pr, omega=w.omega, Kn=w.Kn, limiter=w.limiter),
+                    r.xi, r.w, dt, np.ascontiguousarray(f0[cells]), Wp)
+        assert np.array_equal(fo[pos], r.f[t])
+        assert np.array_equal(Wp[pos], r.Wc[t])
