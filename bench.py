@@ -371,7 +371,8 @@ def run_gpu(args):
         fp64 = {"value": sum(u) / (fms * 1e-3), "ms_per_step": fms / kd, "steps": kd}
         gd.close()
 
-    alu = {"fp32_fma_gflops": A.fma_peak_gflops(False), "fp64_fma_gflops": A.fma_peak_gflops(True),
+    alu = {"fp32_fma_gflops": A.fma_peak_gflops(0), "fp64_fma_gflops": A.fma_peak_gflops(1, iters=2000),
+           "fp32x2_fma_gflops": A.fma_peak_gflops(2),
            "kind": "measured: independent FMA chains, bench.py start-up"}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -217,10 +217,11 @@ avs_status avs_features(avs_ctx *ctx, float *X_out, float *Y_out);
 /* iters SGD steps on the current state's features and labels; last loss out. */
 avs_status avs_mlp_train(avs_ctx *ctx, int iters, float lr, float *loss_out);
 
-/* Measured FMA throughput of the current GPU (GFLOP/s, 2 flops per FMA) in FP64
- * (fp64 = 1) or FP32: independent multiply-add chains, timed with events.  A
+/* Measured FMA throughput of the current GPU (GFLOP/s, 2 flops per FMA):
+ * kind 0 FP32, 1 FP64, 2 FP32 pairs with the packed two-lane FMA.  Independent
+ * multiply-add chains, timed with events; AVS_EINVAL for another kind.  A
  * measurement utility for the ALU rooflines; the paper has no counterpart. */
-avs_status avs_measure_fma_peak(int fp64, int iters, double *gflops);
+avs_status avs_measure_fma_peak(int kind, int iters, double *gflops);
 
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t   avs_kernel_launches(const avs_ctx *ctx);

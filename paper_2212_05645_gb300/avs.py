@@ -342,10 +342,11 @@ class AVS:
         return loss.value
 
 
-def fma_peak_gflops(fp64, iters=20000):
-    """Measured FMA throughput of the current GPU in GFLOP/s."""
+def fma_peak_gflops(kind, iters=20000):
+    """Measured FMA throughput of the current GPU in GFLOP/s; kind 0 FP32,
+    1 FP64, 2 packed FP32 pairs (True / False still mean FP64 / FP32)."""
     out = C.c_double()
-    st = load().avs_measure_fma_peak(int(fp64), int(iters), C.byref(out))
+    st = load().avs_measure_fma_peak(int(kind), int(iters), C.byref(out))
     if st != AVS_OK:
         raise AVSError(st, "avs_measure_fma_peak")
     return out.value
