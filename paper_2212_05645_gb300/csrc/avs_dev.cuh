@@ -421,6 +421,72 @@ __device__ __forceinline__ void crit32(int D, float Gs, float wk, const float* x
     B = 0x1p-17f * (fabsf(m1) + awh * (ac + c2)) + 0x1p-40f * awh * a2 + 0x1p-126f;
 }
 
+// ---------------------------------------------------------------- FP32 pairs
+// Two nodes per instruction with the packed two-lane FP32 operations of
+// sm_100+ (each lane rounds as the scalar operation does; no contraction
+// beyond the explicit fma2).
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// raw_acc for a pair of nodes (per-lane partial sums), D = 2 or 3
+template <int D>
+__device__ __forceinline__ void raw_acc2(float2* m, const float2* xs, float2 wg, float2 wh)
+{
+    if (D == 2) {
+        const float2 s = fma2(xs[1], xs[1], mul2(xs[0], xs[0]));
+        const float2 t0 = mul2(wg, xs[0]), t1 = mul2(wg, xs[1]);
+        m[0] = add2(m[0], wg);
+        m[1] = add2(m[1], t0);
+        m[2] = add2(m[2], t1);
+        m[3] = fma2(t0, xs[0], m[3]);
+        m[4] = fma2(t0, xs[1], m[4]);
+        m[5] = fma2(t1, xs[1], m[5]);
+        m[6] = fma2(t0, s, m[6]);
+        m[7] = fma2(t1, s, m[7]);
+        m[8] = add2(m[8], wh);
+        m[9] = fma2(wh, xs[0], m[9]);
+        m[10] = fma2(wh, xs[1], m[10]);
+    } else {
+        const float2 s = fma2(xs[2], xs[2], fma2(xs[1], xs[1], mul2(xs[0], xs[0])));
+        const float2 t0 = mul2(wg, xs[0]), t1 = mul2(wg, xs[1]), t2 = mul2(wg, xs[2]);
+        m[0] = add2(m[0], wg);
+        m[1] = add2(m[1], t0);
+        m[2] = add2(m[2], t1);
+        m[3] = add2(m[3], t2);
+        m[4] = fma2(t0, xs[0], m[4]);
+        m[5] = fma2(t0, xs[1], m[5]);
+        m[6] = fma2(t0, xs[2], m[6]);
+        m[7] = fma2(t1, xs[1], m[7]);
+        m[8] = fma2(t1, xs[2], m[8]);
+        m[9] = fma2(t2, xs[2], m[9]);
+        m[10] = fma2(t0, s, m[10]);
+        m[11] = fma2(t1, s, m[11]);
+        m[12] = fma2(t2, s, m[12]);
+    }
+}
+
+// eq_eval for a pair of nodes (X[d] = the pair's d-th velocity components)
+template <int D>
+__device__ __forceinline__ void eq_eval2(const EqPar<float>& p, const float2* X, float2& gG, float2& gH)
+{
+    float2 c[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) c[d] = add2(X[d], bc2(-p.U[d]));
+    float2 c2 = mul2(c[0], c[0]), cq = mul2(c[0], bc2(p.alpha[0]));
+#pragma unroll
+    for (int d = 1; d < D; ++d) {
+        c2 = fma2(c[d], c[d], c2);
+        cq = fma2(c[d], bc2(p.alpha[d]), cq);
+    }
+    const float2 a = mul2(c2, bc2(-p.inv2RT));
+    const float2 e = mul2(bc2(p.pref), make_float2(__expf(a.x), __expf(a.y)));
+    const float2 s = mul2(c2, bc2(p.invRT));
+    gG = mul2(e, fma2(cq, add2(s, bc2(-(float)(D + 2))), bc2(1.0f)));
+    gH = (D == 2) ? mul2(mul2(bc2(p.RTH), e), fma2(cq, add2(s, bc2(-(float)D)), bc2(1.0f))) : bc2(0.0f);
+}
+
 // ---------------------------------------------------------------- reductions
 // Deterministic block reduction of N doubles per thread: warp tree with
 // shuffles, then a fixed-order sum over warps.  Result in out[0..N-1] (smem),

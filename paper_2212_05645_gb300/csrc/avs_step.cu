@@ -51,6 +51,25 @@ __device__ __forceinline__ void ldv(const T* __restrict__ p, T* o)
     }
 }
 
+// ldv through L2 only (values this block reads once)
+template <typename T, int V>
+__device__ __forceinline__ void ldv_cg(const T* __restrict__ p, T* o)
+{
+    if constexpr (sizeof(T) == 4 && V == 4) {
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(p));
+        o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+    } else if constexpr (sizeof(T) == 4 && V == 2) {
+        const float2 q = __ldcg(reinterpret_cast<const float2*>(p));
+        o[0] = q.x; o[1] = q.y;
+    } else if constexpr (sizeof(T) == 8 && V == 2) {
+        const double2 q = __ldcg(reinterpret_cast<const double2*>(p));
+        o[0] = q.x; o[1] = q.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = __ldcg(p + v);
+    }
+}
+
 template <typename T, int V>
 __device__ __forceinline__ void stv(T* p, const T* o)
 {
@@ -225,6 +244,58 @@ __device__ __forceinline__ void foot_face(const T* fL, const T* fR, const T* gL,
     }
 }
 
+// foot_face for a pair of FP32 nodes in packed two-lane arithmetic (same
+// operations and rounding per lane): out[a] = the pair's foot values of array a.
+// f and the gradient are read through L2 only (each value is used once by
+// this block), which leaves L1 to the node coordinates and weights that every
+// face block reads.
+template <int D, int NA>
+__device__ __forceinline__ void foot_face2(const float* fL, const float* fR, const float* gL, const float* gR,
+                                           int Nvp, const bool* upL, int k0, const float2* X, const float* rL,
+                                           const float* rR, float h, float2* out)
+{
+    float2 fv[NA], gv[NA][D];
+    if (upL[0] == upL[1]) {
+        const float* fb = (upL[0] ? fL : fR) + k0;
+        const float* gb = (upL[0] ? gL : gR) + k0;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            fv[a] = __ldcg(reinterpret_cast<const float2*>(fb + (size_t)a * Nvp));
+            if (gL) {
+#pragma unroll
+                for (int d = 0; d < D; ++d) gv[a][d] = __ldcg(reinterpret_cast<const float2*>(gb + (size_t)(a * D + d) * Nvp));
+            }
+        }
+    } else {
+        const float* f0 = (upL[0] ? fL : fR) + k0;
+        const float* f1 = (upL[1] ? fL : fR) + k0 + 1;
+        const float* g0 = (upL[0] ? gL : gR) + k0;
+        const float* g1 = (upL[1] ? gL : gR) + k0 + 1;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            fv[a] = make_float2(__ldcg(f0 + (size_t)a * Nvp), __ldcg(f1 + (size_t)a * Nvp));
+            if (gL) {
+#pragma unroll
+                for (int d = 0; d < D; ++d)
+                    gv[a][d] = make_float2(__ldcg(g0 + (size_t)(a * D + d) * Nvp), __ldcg(g1 + (size_t)(a * D + d) * Nvp));
+            }
+        }
+    }
+    float2 o[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+        o[d] = fma2(X[d], bc2(-h), make_float2(upL[0] ? rL[d] : rR[d], upL[1] ? rL[d] : rR[d]));
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        float2 val = fv[a];
+        if (gL) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) val = fma2(gv[a][d], o[d], val);
+        }
+        out[a] = val;
+    }
+}
+
 template <int D, int V, typename T, typename PP>
 __device__ __forceinline__ void load_nodes(const PP& P, int k0, T (*x)[D], T* w)
 {
@@ -297,6 +368,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4) 
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
     constexpr int NR = (NM > 2 * NW) ? NM : 2 * NW;
     constexpr int V = VF;
+    constexpr bool PACK = sizeof(T) == 4 && V == 2;      // FP32 pairs in packed arithmetic
     __shared__ FaceSt<T> S;
     __shared__ double sw[(NT / 32) * NR];
     __shared__ double red[NR];
@@ -351,7 +423,43 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4) 
         T acc[NR];
 #pragma unroll
         for (int m = 0; m < NR; ++m) acc[m] = T(0);
-        if (inter) {
+        bool packed = false;
+        if constexpr (PACK) {
+          if (inter) {
+            packed = true;
+            // FP32 node pairs in packed two-lane arithmetic; per-lane partial sums
+            float2 acc2[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
+            for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+                T x[V][D], wv[V];
+                load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
+                float2 X[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
+                float2 sn = mul2(X[0], bc2(An[0]));
+#pragma unroll
+                for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
+                const bool up[2] = {sn.x >= 0.0f, sn.y >= 0.0f};
+                float2 F[NA];
+                foot_face2<D, NA>((const float*)fL, (const float*)fR, (const float*)gL, (const float*)gR, Nvp, up,
+                                  k0, X, (const float*)rl, (const float*)rr, (float)h, F);
+                if constexpr (CACHE) {
+#pragma unroll
+                    for (int a = 0; a < NA; ++a) *reinterpret_cast<float2*>((float*)fc + a * Nvp + k0) = F[a];
+                }
+                float2 xs[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-(float)Vt[d]));
+                const float2 W2 = make_float2(wv[0], wv[1]);
+                raw_acc2<D>(acc2, xs, mul2(W2, F[0]), NA == 2 ? mul2(W2, F[NA - 1]) : bc2(0.0f));
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) acc[m] = (T)(acc2[m].x + acc2[m].y);
+          }
+        }
+        if (packed) {
+        } else if (inter) {
             for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
                 T x[V][D], wv[V];
                 load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
@@ -447,7 +555,58 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4) 
     __syncthreads();
 
     // ---------------- pass B: per-node flux of the interface distribution
-    if (inter) {
+    bool packed = false;
+    if constexpr (PACK) {
+      if (inter) {
+        packed = true;
+        const float2 wa = bc2((float)S.wa), wb = bc2((float)S.wb);
+        const EqPar<float> eq = *reinterpret_cast<const EqPar<float>*>(&S.eq);
+        float2 acc2[NW];
+#pragma unroll
+        for (int m = 0; m < NW; ++m) acc2[m] = bc2(0.0f);
+        for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+            T x[V][D], wv[V];
+            load_nodes<D, V>(P, k0, x, wv);
+            float2 X[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
+            float2 sn = mul2(X[0], bc2(An[0]));
+#pragma unroll
+            for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
+            float2 F[NA];
+            if constexpr (CACHE) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) F[a] = *reinterpret_cast<const float2*>((const float*)fc + a * Nvp + k0);
+            } else {
+                const bool up[2] = {sn.x >= 0.0f, sn.y >= 0.0f};
+                foot_face2<D, NA>((const float*)fL, (const float*)fR, (const float*)gL, (const float*)gR, Nvp, up,
+                                  k0, X, (const float*)rl, (const float*)rr, (float)h, F);
+            }
+            float2 gG, gH;
+            eq_eval2<D>(eq, X, gG, gH);
+            const float2 pG = fma2(wb, gG, mul2(wa, F[0]));
+            const float2 pH = NA == 2 ? fma2(wb, gH, mul2(wa, F[NA - 1])) : bc2(0.0f);
+            const float2 t = mul2(make_float2(wv[0], wv[1]), sn);
+            float2 x2 = mul2(X[0], X[0]);
+#pragma unroll
+            for (int d = 1; d < D; ++d) x2 = fma2(X[d], X[d], x2);
+            acc2[0] = fma2(t, pG, acc2[0]);
+            const float2 tp = mul2(t, pG);
+#pragma unroll
+            for (int d = 0; d < D; ++d) acc2[1 + d] = fma2(tp, X[d], acc2[1 + d]);
+            acc2[D + 1] = fma2(mul2(t, bc2(0.5f)), fma2(x2, pG, pH), acc2[D + 1]);
+            *reinterpret_cast<float2*>((float*)Fo + k0) = mul2(sn, pG);
+            if (NA == 2) *reinterpret_cast<float2*>((float*)Fo + (size_t)(NA - 1) * Nvp + k0) = mul2(sn, pH);
+        }
+        T acc[NW];
+#pragma unroll
+        for (int m = 0; m < NW; ++m) acc[m] = (T)(acc2[m].x + acc2[m].y);
+        block_sum_t<NW, NT>(acc, sw, red);
+        if (tid < NW) P.AF[(size_t)f * NW + tid] = red[tid];
+      }
+    }
+    if (packed) {
+    } else if (inter) {
         const T wa = S.wa, wb = S.wb;
         T acc[NW];
 #pragma unroll
@@ -680,7 +839,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 5 : 7) : 4) 
         T Nn[NA][V], fv[NA][V], out[NA][V];
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            ldv<T, V>(fi + (size_t)a * P.Nvp + k0, fv[a]);
+            ldv_cg<T, V>(fi + (size_t)a * P.Nvp + k0, fv[a]);
 #pragma unroll
             for (int v = 0; v < V; ++v) Nn[a][v] = T(0);
         }
@@ -692,7 +851,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 5 : 7) : 4) 
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
                 T t[V];
-                ldv<T, V>(Fs + (size_t)a * P.Nvp, t);
+                ldv_cg<T, V>(Fs + (size_t)a * P.Nvp, t);
 #pragma unroll
                 for (int v = 0; v < V; ++v) Nn[a][v] += g * t[v];
             }
