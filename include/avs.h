@@ -101,6 +101,9 @@ typedef struct {
     int W_is_device;
     int skip_correction;      /* 1: remap only (Sec. 3.2), no Sec. 3.3 correction             */
     int force_full;           /* learned form: run the full criterion on this call            */
+    int bypass;               /* 1: f on the new mesh is g^eq of the carried W (Sec. 3.3, the
+                                 bypass for weakly non-equilibrium flows) instead of the remap
+                                 and correction                                              */
 } avs_adapt_opts;
 
 /* Creates a context, uploads the mesh, builds the step-0 velocity mesh

@@ -71,6 +71,11 @@ def lib():
             L.om_dt_unit.argtypes = [C.c_void_p, C.c_int, dp]
             L.om_step.restype = C.c_int
             L.om_step.argtypes = [C.c_void_p, C.c_void_p, C.c_int, dp, dp, C.c_double, dp, dp, dp]
+            L.om_colors.restype = C.c_int
+            L.om_colors.argtypes = [C.c_void_p, ip]
+            L.om_step_implicit.restype = C.c_int
+            L.om_step_implicit.argtypes = [C.c_void_p, C.c_void_p, C.c_int, dp, dp, C.c_double, dp, dp, dp, ip,
+                                           C.c_int, C.c_int, C.c_int]
             L.om_criterion.restype = None
             L.om_criterion.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
             L.om_adapt_tree.restype = C.c_int
@@ -216,6 +221,26 @@ def step(mh: MeshHandle, g: _Gas, xi, w, dt, f_in, Wc):
     return f_out
 
 
+def colors(mh: MeshHandle):
+    """Greedy colouring of the cells in index order; returns (color, ncolor)."""
+    c = np.zeros(mh.mesh.Nc, dtype=np.int32)
+    n = lib().om_colors(mh.ptr, _ip(c))
+    return c, n
+
+
+def step_implicit(mh: MeshHandle, g: _Gas, xi, w, dt, f_in, Wc, color, ncolor, k_macro=60, k_micro=2):
+    """One implicit (IUGKS) step; returns f_out and updates Wc in place."""
+    xi = _f64(xi); w = _f64(w); f_in = _f64(f_in)
+    color = np.ascontiguousarray(color, dtype=np.int32)
+    assert Wc.dtype == np.float64 and Wc.flags.c_contiguous
+    f_out = np.empty_like(f_in)
+    rc = lib().om_step_implicit(mh.ptr, C.byref(g), xi.shape[0], _dp(xi), _dp(w), float(dt), _dp(f_in),
+                                _dp(f_out), _dp(Wc), _ip(color), int(ncolor), int(k_macro), int(k_micro))
+    if rc != 0:
+        raise FloatingPointError(f"oracle implicit step: non-positive density or temperature (status {rc})")
+    return f_out
+
+
 def criterion(D, xi, w, f, Wc):
     xi = _f64(xi); w = _f64(w); f = _f64(f); Wc = _f64(Wc)
     Nc, Nv = f.shape[0], f.shape[-1]
@@ -267,6 +292,18 @@ def conserved_from_primitive(D, Wp, R=0.5):
     Wc[..., 1:1 + D] = rho[..., None] * U
     Wc[..., D + 1] = 0.5 * rho * (U * U).sum(-1) + 1.5 * rho * R * Wp[..., D + 1]
     return Wc
+
+
+def primitive_from_conserved(D, Wc, R=0.5):
+    """rho, U, T from rho, rho U, rho E (monatomic, inverse of the above)."""
+    Wc = _f64(Wc)
+    Wp = np.zeros_like(Wc)
+    rho = Wc[..., 0]
+    Wp[..., 0] = rho
+    Wp[..., 1:1 + D] = Wc[..., 1:1 + D] / rho[..., None]
+    m2 = (Wc[..., 1:1 + D] ** 2).sum(-1)
+    Wp[..., D + 1] = (Wc[..., D + 1] - 0.5 * m2 / rho) / (1.5 * rho * R)
+    return Wp
 
 
 # ---------------------------------------------------------------------------
@@ -328,20 +365,34 @@ class Run:
     def step(self, dt):
         self.f = step(self.mh, self.g, self.xi, self.w, dt, self.f, self.Wc)
 
-    def adapt(self, Wc_override=None, correct_f=True):
+    def step_implicit(self, dt, k_macro=60, k_micro=2, color=None):
+        """IUGKS step (Sec. 2.3.1): macro PRSGS then micro SGS sweeps."""
+        if color is None:
+            if not hasattr(self, "_colors"):
+                self._colors = colors(self.mh)
+            color, nc = self._colors
+        else:
+            nc = int(np.max(color)) + 1
+        self.f = step_implicit(self.mh, self.g, self.xi, self.w, dt, self.f, self.Wc, color, nc, k_macro, k_micro)
+
+    def adapt(self, Wc_override=None, correct_f=True, bypass=False):
         """One adaptation: criterion on the moments of f (Eq. 7), marks, new
-        tree, consanguinity remap, conservation correction."""
+        tree, consanguinity remap, conservation correction (Secs. 3.2-3.4).
+        With bypass, f on the new mesh is g^eq of the carried W instead
+        (the bypass for weakly non-equilibrium flows, end of Sec. 3.3)."""
         D = self.D
         Wf, _ = moments(D, self.xi, self.w, self.f)
         Wcrit = Wf if Wc_override is None else Wc_override
         M = criterion(D, self.xi, self.w, self.f, Wcrit)
         nl, nb, nk, src, kind = adapt_tree(D, self.level, self.base, self.key, M, self.s,
                                            self.wl.C1, self.wl.C2, self.wl.max_refine)
-        f_new = remap(D, self.f, src, kind)
+        f_new = None if bypass else remap(D, self.f, src, kind)
         self.level, self.base, self.key = nl, nb, nk
         self._geom()
         gap = 0.0
-        if correct_f:
+        if bypass:
+            f_new = maxwell_init(D, self.xi, primitive_from_conserved(D, self.Wc))
+        elif correct_f:
             gap = correct(D, self.xi, self.w, Wf, f_new, iters=self.corr_iters)
         self.f = f_new
         return dict(M=M, src=src, kind=kind, gap=gap, Nv=self.Nv)

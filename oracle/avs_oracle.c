@@ -354,19 +354,22 @@ static double venkat(double d1, double d2, double eps2)
 
 /* ---- one explicit step (Sec. 2.3, explicit reading R1/R2) --------------- */
 
-int om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
-            double dt, const double *f_in, double *f_out, double *Wc)
+/* Steps shared by the explicit and the implicit step: limited gradients
+ * (Sec. 2.3.3), the interface distribution phi_ij of every face (Eqs. equ27,
+ * equ28 with R4; boundaries R8) stored in phi [Nf][nA][Nv], and its
+ * area-weighted flux moments A F_ij in F [Nf][D+2].  Returns 1 when an
+ * interface state has rho <= 0 or T <= 0. */
+static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
+                            double dt, const double *f_in, const slots_t *S, double *phi, double *F)
 {
     const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
+    memset(F, 0, (size_t)Nf * NW * sizeof(double));
     const double h = 0.5 * dt;
-    slots_t *S = build_slots(m);
     double *Minv = (double *)calloc((size_t)Nc * 9, sizeof(double));
     int *lsq_ok = (int *)calloc((size_t)Nc, sizeof(int));
     double *eps2 = (double *)malloc((size_t)Nc * sizeof(double));
     double *grad = (double *)malloc((size_t)Nc * nA * Nv * D * sizeof(double));
     double *lim = (double *)malloc((size_t)Nc * nA * Nv * sizeof(double));
-    double *phi = (double *)malloc((size_t)Nf * nA * Nv * sizeof(double));
-    double *F = (double *)calloc((size_t)Nf * NW, sizeof(double));
     int bad = 0;
 
     for (int i = 0; i < Nc; ++i) {
@@ -515,6 +518,19 @@ int om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const d
         }
     }
 
+    free(Minv); free(lsq_ok); free(eps2); free(grad); free(lim);
+    return bad;
+}
+
+int om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
+            double dt, const double *f_in, double *f_out, double *Wc)
+{
+    const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
+    slots_t *S = build_slots(m);
+    double *phi = (double *)malloc((size_t)Nf * nA * Nv * sizeof(double));
+    double *F = (double *)calloc((size_t)Nf * NW, sizeof(double));
+    int bad = interface_fluxes(m, g, Nv, xi, w, dt, f_in, S, phi, F);
+
     /* 3. macroscopic predictor and collision update of every cell */
 #pragma omp parallel for schedule(static) reduction(|:bad)
     for (int i = 0; i < Nc; ++i) {
@@ -556,7 +572,226 @@ int om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const d
         for (int c = 0; c < NW; ++c) Wi[c] = Wt[c];
     }
 
-    free(S); free(Minv); free(lsq_ok); free(eps2); free(grad); free(lim); free(phi); free(F);
+    free(S); free(phi); free(F);
+    return bad ? -5 : 0;
+}
+
+/* ---- implicit step (IUGKS, Sec. 2.3.1 macroscopic and microscopic) ---- */
+
+/* Greedy colouring of the cells in index order (each cell takes the smallest
+ * colour none of its face neighbours has): cells of one colour share no face,
+ * so a colour-by-colour Gauss-Seidel sweep is a sweep in the cell order
+ * "colour 0 cells ascending, colour 1 cells ascending, ...".  Returns the
+ * number of colours. */
+int om_colors(const om_mesh *m, int *color)
+{
+    slots_t *S = build_slots(m);
+    int nc = 0;
+    for (int i = 0; i < m->Nc; ++i) color[i] = -1;
+    for (int i = 0; i < m->Nc; ++i) {
+        unsigned used = 0;
+        for (int s = 0; s < S[i].n; ++s) {
+            int j = slot_nb(m, S, i, s);
+            if (j >= 0 && color[j] >= 0) used |= 1u << color[j];
+        }
+        int c = 0;
+        while (used & (1u << c)) ++c;
+        color[i] = c;
+        if (c + 1 > nc) nc = c + 1;
+    }
+    free(S);
+    return nc;
+}
+
+/* Euler flux of W through the unit normal n: (rho U.n, rho U (U.n) + p n,
+ * (rho E + p) U.n), p = rho R T (monatomic). */
+static void euler_flux(int D, const double *W, const double *n, double *G)
+{
+    double rho, U[3], RT;
+    prim_of(D, W, &rho, U, &RT);
+    double un = 0.0;
+    for (int d = 0; d < D; ++d) un += U[d] * n[d];
+    double p = rho * RT;
+    G[0] = rho * un;
+    for (int d = 0; d < D; ++d) G[1 + d] = W[1 + d] * un + p * n[d];
+    G[D + 1] = (W[D + 1] + p) * un;
+}
+
+/* Spectral radius of the Roe-type dissipation at a face (Eq. after Eq. Roe):
+ * r = |U.n| + a + 2 mu / (rho dl), from the mean of the primitive states of
+ * the two sides (reading: the paper leaves the interface state open), a the
+ * sound speed sqrt(5/3 R T) of a monatomic gas, mu the VHS viscosity. */
+static double roe_radius(const om_gas *g, int D, const double *WL, const double *WR, const double *n, double dl)
+{
+    double rl, Ul[3], RTl, rr, Ur[3], RTr;
+    prim_of(D, WL, &rl, Ul, &RTl);
+    prim_of(D, WR, &rr, Ur, &RTr);
+    double rho = 0.5 * (rl + rr), RT = 0.5 * (RTl + RTr), un = 0.0;
+    for (int d = 0; d < D; ++d) un += 0.5 * (Ul[d] + Ur[d]) * n[d];
+    double T = RT / g->R;
+    double mu = g->mu_ref * pow(T / g->T_ref, g->omega);
+    return fabs(un) + sqrt(5.0 / 3.0 * RT) + 2.0 * mu / (rho * dl);
+}
+
+/* One implicit step: the interface distribution and fluxes at t^n as in the
+ * explicit step, then
+ *  - macroscopic: Eq. (SGS_w) for dW = W~ - W^n, solved by k_macro symmetric
+ *    Gauss-Seidel iterations (a forward and a backward sweep over the colours
+ *    each); boundary faces enter the diagonal with their radius and a fixed
+ *    ghost state (no off-diagonal term);
+ *  - microscopic: Eq. (SGS_phi) for dphi = phi^{n+1} - phi^n with tau~, g~
+ *    from W~ and the lagged heat flux of f^n (R3), k_micro symmetric sweeps;
+ *    boundary faces bring no dphi of a neighbour.
+ * f_out = f_in + dphi, Wc <- W~.  color: a proper colouring (om_colors).
+ * Returns -5 when a state has rho <= 0 or T <= 0. */
+int om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
+                     double dt, const double *f_in, double *f_out, double *Wc,
+                     const int *color, int ncolor, int k_macro, int k_micro)
+{
+    const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
+    slots_t *S = build_slots(m);
+    double *phi = (double *)malloc((size_t)Nf * nA * Nv * sizeof(double));
+    double *F = (double *)calloc((size_t)Nf * NW, sizeof(double));
+    int bad = interface_fluxes(m, g, Nv, xi, w, dt, f_in, S, phi, F);
+
+    /* cells in sweep order: by colour, ascending index within a colour */
+    int *order = (int *)malloc((size_t)Nc * sizeof(int));
+    int *cstart = (int *)calloc((size_t)ncolor + 1, sizeof(int));
+    for (int i = 0; i < Nc; ++i) cstart[color[i] + 1]++;
+    for (int c = 0; c < ncolor; ++c) cstart[c + 1] += cstart[c];
+    {
+        int *pos = (int *)malloc((size_t)ncolor * sizeof(int));
+        for (int c = 0; c < ncolor; ++c) pos[c] = cstart[c];
+        for (int i = 0; i < Nc; ++i) order[pos[color[i]]++] = i;
+        free(pos);
+    }
+
+    /* ---- macroscopic system, Eq. (SGS_w) */
+    double *rad = (double *)malloc((size_t)Nf * sizeof(double));      /* A r per face */
+    for (int f = 0; f < Nf; ++f) {
+        const int L = m->faceL[f], R = m->faceR[f];
+        const double *An = m->An + (size_t)f * D;
+        double A = 0.0, n[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) A += An[d] * An[d];
+        A = sqrt(A);
+        for (int d = 0; d < D; ++d) n[d] = An[d] / A;
+        double dl = 0.0;
+        if (R >= 0) {
+            for (int d = 0; d < D; ++d) {
+                double e = m->rL[(size_t)f * D + d] - m->rR[(size_t)f * D + d];
+                dl += e * e;
+            }
+        } else {
+            for (int d = 0; d < D; ++d) dl += 4.0 * m->rL[(size_t)f * D + d] * m->rL[(size_t)f * D + d];
+        }
+        dl = sqrt(dl);
+        const double *WR = R >= 0 ? Wc + (size_t)R * NW : Wc + (size_t)L * NW;
+        rad[f] = A * roe_radius(g, D, Wc + (size_t)L * NW, WR, n, dl);
+    }
+    double *dW = (double *)calloc((size_t)Nc * NW, sizeof(double));
+    double *Wt = (double *)malloc((size_t)Nc * NW * sizeof(double));
+    memcpy(Wt, Wc, (size_t)Nc * NW * sizeof(double));
+    for (int it = 0; it < k_macro; ++it) {
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int q = 0; q < Nc; ++q) {
+                const int i = order[dir == 0 ? q : Nc - 1 - q];
+                double diag = m->vol[i] / dt, rhs[5];
+                for (int c = 0; c < NW; ++c) {
+                    double acc = 0.0;
+                    for (int sl = 0; sl < S[i].n; ++sl) acc += S[i].sgn[sl] * F[(size_t)S[i].face[sl] * NW + c];
+                    rhs[c] = -acc;
+                }
+                for (int sl = 0; sl < S[i].n; ++sl) {
+                    const int f = S[i].face[sl];
+                    diag += 0.5 * rad[f];
+                    const int j = slot_nb(m, S, i, sl);
+                    if (j < 0) continue;
+                    const double *An = m->An + (size_t)f * D;
+                    double A = 0.0, n[3] = {0, 0, 0};
+                    for (int d = 0; d < D; ++d) A += An[d] * An[d];
+                    A = sqrt(A);
+                    for (int d = 0; d < D; ++d) n[d] = S[i].sgn[sl] * An[d] / A;
+                    double Gt[5], Gn[5];
+                    euler_flux(D, Wt + (size_t)j * NW, n, Gt);
+                    euler_flux(D, Wc + (size_t)j * NW, n, Gn);
+                    for (int c = 0; c < NW; ++c)
+                        rhs[c] += -0.5 * A * (Gt[c] - Gn[c]) + 0.5 * rad[f] * dW[(size_t)j * NW + c];
+                }
+                for (int c = 0; c < NW; ++c) {
+                    dW[(size_t)i * NW + c] = rhs[c] / diag;
+                    Wt[(size_t)i * NW + c] = Wc[(size_t)i * NW + c] + dW[(size_t)i * NW + c];
+                }
+            }
+        }
+    }
+
+    /* ---- microscopic system, Eq. (SGS_phi), every node and array */
+    double *res = (double *)malloc((size_t)Nc * nA * Nv * sizeof(double));
+    double *dg = (double *)malloc((size_t)Nc * Nv * sizeof(double));       /* diagonal per cell and node */
+#pragma omp parallel for schedule(static) reduction(|:bad)
+    for (int i = 0; i < Nc; ++i) {
+        const double *fi = f_in + (size_t)i * nA * Nv;
+        double Wn[5], qn[3];
+        cell_moments(D, Nv, xi, w, fi, Wn, qn);          /* lagged heat flux of f^n (R3) */
+        double rho, U[3], RT;
+        prim_of(D, Wt + (size_t)i * NW, &rho, U, &RT);
+        if (!(rho > 0.0) || !(RT > 0.0)) bad = 1;
+        double tau = tau_of(g, rho, RT), V = m->vol[i];
+        for (int k = 0; k < Nv; ++k) {
+            const double *x = xi + (size_t)k * D;
+            double gG, gH, out = 0.0;
+            shakhov(D, g->Pr, rho, U, RT, qn, x, &gG, &gH);
+            for (int sl = 0; sl < S[i].n; ++sl) {
+                const double *An = m->An + (size_t)S[i].face[sl] * D;
+                double sn = 0.0;
+                for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                sn *= S[i].sgn[sl];
+                if (sn >= 0.0) out += sn;
+            }
+            dg[(size_t)i * Nv + k] = V / dt + V / tau + out;
+            for (int a = 0; a < nA; ++a) {
+                double N = 0.0;
+                for (int sl = 0; sl < S[i].n; ++sl) {
+                    int f = S[i].face[sl];
+                    const double *An = m->An + (size_t)f * D;
+                    double sn = 0.0;
+                    for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                    N += S[i].sgn[sl] * sn * phi[((size_t)f * nA + a) * Nv + k];
+                }
+                double ge = a == 0 ? gG : gH;
+                res[((size_t)i * nA + a) * Nv + k] = V * (ge - fi[a * Nv + k]) / tau - N;
+            }
+        }
+    }
+    double *dphi = (double *)calloc((size_t)Nc * nA * Nv, sizeof(double));
+    for (int it = 0; it < k_micro; ++it) {
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int q = 0; q < Nc; ++q) {
+                const int i = order[dir == 0 ? q : Nc - 1 - q];
+                for (int k = 0; k < Nv; ++k) {
+                    const double *x = xi + (size_t)k * D;
+                    for (int a = 0; a < nA; ++a) {
+                        double acc = res[((size_t)i * nA + a) * Nv + k];
+                        for (int sl = 0; sl < S[i].n; ++sl) {
+                            const int j = slot_nb(m, S, i, sl);
+                            if (j < 0) continue;
+                            const double *An = m->An + (size_t)S[i].face[sl] * D;
+                            double sn = 0.0;
+                            for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                            sn *= S[i].sgn[sl];
+                            if (sn < 0.0) acc -= sn * dphi[((size_t)j * nA + a) * Nv + k];
+                        }
+                        dphi[((size_t)i * nA + a) * Nv + k] = acc / dg[(size_t)i * Nv + k];
+                    }
+                }
+            }
+        }
+    }
+    for (size_t e = 0; e < (size_t)Nc * nA * Nv; ++e) f_out[e] = f_in[e] + dphi[e];
+    memcpy(Wc, Wt, (size_t)Nc * NW * sizeof(double));
+
+    free(S); free(phi); free(F); free(order); free(cstart); free(rad); free(dW); free(Wt);
+    free(res); free(dg); free(dphi);
     return bad ? -5 : 0;
 }
 

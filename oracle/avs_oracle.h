@@ -54,6 +54,11 @@ double om_dt_unit(const om_mesh *m, int Nv, const double *xi);
 int  om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
              double dt, const double *f_in, double *f_out, double *Wc);
 
+int  om_colors(const om_mesh *m, int *color);
+int  om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
+                      double dt, const double *f_in, double *f_out, double *Wc,
+                      const int *color, int ncolor, int k_macro, int k_micro);
+
 void om_criterion(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
                   const double *Wc, double *M);
 int  om_adapt_tree(int D, int Nv, const int *level, const int *base, const unsigned *key,

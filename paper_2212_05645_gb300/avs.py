@@ -62,7 +62,7 @@ class AdaptStats(C.Structure):
 
 class AdaptOpts(C.Structure):
     _fields_ = [("W_override", C.c_void_p), ("W_is_device", C.c_int), ("skip_correction", C.c_int),
-                ("force_full", C.c_int)]
+                ("force_full", C.c_int), ("bypass", C.c_int)]
 
 
 def load():
@@ -224,7 +224,7 @@ class AVS:
         self._ck(self.L.ugks_step(self.h, int(nsteps), float(self.wl.cfl if cfl is None else cfl), C.byref(out)))
         return out.value
 
-    def adapt(self, W_override=None, skip_correction=False, force_full=False):
+    def adapt(self, W_override=None, skip_correction=False, force_full=False, bypass=False):
         o = AdaptOpts()
         keep = None
         if W_override is not None:
@@ -234,6 +234,7 @@ class AVS:
             o.W_is_device = dev
         o.skip_correction = int(skip_correction)
         o.force_full = int(force_full)
+        o.bypass = int(bypass)
         s = AdaptStats()
         self._ck(self.L.avs_adapt(self.h, C.byref(o), C.byref(s)))
         return {k: getattr(s, k) for k, _ in AdaptStats._fields_}

@@ -74,6 +74,22 @@ void cons_host(int D, const double* Wp, double R, double* Wc)
     Wc[D + 1] = 0.5 * rho * u2 + 1.5 * rho * R * Wp[D + 1];
 }
 
+// primitive (rho, U, T) from conserved W (monatomic: rho E = rho U^2 / 2 + 3/2 rho R T)
+__global__ void k_cons_to_prim(int D, int Nc, const double* __restrict__ Wc, double R, double* Wp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nc) return;
+    const double* C = Wc + (size_t)i * (D + 2);
+    double* P = Wp + (size_t)i * (D + 2);
+    double m2 = 0.0;
+    P[0] = C[0];
+    for (int d = 0; d < D; ++d) {
+        P[1 + d] = C[1 + d] / C[0];
+        m2 += C[1 + d] * C[1 + d];
+    }
+    P[D + 1] = (C[D + 1] - 0.5 * m2 / C[0]) / (1.5 * C[0] * R);
+}
+
 __global__ void k_prim_to_cons(int D, int Nc, const double* __restrict__ Wp, double R, double* Wc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -632,9 +648,15 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
         if (st != AVS_OK) return st;
         dst = n0;
     }
-    CK(launch_remap(c, c->f[c->cur], Nvp_old, dst, Nvp_new, Nn));
+    if (!o.bypass) CK(launch_remap(c, c->f[c->cur], Nvp_old, dst, Nvp_new, Nn));
     swap_tree(c, Nn);
     CK(launch_geom(c));
+    if (o.bypass) {
+        // f = g^eq(W) of the carried W on the new mesh (the bypass of Sec. 3.3)
+        k_cons_to_prim<<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nc, c->W[c->wcur], c->cfg.R, c->Wf);
+        c->launches += 1;
+        CK(launch_maxwell(c, c->Wf, c->Nc, 0.0, 0, dst, 0, Nvp_new));
+    }
     if (n0) {
         CK(cudaStreamSynchronize(c->stream));
         cudaFree(c->f[0]);
@@ -647,7 +669,7 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
         c->cur ^= 1;
     }
     double gap = 0.0;
-    if (!o.skip_correction) {
+    if (!o.skip_correction && !o.bypass) {
         CK(launch_correct(c, c->f[c->cur], c->Wf, c->cfg.corr_iters));
         unsigned long long gk = 0;
         CK(cudaMemcpyAsync(&gk, c->gap_d, sizeof(gk), cudaMemcpyDeviceToHost, c->stream));

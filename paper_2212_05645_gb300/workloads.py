@@ -531,6 +531,60 @@ def sphere(n_r=64, n_theta=48, n_phi=48, Ma=4.25, Kn=0.031, C1=2.0, max_refine=3
                     precision=precision, learned=learned)
 
 
+def triangle_mesh(n_points=120, seed=5, bc_wall=None) -> Mesh:
+    """Unstructured mesh of triangles on the unit square: Delaunay
+    triangulation of seeded random interior points plus points along the
+    sides; every boundary edge is a face to the given boundary condition.
+    Faces are edges, oriented from the lower-numbered triangle outwards."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    m = max(3, int(round(math.sqrt(n_points) / 1.5)))
+    side = np.linspace(0.0, 1.0, m + 1)[:-1]
+    edge = np.concatenate([np.stack([side, np.zeros(m)], 1), np.stack([np.ones(m), side], 1),
+                           np.stack([1.0 - side, np.ones(m)], 1), np.stack([np.zeros(m), 1.0 - side], 1)])
+    P = np.concatenate([edge, 0.05 + 0.9 * rng.random((n_points, 2))])
+    tri = Delaunay(P).simplices
+    a, b, c = P[tri[:, 0]], P[tri[:, 1]], P[tri[:, 2]]
+    area = 0.5 * ((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0]))
+    tri[area < 0] = tri[area < 0][:, [0, 2, 1]]
+    xc = P[tri].mean(1)
+    owner = {}
+    faceL, faceR, An, rL, rR = [], [], [], [], []
+    for t, (i, j, k) in enumerate(tri):
+        for p0, p1 in ((i, j), (j, k), (k, i)):
+            key = (min(p0, p1), max(p0, p1))
+            if key in owner:
+                L, q0, q1 = owner.pop(key)
+                mid = 0.5 * (P[q0] + P[q1])
+                e = P[q1] - P[q0]
+                faceL.append(L); faceR.append(t)
+                An.append(np.array([e[1], -e[0]]))          # outward of L (counter-clockwise L)
+                rL.append(mid - xc[L]); rR.append(mid - xc[t])
+            else:
+                owner[key] = (t, p0, p1)
+    for (_, _), (L, q0, q1) in sorted(owner.items()):
+        mid = 0.5 * (P[q0] + P[q1])
+        e = P[q1] - P[q0]
+        faceL.append(L); faceR.append(-1)
+        An.append(np.array([e[1], -e[0]]))
+        rL.append(mid - xc[L]); rR.append(np.zeros(2))
+    vol = np.abs(0.5 * ((P[tri[:, 1], 0] - P[tri[:, 0], 0]) * (P[tri[:, 2], 1] - P[tri[:, 0], 1])
+                        - (P[tri[:, 1], 1] - P[tri[:, 0], 1]) * (P[tri[:, 2], 0] - P[tri[:, 0], 0])))
+    bc = np.array([bc_wall if bc_wall is not None else _bc_row(BC_WALL, T=1.0)])
+    return Mesh(2, np.array(faceL), np.array(faceR), np.array(An), np.array(rL), np.array(rR), vol, xc, bc,
+                name="triangles").contiguous()
+
+
+def triangle_box(n_points=120, seed=5, Kn=0.05, C1=2.0, base=(10, 10), max_refine=1, precision="fp64") -> Workload:
+    """Unstructured-mesh case: triangles on the unit square with isothermal
+    walls, the smooth field of the kernel sweep as initial state."""
+    mesh = triangle_mesh(n_points, seed)
+    v = 4.0 * sqrt_RT(1.0)
+    return Workload(f"triangles-{mesh.Nc}", mesh, 2, tuple(base), (-v, -v), (v, v), max_refine, Kn=Kn,
+                    omega=0.81, Pr=2.0 / 3.0, C1=C1, C2=K_SIGMA * C1, W_inf=(1.0, 0.0, 0.0, 1.0),
+                    W_init=sweep_W(mesh), precision=precision)
+
+
 def sweep_W(mesh: Mesh) -> np.ndarray:
     """Smooth synthetic macroscopic field of the kernel sweep:
     rho = 1 + 0.1 sin(2 pi x) sin(2 pi y), U = 0.3 (sin 2 pi y, cos 2 pi x[, 0]),

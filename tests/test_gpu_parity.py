@@ -178,6 +178,55 @@ def test_criterion_and_dt_bitexact_mixed_with_ties(amp):
     g.close()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_unstructured_triangles_steps_and_adaptation(precision, tol):
+    """Unstructured physical mesh (Delaunay triangles, 3 faces per cell,
+    walls on the boundary): steps and one adaptation against the oracle."""
+    avs = need_gpu()
+    w = wl.triangle_box(precision=precision)
+    r, g = pair(w, avs, precision=precision, amp=1e-2)
+    dt = r.dt()
+    assert g.dt() == dt
+    for _ in range(4):
+        r.step(dt)
+    g.step(4, dt=dt)
+    e = field_err(g.moments()[0], r.Wc, 2)
+    assert max(e.values()) < tol, e
+    if precision == "fp64":
+        assert rel_err(g.get_f(), r.f) < tol
+        o = r.adapt()
+        st = g.adapt()
+        t = g.tree()
+        assert st["Nv"] == o["Nv"]
+        assert np.array_equal(t["level"], r.level) and np.array_equal(t["key"], r.key)
+        assert rel_err(g.get_f(), r.f) < 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
+def test_adapt_equilibrium_bypass(precision, tol):
+    """Adaptation with the equilibrium bypass (end of Sec. 3.3): same tree as
+    the oracle and f = g^eq(W) of the carried W on it."""
+    avs = need_gpu()
+    w = wl.sweep_box((7, 6), base=(10, 10), max_refine=2, C1=2.0, precision=precision)
+    r, g = pair(w, avs, precision=precision, amp=1e-2)
+    dt = r.dt()
+    for _ in range(3):
+        r.step(dt)
+    g.step(3, dt=dt)
+    g.set_W(r.Wc)
+    g.set_f(r.f)
+    r.f = g.get_f()              # the same (FP32-rounded in the mixed form) inputs to the criterion
+    o = r.adapt(bypass=True)
+    st = g.adapt(bypass=True)
+    t = g.tree()
+    assert st["Nv"] == o["Nv"]
+    assert np.array_equal(t["level"], r.level) and np.array_equal(t["key"], r.key)
+    assert rel_err(g.get_f(), r.f) < tol
+    assert np.array_equal(g.moments()[0], r.Wc)
+    g.close()
+
+
 def test_criterion_bitexact_given_W():
     avs = need_gpu()
     w = small_cylinder()

@@ -385,3 +385,106 @@ def test_step_locality_two_face_rings():
                     r.xi, r.w, dt, np.ascontiguousarray(f0[cells]), Wp)
         assert np.array_equal(fo[pos], r.f[t])
         assert np.array_equal(Wp[pos], r.Wc[t])
+
+
+def test_adapt_equilibrium_bypass():
+    """The bypass of the reconstruction (end of Sec. 3.3): after the
+    adaptation, f on the new velocity mesh is the Maxwellian of the carried W
+    (checked against a numpy evaluation of the Maxwellian), H = (3 - D) R T G,
+    and the carried W is unchanged."""
+    w = wl.sweep_box((5, 4), base=(10, 10), max_refine=2, C1=2.0)
+    r = O.Run(w)
+    r.init_field(amp=1e-2, seed=4)
+    dt = r.dt()
+    for _ in range(3):
+        r.step(dt)
+    Wc = r.Wc.copy()
+    r.adapt(bypass=True)
+    assert np.array_equal(r.Wc, Wc)
+    rho = Wc[:, 0]
+    U = Wc[:, 1:3] / rho[:, None]
+    RT = (Wc[:, 3] - 0.5 * rho * (U * U).sum(1)) / (1.5 * rho)
+    c2 = ((r.xi[None, :, :] - U[:, None, :]) ** 2).sum(-1)
+    G = rho[:, None] / (2 * math.pi * RT[:, None]) * np.exp(-c2 / (2 * RT[:, None]))
+    assert np.allclose(r.f[:, 0, :], G, rtol=1e-13, atol=0)
+    assert np.allclose(r.f[:, 1, :], RT[:, None] * G, rtol=1e-13, atol=0)
+
+
+# ---- implicit step (IUGKS, Sec. 2.3.1): macro PRSGS with Roe flux differences, micro SGS
+
+def _other_coloring(mesh):
+    """A second proper colouring: greedy over the cells in reverse order."""
+    nb = [[] for _ in range(mesh.Nc)]
+    for L, R in zip(mesh.faceL, mesh.faceR):
+        if R >= 0:
+            nb[L].append(R)
+            nb[R].append(L)
+    col = -np.ones(mesh.Nc, dtype=np.int32)
+    for i in range(mesh.Nc - 1, -1, -1):
+        used = {col[j] for j in nb[i] if col[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return col
+
+
+def test_implicit_uniform_stream_stays_uniform():
+    """As for the explicit step: periodic box, f = discrete Maxwellian on a
+    symmetric uniform velocity mesh; the implicit step (both residuals zero)
+    leaves W unchanged bit for bit and f to 1e-13."""
+    m = _box(6)
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=0.05)
+    sig = math.sqrt(R)
+    _, _, _, _, xi, w = uniform_forest(2, 40, -10 * sig, 10 * sig)
+    Wp = np.tile([1.0, 0.0, 0.0, 1.0], (m.Nc, 1))
+    f = O.maxwell_init(2, xi, Wp)
+    Wc, _ = O.moments(2, xi, w, f)
+    W0 = Wc.copy()
+    col, nc = O.colors(mh)
+    fo = O.step_implicit(mh, g, xi, w, 3.0 * O.dt_unit(mh, xi), f, Wc, col, nc)
+    assert np.array_equal(Wc, W0)
+    assert np.allclose(fo, f, rtol=0, atol=1e-13 * f.max())
+
+
+def test_implicit_sweeps_converge_independent_of_order_and_conserve():
+    """With enough symmetric sweeps both systems are solved: two different
+    colourings (sweep orders) give the same step, and the converged
+    macroscopic step conserves the totals of rho, rho U, rho E on a periodic
+    box.  The paper's 60 + 2 sweeps stop short of that."""
+    w = wl.sweep_box((6, 5), base=(10, 10), max_refine=1)
+    vol = w.mesh.vol[:, None]
+    outs = []
+    for col in (None, _other_coloring(w.mesh)):
+        r = O.Run(w)
+        r.init_field(amp=1e-2, seed=8)
+        dt = r.dt(1.5)
+        tot0 = (r.Wc * vol).sum(0)
+        r.step_implicit(dt, k_macro=300, k_micro=300, color=col)
+        assert np.allclose((r.Wc * vol).sum(0), tot0, rtol=1e-12, atol=1e-13)
+        outs.append((r.f.copy(), r.Wc.copy()))
+    assert np.abs(outs[0][0] - outs[1][0]).max() <= 1e-11 * np.abs(outs[0][0]).max()
+    assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-11 * np.abs(outs[0][1]).max()
+    r = O.Run(w)
+    r.init_field(amp=1e-2, seed=8)
+    r.step_implicit(r.dt(1.5))
+    assert np.abs(r.f - outs[0][0]).max() > 1e-12 * np.abs(outs[0][0]).max()
+
+
+def test_implicit_matches_explicit_to_first_order_in_dt():
+    """Both steps advance f by dt times the same rate at t^n (the implicit
+    transport and collision terms differ at O(dt^2)): the gap relative to the
+    change halves with dt."""
+    w = wl.sweep_box((6, 5), base=(10, 10), max_refine=1)
+    ratio = []
+    for cfl in (0.4, 0.2):
+        re, ri = O.Run(w), O.Run(w)
+        for r in (re, ri):
+            r.init_field(amp=1e-2, seed=9)
+        f0 = re.f.copy()
+        dt = re.dt(cfl)
+        re.step(dt)
+        ri.step_implicit(dt, k_macro=200, k_micro=200)
+        ratio.append(np.abs(ri.f - re.f).max() / np.abs(re.f - f0).max())
+    assert 0.35 < ratio[1] / ratio[0] < 0.65, ratio
