@@ -134,6 +134,17 @@ avs_status avs_dt(avs_ctx *ctx, double cfl, double *dt_out);
 avs_status ugks_step(avs_ctx *ctx, int nsteps, double cfl, double *dt_out);
 avs_status ugks_step_dt(avs_ctx *ctx, int nsteps, double dt);
 
+/* nsteps implicit steps of size dt (IUGKS, Sec. 2.3.1): the interface
+ * distribution and fluxes at t^n as in ugks_step, then the macroscopic
+ * Eq. (SGS_w) for W~ - W^n (Roe-type flux differences; r = |U.n| + a +
+ * 2 mu / (rho dl) from the mean state of the two cells) and the microscopic
+ * Eq. (SGS_phi) for phi^{n+1} - phi^n, each solved by k_macro / k_micro
+ * symmetric Gauss-Seidel iterations (a forward and a backward sweep over a
+ * greedy cell colouring).  Boundary faces enter both diagonals with a fixed
+ * ghost state.  The paper recommends k_macro = 60, k_micro = 2.  Errors:
+ * EINVAL (nsteps < 0, dt <= 0, negative sweep counts), ECUDA. */
+avs_status ugks_step_implicit(avs_ctx *ctx, int nsteps, double dt, int k_macro, int k_micro);
+
 /* One AVS adaptation (Sec. 3): moments of f (Eq. 7), criterion M_k
  * (Eqs. criterion_rho/_e/_mk), split/merge marks, new depth-first tree,
  * consanguinity remap (Sec. 3.2), conservation correction (Sec. 3.3).

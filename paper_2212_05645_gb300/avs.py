@@ -24,7 +24,7 @@ STATUS = {0: "AVS_OK", -1: "AVS_EINVAL", -2: "AVS_ENOMEM", -3: "AVS_ECUDA", -4: 
 FP64, MIXED = 0, 1
 
 EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs_num_cells", "avs_init_field",
-            "avs_dt", "ugks_step", "ugks_step_dt", "avs_adapt", "avs_moments", "avs_f_moments", "avs_set_W",
+            "avs_dt", "ugks_step", "ugks_step_dt", "ugks_step_implicit", "avs_adapt", "avs_moments", "avs_f_moments", "avs_set_W",
             "avs_criterion", "avs_get_tree", "avs_get_f", "avs_get_f_cells", "avs_set_f", "avs_sync",
             "avs_kernel_launches",
             "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
@@ -91,6 +91,7 @@ def load():
         "avs_criterion": (C.c_int, [vp, dp, C.c_int, dp, C.c_int]),
         "avs_get_tree": (C.c_int, [vp, ip, ip, ip, dp, dp]),
         "avs_get_f": (C.c_int, [vp, dp, C.c_int]),
+        "ugks_step_implicit": (C.c_int, [vp, C.c_int, C.c_double, C.c_int, C.c_int]),
         "avs_get_f_cells": (C.c_int, [vp, C.POINTER(C.c_int), C.c_int, dp]),
         "avs_set_f": (C.c_int, [vp, dp, C.c_int]),
         "avs_sync": (C.c_int, [vp]),
@@ -215,6 +216,13 @@ class AVS:
         out = C.c_double()
         self._ck(self.L.avs_dt(self.h, float(self.wl.cfl if cfl is None else cfl), C.byref(out)))
         return out.value
+
+    def step_implicit(self, nsteps=1, dt=None, cfl=None, k_macro=60, k_micro=2):
+        """Implicit (IUGKS) steps; dt defaults to cfl (default the workload's) times the explicit bound."""
+        if dt is None:
+            dt = self.dt(cfl)
+        self._ck(self.L.ugks_step_implicit(self.h, int(nsteps), float(dt), int(k_macro), int(k_micro)))
+        return dt
 
     def step(self, nsteps=1, dt=None, cfl=None):
         if dt is not None:

@@ -55,7 +55,8 @@ void free_all(avs_ctx* c)
                     c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
                     c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
                     c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mhi, c->Mthr, c->stage, c->dev_err,
-                    c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->rmom, c->cpar, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
+                    c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->rmom, c->cpar, c->clist, c->imp_dW, c->imp_rhs0, c->imp_diag, c->imp_rad,
+                    c->imp_Gn, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
                     c->mlp_X, c->mlp_Y, c->mlp_logits, c->mlp_list, c->mlp_count, c->M_alt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -350,7 +351,10 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
         dalloc(&c->nslot, Nc) || dalloc(&c->nbr, ncs) || dalloc(&c->cg_d, ncsd) || dalloc(&c->r_d, ncsd) ||
         dalloc(&c->eps2_d, Nc) || dalloc(&c->cg_f, ncsd) || dalloc(&c->r_f, ncsd) || dalloc(&c->eps2_f, Nc) ||
         dalloc(&c->AFf, (size_t)Nf * (D + 2)) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * avs::NMom<3>::v) ||
-        dalloc((unsigned char**)&c->cpar, (size_t)Nc * AVS_CELLPAR_BYTES))
+        dalloc((unsigned char**)&c->cpar, (size_t)Nc * AVS_CELLPAR_BYTES) || dalloc(&c->clist, Nc) ||
+        dalloc(&c->imp_dW, (size_t)Nc * (D + 2)) || dalloc(&c->imp_rhs0, (size_t)Nc * (D + 2)) ||
+        dalloc(&c->imp_diag, Nc) || dalloc(&c->imp_rad, (size_t)Nc * AVS_MAXS) ||
+        dalloc(&c->imp_Gn, (size_t)Nc * AVS_MAXS * (D + 2)))
         return fail(c, AVS_ENOMEM, "mesh arrays");
     cudaStream_t s = c->stream;
     CK(up(c->faceL, std::vector<int>(m->faceL, m->faceL + Nf), s));
@@ -379,6 +383,29 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
     auto low = [&](int f) { const int R = m->faceR[f]; return R >= 0 ? std::min(m->faceL[f], R) : m->faceL[f]; };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return low(a) < low(b); });
     CK(up(c->forder, order, s));
+    // greedy colouring in cell order (smallest colour no face neighbour has):
+    // cells of one colour share no face (implicit sweeps)
+    {
+        std::vector<int> col(Nc, -1);
+        c->ncolor = 0;
+        for (int i = 0; i < Nc; ++i) {
+            unsigned used = 0;
+            for (int q = 0; q < ns[i]; ++q) {
+                const int j = nbr[(size_t)i * AVS_MAXS + q];
+                if (j >= 0 && col[j] >= 0) used |= 1u << col[j];
+            }
+            int k = 0;
+            while (used & (1u << k)) ++k;
+            col[i] = k;
+            c->ncolor = std::max(c->ncolor, k + 1);
+        }
+        c->cstart.assign(c->ncolor + 1, 0);
+        for (int i = 0; i < Nc; ++i) c->cstart[col[i] + 1]++;
+        for (int k = 0; k < c->ncolor; ++k) c->cstart[k + 1] += c->cstart[k];
+        std::vector<int> pos(c->cstart.begin(), c->cstart.end() - 1), cl(Nc);
+        for (int i = 0; i < Nc; ++i) cl[pos[col[i]]++] = i;
+        CK(up(c->clist, cl, s));
+    }
     CK(cudaStreamSynchronize(s));    // host vectors go out of scope
     return AVS_OK;
 }
@@ -566,6 +593,18 @@ avs_status ugks_step_dt(avs_ctx* c, int nsteps, double dt)
     if (!c || nsteps < 0 || !(dt > 0)) return AVS_EINVAL;
     for (int s = 0; s < nsteps; ++s) {
         CK(launch_step(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt));
+        c->cur ^= 1;
+        c->wcur ^= 1;
+    }
+    return AVS_OK;
+}
+
+avs_status ugks_step_implicit(avs_ctx* c, int nsteps, double dt, int k_macro, int k_micro)
+{
+    if (!c || nsteps < 0 || !(dt > 0) || k_macro < 0 || k_micro < 0) return AVS_EINVAL;
+    for (int s = 0; s < nsteps; ++s) {
+        CK(launch_step_implicit(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt, k_macro,
+                                k_micro));
         c->cur ^= 1;
         c->wcur ^= 1;
     }

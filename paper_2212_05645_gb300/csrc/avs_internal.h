@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/avs.h"
 
@@ -82,6 +83,15 @@ struct avs_ctx {
     int mom_valid = 0;                               // cmom matches the current f and W
     void *cpar = nullptr;                            // per-cell collision parameters (k_cell_state)
 
+    // ---- implicit step (Sec. 2.3.1): cell colouring and the macroscopic system
+    int ncolor = 0;
+    std::vector<int> cstart;                         // [ncolor+1] offsets into clist (host)
+    int *clist = nullptr;                            // [Nc] cells by colour, ascending within a colour
+    double *imp_dW = nullptr, *imp_rhs0 = nullptr;   // [Nc][D+2]
+    double *imp_diag = nullptr;                      // [Nc]
+    double *imp_rad = nullptr;                       // [Nc][MAXS]
+    double *imp_Gn = nullptr;                        // [Nc][MAXS][D+2]
+
     // ---- learned proposer (MLP 8-64-64-4)
     float *mlp_P = nullptr;                          // FP32 master parameters
     void *mlp_Wb = nullptr;                          // BF16 operand copies
@@ -105,6 +115,8 @@ int round_up(int n, int m);
 
 // ---- launchers (avs_step.cu)
 cudaError_t launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
+cudaError_t launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt,
+                                 int k_macro, int k_micro);
 
 // ---- launchers (avs_adapt.cu)
 cudaError_t launch_geom(avs_ctx* c);                       // xi, w of the current tree

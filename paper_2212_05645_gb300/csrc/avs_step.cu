@@ -875,9 +875,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 5 : 7) : 4) 
     if (tid < NM) P.mom[(size_t)i * NM + tid] = red[tid];
 }
 
+// Limited gradients and the face stage of a step: per-node face flux in
+// c->flux, area-weighted face flux of W in c->AFf (shared by the explicit and
+// the implicit step).
 template <int D, typename T>
-static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout,
-                                 double dt)
+static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, double dt)
 {
     const bool f32 = sizeof(T) == 4;
     const int NA = NArr<D>::v;
@@ -895,7 +897,9 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
         }
     }
     {
-        const size_t need = (size_t)c->Nf * NA * rows * sizeof(T);
+        // room for the face flux, and for one f-sized array (the implicit step's
+        // increment) once the face flux has been used
+        const size_t need = (size_t)std::max(c->Nf, c->Nc) * NA * rows * sizeof(T);
         if (c->flux_bytes < need) {
             if (c->flux) cudaFree(c->flux);
             c->flux = nullptr;
@@ -963,6 +967,20 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
         k_face<D, T, NT, false, VF><<<c->Nf, NT, 0, c->stream>>>(P);
     c->launches += 1;
 
+    return cudaGetLastError();
+}
+
+template <int D, typename T>
+static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout,
+                                 double dt)
+{
+    const bool f32 = sizeof(T) == 4;
+    const int NA = NArr<D>::v;
+    cudaError_t e = face_stage_t<D, T>(c, fin, Win, dt);
+    if (e != cudaSuccess) return e;
+    const T* xi = f32 ? (const T*)c->xi_f : (const T*)c->xi_d;
+    const T* w = f32 ? (const T*)c->w_f : (const T*)c->w_d;
+    constexpr int NT = 128;
     CellP<D, T> Q;
     Q.Nc = c->Nc;
     Q.Nv = c->Nv;
@@ -1002,6 +1020,401 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     c->launches += 2;
     c->mom_valid = 1;          // the raw moments of fout about U(Wout) are in cmom
     return cudaGetLastError();
+}
+
+// ================================================================== implicit step
+// IUGKS (Sec. 2.3.1): after the face stage, the macroscopic Eq. (SGS_w) for
+// dW = W~ - W^n and the microscopic Eq. (SGS_phi) for dphi are solved by
+// symmetric Gauss-Seidel sweeps over a greedy cell colouring: the cells of one
+// colour share no face, so a colour is updated in parallel with the values of
+// the other colours as they stand, which is the sequential sweep in the order
+// "colour 0, colour 1, ..." (forward) and back (backward).
+
+template <int D, typename A>
+__device__ __forceinline__ void euler_flux_a(const double* Wd, const double* n, A* G)
+{
+    constexpr int NW = D + 2;
+    A W[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) W[c] = (A)Wd[c];
+    const A rho = W[0];
+    A m2 = A(0), un = A(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        m2 += W[1 + d] * W[1 + d];
+        un += (W[1 + d] / rho) * (A)n[d];
+    }
+    const A p = rho * ((W[D + 1] - A(0.5) * m2 / rho) / (A(1.5) * rho));
+    G[0] = rho * un;
+#pragma unroll
+    for (int d = 0; d < D; ++d) G[1 + d] = W[1 + d] * un + p * (A)n[d];
+    G[D + 1] = (W[D + 1] + p) * un;
+}
+
+struct ImpP {
+    int Nc;
+    double dt, R, mu_ref, T_ref, omega;
+    const int* slot;
+    const unsigned char* nslot;
+    const int* faceL;
+    const int* faceR;
+    const double* An;
+    const double* rL;
+    const double* rR;
+    const double* vol;
+    const double* AF;
+    const double* Wn;        // W^n
+    double* Wt;              // W~ (the output W)
+    double* dW;              // [cell][NW]
+    double* diag;            // [cell]
+    double* rhs0;            // [cell][NW]
+    double* rad;             // [cell][MAXS]  A r of each face slot
+    double* Gn;              // [cell][MAXS][NW]  Euler flux of the neighbour's W^n through the slot's normal
+    const int* clist;        // cells by colour
+};
+
+// Per cell: diagonal V/dt + 1/2 sum A r, explicit part of the residual
+// -sum sgn A F, and per face slot A r and the neighbour's Euler flux at t^n.
+// r from the face's own orientation (L, R, n_LR) so both cells use one value.
+template <int D, typename A>
+__global__ void k_imp_setup(ImpP P)
+{
+    constexpr int NW = D + 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.Nc) return;
+    const int ns = P.nslot[i];
+    const double* Wi = P.Wn + (size_t)i * NW;
+    for (int c = 0; c < NW; ++c) {
+        double acc = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            const int sl = P.slot[i * AVS_MAXS + s];
+            const double a = P.AF[(size_t)(sl >> 1) * NW + c];
+            acc += (sl & 1) ? -a : a;
+        }
+        P.rhs0[(size_t)i * NW + c] = -acc;
+        P.dW[(size_t)i * NW + c] = 0.0;
+        P.Wt[(size_t)i * NW + c] = Wi[c];
+    }
+    double dg = P.vol[i] / P.dt;
+    for (int s = 0; s < ns; ++s) {
+        const int sl = P.slot[i * AVS_MAXS + s];
+        const int f = sl >> 1;
+        const double sgn = (sl & 1) ? -1.0 : 1.0;
+        const int L = P.faceL[f], R = P.faceR[f];
+        const double* An = P.An + (size_t)f * D;
+        double Aa = 0.0;
+        for (int d = 0; d < D; ++d) Aa += An[d] * An[d];
+        Aa = sqrt(Aa);
+        double n[3] = {0, 0, 0}, dl = 0.0;
+        for (int d = 0; d < D; ++d) n[d] = An[d] / Aa;
+        for (int d = 0; d < D; ++d) {
+            const double e = R >= 0 ? P.rL[(size_t)f * D + d] - P.rR[(size_t)f * D + d] : 2.0 * P.rL[(size_t)f * D + d];
+            dl += e * e;
+        }
+        dl = sqrt(dl);
+        // spectral radius |U.n| + a + 2 mu / (rho dl) from the mean primitive state
+        double rl, Ul[3], RTl, rr, Ur[3], RTr;
+        prim<D>(P.Wn + (size_t)L * NW, rl, Ul, RTl);
+        prim<D>(P.Wn + (size_t)(R >= 0 ? R : L) * NW, rr, Ur, RTr);
+        const double rho = 0.5 * (rl + rr), RT = 0.5 * (RTl + RTr);
+        double un = 0.0;
+        for (int d = 0; d < D; ++d) un += 0.5 * (Ul[d] + Ur[d]) * n[d];
+        const double mu = P.mu_ref * pow(RT / P.R / P.T_ref, P.omega);
+        const double r = Aa * (fabs(un) + sqrt(5.0 / 3.0 * RT) + 2.0 * mu / (rho * dl));
+        P.rad[(size_t)i * AVS_MAXS + s] = r;
+        dg += 0.5 * r;
+        const int j = (sl & 1) ? L : R;
+        if (j >= 0) {
+            double ns_[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) ns_[d] = sgn * An[d] / Aa;
+            A G[NW];
+            euler_flux_a<D, A>(P.Wn + (size_t)j * NW, ns_, G);
+            for (int c = 0; c < NW; ++c) P.Gn[((size_t)i * AVS_MAXS + s) * NW + c] = (double)G[c];
+        }
+    }
+    P.diag[i] = dg;
+}
+
+// One colour of a macroscopic sweep: dW_i = (Res_i(W~) + 1/2 sum A r dW_j) / diag_i,
+// Res_i = -sum sgn A F - 1/2 sum A (G(W~_j) - G(W^n_j)) over the interior faces.
+template <int D, typename A>
+__global__ void k_imp_macro(ImpP P, int c0, int c1)
+{
+    constexpr int NW = D + 2;
+    const int q = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= c1) return;
+    const int i = P.clist[q];
+    const int ns = P.nslot[i];
+    double rhs[NW];
+    for (int c = 0; c < NW; ++c) rhs[c] = P.rhs0[(size_t)i * NW + c];
+    for (int s = 0; s < ns; ++s) {
+        const int sl = P.slot[i * AVS_MAXS + s];
+        const int f = sl >> 1;
+        const int j = (sl & 1) ? P.faceL[f] : P.faceR[f];
+        if (j < 0) continue;
+        const double sgn = (sl & 1) ? -1.0 : 1.0;
+        const double* An = P.An + (size_t)f * D;
+        double Aa = 0.0;
+        for (int d = 0; d < D; ++d) Aa += An[d] * An[d];
+        Aa = sqrt(Aa);
+        double ns_[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) ns_[d] = sgn * An[d] / Aa;
+        A G[NW];
+        euler_flux_a<D, A>(P.Wt + (size_t)j * NW, ns_, G);
+        const double r = P.rad[(size_t)i * AVS_MAXS + s];
+        for (int c = 0; c < NW; ++c)
+            rhs[c] += -0.5 * Aa * ((double)G[c] - P.Gn[((size_t)i * AVS_MAXS + s) * NW + c]) +
+                      0.5 * r * P.dW[(size_t)j * NW + c];
+    }
+    const double dg = P.diag[i];
+    for (int c = 0; c < NW; ++c) {
+        const double d = rhs[c] / dg;
+        P.dW[(size_t)i * NW + c] = d;
+        P.Wt[(size_t)i * NW + c] = P.Wn[(size_t)i * NW + c] + d;
+    }
+}
+
+// Per cell: Shakhov state of W~ with the lagged heat flux of f^n (R3);
+// upd[0] = V/dt + V/tau~, upd[1] = tau~, upd[2] = V.
+template <int D, typename T>
+__global__ void k_imp_state(CellP<D, T> P, const double* Wt)
+{
+    constexpr int NM = NMom<D>::v, NW = D + 2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.Nc) return;
+    const double* Wi = P.Win + (size_t)i * NW;
+    double Vc[3] = {0.0, 0.0, 0.0}, m[NM];
+    for (int d = 0; d < D; ++d) Vc[d] = (double)((T)Wi[1 + d] / (T)Wi[0]);
+    for (int k = 0; k < NM; ++k) m[k] = P.mom[(size_t)i * NM + k];
+    T rn, Un[3], RTn, qn[3];
+    state_from_raw<D, T>(m, Vc, rn, Un, RTn, qn);
+    double rhod, Ud[3], RTd;
+    prim<D>(Wt + (size_t)i * NW, rhod, Ud, RTd);
+    if (!(rhod > 0.0) || !(RTd > 0.0)) atomicOr(P.err, 1);
+    const T rho = (T)rhod, RT = (T)RTd;
+    T U[3];
+    for (int d = 0; d < 3; ++d) U[d] = (T)Ud[d];
+    CellPar<T> cp;
+    const T tau = tau_vhs<T>(rho, RT, (T)P.R, (T)P.mu_ref, (T)P.T_ref, (T)P.omega);
+    cp.eq = make_eq_a<D, T, T>(rho, U, RT, qn, (T)P.Pr);
+    const T V = (T)P.vol[i];
+    cp.upd[0] = V / (T)P.dt + V / tau;
+    cp.upd[1] = tau;
+    cp.upd[2] = V;
+    cp.upd[3] = T(0);
+    for (int d = 0; d < 3; ++d) cp.Vn[d] = T(0);
+    P.par[i] = cp;
+}
+
+// Per cell and node: microscopic residual Res = V (g~ - phi^n) / tau~ - N,
+// N the net flux of the cell's faces (written over the f^{n+1} buffer).
+template <int D, typename T, int NT>
+__global__ void __launch_bounds__(NT) k_imp_res(CellP<D, T> P)
+{
+    constexpr int NA = NArr<D>::v;
+    __shared__ int fs[AVS_MAXS];
+    __shared__ T sg[AVS_MAXS];
+    __shared__ CellPar<T> cp;
+    const int i = blockIdx.x, tid = threadIdx.x;
+    const int ns = P.nslot[i];
+    if (tid < ns) {
+        const int sl = P.slot[i * AVS_MAXS + tid];
+        fs[tid] = sl >> 1;
+        sg[tid] = (sl & 1) ? T(-1) : T(1);
+    }
+    if (tid == 32 % NT) cp = P.par[i];
+    __syncthreads();
+    const T* fi = P.fin + (size_t)i * P.cstride;
+    T* ro = P.fout + (size_t)i * P.cstride;
+    const T V = cp.upd[2], tau = cp.upd[1];
+    for (int k = tid; k < P.Nv; k += NT) {
+        T x[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
+        T gG, gH;
+        eq_eval<D>(cp.eq, x, gG, gH);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            T N = T(0);
+            for (int s = 0; s < ns; ++s) N += sg[s] * P.F[((size_t)fs[s] * NA + a) * P.Nvp + k];
+            const T g = a == 0 ? gG : gH;
+            ro[(size_t)a * P.Nvp + k] = V * (g - fi[(size_t)a * P.Nvp + k]) / tau - N;
+        }
+    }
+}
+
+// One colour of a microscopic sweep: dphi_i = (Res_i - sum_{xi.n<0} (xi.n) dphi_j)
+// / (V/dt + V/tau~ + sum_{xi.n>=0} xi.n), every node and array.
+template <int D, typename T>
+__global__ void k_imp_micro(CellP<D, T> P, const T* __restrict__ res, T* dphi, const double* __restrict__ An_d,
+                            const T* __restrict__ An, const int* __restrict__ faceL, const int* __restrict__ faceR,
+                            const int* __restrict__ clist, int c0)
+{
+    constexpr int NA = NArr<D>::v;
+    const int i = clist[c0 + blockIdx.x];
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= P.Nv) return;
+    const int ns = P.nslot[i];
+    T x[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
+    T out = T(0);
+    T sn[AVS_MAXS];
+    int nb[AVS_MAXS];
+    for (int s = 0; s < ns; ++s) {
+        const int sl = P.slot[i * AVS_MAXS + s];
+        const int f = sl >> 1;
+        T v = dot_rn<D>(x, An + (size_t)f * D);
+        if (sl & 1) v = -v;
+        sn[s] = v;
+        nb[s] = (sl & 1) ? faceL[f] : faceR[f];
+        if (v >= T(0)) out += v;
+    }
+    const T dg = P.par[i].upd[0] + out;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        T acc = res[((size_t)i * NA + a) * P.Nvp + k];
+        for (int s = 0; s < ns; ++s)
+            if (nb[s] >= 0 && sn[s] < T(0)) acc -= sn[s] * dphi[((size_t)nb[s] * NA + a) * P.Nvp + k];
+        dphi[((size_t)i * NA + a) * P.Nvp + k] = acc / dg;
+    }
+    (void)An_d;
+}
+
+// f^{n+1} = f^n + dphi (pad nodes zero)
+template <typename T>
+__global__ void k_imp_finish(int Nrows, int Nv, int Nvp, const T* __restrict__ fin, const T* __restrict__ dphi,
+                             T* fout)
+{
+    const int r = blockIdx.x;
+    for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < Nvp; k += gridDim.y * blockDim.x)
+        fout[(size_t)r * Nvp + k] = k < Nv ? fin[(size_t)r * Nvp + k] + dphi[(size_t)r * Nvp + k] : T(0);
+    (void)Nrows;
+}
+
+template <int D, typename T>
+static cudaError_t launch_step_implicit_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout,
+                                          double dt, int k_macro, int k_micro)
+{
+    const bool f32 = sizeof(T) == 4;
+    const int NA = NArr<D>::v, NW = D + 2;
+    cudaError_t e = face_stage_t<D, T>(c, fin, Win, dt);
+    if (e != cudaSuccess) return e;
+    using A = T;     // macroscopic sweep arithmetic: FP32 in the mixed form, FP64 in the FP64 form
+    ImpP I;
+    I.Nc = c->Nc;
+    I.dt = dt;
+    I.R = c->cfg.R;
+    I.mu_ref = c->mu_ref;
+    I.T_ref = c->cfg.T_ref;
+    I.omega = c->cfg.omega;
+    I.slot = c->slot;
+    I.nslot = c->nslot;
+    I.faceL = c->faceL;
+    I.faceR = c->faceR;
+    I.An = c->An_d;
+    I.rL = c->rL_d;
+    I.rR = c->rR_d;
+    I.vol = c->vol;
+    I.AF = c->AFf;
+    I.Wn = Win;
+    I.Wt = Wout;
+    I.dW = c->imp_dW;
+    I.diag = c->imp_diag;
+    I.rhs0 = c->imp_rhs0;
+    I.rad = c->imp_rad;
+    I.Gn = c->imp_Gn;
+    I.clist = c->clist;
+    const int cb = (c->Nc + 127) / 128;
+    k_imp_setup<D, A><<<cb, 128, 0, c->stream>>>(I);
+    c->launches += 1;
+    const int nc = c->ncolor;
+    for (int it = 0; it < k_macro; ++it)
+        for (int dir = 0; dir < 2; ++dir)
+            for (int q = 0; q < nc; ++q) {
+                const int col = dir == 0 ? q : nc - 1 - q;
+                const int c0 = c->cstart[col], c1 = c->cstart[col + 1];
+                if (c1 > c0) {
+                    k_imp_macro<D, A><<<(c1 - c0 + 127) / 128, 128, 0, c->stream>>>(I, c0, c1);
+                    c->launches += 1;
+                }
+            }
+    // microscopic system
+    const T* xi = f32 ? (const T*)c->xi_f : (const T*)c->xi_d;
+    const T* w = f32 ? (const T*)c->w_f : (const T*)c->w_d;
+    CellP<D, T> Q;
+    Q.Nc = c->Nc;
+    Q.Nv = c->Nv;
+    Q.Nvp = c->Nvp;
+    Q.cstride = (size_t)NA * c->Nvp;
+    Q.dt = dt;
+    Q.R = c->cfg.R;
+    Q.Pr = c->cfg.Pr;
+    Q.omega = c->cfg.omega;
+    Q.mu_ref = c->mu_ref;
+    Q.T_ref = c->cfg.T_ref;
+    Q.fin = (const T*)fin;
+    Q.fout = (T*)fout;
+    Q.F = (const T*)c->flux;
+    Q.AF = c->AFf;
+    Q.Win = Win;
+    Q.Wout = Wout;
+    Q.mom = c->cmom;
+    Q.par = (CellPar<T>*)c->cpar;
+    Q.xi = xi;
+    Q.w = w;
+    Q.slot = c->slot;
+    Q.nslot = c->nslot;
+    Q.vol = c->vol;
+    Q.err = c->dev_err;
+    constexpr int NT = 128;
+    if (!c->mom_valid) {
+        k_raw_moments<D, T, NT, VW<T>::v><<<c->Nc, NT, 0, c->stream>>>(Q);
+        c->launches += 1;
+    }
+    k_imp_state<D, T><<<cb, 128, 0, c->stream>>>(Q, Wout);
+    k_imp_res<D, T, NT><<<c->Nc, NT, 0, c->stream>>>(Q);
+    c->launches += 2;
+    T* dphi = (T*)c->flux;                    // the face flux has been used: its buffer holds dphi
+    e = cudaMemsetAsync(dphi, 0, (size_t)c->Nc * NA * c->Nvp * sizeof(T), c->stream);
+    if (e != cudaSuccess) return e;
+    const int nyb = (c->Nv + 127) / 128;
+    const T* Anv = f32 ? (const T*)c->An_f : (const T*)c->An_d;
+    for (int it = 0; it < k_micro; ++it)
+        for (int dir = 0; dir < 2; ++dir)
+            for (int q = 0; q < nc; ++q) {
+                const int col = dir == 0 ? q : nc - 1 - q;
+                const int c0 = c->cstart[col], c1 = c->cstart[col + 1];
+                if (c1 > c0) {
+                    dim3 g(c1 - c0, nyb);
+                    k_imp_micro<D, T><<<g, 128, 0, c->stream>>>(Q, (const T*)fout, dphi, c->An_d, Anv, c->faceL,
+                                                                c->faceR, c->clist, c0);
+                    c->launches += 1;
+                }
+            }
+    dim3 gf(c->Nc * NA, (c->Nvp + 255) / 256 < 8 ? (c->Nvp + 255) / 256 : 8);
+    k_imp_finish<T><<<gf, 256, 0, c->stream>>>(c->Nc * NA, c->Nv, c->Nvp, (const T*)fin, dphi, (T*)fout);
+    c->launches += 1;
+    c->mom_valid = 0;          // the carried moments are of f^n
+    (void)NW;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt,
+                                 int k_macro, int k_micro)
+{
+    if (c->D == 2)
+        return c->mixed ? launch_step_implicit_t<2, float>(c, fin, fout, Win, Wout, dt, k_macro, k_micro)
+                        : launch_step_implicit_t<2, double>(c, fin, fout, Win, Wout, dt, k_macro, k_micro);
+    return c->mixed ? launch_step_implicit_t<3, float>(c, fin, fout, Win, Wout, dt, k_macro, k_micro)
+                    : launch_step_implicit_t<3, double>(c, fin, fout, Win, Wout, dt, k_macro, k_micro);
+}
+
+cudaError_t launch_face_stage(avs_ctx* c, const void* fin, const double* Win, double dt)
+{
+    if (c->D == 2)
+        return c->mixed ? face_stage_t<2, float>(c, fin, Win, dt) : face_stage_t<2, double>(c, fin, Win, dt);
+    return c->mixed ? face_stage_t<3, float>(c, fin, Win, dt) : face_stage_t<3, double>(c, fin, Win, dt);
 }
 
 cudaError_t launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt)
