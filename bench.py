@@ -53,6 +53,8 @@ def _args():
                     help="cylinder (the benchmark case) or another configuration")
     ap.add_argument("--oracle-threads", type=int, default=0,
                     help="host threads of the CPU oracle (default: all cores)")
+    ap.add_argument("--implicit", type=float, default=0.0, metavar="CFL",
+                    help="time the implicit IUGKS step (60 macro + 2 micro SGS iterations) at this CFL instead")
     ap.add_argument("--sweep", action="store_true",
                     help="kernel sweep over cell and node counts (FP32 and FP64 steps), one JSON line per case")
     return ap.parse_args()
@@ -269,9 +271,15 @@ def run_gpu(args):
     # are not carried on from step to step; see the design notes on long runs)
     W0 = torch.from_numpy(np.ascontiguousarray(w.W_init)).to("cuda")
 
+    def advance(ctx):
+        if args.implicit > 0:
+            ctx.step_implicit(nu, cfl=args.implicit)
+        else:
+            ctx.step(nu)
+
     def bench_step(ctx, updates):
         ctx.init_field(W0)
-        ctx.step(nu)
+        advance(ctx)
         updates.append(Nc * ctx.Nv * nu)
         return ctx.adapt()
 
@@ -301,7 +309,7 @@ def run_gpu(args):
     for j in range(args.steps):
         g.init_field(W0)
         ev_s[j].record(stream)
-        g.step(nu)
+        advance(g)
         ev_e[j].record(stream)
         upd.append(Nc * g.Nv * nu)
         step_cells.append(Nc * g.Nv)
@@ -324,9 +332,13 @@ def run_gpu(args):
     achieved = bytes_per_cn * cn_per_launch / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     # ncu traffic of the step, measured on the cylinder family (2D, mixed)
-    traffic = _traffic("mixed", Nc, cn_per_launch / Nc) if _WL.startswith("cylinder") else None
+    traffic = (_traffic("mixed", Nc, cn_per_launch / Nc) if _WL.startswith("cylinder") and args.implicit <= 0
+               else None)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": f"UGKS step: k_grad + k_face + k_cell_state + k_cell <{w.D},float>",
+            "traffic": traffic,
+            "kernel": (f"implicit UGKS step: k_grad + k_face + k_imp_setup + k_imp_macro + k_imp_state + k_imp_res"
+                       f" + k_imp_micro + k_imp_finish <{w.D},float>" if args.implicit > 0 else
+                       f"UGKS step: k_grad + k_face + k_cell_state + k_cell <{w.D},float>"),
             "peak_source": peak_kind,
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
             "peak_spec_gbs": 8000.0, "frac_of_spec": achieved / 8000.0}
@@ -342,7 +354,7 @@ def run_gpu(args):
         te0 = time.perf_counter()
         for _ in range(ke):
             g.init_field(Wp)          # h2d of the step's input W
-            g.step(nu)
+            advance(g)
             e_upd.append(Nc * g.Nv * nu)
             g.adapt()
             g.moments(out_W=Wout)     # d2h of the step's result
@@ -385,6 +397,8 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": w.name, "cells": Nc, "velocity_nodes": g.Nv,
                            "ugks_steps_per_step": nu, "precision": "mixed (f FP32, sums FP64)",
+                           "time_step": (f"implicit IUGKS, CFL {args.implicit}, 60 macro + 2 micro SGS iterations"
+                                         if args.implicit > 0 else "explicit, CFL 0.8"),
                            "adaptation": "learned proposer, full criterion every 4th adaptation",
                            "l2": f"inputs larger than L2 (f = {f_mb:.0f} MB per buffer)",
                            "parallelism": f"replicas x{ws}"},

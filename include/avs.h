@@ -141,8 +141,11 @@ avs_status ugks_step_dt(avs_ctx *ctx, int nsteps, double dt);
  * Eq. (SGS_phi) for phi^{n+1} - phi^n, each solved by k_macro / k_micro
  * symmetric Gauss-Seidel iterations (a forward and a backward sweep over a
  * greedy cell colouring).  Boundary faces enter both diagonals with a fixed
- * ghost state.  The paper recommends k_macro = 60, k_micro = 2.  Errors:
- * EINVAL (nsteps < 0, dt <= 0, negative sweep counts), ECUDA. */
+ * ghost state.  The paper recommends k_macro = 60, k_micro = 2.  The
+ * macroscopic solve is one cooperative launch with a bounded grid barrier
+ * between colour passes.  Does not synchronise.  Errors: EINVAL (nsteps < 0,
+ * dt <= 0, negative sweep counts), ECUDA; at the next blocking call ENUMERIC
+ * or ETIMEOUT (a grid barrier gave up). */
 avs_status ugks_step_implicit(avs_ctx *ctx, int nsteps, double dt, int k_macro, int k_micro);
 
 /* One AVS adaptation (Sec. 3): moments of f (Eq. 7), criterion M_k
@@ -230,6 +233,15 @@ avs_status avs_mlp_grad(avs_ctx *ctx, const float *X, const float *Y, int n, flo
 avs_status avs_features(avs_ctx *ctx, float *X_out, float *Y_out);
 /* iters SGD steps on the current state's features and labels; last loss out. */
 avs_status avs_mlp_train(avs_ctx *ctx, int iters, float lr, float *loss_out);
+
+/* Self-test of the bounded grid barrier that the implicit macroscopic sweep
+ * uses between colour passes: one cooperative launch of `blocks` blocks
+ * (1..number of SMs) passes `rounds` barriers; with short_by > 0 the last
+ * barrier waits for short_by arrivals that never come, so each block gives up
+ * after its poll limit (about a second) and the call returns AVS_ETIMEOUT with
+ * the context still usable.  *passed (host) = barriers passed, summed over
+ * blocks.  Blocking.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+avs_status avs_grid_barrier_check(avs_ctx *ctx, int blocks, int rounds, int short_by, int *passed);
 
 /* Measured FMA throughput of the current GPU (GFLOP/s, 2 flops per FMA):
  * kind 0 FP32, 1 FP64, 2 FP32 pairs with the packed two-lane FMA.  Independent

@@ -28,7 +28,7 @@ EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs
             "avs_criterion", "avs_get_tree", "avs_get_f", "avs_get_f_cells", "avs_set_f", "avs_sync",
             "avs_kernel_launches",
             "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
-            "avs_mlp_train", "avs_measure_fma_peak"]
+            "avs_mlp_train", "avs_measure_fma_peak", "avs_grid_barrier_check"]
 MLP_NPARAM = 4996
 
 
@@ -103,6 +103,7 @@ def load():
         "avs_features": (C.c_int, [vp, dp, dp]),
         "avs_mlp_train": (C.c_int, [vp, C.c_int, C.c_float, C.POINTER(C.c_float)]),
         "avs_measure_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+        "avs_grid_barrier_check": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     }
     for name, (rt, args) in sig.items():
         fn = getattr(L, name)
@@ -223,6 +224,13 @@ class AVS:
             dt = self.dt(cfl)
         self._ck(self.L.ugks_step_implicit(self.h, int(nsteps), float(dt), int(k_macro), int(k_micro)))
         return dt
+
+    def grid_barrier_check(self, blocks, rounds, short_by=0):
+        """Barriers passed (summed over blocks) by the bounded grid-barrier
+        self-test; raises AVSError(AVS_ETIMEOUT) when short_by > 0."""
+        out = C.c_int()
+        self._ck(self.L.avs_grid_barrier_check(self.h, int(blocks), int(rounds), int(short_by), C.byref(out)))
+        return out.value
 
     def step(self, nsteps=1, dt=None, cfl=None):
         if dt is not None:

@@ -55,8 +55,8 @@ void free_all(avs_ctx* c)
                     c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
                     c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
                     c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mhi, c->Mthr, c->stage, c->dev_err,
-                    c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->rmom, c->cpar, c->clist, c->imp_dW, c->imp_rhs0, c->imp_diag, c->imp_rad,
-                    c->imp_Gn, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
+                    c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->rmom, c->cpar, c->clist, c->cstart_d, c->imp_dW, c->imp_rhs0, c->imp_diag, c->imp_Wta,
+                    c->imp_co, c->imp_nint, c->imp_bar, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
                     c->mlp_X, c->mlp_Y, c->mlp_logits, c->mlp_list, c->mlp_count, c->M_alt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -111,6 +111,10 @@ avs_status read_err(avs_ctx* c)
     int e = 0;
     CK(cudaMemcpyAsync(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (e & 2) {
+        CK(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+        return fail(c, AVS_ETIMEOUT, "a grid barrier of the implicit macroscopic sweep gave up");
+    }
     if (e & 1) {
         CK(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
         return fail(c, AVS_ENUMERIC, "non-positive density or temperature in a step");
@@ -353,8 +357,8 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
         dalloc(&c->AFf, (size_t)Nf * (D + 2)) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * avs::NMom<3>::v) ||
         dalloc((unsigned char**)&c->cpar, (size_t)Nc * AVS_CELLPAR_BYTES) || dalloc(&c->clist, Nc) ||
         dalloc(&c->imp_dW, (size_t)Nc * (D + 2)) || dalloc(&c->imp_rhs0, (size_t)Nc * (D + 2)) ||
-        dalloc(&c->imp_diag, Nc) || dalloc(&c->imp_rad, (size_t)Nc * AVS_MAXS) ||
-        dalloc(&c->imp_Gn, (size_t)Nc * AVS_MAXS * (D + 2)))
+        dalloc(&c->imp_diag, Nc) || dalloc(&c->imp_Wta, (size_t)Nc * (D + 2)) ||
+        dalloc(&c->imp_co, ncs * AVS_IMPSLOT_BYTES) || dalloc(&c->imp_nint, Nc) || dalloc(&c->imp_bar, 1))
         return fail(c, AVS_ENOMEM, "mesh arrays");
     cudaStream_t s = c->stream;
     CK(up(c->faceL, std::vector<int>(m->faceL, m->faceL + Nf), s));
@@ -405,6 +409,8 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
         std::vector<int> pos(c->cstart.begin(), c->cstart.end() - 1), cl(Nc);
         for (int i = 0; i < Nc; ++i) cl[pos[col[i]]++] = i;
         CK(up(c->clist, cl, s));
+        if (dalloc(&c->cstart_d, c->ncolor + 1)) return fail(c, AVS_ENOMEM, "colour offsets");
+        CK(up(c->cstart_d, c->cstart, s));
     }
     CK(cudaStreamSynchronize(s));    // host vectors go out of scope
     return AVS_OK;
@@ -609,6 +615,24 @@ avs_status ugks_step_implicit(avs_ctx* c, int nsteps, double dt, int k_macro, in
         c->wcur ^= 1;
     }
     return AVS_OK;
+}
+
+avs_status avs_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int short_by, int* passed)
+{
+    if (!c || blocks <= 0 || rounds <= 0 || short_by < 0 || !passed) return AVS_EINVAL;
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (blocks > nsm) return fail(c, AVS_EINVAL, "grid barrier check: more blocks than SMs");
+    int* d = nullptr;
+    if (dalloc(&d, 1) != cudaSuccess) return fail(c, AVS_ENOMEM, "grid barrier check");
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_grid_barrier_check(c, blocks, rounds, short_by, d);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(passed, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    CK(e);
+    return read_err(c);
 }
 
 avs_status ugks_step(avs_ctx* c, int nsteps, double cfl, double* dt_out)

@@ -12,6 +12,7 @@
 
 #define AVS_NT 256            // threads per block of the per-cell kernels
 #define AVS_CELLPAR_BYTES 256 // bytes per cell of the collision parameters (CellPar)
+#define AVS_IMPSLOT_BYTES 96  // bytes per slot record of the implicit macroscopic sweep
 
 struct avs_ctx {
     avs_config cfg;
@@ -87,10 +88,13 @@ struct avs_ctx {
     int ncolor = 0;
     std::vector<int> cstart;                         // [ncolor+1] offsets into clist (host)
     int *clist = nullptr;                            // [Nc] cells by colour, ascending within a colour
-    double *imp_dW = nullptr, *imp_rhs0 = nullptr;   // [Nc][D+2]
+    int *cstart_d = nullptr;                         // [ncolor+1] the same offsets on the device
+    double *imp_dW = nullptr, *imp_rhs0 = nullptr;   // [Nc][D+2] (dW and -sum sgn A F, in the sweep type)
+    double *imp_Wta = nullptr;                       // [Nc][D+2] W~ in FP32 (mixed form)
     double *imp_diag = nullptr;                      // [Nc]
-    double *imp_rad = nullptr;                       // [Nc][MAXS]
-    double *imp_Gn = nullptr;                        // [Nc][MAXS][D+2]
+    unsigned char *imp_co = nullptr;                 // [Nc][MAXS] interior slot records (AVS_IMPSLOT_BYTES each)
+    unsigned char *imp_nint = nullptr;               // [Nc] interior slots per cell in sweep order
+    unsigned *imp_bar = nullptr;                     // grid barrier counter of the macroscopic solve
 
     // ---- learned proposer (MLP 8-64-64-4)
     float *mlp_P = nullptr;                          // FP32 master parameters
@@ -115,6 +119,7 @@ int round_up(int n, int m);
 
 // ---- launchers (avs_step.cu)
 cudaError_t launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
+cudaError_t launch_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int short_by, int* passed_dev);
 cudaError_t launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt,
                                  int k_macro, int k_micro);
 

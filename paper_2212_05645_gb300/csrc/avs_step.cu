@@ -1030,27 +1030,38 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
 // the other colours as they stand, which is the sequential sweep in the order
 // "colour 0, colour 1, ..." (forward) and back (backward).
 
+// Euler flux of a conserved state W through the unit normal n (monatomic gas).
 template <int D, typename A>
-__device__ __forceinline__ void euler_flux_a(const double* Wd, const double* n, A* G)
+__device__ __forceinline__ void euler_flux_n(const A* W, const A* n, A* G)
 {
-    constexpr int NW = D + 2;
-    A W[NW];
-#pragma unroll
-    for (int c = 0; c < NW; ++c) W[c] = (A)Wd[c];
     const A rho = W[0];
     A m2 = A(0), un = A(0);
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         m2 += W[1 + d] * W[1 + d];
-        un += (W[1 + d] / rho) * (A)n[d];
+        un += (W[1 + d] / rho) * n[d];
     }
     const A p = rho * ((W[D + 1] - A(0.5) * m2 / rho) / (A(1.5) * rho));
     G[0] = rho * un;
 #pragma unroll
-    for (int d = 0; d < D; ++d) G[1 + d] = W[1 + d] * un + p * (A)n[d];
+    for (int d = 0; d < D; ++d) G[1 + d] = W[1 + d] * un + p * n[d];
     G[D + 1] = (W[D + 1] + p) * un;
 }
 
+// Interior face slot of a cell, in sweep order: the slot's outward unit normal
+// n, -A/2, A r/2 (r the face's spectral radius) and the Euler flux of the
+// neighbour's W^n through n, so that a sweep only evaluates G(W~_j).
+template <typename A>
+struct ImpSlot {
+    A n[3];
+    A nhA;
+    A hr;
+    A Gn[5];
+    int j;
+};
+static_assert(sizeof(ImpSlot<double>) <= AVS_IMPSLOT_BYTES, "slot record");
+
+template <typename A>
 struct ImpP {
     int Nc;
     double dt, R, mu_ref, T_ref, omega;
@@ -1063,25 +1074,28 @@ struct ImpP {
     const double* rR;
     const double* vol;
     const double* AF;
-    const double* Wn;        // W^n
-    double* Wt;              // W~ (the output W)
-    double* dW;              // [cell][NW]
-    double* diag;            // [cell]
-    double* rhs0;            // [cell][NW]
-    double* rad;             // [cell][MAXS]  A r of each face slot
-    double* Gn;              // [cell][MAXS][NW]  Euler flux of the neighbour's W^n through the slot's normal
-    const int* clist;        // cells by colour
+    const double* Wn;        // W^n [cell][NW]
+    double* Wt;              // W~ [cell][NW] (the output W)
+    A* dWa;                  // dW [cell][NW]
+    A* Wta;                  // W~ rounded to A [cell][NW]; aliases Wt when A is double
+    A* rhs;                  // [q][NW]  -sum sgn A F
+    A* dg;                   // [q]      V/dt + 1/2 sum A r
+    ImpSlot<A>* co;          // [q][MAXS] interior slots first
+    unsigned char* nint;     // [q] interior slots
+    const int* clist;        // cells by colour (q -> cell)
+    int* err;
 };
 
-// Per cell: diagonal V/dt + 1/2 sum A r, explicit part of the residual
-// -sum sgn A F, and per face slot A r and the neighbour's Euler flux at t^n.
-// r from the face's own orientation (L, R, n_LR) so both cells use one value.
+// Per cell, in sweep order q: diagonal V/dt + 1/2 sum A r over every slot,
+// explicit residual -sum sgn A F, and the interior slot records.  r from the
+// face's own orientation (L, R, n_LR), so both cells of a face use one value.
 template <int D, typename A>
-__global__ void k_imp_setup(ImpP P)
+__global__ void k_imp_setup(ImpP<A> P)
 {
     constexpr int NW = D + 2;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.Nc) return;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P.Nc) return;
+    const int i = P.clist[q];
     const int ns = P.nslot[i];
     const double* Wi = P.Wn + (size_t)i * NW;
     for (int c = 0; c < NW; ++c) {
@@ -1091,11 +1105,13 @@ __global__ void k_imp_setup(ImpP P)
             const double a = P.AF[(size_t)(sl >> 1) * NW + c];
             acc += (sl & 1) ? -a : a;
         }
-        P.rhs0[(size_t)i * NW + c] = -acc;
-        P.dW[(size_t)i * NW + c] = 0.0;
+        P.rhs[(size_t)q * NW + c] = (A)(-acc);
+        P.dWa[(size_t)i * NW + c] = A(0);
         P.Wt[(size_t)i * NW + c] = Wi[c];
+        P.Wta[(size_t)i * NW + c] = (A)Wi[c];
     }
     double dg = P.vol[i] / P.dt;
+    int nint = 0;
     for (int s = 0; s < ns; ++s) {
         const int sl = P.slot[i * AVS_MAXS + s];
         const int f = sl >> 1;
@@ -1121,57 +1137,150 @@ __global__ void k_imp_setup(ImpP P)
         for (int d = 0; d < D; ++d) un += 0.5 * (Ul[d] + Ur[d]) * n[d];
         const double mu = P.mu_ref * pow(RT / P.R / P.T_ref, P.omega);
         const double r = Aa * (fabs(un) + sqrt(5.0 / 3.0 * RT) + 2.0 * mu / (rho * dl));
-        P.rad[(size_t)i * AVS_MAXS + s] = r;
         dg += 0.5 * r;
         const int j = (sl & 1) ? L : R;
         if (j >= 0) {
-            double ns_[3] = {0, 0, 0};
-            for (int d = 0; d < D; ++d) ns_[d] = sgn * An[d] / Aa;
-            A G[NW];
-            euler_flux_a<D, A>(P.Wn + (size_t)j * NW, ns_, G);
-            for (int c = 0; c < NW; ++c) P.Gn[((size_t)i * AVS_MAXS + s) * NW + c] = (double)G[c];
+            ImpSlot<A> sc;
+            for (int d = 0; d < 3; ++d) sc.n[d] = d < D ? (A)(sgn * An[d] / Aa) : A(0);
+            sc.nhA = (A)(-0.5 * Aa);
+            sc.hr = (A)(0.5 * r);
+            A Wj[NW];
+            for (int c = 0; c < NW; ++c) Wj[c] = (A)P.Wn[(size_t)j * NW + c];
+            euler_flux_n<D, A>(Wj, sc.n, sc.Gn);
+            for (int c = NW; c < 5; ++c) sc.Gn[c] = A(0);
+            sc.j = j;
+            P.co[(size_t)q * AVS_MAXS + nint++] = sc;
         }
     }
-    P.diag[i] = dg;
+    P.dg[q] = (A)dg;
+    P.nint[q] = (unsigned char)nint;
 }
 
-// One colour of a macroscopic sweep: dW_i = (Res_i(W~) + 1/2 sum A r dW_j) / diag_i,
+// Grid-wide barrier of a cooperative launch, bounded: the block's thread 0
+// counts in and waits for the target count at most kGridSpin polls; a timeout
+// (or one seen in another block) sets error bit 2 and makes the block leave.
+// Monotone counter: the n-th barrier waits for n * gridDim.x arrivals.
+constexpr long long kGridSpin = 1ll << 21;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned target, int* err)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        for (long long it = 0; ld_acquire_u32(bar) < target; ++it) {
+            if (it >= kGridSpin || ((it & 255) == 255 && (*(volatile int*)err & 2))) {
+                atomicOr(err, 2);
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Self-test of the bounded grid barrier: `rounds` barriers, the last one
+// waiting for `short_by` arrivals more than the grid has (none when 0), each
+// passed barrier counted once per block in *passed.
+__global__ void k_grid_barrier_check(unsigned* bar, int rounds, int short_by, int* err, int* passed)
+{
+    unsigned gen = 0;
+    for (int r = 0; r < rounds; ++r) {
+        const unsigned target = ++gen * gridDim.x + (r == rounds - 1 ? (unsigned)short_by : 0u);
+        if (!grid_sync_bounded(bar, target, err)) return;
+        if (threadIdx.x == 0) atomicAdd(passed, 1);
+    }
+}
+
+cudaError_t launch_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int short_by, int* passed_dev)
+{
+    cudaError_t e = cudaMemsetAsync(c->imp_bar, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) return e;
+    unsigned* bar = c->imp_bar;
+    int* err = c->dev_err;
+    void* args[] = {&bar, &rounds, &short_by, &err, &passed_dev};
+    e = cudaLaunchCooperativeKernel((const void*)k_grid_barrier_check, dim3(blocks), dim3(128), args, 0, c->stream);
+    if (e == cudaSuccess) c->launches += 1;
+    return e;
+}
+
+// One cell of a macroscopic sweep: dW_i = (Res_i(W~) + 1/2 sum A r dW_j) / diag_i,
 // Res_i = -sum sgn A F - 1/2 sum A (G(W~_j) - G(W^n_j)) over the interior faces.
+// Arithmetic in A (FP32 in the mixed form, where dW is a small correction of
+// the FP64 W^n); W~ = W^n + dW in FP64.  The neighbours' values are read past
+// L1: other blocks wrote them before the last grid barrier.
 template <int D, typename A>
-__global__ void k_imp_macro(ImpP P, int c0, int c1)
+__device__ __forceinline__ void imp_macro_cell(const ImpP<A>& P, int q)
 {
     constexpr int NW = D + 2;
-    const int q = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= c1) return;
     const int i = P.clist[q];
-    const int ns = P.nslot[i];
-    double rhs[NW];
-    for (int c = 0; c < NW; ++c) rhs[c] = P.rhs0[(size_t)i * NW + c];
-    for (int s = 0; s < ns; ++s) {
-        const int sl = P.slot[i * AVS_MAXS + s];
-        const int f = sl >> 1;
-        const int j = (sl & 1) ? P.faceL[f] : P.faceR[f];
-        if (j < 0) continue;
-        const double sgn = (sl & 1) ? -1.0 : 1.0;
-        const double* An = P.An + (size_t)f * D;
-        double Aa = 0.0;
-        for (int d = 0; d < D; ++d) Aa += An[d] * An[d];
-        Aa = sqrt(Aa);
-        double ns_[3] = {0, 0, 0};
-        for (int d = 0; d < D; ++d) ns_[d] = sgn * An[d] / Aa;
-        A G[NW];
-        euler_flux_a<D, A>(P.Wt + (size_t)j * NW, ns_, G);
-        const double r = P.rad[(size_t)i * AVS_MAXS + s];
-        for (int c = 0; c < NW; ++c)
-            rhs[c] += -0.5 * Aa * ((double)G[c] - P.Gn[((size_t)i * AVS_MAXS + s) * NW + c]) +
-                      0.5 * r * P.dW[(size_t)j * NW + c];
+    const int n = P.nint[q];
+    A rhs[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) rhs[c] = P.rhs[(size_t)q * NW + c];
+    for (int s = 0; s < n; ++s) {
+        const ImpSlot<A> sc = P.co[(size_t)q * AVS_MAXS + s];
+        A Wj[NW], dWj[NW], G[NW];
+#pragma unroll
+        for (int c = 0; c < NW; ++c) {
+            Wj[c] = __ldcg(P.Wta + (size_t)sc.j * NW + c);
+            dWj[c] = __ldcg(P.dWa + (size_t)sc.j * NW + c);
+        }
+        euler_flux_n<D, A>(Wj, sc.n, G);
+#pragma unroll
+        for (int c = 0; c < NW; ++c) rhs[c] += sc.nhA * (G[c] - sc.Gn[c]) + sc.hr * dWj[c];
     }
-    const double dg = P.diag[i];
+    const A dg = P.dg[q];
+#pragma unroll
     for (int c = 0; c < NW; ++c) {
-        const double d = rhs[c] / dg;
-        P.dW[(size_t)i * NW + c] = d;
-        P.Wt[(size_t)i * NW + c] = P.Wn[(size_t)i * NW + c] + d;
+        const A d = rhs[c] / dg;
+        const double wt = P.Wn[(size_t)i * NW + c] + (double)d;
+        __stcg(P.dWa + (size_t)i * NW + c, d);
+        if constexpr (sizeof(A) == sizeof(double)) {
+            __stcg(P.Wt + (size_t)i * NW + c, wt);
+        } else {
+            P.Wt[(size_t)i * NW + c] = wt;
+            __stcg(P.Wta + (size_t)i * NW + c, (A)wt);
+        }
     }
+}
+
+// The whole macroscopic solve in one cooperative launch: k_macro symmetric
+// Gauss-Seidel iterations, each colour a grid-stride pass, a grid barrier
+// between passes.  A colour that follows itself (the turn of a symmetric
+// sweep) is skipped: its neighbours have not changed, so the pass would
+// rewrite the same values.
+template <int D, typename A, int NT>
+__global__ void __launch_bounds__(NT) k_imp_macro(ImpP<A> P, int k_macro, int ncolor, const int* __restrict__ cstart,
+                                                  unsigned* bar)
+{
+    const unsigned nb = gridDim.x;
+    unsigned gen = 0;
+    int prev = -1;
+    for (int it = 0; it < k_macro; ++it)
+        for (int dir = 0; dir < 2; ++dir)
+            for (int qq = 0; qq < ncolor; ++qq) {
+                const int col = dir == 0 ? qq : ncolor - 1 - qq;
+                if (col == prev) continue;
+                if (prev >= 0 && !grid_sync_bounded(bar, ++gen * nb, P.err)) return;
+                prev = col;
+                const int c1 = cstart[col + 1];
+                for (int q = cstart[col] + blockIdx.x * NT + threadIdx.x; q < c1; q += nb * NT)
+                    imp_macro_cell<D, A>(P, q);
+            }
 }
 
 // Per cell: Shakhov state of W~ with the lagged heat flux of f^n (R3);
@@ -1207,8 +1316,9 @@ __global__ void k_imp_state(CellP<D, T> P, const double* Wt)
 }
 
 // Per cell and node: microscopic residual Res = V (g~ - phi^n) / tau~ - N,
-// N the net flux of the cell's faces (written over the f^{n+1} buffer).
-template <int D, typename T, int NT>
+// N the net flux of the cell's faces (written over the f^{n+1} buffer).  V
+// consecutive nodes per thread as in k_cell; pad nodes get Res = 0.
+template <int D, typename T, int NT, int V>
 __global__ void __launch_bounds__(NT) k_imp_res(CellP<D, T> P)
 {
     constexpr int NA = NArr<D>::v;
@@ -1226,59 +1336,112 @@ __global__ void __launch_bounds__(NT) k_imp_res(CellP<D, T> P)
     __syncthreads();
     const T* fi = P.fin + (size_t)i * P.cstride;
     T* ro = P.fout + (size_t)i * P.cstride;
-    const T V = cp.upd[2], tau = cp.upd[1];
-    for (int k = tid; k < P.Nv; k += NT) {
-        T x[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
-        T gG, gH;
-        eq_eval<D>(cp.eq, x, gG, gH);
+    const T Vc = cp.upd[2], tau = cp.upd[1];
+    for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+        T x[V][D], wv[V];
+        load_nodes<D, V>(P, k0, x, wv);
+        T Nn[NA][V], fv[NA][V];
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            T N = T(0);
-            for (int s = 0; s < ns; ++s) N += sg[s] * P.F[((size_t)fs[s] * NA + a) * P.Nvp + k];
-            const T g = a == 0 ? gG : gH;
-            ro[(size_t)a * P.Nvp + k] = V * (g - fi[(size_t)a * P.Nvp + k]) / tau - N;
+            ldv_cg<T, V>(fi + (size_t)a * P.Nvp + k0, fv[a]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Nn[a][v] = T(0);
         }
+#pragma unroll
+        for (int s = 0; s < AVS_MAXS; ++s) {
+            if (s >= ns) break;
+            const T* Fs = P.F + (size_t)fs[s] * NA * P.Nvp + k0;
+            const T g = sg[s];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                T t[V];
+                ldv_cg<T, V>(Fs + (size_t)a * P.Nvp, t);
+#pragma unroll
+                for (int v = 0; v < V; ++v) Nn[a][v] += g * t[v];
+            }
+        }
+        T out[NA][V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            T gG, gH;
+            eq_eval<D>(cp.eq, x[v], gG, gH);
+            const bool real = k0 + v < P.Nv;
+            out[0][v] = real ? Vc * (gG - fv[0][v]) / tau - Nn[0][v] : T(0);
+            if (NA == 2) out[NA - 1][v] = real ? Vc * (gH - fv[NA - 1][v]) / tau - Nn[NA - 1][v] : T(0);
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) stv<T, V>(ro + (size_t)a * P.Nvp + k0, out[a]);
     }
 }
 
 // One colour of a microscopic sweep: dphi_i = (Res_i - sum_{xi.n<0} (xi.n) dphi_j)
-// / (V/dt + V/tau~ + sum_{xi.n>=0} xi.n), every node and array.
-template <int D, typename T>
-__global__ void k_imp_micro(CellP<D, T> P, const T* __restrict__ res, T* dphi, const double* __restrict__ An_d,
-                            const T* __restrict__ An, const int* __restrict__ faceL, const int* __restrict__ faceR,
-                            const int* __restrict__ clist, int c0)
+// / (V/dt + V/tau~ + sum_{xi.n>=0} xi.n), every node and array.  V consecutive
+// nodes per thread (16-byte vectors); a neighbour's row is read only where one
+// of the thread's nodes flows in from it.  Pad nodes get dphi = 0.
+template <int D, typename T, int NT, int V>
+__global__ void __launch_bounds__(NT) k_imp_micro(CellP<D, T> P, const T* __restrict__ res, T* dphi,
+                                                  const T* __restrict__ An, const int* __restrict__ faceL,
+                                                  const int* __restrict__ faceR, const int* __restrict__ clist, int c0)
 {
     constexpr int NA = NArr<D>::v;
+    __shared__ T sA[AVS_MAXS][D];
+    __shared__ int snb[AVS_MAXS];
     const int i = clist[c0 + blockIdx.x];
-    const int k = blockIdx.y * blockDim.x + threadIdx.x;
-    if (k >= P.Nv) return;
     const int ns = P.nslot[i];
-    T x[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) x[d] = P.xi[(size_t)k * D + d];
-    T out = T(0);
-    T sn[AVS_MAXS];
-    int nb[AVS_MAXS];
-    for (int s = 0; s < ns; ++s) {
-        const int sl = P.slot[i * AVS_MAXS + s];
+    const int tid = threadIdx.x;
+    if (tid < ns) {
+        const int sl = P.slot[i * AVS_MAXS + tid];
         const int f = sl >> 1;
-        T v = dot_rn<D>(x, An + (size_t)f * D);
-        if (sl & 1) v = -v;
-        sn[s] = v;
-        nb[s] = (sl & 1) ? faceL[f] : faceR[f];
-        if (v >= T(0)) out += v;
+#pragma unroll
+        for (int d = 0; d < D; ++d) sA[tid][d] = (sl & 1) ? -An[(size_t)f * D + d] : An[(size_t)f * D + d];
+        snb[tid] = (sl & 1) ? faceL[f] : faceR[f];
     }
-    const T dg = P.par[i].upd[0] + out;
+    __syncthreads();
+    const int k0 = (blockIdx.y * NT + tid) * V;
+    if (k0 >= P.Nv) return;
+    const T u0 = P.par[i].upd[0];
+    T x[V][D], wv[V];
+    load_nodes<D, V>(P, k0, x, wv);
+    T sn[AVS_MAXS][V], dg[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) dg[v] = T(0);
+#pragma unroll
+    for (int s = 0; s < AVS_MAXS; ++s) {
+        if (s >= ns) break;
+        T a[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) a[d] = sA[s][d];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            sn[s][v] = dot_rn<D>(x[v], a);
+            if (sn[s][v] >= T(0)) dg[v] += sn[s][v];
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) dg[v] = u0 + dg[v];
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
-        T acc = res[((size_t)i * NA + a) * P.Nvp + k];
-        for (int s = 0; s < ns; ++s)
-            if (nb[s] >= 0 && sn[s] < T(0)) acc -= sn[s] * dphi[((size_t)nb[s] * NA + a) * P.Nvp + k];
-        dphi[((size_t)i * NA + a) * P.Nvp + k] = acc / dg;
+        T acc[V];
+        ldv_cg<T, V>(res + ((size_t)i * NA + a) * P.Nvp + k0, acc);
+#pragma unroll
+        for (int s = 0; s < AVS_MAXS; ++s) {
+            if (s >= ns) break;
+            const int j = snb[s];
+            bool in = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) in |= sn[s][v] < T(0);
+            if (j < 0 || !in) continue;
+            T t[V];
+            ldv_cg<T, V>(dphi + ((size_t)j * NA + a) * P.Nvp + k0, t);
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (sn[s][v] < T(0)) acc[v] -= sn[s][v] * t[v];
+        }
+        T o[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = k0 + v < P.Nv ? acc[v] / dg[v] : T(0);
+        stv<T, V>(dphi + ((size_t)i * NA + a) * P.Nvp + k0, o);
     }
-    (void)An_d;
 }
 
 // f^{n+1} = f^n + dphi (pad nodes zero)
@@ -1301,7 +1464,7 @@ static cudaError_t launch_step_implicit_t(avs_ctx* c, const void* fin, void* fou
     cudaError_t e = face_stage_t<D, T>(c, fin, Win, dt);
     if (e != cudaSuccess) return e;
     using A = T;     // macroscopic sweep arithmetic: FP32 in the mixed form, FP64 in the FP64 form
-    ImpP I;
+    ImpP<A> I;
     I.Nc = c->Nc;
     I.dt = dt;
     I.R = c->cfg.R;
@@ -1319,26 +1482,41 @@ static cudaError_t launch_step_implicit_t(avs_ctx* c, const void* fin, void* fou
     I.AF = c->AFf;
     I.Wn = Win;
     I.Wt = Wout;
-    I.dW = c->imp_dW;
-    I.diag = c->imp_diag;
-    I.rhs0 = c->imp_rhs0;
-    I.rad = c->imp_rad;
-    I.Gn = c->imp_Gn;
+    I.dWa = (A*)c->imp_dW;
+    I.Wta = f32 ? (A*)c->imp_Wta : (A*)Wout;
+    I.rhs = (A*)c->imp_rhs0;
+    I.dg = (A*)c->imp_diag;
+    I.co = (ImpSlot<A>*)c->imp_co;
+    I.nint = c->imp_nint;
     I.clist = c->clist;
+    I.err = c->dev_err;
     const int cb = (c->Nc + 127) / 128;
     k_imp_setup<D, A><<<cb, 128, 0, c->stream>>>(I);
     c->launches += 1;
     const int nc = c->ncolor;
-    for (int it = 0; it < k_macro; ++it)
-        for (int dir = 0; dir < 2; ++dir)
-            for (int q = 0; q < nc; ++q) {
-                const int col = dir == 0 ? q : nc - 1 - q;
-                const int c0 = c->cstart[col], c1 = c->cstart[col + 1];
-                if (c1 > c0) {
-                    k_imp_macro<D, A><<<(c1 - c0 + 127) / 128, 128, 0, c->stream>>>(I, c0, c1);
-                    c->launches += 1;
-                }
-            }
+    if (k_macro > 0) {
+        // one cooperative launch: every block resident, so the bounded grid
+        // barriers between colour passes can complete
+        constexpr int NTM = 128;
+        int maxcol = 0;
+        for (int k = 0; k < nc; ++k) maxcol = std::max(maxcol, c->cstart[k + 1] - c->cstart[k]);
+        int dev = 0, nsm = 0, occ = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_imp_macro<D, A, NTM>, NTM, 0);
+        if (e != cudaSuccess) return e;
+        const int nblk = std::max(1, std::min(nsm * std::max(occ, 1), (maxcol + NTM - 1) / NTM));
+        e = cudaMemsetAsync(c->imp_bar, 0, sizeof(unsigned), c->stream);
+        if (e != cudaSuccess) return e;
+        int km = k_macro, ncol = nc;
+        const int* cs = c->cstart_d;
+        unsigned* bar = c->imp_bar;
+        void* args[] = {&I, &km, &ncol, &cs, &bar};
+        e = cudaLaunchCooperativeKernel((const void*)k_imp_macro<D, A, NTM>, dim3(nblk), dim3(NTM), args, 0,
+                                        c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 1;
+    }
     // microscopic system
     const T* xi = f32 ? (const T*)c->xi_f : (const T*)c->xi_d;
     const T* w = f32 ? (const T*)c->w_f : (const T*)c->w_d;
@@ -1373,22 +1551,26 @@ static cudaError_t launch_step_implicit_t(avs_ctx* c, const void* fin, void* fou
         c->launches += 1;
     }
     k_imp_state<D, T><<<cb, 128, 0, c->stream>>>(Q, Wout);
-    k_imp_res<D, T, NT><<<c->Nc, NT, 0, c->stream>>>(Q);
+    k_imp_res<D, T, NT, VW<T>::v><<<c->Nc, NT, 0, c->stream>>>(Q);
     c->launches += 2;
     T* dphi = (T*)c->flux;                    // the face flux has been used: its buffer holds dphi
     e = cudaMemsetAsync(dphi, 0, (size_t)c->Nc * NA * c->Nvp * sizeof(T), c->stream);
     if (e != cudaSuccess) return e;
-    const int nyb = (c->Nv + 127) / 128;
+    constexpr int VM = VW<T>::v;
+    const int nyb = (c->Nv + NT * VM - 1) / (NT * VM);
     const T* Anv = f32 ? (const T*)c->An_f : (const T*)c->An_d;
+    int prev = -1;
     for (int it = 0; it < k_micro; ++it)
         for (int dir = 0; dir < 2; ++dir)
             for (int q = 0; q < nc; ++q) {
                 const int col = dir == 0 ? q : nc - 1 - q;
+                if (col == prev) continue;      // the turn of a symmetric sweep: same inputs, same values
+                prev = col;
                 const int c0 = c->cstart[col], c1 = c->cstart[col + 1];
                 if (c1 > c0) {
                     dim3 g(c1 - c0, nyb);
-                    k_imp_micro<D, T><<<g, 128, 0, c->stream>>>(Q, (const T*)fout, dphi, c->An_d, Anv, c->faceL,
-                                                                c->faceR, c->clist, c0);
+                    k_imp_micro<D, T, NT, VM><<<g, NT, 0, c->stream>>>(Q, (const T*)fout, dphi, Anv, c->faceL,
+                                                                        c->faceR, c->clist, c0);
                     c->launches += 1;
                 }
             }

@@ -65,3 +65,25 @@ def test_implicit_sweep_counts_and_arguments():
     with pytest.raises(avs.AVSError):
         g.step_implicit(1, dt=1e-3, k_macro=-1)
     g.close()
+
+
+def test_grid_barrier_is_bounded():
+    """The grid barrier between the colour passes of the macroscopic solve:
+    every barrier passes when all blocks arrive; one that waits for arrivals
+    that never come gives up within its poll limit, the call reports
+    AVS_ETIMEOUT, and the context still steps correctly afterwards."""
+    import time
+    avs = need_gpu()
+    w = CASES["box"]("fp64")
+    r, g = pair(w, avs, amp=1e-2)
+    assert g.grid_barrier_check(16, 50) == 16 * 50
+    t0 = time.perf_counter()
+    with pytest.raises(avs.AVSError) as ei:
+        g.grid_barrier_check(4, 3, short_by=1)
+    assert ei.value.status == -4                     # AVS_ETIMEOUT
+    assert time.perf_counter() - t0 < 60
+    dt = r.dt(1.0)
+    r.step_implicit(dt)
+    g.step_implicit(1, dt=dt)
+    assert rel_err(g.moments()[0], r.Wc) < 1e-12
+    g.close()
