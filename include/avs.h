@@ -49,6 +49,17 @@ enum { AVS_FP64 = 0, AVS_MIXED = 1 };
 enum { AVS_BC_WALL = 1, AVS_BC_FARFIELD = 2 };
 enum { AVS_LIM_FIRST_ORDER = 0, AVS_LIM_VENKAT = 1, AVS_LIM_NONE = 2 };
 
+#define AVS_MAX_ZONES 4
+
+/* A refinement zone of the velocity space (Sec. 3.5): a node whose centre xi
+ * has r_in^2 <= |xi - c|^2 < r_out^2 (FP64, no fused multiply-add) may be
+ * split up to `level`, counted in levels above the base forest. */
+typedef struct {
+    double c[3];
+    double r_in, r_out;
+    int level;
+} avs_zone;
+
 /* Run configuration.  Units: rho_inf = T_inf = L_ref = 1 and velocity unit
  * sqrt(2 R T_inf), so R = 1/2 (paper Sec. 4.5 tables). */
 typedef struct {
@@ -70,7 +81,26 @@ typedef struct {
     int corr_iters;       /* passes of the conservation correction (Sec. 3.3)               */
     int max_nodes;        /* velocity-node capacity (fixed); 0 = 1.25x the step-0 count, grown on demand */
     int learned_full_every; /* learned form: run the full criterion every n-th adaptation   */
+    int nzones;           /* 0: any node may split up to max_refine.  1..AVS_MAX_ZONES: a node
+                             may split up to the largest level of the zones holding its centre,
+                             else up to zone_outside_level (Sec. 3.5)                        */
+    int zone_outside_level;
+    avs_zone zones[AVS_MAX_ZONES];
+    int init_refine;      /* uniform splits of every base element before the step-0 adaptation
+                             (Sec. 3.5 step 2); 0..max_refine                                */
 } avs_config;
+
+/* Flow data for the adaptive parameters of Sec. 3.5 (avs_paper_parameters). */
+typedef struct {
+    int dim;              /* 2 or 3                                                          */
+    double Ma;            /* free-stream Mach number |U_inf| / sqrt(gamma R T_inf)           */
+    double gamma, R;      /* specific-heat ratio, gas constant (1/2 in these units)          */
+    double T_inf, T_w;    /* free-stream static and wall temperature                         */
+    double dir[3];        /* direction of U_inf (any length > 0)                             */
+    double h_std;         /* standard velocity interval (0.6 in the paper)                   */
+    double rdv_sigma;     /* R_dv / sigma_0: 4, or up to 7 when T_w is close to T_0          */
+    int separated;        /* 1: add the separated zone 3 sigma_w < |xi| < 5 sigma_w          */
+} avs_flow_spec;
 
 /* Physical mesh as a face list (finite-volume form of Eq. 18).
  * faceR[f] < 0 marks a boundary face with condition -1 - faceR[f]; for those
@@ -233,6 +263,25 @@ avs_status avs_mlp_grad(avs_ctx *ctx, const float *X, const float *Y, int n, flo
 avs_status avs_features(avs_ctx *ctx, float *X_out, float *Y_out);
 /* iters SGD steps on the current state's features and labels; last loss out. */
 avs_status avs_mlp_train(avs_ctx *ctx, int iters, float lr, float *loss_out);
+
+/* The adaptive parameters of Sec. 3.5 for a flow.  With sigma = sqrt(R T):
+ * T_0 = T_inf (1 + (gamma - 1)/2 Ma^2) (Eq. totaltemperature); R_dv =
+ * rdv_sigma sigma_0; the domain is the square (cube) of half-width R_dv
+ * centred at 0.4 U_inf; L_max = the least L with 2^L >= 2 R_dv / h_std;
+ * L_w = L_max if T_w / T_inf < 4, else L_max - 1; L_min = 4 for D = 2 and
+ * Ma > 5, else 3 (at most L_max); L_sep = max(L_min, L_w - 1).  The base
+ * forest is the mesh of level L_min (2^L_min elements per axis, so the
+ * paper's root element split L_min times); the tree then reaches L_max.
+ * Zones, levels counted from L_min: free stream (centre U_inf, radius
+ * 3 sigma_inf, L_max), stationary (centre 0, radius 3 sigma_w, L_w) and, with
+ * `separated`, the ring 3 sigma_w .. 5 sigma_w about 0 (L_sep); elsewhere
+ * L_min.  init_refine = max(0, L_w - 1 - L_min) (step 2 splits the root
+ * L_w - 1 times).  C1 = 13.749 Ma^-1.465 (Eq. C1_Ma), C2 = 3.3546e-4 C1
+ * (Eq. c2c1).  Writes dim, base, vlo, vhi, max_refine, nzones, zones,
+ * zone_outside_level, init_refine, C1 and C2 of *cfg and nothing else.  Host
+ * only, no context.  Errors: EINVAL (dim, Ma <= 0, gamma <= 1, R, T_inf,
+ * T_w, h_std or rdv_sigma <= 0, zero direction). */
+avs_status avs_paper_parameters(const avs_flow_spec *spec, avs_config *cfg);
 
 /* Self-test of the bounded grid barrier that the implicit macroscopic sweep
  * uses between colour passes: one cooperative launch of `blocks` blocks

@@ -13,6 +13,7 @@ Parity status of each routine (what pins it) is listed in the tests under
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -80,7 +81,7 @@ def lib():
             L.om_criterion.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
             L.om_adapt_tree.restype = C.c_int
             L.om_adapt_tree.argtypes = [C.c_int, C.c_int, ip, ip, up, dp, C.c_double, C.c_double,
-                                        C.c_double, C.c_int, C.c_int, ip, ip, up, ip, ip]
+                                        C.c_double, C.c_int, ip, C.c_int, ip, ip, up, ip, ip]
             L.om_remap.restype = None
             L.om_remap.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, ip, dp]
             L.om_correct.restype = C.c_double
@@ -249,7 +250,8 @@ def criterion(D, xi, w, f, Wc):
     return M
 
 
-def adapt_tree(D, level, base, key, M, s, C1, C2, max_refine, cap=None):
+def adapt_tree(D, level, base, key, M, s, C1, C2, max_refine, cap=None, lcap=None):
+    """Marks and the new tree; lcap: per-node refinement cap (zones), else max_refine."""
     level = np.ascontiguousarray(level, np.int32)
     base = np.ascontiguousarray(base, np.int32)
     key = np.ascontiguousarray(key, np.uint32)
@@ -258,8 +260,10 @@ def adapt_tree(D, level, base, key, M, s, C1, C2, max_refine, cap=None):
     cap = cap or Nv * (1 << D)
     nl = np.zeros(cap, np.int32); nb = np.zeros(cap, np.int32); nk = np.zeros(cap, np.uint32)
     src = np.zeros(cap, np.int32); kind = np.zeros(cap, np.int32)
+    lc = None if lcap is None else np.ascontiguousarray(lcap, np.int32)
     n = lib().om_adapt_tree(D, Nv, _ip(level), _ip(base), _up(key), _dp(M), float(s), float(C1), float(C2),
-                            int(max_refine), int(cap), _ip(nl), _ip(nb), _up(nk), _ip(src), _ip(kind))
+                            int(max_refine), None if lc is None else _ip(lc), int(cap), _ip(nl), _ip(nb),
+                            _up(nk), _ip(src), _ip(kind))
     if n < 0:
         raise MemoryError("adapted tree exceeds the node capacity")
     return nl[:n].copy(), nb[:n].copy(), nk[:n].copy(), src[:n].copy(), kind[:n].copy()
@@ -280,6 +284,63 @@ def correct(D, xi, w, Wc_target, f, iters=3, R=0.5):
     assert f.dtype == np.float64 and f.flags.c_contiguous
     Nc, Nv = f.shape[0], f.shape[-1]
     return lib().om_correct(D, Nc, Nv, _dp(xi), _dp(w), R, iters, _dp(Wc_target), _dp(f))
+
+
+def paper_parameters(D, Ma, gamma, T_inf=1.0, T_w=1.0, direction=(1.0, 0.0, 0.0), h_std=0.6, rdv_sigma=4.0,
+                     separated=False, R=0.5):
+    """Adaptive parameters of Sec. 3.5 from the flow data, step by step:
+    sigma = sqrt(R T) for T_inf, the total temperature T_0 (Eq.
+    totaltemperature) and T_w; the velocity domain of radius R_dv = rdv_sigma
+    sigma_0 about 0.4 U_inf; L_std the least level with 2^L >= 2 R_dv / h_std,
+    L_max = L_std, h_inf = 2 R_dv / 2^L_max; L_w, L_min and L_sep by their
+    case rules; the three zones; C1 from the fitted law (Eq. C1_Ma) and
+    C2 = k_sigma C1 (Eq. c2c1).  The base forest is read as the level-L_min
+    mesh of the root element, so levels in the returned tree fields count from
+    L_min (reading R21)."""
+    sig_inf = math.sqrt(R * T_inf)
+    T0 = T_inf * (1.0 + 0.5 * (gamma - 1.0) * Ma * Ma)
+    sig0 = math.sqrt(R * T0)
+    sigw = math.sqrt(R * T_w)
+    speed = Ma * math.sqrt(gamma * R * T_inf)
+    norm = math.sqrt(sum(direction[d] * direction[d] for d in range(D)))
+    U = [speed * (direction[d] / norm) for d in range(D)]
+    R_dv = rdv_sigma * sig0
+    L_max = 0
+    while 2.0 ** L_max < 2.0 * R_dv / h_std:
+        L_max += 1
+    h_inf = 2.0 * R_dv / 2 ** L_max
+    L_w = L_max if T_w / T_inf < 4.0 else L_max - 1
+    L_min = min(4 if (D == 2 and Ma > 5.0) else 3, L_max)
+    L_sep = max(L_min, L_w - 1)
+    centre = [0.4 * U[d] for d in range(D)]
+    zones = [(tuple(U), 0.0, 3.0 * sig_inf, L_max - L_min),
+             (tuple([0.0] * D), 0.0, 3.0 * sigw, max(0, L_w - L_min))]
+    if separated:
+        zones.append((tuple([0.0] * D), 3.0 * sigw, 5.0 * sigw, L_sep - L_min))
+    C1 = 13.749 * math.pow(Ma, -1.465)
+    return dict(T0=T0, sigma_inf=sig_inf, sigma_0=sig0, sigma_w=sigw, U=tuple(U), R_dv=R_dv, L_max=L_max,
+                h_inf=h_inf, L_w=L_w, L_min=L_min, L_sep=L_sep,
+                base=tuple([2 ** L_min] * D), vlo=tuple(centre[d] - R_dv for d in range(D)),
+                vhi=tuple(centre[d] + R_dv for d in range(D)), max_refine=L_max - L_min, zones=zones,
+                outside=0, init_refine=max(0, L_w - 1 - L_min), C1=C1, C2=3.3546e-4 * C1)
+
+
+def node_caps(D, xi, zones, outside, max_refine):
+    """Largest level each node may split to: the largest level of the zones
+    whose ring r_in^2 <= |xi - c|^2 < r_out^2 holds the node centre, else
+    `outside`; max_refine for every node when there are no zones."""
+    Nv = len(xi)
+    if not zones:
+        return np.full(Nv, max_refine, np.int32)
+    cap = np.full(Nv, outside, np.int32)
+    for c, r_in, r_out, level in zones:
+        d2 = np.zeros(Nv)
+        for d in range(D):
+            t = xi[:, d] - c[d]
+            d2 = d2 + t * t
+        inside = (d2 >= r_in * r_in) & (d2 < r_out * r_out)
+        cap[inside] = np.maximum(cap[inside], level)
+    return cap
 
 
 def conserved_from_primitive(D, Wp, R=0.5):
@@ -319,8 +380,15 @@ class Run:
         self.g = gas(R=0.5, Pr=wl.Pr, omega=wl.omega, Kn=wl.Kn,
                      limiter=wl.limiter if limiter is None else limiter)
         self.corr_iters = corr_iters
-        self.nb = np.array(wl.base, np.int32)
-        self.s = float(np.prod(wl.base))            # uniform-share normalisation (R10)
+        if getattr(wl, "flow", None) is not None:
+            fl = wl.flow
+            self.p = paper_parameters(self.D, fl.Ma, fl.gamma, fl.T_inf, fl.T_w, fl.dir, fl.h_std, fl.rdv_sigma,
+                                      fl.separated)
+        else:
+            self.p = dict(base=tuple(wl.base), vlo=tuple(wl.vlo), vhi=tuple(wl.vhi), max_refine=wl.max_refine,
+                          zones=[], outside=0, init_refine=0, C1=wl.C1, C2=wl.C2)
+        self.nb = np.array(self.p["base"], np.int32)
+        self.s = float(np.prod(self.p["base"]))     # uniform-share normalisation (R10)
         self.level, self.base, self.key = forest_base(self.D, self.nb)
         self._geom()
         if build_tree:
@@ -329,7 +397,13 @@ class Run:
         self.Wc = None
 
     def _geom(self):
-        self.xi, self.w = forest_geom(self.D, self.nb, self.wl.vlo, self.wl.vhi, self.level, self.base, self.key)
+        self.xi, self.w = forest_geom(self.D, self.nb, self.p["vlo"], self.p["vhi"], self.level, self.base, self.key)
+        self.ncap = node_caps(self.D, self.xi, self.p["zones"], self.p["outside"], self.p["max_refine"])
+
+    def _marks(self, M):
+        p = self.p
+        return adapt_tree(self.D, self.level, self.base, self.key, M, self.s, p["C1"], p["C2"], p["max_refine"],
+                          lcap=self.ncap)
 
     @property
     def Nv(self):
@@ -343,11 +417,15 @@ class Run:
         W0 = Winf.copy(); W0[1:1 + D] = 0.0
         Wp = np.stack([Winf, W0])
         Wc = conserved_from_primitive(D, Wp)
-        for _ in range(max(1, self.wl.max_refine)):
+        for _ in range(self.p["init_refine"]):         # step 2: split every element
+            nl, nb, nk, _, _ = adapt_tree(D, self.level, self.base, self.key, np.full(self.Nv, np.inf), self.s,
+                                          0.0, -1.0, self.p["max_refine"])
+            self.level, self.base, self.key = nl, nb, nk
+            self._geom()
+        for _ in range(max(1, self.p["max_refine"])):
             f = maxwell_init(D, self.xi, Wp)
             M = criterion(D, self.xi, self.w, f, Wc)
-            nl, nb, nk, src, kind = adapt_tree(D, self.level, self.base, self.key, M, self.s,
-                                               self.wl.C1, self.wl.C2, self.wl.max_refine)
+            nl, nb, nk, src, kind = self._marks(M)
             changed = len(nl) != self.Nv or np.any(nl != self.level) or np.any(nk != self.key)
             self.level, self.base, self.key = nl, nb, nk
             self._geom()
@@ -384,8 +462,7 @@ class Run:
         Wf, _ = moments(D, self.xi, self.w, self.f)
         Wcrit = Wf if Wc_override is None else Wc_override
         M = criterion(D, self.xi, self.w, self.f, Wcrit)
-        nl, nb, nk, src, kind = adapt_tree(D, self.level, self.base, self.key, M, self.s,
-                                           self.wl.C1, self.wl.C2, self.wl.max_refine)
+        nl, nb, nk, src, kind = self._marks(M)
         f_new = None if bypass else remap(D, self.f, src, kind)
         self.level, self.base, self.key = nl, nb, nk
         self._geom()

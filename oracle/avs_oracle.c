@@ -833,14 +833,15 @@ void om_criterion(int D, int Nc, int Nv, const double *xi, const double *w, cons
 }
 
 /* ---- marks and the new tree (Sec. 3.1, 3.4; readings R10, R11, R14) ---- */
-/* Split a leaf when s*M_k > C1 and its level < max_refine.  Merge 2^D
+/* Split a leaf when s*M_k > C1 and its level < its cap: lcap[k] when
+ * lcap is given (the refinement zones of Sec. 3.5), else max_refine.  Merge 2^D
  * sibling leaves into their parent when all of them satisfy s*M < C2 (their
  * level >= 1).  New order is depth first: a kept leaf emits itself, a split
  * leaf its children in digit order, a merged group its parent.  src/kind
  * give, per new node, the old node it copies or the first of the 2^D old
  * siblings it averages.  Returns the new count, or -1 if it exceeds cap. */
 int om_adapt_tree(int D, int Nv, const int *level, const int *base, const unsigned *key,
-                  const double *M, double s, double C1, double C2, int max_refine, int cap,
+                  const double *M, double s, double C1, double C2, int max_refine, const int *lcap, int cap,
                   int *nlevel, int *nbase, unsigned *nkey, int *src, int *kind)
 {
     const int nch = 1 << D;
@@ -868,7 +869,7 @@ int om_adapt_tree(int D, int Nv, const int *level, const int *base, const unsign
             k += nch;
             continue;
         }
-        if (s * M[k] > C1 && level[k] < max_refine) {
+        if (s * M[k] > C1 && level[k] < (lcap ? lcap[k] : max_refine)) {
             if (n + nch > cap) return -1;
             for (int c = 0; c < nch; ++c) {
                 nlevel[n] = level[k] + 1;

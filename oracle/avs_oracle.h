@@ -62,7 +62,7 @@ int  om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *x
 void om_criterion(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
                   const double *Wc, double *M);
 int  om_adapt_tree(int D, int Nv, const int *level, const int *base, const unsigned *key,
-                   const double *M, double s, double C1, double C2, int max_refine, int cap,
+                   const double *M, double s, double C1, double C2, int max_refine, const int *lcap, int cap,
                    int *nlevel, int *nbase, unsigned *nkey, int *src, int *kind);
 void om_remap(int D, int Nc, int Nv_old, const double *f_old, int Nv_new,
               const int *src, const int *kind, double *f_new);

@@ -79,7 +79,8 @@ def criterion_values(D, xi, w, f, Wc, s):
 
 
 def labels(m, M, level, C1, C2, max_refine):
-    """Per-cell labels from the scaled criterion values m[i, k] and their max M[k]."""
+    """Per-cell labels from the scaled criterion values m[i, k] and their max M[k].
+    max_refine: the level cap, one value or one per node (refinement zones)."""
     act = M >= C2
     y = np.zeros((m.shape[0], NO))
     y[:, 0] = ((m > C1) & (level < max_refine)[None, :]).any(1)

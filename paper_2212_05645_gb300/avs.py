@@ -28,7 +28,8 @@ EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs
             "avs_criterion", "avs_get_tree", "avs_get_f", "avs_get_f_cells", "avs_set_f", "avs_sync",
             "avs_kernel_launches",
             "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
-            "avs_mlp_train", "avs_measure_fma_peak", "avs_grid_barrier_check"]
+            "avs_mlp_train", "avs_measure_fma_peak", "avs_grid_barrier_check",
+            "avs_paper_parameters"]
 MLP_NPARAM = 4996
 
 
@@ -38,13 +39,28 @@ class AVSError(RuntimeError):
         self.status = status
 
 
+MAX_ZONES = 4
+
+
+class Zone(C.Structure):
+    _fields_ = [("c", C.c_double * 3), ("r_in", C.c_double), ("r_out", C.c_double), ("level", C.c_int)]
+
+
 class Config(C.Structure):
     _fields_ = [("dim", C.c_int), ("base", C.c_int * 3), ("max_refine", C.c_int),
                 ("vlo", C.c_double * 3), ("vhi", C.c_double * 3), ("precision", C.c_int),
                 ("learned", C.c_int), ("R", C.c_double), ("Pr", C.c_double), ("omega", C.c_double),
                 ("Kn", C.c_double), ("T_ref", C.c_double), ("C1", C.c_double), ("C2", C.c_double),
                 ("W_inf", C.c_double * 5), ("limiter", C.c_int), ("lim_K", C.c_double),
-                ("corr_iters", C.c_int), ("max_nodes", C.c_int), ("learned_full_every", C.c_int)]
+                ("corr_iters", C.c_int), ("max_nodes", C.c_int), ("learned_full_every", C.c_int),
+                ("nzones", C.c_int), ("zone_outside_level", C.c_int), ("zones", Zone * MAX_ZONES),
+                ("init_refine", C.c_int)]
+
+
+class FlowSpecS(C.Structure):
+    _fields_ = [("dim", C.c_int), ("Ma", C.c_double), ("gamma", C.c_double), ("R", C.c_double),
+                ("T_inf", C.c_double), ("T_w", C.c_double), ("dir", C.c_double * 3), ("h_std", C.c_double),
+                ("rdv_sigma", C.c_double), ("separated", C.c_int)]
 
 
 class MeshS(C.Structure):
@@ -104,6 +120,7 @@ def load():
         "avs_mlp_train": (C.c_int, [vp, C.c_int, C.c_float, C.POINTER(C.c_float)]),
         "avs_measure_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
         "avs_grid_barrier_check": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+        "avs_paper_parameters": (C.c_int, [C.POINTER(FlowSpecS), C.POINTER(Config)]),
     }
     for name, (rt, args) in sig.items():
         fn = getattr(L, name)
@@ -152,11 +169,14 @@ class AVS:
         prec = wl.precision if precision is None else precision
         cfg = Config()
         cfg.dim = wl.D
-        for d in range(wl.D):
-            cfg.base[d] = wl.base[d]
-            cfg.vlo[d] = wl.vlo[d]
-            cfg.vhi[d] = wl.vhi[d]
-        cfg.max_refine = wl.max_refine
+        if wl.flow is None:
+            for d in range(wl.D):
+                cfg.base[d] = wl.base[d]
+                cfg.vlo[d] = wl.vlo[d]
+                cfg.vhi[d] = wl.vhi[d]
+            cfg.max_refine = wl.max_refine
+            cfg.C1 = wl.C1
+            cfg.C2 = wl.C2
         cfg.precision = MIXED if prec in ("mixed", MIXED) else FP64
         cfg.learned = int(wl.learned if learned is None else learned)
         cfg.R = wlmod.R_GAS
@@ -164,8 +184,6 @@ class AVS:
         cfg.omega = wl.omega
         cfg.Kn = wl.Kn
         cfg.T_ref = 1.0
-        cfg.C1 = wl.C1
-        cfg.C2 = wl.C2
         for j, v in enumerate(wl.W_inf):
             cfg.W_inf[j] = v
         cfg.limiter = wl.limiter if limiter is None else limiter
@@ -173,6 +191,8 @@ class AVS:
         cfg.corr_iters = corr_iters
         cfg.max_nodes = max_nodes
         cfg.learned_full_every = full_every
+        if wl.flow is not None:
+            _fill_paper_parameters(L, wl.D, wl.flow, cfg)
         self.cfg = cfg
         self.stream = _cur_stream() if stream is None else stream
         h = C.c_void_p()
@@ -357,6 +377,36 @@ class AVS:
         loss = C.c_float()
         self._ck(self.L.avs_mlp_train(self.h, int(iters), float(lr), C.byref(loss)))
         return loss.value
+
+
+def _fill_paper_parameters(L, D, flow, cfg):
+    sp = FlowSpecS()
+    sp.dim = D
+    sp.Ma = flow.Ma
+    sp.gamma = flow.gamma
+    sp.R = wlmod.R_GAS
+    sp.T_inf = flow.T_inf
+    sp.T_w = flow.T_w
+    for d in range(3):
+        sp.dir[d] = flow.dir[d] if d < len(flow.dir) else 0.0
+    sp.h_std = flow.h_std
+    sp.rdv_sigma = flow.rdv_sigma
+    sp.separated = int(flow.separated)
+    st = L.avs_paper_parameters(C.byref(sp), C.byref(cfg))
+    if st != AVS_OK:
+        raise AVSError(st, "avs_paper_parameters")
+
+
+def paper_parameters(D, flow):
+    """The library's Sec. 3.5 parameters for a workload's FlowSpec, as a dict
+    (tree levels counted from the base forest)."""
+    cfg = Config()
+    _fill_paper_parameters(load(), D, flow, cfg)
+    zones = [(tuple(cfg.zones[z].c[:D]), cfg.zones[z].r_in, cfg.zones[z].r_out, cfg.zones[z].level)
+             for z in range(cfg.nzones)]
+    return dict(base=tuple(cfg.base[:D]), vlo=tuple(cfg.vlo[:D]), vhi=tuple(cfg.vhi[:D]),
+                max_refine=cfg.max_refine, zones=zones, outside=cfg.zone_outside_level,
+                init_refine=cfg.init_refine, C1=cfg.C1, C2=cfg.C2)
 
 
 def fma_peak_gflops(kind, iters=20000):

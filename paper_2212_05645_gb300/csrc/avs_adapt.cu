@@ -17,10 +17,28 @@ int round_up(int n, int m) { return (n + m - 1) / m * m; }
 // ------------------------------------------------------------------ geometry
 // Mid-point quadrature on the tree (Sec. 3): node = element centre,
 // weight = element area/volume; xi = vlo + hb (b + (2o+1)/2^(l+1)).
+// The node's refinement cap: the largest level of the zones holding its
+// centre (r_in^2 <= |xi - c|^2 < r_out^2, FP64 without contraction), else the
+// outside level; max_refine when no zones are set (Sec. 3.5).
+__device__ int zone_cap(const ZoneSet& Z, int D, const double* x)
+{
+    if (Z.n == 0) return Z.maxr;
+    int cap = Z.outside;
+    for (int z = 0; z < Z.n; ++z) {
+        double d2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double t = __dadd_rn(x[d], -Z.c[z][d]);
+            d2 = __dadd_rn(d2, __dmul_rn(t, t));
+        }
+        if (d2 >= Z.r2in[z] && d2 < Z.r2out[z]) cap = max(cap, Z.level[z]);
+    }
+    return cap;
+}
+
 __global__ void k_geom(int D, int Nv, int Nvp, const int* __restrict__ level, const int* __restrict__ base,
                        const uint32_t* __restrict__ key, int nb0, int nb1, int nb2, double vlo0, double vlo1,
                        double vlo2, double hb0, double hb1, double hb2, double* xi_d, double* w_d, float* xi_f,
-                       float* w_f)
+                       float* w_f, ZoneSet Z, int* ncap)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nvp) return;
@@ -31,8 +49,10 @@ __global__ void k_geom(int D, int Nv, int Nvp, const int* __restrict__ level, co
         }
         w_d[k] = 0.0;
         w_f[k] = 0.0f;
+        ncap[k] = 0;
         return;
     }
+    double xc[3] = {0.0, 0.0, 0.0};
     const int nb[3] = {nb0, nb1, nb2};
     const double vlo[3] = {vlo0, vlo1, vlo2};
     const double hb[3] = {hb0, hb1, hb2};
@@ -50,6 +70,7 @@ __global__ void k_geom(int D, int Nv, int Nvp, const int* __restrict__ level, co
         }
         const double frac = (double)(2u * o + 1u) / (double)(1u << (l + 1));
         const double x = __dadd_rn(vlo[d], __dmul_rn(hb[d], __dadd_rn((double)bi, frac)));
+        xc[d] = x;
         xi_d[(size_t)k * D + d] = x;
         xi_f[(size_t)k * D + d] = (float)x;
         wk = __dmul_rn(wk, hb[d]);
@@ -57,6 +78,7 @@ __global__ void k_geom(int D, int Nv, int Nvp, const int* __restrict__ level, co
     const double wv = ldexp(wk, -D * l);
     w_d[k] = wv;
     w_f[k] = (float)wv;
+    ncap[k] = zone_cap(Z, D, xc);
 }
 
 cudaError_t launch_geom(avs_ctx* c)
@@ -65,7 +87,7 @@ cudaError_t launch_geom(avs_ctx* c)
     k_geom<<<(n + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nv, c->Nvp, c->level, c->base, c->key, c->cfg.base[0],
                                                    c->cfg.base[1], c->cfg.base[2], c->cfg.vlo[0], c->cfg.vlo[1],
                                                    c->cfg.vlo[2], c->hb[0], c->hb[1], c->hb[2], c->xi_d, c->w_d,
-                                                   c->xi_f, c->w_f);
+                                                   c->xi_f, c->w_f, c->zs, c->ncap);
     c->launches += 1;
     return cudaGetLastError();
 }
@@ -553,13 +575,13 @@ cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Nce
 // s*M > C1 below the level cap emits its 2^D children; others emit themselves.
 __global__ void k_group_start(int D, int Nv, const int* __restrict__ level, const int* __restrict__ base,
                               const uint32_t* __restrict__ key, const double* __restrict__ M, double s, double C2,
-                              int* gs)
+                              int uniform, int* gs)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nv) return;
     const int nch = 1 << D;
     int g = 0;
-    if (level[k] >= 1 && (key[k] & (uint32_t)(nch - 1)) == 0u && k + nch <= Nv) {
+    if (!uniform && level[k] >= 1 && (key[k] & (uint32_t)(nch - 1)) == 0u && k + nch <= Nv) {
         g = 1;
         for (int c = 0; c < nch; ++c) {
             const int kk = k + c;
@@ -572,8 +594,8 @@ __global__ void k_group_start(int D, int Nv, const int* __restrict__ level, cons
 }
 
 __global__ void k_emit(int D, int Nv, const int* __restrict__ level, const uint32_t* __restrict__ key,
-                       const double* __restrict__ M, const int* __restrict__ gs, double s, double C1, int max_refine,
-                       int* emit)
+                       const double* __restrict__ M, const int* __restrict__ gs, double s, double C1,
+                       const int* __restrict__ ncap, int uniform, int* emit)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nv) return;
@@ -585,7 +607,7 @@ __global__ void k_emit(int D, int Nv, const int* __restrict__ level, const uint3
         const int dig = (int)(key[k] & (uint32_t)(nch - 1));
         const int st = k - dig;
         if (level[k] >= 1 && dig != 0 && st >= 0 && gs[st]) e = 0;
-        else if (__dmul_rn(s, M[k]) > C1 && level[k] < max_refine) e = nch;
+        else if (uniform || (__dmul_rn(s, M[k]) > C1 && level[k] < ncap[k])) e = nch;
         else e = 1;
     }
     emit[k] = e;
@@ -661,13 +683,15 @@ __global__ void k_build(int D, int Nv, const int* __restrict__ level, const int*
     }
 }
 
-cudaError_t launch_adapt_tree(avs_ctx* c, double C1, double C2)
+// uniform = 1: every leaf splits (step 2 of Sec. 3.5), M is not read.
+cudaError_t launch_adapt_tree(avs_ctx* c, double C1, double C2, int uniform)
 {
     const int n = c->Nv;
     const int g = (n + 255) / 256;
     int* gs = c->newidx + c->cap;    // second half of the index scratch
-    k_group_start<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->base, c->key, c->M, c->s_norm, C2, gs);
-    k_emit<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->key, c->M, gs, c->s_norm, C1, c->cfg.max_refine, c->emit);
+    k_group_start<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->base, c->key, c->M, c->s_norm, C2, uniform, gs);
+    k_emit<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->key, c->M, gs, c->s_norm, C1, c->ncap, uniform,
+                                     c->emit);
     k_scan<<<1, 1024, 0, c->stream>>>(c->emit, c->newidx, n, c->d_count);
     cudaMemsetAsync(c->d_count + 1, 0, 2 * sizeof(int), c->stream);
     k_build<<<g, 256, 0, c->stream>>>(c->D, n, c->level, c->base, c->key, gs, c->emit, c->newidx, c->cap, c->level2,

@@ -54,7 +54,7 @@ void free_all(avs_ctx* c)
                     c->slot, c->nslot, c->nbr, c->cg_d, c->r_d, c->eps2_d, c->cg_f, c->r_f, c->eps2_f,
                     c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
                     c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
-                    c->W[0], c->W[1], c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mhi, c->Mthr, c->stage, c->dev_err,
+                    c->W[0], c->W[1], c->ncap, c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mhi, c->Mthr, c->stage, c->dev_err,
                     c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->rmom, c->cpar, c->clist, c->cstart_d, c->imp_dW, c->imp_rhs0, c->imp_diag, c->imp_Wta,
                     c->imp_co, c->imp_nint, c->imp_bar, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
                     c->mlp_X, c->mlp_Y, c->mlp_logits, c->mlp_list, c->mlp_count, c->M_alt};
@@ -134,9 +134,9 @@ avs_status refresh_dt(avs_ctx* c)
 
 // One pass of marks + compaction on criterion values already in c->M;
 // swaps in the new tree.  Returns counts through out pointers.
-avs_status apply_marks(avs_ctx* c, int* Nv_new, int* splits, int* merges)
+avs_status apply_marks(avs_ctx* c, int* Nv_new, int* splits, int* merges, int uniform)
 {
-    CK(launch_adapt_tree(c, c->cfg.C1, c->cfg.C2));
+    CK(launch_adapt_tree(c, c->cfg.C1, c->cfg.C2, uniform));
     int cnt[3] = {0, 0, 0};
     CK(cudaMemcpyAsync(cnt, c->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -247,6 +247,19 @@ avs_status validate(const avs_config* cfg, const avs_mesh* m, std::string& why)
     if (!(cfg->C1 > cfg->C2)) { why = "C1 must exceed C2"; return AVS_EINVAL; }
     if (cfg->limiter < 0 || cfg->limiter > 2) { why = "bad limiter"; return AVS_EINVAL; }
     if (cfg->corr_iters < 0 || cfg->corr_iters > 64) { why = "bad corr_iters"; return AVS_EINVAL; }
+    if (cfg->nzones < 0 || cfg->nzones > AVS_MAX_ZONES) { why = "nzones out of range"; return AVS_EINVAL; }
+    if (cfg->nzones > 0 && (cfg->zone_outside_level < 0 || cfg->zone_outside_level > cfg->max_refine)) {
+        why = "zone_outside_level out of range";
+        return AVS_EINVAL;
+    }
+    for (int z = 0; z < cfg->nzones; ++z) {
+        const avs_zone& Z = cfg->zones[z];
+        if (Z.level < 0 || Z.level > cfg->max_refine) { why = "zone level out of range"; return AVS_EINVAL; }
+        if (!(Z.r_in >= 0) || !(Z.r_out > Z.r_in)) { why = "zone radii must satisfy 0 <= r_in < r_out"; return AVS_EINVAL; }
+        for (int d = 0; d < D; ++d)
+            if (!std::isfinite(Z.c[d])) { why = "zone centre not finite"; return AVS_EINVAL; }
+    }
+    if (cfg->init_refine < 0 || cfg->init_refine > cfg->max_refine) { why = "init_refine out of range"; return AVS_EINVAL; }
     if (m->Nc <= 0 || m->Nf <= 0 || m->nbc < 0) { why = "empty mesh"; return AVS_EINVAL; }
     if (!m->faceL || !m->faceR || !m->An || !m->rL || !m->rR || !m->vol || (m->nbc > 0 && !m->bc)) {
         why = "null mesh array";
@@ -451,12 +464,20 @@ avs_status initial_tree(avs_ctx* c)
     double* Wc_d = c->pseudo_W + 2 * (D + 2);
     CK(up(Wp_d, wpv, c->stream));
     CK(up(Wc_d, wcv, c->stream));
+    // step 2 of Sec. 3.5: uniform splits of every element before the adaptation
+    for (int p = 0; p < c->cfg.init_refine; ++p) {
+        int Nn, sp, mg;
+        avs_status st = apply_marks(c, &Nn, &sp, &mg, 1);
+        if (st != AVS_OK) return st;
+        swap_tree(c, Nn);
+        CK(launch_geom(c));
+    }
     const int passes = std::max(1, c->cfg.max_refine);
     for (int p = 0; p < passes; ++p) {
         CK(launch_maxwell(c, Wp_d, 2, 0.0, 0, c->pseudo_f, 1, c->Nvp));
         CK(launch_criterion(c, c->pseudo_f, 1, 2, c->Nvp, Wc_d, nullptr, 0, 1));
         int Nn, sp, mg;
-        avs_status st = apply_marks(c, &Nn, &sp, &mg);
+        avs_status st = apply_marks(c, &Nn, &sp, &mg, 0);
         if (st != AVS_OK) return st;
         swap_tree(c, Nn);
         CK(launch_geom(c));
@@ -498,6 +519,15 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
         nbase *= cfg->base[d];
     }
     c->s_norm = (double)nbase;
+    c->zs.n = cfg->nzones;
+    c->zs.outside = cfg->zone_outside_level;
+    c->zs.maxr = cfg->max_refine;
+    for (int z = 0; z < cfg->nzones; ++z) {
+        c->zs.level[z] = cfg->zones[z].level;
+        for (int d = 0; d < 3; ++d) c->zs.c[z][d] = d < c->D ? cfg->zones[z].c[d] : 0.0;
+        c->zs.r2in[z] = cfg->zones[z].r_in * cfg->zones[z].r_in;
+        c->zs.r2out[z] = cfg->zones[z].r_out * cfg->zones[z].r_out;
+    }
     // node capacity of the tree arrays: all leaves at max_refine, bounded
     long long full = nbase << (c->D * cfg->max_refine);
     long long cap = std::min<long long>(full, 1 << 23);
@@ -514,7 +544,7 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     AL(c->newidx, 2 * (size_t)capp); AL(c->d_count, 4);
     AL(c->xi_d, (size_t)capp * c->D); AL(c->w_d, capp);
     AL(c->xi_f, (size_t)capp * c->D); AL(c->w_f, capp);
-    AL(c->M, capp); AL(c->Mkey, capp);
+    AL(c->M, capp); AL(c->Mkey, capp); AL(c->ncap, capp);
     AL(c->pseudo_f, 2 * (size_t)c->NA * capp); AL(c->pseudo_W, 4 * NW);
     AL(c->crit_cp, 5 * (size_t)std::max(c->Nc, 2)); AL(c->crit_cp32, 8 * (size_t)std::max(c->Nc, 2));
     AL(c->Mlo, capp); AL(c->Mhi, capp); AL(c->Mthr, 4 * (size_t)capp);
@@ -617,6 +647,66 @@ avs_status ugks_step_implicit(avs_ctx* c, int nsteps, double dt, int k_macro, in
     return AVS_OK;
 }
 
+// Adaptive parameters of Sec. 3.5 (domain, levels, zones, thresholds) from the flow data.
+avs_status avs_paper_parameters(const avs_flow_spec* sp, avs_config* cfg)
+{
+    if (!sp || !cfg) return AVS_EINVAL;
+    const int D = sp->dim;
+    if (D != 2 && D != 3) return AVS_EINVAL;
+    if (!(sp->Ma > 0) || !(sp->gamma > 1) || !(sp->R > 0) || !(sp->T_inf > 0) || !(sp->T_w > 0) ||
+        !(sp->h_std > 0) || !(sp->rdv_sigma > 0))
+        return AVS_EINVAL;
+    double nd = 0.0;
+    for (int d = 0; d < D; ++d) nd += sp->dir[d] * sp->dir[d];
+    if (!(nd > 0) || !std::isfinite(nd)) return AVS_EINVAL;
+    nd = sqrt(nd);
+    const double sig_inf = sqrt(sp->R * sp->T_inf);
+    const double T0 = sp->T_inf * (1.0 + 0.5 * (sp->gamma - 1.0) * sp->Ma * sp->Ma);
+    const double sig0 = sqrt(sp->R * T0);
+    const double sigw = sqrt(sp->R * sp->T_w);
+    const double Uinf = sp->Ma * sqrt(sp->gamma * sp->R * sp->T_inf);
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < D; ++d) u[d] = Uinf * (sp->dir[d] / nd);
+    const double Rdv = sp->rdv_sigma * sig0;
+    const double ratio = 2.0 * Rdv / sp->h_std;
+    int Lmax = 0;
+    while (ldexp(1.0, Lmax) < ratio) {
+        if (++Lmax > 30) return AVS_EINVAL;
+    }
+    const int Lw = (sp->T_w / sp->T_inf < 4.0) ? Lmax : Lmax - 1;
+    const int Lmin = std::min((D == 2 && sp->Ma > 5.0) ? 4 : 3, Lmax);
+    const int Lsep = std::max(Lmin, Lw - 1);
+    if (D * Lmin > 24 || D * (Lmax - Lmin) > 30) return AVS_EINVAL;
+    cfg->dim = D;
+    for (int d = 0; d < 3; ++d) {
+        const double c0 = d < D ? 0.4 * u[d] : 0.0;
+        cfg->base[d] = d < D ? (1 << Lmin) : 1;
+        cfg->vlo[d] = d < D ? c0 - Rdv : 0.0;
+        cfg->vhi[d] = d < D ? c0 + Rdv : 0.0;
+    }
+    cfg->max_refine = Lmax - Lmin;
+    cfg->zone_outside_level = 0;
+    memset(cfg->zones, 0, sizeof(cfg->zones));
+    for (int d = 0; d < D; ++d) cfg->zones[0].c[d] = u[d];
+    cfg->zones[0].r_in = 0.0;
+    cfg->zones[0].r_out = 3.0 * sig_inf;
+    cfg->zones[0].level = Lmax - Lmin;
+    cfg->zones[1].r_in = 0.0;
+    cfg->zones[1].r_out = 3.0 * sigw;
+    cfg->zones[1].level = std::max(0, Lw - Lmin);
+    cfg->nzones = 2;
+    if (sp->separated) {
+        cfg->zones[2].r_in = 3.0 * sigw;
+        cfg->zones[2].r_out = 5.0 * sigw;
+        cfg->zones[2].level = Lsep - Lmin;
+        cfg->nzones = 3;
+    }
+    cfg->init_refine = std::max(0, Lw - 1 - Lmin);
+    cfg->C1 = 13.749 * pow(sp->Ma, -1.465);
+    cfg->C2 = 3.3546e-4 * cfg->C1;
+    return AVS_OK;
+}
+
 avs_status avs_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int short_by, int* passed)
 {
     if (!c || blocks <= 0 || rounds <= 0 || short_by < 0 || !passed) return AVS_EINVAL;
@@ -700,7 +790,7 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
         CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr, 0, 1));
     }
     int Nn, sp, mg;
-    avs_status st = apply_marks(c, &Nn, &sp, &mg);
+    avs_status st = apply_marks(c, &Nn, &sp, &mg, 0);
     if (st != AVS_OK) return st;
     const int Nvp_new = round_up(Nn, 32);
     void* dst = c->f[c->cur ^ 1];

@@ -14,8 +14,19 @@
 #define AVS_CELLPAR_BYTES 256 // bytes per cell of the collision parameters (CellPar)
 #define AVS_IMPSLOT_BYTES 96  // bytes per slot record of the implicit macroscopic sweep
 
+// Refinement caps of the velocity nodes (Sec. 3.5), passed to kernels by value.
+struct ZoneSet {
+    int n = 0;               // zones in use; 0: every node may split up to maxr
+    int outside = 0;         // cap of a node in no zone
+    int maxr = 0;            // max_refine
+    int level[AVS_MAX_ZONES] = {0, 0, 0, 0};
+    double c[AVS_MAX_ZONES][3] = {};
+    double r2in[AVS_MAX_ZONES] = {}, r2out[AVS_MAX_ZONES] = {};
+};
+
 struct avs_ctx {
     avs_config cfg;
+    ZoneSet zs;
     int D = 2, NA = 2, Nc = 0, Nf = 0, nbc = 0;
     int mixed = 0;
     cudaStream_t stream = nullptr;
@@ -47,6 +58,7 @@ struct avs_ctx {
     int *src = nullptr, *kind = nullptr, *emit = nullptr, *newidx = nullptr;
     int *d_count = nullptr;
     double *xi_d = nullptr, *w_d = nullptr;          // [cap][D], [cap]
+    int *ncap = nullptr;                             // [cap] largest level a node may split to (zones)
     float *xi_f = nullptr, *w_f = nullptr;
     double *M = nullptr;                             // [cap]
     unsigned long long *Mkey = nullptr;              // [cap]
@@ -133,7 +145,7 @@ cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int 
 cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp,
                              const double* Wc, const int* cells, int ncells_list, int decide);
 // decide = 1: M exact only where the split/merge tests need it (marks); 0: M exact everywhere
-cudaError_t launch_adapt_tree(avs_ctx* c, double C1, double C2);  // marks, scan, new tree -> *2 arrays
+cudaError_t launch_adapt_tree(avs_ctx* c, double C1, double C2, int uniform);  // marks, scan, new tree -> *2 arrays
 cudaError_t launch_remap(avs_ctx* c, const void* fold, int Nvp_old, void* fnew, int Nvp_new, int Nv_new);
 cudaError_t launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters);
 cudaError_t launch_to_double(avs_ctx* c, const void* f, double* out, int Nvp);   // packed [Nc][NA][Nv]

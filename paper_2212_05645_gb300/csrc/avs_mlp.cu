@@ -453,7 +453,7 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
                          const double* __restrict__ w, const double* __restrict__ cp, const float* __restrict__ xi32,
                          const float* __restrict__ w32, const float* __restrict__ cp32, const double* __restrict__ M,
                          const float4* __restrict__ thr, const int* __restrict__ level, double s, double C1, double C2,
-                         int max_refine, float* Y)
+                         const int* __restrict__ ncap, float* Y)
 {
     // Every test is first decided on the FP32 screening interval of m_ik
     // (crit32); a test whose threshold lies within 2^-20 relative of the
@@ -472,10 +472,10 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
         crit32(D, crit_scaled(Gt), w32[k], xf, p32, m32, B);
         const float lo = s32 * (m32 - B), hi = s32 * (m32 + B);
         const float4 t = thr[k];               // act, M_k, 0.5 s M_k (scaled like m32)
-        const int lv = level[k];
+        const int lv = level[k], lcap = ncap[k];
         const bool act = t.x != 0.0f;
         bool amb = false;
-        if (lv < max_refine && !y0) {
+        if (lv < lcap && !y0) {
             if (lo > C1f * (1.0f + eps)) y0 = 1;
             else if (!(hi < C1f * (1.0f - eps))) amb = true;
         }
@@ -503,7 +503,7 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
         const double Mk = M[k];
         const double sm = __dmul_rn(s, mk), sM = __dmul_rn(s, Mk);
         const bool actd = sM >= C2;
-        y0 |= (sm > C1 && lv < max_refine);
+        y0 |= (sm > C1 && lv < lcap);
         y1 |= (actd && mk == Mk);
         y2 |= (actd && sm >= 0.5 * sM);
         y3 |= (sm >= C2 && lv >= 1);
@@ -633,11 +633,11 @@ cudaError_t mlp_labels(avs_ctx* c, const void* f, float* Y)
     if (c->mixed)
         k_labels<float><<<c->Nc, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, c->Nvp, (const float*)f, c->xi_d, c->w_d,
                                                       c->crit_cp, c->xi_f, c->w_f, c->crit_cp32, c->M, thr, c->level,
-                                                      c->s_norm, c->cfg.C1, c->cfg.C2, c->cfg.max_refine, Y);
+                                                      c->s_norm, c->cfg.C1, c->cfg.C2, c->ncap, Y);
     else
         k_labels<double><<<c->Nc, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, c->Nvp, (const double*)f, c->xi_d,
                                                        c->w_d, c->crit_cp, c->xi_f, c->w_f, c->crit_cp32, c->M, thr,
-                                                       c->level, c->s_norm, c->cfg.C1, c->cfg.C2, c->cfg.max_refine,
+                                                       c->level, c->s_norm, c->cfg.C1, c->cfg.C2, c->ncap,
                                                        Y);
     c->launches += 2;
     return cudaGetLastError();

@@ -420,6 +420,21 @@ def sphere_shell_mesh(n_r=64, n_theta=48, n_phi=48, r_body=1.0, r_out=10.0, firs
 # flow conditions and velocity forests of the workloads
 # --------------------------------------------------------------------------
 @dataclass
+class FlowSpec:
+    """Flow data of a workload whose velocity space each side derives by the
+    adaptive-parameter rules of Sec. 3.5 (inputs only; the rules themselves
+    live in the library and, separately, in the oracle)."""
+    Ma: float
+    gamma: float = GAMMA_MONO
+    T_inf: float = 1.0
+    T_w: float = 1.0
+    dir: tuple = (1.0, 0.0, 0.0)
+    h_std: float = 0.6
+    rdv_sigma: float = 4.0
+    separated: bool = False
+
+
+@dataclass
 class Workload:
     """Everything needed to set up one run (inputs only)."""
     name: str
@@ -444,6 +459,7 @@ class Workload:
     adapt_first_n: int = 3
     adapt_every: int = 50
     extra: dict = field(default_factory=dict)
+    flow: FlowSpec = None      # set: base, vlo, vhi, max_refine, C1, C2 come from the Sec. 3.5 rules
 
 
 def mach_speed(Ma, gamma=GAMMA_MONO, T=1.0):
@@ -497,6 +513,36 @@ def cylinder(n_theta=96, n_r=128, Ma=5.0, Kn=0.1, C1=1.0, max_refine=4, precisio
                     Kn=Kn, omega=0.81, Pr=2.0 / 3.0, C1=C1, C2=K_SIGMA * C1,
                     W_inf=(1.0, U, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 2, 1.0, (0.0, 0.0), 1.0),
                     precision=precision, steps=200)
+
+
+def cylinder_zones(n_theta=96, n_r=128, Ma=5.0, Kn=0.1, separated=False, rdv_sigma=4.0, precision="mixed",
+                   learned=False) -> Workload:
+    """The cylinder O-mesh with the velocity space of Sec. 3.5: domain,
+    levels, refinement zones and thresholds from Ma, T_w = T_inf and the
+    paper's h_std = 0.6, R_dv = 4 sigma_0 (the paper's setting for this case)."""
+    U = mach_speed(Ma)
+    wall = _bc_row(BC_WALL, T=1.0)
+    far = _bc_row(BC_FARFIELD, rho=1.0, U=(U, 0.0), T=1.0)
+    mesh = cylinder_omesh(n_theta, n_r, bc_wall=wall, bc_far=far)
+    return Workload(f"cylinder-zones-{n_r}x{n_theta}", mesh, 2, None, None, None, None,
+                    Kn=Kn, omega=0.81, Pr=2.0 / 3.0, C1=None, C2=None,
+                    W_inf=(1.0, U, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 2, 1.0, (0.0, 0.0), 1.0),
+                    precision=precision, learned=learned,
+                    flow=FlowSpec(Ma=Ma, T_w=1.0, rdv_sigma=rdv_sigma, separated=separated))
+
+
+def sphere_zones(n_r=64, n_theta=48, n_phi=48, Ma=4.25, Kn=0.031, rdv_sigma=4.0, precision="mixed",
+                 learned=False) -> Workload:
+    """The sphere shell with the velocity space of Sec. 3.5 (octree)."""
+    U = mach_speed(Ma)
+    wall = _bc_row(BC_WALL, T=1.0)
+    far = _bc_row(BC_FARFIELD, rho=1.0, U=(U, 0.0, 0.0), T=1.0)
+    mesh = sphere_shell_mesh(n_r, n_theta, n_phi, bc_wall=wall, bc_far=far)
+    return Workload(f"sphere-zones-{n_r}x{n_theta}x{n_phi}", mesh, 3, None, None, None, None,
+                    Kn=Kn, omega=0.81, Pr=2.0 / 3.0, C1=None, C2=None,
+                    W_inf=(1.0, U, 0.0, 0.0, 1.0), W_init=_uniform_W(mesh.Nc, 3, 1.0, (0.0, 0.0, 0.0), 1.0),
+                    precision=precision, learned=learned,
+                    flow=FlowSpec(Ma=Ma, T_w=1.0, rdv_sigma=rdv_sigma))
 
 
 def blunt_wedge(n_theta=240, n_r=160, Ma=8.0, Kn=0.01, C1=0.5, max_refine=5, precision="mixed",
