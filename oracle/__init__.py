@@ -86,6 +86,20 @@ def lib():
             L.om_remap.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, ip, dp]
             L.om_correct.restype = C.c_double
             L.om_correct.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_double, C.c_int, dp, dp]
+            L.om_rykov_field.restype = None
+            L.om_rykov_field.argtypes = [C.c_int, C.c_int, dp, C.c_void_p, C.c_double, dp, C.c_double,
+                                         C.c_double, dp, dp, dp]
+            L.om_maxwell_init_rykov.restype = None
+            L.om_maxwell_init_rykov.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_double, C.c_double,
+                                                C.c_ulonglong, dp]
+            L.om_moments_rykov.restype = None
+            L.om_moments_rykov.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
+            L.om_criterion_nw.restype = None
+            L.om_criterion_nw.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+            L.om_remap_n.restype = None
+            L.om_remap_n.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, C.c_int, ip, ip, dp]
+            L.om_correct_rykov.restype = C.c_double
+            L.om_correct_rykov.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, C.c_double, C.c_int, dp, dp]
             _lib = L
     return _lib
 
@@ -101,7 +115,16 @@ class _Mesh(C.Structure):
 class _Gas(C.Structure):
     _fields_ = [("R", C.c_double), ("Pr", C.c_double), ("omega", C.c_double),
                 ("mu_ref", C.c_double), ("T_ref", C.c_double), ("lim_K", C.c_double),
-                ("limiter", C.c_int)]
+                ("limiter", C.c_int), ("model", C.c_int), ("Zrot", C.c_double), ("omega0", C.c_double),
+                ("omega1", C.c_double), ("delta", C.c_double)]
+
+
+# Rykov coefficients for nitrogen (Sec. 2.1, after Eq. 13); Z_rot is not given
+# in the paper (reading R26)
+RYKOV_DELTA = 1.0 / 1.55
+RYKOV_OMEGA0 = 0.2354
+RYKOV_OMEGA1 = 0.3049
+RYKOV_ZROT = 3.5
 
 
 def _dp(a):
@@ -200,10 +223,80 @@ class MeshHandle:
         return C.byref(self.s)
 
 
-def gas(R=0.5, Pr=2.0 / 3.0, omega=0.81, mu_ref=None, Kn=None, T_ref=1.0, lim_K=0.3, limiter=1):
+def gas(R=0.5, Pr=2.0 / 3.0, omega=0.81, mu_ref=None, Kn=None, T_ref=1.0, lim_K=0.3, limiter=1,
+        model="shakhov", Zrot=RYKOV_ZROT):
     if mu_ref is None:
         mu_ref = mu_ref_from_Kn(Kn, omega, R)
-    return _Gas(R, Pr, omega, mu_ref, T_ref, lim_K, limiter)
+    return _Gas(R, Pr, omega, mu_ref, T_ref, lim_K, limiter, 1 if model == "rykov" else 0, Zrot,
+                RYKOV_OMEGA0, RYKOV_OMEGA1, RYKOV_DELTA)
+
+
+def rykov_field(D, xi, g, rho, U, RTt, RTr, qt, qr):
+    """Rykov equilibrium (g^G, [g^H,] g^R) at every node, shape (nA, Nv)."""
+    xi = _f64(xi)
+    Nv = xi.shape[0]
+    nA = 3 if D == 2 else 2
+    out = np.zeros((nA, Nv))
+    lib().om_rykov_field(D, Nv, _dp(xi), C.byref(g), float(rho), _dp(_f64(U)), float(RTt), float(RTr),
+                         _dp(_f64(qt)), _dp(_f64(qr)), _dp(out))
+    return out
+
+
+def maxwell_init_rykov(D, xi, Wp, R=0.5, amp=0.0, seed=12345):
+    """Initial f of the Rykov model; Wp per cell rho, U (D), T_t[, T_r] (T_r = T_t if absent)."""
+    xi = _f64(xi); Wp = _f64(Wp)
+    if Wp.shape[1] == D + 2:
+        Wp = np.concatenate([Wp, Wp[:, D + 1:D + 2]], axis=1)
+    Wp = _f64(Wp)
+    Nc, Nv = Wp.shape[0], xi.shape[0]
+    f = np.zeros((Nc, 3 if D == 2 else 2, Nv))
+    lib().om_maxwell_init_rykov(D, Nc, Nv, _dp(xi), _dp(Wp), R, amp, seed, _dp(f))
+    return f
+
+
+def moments_rykov(D, xi, w, f):
+    """W = (rho, rho U, rho E, rho E_rot), q_t and q_r of every cell."""
+    xi = _f64(xi); w = _f64(w); f = _f64(f)
+    Nc, Nv = f.shape[0], f.shape[-1]
+    Wc = np.zeros((Nc, D + 3)); qt = np.zeros((Nc, D)); qr = np.zeros((Nc, D))
+    lib().om_moments_rykov(D, Nc, Nv, _dp(xi), _dp(w), _dp(f), _dp(Wc), _dp(qt), _dp(qr))
+    return Wc, qt, qr
+
+
+def correct_rykov(D, xi, w, Wc_target, f, iters=3, R=0.5):
+    xi = _f64(xi); w = _f64(w); Wc_target = _f64(Wc_target)
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    Nc, Nv = f.shape[0], f.shape[-1]
+    return lib().om_correct_rykov(D, Nc, Nv, _dp(xi), _dp(w), R, iters, _dp(Wc_target), _dp(f))
+
+
+def conserved_rykov(D, Wp, R=0.5):
+    """(rho, rho U, rho E, rho E_rot) from rho, U, T_t[, T_r] with K = 2:
+    rho E = rho U^2/2 + (3/2) rho R T_t + rho R T_r, rho E_rot = rho R T_r."""
+    Wp = _f64(Wp)
+    if Wp.shape[-1] == D + 2:
+        Wp = np.concatenate([Wp, Wp[..., D + 1:D + 2]], axis=-1)
+    Wc = np.zeros(Wp.shape[:-1] + (D + 3,))
+    rho = Wp[..., 0]
+    U = Wp[..., 1:1 + D]
+    Wc[..., 0] = rho
+    Wc[..., 1:1 + D] = rho[..., None] * U
+    Wc[..., D + 2] = rho * R * Wp[..., D + 2]
+    Wc[..., D + 1] = 0.5 * rho * (U * U).sum(-1) + 1.5 * rho * R * Wp[..., D + 1] + Wc[..., D + 2]
+    return Wc
+
+
+def primitive_rykov(D, Wc, R=0.5):
+    """rho, U, T_t, T_r from (rho, rho U, rho E, rho E_rot) (K = 2)."""
+    Wc = _f64(Wc)
+    Wp = np.zeros_like(Wc)
+    rho = Wc[..., 0]
+    Wp[..., 0] = rho
+    Wp[..., 1:1 + D] = Wc[..., 1:1 + D] / rho[..., None]
+    m2 = (Wc[..., 1:1 + D] ** 2).sum(-1)
+    Wp[..., D + 2] = Wc[..., D + 2] / rho / R
+    Wp[..., D + 1] = (Wc[..., D + 1] - 0.5 * m2 / rho - Wc[..., D + 2]) / (1.5 * rho * R)
+    return Wp
 
 
 def dt_unit(mh: MeshHandle, xi):
@@ -244,9 +337,9 @@ def step_implicit(mh: MeshHandle, g: _Gas, xi, w, dt, f_in, Wc, color, ncolor, k
 
 def criterion(D, xi, w, f, Wc):
     xi = _f64(xi); w = _f64(w); f = _f64(f); Wc = _f64(Wc)
-    Nc, Nv = f.shape[0], f.shape[-1]
+    Nc, nA, Nv = f.shape
     M = np.zeros(Nv)
-    lib().om_criterion(D, Nc, Nv, _dp(xi), _dp(w), _dp(f), _dp(Wc), _dp(M))
+    lib().om_criterion_nw(D, nA, Wc.shape[1], Nc, Nv, _dp(xi), _dp(w), _dp(f), _dp(Wc), _dp(M))
     return M
 
 
@@ -274,7 +367,7 @@ def remap(D, f_old, src, kind):
     Nc, nA, Nv_old = f_old.shape
     src = np.ascontiguousarray(src, np.int32); kind = np.ascontiguousarray(kind, np.int32)
     f_new = np.zeros((Nc, nA, len(src)))
-    lib().om_remap(D, Nc, Nv_old, _dp(f_old), len(src), _ip(src), _ip(kind), _dp(f_new))
+    lib().om_remap_n(D, nA, Nc, Nv_old, _dp(f_old), len(src), _ip(src), _ip(kind), _dp(f_new))
     return f_new
 
 
@@ -377,8 +470,10 @@ class Run:
         self.wl = wl
         self.D = wl.D
         self.mh = MeshHandle(wl.mesh)
+        self.rykov = getattr(wl, "model", "shakhov") == "rykov"
         self.g = gas(R=0.5, Pr=wl.Pr, omega=wl.omega, Kn=wl.Kn,
-                     limiter=wl.limiter if limiter is None else limiter)
+                     limiter=wl.limiter if limiter is None else limiter,
+                     model="rykov" if self.rykov else "shakhov", Zrot=getattr(wl, "Zrot", RYKOV_ZROT))
         self.corr_iters = corr_iters
         if getattr(wl, "flow", None) is not None:
             fl = wl.flow
@@ -409,6 +504,24 @@ class Run:
     def Nv(self):
         return len(self.level)
 
+    # model-dependent pieces: Shakhov (G[, H]; W = rho, rho U, rho E) or
+    # Rykov (G[, H], R; W adds rho E_rot)
+    def _init_f(self, Wp, amp=0.0, seed=12345):
+        if self.rykov:
+            return maxwell_init_rykov(self.D, self.xi, Wp, amp=amp, seed=seed)
+        return maxwell_init(self.D, self.xi, Wp, amp=amp, seed=seed)
+
+    def _moments(self, f):
+        if self.rykov:
+            return moments_rykov(self.D, self.xi, self.w, f)[0]
+        return moments(self.D, self.xi, self.w, f)[0]
+
+    def _cons(self, Wp):
+        return conserved_rykov(self.D, Wp) if self.rykov else conserved_from_primitive(self.D, Wp)
+
+    def _prim(self, Wc):
+        return primitive_rykov(self.D, Wc) if self.rykov else primitive_from_conserved(self.D, Wc)
+
     def initial_tree(self):
         """Step-0 AVS (Sec. 3.5, steps 1-3; reading R13): adapt on the two
         pseudo cells g^eq(W_inf) and g^eq(rho_inf, 0, T_inf) until stable."""
@@ -416,14 +529,14 @@ class Run:
         Winf = np.array(self.wl.W_inf, dtype=np.float64)
         W0 = Winf.copy(); W0[1:1 + D] = 0.0
         Wp = np.stack([Winf, W0])
-        Wc = conserved_from_primitive(D, Wp)
+        Wc = self._cons(Wp)
         for _ in range(self.p["init_refine"]):         # step 2: split every element
             nl, nb, nk, _, _ = adapt_tree(D, self.level, self.base, self.key, np.full(self.Nv, np.inf), self.s,
                                           0.0, -1.0, self.p["max_refine"])
             self.level, self.base, self.key = nl, nb, nk
             self._geom()
         for _ in range(max(1, self.p["max_refine"])):
-            f = maxwell_init(D, self.xi, Wp)
+            f = self._init_f(Wp)
             M = criterion(D, self.xi, self.w, f, Wc)
             nl, nb, nk, src, kind = self._marks(M)
             changed = len(nl) != self.Nv or np.any(nl != self.level) or np.any(nk != self.key)
@@ -434,8 +547,8 @@ class Run:
 
     def init_field(self, Wp=None, amp=0.0, seed=12345):
         Wp = self.wl.W_init if Wp is None else Wp
-        self.f = maxwell_init(self.D, self.xi, Wp, amp=amp, seed=seed)
-        self.Wc, _ = moments(self.D, self.xi, self.w, self.f)
+        self.f = self._init_f(Wp, amp=amp, seed=seed)
+        self.Wc = self._moments(self.f)
 
     def dt(self, cfl=None):
         return (self.wl.cfl if cfl is None else cfl) * dt_unit(self.mh, self.xi)
@@ -459,7 +572,7 @@ class Run:
         With bypass, f on the new mesh is g^eq of the carried W instead
         (the bypass for weakly non-equilibrium flows, end of Sec. 3.3)."""
         D = self.D
-        Wf, _ = moments(D, self.xi, self.w, self.f)
+        Wf = self._moments(self.f)
         Wcrit = Wf if Wc_override is None else Wc_override
         M = criterion(D, self.xi, self.w, self.f, Wcrit)
         nl, nb, nk, src, kind = self._marks(M)
@@ -468,8 +581,9 @@ class Run:
         self._geom()
         gap = 0.0
         if bypass:
-            f_new = maxwell_init(D, self.xi, primitive_from_conserved(D, self.Wc))
+            f_new = self._init_f(self._prim(self.Wc))
         elif correct_f:
-            gap = correct(D, self.xi, self.w, Wf, f_new, iters=self.corr_iters)
+            corr = correct_rykov if self.rykov else correct
+            gap = corr(D, self.xi, self.w, Wf, f_new, iters=self.corr_iters)
         self.f = f_new
         return dict(M=M, src=src, kind=kind, gap=gap, Nv=self.Nv)

@@ -78,6 +78,123 @@ static void shakhov(int D, double Pr, double rho, const double *U, double RT, co
     *gH = Heq + a * ((c2 / RT - D) * (3.0 - D)) * RT * geq;          /* + H_Pr      */
 }
 
+/* ---- Rykov model (diatomic gas; Sec. 2.1, Eqs. updat_W, 8, GHR_equ, 11-13) ----
+ * Reduced distributions: G, H, R in 2D and G, R in 3D (H carries the
+ * 3 - D dummy translational components and vanishes for D = 3; reading R23).
+ * W = (rho, rho U, rho E, rho E_rot) with rho E = int (xi^2 G + H)/2 + R and
+ * rho E_rot = int R.  With K = 2 rotational degrees of freedom (R24):
+ * rho E_rot = rho R T_r, (3/2) rho R T_t = rho E - rho U^2/2 - rho E_rot and
+ * the equilibrium temperature T = (3 T_t + 2 T_r) / 5. */
+static int nArrG(const om_gas *g, int D) { return g->model ? (D == 2 ? 3 : 2) : nArr(D); }
+static int nWG(const om_gas *g, int D) { return g->model ? D + 3 : D + 2; }
+
+static void prim_rykov(int D, const double *Wc, double *rho, double *U, double *RTt, double *RTr, double *RT)
+{
+    double r = Wc[0];
+    double m2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        U[d] = Wc[1 + d] / r;
+        m2 += Wc[1 + d] * Wc[1 + d];
+    }
+    *rho = r;
+    *RTr = Wc[D + 2] / r;
+    *RTt = (Wc[D + 1] - 0.5 * m2 / r - Wc[D + 2]) / (1.5 * r);
+    *RT = (Wc[D + 1] - 0.5 * m2 / r) / (2.5 * r);
+}
+
+/* Rykov equilibrium at one node (Eqs. GHR_equ, 11-13): out[0] = g^G,
+ * out[1] = g^H (2D), out[nA - 1] = g^R. */
+static void rykov(int D, const om_gas *g, double rho, const double *U, double RTt, double RTr,
+                  const double *qt, const double *qr, const double *xi, double *out)
+{
+    double c[3], c2 = 0.0, cqt = 0.0, cqr = 0.0;
+    for (int d = 0; d < D; ++d) {
+        c[d] = xi[d] - U[d];
+        c2 += c[d] * c[d];
+        cqt += c[d] * qt[d];
+        cqr += c[d] * qr[d];
+    }
+    double RT = (3.0 * RTt + 2.0 * RTr) / 5.0;
+    double gt = maxwell(D, rho, U, RTt, xi);
+    double gr = maxwell(D, rho, U, RT, xi);
+    double pt = rho * RTt, p = rho * RT;
+    double at = cqt / (15.0 * pt * RTt);
+    double ar = g->omega0 * cqt / (15.0 * p * RT);
+    double Gt = gt * (1.0 + at * (c2 / RTt - D - 2.0));
+    double Gr = gr * (1.0 + ar * (c2 / RT - D - 2.0));
+    double Ht = RTt * gt * (3.0 - D) * (1.0 + at * (c2 / RTt - D));
+    double Hr = RT * gr * (3.0 - D) * (1.0 + ar * (c2 / RT - D));
+    double Rt = RTr * (Gt + (1.0 - g->delta) * cqr / (pt * RTt) * gt);
+    double Rr = RT * (Gr + g->omega1 * (1.0 - g->delta) * cqr / (p * RT) * gr);
+    double iz = 1.0 / g->Zrot;
+    out[0] = (1.0 - iz) * Gt + iz * Gr;
+    if (D == 2) out[1] = (1.0 - iz) * Ht + iz * Hr;
+    out[D == 2 ? 2 : 1] = (1.0 - iz) * Rt + iz * Rr;
+}
+
+void om_rykov_field(int D, int Nv, const double *xi, const om_gas *g, double rho, const double *U,
+                    double RTt, double RTr, const double *qt, const double *qr, double *out)
+{
+    int nA = D == 2 ? 3 : 2;
+    for (int k = 0; k < Nv; ++k) {
+        double v[3];
+        rykov(D, g, rho, U, RTt, RTr, qt, qr, xi + (size_t)k * D, v);
+        for (int a = 0; a < nA; ++a) out[(size_t)a * Nv + k] = v[a];
+    }
+}
+
+/* Moments (Eqs. updat_W, 8): W = (rho, rho U, rho E, rho E_rot); about U,
+ * q_t = int c (c^2 G + H) / 2 and q_r = int c R. */
+static void cell_moments_rykov(int D, int Nv, const double *xi, const double *w, const double *fi,
+                               double *Wc, double *qt, double *qr)
+{
+    const double *G = fi, *H = D == 2 ? fi + Nv : NULL, *Rr = fi + (size_t)(D == 2 ? 2 : 1) * Nv;
+    double rho = 0.0, m[3] = {0, 0, 0}, E = 0.0, Er = 0.0;
+    for (int k = 0; k < Nv; ++k) {
+        const double *x = xi + (size_t)k * D;
+        double x2 = 0.0;
+        for (int d = 0; d < D; ++d) x2 += x[d] * x[d];
+        rho += w[k] * G[k];
+        for (int d = 0; d < D; ++d) m[d] += w[k] * x[d] * G[k];
+        E += w[k] * (0.5 * (x2 * G[k] + (H ? H[k] : 0.0)) + Rr[k]);
+        Er += w[k] * Rr[k];
+    }
+    Wc[0] = rho;
+    for (int d = 0; d < D; ++d) Wc[1 + d] = m[d];
+    Wc[D + 1] = E;
+    Wc[D + 2] = Er;
+    if (qt || qr) {
+        double U[3], a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) U[d] = m[d] / rho;
+        for (int k = 0; k < Nv; ++k) {
+            const double *x = xi + (size_t)k * D;
+            double c[3], c2 = 0.0;
+            for (int d = 0; d < D; ++d) {
+                c[d] = x[d] - U[d];
+                c2 += c[d] * c[d];
+            }
+            for (int d = 0; d < D; ++d) {
+                a[d] += 0.5 * w[k] * c[d] * (c2 * G[k] + (H ? H[k] : 0.0));
+                b[d] += w[k] * c[d] * Rr[k];
+            }
+        }
+        for (int d = 0; d < D; ++d) {
+            if (qt) qt[d] = a[d];
+            if (qr) qr[d] = b[d];
+        }
+    }
+}
+
+void om_moments_rykov(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
+                      double *Wc, double *qt, double *qr)
+{
+    int nA = D == 2 ? 3 : 2;
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < Nc; ++i)
+        cell_moments_rykov(D, Nv, xi, w, f + (size_t)i * nA * Nv, Wc + (size_t)i * (D + 3),
+                           qt ? qt + (size_t)i * D : NULL, qr ? qr + (size_t)i * D : NULL);
+}
+
 /* Shakhov equilibrium (G, H) of one state at every node; exported for tests. */
 void om_shakhov_field(int D, int Nv, const double *xi, double Pr, double rho, const double *U,
                       double RT, const double *q, double *gG, double *gH)
@@ -174,6 +291,25 @@ void om_maxwell_init(int D, int Nc, int Nv, const double *xi, const double *Wp, 
             if (amp != 0.0) G *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
             f[((size_t)i * nA + 0) * Nv + k] = G;
             if (nA == 2) f[((size_t)i * nA + 1) * Nv + k] = (3.0 - D) * RT * G;
+        }
+    }
+}
+
+/* Initial field: G = g^eq(rho, U, T_t)(1 + amp z_ik), H = (3 - D) R T_t G,
+ * R = R T_r G.  Wp per cell: rho, U (D), T_t, T_r. */
+void om_maxwell_init_rykov(int D, int Nc, int Nv, const double *xi, const double *Wp, double R,
+                           double amp, unsigned long long seed, double *f)
+{
+    int nA = D == 2 ? 3 : 2;
+    for (int i = 0; i < Nc; ++i) {
+        const double *P = Wp + (size_t)i * (D + 3);
+        double RTt = R * P[D + 1], RTr = R * P[D + 2];
+        for (int k = 0; k < Nv; ++k) {
+            double G = maxwell(D, P[0], P + 1, RTt, xi + (size_t)k * D);
+            if (amp != 0.0) G *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
+            f[((size_t)i * nA + 0) * Nv + k] = G;
+            if (D == 2) f[((size_t)i * nA + 1) * Nv + k] = (3.0 - D) * RTt * G;
+            f[((size_t)i * nA + nA - 1) * Nv + k] = RTr * G;
         }
     }
 }
@@ -362,7 +498,7 @@ static double venkat(double d1, double d2, double eps2)
 static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
                             double dt, const double *f_in, const slots_t *S, double *phi, double *F)
 {
-    const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
+    const int D = m->D, nA = nArrG(g, D), NW = nWG(g, D), Nc = m->Nc, Nf = m->Nf;
     memset(F, 0, (size_t)Nf * NW * sizeof(double));
     const double h = 0.5 * dt;
     double *Minv = (double *)calloc((size_t)Nc * 9, sizeof(double));
@@ -449,7 +585,37 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
                 pf[a * Nv + k] = f_in[o] + lim[o] * dot;
             }
         }
-        if (R >= 0) {
+        if (R >= 0 && g->model) {
+            /* Rykov interface state (R27): W from the foot values (Eq.
+             * w_interface), tau from T_t; the rotational energy relaxed over
+             * h toward rho R T (the second Eq. w_interface read as a backward
+             * Euler step, so its factor 1 + h/(Z tau) divides); T is fixed by
+             * the total energy; each heat flux relaxed over h at its rate in
+             * the model (the R4 rule): lambda_t = 2/3 + (1 - omega0)/(3 Z),
+             * lambda_r = 1 - (1 - delta)((1 - 1/Z) T_r/T_t + omega1/Z). */
+            double Wf[6], qt[3], qr[3];
+            cell_moments_rykov(D, Nv, xi, w, pf, Wf, qt, qr);
+            double rho, U[3], RTt, RTr, RT;
+            prim_rykov(D, Wf, &rho, U, &RTt, &RTr, &RT);
+            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) bad = 1;
+            double tau = tau_of(g, rho, RTt);
+            double az = h / (g->Zrot * tau);
+            RTr = (Wf[D + 2] + az * rho * RT) / (1.0 + az) / rho;
+            RTt = (5.0 * RT - 2.0 * RTr) / 3.0;
+            double lt = 2.0 / 3.0 + (1.0 - g->omega0) / (3.0 * g->Zrot);
+            double lr = 1.0 - (1.0 - g->delta) * ((1.0 - 1.0 / g->Zrot) * RTr / RTt + g->omega1 / g->Zrot);
+            double qtf[3], qrf[3];
+            for (int d = 0; d < D; ++d) {
+                qtf[d] = tau * qt[d] / (tau + h * lt);
+                qrf[d] = tau * qr[d] / (tau + h * lr);
+            }
+            double wa = tau / (tau + h), wb = h / (tau + h);                        /* Eq. equ28 */
+            for (int k = 0; k < Nv; ++k) {
+                double v[3];
+                rykov(D, g, rho, U, RTt, RTr, qtf, qrf, xi + (size_t)k * D, v);
+                for (int a = 0; a < nA; ++a) pf[a * Nv + k] = wa * pf[a * Nv + k] + wb * v[a];
+            }
+        } else if (R >= 0) {
             /* interface macroscopic state: Eq. (w_interface) */
             double Wf[5];
             cell_moments(D, Nv, xi, w, pf, Wf, NULL);
@@ -461,7 +627,7 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
                     const double *x = xi + (size_t)k * D;
                     double c[3], c2 = 0.0;
                     for (int d = 0; d < D; ++d) { c[d] = x[d] - U[d]; c2 += c[d] * c[d]; }
-                    double Hk = nA == 2 ? pf[Nv + k] : 0.0;
+                    double Hk = D == 2 ? pf[Nv + k] : 0.0;
                     for (int d = 0; d < D; ++d) qq[d] += 0.5 * w[k] * c[d] * (c2 * pf[k] + Hk);
                 }
                 for (int d = 0; d < D; ++d) qbar[d] = qq[d];
@@ -502,7 +668,8 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
                 if (sn >= 0.0) continue;
                 double gk = maxwell(D, rb, Ub, RTb, x);
                 pf[k] = gk;
-                if (nA == 2) pf[Nv + k] = (3.0 - D) * RTb * gk;
+                if (D == 2) pf[Nv + k] = (3.0 - D) * RTb * gk;
+                if (g->model) pf[(size_t)(nA - 1) * Nv + k] = RTb * gk;   /* rotational equilibrium at T_b (R29) */
             }
         }
         /* area-weighted flux  A F = sum_k w (xi . An) psi phi */
@@ -511,10 +678,16 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
             const double *x = xi + (size_t)k * D;
             double sn = 0.0, x2 = 0.0;
             for (int d = 0; d < D; ++d) { sn += x[d] * An[d]; x2 += x[d] * x[d]; }
-            double G = pf[k], H = nA == 2 ? pf[Nv + k] : 0.0;
+            double G = pf[k], H = D == 2 ? pf[Nv + k] : 0.0;
             Ff[0] += w[k] * sn * G;
             for (int d = 0; d < D; ++d) Ff[1 + d] += w[k] * sn * x[d] * G;
-            Ff[D + 1] += w[k] * sn * 0.5 * (x2 * G + H);
+            if (g->model) {
+                double Rk = pf[(size_t)(nA - 1) * Nv + k];
+                Ff[D + 1] += w[k] * sn * (0.5 * (x2 * G + H) + Rk);
+                Ff[D + 2] += w[k] * sn * Rk;
+            } else {
+                Ff[D + 1] += w[k] * sn * 0.5 * (x2 * G + H);
+            }
         }
     }
 
@@ -525,7 +698,7 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
 int om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
             double dt, const double *f_in, double *f_out, double *Wc)
 {
-    const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
+    const int D = m->D, nA = nArrG(g, D), NW = nWG(g, D), Nc = m->Nc, Nf = m->Nf;
     slots_t *S = build_slots(m);
     double *phi = (double *)malloc((size_t)Nf * nA * Nv * sizeof(double));
     double *F = (double *)calloc((size_t)Nf * NW, sizeof(double));
@@ -537,12 +710,45 @@ int om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const d
         double *Wi = Wc + (size_t)i * NW;
         const double *fi = f_in + (size_t)i * nA * Nv;
         double *fo = f_out + (size_t)i * nA * Nv;
-        double Wt[5];
+        double Wt[6];
         /* explicit conservative update, R2 */
         for (int c = 0; c < NW; ++c) {
             double s = 0.0;
             for (int sl = 0; sl < S[i].n; ++sl) s += S[i].sgn[sl] * F[(size_t)S[i].face[sl] * NW + c];
             Wt[c] = Wi[c] - dt / m->vol[i] * s;
+        }
+        if (g->model) {
+            /* Rykov (R28): the rotational source of Eq. (S_rot) taken
+             * implicitly, E_rot~ = (E_rot* + a rho R T)/(1 + a), a = dt/(Z tau),
+             * tau from T_t of the flux-updated state; the same tau in the
+             * collision update, so the moments of f^{n+1} are W~. */
+            double Wn[6], qt[3], qr[3];
+            cell_moments_rykov(D, Nv, xi, w, fi, Wn, qt, qr);       /* lagged heat fluxes (R3) */
+            double rho, U[3], RTt, RTr, RT;
+            prim_rykov(D, Wt, &rho, U, &RTt, &RTr, &RT);
+            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) bad = 1;
+            double tau = tau_of(g, rho, RTt);
+            double az = dt / (g->Zrot * tau);
+            Wt[D + 2] = (Wt[D + 2] + az * rho * RT) / (1.0 + az);
+            prim_rykov(D, Wt, &rho, U, &RTt, &RTr, &RT);
+            for (int k = 0; k < Nv; ++k) {
+                const double *x = xi + (size_t)k * D;
+                double v[3];
+                rykov(D, g, rho, U, RTt, RTr, qt, qr, x, v);
+                for (int a = 0; a < nA; ++a) {
+                    double N = 0.0;
+                    for (int sl = 0; sl < S[i].n; ++sl) {
+                        int f = S[i].face[sl];
+                        const double *An = m->An + (size_t)f * D;
+                        double sn = 0.0;
+                        for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                        N += S[i].sgn[sl] * sn * phi[((size_t)f * nA + a) * Nv + k];
+                    }
+                    fo[a * Nv + k] = (fi[a * Nv + k] / dt + v[a] / tau - N / m->vol[i]) / (1.0 / dt + 1.0 / tau);
+                }
+            }
+            for (int c = 0; c < NW; ++c) Wi[c] = Wt[c];
+            continue;
         }
         /* lagged heat flux of f^n (R3) */
         double Wn[5], qn[3];
@@ -649,6 +855,7 @@ int om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi
                      const int *color, int ncolor, int k_macro, int k_micro)
 {
     const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
+    if (g->model) return -1;                  /* the implicit step is built for the Shakhov model */
     slots_t *S = build_slots(m);
     double *phi = (double *)malloc((size_t)Nf * nA * Nv * sizeof(double));
     double *F = (double *)calloc((size_t)Nf * NW, sizeof(double));
@@ -805,10 +1012,17 @@ int om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi
 void om_criterion(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
                   const double *Wc, double *M)
 {
-    int nA = nArr(D);
+    om_criterion_nw(D, nArr(D), D + 2, Nc, Nv, xi, w, f, Wc, M);
+}
+
+/* The same with nA arrays per cell and nw conserved variables per cell (the
+ * Rykov model: e_int includes the rotational energy, R30). */
+void om_criterion_nw(int D, int nA, int nw, int Nc, int Nv, const double *xi, const double *w,
+                     const double *f, const double *Wc, double *M)
+{
     for (int k = 0; k < Nv; ++k) M[k] = -INFINITY;
     for (int i = 0; i < Nc; ++i) {
-        const double *W = Wc + (size_t)i * (D + 2);
+        const double *W = Wc + (size_t)i * nw;
         double rho = W[0];
         double U[3], mm = 0.0;
         for (int d = 0; d < D; ++d) {
@@ -899,7 +1113,12 @@ int om_adapt_tree(int D, int Nv, const int *level, const int *base, const unsign
 void om_remap(int D, int Nc, int Nv_old, const double *f_old, int Nv_new,
               const int *src, const int *kind, double *f_new)
 {
-    int nA = nArr(D);
+    om_remap_n(D, nArr(D), Nc, Nv_old, f_old, Nv_new, src, kind, f_new);
+}
+
+void om_remap_n(int D, int nA, int Nc, int Nv_old, const double *f_old, int Nv_new,
+                const int *src, const int *kind, double *f_new)
+{
     for (int i = 0; i < Nc; ++i) {
         for (int a = 0; a < nA; ++a) {
             const double *fo = f_old + ((size_t)i * nA + a) * Nv_old;
@@ -955,6 +1174,56 @@ double om_correct(int D, int Nc, int Nv, const double *xi, const double *w, doub
         }
         double t = fabs(Wp[D + 1] - Wt[D + 1]) / fabs(Wt[D + 1]);
         if (t > e) e = t;
+        if (e > worst || e != e) worst = e;
+    }
+    return worst;
+}
+
+/* Conservation correction for the Rykov model (Sec. 3.3 with R30): the
+ * equilibrium set g^M(W) = (G = g^eq(rho, U, T_t), H = (3 - D) R T_t G,
+ * R = R T_r G) carries (rho, rho U, rho E, rho E_rot) of W, and
+ * f <- f + g^M(W) - g^M(W') with W' the moments of f, `iters` times.
+ * Returns the largest relative gap as om_correct, with rho E_rot relative to
+ * rho E. */
+double om_correct_rykov(int D, int Nc, int Nv, const double *xi, const double *w, double R,
+                        int iters, const double *Wc_target, double *f)
+{
+    const int nA = D == 2 ? 3 : 2, NW = D + 3;
+    double worst = 0.0;
+    (void)R;
+    for (int i = 0; i < Nc; ++i) {
+        const double *Wt = Wc_target + (size_t)i * NW;
+        double *fi = f + (size_t)i * nA * Nv;
+        double rho, U[3], RTt, RTr, RT;
+        prim_rykov(D, Wt, &rho, U, &RTt, &RTr, &RT);
+        for (int it = 0; it < iters; ++it) {
+            double Wp[6];
+            cell_moments_rykov(D, Nv, xi, w, fi, Wp, NULL, NULL);
+            double rp, Up[3], RTtp, RTrp, RTp;
+            prim_rykov(D, Wp, &rp, Up, &RTtp, &RTrp, &RTp);
+            for (int k = 0; k < Nv; ++k) {
+                const double *x = xi + (size_t)k * D;
+                double ga = maxwell(D, rho, U, RTt, x);
+                double gb = maxwell(D, rp, Up, RTtp, x);
+                fi[k] += ga - gb;
+                if (D == 2) fi[Nv + k] += (3.0 - D) * (RTt * ga - RTtp * gb);
+                fi[(size_t)(nA - 1) * Nv + k] += RTr * ga - RTrp * gb;
+            }
+        }
+        double Wp[6];
+        cell_moments_rykov(D, Nv, xi, w, fi, Wp, NULL, NULL);
+        double mref = 0.0;
+        for (int d = 0; d < D; ++d) mref += Wt[1 + d] * Wt[1 + d];
+        mref = sqrt(mref) + rho * sqrt(2.0 * RT);
+        double e = fabs(Wp[0] - Wt[0]) / fabs(Wt[0]);
+        for (int d = 0; d < D; ++d) {
+            double t = fabs(Wp[1 + d] - Wt[1 + d]) / mref;
+            if (t > e) e = t;
+        }
+        for (int c = D + 1; c < NW; ++c) {
+            double t = fabs(Wp[c] - Wt[c]) / fabs(Wt[D + 1]);
+            if (t > e) e = t;
+        }
         if (e > worst || e != e) worst = e;
     }
     return worst;

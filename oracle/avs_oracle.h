@@ -5,8 +5,10 @@
  * product path.  It shares no code with the CUDA library.
  *
  * Layouts
- *   f      : [cell][array][node], array 0 = G, array 1 = H (2D only)
- *   Wc     : conserved variables per cell: rho, rho*U (D), rho*E
+ *   f      : [cell][array][node], array 0 = G, array 1 = H (2D only); with the
+ *            Rykov model a last array R (rotational energy)
+ *   Wc     : conserved variables per cell: rho, rho*U (D), rho*E; with the
+ *            Rykov model also rho*E_rot
  *   Wp     : primitive variables per cell: rho, U (D), T
  *   xi     : [node][D] velocity-mesh node (element centre), w : [node] weight
  *   mesh   : face list, see om_mesh
@@ -31,6 +33,8 @@ typedef struct {
     double R, Pr, omega, mu_ref, T_ref;
     double lim_K;                 /* Venkatakrishnan constant K              */
     int limiter;                  /* 0 first order, 1 Venkatakrishnan, 2 unlimited */
+    int model;                    /* 0 Shakhov (monatomic), 1 Rykov (diatomic) */
+    double Zrot, omega0, omega1, delta;   /* Rykov coefficients (Eqs. 11-13)  */
 } om_gas;
 
 enum { OM_COPY = 0, OM_MERGE = 1 };
@@ -68,6 +72,20 @@ void om_remap(int D, int Nc, int Nv_old, const double *f_old, int Nv_new,
               const int *src, const int *kind, double *f_new);
 double om_correct(int D, int Nc, int Nv, const double *xi, const double *w, double R,
                   int iters, const double *Wc_target, double *f);
+
+/* Rykov model (diatomic gas, K = 2 rotational degrees of freedom) */
+void om_rykov_field(int D, int Nv, const double *xi, const om_gas *g, double rho, const double *U,
+                    double RTt, double RTr, const double *qt, const double *qr, double *out);
+void om_maxwell_init_rykov(int D, int Nc, int Nv, const double *xi, const double *Wp, double R,
+                           double amp, unsigned long long seed, double *f);
+void om_moments_rykov(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
+                      double *Wc, double *qt, double *qr);
+void om_criterion_nw(int D, int nA, int nw, int Nc, int Nv, const double *xi, const double *w,
+                     const double *f, const double *Wc, double *M);
+void om_remap_n(int D, int nA, int Nc, int Nv_old, const double *f_old, int Nv_new,
+                const int *src, const int *kind, double *f_new);
+double om_correct_rykov(int D, int Nc, int Nv, const double *xi, const double *w, double R,
+                        int iters, const double *Wc_target, double *f);
 
 #ifdef __cplusplus
 }

@@ -460,6 +460,8 @@ class Workload:
     adapt_every: int = 50
     extra: dict = field(default_factory=dict)
     flow: FlowSpec = None      # set: base, vlo, vhi, max_refine, C1, C2 come from the Sec. 3.5 rules
+    model: str = "shakhov"     # "shakhov" (monatomic) or "rykov" (diatomic, K = 2)
+    Zrot: float = 3.5          # rotational collision number of the Rykov model
 
 
 def mach_speed(Ma, gamma=GAMMA_MONO, T=1.0):
