@@ -16,10 +16,12 @@
  * context, ordered on its stream) when it is 1.  Input pointers are borrowed
  * for the duration of the call only.  Output buffers are owned by the caller.
  *
- * Layouts
- *   f    [cell][array][node]  (array 0 = G, array 1 = H in 2D), FP64 on the ABI
- *   Wc   [cell][D+2]          conserved: rho, rho*U (D), rho*E
- *   Wp   [cell][D+2]          primitive: rho, U (D), T
+ * Layouts (NW = D+2 for the Shakhov model, D+3 for the Rykov model)
+ *   f    [cell][array][node]  (array 0 = G, array 1 = H in 2D; Rykov: last array R),
+ *                             FP64 on the ABI
+ *   Wc   [cell][NW]           conserved: rho, rho*U (D), rho*E (Rykov: total, with the
+ *                             rotational energy), and for Rykov rho*E_rot
+ *   Wp   [cell][NW]           primitive: rho, U (D), T (Rykov: T_t, T_r)
  *   q    [cell][D]            heat flux (Eq. 8)
  *   xi   [node][D], w [node]  velocity node (element centre) and weight (Sec. 3)
  */
@@ -46,6 +48,12 @@ typedef enum {
 } avs_status;
 
 enum { AVS_FP64 = 0, AVS_MIXED = 1 };
+enum { AVS_SHAKHOV = 0, AVS_RYKOV = 1 };
+
+/* Rykov coefficients for nitrogen (Sec. 2.1, after Eq. 13) */
+#define AVS_RYKOV_DELTA (1.0 / 1.55)
+#define AVS_RYKOV_OMEGA0 0.2354
+#define AVS_RYKOV_OMEGA1 0.3049
 enum { AVS_BC_WALL = 1, AVS_BC_FARFIELD = 2 };
 enum { AVS_LIM_FIRST_ORDER = 0, AVS_LIM_VENKAT = 1, AVS_LIM_NONE = 2 };
 
@@ -88,6 +96,11 @@ typedef struct {
     avs_zone zones[AVS_MAX_ZONES];
     int init_refine;      /* uniform splits of every base element before the step-0 adaptation
                              (Sec. 3.5 step 2); 0..max_refine                                */
+    int model;            /* AVS_SHAKHOV (monatomic, Eqs. 14-17) or AVS_RYKOV (diatomic,
+                             Eqs. GHR_equ, 11-13).  Rykov: f has the arrays G, H, R in 2D and
+                             G, R in 3D; W adds rho E_rot (NW = D+3 values per cell); no
+                             learned proposer and no implicit step                          */
+    double Zrot;          /* rotational collision number Z_rot of the Rykov model (>= 1)     */
 } avs_config;
 
 /* Flow data for the adaptive parameters of Sec. 3.5 (avs_paper_parameters). */
@@ -126,7 +139,7 @@ typedef struct {
 } avs_adapt_stats;
 
 typedef struct {
-    const double *W_override; /* nullable: conserved W [Nc][D+2] used by the criterion and as
+    const double *W_override; /* nullable: conserved W [Nc][NW] used by the criterion and as
                                  the correction target instead of the moments of f           */
     int W_is_device;
     int skip_correction;      /* 1: remap only (Sec. 3.2), no Sec. 3.3 correction             */
@@ -149,7 +162,9 @@ int        avs_num_cells(const avs_ctx *ctx);
 
 /* f = g^eq(Wp_i)(xi_k) (1 + amp z_ik), H = (3-D) R T G (Eq. 16), with z_ik a
  * standard normal from SplitMix64 (key (i << 32) | k, Box-Muller); then the
- * carried W = moments of f (Eq. 7).  Wp: primitive, host or device. */
+ * carried W = moments of f (Eq. 7).  Wp: primitive [Nc][NW], host or device.
+ * Rykov model: G = g^eq(rho, U, T_t)(1 + amp z), H = (3-D) R T_t G,
+ * R = R T_r G from Wp = (rho, U, T_t, T_r), and W by Eq. (updat_W). */
 avs_status avs_init_field(avs_ctx *ctx, const double *Wp, int is_device, double amp, uint64_t seed);
 
 /* dt = cfl * min over cells i and nodes k of |V_i| / sum_j A_ij max(xi_k . n_ij, 0). */

@@ -54,7 +54,7 @@ class Config(C.Structure):
                 ("W_inf", C.c_double * 5), ("limiter", C.c_int), ("lim_K", C.c_double),
                 ("corr_iters", C.c_int), ("max_nodes", C.c_int), ("learned_full_every", C.c_int),
                 ("nzones", C.c_int), ("zone_outside_level", C.c_int), ("zones", Zone * MAX_ZONES),
-                ("init_refine", C.c_int)]
+                ("init_refine", C.c_int), ("model", C.c_int), ("Zrot", C.c_double)]
 
 
 class FlowSpecS(C.Structure):
@@ -158,7 +158,9 @@ class AVS:
         L = load()
         self.wl = wl
         self.D = wl.D
-        self.NA = 2 if wl.D == 2 else 1
+        self.rykov = getattr(wl, "model", "shakhov") == "rykov"
+        self.NA = (3 if wl.D == 2 else 2) if self.rykov else (2 if wl.D == 2 else 1)
+        self.NW = wl.D + (3 if self.rykov else 2)
         m = wl.mesh
         self._mesh_keep = [m.faceL, m.faceR, m.An, m.rL, m.rR, m.vol, m.bc]
         dp = C.POINTER(C.c_double)
@@ -191,6 +193,8 @@ class AVS:
         cfg.corr_iters = corr_iters
         cfg.max_nodes = max_nodes
         cfg.learned_full_every = full_every
+        cfg.model = 1 if self.rykov else 0
+        cfg.Zrot = float(getattr(wl, "Zrot", 3.5))
         if wl.flow is not None:
             _fill_paper_parameters(L, wl.D, wl.flow, cfg)
         self.cfg = cfg
@@ -228,8 +232,16 @@ class AVS:
 
     # ------------------------------------------------------------------ API
     def init_field(self, Wp=None, amp=0.0, seed=12345):
+        """Maxwellian start from primitive W per cell (rho, U, T; the Rykov
+        model also takes T_r as a last column, else T_r = T)."""
         Wp = np.ascontiguousarray(self.wl.W_init if Wp is None else Wp, dtype=np.float64) \
             if not _is_torch(Wp) else Wp
+        if self.rykov and Wp.shape[1] == self.D + 2:
+            if _is_torch(Wp):
+                import torch
+                Wp = torch.cat([Wp, Wp[:, self.D + 1:self.D + 2]], dim=1).contiguous()
+            else:
+                Wp = np.ascontiguousarray(np.concatenate([Wp, Wp[:, self.D + 1:self.D + 2]], axis=1))
         p, dev = _ptr(Wp)
         self._ck(self.L.avs_init_field(self.h, p, dev, float(amp), int(seed)))
 
@@ -278,7 +290,7 @@ class AVS:
     def moments(self, out_W=None, out_q=None):
         """Carried conserved W and heat flux q of f (host numpy by default)."""
         if out_W is None and out_q is None:
-            out_W = np.zeros((self.Nc, self.D + 2))
+            out_W = np.zeros((self.Nc, self.NW))
             out_q = np.zeros((self.Nc, self.D))
         pW, dW = _ptr(out_W)
         pq, dq = _ptr(out_q)
@@ -286,7 +298,7 @@ class AVS:
         return out_W, out_q
 
     def f_moments(self):
-        out = np.zeros((self.Nc, self.D + 2))
+        out = np.zeros((self.Nc, self.NW))
         self._ck(self.L.avs_f_moments(self.h, out.ctypes.data, 0))
         return out
 

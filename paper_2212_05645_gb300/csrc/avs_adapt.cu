@@ -262,9 +262,49 @@ __global__ void __launch_bounds__(256) k_maxwell(int D, int NA, int Nv, int Nvp,
     }
 }
 
+// Rykov model: G = g^eq(rho, U, T_t)(1 + amp z_ik), H = (3 - D) R T_t G,
+// R = R T_r G from Wp = (rho, U, T_t, T_r); evaluated in FP64, then stored.
+template <typename T>
+__global__ void __launch_bounds__(256) k_maxwell_rk(int D, int NA, int Nv, int Nvp, const double* __restrict__ xi,
+                                                    const double* __restrict__ Wp, double R, double amp,
+                                                    uint64_t seed, T* f)
+{
+    const int i = blockIdx.x;
+    T* fi = f + (size_t)i * NA * Nvp;
+    const double* P = Wp + (size_t)i * (D + 3);
+    const double rho = P[0], RTt = R * P[D + 1], RTr = R * P[D + 2];
+    const double pref = rho / pow(2.0 * AVS_PI * RTt, 0.5 * D);
+    for (int k = threadIdx.x; k < Nvp; k += blockDim.x) {
+        if (k >= Nv) {
+            for (int a = 0; a < NA; ++a) fi[(size_t)a * Nvp + k] = T(0);
+            continue;
+        }
+        double c2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double c = xi[(size_t)k * D + d] - P[1 + d];
+            c2 += c * c;
+        }
+        double g = pref * exp(-c2 / (2.0 * RTt));
+        if (amp != 0.0) g *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
+        fi[k] = (T)g;
+        if (D == 2) fi[Nvp + k] = (T)((3 - D) * RTt * g);
+        fi[(size_t)(NA - 1) * Nvp + k] = (T)(RTr * g);
+    }
+}
+
 cudaError_t launch_maxwell(avs_ctx* c, const double* Wp, int Ncells, double amp, uint64_t seed, void* fout,
                            int f_is_double, int Nvp)
 {
+    if (c->model == AVS_RYKOV) {
+        if (f_is_double || !c->mixed)
+            k_maxwell_rk<double><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp,
+                                                                seed, (double*)fout);
+        else
+            k_maxwell_rk<float><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp,
+                                                               seed, (float*)fout);
+        c->launches += 1;
+        return cudaGetLastError();
+    }
     if (f_is_double || !c->mixed)
         k_maxwell<double><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, c->xi_f, Wp, c->cfg.R, amp,
                                                          seed, (double*)fout);
@@ -355,6 +395,7 @@ static cudaError_t cell_moments_t(avs_ctx* c, const T* f, const T* xi, const T* 
 cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wc_out,
                                 double* q_out)
 {
+    if (c->model == AVS_RYKOV) return rk_launch_moments(c, f, f_is_double, Ncells, Nvp, Wc_out, q_out);
     const bool dbl = f_is_double || !c->mixed;
     const double* Wref = (Ncells == c->Nc) ? c->W[c->wcur] : nullptr;
     if (c->D == 2)
@@ -368,11 +409,11 @@ cudaError_t launch_cell_moments(avs_ctx* c, const void* f, int f_is_double, int 
 // Per-cell inputs of the criterion, in the fixed order of the definition:
 // rho, U_d = m_d / rho, e_int = rho E - 0.5 (sum m_d m_d) / rho.  The FP32
 // screening form holds 1/rho, U_d, 0.5/e_int rounded to FP32.
-__global__ void k_crit_cells(int D, int Ncells, const double* __restrict__ Wc, double* cp, float* cp32)
+__global__ void k_crit_cells(int D, int NW, int Ncells, const double* __restrict__ Wc, double* cp, float* cp32)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Ncells) return;
-    const double* W = Wc + (size_t)i * (D + 2);
+    const double* W = Wc + (size_t)i * NW;
     const double rho = W[0];
     double mm = 0.0;
     float* c32 = cp32 + (size_t)i * 8;
@@ -538,7 +579,7 @@ cudaError_t launch_criterion(avs_ctx* c, const void* f, int f_is_double, int Nce
                              const int* cells, int ncells_list, int decide)
 {
     double* cp = c->crit_cp;
-    k_crit_cells<<<(Ncells + 255) / 256, 256, 0, c->stream>>>(c->D, Ncells, Wc, cp, c->crit_cp32);
+    k_crit_cells<<<(Ncells + 255) / 256, 256, 0, c->stream>>>(c->D, c->NW, Ncells, Wc, cp, c->crit_cp32);
     const unsigned long long ninf = dkey(-INFINITY);
     k_fill_key<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mkey, c->Nv, ninf);
     k_fill_u32<<<(c->Nv + 255) / 256, 256, 0, c->stream>>>(c->Mlo, c->Nv, 0x007fffffu);   // key of -inf
@@ -823,6 +864,7 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
 
 cudaError_t launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters)
 {
+    if (c->model == AVS_RYKOV) return rk_launch_correct(c, f, Wtarget, iters);
     const unsigned long long zero = dkey(0.0);
     cudaError_t e = cudaMemcpyAsync(c->gap_d, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return e;

@@ -205,6 +205,7 @@ void mlp_default_params(std::vector<float>& P)
 
 avs_status ensure_mlp(avs_ctx* c, int rows)
 {
+    if (c->model != AVS_SHAKHOV) return fail(c, AVS_EINVAL, "the learned proposer is built for the Shakhov model");
     if (c->mlp_P && rows <= c->mlp_rows) return AVS_OK;
     const int nrows = std::max(rows, std::max(c->Nc, 1024));
     if (!c->mlp_P) {
@@ -260,6 +261,9 @@ avs_status validate(const avs_config* cfg, const avs_mesh* m, std::string& why)
             if (!std::isfinite(Z.c[d])) { why = "zone centre not finite"; return AVS_EINVAL; }
     }
     if (cfg->init_refine < 0 || cfg->init_refine > cfg->max_refine) { why = "init_refine out of range"; return AVS_EINVAL; }
+    if (cfg->model != AVS_SHAKHOV && cfg->model != AVS_RYKOV) { why = "bad model"; return AVS_EINVAL; }
+    if (cfg->model == AVS_RYKOV && !(cfg->Zrot >= 1.0)) { why = "Zrot must be at least 1"; return AVS_EINVAL; }
+    if (cfg->model == AVS_RYKOV && cfg->learned) { why = "the learned proposer is built for the Shakhov model"; return AVS_EINVAL; }
     if (m->Nc <= 0 || m->Nf <= 0 || m->nbc < 0) { why = "empty mesh"; return AVS_EINVAL; }
     if (!m->faceL || !m->faceR || !m->An || !m->rL || !m->rR || !m->vol || (m->nbc > 0 && !m->bc)) {
         why = "null mesh array";
@@ -367,7 +371,7 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
         dalloc(&c->vol, Nc) || dalloc(&c->bc, (size_t)std::max(1, c->nbc) * 6) || dalloc(&c->slot, ncs) ||
         dalloc(&c->nslot, Nc) || dalloc(&c->nbr, ncs) || dalloc(&c->cg_d, ncsd) || dalloc(&c->r_d, ncsd) ||
         dalloc(&c->eps2_d, Nc) || dalloc(&c->cg_f, ncsd) || dalloc(&c->r_f, ncsd) || dalloc(&c->eps2_f, Nc) ||
-        dalloc(&c->AFf, (size_t)Nf * (D + 2)) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * avs::NMom<3>::v) ||
+        dalloc(&c->AFf, (size_t)Nf * c->NW) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * avs::NMom<3>::v) ||
         dalloc((unsigned char**)&c->cpar, (size_t)Nc * AVS_CELLPAR_BYTES) || dalloc(&c->clist, Nc) ||
         dalloc(&c->imp_dW, (size_t)Nc * (D + 2)) || dalloc(&c->imp_rhs0, (size_t)Nc * (D + 2)) ||
         dalloc(&c->imp_diag, Nc) || dalloc(&c->imp_Wta, (size_t)Nc * (D + 2)) ||
@@ -446,22 +450,27 @@ avs_status initial_tree(avs_ctx* c)
     c->Nv = nbase;
     c->Nvp = round_up(nbase, 32);
     CK(launch_geom(c));
-    double Wp[2][5] = {{0}}, Wc[2][5];
+    const int NW = c->NW;
+    double Wp[2][6] = {{0}}, Wc[2][6];
     for (int m = 0; m < D + 2; ++m) Wp[0][m] = Wp[1][m] = c->cfg.W_inf[m];
     for (int d = 0; d < D; ++d) Wp[1][1 + d] = 0.0;
+    if (c->model == AVS_RYKOV) Wp[0][D + 2] = Wp[1][D + 2] = c->cfg.W_inf[D + 1];   // T_r = T_t
     std::vector<double> wpv, wcv;
     for (int j = 0; j < 2; ++j) {
         cons_host(D, Wp[j], c->cfg.R, Wc[j]);
-        for (int m = 0; m < D + 2; ++m) {
+        if (c->model == AVS_RYKOV) {
+            // rho E_rot = rho R T_r (K = 2), added to the total energy
+            Wc[j][D + 2] = Wp[j][0] * c->cfg.R * Wp[j][D + 2];
+            Wc[j][D + 1] += Wc[j][D + 2];
+        }
+        for (int m = 0; m < NW; ++m) {
             wpv.push_back(Wp[j][m]);
             wcv.push_back(Wc[j][m]);
         }
     }
-    for (int m = 0; m < D + 2; ++m) {
-        if (!(Wp[0][0] > 0) || !(Wp[0][D + 1] > 0)) return fail(c, AVS_EINVAL, "W_inf must have rho, T > 0");
-    }
+    if (!(Wp[0][0] > 0) || !(Wp[0][D + 1] > 0)) return fail(c, AVS_EINVAL, "W_inf must have rho, T > 0");
     double* Wp_d = c->pseudo_W;
-    double* Wc_d = c->pseudo_W + 2 * (D + 2);
+    double* Wc_d = c->pseudo_W + 2 * NW;
     CK(up(Wp_d, wpv, c->stream));
     CK(up(Wc_d, wcv, c->stream));
     // step 2 of Sec. 3.5: uniform splits of every element before the adaptation
@@ -503,7 +512,9 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     avs_ctx* c = new avs_ctx();
     c->cfg = *cfg;
     c->D = cfg->dim;
-    c->NA = cfg->dim == 2 ? 2 : 1;
+    c->model = cfg->model;
+    c->NA = cfg->model == AVS_RYKOV ? (cfg->dim == 2 ? 3 : 2) : (cfg->dim == 2 ? 2 : 1);
+    c->NW = cfg->dim + 2 + (cfg->model == AVS_RYKOV ? 1 : 0);
     c->Nc = mesh->Nc;
     c->Nf = mesh->Nf;
     c->nbc = mesh->nbc;
@@ -535,7 +546,7 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     cap = std::max<long long>(cap, nbase);
     c->cap = (int)cap;
     const int capp = round_up(c->cap, 32);
-    const int NW = c->D + 2;
+    const int NW = c->NW;
 #define AL(p, n) \
     if (dalloc(&(p), (n)) != cudaSuccess) { st = fail(c, AVS_ENOMEM, "allocation of " #p); goto bad; }
     AL(c->level, capp); AL(c->base, capp); AL(c->key, capp);
@@ -601,16 +612,19 @@ avs_status avs_init_field(avs_ctx* c, const double* Wp, int is_device, double am
 {
     if (!c || !Wp) return AVS_EINVAL;
     c->mom_valid = 0;                 // f or W change outside a step
-    const size_t n = (size_t)c->Nc * (c->D + 2);
+    const size_t n = (size_t)c->Nc * c->NW;
     const double* Wp_d = Wp;
     if (!is_device) {
         CK(cudaMemcpyAsync(c->Wf, Wp, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         Wp_d = c->Wf;
     }
     CK(launch_maxwell(c, Wp_d, c->Nc, amp, seed, c->f[c->cur], 0, c->Nvp));
-    k_prim_to_cons<<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nc, Wp_d, c->cfg.R, c->W[c->wcur]);
-    c->launches += 1;
-    CK(cudaGetLastError());
+    if (c->model == AVS_SHAKHOV) {
+        // W of the primitive input: the reference velocity of the moment sums below
+        k_prim_to_cons<<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nc, Wp_d, c->cfg.R, c->W[c->wcur]);
+        c->launches += 1;
+        CK(cudaGetLastError());
+    }
     // carried W = moments of the discrete initial f (Eq. 7)
     CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->W[c->wcur], nullptr));
     if (!is_device) CK(cudaStreamSynchronize(c->stream));
@@ -628,7 +642,10 @@ avs_status ugks_step_dt(avs_ctx* c, int nsteps, double dt)
 {
     if (!c || nsteps < 0 || !(dt > 0)) return AVS_EINVAL;
     for (int s = 0; s < nsteps; ++s) {
-        CK(launch_step(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt));
+        if (c->model == AVS_RYKOV)
+            CK(rk_launch_step(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt));
+        else
+            CK(launch_step(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt));
         c->cur ^= 1;
         c->wcur ^= 1;
     }
@@ -638,6 +655,7 @@ avs_status ugks_step_dt(avs_ctx* c, int nsteps, double dt)
 avs_status ugks_step_implicit(avs_ctx* c, int nsteps, double dt, int k_macro, int k_micro)
 {
     if (!c || nsteps < 0 || !(dt > 0) || k_macro < 0 || k_micro < 0) return AVS_EINVAL;
+    if (c->model != AVS_SHAKHOV) return fail(c, AVS_EINVAL, "the implicit step is built for the Shakhov model");
     for (int s = 0; s < nsteps; ++s) {
         CK(launch_step_implicit(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt, k_macro,
                                 k_micro));
@@ -739,7 +757,7 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
     c->mom_valid = 0;                 // f or W change outside a step
     avs_adapt_opts o = {};
     if (opts) o = *opts;
-    const int NW = c->D + 2;
+    const int NW = c->NW;
     const int Nv_old = c->Nv, Nvp_old = c->Nvp;
     // moments of f on the old mesh (Eq. 7): criterion input and correction
     // target; with the proposer also the heat flux of its features
@@ -806,8 +824,12 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
     CK(launch_geom(c));
     if (o.bypass) {
         // f = g^eq(W) of the carried W on the new mesh (the bypass of Sec. 3.3)
-        k_cons_to_prim<<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nc, c->W[c->wcur], c->cfg.R, c->Wf);
-        c->launches += 1;
+        if (c->model == AVS_RYKOV) {
+            CK(rk_launch_cons_to_prim(c, c->W[c->wcur], c->Wf));
+        } else {
+            k_cons_to_prim<<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nc, c->W[c->wcur], c->cfg.R, c->Wf);
+            c->launches += 1;
+        }
         CK(launch_maxwell(c, c->Wf, c->Nc, 0.0, 0, dst, 0, Nvp_new));
     }
     if (n0) {
@@ -851,7 +873,7 @@ avs_status avs_moments(avs_ctx* c, double* Wc_out, double* q_out, int is_device)
     if (!c) return AVS_EINVAL;
     const cudaMemcpyKind kd = is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (Wc_out)
-        CK(cudaMemcpyAsync(Wc_out, c->W[c->wcur], sizeof(double) * c->Nc * (c->D + 2), kd, c->stream));
+        CK(cudaMemcpyAsync(Wc_out, c->W[c->wcur], sizeof(double) * c->Nc * c->NW, kd, c->stream));
     if (q_out) {
         CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, nullptr, c->q));
         CK(cudaMemcpyAsync(q_out, c->q, sizeof(double) * c->Nc * c->D, kd, c->stream));
@@ -864,7 +886,7 @@ avs_status avs_f_moments(avs_ctx* c, double* Wc_out, int is_device)
 {
     if (!c || !Wc_out) return AVS_EINVAL;
     CK(launch_cell_moments(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, nullptr));
-    CK(cudaMemcpyAsync(Wc_out, c->Wf, sizeof(double) * c->Nc * (c->D + 2),
+    CK(cudaMemcpyAsync(Wc_out, c->Wf, sizeof(double) * c->Nc * c->NW,
                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!is_device) CK(cudaStreamSynchronize(c->stream));
     return AVS_OK;
@@ -874,7 +896,7 @@ avs_status avs_set_W(avs_ctx* c, const double* Wc, int is_device)
 {
     if (!c || !Wc) return AVS_EINVAL;
     c->mom_valid = 0;                 // f or W change outside a step
-    CK(cudaMemcpyAsync(c->W[c->wcur], Wc, sizeof(double) * c->Nc * (c->D + 2),
+    CK(cudaMemcpyAsync(c->W[c->wcur], Wc, sizeof(double) * c->Nc * c->NW,
                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (!is_device) CK(cudaStreamSynchronize(c->stream));
     return AVS_OK;
@@ -883,7 +905,7 @@ avs_status avs_set_W(avs_ctx* c, const double* Wc, int is_device)
 avs_status avs_criterion(avs_ctx* c, const double* Wc, int W_is_device, double* M_out, int M_is_device)
 {
     if (!c || !M_out) return AVS_EINVAL;
-    const int NW = c->D + 2;
+    const int NW = c->NW;
     if (Wc)
         CK(cudaMemcpyAsync(c->Wf, Wc, sizeof(double) * c->Nc * NW,
                            W_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));

@@ -28,6 +28,8 @@ struct avs_ctx {
     avs_config cfg;
     ZoneSet zs;
     int D = 2, NA = 2, Nc = 0, Nf = 0, nbc = 0;
+    int model = 0;           // AVS_SHAKHOV or AVS_RYKOV
+    int NW = 4;              // conserved variables per cell: D+2, or D+3 for the Rykov model
     int mixed = 0;
     cudaStream_t stream = nullptr;
     std::string err;
@@ -131,6 +133,12 @@ int round_up(int n, int m);
 
 // ---- launchers (avs_step.cu)
 cudaError_t launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
+// Rykov model (csrc/avs_rykov.cu)
+cudaError_t rk_launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
+cudaError_t rk_launch_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wout,
+                              double* qout);
+cudaError_t rk_launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters);
+cudaError_t rk_launch_cons_to_prim(avs_ctx* c, const double* Wc, double* Wp);
 cudaError_t launch_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int short_by, int* passed_dev);
 cudaError_t launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt,
                                  int k_macro, int k_micro);

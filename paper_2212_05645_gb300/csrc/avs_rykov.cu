@@ -1,0 +1,734 @@
+// Rykov model (diatomic gas, K = 2 rotational degrees of freedom) on the GPU:
+// the explicit UGKS step, the cell moments and the conservation correction
+// for the reduced distributions G, H, R in 2D and G, R in 3D (Sec. 2.1,
+// Eqs. updat_W, 8, GHR_equ, 11-13; interface state of Sec. 2.3.3).
+//
+// W = (rho, rho U, rho E, rho E_rot): rho E = int (xi^2 G + H)/2 + R,
+// rho E_rot = int R = rho R T_r, (3/2) rho R T_t = rho E - rho U^2/2 - rho E_rot,
+// and the equilibrium temperature T = (3 T_t + 2 T_r) / 5.
+//
+// The kernels take one block per face or cell and sum over the nodes in FP64;
+// the equilibrium is evaluated in the element type (FP32 in the mixed form).
+#include <algorithm>
+
+#include "avs_dev.cuh"
+#include "avs_internal.h"
+
+namespace avs {
+namespace {
+
+constexpr int RK_NT = 128;
+
+template <int D>
+struct RkNA {
+    static constexpr int v = D == 2 ? 3 : 2;
+};
+
+// gas constants and the Rykov coefficients: Z_rot, iz = 1/Z_rot, omega0, omega1, delta
+struct RkGas {
+    double R, mu_ref, T_ref, omega, Z, iz, om0, om1, dl;
+};
+
+// conserved -> rho, U, R T_t, R T_r, R T
+template <int D>
+__device__ void rk_prim(const double* W, double& rho, double* U, double& RTt, double& RTr, double& RT)
+{
+    rho = W[0];
+    double m2 = 0.0;
+    for (int d = 0; d < 3; ++d) U[d] = 0.0;
+    for (int d = 0; d < D; ++d) {
+        U[d] = W[1 + d] / rho;
+        m2 += W[1 + d] * W[1 + d];
+    }
+    RTr = W[D + 2] / rho;
+    RTt = (W[D + 1] - 0.5 * m2 / rho - W[D + 2]) / (1.5 * rho);
+    RT = (W[D + 1] - 0.5 * m2 / rho) / (2.5 * rho);
+}
+
+// tau = mu(T_t) / p_t with the VHS viscosity (Eq. 3)
+__device__ double rk_tau(const RkGas& g, double rho, double RTt)
+{
+    const double T = RTt / g.R;
+    const double mu = g.mu_ref * pow(T / g.T_ref, g.omega);
+    return mu / (rho * RTt);
+}
+
+// Parameters of the Rykov equilibrium of one state, in the element type.
+template <typename T>
+struct RkEq {
+    T U[3];
+    T pt, pr;                 // rho / (2 pi R T_t)^(D/2), rho / (2 pi R T)^(D/2)
+    T RTt, RTr, RT;
+    T at[3], ar[3];           // q_t / (15 p_t R T_t), omega0 q_t / (15 p R T)
+    T bt[3], br[3];           // (1 - delta) q_r / (p_t R T_t), omega1 (1 - delta) q_r / (p R T)
+    T iz;
+};
+
+template <int D, typename T>
+__device__ RkEq<T> rk_make(const RkGas& g, double rho, const double* U, double RTt, double RTr, const double* qt,
+                           const double* qr)
+{
+    RkEq<T> e;
+    const double RT = (3.0 * RTt + 2.0 * RTr) / 5.0;
+    const double pt = rho * RTt, p = rho * RT;
+    for (int d = 0; d < 3; ++d) {
+        const bool on = d < D;
+        e.U[d] = on ? (T)U[d] : T(0);
+        e.at[d] = on ? (T)(qt[d] / (15.0 * pt * RTt)) : T(0);
+        e.ar[d] = on ? (T)(g.om0 * qt[d] / (15.0 * p * RT)) : T(0);
+        e.bt[d] = on ? (T)((1.0 - g.dl) * qr[d] / (pt * RTt)) : T(0);
+        e.br[d] = on ? (T)(g.om1 * (1.0 - g.dl) * qr[d] / (p * RT)) : T(0);
+    }
+    e.pt = (T)(rho / pow(2.0 * AVS_PI * RTt, 0.5 * D));
+    e.pr = (T)(rho / pow(2.0 * AVS_PI * RT, 0.5 * D));
+    e.RTt = (T)RTt;
+    e.RTr = (T)RTr;
+    e.RT = (T)RT;
+    e.iz = (T)g.iz;
+    return e;
+}
+
+// Eqs. (GHR_equ), (11)-(13) at one node: out[0] = g^G, out[1] = g^H (2D),
+// out[NA - 1] = g^R.
+template <int D, typename T>
+__device__ __forceinline__ void rk_eval(const RkEq<T>& e, const T* x, T* out)
+{
+    T c2 = T(0), cat = T(0), car = T(0), cbt = T(0), cbr = T(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const T c = x[d] - e.U[d];
+        c2 += c * c;
+        cat += c * e.at[d];
+        car += c * e.ar[d];
+        cbt += c * e.bt[d];
+        cbr += c * e.br[d];
+    }
+    const T gt = e.pt * ex(-c2 / (T(2) * e.RTt));
+    const T gr = e.pr * ex(-c2 / (T(2) * e.RT));
+    const T Gt = gt * (T(1) + cat * (c2 / e.RTt - T(D + 2)));
+    const T Gr = gr * (T(1) + car * (c2 / e.RT - T(D + 2)));
+    const T a = T(1) - e.iz;
+    out[0] = a * Gt + e.iz * Gr;
+    if (D == 2) {
+        const T Ht = e.RTt * gt * (T(1) + cat * (c2 / e.RTt - T(D)));
+        const T Hr = e.RT * gr * (T(1) + car * (c2 / e.RT - T(D)));
+        out[1] = a * Ht + e.iz * Hr;
+    }
+    const T Rt = e.RTr * (Gt + cbt * gt);
+    const T Rr = e.RT * (Gr + cbr * gr);
+    out[RkNA<D>::v - 1] = a * Rt + e.iz * Rr;
+}
+
+// Moments of one cell's f (all threads of the block): W = (rho, rho U, rho E,
+// rho E_rot) and, when qt is given, q_t = int c (c^2 G + H)/2 and q_r = int c R
+// about the cell's mean velocity (Eqs. updat_W, 8).  FP64 sums.
+template <int D, typename T>
+__device__ void rk_cell_mom(const T* fi, int Nv, int Nvp, const double* __restrict__ xi,
+                            const double* __restrict__ w, double* W, double* qt, double* qr, double* sred,
+                            double* sout)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3;
+    double acc[NW];
+#pragma unroll
+    for (int m = 0; m < NW; ++m) acc[m] = 0.0;
+    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+        const double wk = w[k];
+        double x[D], x2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            x[d] = xi[(size_t)k * D + d];
+            x2 += x[d] * x[d];
+        }
+        const double G = (double)fi[k], H = D == 2 ? (double)fi[Nvp + k] : 0.0;
+        const double Rr = (double)fi[(size_t)(NA - 1) * Nvp + k];
+        acc[0] += wk * G;
+#pragma unroll
+        for (int d = 0; d < D; ++d) acc[1 + d] += wk * x[d] * G;
+        acc[D + 1] += wk * (0.5 * (x2 * G + H) + Rr);
+        acc[D + 2] += wk * Rr;
+    }
+    block_sum<NW, RK_NT>(acc, sred, sout);
+#pragma unroll
+    for (int m = 0; m < NW; ++m) W[m] = sout[m];
+    if (!qt) return;
+    double U[D], a[2 * D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        U[d] = W[1 + d] / W[0];
+        a[d] = a[D + d] = 0.0;
+    }
+    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+        const double wk = w[k];
+        double c[D], c2 = 0.0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            c[d] = xi[(size_t)k * D + d] - U[d];
+            c2 += c[d] * c[d];
+        }
+        const double G = (double)fi[k], H = D == 2 ? (double)fi[Nvp + k] : 0.0;
+        const double Rr = (double)fi[(size_t)(NA - 1) * Nvp + k];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            a[d] += 0.5 * wk * c[d] * (c2 * G + H);
+            a[D + d] += wk * c[d] * Rr;
+        }
+    }
+    block_sum<2 * D, RK_NT>(a, sred, sout);
+    for (int d = 0; d < D; ++d) {
+        qt[d] = sout[d];
+        qr[d] = sout[D + d];
+    }
+}
+
+template <typename T>
+struct RkP {
+    int Nv, Nvp, Nc, limiter;
+    double dt, h;
+    RkGas g;
+    const int* faceL;
+    const int* faceR;
+    const double* An;
+    const double* rL;
+    const double* rR;
+    const double* bc;
+    const double* xi;
+    const double* w;
+    const double* vol;
+    const int* slot;
+    const unsigned char* nslot;
+    const T* f;               // f^n [cell][NA][Nvp]
+    const T* G;               // limited gradients [cell][NA][D][Nvp], or null (first order)
+    T* FX;                    // [face][NA][Nvp]: foot values, then the face flux (xi . A n) phi
+    double* AF;               // [face][D + 3] area-weighted flux of W
+    const double* Win;
+    double* Wout;
+    T* fout;
+    int* err;
+};
+
+// Limited least-squares gradient of every cell, array and node (Sec. 2.3.3,
+// reading R6), one thread per node.
+template <int D, typename T>
+__global__ void __launch_bounds__(256) rk_grad(int Nv, int Nvp, int limiter, const T* __restrict__ f, T* G,
+                                               const unsigned char* __restrict__ nslot, const int* __restrict__ nbr,
+                                               const T* __restrict__ cg, const T* __restrict__ r,
+                                               const T* __restrict__ eps2)
+{
+    constexpr int NA = RkNA<D>::v;
+    const int i = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= Nv) return;
+    const int ns = nslot[i];
+    const size_t cs = (size_t)NA * Nvp;
+    const T e2 = eps2[i];
+    for (int a = 0; a < NA; ++a) {
+        const T phi = f[(size_t)i * cs + (size_t)a * Nvp + k];
+        T g[D], dmax = T(0), dmin = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) g[d] = T(0);
+        for (int s = 0; s < ns; ++s) {
+            const int nb = nbr[i * AVS_MAXS + s];
+            if (nb < 0) continue;
+            const T dd = f[(size_t)nb * cs + (size_t)a * Nvp + k] - phi;
+#pragma unroll
+            for (int d = 0; d < D; ++d) g[d] += cg[(size_t)(i * AVS_MAXS + s) * D + d] * dd;
+            dmax = dd > dmax ? dd : dmax;
+            dmin = dd < dmin ? dd : dmin;
+        }
+        T L = T(1);
+        if (limiter == 1) {
+            T p = T(0), n = T(0);
+            for (int s = 0; s < ns; ++s) {
+                T d2 = T(0);
+#pragma unroll
+                for (int d = 0; d < D; ++d) d2 += g[d] * r[(size_t)(i * AVS_MAXS + s) * D + d];
+                p = d2 > p ? d2 : p;
+                n = d2 < n ? d2 : n;
+            }
+            if (p > T(0)) { const T t = venkat(dmax, p, e2); L = t < L ? t : L; }
+            if (n < T(0)) { const T t = venkat(dmin, n, e2); L = t < L ? t : L; }
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) G[(((size_t)i * NA + a) * D + d) * Nvp + k] = L * g[d];
+    }
+}
+
+// One face: foot values from the upwind cell, the Rykov interface state
+// (reading R27) and phi_ij = tau/(tau+h) phi_bar + h/(tau+h) g (Eq. equ28);
+// boundary faces as in R8/R29.  Writes the per-node face flux and A F.
+template <int D, typename T>
+__global__ void __launch_bounds__(RK_NT) rk_face(RkP<T> P)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3;
+    __shared__ double sred[(RK_NT / 32) * 6], sout[6];
+    __shared__ RkEq<T> eq;
+    __shared__ double blend[2];
+    const int f = blockIdx.x;
+    const int L = P.faceL[f], R = P.faceR[f];
+    const int Nv = P.Nv, Nvp = P.Nvp;
+    double An[3] = {0, 0, 0}, rl[3] = {0, 0, 0}, rr[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) {
+        An[d] = P.An[(size_t)f * D + d];
+        rl[d] = P.rL[(size_t)f * D + d];
+        if (R >= 0) rr[d] = P.rR[(size_t)f * D + d];
+    }
+    T* fx = P.FX + (size_t)f * NA * Nvp;
+    const size_t cs = (size_t)NA * Nvp;
+    int btype = 0;
+    double rb = 0.0, Ub[3] = {0, 0, 0}, RTb = 0.0;
+    if (R < 0) {
+        const double* B = P.bc + (size_t)(-1 - R) * 6;
+        btype = (int)B[0];
+        rb = B[1];
+        for (int d = 0; d < 3; ++d) Ub[d] = B[2 + d];
+        RTb = P.g.R * B[5];
+    }
+    // pass A: foot values phi_C + (L grad phi)_C . (r_C - xi h), C upwind by xi . n
+    double acc[NW];
+#pragma unroll
+    for (int m = 0; m < NW; ++m) acc[m] = 0.0;
+    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+        double x[3] = {0, 0, 0}, sn = 0.0, x2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            x[d] = P.xi[(size_t)k * D + d];
+            sn += x[d] * An[d];
+            x2 += x[d] * x[d];
+        }
+        const int C = sn >= 0.0 ? L : R;
+        const double* r = sn >= 0.0 ? rl : rr;
+        T ph[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) ph[a] = T(0);
+        if (C >= 0) {
+            T off[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) off[d] = (T)(r[d] - x[d] * P.h);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                T v = P.f[(size_t)C * cs + (size_t)a * Nvp + k];
+                if (P.G)
+#pragma unroll
+                    for (int d = 0; d < D; ++d) v += P.G[(((size_t)C * NA + a) * D + d) * Nvp + k] * off[d];
+                ph[a] = v;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) fx[(size_t)a * Nvp + k] = ph[a];
+        const double wk = P.w[k];
+        if (R >= 0) {
+            const double G = (double)ph[0], H = D == 2 ? (double)ph[1] : 0.0, Rr = (double)ph[NA - 1];
+            acc[0] += wk * G;
+            for (int d = 0; d < D; ++d) acc[1 + d] += wk * x[d] * G;
+            acc[D + 1] += wk * (0.5 * (x2 * G + H) + Rr);
+            acc[D + 2] += wk * Rr;
+        } else if (btype == AVS_BC_WALL) {
+            if (sn >= 0.0) {
+                acc[0] += wk * sn * (double)ph[0];
+            } else {
+                double c2 = 0.0;
+                for (int d = 0; d < D; ++d) c2 += (x[d] - Ub[d]) * (x[d] - Ub[d]);
+                acc[1] += wk * (-sn) * (1.0 / pow(2.0 * AVS_PI * RTb, 0.5 * D) * exp(-c2 / (2.0 * RTb)));
+            }
+        }
+    }
+    block_sum<NW, RK_NT>(acc, sred, sout);
+    if (R >= 0) {
+        double W[NW];
+#pragma unroll
+        for (int m = 0; m < NW; ++m) W[m] = sout[m];
+        double U[D], a2[2 * D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            U[d] = W[1 + d] / W[0];
+            a2[d] = a2[D + d] = 0.0;
+        }
+        for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+            const double wk = P.w[k];
+            double c[D], c2 = 0.0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                c[d] = P.xi[(size_t)k * D + d] - U[d];
+                c2 += c[d] * c[d];
+            }
+            const double G = (double)fx[k], H = D == 2 ? (double)fx[Nvp + k] : 0.0;
+            const double Rr = (double)fx[(size_t)(NA - 1) * Nvp + k];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                a2[d] += 0.5 * wk * c[d] * (c2 * G + H);
+                a2[D + d] += wk * c[d] * Rr;
+            }
+        }
+        block_sum<2 * D, RK_NT>(a2, sred, sout);
+        if (threadIdx.x == 0) {
+            double rho, Uu[3], RTt, RTr, RT;
+            rk_prim<D>(W, rho, Uu, RTt, RTr, RT);
+            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+            const double tau = rk_tau(P.g, rho, RTt);
+            // rotational energy relaxed over h toward rho R T, T fixed by the total energy
+            const double az = P.h / (P.g.Z * tau);
+            RTr = (W[D + 2] + az * rho * RT) / (1.0 + az) / rho;
+            RTt = (5.0 * RT - 2.0 * RTr) / 3.0;
+            const double lt = 2.0 / 3.0 + (1.0 - P.g.om0) / (3.0 * P.g.Z);
+            const double lr = 1.0 - (1.0 - P.g.dl) * ((1.0 - 1.0 / P.g.Z) * RTr / RTt + P.g.om1 / P.g.Z);
+            double qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) {
+                qt[d] = tau * sout[d] / (tau + P.h * lt);
+                qr[d] = tau * sout[D + d] / (tau + P.h * lr);
+            }
+            eq = rk_make<D, T>(P.g, rho, Uu, RTt, RTr, qt, qr);
+            blend[0] = tau / (tau + P.h);
+            blend[1] = P.h / (tau + P.h);
+        }
+    } else if (threadIdx.x == 0) {
+        // incoming half: rho_b g^eq(U_b, T_b) with H = (3 - D) R T_b G, R = R T_b G
+        const double rho_b = btype == AVS_BC_WALL ? (sout[1] > 0.0 ? sout[0] / sout[1] : 0.0) : rb;
+        const double z[3] = {0, 0, 0};
+        RkGas g0 = P.g;
+        g0.iz = 0.0;
+        eq = rk_make<D, T>(g0, rho_b, Ub, RTb, RTb, z, z);
+        blend[0] = 1.0;
+        blend[1] = 0.0;
+    }
+    __syncthreads();
+    // pass B: phi_ij, per-node flux (xi . A n) phi and its moments
+    const T wa = (T)blend[0], wb = (T)blend[1];
+    double af[NW];
+#pragma unroll
+    for (int m = 0; m < NW; ++m) af[m] = 0.0;
+    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+        double x[3] = {0, 0, 0}, sn = 0.0, x2 = 0.0;
+        T xt[D];
+        for (int d = 0; d < D; ++d) {
+            x[d] = P.xi[(size_t)k * D + d];
+            sn += x[d] * An[d];
+            x2 += x[d] * x[d];
+            xt[d] = (T)x[d];
+        }
+        T ph[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) ph[a] = fx[(size_t)a * Nvp + k];
+        if (R >= 0 || sn < 0.0) {
+            T gv[NA];
+            rk_eval<D, T>(eq, xt, gv);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) ph[a] = R >= 0 ? wa * ph[a] + wb * gv[a] : gv[a];
+        }
+        const T st = (T)sn;
+        double Fd[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const T F = st * ph[a];
+            fx[(size_t)a * Nvp + k] = F;
+            Fd[a] = (double)F;
+        }
+        const double wk = P.w[k];
+        af[0] += wk * Fd[0];
+        for (int d = 0; d < D; ++d) af[1 + d] += wk * x[d] * Fd[0];
+        af[D + 1] += wk * (0.5 * (x2 * Fd[0] + (D == 2 ? Fd[1] : 0.0)) + Fd[NA - 1]);
+        af[D + 2] += wk * Fd[NA - 1];
+    }
+    block_sum<NW, RK_NT>(af, sred, sout);
+    if (threadIdx.x < NW) P.AF[(size_t)f * NW + threadIdx.x] = sout[threadIdx.x];
+}
+
+// One cell: W~ = W - dt/|V| sum A F with the rotational source of Eq. (S_rot)
+// taken implicitly, tau from T_t of the flux-updated state (reading R28);
+// lagged heat fluxes of f^n (R3); the collision update of every array.
+template <int D, typename T>
+__global__ void __launch_bounds__(RK_NT) rk_cell(RkP<T> P)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3;
+    __shared__ double sred[(RK_NT / 32) * 6], sout[6];
+    __shared__ RkEq<T> eq;
+    __shared__ double tau_s;
+    __shared__ int fs[AVS_MAXS];
+    __shared__ T sg[AVS_MAXS];
+    const int i = blockIdx.x;
+    const int ns = P.nslot[i];
+    const int Nv = P.Nv, Nvp = P.Nvp;
+    if (threadIdx.x < ns) {
+        const int sl = P.slot[i * AVS_MAXS + threadIdx.x];
+        fs[threadIdx.x] = sl >> 1;
+        sg[threadIdx.x] = (sl & 1) ? T(-1) : T(1);
+    }
+    const size_t cs = (size_t)NA * Nvp;
+    const T* fi = P.f + (size_t)i * cs;
+    double Wn[NW], qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+    rk_cell_mom<D, T>(fi, Nv, Nvp, P.xi, P.w, Wn, qt, qr, sred, sout);
+    if (threadIdx.x == 0) {
+        const double V = P.vol[i];
+        double Wt[NW];
+        for (int c = 0; c < NW; ++c) {
+            double s = 0.0;
+            for (int q = 0; q < ns; ++q) {
+                const double a = P.AF[(size_t)fs[q] * NW + c];
+                s += sg[q] > T(0) ? a : -a;
+            }
+            Wt[c] = P.Win[(size_t)i * NW + c] - P.dt / V * s;
+        }
+        double rho, U[3], RTt, RTr, RT;
+        rk_prim<D>(Wt, rho, U, RTt, RTr, RT);
+        if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+        const double tau = rk_tau(P.g, rho, RTt);
+        const double az = P.dt / (P.g.Z * tau);
+        Wt[D + 2] = (Wt[D + 2] + az * rho * RT) / (1.0 + az);
+        rk_prim<D>(Wt, rho, U, RTt, RTr, RT);
+        eq = rk_make<D, T>(P.g, rho, U, RTt, RTr, qt, qr);
+        tau_s = tau;
+        for (int c = 0; c < NW; ++c) P.Wout[(size_t)i * NW + c] = Wt[c];
+    }
+    __syncthreads();
+    const T dt = (T)P.dt, tau = (T)tau_s, V = (T)P.vol[i];
+    const T den = T(1) / dt + T(1) / tau;
+    T* fo = P.fout + (size_t)i * cs;
+    for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
+        if (k >= Nv) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) fo[(size_t)a * Nvp + k] = T(0);
+            continue;
+        }
+        T xt[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) xt[d] = (T)P.xi[(size_t)k * D + d];
+        T gv[NA];
+        rk_eval<D, T>(eq, xt, gv);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            T N = T(0);
+            for (int q = 0; q < ns; ++q) N += sg[q] * P.FX[((size_t)fs[q] * NA + a) * Nvp + k];
+            fo[(size_t)a * Nvp + k] = (fi[(size_t)a * Nvp + k] / dt + gv[a] / tau - N / V) / den;
+        }
+    }
+}
+
+// W (and the total heat flux q_t + q_r) of every cell.
+template <int D, typename T>
+__global__ void __launch_bounds__(RK_NT) rk_moments(int Nv, int Nvp, const T* __restrict__ f,
+                                                    const double* __restrict__ xi, const double* __restrict__ w,
+                                                    double* Wout, double* qout)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3;
+    __shared__ double sred[(RK_NT / 32) * 6], sout[6];
+    const int i = blockIdx.x;
+    double W[NW], qt[3], qr[3];
+    rk_cell_mom<D, T>(f + (size_t)i * NA * Nvp, Nv, Nvp, xi, w, W, qout ? qt : nullptr, qr, sred, sout);
+    if (threadIdx.x == 0) {
+        if (Wout)
+            for (int m = 0; m < NW; ++m) Wout[(size_t)i * NW + m] = W[m];
+        if (qout)
+            for (int d = 0; d < D; ++d) qout[(size_t)i * D + d] = qt[d] + qr[d];
+    }
+}
+
+// Conservation correction (Sec. 3.3, reading R30): f <- f + g^M(W) - g^M(W')
+// with g^M = (g^eq(T_t), (3 - D) R T_t g^eq(T_t), R T_r g^eq(T_t)), `iters`
+// times; the largest remaining relative gap into *gap_key.
+template <int D, typename T>
+__global__ void __launch_bounds__(RK_NT) rk_correct(int Nv, int Nvp, T* f, const double* __restrict__ xi,
+                                                    const double* __restrict__ w, const double* __restrict__ Wt,
+                                                    RkGas g, int iters, unsigned long long* gap_key)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3;
+    __shared__ double sred[(RK_NT / 32) * 6], sout[6];
+    __shared__ RkEq<T> ea, eb;
+    const int i = blockIdx.x;
+    T* fi = f + (size_t)i * NA * Nvp;
+    const double* Wi = Wt + (size_t)i * NW;
+    g.iz = 0.0;
+    const double z[3] = {0, 0, 0};
+    double rho, U[3], RTt, RTr, RT;
+    rk_prim<D>(Wi, rho, U, RTt, RTr, RT);
+    if (threadIdx.x == 0) ea = rk_make<D, T>(g, rho, U, RTt, RTr, z, z);
+    for (int it = 0; it <= iters; ++it) {
+        double Wp[NW];
+        rk_cell_mom<D, T>(fi, Nv, Nvp, xi, w, Wp, nullptr, nullptr, sred, sout);
+        if (it == iters) {
+            if (threadIdx.x == 0) {
+                double mref = 0.0;
+                for (int d = 0; d < D; ++d) mref += Wi[1 + d] * Wi[1 + d];
+                mref = sqrt(mref) + rho * sqrt(2.0 * RT);
+                double e = fabs(Wp[0] - Wi[0]) / fabs(Wi[0]);
+                for (int d = 0; d < D; ++d) e = fmax(e, fabs(Wp[1 + d] - Wi[1 + d]) / mref);
+                for (int c = D + 1; c < NW; ++c) e = fmax(e, fabs(Wp[c] - Wi[c]) / fabs(Wi[D + 1]));
+                if (e != e) e = INFINITY;
+                atomicMax(gap_key, dkey(e));
+            }
+            break;
+        }
+        if (threadIdx.x == 0) {
+            double rp, Up[3], RTtp, RTrp, RTp;
+            rk_prim<D>(Wp, rp, Up, RTtp, RTrp, RTp);
+            eb = rk_make<D, T>(g, rp, Up, RTtp, RTrp, z, z);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+            T xt[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) xt[d] = (T)xi[(size_t)k * D + d];
+            T va[NA], vb[NA];
+            rk_eval<D, T>(ea, xt, va);
+            rk_eval<D, T>(eb, xt, vb);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) fi[(size_t)a * Nvp + k] += va[a] - vb[a];
+        }
+        __syncthreads();
+    }
+}
+
+// conserved -> primitive rho, U, T_t, T_r (the initial-field layout)
+template <int D>
+__global__ void rk_cons_to_prim(int Nc, const double* __restrict__ Wc, double R, double* Wp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Nc) return;
+    constexpr int NW = D + 3;
+    double rho, U[3], RTt, RTr, RT;
+    rk_prim<D>(Wc + (size_t)i * NW, rho, U, RTt, RTr, RT);
+    double* P = Wp + (size_t)i * NW;
+    P[0] = rho;
+    for (int d = 0; d < D; ++d) P[1 + d] = U[d];
+    P[D + 1] = RTt / R;
+    P[D + 2] = RTr / R;
+}
+
+RkGas rk_gas(const avs_ctx* c)
+{
+    RkGas g;
+    g.R = c->cfg.R;
+    g.mu_ref = c->mu_ref;
+    g.T_ref = c->cfg.T_ref;
+    g.omega = c->cfg.omega;
+    g.Z = c->cfg.Zrot;
+    g.iz = 1.0 / c->cfg.Zrot;
+    g.om0 = AVS_RYKOV_OMEGA0;
+    g.om1 = AVS_RYKOV_OMEGA1;
+    g.dl = AVS_RYKOV_DELTA;
+    return g;
+}
+
+cudaError_t ensure_bytes(void** p, size_t* have, size_t need)
+{
+    if (*have >= need) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, need);
+    if (e == cudaSuccess) *have = need;
+    return e;
+}
+
+template <int D, typename T>
+cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt)
+{
+    constexpr int NA = RkNA<D>::v;
+    const bool f32 = sizeof(T) == 4;
+    const size_t rows = (size_t)std::max(c->fcap, c->Nvp);
+    const bool grad = c->cfg.limiter != 0;
+    cudaError_t e;
+    if (grad) {
+        e = ensure_bytes(&c->grad, &c->grad_bytes, (size_t)c->Nc * NA * D * rows * sizeof(T));
+        if (e != cudaSuccess) return e;
+    }
+    e = ensure_bytes(&c->flux, &c->flux_bytes, (size_t)c->Nf * NA * rows * sizeof(T));
+    if (e != cudaSuccess) return e;
+    RkP<T> P;
+    P.Nv = c->Nv;
+    P.Nvp = c->Nvp;
+    P.Nc = c->Nc;
+    P.limiter = c->cfg.limiter;
+    P.dt = dt;
+    P.h = 0.5 * dt;
+    P.g = rk_gas(c);
+    P.faceL = c->faceL;
+    P.faceR = c->faceR;
+    P.An = c->An_d;
+    P.rL = c->rL_d;
+    P.rR = c->rR_d;
+    P.bc = c->bc;
+    P.xi = c->xi_d;
+    P.w = c->w_d;
+    P.vol = c->vol;
+    P.slot = c->slot;
+    P.nslot = c->nslot;
+    P.f = (const T*)fin;
+    P.G = grad ? (const T*)c->grad : nullptr;
+    P.FX = (T*)c->flux;
+    P.AF = c->AFf;
+    P.Win = Win;
+    P.Wout = Wout;
+    P.fout = (T*)fout;
+    P.err = c->dev_err;
+    if (grad) {
+        dim3 g(c->Nc, (c->Nv + 255) / 256);
+        rk_grad<D, T><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin, (T*)c->grad, c->nslot,
+                                                c->nbr, f32 ? (const T*)c->cg_f : (const T*)c->cg_d,
+                                                f32 ? (const T*)c->r_f : (const T*)c->r_d,
+                                                f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d);
+        c->launches += 1;
+    }
+    rk_face<D, T><<<c->Nf, RK_NT, 0, c->stream>>>(P);
+    rk_cell<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t rk_launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt)
+{
+    if (c->D == 2)
+        return c->mixed ? rk_step_t<2, float>(c, fin, fout, Win, Wout, dt)
+                        : rk_step_t<2, double>(c, fin, fout, Win, Wout, dt);
+    return c->mixed ? rk_step_t<3, float>(c, fin, fout, Win, Wout, dt)
+                    : rk_step_t<3, double>(c, fin, fout, Win, Wout, dt);
+}
+
+cudaError_t rk_launch_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wout,
+                              double* qout)
+{
+    const bool dbl = f_is_double || !c->mixed;
+    if (c->D == 2) {
+        if (dbl) rk_moments<2, double><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const double*)f, c->xi_d,
+                                                                        c->w_d, Wout, qout);
+        else rk_moments<2, float><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const float*)f, c->xi_d, c->w_d,
+                                                                   Wout, qout);
+    } else {
+        if (dbl) rk_moments<3, double><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const double*)f, c->xi_d,
+                                                                        c->w_d, Wout, qout);
+        else rk_moments<3, float><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const float*)f, c->xi_d, c->w_d,
+                                                                   Wout, qout);
+    }
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t rk_launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters)
+{
+    const unsigned long long zero = dkey(0.0);
+    cudaError_t e = cudaMemcpyAsync(c->gap_d, &zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    unsigned long long* gk = (unsigned long long*)c->gap_d;
+    const RkGas g = rk_gas(c);
+    if (c->D == 2) {
+        if (c->mixed) rk_correct<2, float><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_d, c->w_d,
+                                                                           Wtarget, g, iters, gk);
+        else rk_correct<2, double><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d, c->w_d,
+                                                                   Wtarget, g, iters, gk);
+    } else {
+        if (c->mixed) rk_correct<3, float><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_d, c->w_d,
+                                                                           Wtarget, g, iters, gk);
+        else rk_correct<3, double><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d, c->w_d,
+                                                                   Wtarget, g, iters, gk);
+    }
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t rk_launch_cons_to_prim(avs_ctx* c, const double* Wc, double* Wp)
+{
+    if (c->D == 2) rk_cons_to_prim<2><<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->Nc, Wc, c->cfg.R, Wp);
+    else rk_cons_to_prim<3><<<(c->Nc + 255) / 256, 256, 0, c->stream>>>(c->Nc, Wc, c->cfg.R, Wp);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace avs
