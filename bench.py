@@ -73,14 +73,27 @@ WORKLOADS = {
     "sphere": ("sphere", dict()),
     # the cylinder with the velocity space of the adaptive-parameter rules (zones, C1(Ma))
     "cylinder-zones": ("cylinder_zones", dict()),
+    # the cylinder with a diatomic gas (Rykov model: G, H, R; no learned proposer)
+    "cylinder-rykov": ("cylinder", dict(model="rykov")),
 }
 _WL = "cylinder"
 
 
-def _workload(precision="mixed"):
+def _build(fn, kw, precision):
+    """A workload by builder name; the key `model` selects the gas model."""
     from paper_2212_05645_gb300 import workloads as wl
+    kw = dict(kw)
+    model = kw.pop("model", "shakhov")
+    w = getattr(wl, fn)(precision=precision, **kw)
+    w.model = model
+    if model != "shakhov":
+        w.learned = False
+    return w
+
+
+def _workload(precision="mixed"):
     fn, kw = WORKLOADS[_WL]
-    return getattr(wl, fn)(precision=precision, **kw)
+    return _build(fn, kw, precision)
 
 
 def _dist():
@@ -199,6 +212,7 @@ ORACLE_SAMPLES = {
     "wedge": ("blunt_wedge", dict(n_r=8, learned=False), "the first 8 wall-normal rows (1920 cells)"),
     "sphere": ("sphere", dict(n_r=2, learned=False), "the first 2 radial shells (4608 cells)"),
     "cylinder-zones": ("cylinder_zones", dict(), "the whole 128 x 96 O-mesh (12288 cells)"),
+    "cylinder-rykov": ("cylinder", dict(n_r=12, model="rykov"), "the first 12 radial rows (1152 cells)"),
 }
 
 
@@ -210,7 +224,7 @@ def cpu_baseline(seconds=12.0, nu=NU):
     import oracle as O
     from paper_2212_05645_gb300 import workloads as wl
     fn, kw, what = ORACLE_SAMPLES[_WL]
-    w = getattr(wl, fn)(precision="fp64", **kw)
+    w = _build(fn, kw, "fp64")
     r = O.Run(w)
     r.init_field()
     dt = r.dt()
@@ -266,7 +280,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     w = _workload("mixed")
     # headline form: mixed precision with the learned proposer (full criterion every 4th adaptation)
-    g = A.AVS(w, precision="mixed", stream=stream.cuda_stream, learned=True, full_every=4)
+    learned = w.model == "shakhov"           # the proposer is built for the monatomic gas
+    g = A.AVS(w, precision="mixed", stream=stream.cuda_stream, learned=learned, full_every=4)
     Nc = g.Nc
     nu = args.nu
     # every bench step is one batch: a flow started from the resident initial
@@ -340,12 +355,13 @@ def run_gpu(args):
     achieved = bytes_per_cn * cn_per_launch / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     # ncu traffic of the step, measured on the cylinder family (2D, mixed)
-    traffic = (_traffic("mixed", Nc, cn_per_launch / Nc) if _WL.startswith("cylinder") and args.implicit <= 0
-               else None)
+    traffic = (_traffic("mixed", Nc, cn_per_launch / Nc)
+               if _WL in ("cylinder", "cylinder-r64") and args.implicit <= 0 else None)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
             "kernel": (f"implicit UGKS step: k_grad + k_face + k_imp_setup + k_imp_macro + k_imp_state + k_imp_res"
                        f" + k_imp_micro + k_imp_finish <{w.D},float>" if args.implicit > 0 else
+                       f"Rykov UGKS step: rk_grad + rk_face + rk_cell <{w.D},float>" if w.model == "rykov" else
                        f"UGKS step: k_grad + k_face + k_cell_state + k_cell <{w.D},float>"),
             "peak_source": peak_kind,
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
@@ -407,7 +423,9 @@ def run_gpu(args):
                            "ugks_steps_per_step": nu, "precision": "mixed (f FP32, sums FP64)",
                            "time_step": (f"implicit IUGKS, CFL {args.implicit}, 60 macro + 2 micro SGS iterations"
                                          if args.implicit > 0 else "explicit, CFL 0.8"),
-                           "adaptation": "learned proposer, full criterion every 4th adaptation",
+                           "adaptation": ("learned proposer, full criterion every 4th adaptation" if learned
+                                          else "plain criterion every adaptation"),
+                           "gas": ("Rykov (diatomic: G, H, R)" if w.model == "rykov" else "Shakhov (monatomic: G, H)"),
                            "l2": (f"L2 flushed before each timed step (f = {f_mb:.0f} MB per buffer)"
                                   if flush is not None else f"inputs larger than L2 (f = {f_mb:.0f} MB per buffer)"),
                            "parallelism": f"replicas x{ws}"},

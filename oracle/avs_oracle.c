@@ -6,7 +6,7 @@
  * Every routine follows the paper's definitions in the paper's order, with
  * plain loops (cells, then arrays, then nodes; faces in list order) and no
  * blocking or fusion.  Where the paper is silent the reading used is named
- * in the comment (R1..R14 are the readings listed in the design notes).
+ * in the comment (R1..R30 are the readings listed in the design notes).
  * Build with -ffp-contract=off so that no multiply-add is fused.
  */
 #include "avs_oracle.h"

@@ -287,12 +287,13 @@ __global__ void __launch_bounds__(RK_NT) rk_face(RkP<T> P)
 #pragma unroll
     for (int m = 0; m < NW; ++m) acc[m] = 0.0;
     for (int k = threadIdx.x; k < Nv; k += RK_NT) {
-        double x[3] = {0, 0, 0}, sn = 0.0, x2 = 0.0;
+        double x[3] = {0, 0, 0}, x2 = 0.0;
         for (int d = 0; d < D; ++d) {
             x[d] = P.xi[(size_t)k * D + d];
-            sn += x[d] * An[d];
             x2 += x[d] * x[d];
         }
+        // xi . A n without contraction: the upwind decision is taken exactly as in a plain FP64 code
+        const double sn = dot_rn<D>(x, An);
         const int C = sn >= 0.0 ? L : R;
         const double* r = sn >= 0.0 ? rl : rr;
         T ph[NA];
@@ -395,14 +396,14 @@ __global__ void __launch_bounds__(RK_NT) rk_face(RkP<T> P)
 #pragma unroll
     for (int m = 0; m < NW; ++m) af[m] = 0.0;
     for (int k = threadIdx.x; k < Nv; k += RK_NT) {
-        double x[3] = {0, 0, 0}, sn = 0.0, x2 = 0.0;
+        double x[3] = {0, 0, 0}, x2 = 0.0;
         T xt[D];
         for (int d = 0; d < D; ++d) {
             x[d] = P.xi[(size_t)k * D + d];
-            sn += x[d] * An[d];
             x2 += x[d] * x[d];
             xt[d] = (T)x[d];
         }
+        const double sn = dot_rn<D>(x, An);
         T ph[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a) ph[a] = fx[(size_t)a * Nvp + k];
