@@ -7,8 +7,10 @@
 // rho E_rot = int R = rho R T_r, (3/2) rho R T_t = rho E - rho U^2/2 - rho E_rot,
 // and the equilibrium temperature T = (3 T_t + 2 T_r) / 5.
 //
-// The kernels take one block per face or cell and sum over the nodes in FP64;
-// the equilibrium is evaluated in the element type (FP32 in the mixed form).
+// The kernels take one block per face or cell.  The FP64 form sums over the
+// nodes in FP64 directly; the FP32 (mixed) form sums raw moments in FP32 per
+// thread and in FP64 across warps.  The equilibrium is evaluated in the
+// element type.
 #include <algorithm>
 
 #include "avs_dev.cuh"
@@ -501,6 +503,367 @@ __global__ void __launch_bounds__(RK_NT) rk_cell(RkP<T> P)
     }
 }
 
+// ---------------------------------------------------------------- mixed form
+// The FP32 form sums over the nodes in FP32 per thread (FP64 across warps),
+// as raw moments about a reference velocity V near the local mean velocity
+// (the upwind-side cell's carried U), so that no per-node FP64 arithmetic is
+// left: on GB300 an FP64 operation costs about as much as 70 FP32 ones.
+
+template <int D>
+struct RkNR {
+    static constexpr int v = D == 2 ? 14 : 17;
+};
+
+// Raw moments of one node about V (c = xi - V): w G; w c_d G; w c_d c_e G
+// (d <= e); w c_d c^2 G; in 2D w H and w c_d H; w R and w c_d R.
+template <int D>
+__device__ __forceinline__ void rk_raw_acc(float* m, const float* c, float wG, float wH, float wR)
+{
+    int o = 0;
+    float c2 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) c2 += c[d] * c[d];
+    m[o++] += wG;
+#pragma unroll
+    for (int d = 0; d < D; ++d) m[o++] += c[d] * wG;
+#pragma unroll
+    for (int d = 0; d < D; ++d)
+#pragma unroll
+        for (int e = d; e < D; ++e) m[o++] += c[d] * c[e] * wG;
+#pragma unroll
+    for (int d = 0; d < D; ++d) m[o++] += c[d] * c2 * wG;
+    if (D == 2) {
+        m[o++] += wH;
+#pragma unroll
+        for (int d = 0; d < D; ++d) m[o++] += c[d] * wH;
+    }
+    m[o++] += wR;
+#pragma unroll
+    for (int d = 0; d < D; ++d) m[o++] += c[d] * wR;
+}
+
+// W = (rho, rho U, rho E, rho E_rot) and, when qt is given, the heat fluxes
+// about U (Eq. 8) from the raw moments about V: with delta = U - V,
+// c' = c - delta, sum w c'_i c'^2 G = m3_i - 2 delta_j m2_ij + delta^2 m1_i
+// - delta_i tr m2 + 2 delta_i (delta . m1) - delta_i delta^2 m0.
+template <int D>
+__device__ void rk_from_raw(const double* m, const double* V, double* W, double* qt, double* qr)
+{
+    int o = 0;
+    const double m0 = m[o++];
+    double m1[3] = {0, 0, 0}, m2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, m3[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) m1[d] = m[o++];
+    for (int d = 0; d < D; ++d)
+        for (int e = d; e < D; ++e) m2[d][e] = m2[e][d] = m[o++];
+    for (int d = 0; d < D; ++d) m3[d] = m[o++];
+    double h0 = 0.0, h1[3] = {0, 0, 0};
+    if (D == 2) {
+        h0 = m[o++];
+        for (int d = 0; d < D; ++d) h1[d] = m[o++];
+    }
+    const double r0 = m[o++];
+    double r1[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) r1[d] = m[o++];
+    const double rho = m0;
+    double dl[3] = {0, 0, 0}, d2 = 0.0, tr = 0.0, VV = 0.0, Vm = 0.0, dm = 0.0;
+    for (int d = 0; d < D; ++d) {
+        dl[d] = m1[d] / rho;
+        d2 += dl[d] * dl[d];
+        tr += m2[d][d];
+        VV += V[d] * V[d];
+        Vm += V[d] * m1[d];
+        dm += dl[d] * m1[d];
+    }
+    W[0] = rho;
+    for (int d = 0; d < D; ++d) W[1 + d] = rho * V[d] + m1[d];
+    W[D + 1] = 0.5 * (VV * m0 + 2.0 * Vm + tr + h0) + r0;
+    W[D + 2] = r0;
+    if (!qt) return;
+    for (int i = 0; i < D; ++i) {
+        double s = m3[i] + d2 * m1[i] - dl[i] * tr + 2.0 * dl[i] * dm - dl[i] * d2 * m0;
+        for (int j = 0; j < D; ++j) s -= 2.0 * dl[j] * m2[i][j];
+        qt[i] = 0.5 * (s + (h1[i] - dl[i] * h0));
+        qr[i] = r1[i] - dl[i] * r0;
+    }
+}
+
+// Upwind side of a node: xi . A n >= 0 decided in FP32 when the FP32 sum is
+// farther from zero than its rounding bound, else in FP64 without
+// contraction, so the decision always equals the FP64 one.
+template <int D>
+__device__ __forceinline__ bool rk_upwind_L(const float* x, const float* Af, const double* __restrict__ xi, int k,
+                                            const double* An, float& s)
+{
+    float a = 0.0f;
+    s = 0.0f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const float p = __fmul_rn(x[d], Af[d]);
+        s = __fadd_rn(s, p);
+        a += fabsf(p);
+    }
+    if (fabsf(s) > a * 0x1p-20f) return s >= 0.0f;
+    double xd[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) xd[d] = xi[(size_t)k * D + d];
+    return dot_rn<D>(xd, An) >= 0.0;
+}
+
+// rk_face for the FP32 form (same steps; sums as above).
+template <int D>
+__global__ void __launch_bounds__(RK_NT) rk_face32(RkP<float> P, const float* __restrict__ xif,
+                                                   const float* __restrict__ wf, const float* __restrict__ Anf,
+                                                   const float* __restrict__ rLf, const float* __restrict__ rRf)
+{
+    using T = float;
+    constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
+    __shared__ double sw[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
+    __shared__ RkEq<T> eq;
+    __shared__ double blend[2];
+    const int f = blockIdx.x;
+    const int L = P.faceL[f], R = P.faceR[f];
+    const int Nv = P.Nv, Nvp = P.Nvp;
+    double An[3] = {0, 0, 0};
+    T Af[D], rl[D], rr[D];
+    for (int d = 0; d < D; ++d) {
+        An[d] = P.An[(size_t)f * D + d];
+        Af[d] = Anf[(size_t)f * D + d];
+        rl[d] = rLf[(size_t)f * D + d];
+        rr[d] = R >= 0 ? rRf[(size_t)f * D + d] : T(0);
+    }
+    T* fx = P.FX + (size_t)f * NA * Nvp;
+    const size_t cs = (size_t)NA * Nvp;
+    int btype = 0;
+    double rb = 0.0, Ub[3] = {0, 0, 0}, RTb = 1.0;
+    if (R < 0) {
+        const double* B = P.bc + (size_t)(-1 - R) * 6;
+        btype = (int)B[0];
+        rb = B[1];
+        for (int d = 0; d < 3; ++d) Ub[d] = B[2 + d];
+        RTb = P.g.R * B[5];
+    }
+    const T h = (T)P.h;
+    T V[D], Ubf[D];
+    double Vd[3] = {0, 0, 0};
+    const double* WL = P.Win + (size_t)L * NW;
+    for (int d = 0; d < D; ++d) {
+        V[d] = (T)(WL[1 + d] / WL[0]);
+        Vd[d] = (double)V[d];
+        Ubf[d] = (T)Ub[d];
+    }
+    const T pw = (T)(1.0 / pow(2.0 * AVS_PI * RTb, 0.5 * D)), i2b = (T)(1.0 / (2.0 * RTb));
+    T racc[NR], wacc[2] = {T(0), T(0)};
+#pragma unroll
+    for (int m = 0; m < NR; ++m) racc[m] = T(0);
+    // pass A: foot values and their raw moments (or the wall balance)
+    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+        T x[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) x[d] = xif[(size_t)k * D + d];
+        T s;
+        const bool up = rk_upwind_L<D>(x, Af, P.xi, k, An, s);
+        const int C = up ? L : R;
+        T ph[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) ph[a] = T(0);
+        if (C >= 0) {
+            T off[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) off[d] = (up ? rl[d] : rr[d]) - x[d] * h;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                T v = P.f[(size_t)C * cs + (size_t)a * Nvp + k];
+                if (P.G)
+#pragma unroll
+                    for (int d = 0; d < D; ++d) v += P.G[(((size_t)C * NA + a) * D + d) * Nvp + k] * off[d];
+                ph[a] = v;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) fx[(size_t)a * Nvp + k] = ph[a];
+        const T wk = wf[k];
+        if (R >= 0) {
+            T c[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) c[d] = x[d] - V[d];
+            rk_raw_acc<D>(racc, c, wk * ph[0], D == 2 ? wk * ph[1] : T(0), wk * ph[NA - 1]);
+        } else if (btype == AVS_BC_WALL) {
+            if (up) {
+                wacc[0] += wk * s * ph[0];
+            } else {
+                T c2 = T(0);
+#pragma unroll
+                for (int d = 0; d < D; ++d) c2 += (x[d] - Ubf[d]) * (x[d] - Ubf[d]);
+                wacc[1] += wk * (-s) * (pw * ex(-c2 * i2b));
+            }
+        }
+    }
+    if (R >= 0) {
+        block_sum_t<NR, RK_NT>(racc, sw, sout);
+        if (threadIdx.x == 0) {
+            double m[NR], W[NW], qb[3] = {0, 0, 0}, qrb[3] = {0, 0, 0};
+            for (int q = 0; q < NR; ++q) m[q] = sout[q];
+            rk_from_raw<D>(m, Vd, W, qb, qrb);
+            double rho, Uu[3], RTt, RTr, RT;
+            rk_prim<D>(W, rho, Uu, RTt, RTr, RT);
+            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+            const double tau = rk_tau(P.g, rho, RTt);
+            const double az = P.h / (P.g.Z * tau);
+            RTr = (W[D + 2] + az * rho * RT) / (1.0 + az) / rho;
+            RTt = (5.0 * RT - 2.0 * RTr) / 3.0;
+            const double lt = 2.0 / 3.0 + (1.0 - P.g.om0) / (3.0 * P.g.Z);
+            const double lr = 1.0 - (1.0 - P.g.dl) * ((1.0 - 1.0 / P.g.Z) * RTr / RTt + P.g.om1 / P.g.Z);
+            double qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) {
+                qt[d] = tau * qb[d] / (tau + P.h * lt);
+                qr[d] = tau * qrb[d] / (tau + P.h * lr);
+            }
+            eq = rk_make<D, T>(P.g, rho, Uu, RTt, RTr, qt, qr);
+            blend[0] = tau / (tau + P.h);
+            blend[1] = P.h / (tau + P.h);
+        }
+    } else {
+        block_sum_t<2, RK_NT>(wacc, sw, sout);
+        if (threadIdx.x == 0) {
+            const double rho_b = btype == AVS_BC_WALL ? (sout[1] > 0.0 ? sout[0] / sout[1] : 0.0) : rb;
+            const double z[3] = {0, 0, 0};
+            RkGas g0 = P.g;
+            g0.iz = 0.0;
+            eq = rk_make<D, T>(g0, rho_b, Ub, RTb, RTb, z, z);
+            blend[0] = 1.0;
+            blend[1] = 0.0;
+        }
+    }
+    __syncthreads();
+    // pass B: phi_ij, per-node flux (xi . A n) phi and its moments
+    const T wa = (T)blend[0], wb = (T)blend[1];
+    T af[NW];
+#pragma unroll
+    for (int m = 0; m < NW; ++m) af[m] = T(0);
+    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+        T x[D], x2 = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            x[d] = xif[(size_t)k * D + d];
+            x2 += x[d] * x[d];
+        }
+        T s;
+        const bool up = rk_upwind_L<D>(x, Af, P.xi, k, An, s);
+        T ph[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) ph[a] = fx[(size_t)a * Nvp + k];
+        if (R >= 0 || !up) {
+            T gv[NA];
+            rk_eval<D, T>(eq, x, gv);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) ph[a] = R >= 0 ? wa * ph[a] + wb * gv[a] : gv[a];
+        }
+        T F[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            F[a] = s * ph[a];
+            fx[(size_t)a * Nvp + k] = F[a];
+        }
+        const T wk = wf[k];
+        af[0] += wk * F[0];
+#pragma unroll
+        for (int d = 0; d < D; ++d) af[1 + d] += wk * x[d] * F[0];
+        af[D + 1] += wk * (T(0.5) * (x2 * F[0] + (D == 2 ? F[1] : T(0))) + F[NA - 1]);
+        af[D + 2] += wk * F[NA - 1];
+    }
+    block_sum_t<NW, RK_NT>(af, sw, sout);
+    if (threadIdx.x < NW) P.AF[(size_t)f * NW + threadIdx.x] = sout[threadIdx.x];
+}
+
+// rk_cell for the FP32 form: the lagged heat fluxes from raw moments about
+// the cell's carried U.
+template <int D>
+__global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __restrict__ xif,
+                                                   const float* __restrict__ wf)
+{
+    using T = float;
+    constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
+    __shared__ double sw[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
+    __shared__ RkEq<T> eq;
+    __shared__ double tau_s;
+    __shared__ int fs[AVS_MAXS];
+    __shared__ T sg[AVS_MAXS];
+    const int i = blockIdx.x;
+    const int ns = P.nslot[i];
+    const int Nv = P.Nv, Nvp = P.Nvp;
+    if (threadIdx.x < ns) {
+        const int sl = P.slot[i * AVS_MAXS + threadIdx.x];
+        fs[threadIdx.x] = sl >> 1;
+        sg[threadIdx.x] = (sl & 1) ? T(-1) : T(1);
+    }
+    const size_t cs = (size_t)NA * Nvp;
+    const T* fi = P.f + (size_t)i * cs;
+    const double* Wi = P.Win + (size_t)i * NW;
+    T V[D];
+    double Vd[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) {
+        V[d] = (T)(Wi[1 + d] / Wi[0]);
+        Vd[d] = (double)V[d];
+    }
+    T racc[NR];
+#pragma unroll
+    for (int m = 0; m < NR; ++m) racc[m] = T(0);
+    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+        T c[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) c[d] = xif[(size_t)k * D + d] - V[d];
+        const T wk = wf[k];
+        rk_raw_acc<D>(racc, c, wk * fi[k], D == 2 ? wk * fi[Nvp + k] : T(0), wk * fi[(size_t)(NA - 1) * Nvp + k]);
+    }
+    block_sum_t<NR, RK_NT>(racc, sw, sout);
+    if (threadIdx.x == 0) {
+        double m[NR], Wn[NW], qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+        for (int q = 0; q < NR; ++q) m[q] = sout[q];
+        rk_from_raw<D>(m, Vd, Wn, qt, qr);
+        const double Vol = P.vol[i];
+        double Wt[NW];
+        for (int c = 0; c < NW; ++c) {
+            double s = 0.0;
+            for (int q = 0; q < ns; ++q) {
+                const double a = P.AF[(size_t)fs[q] * NW + c];
+                s += sg[q] > T(0) ? a : -a;
+            }
+            Wt[c] = Wi[c] - P.dt / Vol * s;
+        }
+        double rho, U[3], RTt, RTr, RT;
+        rk_prim<D>(Wt, rho, U, RTt, RTr, RT);
+        if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+        const double tau = rk_tau(P.g, rho, RTt);
+        const double az = P.dt / (P.g.Z * tau);
+        Wt[D + 2] = (Wt[D + 2] + az * rho * RT) / (1.0 + az);
+        rk_prim<D>(Wt, rho, U, RTt, RTr, RT);
+        eq = rk_make<D, T>(P.g, rho, U, RTt, RTr, qt, qr);
+        tau_s = tau;
+        for (int c = 0; c < NW; ++c) P.Wout[(size_t)i * NW + c] = Wt[c];
+    }
+    __syncthreads();
+    const T dt = (T)P.dt, tau = (T)tau_s, Vc = (T)P.vol[i];
+    const T den = T(1) / dt + T(1) / tau;
+    T* fo = P.fout + (size_t)i * cs;
+    for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
+        if (k >= Nv) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) fo[(size_t)a * Nvp + k] = T(0);
+            continue;
+        }
+        T xt[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) xt[d] = xif[(size_t)k * D + d];
+        T gv[NA];
+        rk_eval<D, T>(eq, xt, gv);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            T N = T(0);
+            for (int q = 0; q < ns; ++q) N += sg[q] * P.FX[((size_t)fs[q] * NA + a) * Nvp + k];
+            fo[(size_t)a * Nvp + k] = (fi[(size_t)a * Nvp + k] / dt + gv[a] / tau - N / Vc) / den;
+        }
+    }
+}
+
 // W (and the total heat flux q_t + q_r) of every cell.
 template <int D, typename T>
 __global__ void __launch_bounds__(RK_NT) rk_moments(int Nv, int Nvp, const T* __restrict__ f,
@@ -666,8 +1029,13 @@ cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win
                                                 f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d);
         c->launches += 1;
     }
-    rk_face<D, T><<<c->Nf, RK_NT, 0, c->stream>>>(P);
-    rk_cell<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P);
+    if constexpr (sizeof(T) == 4) {
+        rk_face32<D><<<c->Nf, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f, c->An_f, c->rL_f, c->rR_f);
+        rk_cell32<D><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f);
+    } else {
+        rk_face<D, T><<<c->Nf, RK_NT, 0, c->stream>>>(P);
+        rk_cell<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P);
+    }
     c->launches += 2;
     return cudaGetLastError();
 }

@@ -35,8 +35,8 @@ def _sampled_step(avs, w, precision, pre_steps, tol_f, tol_W):
     g.step(1, dt=dt)
     f1 = g.get_f_cells(t)
     W1 = g.moments()[0][t]
-    fo = O.step(O.MeshHandle(sub), O.gas(R=0.5, Pr=w.Pr, omega=w.omega, Kn=w.Kn, limiter=w.limiter),
-                xi, wq, dt, f0, W0)
+    gas = O.gas(R=0.5, Pr=w.Pr, omega=w.omega, Kn=w.Kn, limiter=w.limiter, model=w.model, Zrot=w.Zrot)
+    fo = O.step(O.MeshHandle(sub), gas, xi, wq, dt, f0, W0)
     e = field_err(W1, W0[pos], w.D)
     assert max(e.values()) < tol_W, e
     assert rel_err(f1, fo[pos]) < tol_f
@@ -62,3 +62,26 @@ def test_sphere_full_size_mixed_sampled():
     """147456 cells x ~21k octree nodes (FP32 f of 12.6 GB per buffer)."""
     avs = need_gpu()
     _sampled_step(avs, wl.sphere(precision="mixed", learned=False), "mixed", 5, 1e-5, 1e-5)
+
+
+def _rykov(w):
+    w.model = "rykov"
+    w.learned = False
+    return w
+
+
+def test_rykov_cylinder_full_size_fp64_sampled():
+    """The cylinder with the diatomic gas (G, H, R arrays, rotational exchange)."""
+    avs = need_gpu()
+    _sampled_step(avs, _rykov(wl.cylinder(precision="fp64")), "fp64", 2, 1e-12, 1e-12)
+
+
+def test_rykov_cylinder_full_size_mixed_sampled():
+    avs = need_gpu()
+    _sampled_step(avs, _rykov(wl.cylinder(precision="mixed")), "mixed", 10, 1e-5, 1e-5)
+
+
+def test_zoned_cylinder_full_size_mixed_sampled():
+    """The cylinder with the velocity space of the Sec. 3.5 rules."""
+    avs = need_gpu()
+    _sampled_step(avs, wl.cylinder_zones(precision="mixed"), "mixed", 20, 1e-5, 1e-5)
