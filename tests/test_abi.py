@@ -62,3 +62,42 @@ def test_bad_configs_rejected_on_host():
     assert try_cfg(limiter=5) == -1
     assert try_cfg(max_refine=20) == -1
     assert try_cfg(Kn=-1.0) == -1
+    # the options of the next rows are checked on the host too
+    assert try_cfg(model=5) == -1
+    assert try_cfg(model=1, Zrot=0.5) == -1              # Rykov: Z_rot >= 1
+    assert try_cfg(model=1, Zrot=3.5, learned=1) == -1   # no learned proposer for the diatomic gas
+    assert try_cfg(nzones=9) == -1
+    assert try_cfg(init_refine=2) == -1                  # beyond max_refine
+    z = avs.Zone()
+    z.r_in, z.r_out, z.level = 0.0, 1.0, 3              # level beyond max_refine
+    cfgz = {"nzones": 1, "zones": (avs.Zone * avs.MAX_ZONES)(z)}
+    assert try_cfg(**cfgz) == -1
+    z.level, z.r_in, z.r_out = 1, 2.0, 1.0              # r_out must exceed r_in
+    cfgz = {"nzones": 1, "zones": (avs.Zone * avs.MAX_ZONES)(z)}
+    assert try_cfg(**cfgz) == -1
+
+
+def test_paper_parameters_entry_point_on_host():
+    """avs_paper_parameters is host code: it needs no GPU and rejects bad flow data."""
+    from paper_2212_05645_gb300 import avs
+    B.build()
+    L = avs.load()
+    sp = avs.FlowSpecS()
+    sp.dim, sp.Ma, sp.gamma, sp.R, sp.T_inf, sp.T_w = 2, 5.0, 5.0 / 3.0, 0.5, 1.0, 1.0
+    sp.dir[0], sp.h_std, sp.rdv_sigma = 1.0, 0.6, 4.0
+    cfg = avs.Config()
+    assert L.avs_paper_parameters(C.byref(sp), C.byref(cfg)) == 0
+    assert (cfg.base[0], cfg.base[1], cfg.max_refine, cfg.init_refine, cfg.nzones) == (8, 8, 2, 1, 2)
+    sp.Ma = -1.0
+    assert L.avs_paper_parameters(C.byref(sp), C.byref(cfg)) == -1
+    sp.Ma, sp.dir[0] = 5.0, 0.0                         # zero direction
+    assert L.avs_paper_parameters(C.byref(sp), C.byref(cfg)) == -1
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the library missing, loading raises."""
+    from paper_2212_05645_gb300 import avs
+    monkeypatch.setattr(avs, "_lib", None)
+    monkeypatch.setattr(avs, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        avs.load()
