@@ -804,7 +804,7 @@ __global__ void k_cell_state(CellP<D, T> P)
 // raw moments of the new f about U(W~) are summed on the way for the next
 // step (same nodes per thread and order as k_raw_moments).
 template <int D, typename T, int NT, int VC>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 5 : 7) : 4) k_cell(CellP<D, T> P)
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 7 : 7) : 4) k_cell(CellP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v;
     constexpr int V = VC;
