@@ -823,6 +823,27 @@ static void euler_flux(int D, const double *W, const double *n, double *G)
     G[D + 1] = (W[D + 1] + p) * un;
 }
 
+/* Euler flux of a diatomic gas (Rykov W): p = rho R T with the equilibrium
+ * temperature of the total energy; rho E_rot is carried with the flow (R31). */
+static void euler_flux_rykov(int D, const double *W, const double *n, double *G)
+{
+    double rho, U[3], RTt, RTr, RT;
+    prim_rykov(D, W, &rho, U, &RTt, &RTr, &RT);
+    double un = 0.0;
+    for (int d = 0; d < D; ++d) un += U[d] * n[d];
+    double p = rho * RT;
+    G[0] = rho * un;
+    for (int d = 0; d < D; ++d) G[1 + d] = W[1 + d] * un + p * n[d];
+    G[D + 1] = (W[D + 1] + p) * un;
+    G[D + 2] = W[D + 2] * un;
+}
+
+static void euler_flux_g(const om_gas *g, int D, const double *W, const double *n, double *G)
+{
+    if (g->model) euler_flux_rykov(D, W, n, G);
+    else euler_flux(D, W, n, G);
+}
+
 /* Spectral radius of the Roe-type dissipation at a face (Eq. after Eq. Roe):
  * r = |U.n| + a + 2 mu / (rho dl), from the mean of the primitive states of
  * the two sides (reading: the paper leaves the interface state open), a the
@@ -830,6 +851,16 @@ static void euler_flux(int D, const double *W, const double *n, double *G)
 static double roe_radius(const om_gas *g, int D, const double *WL, const double *WR, const double *n, double dl)
 {
     double rl, Ul[3], RTl, rr, Ur[3], RTr;
+    if (g->model) {
+        /* Rykov (R31): a = sqrt(7/5 R T) with the equilibrium T, mu at the mean T_t */
+        double tl, ql, tr, qr;
+        prim_rykov(D, WL, &rl, Ul, &tl, &ql, &RTl);
+        prim_rykov(D, WR, &rr, Ur, &tr, &qr, &RTr);
+        double rho = 0.5 * (rl + rr), RT = 0.5 * (RTl + RTr), RTt = 0.5 * (tl + tr), un = 0.0;
+        for (int d = 0; d < D; ++d) un += 0.5 * (Ul[d] + Ur[d]) * n[d];
+        double mu = g->mu_ref * pow(RTt / g->R / g->T_ref, g->omega);
+        return fabs(un) + sqrt(7.0 / 5.0 * RT) + 2.0 * mu / (rho * dl);
+    }
     prim_of(D, WL, &rl, Ul, &RTl);
     prim_of(D, WR, &rr, Ur, &RTr);
     double rho = 0.5 * (rl + rr), RT = 0.5 * (RTl + RTr), un = 0.0;
@@ -854,8 +885,7 @@ int om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi
                      double dt, const double *f_in, double *f_out, double *Wc,
                      const int *color, int ncolor, int k_macro, int k_micro)
 {
-    const int D = m->D, nA = nArr(D), NW = D + 2, Nc = m->Nc, Nf = m->Nf;
-    if (g->model) return -1;                  /* the implicit step is built for the Shakhov model */
+    const int D = m->D, nA = nArrG(g, D), NW = nWG(g, D), Nc = m->Nc, Nf = m->Nf;
     slots_t *S = build_slots(m);
     double *phi = (double *)malloc((size_t)Nf * nA * Nv * sizeof(double));
     double *F = (double *)calloc((size_t)Nf * NW, sizeof(double));
@@ -902,7 +932,7 @@ int om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi
         for (int dir = 0; dir < 2; ++dir) {
             for (int q = 0; q < Nc; ++q) {
                 const int i = order[dir == 0 ? q : Nc - 1 - q];
-                double diag = m->vol[i] / dt, rhs[5];
+                double diag = m->vol[i] / dt, rhs[6];
                 for (int c = 0; c < NW; ++c) {
                     double acc = 0.0;
                     for (int sl = 0; sl < S[i].n; ++sl) acc += S[i].sgn[sl] * F[(size_t)S[i].face[sl] * NW + c];
@@ -918,14 +948,26 @@ int om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi
                     for (int d = 0; d < D; ++d) A += An[d] * An[d];
                     A = sqrt(A);
                     for (int d = 0; d < D; ++d) n[d] = S[i].sgn[sl] * An[d] / A;
-                    double Gt[5], Gn[5];
-                    euler_flux(D, Wt + (size_t)j * NW, n, Gt);
-                    euler_flux(D, Wc + (size_t)j * NW, n, Gn);
+                    double Gt[6], Gn[6];
+                    euler_flux_g(g, D, Wt + (size_t)j * NW, n, Gt);
+                    euler_flux_g(g, D, Wc + (size_t)j * NW, n, Gn);
                     for (int c = 0; c < NW; ++c)
                         rhs[c] += -0.5 * A * (Gt[c] - Gn[c]) + 0.5 * rad[f] * dW[(size_t)j * NW + c];
                 }
+                double diag_rot = diag;
+                if (g->model) {
+                    /* rotational source of Eq. (SGS_wrot), (rho R T - rho E_rot^n)/(Z tau), with
+                     * rho R T and tau from the cell's current W~ (reading R32); its implicit
+                     * part V/(Z tau) joins the diagonal of the rho E_rot row */
+                    double rho, U[3], RTt, RTr, RT;
+                    prim_rykov(D, Wt + (size_t)i * NW, &rho, U, &RTt, &RTr, &RT);
+                    if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) bad = 1;
+                    double tau = tau_of(g, rho, RTt), V = m->vol[i];
+                    rhs[D + 2] += V * (rho * RT - Wc[(size_t)i * NW + D + 2]) / (g->Zrot * tau);
+                    diag_rot = diag + V / (g->Zrot * tau);
+                }
                 for (int c = 0; c < NW; ++c) {
-                    dW[(size_t)i * NW + c] = rhs[c] / diag;
+                    dW[(size_t)i * NW + c] = rhs[c] / (c == D + 2 ? diag_rot : diag);
                     Wt[(size_t)i * NW + c] = Wc[(size_t)i * NW + c] + dW[(size_t)i * NW + c];
                 }
             }
@@ -938,6 +980,40 @@ int om_step_implicit(const om_mesh *m, const om_gas *g, int Nv, const double *xi
 #pragma omp parallel for schedule(static) reduction(|:bad)
     for (int i = 0; i < Nc; ++i) {
         const double *fi = f_in + (size_t)i * nA * Nv;
+        if (g->model) {
+            /* Rykov: g~ from W~ with the lagged q_t, q_r of f^n, tau~ from T_t of W~ */
+            double Wr[6], qt[3], qr[3];
+            cell_moments_rykov(D, Nv, xi, w, fi, Wr, qt, qr);
+            double rho, U[3], RTt, RTr, RT;
+            prim_rykov(D, Wt + (size_t)i * NW, &rho, U, &RTt, &RTr, &RT);
+            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) bad = 1;
+            double tau = tau_of(g, rho, RTt), V = m->vol[i];
+            for (int k = 0; k < Nv; ++k) {
+                const double *x = xi + (size_t)k * D;
+                double v[3], out = 0.0;
+                rykov(D, g, rho, U, RTt, RTr, qt, qr, x, v);
+                for (int sl = 0; sl < S[i].n; ++sl) {
+                    const double *An = m->An + (size_t)S[i].face[sl] * D;
+                    double sn = 0.0;
+                    for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                    sn *= S[i].sgn[sl];
+                    if (sn >= 0.0) out += sn;
+                }
+                dg[(size_t)i * Nv + k] = V / dt + V / tau + out;
+                for (int a = 0; a < nA; ++a) {
+                    double N = 0.0;
+                    for (int sl = 0; sl < S[i].n; ++sl) {
+                        int f = S[i].face[sl];
+                        const double *An = m->An + (size_t)f * D;
+                        double sn = 0.0;
+                        for (int d = 0; d < D; ++d) sn += x[d] * An[d];
+                        N += S[i].sgn[sl] * sn * phi[((size_t)f * nA + a) * Nv + k];
+                    }
+                    res[((size_t)i * nA + a) * Nv + k] = V * (v[a] - fi[a * Nv + k]) / tau - N;
+                }
+            }
+            continue;
+        }
         double Wn[5], qn[3];
         cell_moments(D, Nv, xi, w, fi, Wn, qn);          /* lagged heat flux of f^n (R3) */
         double rho, U[3], RT;

@@ -219,3 +219,70 @@ def test_correction_restores_rykov_moments():
         gaps.append(O.correct_rykov(D, xi2, w2, W, g2, iters=it))
     assert all(b < a for a, b in zip(gaps, gaps[1:]))
     assert gaps[-1] < 1e-13
+
+
+# ---------------------------------------------------------------- implicit step (Eqs. SGS_w, SGS_wrot, SGS_phi)
+def test_implicit_uniform_gas_rotational_relaxation_fixed_point():
+    """Uniform gas at rest, T_r != T_t, periodic box: no net transport, so the
+    converged macroscopic sweeps solve the backward-Euler rotational exchange
+    E_rot^{n+1} = E_rot^n + dt (rho R T - E_rot^{n+1}) / (Z tau(T_t^{n+1}))
+    of Eq. (SGS_wrot) with rho R T fixed by the total energy; mass, momentum
+    and total energy stay."""
+    m = _box(3)
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=0.05, model="rykov")
+    sig = math.sqrt(R * 1.6)
+    xi, w = uniform_forest(2, 40, -10 * sig, 10 * sig)
+    Wp = np.tile([1.0, 0.0, 0.0, 1.6, 0.6], (m.Nc, 1))
+    f = O.maxwell_init_rykov(2, xi, Wp)
+    Wc = O.moments_rykov(2, xi, w, f)[0]
+    W0 = Wc.copy()
+    col, nc = O.colors(mh)
+    dt = 2.0 * O.dt_unit(mh, xi)
+    O.step_implicit(mh, g, xi, w, dt, f, Wc, col, nc, k_macro=60, k_micro=2)
+    rho = W0[0, 0]
+    RT = W0[0, 3] / (2.5 * rho)
+    E = Wc[:, 4]
+    RTt = (W0[0, 3] - E) / (1.5 * rho)
+    tau = g.mu_ref * (RTt / R) ** g.omega / (rho * RTt)
+    resid = E - W0[:, 4] - dt * (rho * RT - E) / (Z * tau)
+    assert np.abs(resid).max() < 1e-12 * W0[0, 4]
+    assert np.allclose(Wc[:, :4], W0[:, :4], rtol=1e-13, atol=1e-15)
+    assert (E > W0[:, 4]).all() and (E < rho * RT).all()        # toward equilibrium, not past it
+
+
+def test_implicit_rykov_sweeps_converge_independent_of_order_and_conserve():
+    from test_oracle_pins import _other_coloring
+    w = wl.sweep_box((6, 5), base=(10, 10), max_refine=1)
+    w.model = "rykov"
+    vol = w.mesh.vol[:, None]
+    outs = []
+    for col in (None, _other_coloring(w.mesh)):
+        r = O.Run(w)
+        Wp = np.column_stack([w.W_init, 0.8 * w.W_init[:, 3]])
+        r.init_field(Wp, amp=1e-2, seed=8)
+        dt = r.dt(1.5)
+        tot0 = (r.Wc * vol).sum(0)
+        r.step_implicit(dt, k_macro=300, k_micro=300, color=col)
+        tot = (r.Wc * vol).sum(0)
+        assert np.allclose(tot[:4], tot0[:4], rtol=1e-12, atol=1e-13)
+        outs.append((r.f.copy(), r.Wc.copy()))
+    assert np.abs(outs[0][0] - outs[1][0]).max() <= 1e-11 * np.abs(outs[0][0]).max()
+    assert np.abs(outs[0][1] - outs[1][1]).max() <= 1e-11 * np.abs(outs[0][1]).max()
+
+
+def test_implicit_rykov_matches_explicit_to_first_order_in_dt():
+    w = wl.sweep_box((6, 5), base=(10, 10), max_refine=1)
+    w.model = "rykov"
+    ratio = []
+    for cfl in (0.4, 0.2):
+        re, ri = O.Run(w), O.Run(w)
+        Wp = np.column_stack([w.W_init, 0.8 * w.W_init[:, 3]])
+        for r in (re, ri):
+            r.init_field(Wp, amp=1e-2, seed=9)
+        f0 = re.f.copy()
+        dt = re.dt(cfl)
+        re.step(dt)
+        ri.step_implicit(dt, k_macro=200, k_micro=200)
+        ratio.append(np.abs(ri.f - re.f).max() / np.abs(re.f - f0).max())
+    assert 0.35 < ratio[1] / ratio[0] < 0.65, ratio
