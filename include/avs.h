@@ -186,7 +186,11 @@ avs_status ugks_step_dt(avs_ctx *ctx, int nsteps, double dt);
  * Eq. (SGS_phi) for phi^{n+1} - phi^n, each solved by k_macro / k_micro
  * symmetric Gauss-Seidel iterations (a forward and a backward sweep over a
  * greedy cell colouring).  Boundary faces enter both diagonals with a fixed
- * ghost state.  The paper recommends k_macro = 60, k_micro = 2.  The
+ * ghost state.  Rykov model: the diatomic Euler flux (p from the equilibrium
+ * temperature, rho E_rot carried) and radius (a = sqrt(7/5 R T)), and Eq.
+ * (SGS_wrot) for rho E_rot with the rotational source taken from the cell's
+ * current W~ and its implicit part in the diagonal.  The paper recommends
+ * k_macro = 60, k_micro = 2.  The
  * macroscopic solve is one cooperative launch with a bounded grid barrier
  * between colour passes.  Does not synchronise.  Errors: EINVAL (nsteps < 0,
  * dt <= 0, negative sweep counts), ECUDA; at the next blocking call ENUMERIC

@@ -373,8 +373,8 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
         dalloc(&c->eps2_d, Nc) || dalloc(&c->cg_f, ncsd) || dalloc(&c->r_f, ncsd) || dalloc(&c->eps2_f, Nc) ||
         dalloc(&c->AFf, (size_t)Nf * c->NW) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * avs::NMom<3>::v) ||
         dalloc((unsigned char**)&c->cpar, (size_t)Nc * AVS_CELLPAR_BYTES) || dalloc(&c->clist, Nc) ||
-        dalloc(&c->imp_dW, (size_t)Nc * (D + 2)) || dalloc(&c->imp_rhs0, (size_t)Nc * (D + 2)) ||
-        dalloc(&c->imp_diag, Nc) || dalloc(&c->imp_Wta, (size_t)Nc * (D + 2)) ||
+        dalloc(&c->imp_dW, (size_t)Nc * c->NW) || dalloc(&c->imp_rhs0, (size_t)Nc * c->NW) ||
+        dalloc(&c->imp_diag, Nc) || dalloc(&c->imp_Wta, (size_t)Nc * c->NW) ||
         dalloc(&c->imp_co, ncs * AVS_IMPSLOT_BYTES) || dalloc(&c->imp_nint, Nc) || dalloc(&c->imp_bar, 1))
         return fail(c, AVS_ENOMEM, "mesh arrays");
     cudaStream_t s = c->stream;
@@ -655,10 +655,13 @@ avs_status ugks_step_dt(avs_ctx* c, int nsteps, double dt)
 avs_status ugks_step_implicit(avs_ctx* c, int nsteps, double dt, int k_macro, int k_micro)
 {
     if (!c || nsteps < 0 || !(dt > 0) || k_macro < 0 || k_micro < 0) return AVS_EINVAL;
-    if (c->model != AVS_SHAKHOV) return fail(c, AVS_EINVAL, "the implicit step is built for the Shakhov model");
     for (int s = 0; s < nsteps; ++s) {
-        CK(launch_step_implicit(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt, k_macro,
-                                k_micro));
+        if (c->model == AVS_RYKOV)
+            CK(rk_launch_step_implicit(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt,
+                                       k_macro, k_micro));
+        else
+            CK(launch_step_implicit(c, c->f[c->cur], c->f[c->cur ^ 1], c->W[c->wcur], c->W[c->wcur ^ 1], dt, k_macro,
+                                    k_micro));
         c->cur ^= 1;
         c->wcur ^= 1;
     }

@@ -573,4 +573,40 @@ __host__ __device__ inline double dkey_inv(unsigned long long k)
     return x;
 }
 
+// Grid-wide barrier of a cooperative launch, bounded: the block's thread 0
+// counts in and waits for the target count at most kGridSpin polls; a timeout
+// (or one seen in another block) sets error bit 2 and makes the block leave.
+// Monotone counter: the n-th barrier waits for n * gridDim.x arrivals.
+constexpr long long kGridSpin = 1ll << 21;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned target, int* err)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int good = 1;
+        for (long long it = 0; ld_acquire_u32(bar) < target; ++it) {
+            if (it >= kGridSpin || ((it & 255) == 255 && (*(volatile int*)err & 2))) {
+                atomicOr(err, 2);
+                good = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
 }  // namespace avs

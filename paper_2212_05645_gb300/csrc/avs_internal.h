@@ -103,8 +103,8 @@ struct avs_ctx {
     std::vector<int> cstart;                         // [ncolor+1] offsets into clist (host)
     int *clist = nullptr;                            // [Nc] cells by colour, ascending within a colour
     int *cstart_d = nullptr;                         // [ncolor+1] the same offsets on the device
-    double *imp_dW = nullptr, *imp_rhs0 = nullptr;   // [Nc][D+2] (dW and -sum sgn A F, in the sweep type)
-    double *imp_Wta = nullptr;                       // [Nc][D+2] W~ in FP32 (mixed form)
+    double *imp_dW = nullptr, *imp_rhs0 = nullptr;   // [Nc][NW] (dW and -sum sgn A F, in the sweep type)
+    double *imp_Wta = nullptr;                       // [Nc][NW] W~ in FP32 (mixed form)
     double *imp_diag = nullptr;                      // [Nc]
     unsigned char *imp_co = nullptr;                 // [Nc][MAXS] interior slot records (AVS_IMPSLOT_BYTES each)
     unsigned char *imp_nint = nullptr;               // [Nc] interior slots per cell in sweep order
@@ -135,6 +135,8 @@ int round_up(int n, int m);
 cudaError_t launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
 // Rykov model (csrc/avs_rykov.cu)
 cudaError_t rk_launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
+cudaError_t rk_launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout,
+                                    double dt, int k_macro, int k_micro);
 cudaError_t rk_launch_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wout,
                               double* qout);
 cudaError_t rk_launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters);

@@ -954,6 +954,369 @@ __global__ void rk_cons_to_prim(int Nc, const double* __restrict__ Wc, double R,
     P[D + 2] = RTr / R;
 }
 
+// ---------------------------------------------------------------- implicit step
+// IUGKS for the Rykov model (Sec. 2.3.1): the face stage of the explicit step,
+// then Eq. (SGS_w) for rho, rho U, rho E and Eq. (SGS_wrot) for rho E_rot by
+// symmetric Gauss-Seidel over the cell colouring (one cooperative launch,
+// bounded grid barrier between colour passes), then Eq. (SGS_phi) for G, H,
+// R.  The same structure as the monatomic implicit step; readings R31-R32.
+
+// Euler flux of a diatomic gas: p = rho R T (equilibrium T of the total
+// energy), rho E_rot carried with the flow.
+template <int D, typename A>
+__device__ __forceinline__ void rk_euler_flux(const A* W, const A* n, A* G)
+{
+    const A rho = W[0];
+    A m2 = A(0), un = A(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        m2 += W[1 + d] * W[1 + d];
+        un += (W[1 + d] / rho) * n[d];
+    }
+    const A p = rho * ((W[D + 1] - A(0.5) * m2 / rho) / (A(2.5) * rho));
+    G[0] = rho * un;
+#pragma unroll
+    for (int d = 0; d < D; ++d) G[1 + d] = W[1 + d] * un + p * n[d];
+    G[D + 1] = (W[D + 1] + p) * un;
+    G[D + 2] = W[D + 2] * un;
+}
+
+template <typename A>
+struct RkImpSlot {
+    A n[3];
+    A nhA;
+    A hr;
+    A Gn[6];
+    int j;
+};
+static_assert(sizeof(RkImpSlot<double>) <= AVS_IMPSLOT_BYTES, "slot record");
+
+template <typename A>
+struct RkImpP {
+    int Nc;
+    double dt;
+    RkGas g;
+    const int* slot;
+    const unsigned char* nslot;
+    const int* faceL;
+    const int* faceR;
+    const double* An;
+    const double* rL;
+    const double* rR;
+    const double* vol;
+    const double* AF;
+    const double* Wn;        // W^n [cell][NW]
+    double* Wt;              // W~ [cell][NW]
+    A* dWa;                  // dW [cell][NW]
+    A* Wta;                  // W~ in A [cell][NW]; aliases Wt when A is double
+    A* rhs;                  // [q][NW]
+    A* dg;                   // [q]
+    RkImpSlot<A>* co;        // [q][MAXS]
+    unsigned char* nint;     // [q]
+    const int* clist;
+    int* err;
+};
+
+template <int D, typename A>
+__global__ void rk_imp_setup(RkImpP<A> P)
+{
+    constexpr int NW = D + 3;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= P.Nc) return;
+    const int i = P.clist[q];
+    const int ns = P.nslot[i];
+    const double* Wi = P.Wn + (size_t)i * NW;
+    for (int c = 0; c < NW; ++c) {
+        double acc = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            const int sl = P.slot[i * AVS_MAXS + s];
+            const double a = P.AF[(size_t)(sl >> 1) * NW + c];
+            acc += (sl & 1) ? -a : a;
+        }
+        P.rhs[(size_t)q * NW + c] = (A)(-acc);
+        P.dWa[(size_t)i * NW + c] = A(0);
+        P.Wt[(size_t)i * NW + c] = Wi[c];
+        P.Wta[(size_t)i * NW + c] = (A)Wi[c];
+    }
+    double dg = P.vol[i] / P.dt;
+    int nint = 0;
+    for (int s = 0; s < ns; ++s) {
+        const int sl = P.slot[i * AVS_MAXS + s];
+        const int f = sl >> 1;
+        const double sgn = (sl & 1) ? -1.0 : 1.0;
+        const int L = P.faceL[f], R = P.faceR[f];
+        const double* An = P.An + (size_t)f * D;
+        double Aa = 0.0;
+        for (int d = 0; d < D; ++d) Aa += An[d] * An[d];
+        Aa = sqrt(Aa);
+        double n[3] = {0, 0, 0}, dl = 0.0;
+        for (int d = 0; d < D; ++d) n[d] = An[d] / Aa;
+        for (int d = 0; d < D; ++d) {
+            const double e = R >= 0 ? P.rL[(size_t)f * D + d] - P.rR[(size_t)f * D + d] : 2.0 * P.rL[(size_t)f * D + d];
+            dl += e * e;
+        }
+        dl = sqrt(dl);
+        // radius |U.n| + a + 2 mu / (rho dl): a = sqrt(7/5 R T), mu at the mean T_t (R31)
+        double rl, Ul[3], tl, ql, RTl, rr, Ur[3], tr, qr2, RTr;
+        rk_prim<D>(P.Wn + (size_t)L * NW, rl, Ul, tl, ql, RTl);
+        rk_prim<D>(P.Wn + (size_t)(R >= 0 ? R : L) * NW, rr, Ur, tr, qr2, RTr);
+        const double rho = 0.5 * (rl + rr), RT = 0.5 * (RTl + RTr), RTt = 0.5 * (tl + tr);
+        double un = 0.0;
+        for (int d = 0; d < D; ++d) un += 0.5 * (Ul[d] + Ur[d]) * n[d];
+        const double mu = P.g.mu_ref * pow(RTt / P.g.R / P.g.T_ref, P.g.omega);
+        const double r = Aa * (fabs(un) + sqrt(7.0 / 5.0 * RT) + 2.0 * mu / (rho * dl));
+        dg += 0.5 * r;
+        const int j = (sl & 1) ? L : R;
+        if (j >= 0) {
+            RkImpSlot<A> sc;
+            for (int d = 0; d < 3; ++d) sc.n[d] = d < D ? (A)(sgn * An[d] / Aa) : A(0);
+            sc.nhA = (A)(-0.5 * Aa);
+            sc.hr = (A)(0.5 * r);
+            A Wj[NW];
+            for (int c = 0; c < NW; ++c) Wj[c] = (A)P.Wn[(size_t)j * NW + c];
+            rk_euler_flux<D, A>(Wj, sc.n, sc.Gn);
+            for (int c = NW; c < 6; ++c) sc.Gn[c] = A(0);
+            sc.j = j;
+            P.co[(size_t)q * AVS_MAXS + nint++] = sc;
+        }
+    }
+    P.dg[q] = (A)dg;
+    P.nint[q] = (unsigned char)nint;
+}
+
+// One cell of a macroscopic sweep, with the rotational source of Eq.
+// (SGS_wrot) from the cell's current W~ (reading R32).
+template <int D, typename A>
+__device__ __forceinline__ void rk_imp_cell(const RkImpP<A>& P, int q)
+{
+    constexpr int NW = D + 3;
+    const int i = P.clist[q];
+    const int n = P.nint[q];
+    A rhs[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) rhs[c] = P.rhs[(size_t)q * NW + c];
+    for (int s = 0; s < n; ++s) {
+        const RkImpSlot<A> sc = P.co[(size_t)q * AVS_MAXS + s];
+        A Wj[NW], dWj[NW], G[NW];
+#pragma unroll
+        for (int c = 0; c < NW; ++c) {
+            Wj[c] = __ldcg(P.Wta + (size_t)sc.j * NW + c);
+            dWj[c] = __ldcg(P.dWa + (size_t)sc.j * NW + c);
+        }
+        rk_euler_flux<D, A>(Wj, sc.n, G);
+#pragma unroll
+        for (int c = 0; c < NW; ++c) rhs[c] += sc.nhA * (G[c] - sc.Gn[c]) + sc.hr * dWj[c];
+    }
+    const A dg = P.dg[q];
+    A dgr = dg;
+    {
+        A W[NW];
+#pragma unroll
+        for (int c = 0; c < NW; ++c) W[c] = __ldcg(P.Wta + (size_t)i * NW + c);
+        const A rho = W[0];
+        A m2 = A(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) m2 += W[1 + d] * W[1 + d];
+        const A eint = W[D + 1] - A(0.5) * m2 / rho;
+        const A RT = eint / (A(2.5) * rho);
+        const A RTt = (eint - W[D + 2]) / (A(1.5) * rho);
+        if (!(rho > A(0)) || !(RTt > A(0)) || !(RT > A(0))) atomicOr(P.err, 1);
+        const A T = RTt / (A)P.g.R;
+        const A mu = (A)P.g.mu_ref * powa(T / (A)P.g.T_ref, (A)P.g.omega);
+        const A tau = mu / (rho * RTt);
+        const A V = (A)P.vol[i], Z = (A)P.g.Z;
+        rhs[D + 2] += V * (rho * RT - (A)P.Wn[(size_t)i * NW + D + 2]) / (Z * tau);
+        dgr = dg + V / (Z * tau);
+    }
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        const A d = rhs[c] / (c == D + 2 ? dgr : dg);
+        const double wt = P.Wn[(size_t)i * NW + c] + (double)d;
+        __stcg(P.dWa + (size_t)i * NW + c, d);
+        if constexpr (sizeof(A) == sizeof(double)) {
+            __stcg(P.Wt + (size_t)i * NW + c, wt);
+        } else {
+            P.Wt[(size_t)i * NW + c] = wt;
+            __stcg(P.Wta + (size_t)i * NW + c, (A)wt);
+        }
+    }
+}
+
+// All colour passes of the macroscopic solve in one cooperative launch.
+// Unlike the monatomic sweep, a colour that follows itself is not skipped:
+// the rotational source reads the cell's own W~, which the first of the two
+// passes changes.
+template <int D, typename A, int NT>
+__global__ void __launch_bounds__(NT) rk_imp_macro(RkImpP<A> P, int k_macro, int ncolor,
+                                                   const int* __restrict__ cstart, unsigned* bar)
+{
+    const unsigned nb = gridDim.x;
+    unsigned gen = 0;
+    bool first = true;
+    for (int it = 0; it < k_macro; ++it)
+        for (int dir = 0; dir < 2; ++dir)
+            for (int qq = 0; qq < ncolor; ++qq) {
+                const int col = dir == 0 ? qq : ncolor - 1 - qq;
+                if (!first && !grid_sync_bounded(bar, ++gen * nb, P.err)) return;
+                first = false;
+                const int c1 = cstart[col + 1];
+                for (int q = cstart[col] + blockIdx.x * NT + threadIdx.x; q < c1; q += nb * NT)
+                    rk_imp_cell<D, A>(P, q);
+            }
+}
+// Per cell: Rykov state of W~ with the lagged q_t, q_r of f^n, and the
+// microscopic residual Res = V (g~ - phi^n) / tau~ - N of every array (written
+// over the f^{n+1} buffer); u0[i] = V/dt + V/tau~ for the sweeps.
+template <int D, typename T>
+__global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restrict__ xiT,
+                                                    const T* __restrict__ wT, double* u0)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
+    __shared__ double sred[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
+    __shared__ RkEq<T> eq;
+    __shared__ double tau_s;
+    __shared__ int fs[AVS_MAXS];
+    __shared__ T sg[AVS_MAXS];
+    const int i = blockIdx.x;
+    const int ns = P.nslot[i];
+    const int Nv = P.Nv, Nvp = P.Nvp;
+    if (threadIdx.x < ns) {
+        const int sl = P.slot[i * AVS_MAXS + threadIdx.x];
+        fs[threadIdx.x] = sl >> 1;
+        sg[threadIdx.x] = (sl & 1) ? T(-1) : T(1);
+    }
+    const size_t cs = (size_t)NA * Nvp;
+    const T* fi = P.f + (size_t)i * cs;
+    double qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+    if constexpr (sizeof(T) == 4) {
+        const double* Wi = P.Win + (size_t)i * NW;
+        T V[D];
+        double Vd[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) {
+            V[d] = (T)(Wi[1 + d] / Wi[0]);
+            Vd[d] = (double)V[d];
+        }
+        T racc[NR];
+#pragma unroll
+        for (int m = 0; m < NR; ++m) racc[m] = T(0);
+        for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+            T c[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) c[d] = xiT[(size_t)k * D + d] - V[d];
+            const T wk = wT[k];
+            rk_raw_acc<D>(racc, c, wk * fi[k], D == 2 ? wk * fi[Nvp + k] : T(0), wk * fi[(size_t)(NA - 1) * Nvp + k]);
+        }
+        block_sum_t<NR, RK_NT>(racc, sred, sout);
+        if (threadIdx.x == 0) {
+            double m[NR], Wn[NW];
+            for (int q = 0; q < NR; ++q) m[q] = sout[q];
+            rk_from_raw<D>(m, Vd, Wn, qt, qr);
+        }
+    } else {
+        double Wn[NW];
+        rk_cell_mom<D, T>(fi, Nv, Nvp, P.xi, P.w, Wn, qt, qr, sred, sout);
+    }
+    if (threadIdx.x == 0) {
+        double rho, U[3], RTt, RTr, RT;
+        rk_prim<D>(P.Wout + (size_t)i * NW, rho, U, RTt, RTr, RT);
+        if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+        const double tau = rk_tau(P.g, rho, RTt);
+        eq = rk_make<D, T>(P.g, rho, U, RTt, RTr, qt, qr);
+        tau_s = tau;
+        u0[i] = P.vol[i] / P.dt + P.vol[i] / tau;
+    }
+    __syncthreads();
+    const T tau = (T)tau_s, Vc = (T)P.vol[i];
+    T* ro = P.fout + (size_t)i * cs;
+    for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
+        if (k >= Nv) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) ro[(size_t)a * Nvp + k] = T(0);
+            continue;
+        }
+        T xt[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) xt[d] = xiT[(size_t)k * D + d];
+        T gv[NA];
+        rk_eval<D, T>(eq, xt, gv);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            T N = T(0);
+            for (int q = 0; q < ns; ++q) N += sg[q] * P.FX[((size_t)fs[q] * NA + a) * Nvp + k];
+            ro[(size_t)a * Nvp + k] = Vc * (gv[a] - fi[(size_t)a * Nvp + k]) / tau - N;
+        }
+    }
+}
+
+// One colour of a microscopic sweep (Eq. SGS_phi), every node and array:
+// dphi_i = (Res_i - sum_{xi.n<0} (xi.n) dphi_j) / (u0_i + sum_{xi.n>=0} xi.n).
+template <int D, typename T>
+__global__ void __launch_bounds__(RK_NT) rk_imp_micro(int Nv, int Nvp, const T* __restrict__ res, T* dphi,
+                                                      const double* __restrict__ u0, const T* __restrict__ xiT,
+                                                      const double* __restrict__ xid, const double* __restrict__ Ad,
+                                                      const T* __restrict__ An, const int* __restrict__ slot,
+                                                      const unsigned char* __restrict__ nslot,
+                                                      const int* __restrict__ faceL, const int* __restrict__ faceR,
+                                                      const int* __restrict__ clist, int c0)
+{
+    constexpr int NA = RkNA<D>::v;
+    __shared__ T sA[AVS_MAXS][D];
+    __shared__ double sAd[AVS_MAXS][3];
+    __shared__ int snb[AVS_MAXS];
+    const int i = clist[c0 + blockIdx.x];
+    const int ns = nslot[i];
+    if (threadIdx.x < ns) {
+        const int sl = slot[i * AVS_MAXS + threadIdx.x];
+        const int f = sl >> 1;
+        for (int d = 0; d < D; ++d) {
+            sA[threadIdx.x][d] = (sl & 1) ? -An[(size_t)f * D + d] : An[(size_t)f * D + d];
+            sAd[threadIdx.x][d] = (sl & 1) ? -Ad[(size_t)f * D + d] : Ad[(size_t)f * D + d];
+        }
+        snb[threadIdx.x] = (sl & 1) ? faceL[f] : faceR[f];
+    }
+    __syncthreads();
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= Nvp) return;
+    if (k >= Nv) {
+        for (int a = 0; a < NA; ++a) dphi[((size_t)i * NA + a) * Nvp + k] = T(0);
+        return;
+    }
+    // xi . n per slot: FP64 without contraction in the FP64 form (the oracle's
+    // upwind split), the element type otherwise
+    T sn[AVS_MAXS];
+    T out = T(0);
+    for (int s = 0; s < ns; ++s) {
+        T v;
+        if constexpr (sizeof(T) == 8) {
+            double xd[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) xd[d] = xid[(size_t)k * D + d];
+            v = (T)dot_rn<D>(xd, sAd[s]);
+        } else {
+            v = T(0);
+            for (int d = 0; d < D; ++d) v += xiT[(size_t)k * D + d] * sA[s][d];
+        }
+        sn[s] = v;
+        if (v >= T(0)) out += v;
+    }
+    const T dg = (T)u0[i] + out;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        T acc = res[((size_t)i * NA + a) * Nvp + k];
+        for (int s = 0; s < ns; ++s)
+            if (snb[s] >= 0 && sn[s] < T(0)) acc -= sn[s] * dphi[((size_t)snb[s] * NA + a) * Nvp + k];
+        dphi[((size_t)i * NA + a) * Nvp + k] = acc / dg;
+    }
+}
+
+// f^{n+1} = f^n + dphi (pad nodes zero)
+template <typename T>
+__global__ void rk_imp_finish(int Nv, int Nvp, const T* __restrict__ fin, const T* __restrict__ dphi, T* fout)
+{
+    const int r = blockIdx.x;
+    for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < Nvp; k += gridDim.y * blockDim.x)
+        fout[(size_t)r * Nvp + k] = k < Nv ? fin[(size_t)r * Nvp + k] + dphi[(size_t)r * Nvp + k] : T(0);
+}
+
 RkGas rk_gas(const avs_ctx* c)
 {
     RkGas g;
@@ -980,8 +1343,9 @@ cudaError_t ensure_bytes(void** p, size_t* have, size_t need)
     return e;
 }
 
+// Gradient and face kernels of a step: fills P and launches them.
 template <int D, typename T>
-cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt)
+cudaError_t rk_face_stage(avs_ctx* c, const void* fin, const double* Win, double dt, RkP<T>& P)
 {
     constexpr int NA = RkNA<D>::v;
     const bool f32 = sizeof(T) == 4;
@@ -992,9 +1356,9 @@ cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win
         e = ensure_bytes(&c->grad, &c->grad_bytes, (size_t)c->Nc * NA * D * rows * sizeof(T));
         if (e != cudaSuccess) return e;
     }
-    e = ensure_bytes(&c->flux, &c->flux_bytes, (size_t)c->Nf * NA * rows * sizeof(T));
+    // the face flux, and in the implicit step afterwards the per-cell dphi
+    e = ensure_bytes(&c->flux, &c->flux_bytes, (size_t)std::max(c->Nf, c->Nc) * NA * rows * sizeof(T));
     if (e != cudaSuccess) return e;
-    RkP<T> P;
     P.Nv = c->Nv;
     P.Nvp = c->Nvp;
     P.Nc = c->Nc;
@@ -1018,8 +1382,8 @@ cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win
     P.FX = (T*)c->flux;
     P.AF = c->AFf;
     P.Win = Win;
-    P.Wout = Wout;
-    P.fout = (T*)fout;
+    P.Wout = nullptr;
+    P.fout = nullptr;
     P.err = c->dev_err;
     if (grad) {
         dim3 g(c->Nc, (c->Nv + 255) / 256);
@@ -1029,14 +1393,119 @@ cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win
                                                 f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d);
         c->launches += 1;
     }
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4)
         rk_face32<D><<<c->Nf, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f, c->An_f, c->rL_f, c->rR_f);
-        rk_cell32<D><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f);
-    } else {
+    else
         rk_face<D, T><<<c->Nf, RK_NT, 0, c->stream>>>(P);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+template <int D, typename T>
+cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt)
+{
+    RkP<T> P;
+    cudaError_t e = rk_face_stage<D, T>(c, fin, Win, dt, P);
+    if (e != cudaSuccess) return e;
+    P.Wout = Wout;
+    P.fout = (T*)fout;
+    if constexpr (sizeof(T) == 4)
+        rk_cell32<D><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f);
+    else
         rk_cell<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+template <int D, typename T>
+cudaError_t rk_step_implicit_t(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt,
+                               int k_macro, int k_micro)
+{
+    constexpr int NA = RkNA<D>::v;
+    const bool f32 = sizeof(T) == 4;
+    RkP<T> P;
+    cudaError_t e = rk_face_stage<D, T>(c, fin, Win, dt, P);
+    if (e != cudaSuccess) return e;
+    // ---- macroscopic system, Eqs. (SGS_w), (SGS_wrot)
+    using A = T;
+    RkImpP<A> I;
+    I.Nc = c->Nc;
+    I.dt = dt;
+    I.g = P.g;
+    I.slot = c->slot;
+    I.nslot = c->nslot;
+    I.faceL = c->faceL;
+    I.faceR = c->faceR;
+    I.An = c->An_d;
+    I.rL = c->rL_d;
+    I.rR = c->rR_d;
+    I.vol = c->vol;
+    I.AF = c->AFf;
+    I.Wn = Win;
+    I.Wt = Wout;
+    I.dWa = (A*)c->imp_dW;
+    I.Wta = f32 ? (A*)c->imp_Wta : (A*)Wout;
+    I.rhs = (A*)c->imp_rhs0;
+    I.dg = (A*)c->imp_diag;
+    I.co = (RkImpSlot<A>*)c->imp_co;
+    I.nint = c->imp_nint;
+    I.clist = c->clist;
+    I.err = c->dev_err;
+    const int cb = (c->Nc + 127) / 128;
+    rk_imp_setup<D, A><<<cb, 128, 0, c->stream>>>(I);
+    c->launches += 1;
+    const int nc = c->ncolor;
+    if (k_macro > 0) {
+        constexpr int NTM = 128;
+        int maxcol = 0;
+        for (int k = 0; k < nc; ++k) maxcol = std::max(maxcol, c->cstart[k + 1] - c->cstart[k]);
+        int dev = 0, nsm = 0, occ = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rk_imp_macro<D, A, NTM>, NTM, 0);
+        if (e != cudaSuccess) return e;
+        const int nblk = std::max(1, std::min(nsm * std::max(occ, 1), (maxcol + NTM - 1) / NTM));
+        e = cudaMemsetAsync(c->imp_bar, 0, sizeof(unsigned), c->stream);
+        if (e != cudaSuccess) return e;
+        int km = k_macro, ncol = nc;
+        const int* cs = c->cstart_d;
+        unsigned* bar = c->imp_bar;
+        void* args[] = {&I, &km, &ncol, &cs, &bar};
+        e = cudaLaunchCooperativeKernel((const void*)rk_imp_macro<D, A, NTM>, dim3(nblk), dim3(NTM), args, 0,
+                                        c->stream);
+        if (e != cudaSuccess) return e;
+        c->launches += 1;
     }
-    c->launches += 2;
+    // ---- microscopic system, Eq. (SGS_phi)
+    P.Wout = Wout;                      // W~
+    P.fout = (T*)fout;                  // holds the residual until the finish
+    double* u0 = c->imp_diag;           // the macroscopic diagonal is no longer needed
+    rk_imp_res<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P, f32 ? (const T*)c->xi_f : (const T*)c->xi_d,
+                                                     f32 ? (const T*)c->w_f : (const T*)c->w_d, u0);
+    c->launches += 1;
+    T* dphi = (T*)c->flux;              // the face flux has been used
+    e = cudaMemsetAsync(dphi, 0, (size_t)c->Nc * NA * c->Nvp * sizeof(T), c->stream);
+    if (e != cudaSuccess) return e;
+    const int nyb = (c->Nvp + 127) / 128;
+    int prev = -1;
+    for (int it = 0; it < k_micro; ++it)
+        for (int dir = 0; dir < 2; ++dir)
+            for (int q = 0; q < nc; ++q) {
+                const int col = dir == 0 ? q : nc - 1 - q;
+                if (col == prev) continue;      // same inputs as the pass before: same values
+                prev = col;
+                const int c0 = c->cstart[col], c1 = c->cstart[col + 1];
+                if (c1 > c0) {
+                    rk_imp_micro<D, T><<<dim3(c1 - c0, nyb), 128, 0, c->stream>>>(
+                        c->Nv, c->Nvp, (const T*)fout, dphi, u0, f32 ? (const T*)c->xi_f : (const T*)c->xi_d,
+                        c->xi_d, c->An_d, f32 ? (const T*)c->An_f : (const T*)c->An_d, c->slot, c->nslot, c->faceL,
+                        c->faceR, c->clist, c0);
+                    c->launches += 1;
+                }
+            }
+    dim3 gf(c->Nc * NA, std::min(8, (c->Nvp + 255) / 256));
+    rk_imp_finish<T><<<gf, 256, 0, c->stream>>>(c->Nv, c->Nvp, (const T*)fin, dphi, (T*)fout);
+    c->launches += 1;
     return cudaGetLastError();
 }
 
@@ -1049,6 +1518,16 @@ cudaError_t rk_launch_step(avs_ctx* c, const void* fin, void* fout, const double
                         : rk_step_t<2, double>(c, fin, fout, Win, Wout, dt);
     return c->mixed ? rk_step_t<3, float>(c, fin, fout, Win, Wout, dt)
                     : rk_step_t<3, double>(c, fin, fout, Win, Wout, dt);
+}
+
+cudaError_t rk_launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout,
+                                    double dt, int k_macro, int k_micro)
+{
+    if (c->D == 2)
+        return c->mixed ? rk_step_implicit_t<2, float>(c, fin, fout, Win, Wout, dt, k_macro, k_micro)
+                        : rk_step_implicit_t<2, double>(c, fin, fout, Win, Wout, dt, k_macro, k_micro);
+    return c->mixed ? rk_step_implicit_t<3, float>(c, fin, fout, Win, Wout, dt, k_macro, k_micro)
+                    : rk_step_implicit_t<3, double>(c, fin, fout, Win, Wout, dt, k_macro, k_micro);
 }
 
 cudaError_t rk_launch_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wout,

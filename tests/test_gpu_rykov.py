@@ -115,13 +115,40 @@ def test_rykov_adapt_topology_remap_and_correction(D):
     g.close()
 
 
-def test_rykov_rejects_what_it_does_not_build():
+def test_rykov_rejects_the_learned_proposer():
     avs = need_gpu()
     w = rykov(CASES["box"]("fp64"))
     with pytest.raises(avs.AVSError):
         avs.AVS(w, learned=True)
-    g = avs.AVS(w)
-    g.init_field(amp=1e-3)
-    with pytest.raises(avs.AVSError):
-        g.step_implicit(1, dt=1e-3)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("cfl", [0.8, 3.0])
+def test_rykov_implicit_fp64_matches_oracle(case, cfl):
+    """IUGKS with the Rykov model: Eqs. (SGS_w), (SGS_wrot), (SGS_phi)."""
+    avs = need_gpu()
+    w = rykov(CASES[case]("fp64"))
+    r, g = pair_rykov(w, avs)
+    dt = r.dt(cfl)
+    for _ in range(2):
+        r.step_implicit(dt)
+    g.step_implicit(2, dt=dt)
+    assert rel_err(g.moments()[0], r.Wc) < 1e-12
+    assert rel_err(g.get_f(), r.f) < 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("case", ["box", "omesh"])
+def test_rykov_implicit_mixed_fields_within_1e5(case):
+    avs = need_gpu()
+    w = rykov(CASES[case]("mixed"))
+    r, g = pair_rykov(w, avs, precision="mixed")
+    dt = r.dt(2.0)
+    for _ in range(3):
+        r.step_implicit(dt)
+    g.step_implicit(3, dt=dt)
+    Wg = g.moments()[0]
+    e = field_err(Wg, r.Wc, w.D)
+    assert max(e.values()) < 1e-5, e
+    assert erot_err(Wg, r.Wc, w.D) < 1e-5
     g.close()
