@@ -61,6 +61,7 @@ struct RkEq {
     T U[3];
     T pt, pr;                 // rho / (2 pi R T_t)^(D/2), rho / (2 pi R T)^(D/2)
     T RTt, RTr, RT;
+    T iRTt, iRT;              // 1 / R T_t, 1 / R T (the FP32 form multiplies by them)
     T at[3], ar[3];           // q_t / (15 p_t R T_t), omega0 q_t / (15 p R T)
     T bt[3], br[3];           // (1 - delta) q_r / (p_t R T_t), omega1 (1 - delta) q_r / (p R T)
     T iz;
@@ -86,6 +87,8 @@ __device__ RkEq<T> rk_make(const RkGas& g, double rho, const double* U, double R
     e.RTt = (T)RTt;
     e.RTr = (T)RTr;
     e.RT = (T)RT;
+    e.iRTt = (T)(1.0 / RTt);
+    e.iRT = (T)(1.0 / RT);
     e.iz = (T)g.iz;
     return e;
 }
@@ -105,15 +108,24 @@ __device__ __forceinline__ void rk_eval(const RkEq<T>& e, const T* x, T* out)
         cbt += c * e.bt[d];
         cbr += c * e.br[d];
     }
-    const T gt = e.pt * ex(-c2 / (T(2) * e.RTt));
-    const T gr = e.pr * ex(-c2 / (T(2) * e.RT));
-    const T Gt = gt * (T(1) + cat * (c2 / e.RTt - T(D + 2)));
-    const T Gr = gr * (T(1) + car * (c2 / e.RT - T(D + 2)));
+    // c^2 / R T: divisions in the FP64 form (as the oracle), reciprocals in FP32
+    T st, sr;
+    if constexpr (sizeof(T) == 4) {
+        st = c2 * e.iRTt;
+        sr = c2 * e.iRT;
+    } else {
+        st = c2 / e.RTt;
+        sr = c2 / e.RT;
+    }
+    const T gt = e.pt * ex(sizeof(T) == 4 ? T(-0.5) * st : -c2 / (T(2) * e.RTt));
+    const T gr = e.pr * ex(sizeof(T) == 4 ? T(-0.5) * sr : -c2 / (T(2) * e.RT));
+    const T Gt = gt * (T(1) + cat * (st - T(D + 2)));
+    const T Gr = gr * (T(1) + car * (sr - T(D + 2)));
     const T a = T(1) - e.iz;
     out[0] = a * Gt + e.iz * Gr;
     if (D == 2) {
-        const T Ht = e.RTt * gt * (T(1) + cat * (c2 / e.RTt - T(D)));
-        const T Hr = e.RT * gr * (T(1) + car * (c2 / e.RT - T(D)));
+        const T Ht = e.RTt * gt * (T(1) + cat * (st - T(D)));
+        const T Hr = e.RT * gr * (T(1) + car * (sr - T(D)));
         out[1] = a * Ht + e.iz * Hr;
     }
     const T Rt = e.RTr * (Gt + cbt * gt);
@@ -841,8 +853,8 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
         for (int c = 0; c < NW; ++c) P.Wout[(size_t)i * NW + c] = Wt[c];
     }
     __syncthreads();
-    const T dt = (T)P.dt, tau = (T)tau_s, Vc = (T)P.vol[i];
-    const T den = T(1) / dt + T(1) / tau;
+    const T idt = (T)(1.0 / P.dt), itau = (T)(1.0 / tau_s), iV = (T)(1.0 / P.vol[i]);
+    const T iden = (T)(1.0 / (1.0 / P.dt + 1.0 / tau_s));
     T* fo = P.fout + (size_t)i * cs;
     for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
         if (k >= Nv) {
@@ -859,7 +871,7 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
         for (int a = 0; a < NA; ++a) {
             T N = T(0);
             for (int q = 0; q < ns; ++q) N += sg[q] * P.FX[((size_t)fs[q] * NA + a) * Nvp + k];
-            fo[(size_t)a * Nvp + k] = (fi[(size_t)a * Nvp + k] / dt + gv[a] / tau - N / Vc) / den;
+            fo[(size_t)a * Nvp + k] = (fi[(size_t)a * Nvp + k] * idt + gv[a] * itau - N * iV) * iden;
         }
     }
 }
