@@ -75,6 +75,8 @@ WORKLOADS = {
     "cylinder-zones": ("cylinder_zones", dict()),
     # the cylinder with a diatomic gas (Rykov model: G, H, R; no learned proposer)
     "cylinder-rykov": ("cylinder", dict(model="rykov")),
+    # the same on the inner 64 radial rows (profiling case)
+    "cylinder-rykov-r64": ("cylinder", dict(n_r=64, model="rykov")),
 }
 _WL = "cylinder"
 
@@ -213,6 +215,7 @@ ORACLE_SAMPLES = {
     "sphere": ("sphere", dict(n_r=2, learned=False), "the first 2 radial shells (4608 cells)"),
     "cylinder-zones": ("cylinder_zones", dict(), "the whole 128 x 96 O-mesh (12288 cells)"),
     "cylinder-rykov": ("cylinder", dict(n_r=12, model="rykov"), "the first 12 radial rows (1152 cells)"),
+    "cylinder-rykov-r64": ("cylinder", dict(n_r=12, model="rykov"), "the first 12 radial rows (1152 cells)"),
 }
 
 
