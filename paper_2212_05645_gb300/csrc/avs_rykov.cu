@@ -599,6 +599,88 @@ __device__ void rk_from_raw(const double* m, const double* V, double* W, double*
     }
 }
 
+// FP32 state of the raw moments about V (the mixed form's per-face and
+// per-cell parameters; FP64 is 70x scarcer than FP32 on GB300): rho, U, the
+// translational internal energy (with H) e_t = (sum w (c'^2 G + H))/2 about
+// U, the rotational energy r0 and the heat fluxes, all from the centred
+// sums, so that no bulk kinetic energy cancels.
+template <int D>
+__device__ void rk_state_raw32(const double* md, const double* V, float& rho, float* U, float& et, float& r0,
+                               float* qt, float* qr)
+{
+    constexpr int NR = RkNR<D>::v;
+    float m[NR];
+    for (int q = 0; q < NR; ++q) m[q] = (float)md[q];
+    int o = 0;
+    const float m0 = m[o++];
+    float m1[3] = {0, 0, 0}, m2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, m3[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) m1[d] = m[o++];
+    for (int d = 0; d < D; ++d)
+        for (int e = d; e < D; ++e) m2[d][e] = m2[e][d] = m[o++];
+    for (int d = 0; d < D; ++d) m3[d] = m[o++];
+    float h0 = 0.0f, h1[3] = {0, 0, 0};
+    if (D == 2) {
+        h0 = m[o++];
+        for (int d = 0; d < D; ++d) h1[d] = m[o++];
+    }
+    r0 = m[o++];
+    float r1[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) r1[d] = m[o++];
+    rho = m0;
+    const float ir = 1.0f / m0;
+    float dl[3] = {0, 0, 0}, d2 = 0.0f, tr = 0.0f, dm = 0.0f;
+    for (int d = 0; d < D; ++d) {
+        dl[d] = m1[d] * ir;
+        U[d] = (float)V[d] + dl[d];
+        d2 += dl[d] * dl[d];
+        tr += m2[d][d];
+        dm += dl[d] * m1[d];
+    }
+    et = 0.5f * (tr + h0 - m0 * d2);
+    for (int i = 0; i < D; ++i) {
+        float s = m3[i] + d2 * m1[i] - dl[i] * tr + 2.0f * dl[i] * dm - dl[i] * d2 * m0;
+        for (int j = 0; j < D; ++j) s -= 2.0f * dl[j] * m2[i][j];
+        qt[i] = 0.5f * (s + (h1[i] - dl[i] * h0));
+        qr[i] = r1[i] - dl[i] * r0;
+    }
+}
+
+// RkEq<float> of a state given in FP32, without FP64 arithmetic.
+template <int D>
+__device__ RkEq<float> rk_make32(const RkGas& g, float rho, const float* U, float RTt, float RTr, const float* qt,
+                                 const float* qr)
+{
+    RkEq<float> e;
+    const float RT = (3.0f * RTt + 2.0f * RTr) * 0.2f;
+    const float pt = rho * RTt, p = rho * RT;
+    const float om0 = (float)g.om0, om1 = (float)g.om1, dl = (float)g.dl;
+    for (int d = 0; d < 3; ++d) {
+        const bool on = d < D;
+        e.U[d] = on ? U[d] : 0.0f;
+        e.at[d] = on ? qt[d] / (15.0f * pt * RTt) : 0.0f;
+        e.ar[d] = on ? om0 * qt[d] / (15.0f * p * RT) : 0.0f;
+        e.bt[d] = on ? (1.0f - dl) * qr[d] / (pt * RTt) : 0.0f;
+        e.br[d] = on ? om1 * (1.0f - dl) * qr[d] / (p * RT) : 0.0f;
+    }
+    const float xt = 2.0f * (float)AVS_PI * RTt, xr = 2.0f * (float)AVS_PI * RT;
+    e.pt = D == 2 ? rho / xt : rho / (xt * sqrtf(xt));
+    e.pr = D == 2 ? rho / xr : rho / (xr * sqrtf(xr));
+    e.RTt = RTt;
+    e.RTr = RTr;
+    e.RT = RT;
+    e.iRTt = 1.0f / RTt;
+    e.iRT = 1.0f / RT;
+    e.iz = (float)g.iz;
+    return e;
+}
+
+// tau = mu(T_t) / p_t in FP32
+__device__ __forceinline__ float rk_tau32(const RkGas& g, float rho, float RTt)
+{
+    const float T = RTt / (float)g.R;
+    return (float)g.mu_ref * powa(T / (float)g.T_ref, (float)g.omega) / (rho * RTt);
+}
+
 // Upwind side of a node: xi . A n >= 0 decided in FP32 when the FP32 sum is
 // farther from zero than its rounding bound, else in FP64 without
 // contraction, so the decision always equals the FP64 one.
@@ -712,26 +794,25 @@ __global__ void __launch_bounds__(RK_NT) rk_face32(RkP<float> P, const float* __
     if (R >= 0) {
         block_sum_t<NR, RK_NT>(racc, sw, sout);
         if (threadIdx.x == 0) {
-            double m[NR], W[NW], qb[3] = {0, 0, 0}, qrb[3] = {0, 0, 0};
-            for (int q = 0; q < NR; ++q) m[q] = sout[q];
-            rk_from_raw<D>(m, Vd, W, qb, qrb);
-            double rho, Uu[3], RTt, RTr, RT;
-            rk_prim<D>(W, rho, Uu, RTt, RTr, RT);
-            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
-            const double tau = rk_tau(P.g, rho, RTt);
-            const double az = P.h / (P.g.Z * tau);
-            RTr = (W[D + 2] + az * rho * RT) / (1.0 + az) / rho;
-            RTt = (5.0 * RT - 2.0 * RTr) / 3.0;
-            const double lt = 2.0 / 3.0 + (1.0 - P.g.om0) / (3.0 * P.g.Z);
-            const double lr = 1.0 - (1.0 - P.g.dl) * ((1.0 - 1.0 / P.g.Z) * RTr / RTt + P.g.om1 / P.g.Z);
-            double qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+            // the interface state in FP32 (as the monatomic mixed form): no FP64 pow or division here
+            float rho, Uu[3] = {0, 0, 0}, et, r0, qb[3] = {0, 0, 0}, qrb[3] = {0, 0, 0};
+            rk_state_raw32<D>(sout, Vd, rho, Uu, et, r0, qb, qrb);
+            float RTt = et / (1.5f * rho), RT = (et + r0) / (2.5f * rho);
+            if (!(rho > 0.0f) || !(RTt > 0.0f) || !(RT > 0.0f)) atomicOr(P.err, 1);
+            const float tau = rk_tau32(P.g, rho, RTt), hf = (float)P.h, Z = (float)P.g.Z;
+            const float az = hf / (Z * tau);
+            const float RTr = (r0 + az * rho * RT) / (1.0f + az) / rho;
+            RTt = (5.0f * RT - 2.0f * RTr) * (1.0f / 3.0f);
+            const float lt = 2.0f / 3.0f + (1.0f - (float)P.g.om0) / (3.0f * Z);
+            const float lr = 1.0f - (1.0f - (float)P.g.dl) * ((1.0f - 1.0f / Z) * RTr / RTt + (float)P.g.om1 / Z);
+            float qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
             for (int d = 0; d < D; ++d) {
-                qt[d] = tau * qb[d] / (tau + P.h * lt);
-                qr[d] = tau * qrb[d] / (tau + P.h * lr);
+                qt[d] = tau * qb[d] / (tau + hf * lt);
+                qr[d] = tau * qrb[d] / (tau + hf * lr);
             }
-            eq = rk_make<D, T>(P.g, rho, Uu, RTt, RTr, qt, qr);
-            blend[0] = tau / (tau + P.h);
-            blend[1] = P.h / (tau + P.h);
+            eq = rk_make32<D>(P.g, rho, Uu, RTt, RTr, qt, qr);
+            blend[0] = tau / (tau + hf);
+            blend[1] = hf / (tau + hf);
         }
     } else {
         block_sum_t<2, RK_NT>(wacc, sw, sout);
@@ -828,10 +909,10 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
     }
     block_sum_t<NR, RK_NT>(racc, sw, sout);
     if (threadIdx.x == 0) {
-        double m[NR], Wn[NW], qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
-        for (int q = 0; q < NR; ++q) m[q] = sout[q];
-        rk_from_raw<D>(m, Vd, Wn, qt, qr);
-        const double Vol = P.vol[i];
+        // heat fluxes of f^n and tau, eq in FP32; the carried W^{n+1} in FP64
+        float rn, Un[3] = {0, 0, 0}, etn, r0n, qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+        rk_state_raw32<D>(sout, Vd, rn, Un, etn, r0n, qt, qr);
+        const double dtV = P.dt / P.vol[i];
         double Wt[NW];
         for (int c = 0; c < NW; ++c) {
             double s = 0.0;
@@ -839,22 +920,30 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
                 const double a = P.AF[(size_t)fs[q] * NW + c];
                 s += sg[q] > T(0) ? a : -a;
             }
-            Wt[c] = Wi[c] - P.dt / Vol * s;
+            Wt[c] = Wi[c] - dtV * s;
         }
-        double rho, U[3], RTt, RTr, RT;
-        rk_prim<D>(Wt, rho, U, RTt, RTr, RT);
+        const double rho = Wt[0], ir = 1.0 / rho;
+        double m2 = 0.0;
+        float U[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) {
+            m2 += Wt[1 + d] * Wt[1 + d];
+            U[d] = (float)(Wt[1 + d] * ir);
+        }
+        const double ein = Wt[D + 1] - 0.5 * m2 * ir;  // rho e, translational + rotational
+        const double RT = ein * ir * 0.4, RTt = (ein - Wt[D + 2]) * ir * (1.0 / 1.5);
         if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
-        const double tau = rk_tau(P.g, rho, RTt);
-        const double az = P.dt / (P.g.Z * tau);
+        const float tau = rk_tau32(P.g, (float)rho, (float)RTt);
+        const double az = P.dt / (P.g.Z * (double)tau);
         Wt[D + 2] = (Wt[D + 2] + az * rho * RT) / (1.0 + az);
-        rk_prim<D>(Wt, rho, U, RTt, RTr, RT);
-        eq = rk_make<D, T>(P.g, rho, U, RTt, RTr, qt, qr);
+        const double RTr = Wt[D + 2] * ir;
+        eq = rk_make32<D>(P.g, (float)rho, U, (float)((5.0 * RT - 2.0 * RTr) * (1.0 / 3.0)), (float)RTr, qt, qr);
         tau_s = tau;
         for (int c = 0; c < NW; ++c) P.Wout[(size_t)i * NW + c] = Wt[c];
     }
     __syncthreads();
-    const T idt = (T)(1.0 / P.dt), itau = (T)(1.0 / tau_s), iV = (T)(1.0 / P.vol[i]);
-    const T iden = (T)(1.0 / (1.0 / P.dt + 1.0 / tau_s));
+    const float tf = (float)tau_s, dtf = (float)P.dt;
+    const T idt = 1.0f / dtf, itau = 1.0f / tf, iV = (T)(1.0 / P.vol[i]);
+    const T iden = dtf * tf / (dtf + tf);
     T* fo = P.fout + (size_t)i * cs;
     for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
         if (k >= Nv) {
