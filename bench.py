@@ -362,11 +362,11 @@ def run_gpu(args):
                if _WL in ("cylinder", "cylinder-r64") and args.implicit <= 0 else None)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
-            "kernel": (f"implicit Rykov UGKS step: rk_grad + rk_face + rk_imp_setup + rk_imp_macro + rk_imp_res"
+            "kernel": (f"implicit Rykov UGKS step: k_grad + rk_face + rk_imp_setup + rk_imp_macro + rk_imp_res"
                        f" + rk_imp_micro + rk_imp_finish <{w.D},float>" if args.implicit > 0 and w.model == "rykov" else
                        f"implicit UGKS step: k_grad + k_face + k_imp_setup + k_imp_macro + k_imp_state + k_imp_res"
                        f" + k_imp_micro + k_imp_finish <{w.D},float>" if args.implicit > 0 else
-                       f"Rykov UGKS step: rk_grad + rk_face + rk_cell <{w.D},float>" if w.model == "rykov" else
+                       f"Rykov UGKS step: k_grad + rk_face + rk_cell <{w.D},float>" if w.model == "rykov" else
                        f"UGKS step: k_grad + k_face + k_cell_state + k_cell <{w.D},float>"),
             "peak_source": peak_kind,
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,

@@ -134,6 +134,8 @@ int round_up(int n, int m);
 // ---- launchers (avs_step.cu)
 cudaError_t launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
 // Rykov model (csrc/avs_rykov.cu)
+// limited gradients of the Rykov arrays (3 in 2D, 2 in 3D) into c->grad
+void launch_grad_rykov(avs_ctx* c, const void* fin);
 cudaError_t rk_launch_step(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt);
 cudaError_t rk_launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout,
                                     double dt, int k_macro, int k_micro);

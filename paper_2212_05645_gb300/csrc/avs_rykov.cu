@@ -220,52 +220,6 @@ struct RkP {
     int* err;
 };
 
-// Limited least-squares gradient of every cell, array and node (Sec. 2.3.3,
-// reading R6), one thread per node.
-template <int D, typename T>
-__global__ void __launch_bounds__(256) rk_grad(int Nv, int Nvp, int limiter, const T* __restrict__ f, T* G,
-                                               const unsigned char* __restrict__ nslot, const int* __restrict__ nbr,
-                                               const T* __restrict__ cg, const T* __restrict__ r,
-                                               const T* __restrict__ eps2)
-{
-    constexpr int NA = RkNA<D>::v;
-    const int i = blockIdx.x, k = blockIdx.y * blockDim.x + threadIdx.x;
-    if (k >= Nv) return;
-    const int ns = nslot[i];
-    const size_t cs = (size_t)NA * Nvp;
-    const T e2 = eps2[i];
-    for (int a = 0; a < NA; ++a) {
-        const T phi = f[(size_t)i * cs + (size_t)a * Nvp + k];
-        T g[D], dmax = T(0), dmin = T(0);
-#pragma unroll
-        for (int d = 0; d < D; ++d) g[d] = T(0);
-        for (int s = 0; s < ns; ++s) {
-            const int nb = nbr[i * AVS_MAXS + s];
-            if (nb < 0) continue;
-            const T dd = f[(size_t)nb * cs + (size_t)a * Nvp + k] - phi;
-#pragma unroll
-            for (int d = 0; d < D; ++d) g[d] += cg[(size_t)(i * AVS_MAXS + s) * D + d] * dd;
-            dmax = dd > dmax ? dd : dmax;
-            dmin = dd < dmin ? dd : dmin;
-        }
-        T L = T(1);
-        if (limiter == 1) {
-            T p = T(0), n = T(0);
-            for (int s = 0; s < ns; ++s) {
-                T d2 = T(0);
-#pragma unroll
-                for (int d = 0; d < D; ++d) d2 += g[d] * r[(size_t)(i * AVS_MAXS + s) * D + d];
-                p = d2 > p ? d2 : p;
-                n = d2 < n ? d2 : n;
-            }
-            if (p > T(0)) { const T t = venkat(dmax, p, e2); L = t < L ? t : L; }
-            if (n < T(0)) { const T t = venkat(dmin, n, e2); L = t < L ? t : L; }
-        }
-#pragma unroll
-        for (int d = 0; d < D; ++d) G[(((size_t)i * NA + a) * D + d) * Nvp + k] = L * g[d];
-    }
-}
-
 // One face: foot values from the upwind cell, the Rykov interface state
 // (reading R27) and phi_ij = tau/(tau+h) phi_bar + h/(tau+h) g (Eq. equ28);
 // boundary faces as in R8/R29.  Writes the per-node face flux and A F.
@@ -736,15 +690,20 @@ __global__ void __launch_bounds__(RK_NT) rk_face32(RkP<float> P, const float* __
         RTb = P.g.R * B[5];
     }
     const T h = (T)P.h;
+    // reference velocity of the sums: the left cell's mean velocity in FP32
+    // (any V gives the same moments; Vd is its exact FP64 value)
     T V[D], Ubf[D];
     double Vd[3] = {0, 0, 0};
     const double* WL = P.Win + (size_t)L * NW;
+    const T irL = 1.0f / (T)WL[0];
     for (int d = 0; d < D; ++d) {
-        V[d] = (T)(WL[1 + d] / WL[0]);
+        V[d] = (T)WL[1 + d] * irL;
         Vd[d] = (double)V[d];
         Ubf[d] = (T)Ub[d];
     }
-    const T pw = (T)(1.0 / pow(2.0 * AVS_PI * RTb, 0.5 * D)), i2b = (T)(1.0 / (2.0 * RTb));
+    // wall Maxwellian prefactor (2 pi RT_w)^(-D/2) and 1/(2 RT_w) in FP32
+    const T xb = 2.0f * (T)AVS_PI * (T)RTb;
+    const T pw = D == 2 ? 1.0f / xb : 1.0f / (xb * sqrtf(xb)), i2b = 0.5f / (T)RTb;
     T racc[NR], wacc[2] = {T(0), T(0)};
 #pragma unroll
     for (int m = 0; m < NR; ++m) racc[m] = T(0);
@@ -893,8 +852,9 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
     const double* Wi = P.Win + (size_t)i * NW;
     T V[D];
     double Vd[3] = {0, 0, 0};
+    const T irW = T(1) / (T)Wi[0];
     for (int d = 0; d < D; ++d) {
-        V[d] = (T)(Wi[1 + d] / Wi[0]);
+        V[d] = (T)Wi[1 + d] * irW;
         Vd[d] = (double)V[d];
     }
     T racc[NR];
@@ -942,7 +902,7 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
     }
     __syncthreads();
     const float tf = (float)tau_s, dtf = (float)P.dt;
-    const T idt = 1.0f / dtf, itau = 1.0f / tf, iV = (T)(1.0 / P.vol[i]);
+    const T idt = 1.0f / dtf, itau = 1.0f / tf, iV = 1.0f / (T)P.vol[i];
     const T iden = dtf * tf / (dtf + tf);
     T* fo = P.fout + (size_t)i * cs;
     for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
@@ -1293,8 +1253,9 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
         const double* Wi = P.Win + (size_t)i * NW;
         T V[D];
         double Vd[3] = {0, 0, 0};
+        const T irW = T(1) / (T)Wi[0];
         for (int d = 0; d < D; ++d) {
-            V[d] = (T)(Wi[1 + d] / Wi[0]);
+            V[d] = (T)Wi[1 + d] * irW;
             Vd[d] = (double)V[d];
         }
         T racc[NR];
@@ -1486,14 +1447,7 @@ cudaError_t rk_face_stage(avs_ctx* c, const void* fin, const double* Win, double
     P.Wout = nullptr;
     P.fout = nullptr;
     P.err = c->dev_err;
-    if (grad) {
-        dim3 g(c->Nc, (c->Nv + 255) / 256);
-        rk_grad<D, T><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin, (T*)c->grad, c->nslot,
-                                                c->nbr, f32 ? (const T*)c->cg_f : (const T*)c->cg_d,
-                                                f32 ? (const T*)c->r_f : (const T*)c->r_d,
-                                                f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d);
-        c->launches += 1;
-    }
+    if (grad) launch_grad_rykov(c, fin);     // the monatomic gradient kernel over NA arrays
     if constexpr (sizeof(T) == 4)
         rk_face32<D><<<c->Nf, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f, c->An_f, c->rL_f, c->rR_f);
     else

@@ -108,11 +108,11 @@ __device__ __forceinline__ void stvn(T* p, const T* o)
 // thread handles VG consecutive nodes (rows are padded to 32 nodes, so the
 // vector stays inside the row) to keep more loads in flight.  NS: face slots
 // unrolled (4 when every cell of a 2D mesh has at most 4 faces, else 6).
-template <int D, typename T, int VG, int NS>
+// NA: arrays per cell (2 or 1 for the monatomic gas, 3 or 2 for the Rykov model).
+template <int D, typename T, int VG, int NS, int NA>
 __global__ void __launch_bounds__(256) k_grad(int Nv, int Nvp, int limiter, const T* __restrict__ f,
                                               T* __restrict__ G, CellGeo<T> geo)
 {
-    constexpr int NA = NArr<D>::v;
     static_assert((VG * sizeof(T)) % 16 == 0, "whole 16-byte vectors per thread");
     const int i = blockIdx.x;
     const int k0 = (blockIdx.y * blockDim.x + threadIdx.x) * VG;
@@ -875,6 +875,27 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 7 : 7) : 4) 
     if (tid < NM) P.mom[(size_t)i * NM + tid] = red[tid];
 }
 
+// Limited gradients of every array of every cell into c->grad (allocated by the caller).
+template <int D, typename T, int NA>
+static void grad_t(avs_ctx* c, const void* fin)
+{
+    const bool f32 = sizeof(T) == 4;
+    CellGeo<T> geo;
+    geo.nbr = c->nbr;
+    geo.cg = f32 ? (const T*)c->cg_f : (const T*)c->cg_d;
+    geo.r = f32 ? (const T*)c->r_f : (const T*)c->r_d;
+    geo.eps2 = f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d;
+    geo.ns = c->nslot;
+    constexpr int VG = 4;
+    dim3 g(c->Nc, (c->Nv + 256 * VG - 1) / (256 * VG));
+    if (D == 2 && c->max_ns <= 4)
+        k_grad<D, T, VG, 4, NA><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin, (T*)c->grad, geo);
+    else
+        k_grad<D, T, VG, AVS_MAXS, NA><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin,
+                                                                  (T*)c->grad, geo);
+    c->launches += 1;
+}
+
 // Limited gradients and the face stage of a step: per-node face flux in
 // c->flux, area-weighted face flux of W in c->AFf (shared by the explicit and
 // the implicit step).
@@ -909,22 +930,7 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
             c->flux_bytes = need;
         }
     }
-    if (grad) {
-        CellGeo<T> geo;
-        geo.nbr = c->nbr;
-        geo.cg = f32 ? (const T*)c->cg_f : (const T*)c->cg_d;
-        geo.r = f32 ? (const T*)c->r_f : (const T*)c->r_d;
-        geo.eps2 = f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d;
-        geo.ns = c->nslot;
-        constexpr int VG = 4;
-        dim3 g(c->Nc, (c->Nv + 256 * VG - 1) / (256 * VG));
-        if (D == 2 && c->max_ns <= 4)
-            k_grad<D, T, VG, 4><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin, (T*)c->grad, geo);
-        else
-            k_grad<D, T, VG, AVS_MAXS><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin,
-                                                                  (T*)c->grad, geo);
-        c->launches += 1;
-    }
+    if (grad) grad_t<D, T, NArr<D>::v>(c, fin);
     const T* xi = f32 ? (const T*)c->xi_f : (const T*)c->xi_d;
     const T* w = f32 ? (const T*)c->w_f : (const T*)c->w_d;
     FaceP<D, T> P;
@@ -1554,6 +1560,17 @@ cudaError_t launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const 
                         : launch_step_implicit_t<2, double>(c, fin, fout, Win, Wout, dt, k_macro, k_micro);
     return c->mixed ? launch_step_implicit_t<3, float>(c, fin, fout, Win, Wout, dt, k_macro, k_micro)
                     : launch_step_implicit_t<3, double>(c, fin, fout, Win, Wout, dt, k_macro, k_micro);
+}
+
+void launch_grad_rykov(avs_ctx* c, const void* fin)
+{
+    if (c->D == 2) {
+        if (c->mixed) grad_t<2, float, 3>(c, fin);
+        else grad_t<2, double, 3>(c, fin);
+    } else {
+        if (c->mixed) grad_t<3, float, 2>(c, fin);
+        else grad_t<3, double, 2>(c, fin);
+    }
 }
 
 cudaError_t launch_face_stage(avs_ctx* c, const void* fin, const double* Win, double dt)
