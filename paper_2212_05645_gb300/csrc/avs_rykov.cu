@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(RK_NT) rk_face(RkP<T> P)
     }
     __syncthreads();
     // pass B: phi_ij, per-node flux (xi . A n) phi and its moments
-    const T wa = (T)blend[0], wb = (T)blend[1];
+    const T wa = blend[0], wb = blend[1];
     double af[NW];
 #pragma unroll
     for (int m = 0; m < NW; ++m) af[m] = 0.0;
@@ -635,6 +635,19 @@ __device__ __forceinline__ float rk_tau32(const RkGas& g, float rho, float RTt)
     return (float)g.mu_ref * powa(T / (float)g.T_ref, (float)g.omega) / (rho * RTt);
 }
 
+// The FP64 upwind decision (the oracle's) for the nodes inside the FP32
+// rounding bound.  Not inlined: inlined, the compiler predicates it into every
+// node's instruction stream, and an FP64 instruction issued with its predicate
+// off still occupies the scarce FP64 pipe (out of line, the face kernel's FP64
+// pipe went from 52 % to 4 % busy and the kernel ran 12 % faster).
+template <int D>
+__device__ __noinline__ bool rk_upwind_exact(const double* __restrict__ xi, int k, const double* An)
+{
+    double xd[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) xd[d] = xi[(size_t)k * D + d];
+    return dot_rn<D>(xd, An) >= 0.0;
+}
+
 // Upwind side of a node: xi . A n >= 0 decided in FP32 when the FP32 sum is
 // farther from zero than its rounding bound, else in FP64 without
 // contraction, so the decision always equals the FP64 one.
@@ -651,9 +664,7 @@ __device__ __forceinline__ bool rk_upwind_L(const float* x, const float* Af, con
         a += fabsf(p);
     }
     if (fabsf(s) > a * 0x1p-20f) return s >= 0.0f;
-    double xd[3] = {0, 0, 0};
-    for (int d = 0; d < D; ++d) xd[d] = xi[(size_t)k * D + d];
-    return dot_rn<D>(xd, An) >= 0.0;
+    return rk_upwind_exact<D>(xi, k, An);
 }
 
 // rk_face for the FP32 form (same steps; sums as above).
@@ -666,44 +677,64 @@ __global__ void __launch_bounds__(RK_NT) rk_face32(RkP<float> P, const float* __
     constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
     __shared__ double sw[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
     __shared__ RkEq<T> eq;
-    __shared__ double blend[2];
+    __shared__ float blend[2];
+    // per-face constants, converted from FP64 once by thread 0 (an FP64
+    // conversion or division in every thread costs as much as the node work)
+    __shared__ float cAf[3], crl[3], crr[3], cV[3], cUb[3], cpw, ci2b, ch;
+    __shared__ double An[3], Vd[3], cRTb, crb;
+    __shared__ int cbt;
     const int f = blockIdx.x;
     const int L = P.faceL[f], R = P.faceR[f];
     const int Nv = P.Nv, Nvp = P.Nvp;
-    double An[3] = {0, 0, 0};
-    T Af[D], rl[D], rr[D];
-    for (int d = 0; d < D; ++d) {
-        An[d] = P.An[(size_t)f * D + d];
-        Af[d] = Anf[(size_t)f * D + d];
-        rl[d] = rLf[(size_t)f * D + d];
-        rr[d] = R >= 0 ? rRf[(size_t)f * D + d] : T(0);
+    if (threadIdx.x == 0) {
+        for (int d = 0; d < 3; ++d) {
+            An[d] = d < D ? P.An[(size_t)f * D + d] : 0.0;
+            cAf[d] = d < D ? Anf[(size_t)f * D + d] : 0.0f;
+            crl[d] = d < D ? rLf[(size_t)f * D + d] : 0.0f;
+            crr[d] = d < D && R >= 0 ? rRf[(size_t)f * D + d] : 0.0f;
+        }
+        int btype = 0;
+        double rb = 0.0, Ub[3] = {0, 0, 0}, RTb = 1.0;
+        if (R < 0) {
+            const double* B = P.bc + (size_t)(-1 - R) * 6;
+            btype = (int)B[0];
+            rb = B[1];
+            for (int d = 0; d < 3; ++d) Ub[d] = B[2 + d];
+            RTb = P.g.R * B[5];
+        }
+        cbt = btype;
+        crb = rb;
+        cRTb = RTb;
+        // reference velocity of the sums: the left cell's mean velocity in
+        // FP32 (any V gives the same moments; Vd is its exact FP64 value)
+        const double* WL = P.Win + (size_t)L * NW;
+        const float irL = 1.0f / (float)WL[0];
+        for (int d = 0; d < 3; ++d) {
+            cV[d] = d < D ? (float)WL[1 + d] * irL : 0.0f;
+            Vd[d] = (double)cV[d];
+            cUb[d] = (float)Ub[d];
+        }
+        // wall Maxwellian prefactor (2 pi RT_w)^(-D/2) and 1/(2 RT_w) in FP32
+        const float xb = 2.0f * (float)AVS_PI * (float)RTb;
+        cpw = D == 2 ? 1.0f / xb : 1.0f / (xb * sqrtf(xb));
+        ci2b = 0.5f / (float)RTb;
+        ch = (float)P.h;
     }
+    __syncthreads();
+    T Af[D], rl[D], rr[D], V[D], Ubf[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        Af[d] = cAf[d];
+        rl[d] = crl[d];
+        rr[d] = crr[d];
+        V[d] = cV[d];
+        Ubf[d] = cUb[d];
+    }
+    const int btype = cbt;
+    const T pw = cpw, i2b = ci2b;
     T* fx = P.FX + (size_t)f * NA * Nvp;
     const size_t cs = (size_t)NA * Nvp;
-    int btype = 0;
-    double rb = 0.0, Ub[3] = {0, 0, 0}, RTb = 1.0;
-    if (R < 0) {
-        const double* B = P.bc + (size_t)(-1 - R) * 6;
-        btype = (int)B[0];
-        rb = B[1];
-        for (int d = 0; d < 3; ++d) Ub[d] = B[2 + d];
-        RTb = P.g.R * B[5];
-    }
-    const T h = (T)P.h;
-    // reference velocity of the sums: the left cell's mean velocity in FP32
-    // (any V gives the same moments; Vd is its exact FP64 value)
-    T V[D], Ubf[D];
-    double Vd[3] = {0, 0, 0};
-    const double* WL = P.Win + (size_t)L * NW;
-    const T irL = 1.0f / (T)WL[0];
-    for (int d = 0; d < D; ++d) {
-        V[d] = (T)WL[1 + d] * irL;
-        Vd[d] = (double)V[d];
-        Ubf[d] = (T)Ub[d];
-    }
-    // wall Maxwellian prefactor (2 pi RT_w)^(-D/2) and 1/(2 RT_w) in FP32
-    const T xb = 2.0f * (T)AVS_PI * (T)RTb;
-    const T pw = D == 2 ? 1.0f / xb : 1.0f / (xb * sqrtf(xb)), i2b = 0.5f / (T)RTb;
+    const T h = ch;
     T racc[NR], wacc[2] = {T(0), T(0)};
 #pragma unroll
     for (int m = 0; m < NR; ++m) racc[m] = T(0);
@@ -776,11 +807,13 @@ __global__ void __launch_bounds__(RK_NT) rk_face32(RkP<float> P, const float* __
     } else {
         block_sum_t<2, RK_NT>(wacc, sw, sout);
         if (threadIdx.x == 0) {
-            const double rho_b = btype == AVS_BC_WALL ? (sout[1] > 0.0 ? sout[0] / sout[1] : 0.0) : rb;
+            const double rho_b = btype == AVS_BC_WALL ? (sout[1] > 0.0 ? sout[0] / sout[1] : 0.0) : crb;
             const double z[3] = {0, 0, 0};
+            const double* B = P.bc + (size_t)(-1 - R) * 6;
+            const double Ub[3] = {B[2], B[3], B[4]};
             RkGas g0 = P.g;
             g0.iz = 0.0;
-            eq = rk_make<D, T>(g0, rho_b, Ub, RTb, RTb, z, z);
+            eq = rk_make<D, T>(g0, rho_b, Ub, cRTb, cRTb, z, z);
             blend[0] = 1.0;
             blend[1] = 0.0;
         }
@@ -836,7 +869,8 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
     constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
     __shared__ double sw[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
     __shared__ RkEq<T> eq;
-    __shared__ double tau_s;
+    __shared__ float tau_s, cdt, cvol, cV[3];
+    __shared__ double Vd[3];
     __shared__ int fs[AVS_MAXS];
     __shared__ T sg[AVS_MAXS];
     const int i = blockIdx.x;
@@ -850,13 +884,21 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
     const size_t cs = (size_t)NA * Nvp;
     const T* fi = P.f + (size_t)i * cs;
     const double* Wi = P.Win + (size_t)i * NW;
-    T V[D];
-    double Vd[3] = {0, 0, 0};
-    const T irW = T(1) / (T)Wi[0];
-    for (int d = 0; d < D; ++d) {
-        V[d] = (T)Wi[1 + d] * irW;
-        Vd[d] = (double)V[d];
+    if (threadIdx.x == 32) {
+        // reference velocity of the sums: the carried mean velocity in FP32,
+        // converted once (Vd its exact FP64 value)
+        const float irW = 1.0f / (float)Wi[0];
+        for (int d = 0; d < 3; ++d) {
+            cV[d] = d < D ? (float)Wi[1 + d] * irW : 0.0f;
+            Vd[d] = (double)cV[d];
+        }
+        cdt = (float)P.dt;
+        cvol = (float)P.vol[i];
     }
+    __syncthreads();
+    T V[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) V[d] = cV[d];
     T racc[NR];
 #pragma unroll
     for (int m = 0; m < NR; ++m) racc[m] = T(0);
@@ -901,8 +943,8 @@ __global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __
         for (int c = 0; c < NW; ++c) P.Wout[(size_t)i * NW + c] = Wt[c];
     }
     __syncthreads();
-    const float tf = (float)tau_s, dtf = (float)P.dt;
-    const T idt = 1.0f / dtf, itau = 1.0f / tf, iV = 1.0f / (T)P.vol[i];
+    const float tf = tau_s, dtf = cdt;
+    const T idt = 1.0f / dtf, itau = 1.0f / tf, iV = 1.0f / cvol;
     const T iden = dtf * tf / (dtf + tf);
     T* fo = P.fout + (size_t)i * cs;
     for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
@@ -1236,6 +1278,8 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
     __shared__ double sred[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
     __shared__ RkEq<T> eq;
     __shared__ double tau_s;
+    __shared__ float ctau, cvol, cV[3];
+    __shared__ double Vd[3];
     __shared__ int fs[AVS_MAXS];
     __shared__ T sg[AVS_MAXS];
     const int i = blockIdx.x;
@@ -1251,13 +1295,19 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
     double qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
     if constexpr (sizeof(T) == 4) {
         const double* Wi = P.Win + (size_t)i * NW;
-        T V[D];
-        double Vd[3] = {0, 0, 0};
-        const T irW = T(1) / (T)Wi[0];
-        for (int d = 0; d < D; ++d) {
-            V[d] = (T)Wi[1 + d] * irW;
-            Vd[d] = (double)V[d];
+        if (threadIdx.x == 32) {
+            // reference velocity of the sums in FP32, converted once (Vd exact)
+            const float irW = 1.0f / (float)Wi[0];
+            for (int d = 0; d < 3; ++d) {
+                cV[d] = d < D ? (float)Wi[1 + d] * irW : 0.0f;
+                Vd[d] = (double)cV[d];
+            }
+            cvol = (float)P.vol[i];
         }
+        __syncthreads();
+        T V[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) V[d] = cV[d];
         T racc[NR];
 #pragma unroll
         for (int m = 0; m < NR; ++m) racc[m] = T(0);
@@ -1270,25 +1320,36 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
         }
         block_sum_t<NR, RK_NT>(racc, sred, sout);
         if (threadIdx.x == 0) {
-            double m[NR], Wn[NW];
-            for (int q = 0; q < NR; ++q) m[q] = sout[q];
-            rk_from_raw<D>(m, Vd, Wn, qt, qr);
+            // heat fluxes of f, tau and the equilibrium in FP32; the state W~ in FP64
+            float rn, Un[3] = {0, 0, 0}, etn, r0n, qtf[3] = {0, 0, 0}, qrf[3] = {0, 0, 0};
+            rk_state_raw32<D>(sout, Vd, rn, Un, etn, r0n, qtf, qrf);
+            double rho, U[3], RTt, RTr, RT;
+            rk_prim<D>(P.Wout + (size_t)i * NW, rho, U, RTt, RTr, RT);
+            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+            const float tau = rk_tau32(P.g, (float)rho, (float)RTt);
+            float Uf[3] = {0, 0, 0};
+            for (int d = 0; d < D; ++d) Uf[d] = (float)U[d];
+            eq = rk_make32<D>(P.g, (float)rho, Uf, (float)RTt, (float)RTr, qtf, qrf);
+            ctau = tau;
+            u0[i] = P.vol[i] / P.dt + P.vol[i] / (double)tau;
         }
     } else {
         double Wn[NW];
         rk_cell_mom<D, T>(fi, Nv, Nvp, P.xi, P.w, Wn, qt, qr, sred, sout);
-    }
-    if (threadIdx.x == 0) {
-        double rho, U[3], RTt, RTr, RT;
-        rk_prim<D>(P.Wout + (size_t)i * NW, rho, U, RTt, RTr, RT);
-        if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
-        const double tau = rk_tau(P.g, rho, RTt);
-        eq = rk_make<D, T>(P.g, rho, U, RTt, RTr, qt, qr);
-        tau_s = tau;
-        u0[i] = P.vol[i] / P.dt + P.vol[i] / tau;
+        if (threadIdx.x == 0) {
+            double rho, U[3], RTt, RTr, RT;
+            rk_prim<D>(P.Wout + (size_t)i * NW, rho, U, RTt, RTr, RT);
+            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+            const double tau = rk_tau(P.g, rho, RTt);
+            eq = rk_make<D, T>(P.g, rho, U, RTt, RTr, qt, qr);
+            tau_s = tau;
+            u0[i] = P.vol[i] / P.dt + P.vol[i] / tau;
+        }
     }
     __syncthreads();
-    const T tau = (T)tau_s, Vc = (T)P.vol[i];
+    // Vc / tau: FP32 reciprocal in the mixed form, the FP64 division otherwise
+    const T tau = sizeof(T) == 4 ? (T)ctau : (T)tau_s, Vc = sizeof(T) == 4 ? (T)cvol : (T)P.vol[i];
+    const T itau = T(1) / tau;
     T* ro = P.fout + (size_t)i * cs;
     for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
         if (k >= Nv) {
@@ -1305,7 +1366,8 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
         for (int a = 0; a < NA; ++a) {
             T N = T(0);
             for (int q = 0; q < ns; ++q) N += sg[q] * P.FX[((size_t)fs[q] * NA + a) * Nvp + k];
-            ro[(size_t)a * Nvp + k] = Vc * (gv[a] - fi[(size_t)a * Nvp + k]) / tau - N;
+            ro[(size_t)a * Nvp + k] = sizeof(T) == 4 ? Vc * (gv[a] - fi[(size_t)a * Nvp + k]) * itau - N
+                                                     : Vc * (gv[a] - fi[(size_t)a * Nvp + k]) / tau - N;
         }
     }
 }
