@@ -371,7 +371,7 @@ avs_status setup_mesh(avs_ctx* c, const avs_mesh* m)
         dalloc(&c->vol, Nc) || dalloc(&c->bc, (size_t)std::max(1, c->nbc) * 6) || dalloc(&c->slot, ncs) ||
         dalloc(&c->nslot, Nc) || dalloc(&c->nbr, ncs) || dalloc(&c->cg_d, ncsd) || dalloc(&c->r_d, ncsd) ||
         dalloc(&c->eps2_d, Nc) || dalloc(&c->cg_f, ncsd) || dalloc(&c->r_f, ncsd) || dalloc(&c->eps2_f, Nc) ||
-        dalloc(&c->AFf, (size_t)Nf * c->NW) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * avs::NMom<3>::v) ||
+        dalloc(&c->AFf, (size_t)Nf * c->NW) || dalloc(&c->forder, Nf) || dalloc(&c->cmom, (size_t)Nc * AVS_CMOM_MAX) ||
         dalloc((unsigned char**)&c->cpar, (size_t)Nc * AVS_CELLPAR_BYTES) || dalloc(&c->clist, Nc) ||
         dalloc(&c->imp_dW, (size_t)Nc * c->NW) || dalloc(&c->imp_rhs0, (size_t)Nc * c->NW) ||
         dalloc(&c->imp_diag, Nc) || dalloc(&c->imp_Wta, (size_t)Nc * c->NW) ||

@@ -859,112 +859,254 @@ __global__ void __launch_bounds__(RK_NT) rk_face32(RkP<float> P, const float* __
     if (threadIdx.x < NW) P.AF[(size_t)f * NW + threadIdx.x] = sout[threadIdx.x];
 }
 
-// rk_cell for the FP32 form: the lagged heat fluxes from raw moments about
-// the cell's carried U.
+// ---------------------------------------------------------------- mixed-form cell stage
+// As the monatomic mixed form: the raw moments of f^{n+1} that the next step
+// needs for its lagged heat fluxes are summed while f^{n+1} is written and
+// carried per cell ([cell][NR] FP64, about V(W^{n+1})); all per-cell FP64
+// work (the balance of W, the rotational relaxation) runs one thread per
+// cell in rk_cell_state32; the cell kernel streams f, the face fluxes and
+// f^{n+1} RK_VC nodes per thread in vector loads.
+
+// Per-cell parameters of the Rykov collision update (mixed form).
+struct RkCellPar {
+    RkEq<float> eq;          // Rykov equilibrium of (W~ with relaxed E_rot, q~)
+    float upd[4];            // 1/dt, 1/tau~, 1/|V|, 1/(1/dt + 1/tau~)
+    float Vn[3];             // reference velocity of the next raw moments: V(W^{n+1})
+};
+static_assert(sizeof(RkCellPar) <= AVS_CELLPAR_BYTES, "RkCellPar buffer size");
+static_assert(RkNR<3>::v <= AVS_CMOM_MAX, "carried moments buffer size");
+
+constexpr int RK_VC = 2;     // nodes per thread per iteration of the cell kernels (2 or 4)
+
+// Reference velocity of the raw sums of a cell from a carried W (FP32; the
+// same expression wherever carried moments are taken or used).
 template <int D>
-__global__ void __launch_bounds__(RK_NT) rk_cell32(RkP<float> P, const float* __restrict__ xif,
-                                                   const float* __restrict__ wf)
+__device__ __forceinline__ void rk_vref(const double* W, float* V)
 {
-    using T = float;
+    const float ir = 1.0f / (float)W[0];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) V[d] = d < D ? (float)W[1 + d] * ir : 0.0f;
+}
+
+// V = RK_VC consecutive nodes of an FP32 row in one vector load (L2 only).
+__device__ __forceinline__ void rk_ldv(const float* p, float* o)
+{
+    if constexpr (RK_VC == 4) {
+        const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+        o[0] = t.x;
+        o[1] = t.y;
+        o[2] = t.z;
+        o[3] = t.w;
+    } else {
+        const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+        o[0] = t.x;
+        o[1] = t.y;
+    }
+}
+
+__device__ __forceinline__ void rk_stv(float* p, const float* o)
+{
+    if constexpr (RK_VC == 4)
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    else
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+}
+
+// xi (D per node) and w of the RK_VC nodes from k0 (rows padded to 32 nodes;
+// k0 is a multiple of RK_VC, so the vectors are aligned).
+template <int D>
+__device__ __forceinline__ void rk_ld_nodes(const float* __restrict__ xif, const float* __restrict__ wf, int k0,
+                                            float (*x)[D], float* w)
+{
+    constexpr int V = RK_VC;
+    float t[V * D];
+#pragma unroll
+    for (int j = 0; j < V * D / 2; ++j) {
+        const float2 q = __ldg(reinterpret_cast<const float2*>(xif + (size_t)k0 * D) + j);
+        t[2 * j] = q.x;
+        t[2 * j + 1] = q.y;
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int d = 0; d < D; ++d) x[v][d] = t[v * D + d];
+#pragma unroll
+    for (int j = 0; j < V / 2; ++j) {
+        const float2 q = __ldg(reinterpret_cast<const float2*>(wf + k0) + j);
+        w[2 * j] = q.x;
+        w[2 * j + 1] = q.y;
+    }
+}
+
+// Raw moments of the own f^n of every cell about V(W^n), when the previous
+// step did not leave them (after init, set_f, an adaptation or an implicit
+// step).  Same nodes per thread and order as rk_cell32, so the sums are the
+// carried ones bit for bit.
+template <int D>
+__global__ void __launch_bounds__(RK_NT) rk_raw_moments32(RkP<float> P, const float* __restrict__ xif,
+                                                          const float* __restrict__ wf, double* mom)
+{
     constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
-    __shared__ double sw[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
-    __shared__ RkEq<T> eq;
-    __shared__ float tau_s, cdt, cvol, cV[3];
-    __shared__ double Vd[3];
+    __shared__ double sw[(RK_NT / 32) * NR], red[NR];
+    const int i = blockIdx.x;
+    const int Nvp = P.Nvp;
+    float V[3];
+    rk_vref<D>(P.Win + (size_t)i * NW, V);
+    const float* fi = P.f + (size_t)i * NA * Nvp;
+    float acc[NR];
+#pragma unroll
+    for (int m = 0; m < NR; ++m) acc[m] = 0.0f;
+    for (int k0 = threadIdx.x * RK_VC; k0 < P.Nv; k0 += RK_NT * RK_VC) {
+        float x[RK_VC][D], wv[RK_VC], fv[NA][RK_VC];
+        rk_ld_nodes<D>(xif, wf, k0, x, wv);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) rk_ldv(fi + (size_t)a * Nvp + k0, fv[a]);
+#pragma unroll
+        for (int v = 0; v < RK_VC; ++v) {
+            float c[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) c[d] = x[v][d] - V[d];
+            rk_raw_acc<D>(acc, c, wv[v] * fv[0][v], D == 2 ? wv[v] * fv[1][v] : 0.0f, wv[v] * fv[NA - 1][v]);
+        }
+    }
+    block_sum_t<NR, RK_NT>(acc, sw, red);
+    if (threadIdx.x < NR) mom[(size_t)i * NR + threadIdx.x] = red[threadIdx.x];
+}
+
+// One thread per cell: lagged q_t, q_r of f^n from its carried moments,
+// W~ = W - dt/|V| sum_j sgn_j A F_j (FP64), the implicit rotational relaxation
+// of E_rot over dt with tau~ (reading R28), and the collision parameters.
+template <int D>
+__global__ void rk_cell_state32(RkP<float> P, const double* __restrict__ mom, RkCellPar* par)
+{
+    constexpr int NW = D + 3, NR = RkNR<D>::v;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.Nc) return;
+    const double* Wi = P.Win + (size_t)i * NW;
+    float V[3];
+    rk_vref<D>(Wi, V);
+    const double Vd[3] = {V[0], V[1], V[2]};
+    float rn, Un[3], etn, r0n, qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+    rk_state_raw32<D>(mom + (size_t)i * NR, Vd, rn, Un, etn, r0n, qt, qr);
+    const int ns = P.nslot[i];
+    const double dtV = P.dt / P.vol[i];
+    double Wt[NW];
+    for (int c = 0; c < NW; ++c) {
+        double sum = 0.0;
+        for (int q = 0; q < ns; ++q) {
+            const int sl = P.slot[i * AVS_MAXS + q];
+            const double a = P.AF[(size_t)(sl >> 1) * NW + c];
+            sum += (sl & 1) ? -a : a;
+        }
+        Wt[c] = Wi[c] - dtV * sum;
+    }
+    const double rho = Wt[0], ir = 1.0 / rho;
+    double m2 = 0.0;
+    float U[3] = {0, 0, 0};
+    for (int d = 0; d < D; ++d) {
+        m2 += Wt[1 + d] * Wt[1 + d];
+        U[d] = (float)(Wt[1 + d] * ir);
+    }
+    const double ein = Wt[D + 1] - 0.5 * m2 * ir;   // rho e, translational + rotational
+    const double RT = ein * ir * 0.4, RTt = (ein - Wt[D + 2]) * ir * (1.0 / 1.5);
+    if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+    const float tau = rk_tau32(P.g, (float)rho, (float)RTt);
+    const double az = P.dt / (P.g.Z * (double)tau);
+    Wt[D + 2] = (Wt[D + 2] + az * rho * RT) / (1.0 + az);
+    const double RTr = Wt[D + 2] * ir;
+    for (int c = 0; c < NW; ++c) P.Wout[(size_t)i * NW + c] = Wt[c];
+    RkCellPar cp;
+    cp.eq = rk_make32<D>(P.g, (float)rho, U, (float)((5.0 * RT - 2.0 * RTr) * (1.0 / 3.0)), (float)RTr, qt, qr);
+    const float dtf = (float)P.dt, idt = 1.0f / dtf, itau = 1.0f / tau;
+    cp.upd[0] = idt;
+    cp.upd[1] = itau;
+    cp.upd[2] = 1.0f / (float)P.vol[i];
+    cp.upd[3] = dtf * tau / (dtf + tau);
+    rk_vref<D>(Wt, cp.Vn);
+    par[i] = cp;
+}
+
+// One block per cell: net flux N = sum_j sgn_j F_j per node, the collision
+// update (Eq. SGS_phi's diagonal, R1) with the Rykov equilibrium, pad nodes
+// written as zero, and the raw moments of f^{n+1} about V(W^{n+1}) for the
+// next step.
+template <int D>
+__global__ void __launch_bounds__(RK_NT, 7) rk_cell32(RkP<float> P, const float* __restrict__ xif,
+                                                   const float* __restrict__ wf, double* mom,
+                                                   const RkCellPar* __restrict__ par)
+{
+    constexpr int NA = RkNA<D>::v, NR = RkNR<D>::v, V = RK_VC;
+    __shared__ double sw[(RK_NT / 32) * NR], red[NR];
+    __shared__ RkCellPar cp;
     __shared__ int fs[AVS_MAXS];
-    __shared__ T sg[AVS_MAXS];
+    __shared__ float sg[AVS_MAXS];
+    const int tid = threadIdx.x;
     const int i = blockIdx.x;
     const int ns = P.nslot[i];
     const int Nv = P.Nv, Nvp = P.Nvp;
-    if (threadIdx.x < ns) {
-        const int sl = P.slot[i * AVS_MAXS + threadIdx.x];
-        fs[threadIdx.x] = sl >> 1;
-        sg[threadIdx.x] = (sl & 1) ? T(-1) : T(1);
+    if (tid < ns) {
+        const int sl = P.slot[i * AVS_MAXS + tid];
+        fs[tid] = sl >> 1;
+        sg[tid] = (sl & 1) ? -1.0f : 1.0f;
     }
+    if (tid == 32) cp = par[i];
+    __syncthreads();
     const size_t cs = (size_t)NA * Nvp;
-    const T* fi = P.f + (size_t)i * cs;
-    const double* Wi = P.Win + (size_t)i * NW;
-    if (threadIdx.x == 32) {
-        // reference velocity of the sums: the carried mean velocity in FP32,
-        // converted once (Vd its exact FP64 value)
-        const float irW = 1.0f / (float)Wi[0];
-        for (int d = 0; d < 3; ++d) {
-            cV[d] = d < D ? (float)Wi[1 + d] * irW : 0.0f;
-            Vd[d] = (double)cV[d];
-        }
-        cdt = (float)P.dt;
-        cvol = (float)P.vol[i];
-    }
-    __syncthreads();
-    T V[D];
+    const float* fi = P.f + (size_t)i * cs;
+    float* fo = P.fout + (size_t)i * cs;
+    const float u0 = cp.upd[0], u1 = cp.upd[1], u2 = cp.upd[2], u3 = cp.upd[3];
+    float Vn[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) V[d] = cV[d];
-    T racc[NR];
+    for (int d = 0; d < D; ++d) Vn[d] = cp.Vn[d];
+    float acc[NR];
 #pragma unroll
-    for (int m = 0; m < NR; ++m) racc[m] = T(0);
-    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
-        T c[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) c[d] = xif[(size_t)k * D + d] - V[d];
-        const T wk = wf[k];
-        rk_raw_acc<D>(racc, c, wk * fi[k], D == 2 ? wk * fi[Nvp + k] : T(0), wk * fi[(size_t)(NA - 1) * Nvp + k]);
-    }
-    block_sum_t<NR, RK_NT>(racc, sw, sout);
-    if (threadIdx.x == 0) {
-        // heat fluxes of f^n and tau, eq in FP32; the carried W^{n+1} in FP64
-        float rn, Un[3] = {0, 0, 0}, etn, r0n, qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
-        rk_state_raw32<D>(sout, Vd, rn, Un, etn, r0n, qt, qr);
-        const double dtV = P.dt / P.vol[i];
-        double Wt[NW];
-        for (int c = 0; c < NW; ++c) {
-            double s = 0.0;
-            for (int q = 0; q < ns; ++q) {
-                const double a = P.AF[(size_t)fs[q] * NW + c];
-                s += sg[q] > T(0) ? a : -a;
-            }
-            Wt[c] = Wi[c] - dtV * s;
-        }
-        const double rho = Wt[0], ir = 1.0 / rho;
-        double m2 = 0.0;
-        float U[3] = {0, 0, 0};
-        for (int d = 0; d < D; ++d) {
-            m2 += Wt[1 + d] * Wt[1 + d];
-            U[d] = (float)(Wt[1 + d] * ir);
-        }
-        const double ein = Wt[D + 1] - 0.5 * m2 * ir;  // rho e, translational + rotational
-        const double RT = ein * ir * 0.4, RTt = (ein - Wt[D + 2]) * ir * (1.0 / 1.5);
-        if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
-        const float tau = rk_tau32(P.g, (float)rho, (float)RTt);
-        const double az = P.dt / (P.g.Z * (double)tau);
-        Wt[D + 2] = (Wt[D + 2] + az * rho * RT) / (1.0 + az);
-        const double RTr = Wt[D + 2] * ir;
-        eq = rk_make32<D>(P.g, (float)rho, U, (float)((5.0 * RT - 2.0 * RTr) * (1.0 / 3.0)), (float)RTr, qt, qr);
-        tau_s = tau;
-        for (int c = 0; c < NW; ++c) P.Wout[(size_t)i * NW + c] = Wt[c];
-    }
-    __syncthreads();
-    const float tf = tau_s, dtf = cdt;
-    const T idt = 1.0f / dtf, itau = 1.0f / tf, iV = 1.0f / cvol;
-    const T iden = dtf * tf / (dtf + tf);
-    T* fo = P.fout + (size_t)i * cs;
-    for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
-        if (k >= Nv) {
-#pragma unroll
-            for (int a = 0; a < NA; ++a) fo[(size_t)a * Nvp + k] = T(0);
-            continue;
-        }
-        T xt[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) xt[d] = xif[(size_t)k * D + d];
-        T gv[NA];
-        rk_eval<D, T>(eq, xt, gv);
+    for (int m = 0; m < NR; ++m) acc[m] = 0.0f;
+    for (int k0 = tid * V; k0 < Nv; k0 += RK_NT * V) {
+        float x[V][D], wv[V], fv[NA][V], Nn[NA][V];
+        rk_ld_nodes<D>(xif, wf, k0, x, wv);
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            T N = T(0);
-            for (int q = 0; q < ns; ++q) N += sg[q] * P.FX[((size_t)fs[q] * NA + a) * Nvp + k];
-            fo[(size_t)a * Nvp + k] = (fi[(size_t)a * Nvp + k] * idt + gv[a] * itau - N * iV) * iden;
+            rk_ldv(fi + (size_t)a * Nvp + k0, fv[a]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Nn[a][v] = 0.0f;
         }
+#pragma unroll
+        for (int q = 0; q < AVS_MAXS; ++q) {
+            if (q >= ns) break;
+            const float* Fq = P.FX + (size_t)fs[q] * cs + k0;
+            const float g = sg[q];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                float t[V];
+                rk_ldv(Fq + (size_t)a * Nvp, t);
+#pragma unroll
+                for (int v = 0; v < V; ++v) Nn[a][v] += g * t[v];
+            }
+        }
+        float out[NA][V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float gv[NA];
+            rk_eval<D, float>(cp.eq, x[v], gv);
+            const bool real = k0 + v < Nv;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) out[a][v] = real ? (fv[a][v] * u0 + gv[a] * u1 - Nn[a][v] * u2) * u3 : 0.0f;
+            float c[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) c[d] = x[v][d] - Vn[d];
+            rk_raw_acc<D>(acc, c, wv[v] * out[0][v], D == 2 ? wv[v] * out[1][v] : 0.0f, wv[v] * out[NA - 1][v]);
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) rk_stv(fo + (size_t)a * Nvp + k0, out[a]);
     }
+    // rows are padded to a multiple of 32 nodes and every thread's k0 is a
+    // multiple of V, so the loop above wrote every node below the first k0 >= Nv;
+    // the pad nodes from there to Nvp are zeroed here
+    for (int k = ((Nv + V - 1) / V) * V + tid; k < Nvp; k += RK_NT)
+#pragma unroll
+        for (int a = 0; a < NA; ++a) fo[(size_t)a * Nvp + k] = 0.0f;
+    block_sum_t<NR, RK_NT>(acc, sw, red);
+    if (tid < NR) mom[(size_t)i * NR + tid] = red[tid];
 }
 
 // W (and the total heat flux q_t + q_r) of every cell.
@@ -1526,11 +1668,21 @@ cudaError_t rk_step_t(avs_ctx* c, const void* fin, void* fout, const double* Win
     if (e != cudaSuccess) return e;
     P.Wout = Wout;
     P.fout = (T*)fout;
-    if constexpr (sizeof(T) == 4)
-        rk_cell32<D><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f);
-    else
+    if constexpr (sizeof(T) == 4) {
+        RkCellPar* par = reinterpret_cast<RkCellPar*>(c->cpar);
+        if (!c->mom_valid) {
+            rk_raw_moments32<D><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f, c->cmom);
+            c->launches += 1;
+        }
+        rk_cell_state32<D><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(P, c->cmom, par);
+        rk_cell32<D><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f, c->cmom, par);
+        c->launches += 2;
+        c->mom_valid = 1;      // the raw moments of fout about V(Wout) are in cmom
+    } else {
         rk_cell<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P);
-    c->launches += 1;
+        c->launches += 1;
+        c->mom_valid = 0;
+    }
     return cudaGetLastError();
 }
 
@@ -1623,6 +1775,7 @@ cudaError_t rk_step_implicit_t(avs_ctx* c, const void* fin, void* fout, const do
     dim3 gf(c->Nc * NA, std::min(8, (c->Nvp + 255) / 256));
     rk_imp_finish<T><<<gf, 256, 0, c->stream>>>(c->Nv, c->Nvp, (const T*)fin, dphi, (T*)fout);
     c->launches += 1;
+    c->mom_valid = 0;          // no carried moments of fout
     return cudaGetLastError();
 }
 
