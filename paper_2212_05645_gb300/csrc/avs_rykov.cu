@@ -669,7 +669,7 @@ __device__ __forceinline__ bool rk_upwind_L(const float* x, const float* Af, con
 
 // rk_face for the FP32 form (same steps; sums as above).
 template <int D>
-__global__ void __launch_bounds__(RK_NT) rk_face32(RkP<float> P, const float* __restrict__ xif,
+__global__ void __launch_bounds__(RK_NT, D == 2 ? 8 : 7) rk_face32(RkP<float> P, const float* __restrict__ xif,
                                                    const float* __restrict__ wf, const float* __restrict__ Anf,
                                                    const float* __restrict__ rLf, const float* __restrict__ rRf)
 {
