@@ -738,46 +738,82 @@ __global__ void __launch_bounds__(RK_NT, D == 2 ? 8 : 7) rk_face32(RkP<float> P,
     T racc[NR], wacc[2] = {T(0), T(0)};
 #pragma unroll
     for (int m = 0; m < NR; ++m) racc[m] = T(0);
-    // pass A: foot values and their raw moments (or the wall balance)
-    for (int k = threadIdx.x; k < Nv; k += RK_NT) {
-        T x[D];
+    // pass A: foot values and their raw moments (or the wall balance); the
+    // interior and boundary loops are separate so that neither carries the
+    // other's instructions predicated off
+    const int Rc = R >= 0 ? R : L;
+    const float* fLp = P.f + (size_t)L * cs;
+    const float* fRp = P.f + (size_t)Rc * cs;
+    const float* gLp = P.G ? P.G + (size_t)L * NA * D * Nvp : nullptr;
+    const float* gRp = P.G ? P.G + (size_t)Rc * NA * D * Nvp : nullptr;
+    if (R >= 0) {
+        for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+            T x[D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) x[d] = xif[(size_t)k * D + d];
-        T s;
-        const bool up = rk_upwind_L<D>(x, Af, P.xi, k, An, s);
-        const int C = up ? L : R;
-        T ph[NA];
+            for (int d = 0; d < D; ++d) x[d] = xif[(size_t)k * D + d];
+            T s;
+            const bool up = rk_upwind_L<D>(x, Af, P.xi, k, An, s);
+            const float* fb = (up ? fLp : fRp) + k;
+            T ph[NA];
+            if (gLp) {
+                const float* gb = (up ? gLp : gRp) + k;
+                T off[D];
 #pragma unroll
-        for (int a = 0; a < NA; ++a) ph[a] = T(0);
-        if (C >= 0) {
-            T off[D];
+                for (int d = 0; d < D; ++d) off[d] = (up ? rl[d] : rr[d]) - x[d] * h;
 #pragma unroll
-            for (int d = 0; d < D; ++d) off[d] = (up ? rl[d] : rr[d]) - x[d] * h;
+                for (int a = 0; a < NA; ++a) {
+                    T v = fb[a * Nvp];
 #pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                T v = P.f[(size_t)C * cs + (size_t)a * Nvp + k];
-                if (P.G)
+                    for (int d = 0; d < D; ++d) v += gb[(a * D + d) * Nvp] * off[d];
+                    ph[a] = v;
+                }
+            } else {
 #pragma unroll
-                    for (int d = 0; d < D; ++d) v += P.G[(((size_t)C * NA + a) * D + d) * Nvp + k] * off[d];
-                ph[a] = v;
+                for (int a = 0; a < NA; ++a) ph[a] = fb[a * Nvp];
             }
-        }
 #pragma unroll
-        for (int a = 0; a < NA; ++a) fx[(size_t)a * Nvp + k] = ph[a];
-        const T wk = wf[k];
-        if (R >= 0) {
+            for (int a = 0; a < NA; ++a) fx[(size_t)a * Nvp + k] = ph[a];
+            const T wk = wf[k];
             T c[D];
 #pragma unroll
             for (int d = 0; d < D; ++d) c[d] = x[d] - V[d];
             rk_raw_acc<D>(racc, c, wk * ph[0], D == 2 ? wk * ph[1] : T(0), wk * ph[NA - 1]);
-        } else if (btype == AVS_BC_WALL) {
-            if (up) {
-                wacc[0] += wk * s * ph[0];
-            } else {
-                T c2 = T(0);
+        }
+    } else {
+        for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+            T x[D];
 #pragma unroll
-                for (int d = 0; d < D; ++d) c2 += (x[d] - Ubf[d]) * (x[d] - Ubf[d]);
-                wacc[1] += wk * (-s) * (pw * ex(-c2 * i2b));
+            for (int d = 0; d < D; ++d) x[d] = xif[(size_t)k * D + d];
+            T s;
+            const bool up = rk_upwind_L<D>(x, Af, P.xi, k, An, s);
+            T ph[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) ph[a] = T(0);
+            if (up) {
+                T off[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) off[d] = rl[d] - x[d] * h;
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    T v = fLp[a * Nvp + k];
+                    if (gLp)
+#pragma unroll
+                        for (int d = 0; d < D; ++d) v += gLp[(a * D + d) * Nvp + k] * off[d];
+                    ph[a] = v;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < NA; ++a) fx[(size_t)a * Nvp + k] = ph[a];
+            if (btype == AVS_BC_WALL) {
+                const T wk = wf[k];
+                if (up) {
+                    wacc[0] += wk * s * ph[0];
+                } else {
+                    T c2 = T(0);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) c2 += (x[d] - Ubf[d]) * (x[d] - Ubf[d]);
+                    wacc[1] += wk * (-s) * (pw * ex(-c2 * i2b));
+                }
             }
         }
     }
@@ -824,6 +860,9 @@ __global__ void __launch_bounds__(RK_NT, D == 2 ? 8 : 7) rk_face32(RkP<float> P,
     T af[NW];
 #pragma unroll
     for (int m = 0; m < NW; ++m) af[m] = T(0);
+    // interior: phi = wa phi_bar + wb g at every node; boundary: the
+    // incoming nodes take g (wall or far-field Maxwellian)
+    const bool inter = R >= 0;
     for (int k = threadIdx.x; k < Nv; k += RK_NT) {
         T x[D], x2 = T(0);
 #pragma unroll
@@ -836,11 +875,16 @@ __global__ void __launch_bounds__(RK_NT, D == 2 ? 8 : 7) rk_face32(RkP<float> P,
         T ph[NA];
 #pragma unroll
         for (int a = 0; a < NA; ++a) ph[a] = fx[(size_t)a * Nvp + k];
-        if (R >= 0 || !up) {
+        if (inter) {
             T gv[NA];
             rk_eval<D, T>(eq, x, gv);
 #pragma unroll
-            for (int a = 0; a < NA; ++a) ph[a] = R >= 0 ? wa * ph[a] + wb * gv[a] : gv[a];
+            for (int a = 0; a < NA; ++a) ph[a] = wa * ph[a] + wb * gv[a];
+        } else if (!up) {
+            T gv[NA];
+            rk_eval<D, T>(eq, x, gv);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) ph[a] = gv[a];
         }
         T F[NA];
 #pragma unroll
