@@ -1618,6 +1618,94 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_micro(int Nv, int Nvp, const T* 
     }
 }
 
+// One colour of a microscopic sweep in the mixed form: as rk_imp_micro, four
+// nodes per thread in 16-byte vectors; a neighbour's dphi row is read only
+// when one of the four nodes is downwind of it.
+template <int D>
+__global__ void __launch_bounds__(RK_NT) rk_imp_micro32(int Nv, int Nvp, const float* __restrict__ res, float* dphi,
+                                                        const double* __restrict__ u0, const float* __restrict__ xif,
+                                                        const float* __restrict__ An, const int* __restrict__ slot,
+                                                        const unsigned char* __restrict__ nslot,
+                                                        const int* __restrict__ faceL, const int* __restrict__ faceR,
+                                                        const int* __restrict__ clist, int c0)
+{
+    constexpr int NA = RkNA<D>::v, V = 4;
+    __shared__ float sA[AVS_MAXS][D];
+    __shared__ int snb[AVS_MAXS];
+    __shared__ float su0;
+    const int tid = threadIdx.x;
+    const int i = clist[c0 + blockIdx.x];
+    const int ns = nslot[i];
+    if (tid < ns) {
+        const int sl = slot[i * AVS_MAXS + tid];
+        const int f = sl >> 1;
+#pragma unroll
+        for (int d = 0; d < D; ++d) sA[tid][d] = (sl & 1) ? -An[(size_t)f * D + d] : An[(size_t)f * D + d];
+        snb[tid] = (sl & 1) ? faceL[f] : faceR[f];
+    }
+    if (tid == 32) su0 = (float)u0[i];
+    __syncthreads();
+    const int k0 = (blockIdx.y * RK_NT + tid) * V;
+    if (k0 >= Nv) return;                          // pad nodes keep the zero of the initial dphi
+    float x[V][D];
+    {
+        float t[V * D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(xif + (size_t)k0 * D) + j);
+            t[4 * j] = q.x;
+            t[4 * j + 1] = q.y;
+            t[4 * j + 2] = q.z;
+            t[4 * j + 3] = q.w;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int d = 0; d < D; ++d) x[v][d] = t[v * D + d];
+    }
+    float sn[AVS_MAXS][V], idg[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) idg[v] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < AVS_MAXS; ++s) {
+        if (s >= ns) break;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float p = 0.0f;
+#pragma unroll
+            for (int d = 0; d < D; ++d) p += x[v][d] * sA[s][d];
+            sn[s][v] = p;
+            if (p >= 0.0f) idg[v] += p;
+        }
+    }
+    const float u = su0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) idg[v] = 1.0f / (u + idg[v]);
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const float4 r4 = __ldcg(reinterpret_cast<const float4*>(res + ((size_t)i * NA + a) * Nvp + k0));
+        float acc[V] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+        for (int s = 0; s < AVS_MAXS; ++s) {
+            if (s >= ns) break;
+            const int j = snb[s];
+            bool in = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) in |= sn[s][v] < 0.0f;
+            if (j < 0 || !in) continue;
+            const float4 t4 = __ldcg(reinterpret_cast<const float4*>(dphi + ((size_t)j * NA + a) * Nvp + k0));
+            const float t[V] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (sn[s][v] < 0.0f) acc[v] -= sn[s][v] * t[v];
+        }
+        float o[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = k0 + v < Nv ? acc[v] * idg[v] : 0.0f;
+        *reinterpret_cast<float4*>(dphi + ((size_t)i * NA + a) * Nvp + k0) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
 // f^{n+1} = f^n + dphi (pad nodes zero)
 template <typename T>
 __global__ void rk_imp_finish(int Nv, int Nvp, const T* __restrict__ fin, const T* __restrict__ dphi, T* fout)
@@ -1808,7 +1896,12 @@ cudaError_t rk_step_implicit_t(avs_ctx* c, const void* fin, void* fout, const do
                 if (col == prev) continue;      // same inputs as the pass before: same values
                 prev = col;
                 const int c0 = c->cstart[col], c1 = c->cstart[col + 1];
-                if (c1 > c0) {
+                if (c1 > c0 && f32) {
+                    rk_imp_micro32<D><<<dim3(c1 - c0, (c->Nv + RK_NT * 4 - 1) / (RK_NT * 4)), RK_NT, 0, c->stream>>>(
+                        c->Nv, c->Nvp, (const float*)fout, (float*)dphi, u0, c->xi_f, c->An_f, c->slot, c->nslot,
+                        c->faceL, c->faceR, c->clist, c0);
+                    c->launches += 1;
+                } else if (c1 > c0) {
                     rk_imp_micro<D, T><<<dim3(c1 - c0, nyb), 128, 0, c->stream>>>(
                         c->Nv, c->Nvp, (const T*)fout, dphi, u0, f32 ? (const T*)c->xi_f : (const T*)c->xi_d,
                         c->xi_d, c->An_d, f32 ? (const T*)c->An_f : (const T*)c->An_d, c->slot, c->nslot, c->faceL,
