@@ -214,81 +214,117 @@ __device__ __forceinline__ double normal_ik(uint64_t seed, uint64_t i, uint64_t 
     return sqrt(-2.0 * log(U1)) * cos(2.0 * AVS_PI * U2);
 }
 
-// f = g^eq(W_p) (1 + amp z_ik) per cell and node, pads zero.  One block per
-// cell; the per-cell factors are formed once.  The FP64 form evaluates the
-// exponential in FP64; the mixed form, whose f is stored in FP32, in FP32
-// (correctly rounded expf, a few ulp of FP32 at most).  The noise z is the
-// FP64 SplitMix64/Box-Muller normal in both forms.
+// Per-cell factors of the Maxwellian start, formed once per block by thread 0
+// (an FP64 pow in every thread costs more than the block's node work).
+struct MaxwellC {
+    double pref, twoRT, U[3];    // rho / (2 pi R T)^(D/2), 2 R T, U
+    float pref32, i2RT32, U32[3];
+};
+
+__device__ __forceinline__ void maxwell_consts(int D, double rho, const double* U, double RT, MaxwellC& m)
+{
+    m.pref = rho / pow(2.0 * AVS_PI * RT, 0.5 * D);
+    m.twoRT = 2.0 * RT;
+    m.pref32 = (float)m.pref;
+    m.i2RT32 = (float)(1.0 / (2.0 * RT));
+    for (int d = 0; d < 3; ++d) {
+        m.U[d] = d < D ? U[d] : 0.0;
+        m.U32[d] = (float)m.U[d];
+    }
+}
+
+// g^eq at node k: FP64 (as the oracle) in the FP64 form; FP32 in the mixed
+// form, whose f is stored in FP32 (expf, a few ulp of FP32 at most).  The
+// noise factor 1 + amp z_ik uses the FP64 SplitMix64/Box-Muller normal in both.
+template <typename T>
+__device__ __forceinline__ double maxwell_node(int D, const MaxwellC& m, const double* __restrict__ xi,
+                                               const float* __restrict__ xi32, int k, double amp, uint64_t seed,
+                                               int i)
+{
+    if (sizeof(T) == 8) {
+        double c2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const double c = __dsub_rn(xi[(size_t)k * D + d], m.U[d]);
+            c2 = __dadd_rn(c2, __dmul_rn(c, c));
+        }
+        double g = m.pref * exp(-c2 / m.twoRT);
+        if (amp != 0.0) g *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
+        return g;
+    }
+    float c2 = 0.0f;
+    for (int d = 0; d < D; ++d) {
+        const float c = xi32[(size_t)k * D + d] - m.U32[d];
+        c2 += c * c;
+    }
+    float g = m.pref32 * expf(-c2 * m.i2RT32);
+    if (amp != 0.0) g *= (float)(1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k));
+    return (double)g;
+}
+
+// f = g^eq(W_p) (1 + amp z_ik) per cell and node, pads zero; one block per cell.
 template <typename T>
 __global__ void __launch_bounds__(256) k_maxwell(int D, int NA, int Nv, int Nvp, const double* __restrict__ xi,
                                                  const float* __restrict__ xi32, const double* __restrict__ Wp,
                                                  double R, double amp, uint64_t seed, T* f)
 {
+    __shared__ MaxwellC m;
+    __shared__ T h0;
     const int i = blockIdx.x;
     T* fi = f + (size_t)i * NA * Nvp;
-    const double* P = Wp + (size_t)i * (D + 2);
-    const double rho = P[0], RT = R * P[D + 1];
-    const double pref = rho / pow(2.0 * AVS_PI * RT, 0.5 * D);
-    const float pref32 = (float)pref, i2RT32 = (float)(1.0 / (2.0 * RT));
-    float U32[3] = {0.0f, 0.0f, 0.0f};
-    for (int d = 0; d < D; ++d) U32[d] = (float)P[1 + d];
+    if (threadIdx.x == 0) {
+        const double* P = Wp + (size_t)i * (D + 2);
+        const double RT = R * P[D + 1];
+        maxwell_consts(D, P[0], P + 1, RT, m);
+        h0 = (T)((3 - D) * RT);
+    }
+    __syncthreads();
     for (int k = threadIdx.x; k < Nvp; k += blockDim.x) {
         if (k >= Nv) {
             for (int a = 0; a < NA; ++a) fi[(size_t)a * Nvp + k] = T(0);
             continue;
         }
-        T G;
-        if (sizeof(T) == 8) {
-            double c2 = 0.0;
-            for (int d = 0; d < D; ++d) {
-                const double c = __dsub_rn(xi[(size_t)k * D + d], P[1 + d]);
-                c2 = __dadd_rn(c2, __dmul_rn(c, c));
-            }
-            double g = pref * exp(-c2 / (2.0 * RT));
-            if (amp != 0.0) g *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
-            G = (T)g;
-        } else {
-            float c2 = 0.0f;
-            for (int d = 0; d < D; ++d) {
-                const float c = xi32[(size_t)k * D + d] - U32[d];
-                c2 += c * c;
-            }
-            float g = pref32 * expf(-c2 * i2RT32);
-            if (amp != 0.0) g *= (float)(1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k));
-            G = (T)g;
-        }
+        const T G = (T)maxwell_node<T>(D, m, xi, xi32, k, amp, seed, i);
         fi[k] = G;
-        if (NA == 2) fi[Nvp + k] = (T)((3 - D) * RT) * G;
+        if (NA == 2) fi[Nvp + k] = h0 * G;
     }
 }
 
 // Rykov model: G = g^eq(rho, U, T_t)(1 + amp z_ik), H = (3 - D) R T_t G,
-// R = R T_r G from Wp = (rho, U, T_t, T_r); evaluated in FP64, then stored.
+// R = R T_r G from Wp = (rho, U, T_t, T_r).
 template <typename T>
 __global__ void __launch_bounds__(256) k_maxwell_rk(int D, int NA, int Nv, int Nvp, const double* __restrict__ xi,
-                                                    const double* __restrict__ Wp, double R, double amp,
-                                                    uint64_t seed, T* f)
+                                                    const float* __restrict__ xi32, const double* __restrict__ Wp,
+                                                    double R, double amp, uint64_t seed, T* f)
 {
+    __shared__ MaxwellC m;
+    __shared__ double RTt_s, RTr_s;
     const int i = blockIdx.x;
     T* fi = f + (size_t)i * NA * Nvp;
-    const double* P = Wp + (size_t)i * (D + 3);
-    const double rho = P[0], RTt = R * P[D + 1], RTr = R * P[D + 2];
-    const double pref = rho / pow(2.0 * AVS_PI * RTt, 0.5 * D);
+    if (threadIdx.x == 0) {
+        const double* P = Wp + (size_t)i * (D + 3);
+        RTt_s = R * P[D + 1];
+        RTr_s = R * P[D + 2];
+        maxwell_consts(D, P[0], P + 1, RTt_s, m);
+    }
+    __syncthreads();
+    const double RTt = RTt_s, RTr = RTr_s;
+    const T h0 = (T)((3 - D) * RTt), r0 = (T)RTr;
     for (int k = threadIdx.x; k < Nvp; k += blockDim.x) {
         if (k >= Nv) {
             for (int a = 0; a < NA; ++a) fi[(size_t)a * Nvp + k] = T(0);
             continue;
         }
-        double c2 = 0.0;
-        for (int d = 0; d < D; ++d) {
-            const double c = xi[(size_t)k * D + d] - P[1 + d];
-            c2 += c * c;
+        const double g = maxwell_node<T>(D, m, xi, xi32, k, amp, seed, i);
+        if (sizeof(T) == 8) {
+            fi[k] = (T)g;
+            if (D == 2) fi[Nvp + k] = (T)((3 - D) * RTt * g);
+            fi[(size_t)(NA - 1) * Nvp + k] = (T)(RTr * g);
+        } else {
+            const T G = (T)g;
+            fi[k] = G;
+            if (D == 2) fi[Nvp + k] = h0 * G;
+            fi[(size_t)(NA - 1) * Nvp + k] = r0 * G;
         }
-        double g = pref * exp(-c2 / (2.0 * RTt));
-        if (amp != 0.0) g *= 1.0 + amp * normal_ik(seed, (uint64_t)i, (uint64_t)k);
-        fi[k] = (T)g;
-        if (D == 2) fi[Nvp + k] = (T)((3 - D) * RTt * g);
-        fi[(size_t)(NA - 1) * Nvp + k] = (T)(RTr * g);
     }
 }
 
@@ -297,11 +333,11 @@ cudaError_t launch_maxwell(avs_ctx* c, const double* Wp, int Ncells, double amp,
 {
     if (c->model == AVS_RYKOV) {
         if (f_is_double || !c->mixed)
-            k_maxwell_rk<double><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp,
-                                                                seed, (double*)fout);
+            k_maxwell_rk<double><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, c->xi_f, Wp,
+                                                                c->cfg.R, amp, seed, (double*)fout);
         else
-            k_maxwell_rk<float><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, Wp, c->cfg.R, amp,
-                                                               seed, (float*)fout);
+            k_maxwell_rk<float><<<Ncells, 256, 0, c->stream>>>(c->D, c->NA, c->Nv, Nvp, c->xi_d, c->xi_f, Wp,
+                                                               c->cfg.R, amp, seed, (float*)fout);
         c->launches += 1;
         return cudaGetLastError();
     }

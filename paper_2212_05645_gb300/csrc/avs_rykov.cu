@@ -1177,11 +1177,12 @@ __global__ void __launch_bounds__(RK_NT) rk_moments(int Nv, int Nvp, const T* __
 // times; the largest remaining relative gap into *gap_key.
 template <int D, typename T>
 __global__ void __launch_bounds__(RK_NT) rk_correct(int Nv, int Nvp, T* f, const double* __restrict__ xi,
-                                                    const double* __restrict__ w, const double* __restrict__ Wt,
+                                                    const double* __restrict__ w, const float* __restrict__ xif,
+                                                    const float* __restrict__ wf, const double* __restrict__ Wt,
                                                     RkGas g, int iters, unsigned long long* gap_key)
 {
-    constexpr int NA = RkNA<D>::v, NW = D + 3;
-    __shared__ double sred[(RK_NT / 32) * 6], sout[6];
+    constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
+    __shared__ double sred[(RK_NT / 32) * NR], sout[NR];
     __shared__ RkEq<T> ea, eb;
     const int i = blockIdx.x;
     T* fi = f + (size_t)i * NA * Nvp;
@@ -1191,9 +1192,32 @@ __global__ void __launch_bounds__(RK_NT) rk_correct(int Nv, int Nvp, T* f, const
     double rho, U[3], RTt, RTr, RT;
     rk_prim<D>(Wi, rho, U, RTt, RTr, RT);
     if (threadIdx.x == 0) ea = rk_make<D, T>(g, rho, U, RTt, RTr, z, z);
+    // mixed form: the moments as FP32 raw sums about V = U(W~) with an FP64
+    // combine (the monatomic correction's scheme), the nodes in FP32
+    float V[3];
+    rk_vref<D>(Wi, V);
+    const double Vd[3] = {V[0], V[1], V[2]};
     for (int it = 0; it <= iters; ++it) {
         double Wp[NW];
-        rk_cell_mom<D, T>(fi, Nv, Nvp, xi, w, Wp, nullptr, nullptr, sred, sout);
+        if constexpr (sizeof(T) == 4) {
+            float acc[NR];
+#pragma unroll
+            for (int m = 0; m < NR; ++m) acc[m] = 0.0f;
+            for (int k = threadIdx.x; k < Nv; k += RK_NT) {
+                float c[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) c[d] = xif[(size_t)k * D + d] - V[d];
+                const float wk = wf[k];
+                rk_raw_acc<D>(acc, c, wk * fi[k], D == 2 ? wk * fi[Nvp + k] : 0.0f, wk * fi[(size_t)(NA - 1) * Nvp + k]);
+            }
+            block_sum_t<NR, RK_NT>(acc, sred, sout);
+            if (threadIdx.x == 0) {
+                double qd[3], rd[3];
+                rk_from_raw<D>(sout, Vd, Wp, qd, rd);
+            }
+        } else {
+            rk_cell_mom<D, T>(fi, Nv, Nvp, xi, w, Wp, nullptr, nullptr, sred, sout);
+        }
         if (it == iters) {
             if (threadIdx.x == 0) {
                 double mref = 0.0;
@@ -1216,7 +1240,7 @@ __global__ void __launch_bounds__(RK_NT) rk_correct(int Nv, int Nvp, T* f, const
         for (int k = threadIdx.x; k < Nv; k += RK_NT) {
             T xt[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) xt[d] = (T)xi[(size_t)k * D + d];
+            for (int d = 0; d < D; ++d) xt[d] = sizeof(T) == 4 ? (T)xif[(size_t)k * D + d] : (T)xi[(size_t)k * D + d];
             T va[NA], vb[NA];
             rk_eval<D, T>(ea, xt, va);
             rk_eval<D, T>(eb, xt, vb);
@@ -1965,14 +1989,14 @@ cudaError_t rk_launch_correct(avs_ctx* c, void* f, const double* Wtarget, int it
     const RkGas g = rk_gas(c);
     if (c->D == 2) {
         if (c->mixed) rk_correct<2, float><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_d, c->w_d,
-                                                                           Wtarget, g, iters, gk);
+                                                                           c->xi_f, c->w_f, Wtarget, g, iters, gk);
         else rk_correct<2, double><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d, c->w_d,
-                                                                   Wtarget, g, iters, gk);
+                                                                   c->xi_f, c->w_f, Wtarget, g, iters, gk);
     } else {
         if (c->mixed) rk_correct<3, float><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (float*)f, c->xi_d, c->w_d,
-                                                                           Wtarget, g, iters, gk);
+                                                                           c->xi_f, c->w_f, Wtarget, g, iters, gk);
         else rk_correct<3, double><<<c->Nc, RK_NT, 0, c->stream>>>(c->Nv, c->Nvp, (double*)f, c->xi_d, c->w_d,
-                                                                   Wtarget, g, iters, gk);
+                                                                   c->xi_f, c->w_f, Wtarget, g, iters, gk);
     }
     c->launches += 1;
     return cudaGetLastError();
