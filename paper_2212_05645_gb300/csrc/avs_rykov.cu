@@ -1477,6 +1477,113 @@ __global__ void __launch_bounds__(NT) rk_imp_macro(RkImpP<A> P, int k_macro, int
                     rk_imp_cell<D, A>(P, q);
             }
 }
+// rk_imp_res for the mixed form: the raw moments of f^n and the residual
+// RK_VC nodes per thread in vector loads (the cell kernel's layout), the
+// state of W~ by thread 0 (FP64 W~, FP32 tau~ and equilibrium).
+template <int D>
+__global__ void __launch_bounds__(RK_NT, 7) rk_imp_res32(RkP<float> P, const float* __restrict__ xif,
+                                                         const float* __restrict__ wf, double* u0)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v, V = RK_VC;
+    __shared__ double sw[(RK_NT / 32) * NR], red[NR];
+    __shared__ RkEq<float> eq;
+    __shared__ float ctau, cvol, cV[3];
+    __shared__ double Vd[3];
+    __shared__ int fs[AVS_MAXS];
+    __shared__ float sg[AVS_MAXS];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x;
+    const int ns = P.nslot[i];
+    const int Nv = P.Nv, Nvp = P.Nvp;
+    if (tid < ns) {
+        const int sl = P.slot[i * AVS_MAXS + tid];
+        fs[tid] = sl >> 1;
+        sg[tid] = (sl & 1) ? -1.0f : 1.0f;
+    }
+    if (tid == 32) {
+        rk_vref<D>(P.Win + (size_t)i * NW, cV);
+        for (int d = 0; d < 3; ++d) Vd[d] = cV[d];
+        cvol = (float)P.vol[i];
+    }
+    __syncthreads();
+    const size_t cs = (size_t)NA * Nvp;
+    const float* fi = P.f + (size_t)i * cs;
+    float Vr[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) Vr[d] = cV[d];
+    float acc[NR];
+#pragma unroll
+    for (int m = 0; m < NR; ++m) acc[m] = 0.0f;
+    for (int k0 = tid * V; k0 < Nv; k0 += RK_NT * V) {
+        float x[V][D], wv[V], fv[NA][V];
+        rk_ld_nodes<D>(xif, wf, k0, x, wv);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) rk_ldv(fi + (size_t)a * Nvp + k0, fv[a]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float c[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) c[d] = x[v][d] - Vr[d];
+            rk_raw_acc<D>(acc, c, wv[v] * fv[0][v], D == 2 ? wv[v] * fv[1][v] : 0.0f, wv[v] * fv[NA - 1][v]);
+        }
+    }
+    block_sum_t<NR, RK_NT>(acc, sw, red);
+    if (tid == 0) {
+        float rn, Un[3], etn, r0n, qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+        rk_state_raw32<D>(red, Vd, rn, Un, etn, r0n, qt, qr);
+        double rho, U[3], RTt, RTr, RT;
+        rk_prim<D>(P.Wout + (size_t)i * NW, rho, U, RTt, RTr, RT);
+        if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
+        const float tau = rk_tau32(P.g, (float)rho, (float)RTt);
+        float Uf[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) Uf[d] = (float)U[d];
+        eq = rk_make32<D>(P.g, (float)rho, Uf, (float)RTt, (float)RTr, qt, qr);
+        ctau = tau;
+        u0[i] = P.vol[i] / P.dt + P.vol[i] / (double)tau;
+    }
+    __syncthreads();
+    const float Vc = cvol, vit = cvol / ctau;
+    float* ro = P.fout + (size_t)i * cs;
+    for (int k0 = tid * V; k0 < Nv; k0 += RK_NT * V) {
+        float x[V][D], wv[V], fv[NA][V], Nn[NA][V];
+        rk_ld_nodes<D>(xif, wf, k0, x, wv);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            rk_ldv(fi + (size_t)a * Nvp + k0, fv[a]);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Nn[a][v] = 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < AVS_MAXS; ++q) {
+            if (q >= ns) break;
+            const float* Fq = P.FX + (size_t)fs[q] * cs + k0;
+            const float g = sg[q];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                float t[V];
+                rk_ldv(Fq + (size_t)a * Nvp, t);
+#pragma unroll
+                for (int v = 0; v < V; ++v) Nn[a][v] += g * t[v];
+            }
+        }
+        float out[NA][V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float gv[NA];
+            rk_eval<D, float>(eq, x[v], gv);
+            const bool real = k0 + v < Nv;
+#pragma unroll
+            for (int a = 0; a < NA; ++a) out[a][v] = real ? (gv[a] - fv[a][v]) * vit - Nn[a][v] : 0.0f;
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) rk_stv(ro + (size_t)a * Nvp + k0, out[a]);
+    }
+    for (int k = ((Nv + V - 1) / V) * V + tid; k < Nvp; k += RK_NT)
+#pragma unroll
+        for (int a = 0; a < NA; ++a) ro[(size_t)a * Nvp + k] = 0.0f;
+    (void)Vc;
+}
+
 // Per cell: Rykov state of W~ with the lagged q_t, q_r of f^n, and the
 // microscopic residual Res = V (g~ - phi^n) / tau~ - N of every array (written
 // over the f^{n+1} buffer); u0[i] = V/dt + V/tau~ for the sweeps.
@@ -1484,12 +1591,11 @@ template <int D, typename T>
 __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restrict__ xiT,
                                                     const T* __restrict__ wT, double* u0)
 {
-    constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v;
+    static_assert(sizeof(T) == 8, "the mixed form uses rk_imp_res32");
+    constexpr int NA = RkNA<D>::v, NW = D + 3;
     __shared__ double sred[(RK_NT / 32) * RkNR<3>::v], sout[RkNR<3>::v];
     __shared__ RkEq<T> eq;
     __shared__ double tau_s;
-    __shared__ float ctau, cvol, cV[3];
-    __shared__ double Vd[3];
     __shared__ int fs[AVS_MAXS];
     __shared__ T sg[AVS_MAXS];
     const int i = blockIdx.x;
@@ -1503,47 +1609,7 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
     const size_t cs = (size_t)NA * Nvp;
     const T* fi = P.f + (size_t)i * cs;
     double qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
-    if constexpr (sizeof(T) == 4) {
-        const double* Wi = P.Win + (size_t)i * NW;
-        if (threadIdx.x == 32) {
-            // reference velocity of the sums in FP32, converted once (Vd exact)
-            const float irW = 1.0f / (float)Wi[0];
-            for (int d = 0; d < 3; ++d) {
-                cV[d] = d < D ? (float)Wi[1 + d] * irW : 0.0f;
-                Vd[d] = (double)cV[d];
-            }
-            cvol = (float)P.vol[i];
-        }
-        __syncthreads();
-        T V[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) V[d] = cV[d];
-        T racc[NR];
-#pragma unroll
-        for (int m = 0; m < NR; ++m) racc[m] = T(0);
-        for (int k = threadIdx.x; k < Nv; k += RK_NT) {
-            T c[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) c[d] = xiT[(size_t)k * D + d] - V[d];
-            const T wk = wT[k];
-            rk_raw_acc<D>(racc, c, wk * fi[k], D == 2 ? wk * fi[Nvp + k] : T(0), wk * fi[(size_t)(NA - 1) * Nvp + k]);
-        }
-        block_sum_t<NR, RK_NT>(racc, sred, sout);
-        if (threadIdx.x == 0) {
-            // heat fluxes of f, tau and the equilibrium in FP32; the state W~ in FP64
-            float rn, Un[3] = {0, 0, 0}, etn, r0n, qtf[3] = {0, 0, 0}, qrf[3] = {0, 0, 0};
-            rk_state_raw32<D>(sout, Vd, rn, Un, etn, r0n, qtf, qrf);
-            double rho, U[3], RTt, RTr, RT;
-            rk_prim<D>(P.Wout + (size_t)i * NW, rho, U, RTt, RTr, RT);
-            if (!(rho > 0.0) || !(RTt > 0.0) || !(RT > 0.0)) atomicOr(P.err, 1);
-            const float tau = rk_tau32(P.g, (float)rho, (float)RTt);
-            float Uf[3] = {0, 0, 0};
-            for (int d = 0; d < D; ++d) Uf[d] = (float)U[d];
-            eq = rk_make32<D>(P.g, (float)rho, Uf, (float)RTt, (float)RTr, qtf, qrf);
-            ctau = tau;
-            u0[i] = P.vol[i] / P.dt + P.vol[i] / (double)tau;
-        }
-    } else {
+    {
         double Wn[NW];
         rk_cell_mom<D, T>(fi, Nv, Nvp, P.xi, P.w, Wn, qt, qr, sred, sout);
         if (threadIdx.x == 0) {
@@ -1557,9 +1623,7 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
         }
     }
     __syncthreads();
-    // Vc / tau: FP32 reciprocal in the mixed form, the FP64 division otherwise
-    const T tau = sizeof(T) == 4 ? (T)ctau : (T)tau_s, Vc = sizeof(T) == 4 ? (T)cvol : (T)P.vol[i];
-    const T itau = T(1) / tau;
+    const T tau = (T)tau_s, Vc = (T)P.vol[i];
     T* ro = P.fout + (size_t)i * cs;
     for (int k = threadIdx.x; k < Nvp; k += RK_NT) {
         if (k >= Nv) {
@@ -1576,8 +1640,7 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_res(RkP<T> P, const T* __restric
         for (int a = 0; a < NA; ++a) {
             T N = T(0);
             for (int q = 0; q < ns; ++q) N += sg[q] * P.FX[((size_t)fs[q] * NA + a) * Nvp + k];
-            ro[(size_t)a * Nvp + k] = sizeof(T) == 4 ? Vc * (gv[a] - fi[(size_t)a * Nvp + k]) * itau - N
-                                                     : Vc * (gv[a] - fi[(size_t)a * Nvp + k]) / tau - N;
+            ro[(size_t)a * Nvp + k] = Vc * (gv[a] - fi[(size_t)a * Nvp + k]) / tau - N;
         }
     }
 }
@@ -1593,8 +1656,8 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_micro(int Nv, int Nvp, const T* 
                                                       const int* __restrict__ faceL, const int* __restrict__ faceR,
                                                       const int* __restrict__ clist, int c0)
 {
+    static_assert(sizeof(T) == 8, "the mixed form uses rk_imp_micro32");
     constexpr int NA = RkNA<D>::v;
-    __shared__ T sA[AVS_MAXS][D];
     __shared__ double sAd[AVS_MAXS][3];
     __shared__ int snb[AVS_MAXS];
     const int i = clist[c0 + blockIdx.x];
@@ -1602,10 +1665,7 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_micro(int Nv, int Nvp, const T* 
     if (threadIdx.x < ns) {
         const int sl = slot[i * AVS_MAXS + threadIdx.x];
         const int f = sl >> 1;
-        for (int d = 0; d < D; ++d) {
-            sA[threadIdx.x][d] = (sl & 1) ? -An[(size_t)f * D + d] : An[(size_t)f * D + d];
-            sAd[threadIdx.x][d] = (sl & 1) ? -Ad[(size_t)f * D + d] : Ad[(size_t)f * D + d];
-        }
+        for (int d = 0; d < D; ++d) sAd[threadIdx.x][d] = (sl & 1) ? -Ad[(size_t)f * D + d] : Ad[(size_t)f * D + d];
         snb[threadIdx.x] = (sl & 1) ? faceL[f] : faceR[f];
     }
     __syncthreads();
@@ -1615,20 +1675,13 @@ __global__ void __launch_bounds__(RK_NT) rk_imp_micro(int Nv, int Nvp, const T* 
         for (int a = 0; a < NA; ++a) dphi[((size_t)i * NA + a) * Nvp + k] = T(0);
         return;
     }
-    // xi . n per slot: FP64 without contraction in the FP64 form (the oracle's
-    // upwind split), the element type otherwise
+    // xi . n per slot in FP64 without contraction (the oracle's upwind split)
     T sn[AVS_MAXS];
     T out = T(0);
     for (int s = 0; s < ns; ++s) {
-        T v;
-        if constexpr (sizeof(T) == 8) {
-            double xd[3] = {0, 0, 0};
-            for (int d = 0; d < D; ++d) xd[d] = xid[(size_t)k * D + d];
-            v = (T)dot_rn<D>(xd, sAd[s]);
-        } else {
-            v = T(0);
-            for (int d = 0; d < D; ++d) v += xiT[(size_t)k * D + d] * sA[s][d];
-        }
+        double xd[3] = {0, 0, 0};
+        for (int d = 0; d < D; ++d) xd[d] = xid[(size_t)k * D + d];
+        const T v = (T)dot_rn<D>(xd, sAd[s]);
         sn[s] = v;
         if (v >= T(0)) out += v;
     }
@@ -1905,8 +1958,10 @@ cudaError_t rk_step_implicit_t(avs_ctx* c, const void* fin, void* fout, const do
     P.Wout = Wout;                      // W~
     P.fout = (T*)fout;                  // holds the residual until the finish
     double* u0 = c->imp_diag;           // the macroscopic diagonal is no longer needed
-    rk_imp_res<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P, f32 ? (const T*)c->xi_f : (const T*)c->xi_d,
-                                                     f32 ? (const T*)c->w_f : (const T*)c->w_d, u0);
+    if constexpr (sizeof(T) == 4)
+        rk_imp_res32<D><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_f, c->w_f, u0);
+    else
+        rk_imp_res<D, T><<<c->Nc, RK_NT, 0, c->stream>>>(P, c->xi_d, c->w_d, u0);
     c->launches += 1;
     T* dphi = (T*)c->flux;              // the face flux has been used
     e = cudaMemsetAsync(dphi, 0, (size_t)c->Nc * NA * c->Nvp * sizeof(T), c->stream);
@@ -1920,12 +1975,13 @@ cudaError_t rk_step_implicit_t(avs_ctx* c, const void* fin, void* fout, const do
                 if (col == prev) continue;      // same inputs as the pass before: same values
                 prev = col;
                 const int c0 = c->cstart[col], c1 = c->cstart[col + 1];
-                if (c1 > c0 && f32) {
+                if (c1 <= c0) continue;
+                if constexpr (sizeof(T) == 4) {
                     rk_imp_micro32<D><<<dim3(c1 - c0, (c->Nv + RK_NT * 4 - 1) / (RK_NT * 4)), RK_NT, 0, c->stream>>>(
                         c->Nv, c->Nvp, (const float*)fout, (float*)dphi, u0, c->xi_f, c->An_f, c->slot, c->nslot,
                         c->faceL, c->faceR, c->clist, c0);
                     c->launches += 1;
-                } else if (c1 > c0) {
+                } else {
                     rk_imp_micro<D, T><<<dim3(c1 - c0, nyb), 128, 0, c->stream>>>(
                         c->Nv, c->Nvp, (const T*)fout, dphi, u0, f32 ? (const T*)c->xi_f : (const T*)c->xi_d,
                         c->xi_d, c->An_d, f32 ? (const T*)c->An_f : (const T*)c->An_d, c->slot, c->nslot, c->faceL,

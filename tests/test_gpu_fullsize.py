@@ -86,3 +86,46 @@ def test_full_sphere_mixed_properties():
         outs.append(g.moments()[0])
         g.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_cylinder_implicit_one_step_all_cells(precision):
+    """The implicit step (IUGKS at CFL 0.8, 60 macroscopic and 2 microscopic
+    sweeps, as `bench.py --implicit 0.8` runs it) on the full cylinder, every
+    cell against the oracle: FP64 within 1e-12, mixed fields within 1e-5."""
+    avs = need_gpu()
+    w = wl.cylinder(precision=precision)
+    r, g = pair(w, avs, precision=None if precision == "fp64" else precision, amp=1e-3)
+    dt = r.dt(0.8)
+    r.step_implicit(dt)
+    g.step_implicit(1, dt=dt)
+    if precision == "fp64":
+        assert rel_err(g.moments()[0], r.Wc) < 1e-12
+        assert rel_err(g.get_f(), r.f) < 1e-12
+    else:
+        e = field_err(g.moments()[0], r.Wc, 2)
+        assert max(e.values()) < 1e-5, e
+    g.close()
+
+
+def test_full_rykov_cylinder_implicit_mixed_all_cells():
+    """The Rykov model's implicit step on the full cylinder (mixed form, as
+    `bench.py --workload cylinder-rykov --implicit 0.8` runs it): all fields,
+    the rotational energy included, within 1e-5 of the oracle."""
+    avs = need_gpu()
+    w = wl.cylinder(precision="mixed")
+    w.model = "rykov"
+    r = O.Run(w)
+    g = avs.AVS(w, precision="mixed")
+    Wp = np.column_stack([w.W_init, 0.8 * w.W_init[:, 3]])
+    r.init_field(Wp, amp=1e-3, seed=3)
+    g.set_f(r.f)
+    g.set_W(r.Wc)
+    dt = r.dt(0.8)
+    r.step_implicit(dt)
+    g.step_implicit(1, dt=dt)
+    Wg = g.moments()[0]
+    e = field_err(Wg, r.Wc, 2)
+    assert max(e.values()) < 1e-5, e
+    assert float((np.abs(Wg[:, 4] - r.Wc[:, 4]) / np.abs(r.Wc[:, 3])).max()) < 1e-5
+    g.close()
