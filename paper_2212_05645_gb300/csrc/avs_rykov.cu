@@ -199,6 +199,7 @@ struct RkP {
     int Nv, Nvp, Nc, limiter;
     double dt, h;
     RkGas g;
+    const int* order;         // face processing order (by lower cell index: neighbouring faces share L2 rows)
     const int* faceL;
     const int* faceR;
     const double* An;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(RK_NT) rk_face(RkP<T> P)
     __shared__ double sred[(RK_NT / 32) * 6], sout[6];
     __shared__ RkEq<T> eq;
     __shared__ double blend[2];
-    const int f = blockIdx.x;
+    const int f = P.order[blockIdx.x];
     const int L = P.faceL[f], R = P.faceR[f];
     const int Nv = P.Nv, Nvp = P.Nvp;
     double An[3] = {0, 0, 0}, rl[3] = {0, 0, 0}, rr[3] = {0, 0, 0};
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(RK_NT, D == 2 ? 8 : 7) rk_face32(RkP<float> P,
     __shared__ float cAf[3], crl[3], crr[3], cV[3], cUb[3], cpw, ci2b, ch;
     __shared__ double An[3], Vd[3], cRTb, crb;
     __shared__ int cbt;
-    const int f = blockIdx.x;
+    const int f = P.order[blockIdx.x];
     const int L = P.faceL[f], R = P.faceR[f];
     const int Nv = P.Nv, Nvp = P.Nvp;
     if (threadIdx.x == 0) {
@@ -1841,6 +1842,7 @@ cudaError_t rk_face_stage(avs_ctx* c, const void* fin, const double* Win, double
     P.dt = dt;
     P.h = 0.5 * dt;
     P.g = rk_gas(c);
+    P.order = c->forder;
     P.faceL = c->faceL;
     P.faceR = c->faceR;
     P.An = c->An_d;
