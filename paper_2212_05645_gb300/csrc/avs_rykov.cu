@@ -2019,20 +2019,79 @@ cudaError_t rk_launch_step_implicit(avs_ctx* c, const void* fin, void* fout, con
                     : rk_step_implicit_t<3, double>(c, fin, fout, Win, Wout, dt, k_macro, k_micro);
 }
 
+// W and the total heat flux of every cell in the mixed form: FP32 raw sums
+// about the carried velocity (when given) with an FP64 combine, converted by
+// the shift formulas (the monatomic moments' scheme; FP64 node sums cost as
+// much as the rest of an adaptation).
+template <int D>
+__global__ void __launch_bounds__(RK_NT) rk_moments32(int Nv, int Nvp, const float* __restrict__ f,
+                                                      const float* __restrict__ xif, const float* __restrict__ wf,
+                                                      const double* __restrict__ Wref, double* Wout, double* qout)
+{
+    constexpr int NA = RkNA<D>::v, NW = D + 3, NR = RkNR<D>::v, V = RK_VC;
+    __shared__ double sw[(RK_NT / 32) * NR], red[NR];
+    __shared__ float cV[3];
+    __shared__ double Vd[3];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x;
+    if (tid == 32) {
+        cV[0] = cV[1] = cV[2] = 0.0f;
+        if (Wref && Wref[(size_t)i * NW] > 0.0) {
+            rk_vref<D>(Wref + (size_t)i * NW, cV);
+            for (int d = 0; d < 3; ++d)
+                if (!isfinite(cV[d])) cV[d] = 0.0f;
+        }
+        for (int d = 0; d < 3; ++d) Vd[d] = cV[d];
+    }
+    __syncthreads();
+    float Vr[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) Vr[d] = cV[d];
+    const float* fi = f + (size_t)i * NA * Nvp;
+    float acc[NR];
+#pragma unroll
+    for (int m = 0; m < NR; ++m) acc[m] = 0.0f;
+    for (int k0 = tid * V; k0 < Nv; k0 += RK_NT * V) {
+        float x[V][D], wv[V], fv[NA][V];
+        rk_ld_nodes<D>(xif, wf, k0, x, wv);
+#pragma unroll
+        for (int a = 0; a < NA; ++a) rk_ldv(fi + (size_t)a * Nvp + k0, fv[a]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            float c[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) c[d] = x[v][d] - Vr[d];
+            rk_raw_acc<D>(acc, c, wv[v] * fv[0][v], D == 2 ? wv[v] * fv[1][v] : 0.0f, wv[v] * fv[NA - 1][v]);
+        }
+    }
+    block_sum_t<NR, RK_NT>(acc, sw, red);
+    if (tid == 0) {
+        double W[NW], qt[3] = {0, 0, 0}, qr[3] = {0, 0, 0};
+        rk_from_raw<D>(red, Vd, W, qt, qr);
+        if (Wout)
+            for (int m = 0; m < NW; ++m) Wout[(size_t)i * NW + m] = W[m];
+        if (qout)
+            for (int d = 0; d < D; ++d) qout[(size_t)i * D + d] = qt[d] + qr[d];
+    }
+}
+
 cudaError_t rk_launch_moments(avs_ctx* c, const void* f, int f_is_double, int Ncells, int Nvp, double* Wout,
                               double* qout)
 {
     const bool dbl = f_is_double || !c->mixed;
+    // the carried W as the reference velocity of the sums, unless it is the
+    // output (the initial field, whose carried W is being formed)
+    const double* Wref = (Ncells == c->Nc && Wout != c->W[c->wcur]) ? c->W[c->wcur] : nullptr;
     if (c->D == 2) {
         if (dbl) rk_moments<2, double><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const double*)f, c->xi_d,
                                                                         c->w_d, Wout, qout);
-        else rk_moments<2, float><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const float*)f, c->xi_d, c->w_d,
-                                                                   Wout, qout);
+        else rk_moments32<2><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const float*)f, c->xi_f, c->w_f, Wref,
+                                                              Wout, qout);
     } else {
         if (dbl) rk_moments<3, double><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const double*)f, c->xi_d,
                                                                         c->w_d, Wout, qout);
-        else rk_moments<3, float><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const float*)f, c->xi_d, c->w_d,
-                                                                   Wout, qout);
+        else rk_moments32<3><<<Ncells, RK_NT, 0, c->stream>>>(c->Nv, Nvp, (const float*)f, c->xi_f, c->w_f, Wref,
+                                                              Wout, qout);
     }
     c->launches += 1;
     return cudaGetLastError();
