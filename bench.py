@@ -377,7 +377,9 @@ def run_gpu(args):
     if rank == 0 or ws > 1:
         Wp = torch.from_numpy(np.ascontiguousarray(w.W_init)).pin_memory()
         Wout = torch.zeros((Nc, w.D + 2), dtype=torch.float64).pin_memory()
-        ke = max(2, args.steps // 2)
+        # whole cycles of the proposer (a full criterion every 4th adaptation),
+        # so the mix of full and learned adaptations is the long-run one
+        ke = 4 * max(1, -(-args.steps // 4))
         torch.cuda.synchronize()
         e_upd = []
         te0 = time.perf_counter()
