@@ -376,10 +376,13 @@ def run_gpu(args):
     e2e = None
     if rank == 0 or ws > 1:
         Wp = torch.from_numpy(np.ascontiguousarray(w.W_init)).pin_memory()
-        Wout = torch.zeros((Nc, w.D + 2), dtype=torch.float64).pin_memory()
-        # whole cycles of the proposer (a full criterion every 4th adaptation),
-        # so the mix of full and learned adaptations is the long-run one
-        ke = 4 * max(1, -(-args.steps // 4))
+        Wout = torch.zeros((Nc, g.NW), dtype=torch.float64).pin_memory()   # D + 2, or D + 3 (Rykov)
+        # the same number of steps as the timed region, started at the same
+        # phase of the proposer's cycle (a full criterion every 4th adaptation):
+        # untimed steps first bring the adaptation counter back to that phase
+        for _ in range((-args.steps) % 4):
+            bench_step(g, [])
+        ke = args.steps
         torch.cuda.synchronize()
         e_upd = []
         te0 = time.perf_counter()

@@ -140,6 +140,20 @@ def _ptr(a):
     return a.data_ptr(), int(a.is_cuda)
 
 
+def _check_buf(a, n, name):
+    """Reject a buffer that is not at least n contiguous float64 values (the
+    library reads or writes n values through its pointer)."""
+    if a is None:
+        return
+    if _is_torch(a):
+        import torch
+        ok = a.dtype == torch.float64 and a.is_contiguous() and a.numel() >= n
+    else:
+        ok = isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.size >= n
+    if not ok:
+        raise ValueError(f"{name}: need a contiguous float64 buffer of at least {n} values")
+
+
 def _cur_stream():
     try:
         import torch
@@ -242,6 +256,7 @@ class AVS:
                 Wp = torch.cat([Wp, Wp[:, self.D + 1:self.D + 2]], dim=1).contiguous()
             else:
                 Wp = np.ascontiguousarray(np.concatenate([Wp, Wp[:, self.D + 1:self.D + 2]], axis=1))
+        _check_buf(Wp, self.Nc * self.NW, "Wp")
         p, dev = _ptr(Wp)
         self._ck(self.L.avs_init_field(self.h, p, dev, float(amp), int(seed)))
 
@@ -277,6 +292,7 @@ class AVS:
         keep = None
         if W_override is not None:
             keep = W_override if _is_torch(W_override) else np.ascontiguousarray(W_override, np.float64)
+            _check_buf(keep, self.Nc * self.NW, "W_override")
             p, dev = _ptr(keep)
             o.W_override = p
             o.W_is_device = dev
@@ -292,8 +308,12 @@ class AVS:
         if out_W is None and out_q is None:
             out_W = np.zeros((self.Nc, self.NW))
             out_q = np.zeros((self.Nc, self.D))
+        _check_buf(out_W, self.Nc * self.NW, "out_W")
+        _check_buf(out_q, self.Nc * self.D, "out_q")
         pW, dW = _ptr(out_W)
         pq, dq = _ptr(out_q)
+        if out_W is not None and out_q is not None and dW != dq:
+            raise ValueError("out_W and out_q: both on the host or both on the device")
         self._ck(self.L.avs_moments(self.h, pW, pq, dW or dq))
         return out_W, out_q
 
@@ -304,12 +324,14 @@ class AVS:
 
     def set_W(self, Wc):
         Wc = np.ascontiguousarray(Wc, np.float64)
+        _check_buf(Wc, self.Nc * self.NW, "Wc")
         self._ck(self.L.avs_set_W(self.h, Wc.ctypes.data, 0))
 
     def criterion(self, Wc=None):
         M = np.zeros(self.Nv)
         if Wc is not None:
             Wc = np.ascontiguousarray(Wc, np.float64)
+            _check_buf(Wc, self.Nc * self.NW, "Wc")
         self._ck(self.L.avs_criterion(self.h, None if Wc is None else Wc.ctypes.data, 0, M.ctypes.data, 0))
         return M
 
@@ -327,6 +349,7 @@ class AVS:
     def get_f(self, out=None):
         if out is None:
             out = np.zeros((self.Nc, self.NA, self.Nv))
+        _check_buf(out, self.Nc * self.NA * self.Nv, "out")
         p, dev = _ptr(out)
         self._ck(self.L.avs_get_f(self.h, p, dev))
         return out
@@ -343,6 +366,7 @@ class AVS:
         if not _is_torch(f):
             f = np.ascontiguousarray(f, np.float64)
             assert f.shape == (self.Nc, self.NA, self.Nv), f.shape
+        _check_buf(f, self.Nc * self.NA * self.Nv, "f")
         p, dev = _ptr(f)
         self._ck(self.L.avs_set_f(self.h, p, dev))
 

@@ -101,3 +101,20 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(avs, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         avs.load()
+
+
+def test_binding_rejects_short_or_mistyped_buffers():
+    """The binding checks every buffer it hands to the library for length,
+    element type and contiguity before the call (the library reads or writes
+    that many values through the pointer)."""
+    import numpy as np
+    import torch
+    from paper_2212_05645_gb300.avs import _check_buf
+    _check_buf(np.zeros((4, 5)), 20, "W")
+    _check_buf(torch.zeros(20, dtype=torch.float64), 20, "W")
+    _check_buf(None, 20, "W")
+    for bad in (np.zeros((4, 4)), np.zeros((4, 5), np.float32), np.zeros((5, 4)).T,
+                torch.zeros(19, dtype=torch.float64), torch.zeros(20, dtype=torch.float32),
+                torch.zeros((5, 8), dtype=torch.float64)[:, :4], [0.0] * 20):
+        with pytest.raises(ValueError):
+            _check_buf(bad, 20, "W")
