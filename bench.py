@@ -377,27 +377,30 @@ def run_gpu(args):
     if rank == 0 or ws > 1:
         Wp = torch.from_numpy(np.ascontiguousarray(w.W_init)).pin_memory()
         Wout = torch.zeros((Nc, g.NW), dtype=torch.float64).pin_memory()   # D + 2, or D + 3 (Rykov)
-        # the same number of steps as the timed region, started at the same
-        # phase of the proposer's cycle (a full criterion every 4th adaptation):
-        # untimed steps first bring the adaptation counter back to that phase
-        for _ in range((-args.steps) % 4):
-            bench_step(g, [])
+        # a fresh context through the same warm-up, so that the timed steps see
+        # the same sequence of velocity meshes and of full and learned
+        # adaptations as the device-timed ones
+        ge = A.AVS(w, precision="mixed", stream=stream.cuda_stream, learned=learned, full_every=4)
+        for _ in range(args.warmup):
+            bench_step(ge, [])
         ke = args.steps
         torch.cuda.synchronize()
         e_upd = []
         te0 = time.perf_counter()
         for j in range(ke):
             if flush is not None:     # the same cold L2 as the device-timed steps
-                flush.fill_((j + 7) & 255)
-            g.init_field(Wp)          # h2d of the step's input W
-            advance(g)
-            e_upd.append(Nc * g.Nv * nu)
-            g.adapt()
-            g.moments(out_W=Wout)     # d2h of the step's result
+                flush.fill_(j & 255)
+            ge.init_field(Wp)         # h2d of the step's input W
+            advance(ge)
+            e_upd.append(Nc * ge.Nv * nu)
+            ge.adapt()
+            ge.moments(out_W=Wout)    # d2h of the step's result
         torch.cuda.synchronize()
         te = time.perf_counter() - te0
+        ge.close()
         e2e = {"value": sum(e_upd) / te, "unit": UNIT, "h2d_bytes_per_step": int(Wp.numel() * 8),
-               "d2h_bytes_per_step": int(Wout.numel() * 8)}
+               "d2h_bytes_per_step": int(Wout.numel() * 8), "steps": ke,
+               "velocity_nodes": [int(u // (Nc * nu)) for u in e_upd]}
 
     # plain FP64 GPU form on the same workload (same definition of a step)
     fp64 = None
@@ -446,7 +449,8 @@ def run_gpu(args):
                 "adaptation": {"full": sum(a["full"] for a in astats), "learned": sum(1 - a["full"] for a in astats),
                                "mean_checked_cells": statistics.mean(a["checked_cells"] for a in astats),
                                "missed_nodes_on_full_steps": [a["missed_nodes"] for a in astats if a["full"]],
-                               "nodes": [a["Nv"] for a in astats]},
+                               "nodes": [a["Nv"] for a in astats],
+                               "step_velocity_nodes": [int(c // Nc) for c in step_cells]},
                 "speedup_vs_fp64_form": (value / ws / fp64["value"]) if fp64 else None}
         print(json.dumps(line), flush=True)
     g.close()
