@@ -13,6 +13,7 @@
 #define AVS_NT 256            // threads per block of the per-cell kernels
 #define AVS_CELLPAR_BYTES 256 // bytes per cell of the collision parameters (CellPar)
 #define AVS_CMOM_MAX 17       // carried raw moments per cell (monatomic 11 / 13, Rykov 14 / 17)
+#define AVS_SMALL_NV 256      // velocity meshes up to this size: one warp per face / cell in the mixed step
 #define AVS_IMPSLOT_BYTES 96  // bytes per slot record of the implicit macroscopic sweep
 
 // Refinement caps of the velocity nodes (Sec. 3.5), passed to kernels by value.

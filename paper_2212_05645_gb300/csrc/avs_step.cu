@@ -24,6 +24,7 @@
 // the step; no block waits on another.  Sums: per-thread and warp sums in the
 // element type, FP64 across warps and in every per-cell / per-face formula.
 #include <algorithm>
+#include <type_traits>
 
 #include "avs_dev.cuh"
 #include "avs_internal.h"
@@ -363,7 +364,7 @@ struct FaceSt {
 //      (xi . An) phi_ij and the flux moments sum_k w (xi . An) psi phi_ij;
 //      boundary: outgoing foot value / incoming Maxwellian.
 template <int D, typename T, int NT, bool CACHE, int VF>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4) k_face(FaceP<D, T> P)
+__global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4)) k_face(FaceP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
     constexpr int NR = (NM > 2 * NW) ? NM : 2 * NW;
@@ -804,7 +805,7 @@ __global__ void k_cell_state(CellP<D, T> P)
 // raw moments of the new f about U(W~) are summed on the way for the next
 // step (same nodes per thread and order as k_raw_moments).
 template <int D, typename T, int NT, int VC>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4) ? (VC == 4 ? 7 : 7) : 4) k_cell(CellP<D, T> P)
+__global__ void __launch_bounds__(NT, NT == 32 ? 28 : ((sizeof(T) == 4) ? (VC == 4 ? 7 : 7) : 4)) k_cell(CellP<D, T> P)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v;
     constexpr int V = VC;
@@ -967,7 +968,18 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
     // fewer registers and more resident warps than 16-byte FP32 vectors, which
     // the latency-bound face passes prefer
     constexpr int VF = 2;
-    if (cache_bytes <= 48 * 1024)
+    // velocity meshes of a few hundred nodes (the Sec. 3.5 spaces): one warp
+    // per face, so that threads are not left idle and the block's serial
+    // state section holds no other warp
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (c->Nv <= AVS_SMALL_NV && cache_bytes <= 48 * 1024) {
+            k_face<D, T, 32, true, VF><<<c->Nf, 32, cache_bytes, c->stream>>>(P);
+            done = true;
+        }
+    }
+    if (done) {
+    } else if (cache_bytes <= 48 * 1024)
         k_face<D, T, NT, true, VF><<<c->Nf, NT, cache_bytes, c->stream>>>(P);
     else
         k_face<D, T, NT, false, VF><<<c->Nf, NT, 0, c->stream>>>(P);
@@ -1017,13 +1029,25 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     // extra warps of narrower vectors; k_raw_moments uses the same node mapping
     // so that its sums equal the carried ones bit for bit
     constexpr int VC = VW<T>::v;
-    if (!c->mom_valid) {
-        k_raw_moments<D, T, NT, VC><<<c->Nc, NT, 0, c->stream>>>(Q);
-        c->launches += 1;
+    // one warp per cell for small velocity meshes, as the face kernel; the
+    // raw-moment kernel takes the same node mapping (the sums stay the carried
+    // ones bit for bit; an adaptation, which may change Nv, drops them)
+    auto cell_stage = [&](auto ntc) {
+        constexpr int NTc = decltype(ntc)::value;
+        if (!c->mom_valid) {
+            k_raw_moments<D, T, NTc, VC><<<c->Nc, NTc, 0, c->stream>>>(Q);
+            c->launches += 1;
+        }
+        k_cell_state<D, T><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(Q);
+        k_cell<D, T, NTc, VC><<<c->Nc, NTc, 0, c->stream>>>(Q);
+        c->launches += 2;
+    };
+    if constexpr (sizeof(T) == 4) {
+        if (c->Nv <= AVS_SMALL_NV) cell_stage(std::integral_constant<int, 32>{});
+        else cell_stage(std::integral_constant<int, NT>{});
+    } else {
+        cell_stage(std::integral_constant<int, NT>{});
     }
-    k_cell_state<D, T><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(Q);
-    k_cell<D, T, NT, VC><<<c->Nc, NT, 0, c->stream>>>(Q);
-    c->launches += 2;
     c->mom_valid = 1;          // the raw moments of fout about U(Wout) are in cmom
     return cudaGetLastError();
 }
