@@ -520,6 +520,11 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     c->nbc = mesh->nbc;
     c->mixed = cfg->precision == AVS_MIXED;
     c->stream = (cudaStream_t)cuda_stream;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            c->nsm = 0;
+    }
     if (c->cfg.corr_iters == 0) c->cfg.corr_iters = 3;
     // Eq. (4)-(5) with rho = T = L_ref = 1
     c->mu_ref = 15.0 * sqrt(2.0 * AVS_PI * cfg->R) * cfg->Kn /

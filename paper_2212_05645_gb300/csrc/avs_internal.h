@@ -13,7 +13,7 @@
 #define AVS_NT 256            // threads per block of the per-cell kernels
 #define AVS_CELLPAR_BYTES 256 // bytes per cell of the collision parameters (CellPar)
 #define AVS_CMOM_MAX 17       // carried raw moments per cell (monatomic 11 / 13, Rykov 14 / 17)
-#define AVS_SMALL_NV 256      // velocity meshes up to this size: one warp per face / cell in the mixed step
+#define AVS_SMALL_ROW_BYTES 8192 // f rows of a cell up to this size: one warp per face / cell in the mixed step
 #define AVS_IMPSLOT_BYTES 96  // bytes per slot record of the implicit macroscopic sweep
 
 // Refinement caps of the velocity nodes (Sec. 3.5), passed to kernels by value.
@@ -111,6 +111,7 @@ struct avs_ctx {
     unsigned char *imp_co = nullptr;                 // [Nc][MAXS] interior slot records (AVS_IMPSLOT_BYTES each)
     unsigned char *imp_nint = nullptr;               // [Nc] interior slots per cell in sweep order
     unsigned *imp_bar = nullptr;                     // grid barrier counter of the macroscopic solve
+    int nsm = 0;                                     // multiprocessors of the device
 
     // ---- learned proposer (MLP 8-64-64-4)
     float *mlp_P = nullptr;                          // FP32 master parameters

@@ -968,12 +968,14 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
     // fewer registers and more resident warps than 16-byte FP32 vectors, which
     // the latency-bound face passes prefer
     constexpr int VF = 2;
-    // velocity meshes of a few hundred nodes (the Sec. 3.5 spaces): one warp
-    // per face, so that threads are not left idle and the block's serial
-    // state section holds no other warp
+    // small velocity meshes (the Sec. 3.5 spaces): one warp per face, so that
+    // threads are not left idle and the block's serial state section holds no
+    // other warp; the foot cache then stays small enough for 28+ blocks per SM.
+    // Above 256 nodes only with faces enough to fill every SM with such
+    // blocks (on fewer faces, 128-thread blocks keep more nodes in flight).
     bool done = false;
     if constexpr (sizeof(T) == 4) {
-        if (c->Nv <= AVS_SMALL_NV && cache_bytes <= 48 * 1024) {
+        if (cache_bytes <= AVS_SMALL_ROW_BYTES && (c->Nv <= 256 || c->Nf >= 32 * c->nsm)) {
             k_face<D, T, 32, true, VF><<<c->Nf, 32, cache_bytes, c->stream>>>(P);
             done = true;
         }
@@ -1043,7 +1045,8 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
         c->launches += 2;
     };
     if constexpr (sizeof(T) == 4) {
-        if (c->Nv <= AVS_SMALL_NV) cell_stage(std::integral_constant<int, 32>{});
+        if ((size_t)NA * c->Nvp * sizeof(T) <= AVS_SMALL_ROW_BYTES && (c->Nv <= 256 || c->Nc >= 28 * c->nsm))
+            cell_stage(std::integral_constant<int, 32>{});
         else cell_stage(std::integral_constant<int, NT>{});
     } else {
         cell_stage(std::integral_constant<int, NT>{});
