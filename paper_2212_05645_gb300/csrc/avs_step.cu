@@ -1031,9 +1031,11 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     // extra warps of narrower vectors; k_raw_moments uses the same node mapping
     // so that its sums equal the carried ones bit for bit
     constexpr int VC = VW<T>::v;
-    // one warp per cell for small velocity meshes, as the face kernel; the
-    // raw-moment kernel takes the same node mapping (the sums stay the carried
-    // ones bit for bit; an adaptation, which may change Nv, drops them)
+    // one warp per cell wherever the cells fill every SM with such blocks (and
+    // on small velocity meshes): the cell kernel streams its rows, so a warp
+    // per cell keeps as many loads in flight and ends with a warp-only
+    // reduction; the raw-moment kernel takes the same node mapping (the sums
+    // stay the carried ones bit for bit; an adaptation drops them)
     auto cell_stage = [&](auto ntc) {
         constexpr int NTc = decltype(ntc)::value;
         if (!c->mom_valid) {
@@ -1045,8 +1047,7 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
         c->launches += 2;
     };
     if constexpr (sizeof(T) == 4) {
-        if ((size_t)NA * c->Nvp * sizeof(T) <= AVS_SMALL_ROW_BYTES && (c->Nv <= 256 || c->Nc >= 28 * c->nsm))
-            cell_stage(std::integral_constant<int, 32>{});
+        if (c->Nv <= 256 || c->Nc >= 28 * c->nsm) cell_stage(std::integral_constant<int, 32>{});
         else cell_stage(std::integral_constant<int, NT>{});
     } else {
         cell_stage(std::integral_constant<int, NT>{});
