@@ -70,6 +70,10 @@ def lib():
             L.om_moments.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp]
             L.om_dt_unit.restype = C.c_double
             L.om_dt_unit.argtypes = [C.c_void_p, C.c_int, dp]
+            L.om_limited_gradients.restype = None
+            L.om_limited_gradients.argtypes = [C.c_void_p, C.c_void_p, C.c_int, dp, dp, dp]
+            L.om_venkat.restype = C.c_double
+            L.om_venkat.argtypes = [C.c_double, C.c_double, C.c_double]
             L.om_step.restype = C.c_int
             L.om_step.argtypes = [C.c_void_p, C.c_void_p, C.c_int, dp, dp, C.c_double, dp, dp, dp]
             L.om_colors.restype = C.c_int
@@ -302,6 +306,24 @@ def primitive_rykov(D, Wc, R=0.5):
 def dt_unit(mh: MeshHandle, xi):
     xi = _f64(xi)
     return lib().om_dt_unit(mh.ptr, xi.shape[0], _dp(xi))
+
+
+def limited_gradients(mh: MeshHandle, g: _Gas, f_in):
+    """Step 1 of the step alone (Sec. 2.3.3): the unlimited least-squares
+    gradient [Nc][nA][Nv][D] and the Venkatakrishnan factor [Nc][nA][Nv]."""
+    f_in = _f64(f_in)
+    Nc, nA, Nv = f_in.shape
+    D = mh.mesh.D
+    grad = np.zeros((Nc, nA, Nv, D))
+    lim = np.zeros((Nc, nA, Nv))
+    lib().om_limited_gradients(mh.ptr, C.byref(g), Nv, _dp(f_in), _dp(grad), _dp(lim))
+    return grad, lim
+
+
+def venkat(d1, d2, eps2):
+    """Venkatakrishnan's function of (largest neighbour difference, unlimited
+    change, epsilon^2), capped at 1."""
+    return lib().om_venkat(float(d1), float(d2), float(eps2))
 
 
 def step(mh: MeshHandle, g: _Gas, xi, w, dt, f_in, Wc):

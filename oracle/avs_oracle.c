@@ -5,8 +5,8 @@
  *
  * Every routine follows the paper's definitions in the paper's order, with
  * plain loops (cells, then arrays, then nodes; faces in list order) and no
- * blocking or fusion.  Where the paper is silent the reading used is named
- * in the comment (R1..R30 are the readings listed in the design notes).
+ * blocking or fusion.  Where the paper is silent, the comment beside the code
+ * states the reading taken (tagged R1..R32 so that the tests can name it).
  * Build with -ffp-contract=off so that no multiply-add is fused.
  */
 #include "avs_oracle.h"
@@ -490,23 +490,21 @@ static double venkat(double d1, double d2, double eps2)
 
 /* ---- one explicit step (Sec. 2.3, explicit reading R1/R2) --------------- */
 
-/* Steps shared by the explicit and the implicit step: limited gradients
- * (Sec. 2.3.3), the interface distribution phi_ij of every face (Eqs. equ27,
- * equ28 with R4; boundaries R8) stored in phi [Nf][nA][Nv], and its
- * area-weighted flux moments A F_ij in F [Nf][D+2].  Returns 1 when an
- * interface state has rho <= 0 or T <= 0. */
-static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
-                            double dt, const double *f_in, const slots_t *S, double *phi, double *F)
+/* Step 1 of the step: least-squares gradient (weights 1/|d|^2) of every cell,
+ * array and node, and its Venkatakrishnan limiter factor L (Sec. 2.3.3, R6):
+ * grad [Nc][nA][Nv][D] unlimited gradient, lim [Nc][nA][Nv] the factor, so the
+ * limited gradient is lim * grad.  epsilon^2 = (K dx)^3 with dx = |V|^(1/D);
+ * the limiter is the least Venkatakrishnan value over the cell's faces, taken
+ * with the largest (smallest) neighbour difference on faces where the
+ * unlimited change grad . r is positive (negative).  A cell whose LSQ matrix
+ * is singular gets a zero gradient. */
+static void limited_gradients(const om_mesh *m, const om_gas *g, int Nv, const double *f_in, const slots_t *S,
+                              double *grad, double *lim)
 {
-    const int D = m->D, nA = nArrG(g, D), NW = nWG(g, D), Nc = m->Nc, Nf = m->Nf;
-    memset(F, 0, (size_t)Nf * NW * sizeof(double));
-    const double h = 0.5 * dt;
+    const int D = m->D, nA = nArrG(g, D), Nc = m->Nc;
     double *Minv = (double *)calloc((size_t)Nc * 9, sizeof(double));
     int *lsq_ok = (int *)calloc((size_t)Nc, sizeof(int));
     double *eps2 = (double *)malloc((size_t)Nc * sizeof(double));
-    double *grad = (double *)malloc((size_t)Nc * nA * Nv * D * sizeof(double));
-    double *lim = (double *)malloc((size_t)Nc * nA * Nv * sizeof(double));
-    int bad = 0;
 
     for (int i = 0; i < Nc; ++i) {
         lsq_ok[i] = lsq_inverse(m, S, i, Minv + (size_t)i * 9);
@@ -514,7 +512,6 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
         eps2[i] = pow(g->lim_K * dx, 3.0);
     }
 
-    /* 1. gradient and limiter of every cell, array and node */
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < Nc; ++i) {
         for (int a = 0; a < nA; ++a) {
@@ -561,6 +558,35 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
             }
         }
     }
+    free(Minv); free(lsq_ok); free(eps2);
+}
+
+void om_limited_gradients(const om_mesh *m, const om_gas *g, int Nv, const double *f_in, double *grad, double *lim)
+{
+    slots_t *S = build_slots(m);
+    limited_gradients(m, g, Nv, f_in, S, grad, lim);
+    free(S);
+}
+
+double om_venkat(double d1, double d2, double eps2) { return venkat(d1, d2, eps2); }
+
+/* Steps shared by the explicit and the implicit step: limited gradients
+ * (Sec. 2.3.3), the interface distribution phi_ij of every face (Eqs. equ27,
+ * equ28 with R4; boundaries R8) stored in phi [Nf][nA][Nv], and its
+ * area-weighted flux moments A F_ij in F [Nf][D+2].  Returns 1 when an
+ * interface state has rho <= 0 or T <= 0. */
+static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
+                            double dt, const double *f_in, const slots_t *S, double *phi, double *F)
+{
+    const int D = m->D, nA = nArrG(g, D), NW = nWG(g, D), Nc = m->Nc, Nf = m->Nf;
+    memset(F, 0, (size_t)Nf * NW * sizeof(double));
+    const double h = 0.5 * dt;
+    double *grad = (double *)malloc((size_t)Nc * nA * Nv * D * sizeof(double));
+    double *lim = (double *)malloc((size_t)Nc * nA * Nv * sizeof(double));
+    int bad = 0;
+
+    /* 1. gradient and limiter of every cell, array and node */
+    limited_gradients(m, g, Nv, f_in, S, grad, lim);
 
     /* 2. interface distribution and flux of every face */
 #pragma omp parallel for schedule(static) reduction(|:bad)
@@ -691,7 +717,7 @@ static int interface_fluxes(const om_mesh *m, const om_gas *g, int Nv, const dou
         }
     }
 
-    free(Minv); free(lsq_ok); free(eps2); free(grad); free(lim);
+    free(grad); free(lim);
     return bad;
 }
 

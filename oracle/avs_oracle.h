@@ -55,6 +55,12 @@ void om_normal_field(unsigned long long seed, int Nc, int Nv, double *z);
 void om_moments(int D, int Nc, int Nv, const double *xi, const double *w, const double *f,
                 double *Wc, double *q);
 double om_dt_unit(const om_mesh *m, int Nv, const double *xi);
+/* step 1 of om_step alone: unlimited LSQ gradient grad [Nc][nA][Nv][D] and
+ * Venkatakrishnan factor lim [Nc][nA][Nv] (Sec. 2.3.3) */
+void om_limited_gradients(const om_mesh *m, const om_gas *g, int Nv, const double *f_in, double *grad, double *lim);
+/* Venkatakrishnan's function of (largest neighbour difference, unlimited
+ * change, epsilon^2), capped at 1 */
+double om_venkat(double d1, double d2, double eps2);
 int  om_step(const om_mesh *m, const om_gas *g, int Nv, const double *xi, const double *w,
              double dt, const double *f_in, double *f_out, double *Wc);
 
