@@ -189,42 +189,25 @@ __device__ __forceinline__ A tau_vhs(A rho, A RT, A R, A mu_ref, A T_ref, A omeg
 
 // Foot values of both arrays at the V nodes k0.. of one face: the f rows of
 // its cells start at fL, fR and their gradient rows at gL, gR (null for first
-// order); node v is upwind from L when upL[v].  Vector loads when all V nodes
-// share the upwind cell; face-centre offsets rL, rR are in registers.
+// order); node v is upwind from L when upL[v].  Both cells' vectors are loaded
+// (independent of the upwind test, so the loads issue together with those of
+// the node coordinates) and each node takes its upwind cell's values;
+// face-centre offsets rL, rR are in registers.
 template <int D, int NA, int V, typename T>
 __device__ __forceinline__ void foot_face(const T* fL, const T* fR, const T* gL, const T* gR, int Nvp,
                                           const bool* upL, int k0, const T (*x)[D], const T* rL, const T* rR, T h,
                                           T (*out)[NA])
 {
-    bool uni = true;
+    T fa[NA][V], fb[NA][V], ga[NA][D][V], gb[NA][D][V];
 #pragma unroll
-    for (int v = 1; v < V; ++v) uni = uni && (upL[v] == upL[0]);
-    T fv[NA][V], gv[NA][D][V];
-    // one cell's vectors when the V nodes share their upwind cell, else a
-    // scalar load per node from its own upwind cell
-    if (uni) {
-        const T* fb = (upL[0] ? fL : fR) + k0;
-        const T* gb = (upL[0] ? gL : gR) + k0;
+    for (int a = 0; a < NA; ++a) {
+        ldv<T, V>(fL + k0 + (size_t)a * Nvp, fa[a]);
+        ldv<T, V>(fR + k0 + (size_t)a * Nvp, fb[a]);
+        if (gL) {
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            ldv<T, V>(fb + (size_t)a * Nvp, fv[a]);
-            if (gL) {
-#pragma unroll
-                for (int d = 0; d < D; ++d) ldv<T, V>(gb + (size_t)(a * D + d) * Nvp, gv[a][d]);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const T* fb = (upL[v] ? fL : fR) + k0 + v;
-            const T* gb = (upL[v] ? gL : gR) + k0 + v;
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                fv[a][v] = fb[(size_t)a * Nvp];
-                if (gL) {
-#pragma unroll
-                    for (int d = 0; d < D; ++d) gv[a][d][v] = gb[(size_t)(a * D + d) * Nvp];
-                }
+            for (int d = 0; d < D; ++d) {
+                ldv<T, V>(gL + k0 + (size_t)(a * D + d) * Nvp, ga[a][d]);
+                ldv<T, V>(gR + k0 + (size_t)(a * D + d) * Nvp, gb[a][d]);
             }
         }
     }
@@ -235,10 +218,10 @@ __device__ __forceinline__ void foot_face(const T* fL, const T* fR, const T* gL,
         for (int d = 0; d < D; ++d) o[d] = (upL[v] ? rL[d] : rR[d]) - x[v][d] * h;
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            T val = fv[a][v];
+            T val = upL[v] ? fa[a][v] : fb[a][v];
             if (gL) {
 #pragma unroll
-                for (int d = 0; d < D; ++d) val += gv[a][d][v] * o[d];
+                for (int d = 0; d < D; ++d) val += (upL[v] ? ga[a][d][v] : gb[a][d][v]) * o[d];
             }
             out[v][a] = val;
         }
@@ -246,39 +229,25 @@ __device__ __forceinline__ void foot_face(const T* fL, const T* fR, const T* gL,
 }
 
 // foot_face for a pair of FP32 nodes in packed two-lane arithmetic (same
-// operations and rounding per lane): out[a] = the pair's foot values of array a.
-// f and the gradient are read through L2 only (each value is used once by
-// this block), which leaves L1 to the node coordinates and weights that every
-// face block reads.
+// operations and rounding per lane): out[a] = the pair's foot values of array
+// a.  Both cells' pairs are loaded as above, through L2 only (each value is
+// used once by this block), which leaves L1 to the node coordinates and
+// weights that every face block reads.
 template <int D, int NA>
 __device__ __forceinline__ void foot_face2(const float* fL, const float* fR, const float* gL, const float* gR,
                                            int Nvp, const bool* upL, int k0, const float2* X, const float* rL,
                                            const float* rR, float h, float2* out)
 {
-    float2 fv[NA], gv[NA][D];
-    if (upL[0] == upL[1]) {
-        const float* fb = (upL[0] ? fL : fR) + k0;
-        const float* gb = (upL[0] ? gL : gR) + k0;
+    float2 fa[NA], fb[NA], ga[NA][D], gb[NA][D];
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            fv[a] = __ldcg(reinterpret_cast<const float2*>(fb + (size_t)a * Nvp));
-            if (gL) {
+    for (int a = 0; a < NA; ++a) {
+        fa[a] = __ldcg(reinterpret_cast<const float2*>(fL + k0 + (size_t)a * Nvp));
+        fb[a] = __ldcg(reinterpret_cast<const float2*>(fR + k0 + (size_t)a * Nvp));
+        if (gL) {
 #pragma unroll
-                for (int d = 0; d < D; ++d) gv[a][d] = __ldcg(reinterpret_cast<const float2*>(gb + (size_t)(a * D + d) * Nvp));
-            }
-        }
-    } else {
-        const float* f0 = (upL[0] ? fL : fR) + k0;
-        const float* f1 = (upL[1] ? fL : fR) + k0 + 1;
-        const float* g0 = (upL[0] ? gL : gR) + k0;
-        const float* g1 = (upL[1] ? gL : gR) + k0 + 1;
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            fv[a] = make_float2(__ldcg(f0 + (size_t)a * Nvp), __ldcg(f1 + (size_t)a * Nvp));
-            if (gL) {
-#pragma unroll
-                for (int d = 0; d < D; ++d)
-                    gv[a][d] = make_float2(__ldcg(g0 + (size_t)(a * D + d) * Nvp), __ldcg(g1 + (size_t)(a * D + d) * Nvp));
+            for (int d = 0; d < D; ++d) {
+                ga[a][d] = __ldcg(reinterpret_cast<const float2*>(gL + k0 + (size_t)(a * D + d) * Nvp));
+                gb[a][d] = __ldcg(reinterpret_cast<const float2*>(gR + k0 + (size_t)(a * D + d) * Nvp));
             }
         }
     }
@@ -288,10 +257,11 @@ __device__ __forceinline__ void foot_face2(const float* fL, const float* fR, con
         o[d] = fma2(X[d], bc2(-h), make_float2(upL[0] ? rL[d] : rR[d], upL[1] ? rL[d] : rR[d]));
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
-        float2 val = fv[a];
+        float2 val = make_float2(upL[0] ? fa[a].x : fb[a].x, upL[1] ? fa[a].y : fb[a].y);
         if (gL) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) val = fma2(gv[a][d], o[d], val);
+            for (int d = 0; d < D; ++d)
+                val = fma2(make_float2(upL[0] ? ga[a][d].x : gb[a][d].x, upL[1] ? ga[a][d].y : gb[a][d].y), o[d], val);
         }
         out[a] = val;
     }
@@ -351,57 +321,66 @@ struct FaceSt {
     T wa, wb;
 };
 
-// One block per face, two passes over the nodes (thread t owns nodes
-// k = tV.., tV + NT V.., V = VF = 2 nodes):
-//   A  interior: raw moments about V of the foot distribution phi_bar
-//      (upwind cell by the sign of xi . An), the foot values kept in shared
-//      memory when CACHE; boundary: flux moments of the outgoing foot values
-//      and of the incoming Maxwellian (unit density at a wall).  Then the
-//      interface state: tau (Eq. 3), q_ij (R4), Shakhov parameters, weights
-//      tau/(tau+h), h/(tau+h) (Eq. equ28); wall density from zero net mass
-//      flux (R8).
-//   B  interior: phi_ij = wa phi_bar + wb g_ij per node, its flux
-//      (xi . An) phi_ij and the flux moments sum_k w (xi . An) psi phi_ij;
-//      boundary: outgoing foot value / incoming Maxwellian.
-template <int D, typename T, int NT, bool CACHE, int VF>
-__global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4)) k_face(FaceP<D, T> P)
+// The face stage in pieces.  One face, nodes [kb, ke) (thread t of NT owns
+// nodes k = kb + tV.., kb + tV + NT V.., V = 2 nodes per iteration):
+//   face_setup   (one thread) cells, geometry, reference velocity V of the
+//                moment sums (mean of the two cells' velocities), and for a
+//                boundary face the incoming Maxwellian (unit density at a wall);
+//   face_pass_a  interior: raw moments about V of the foot distribution
+//                phi_bar (upwind cell by the sign of xi . An), the foot values
+//                kept in shared memory when CACHE; boundary: flux moments of
+//                the outgoing foot values and of the incoming Maxwellian;
+//   face_state   (one thread, from the summed pass-A moments) the interface
+//                state: tau (Eq. 3), q_ij (R4), Shakhov parameters, weights
+//                tau/(tau+h), h/(tau+h) (Eq. equ28); wall density from zero
+//                net mass flux (R8) and the boundary face's A F;
+//   face_pass_b  interior: phi_ij = wa phi_bar + wb g_ij per node, its flux
+//                (xi . An) phi_ij and the flux moments
+//                sum_k w (xi . An) psi phi_ij; boundary: outgoing foot value /
+//                incoming Maxwellian.
+// k_face runs them all in one block per face.
+template <int D, typename T>
+__device__ __forceinline__ void face_setup(const FaceP<D, T>& P, int f, FaceSt<T>& S)
+{
+    constexpr int NW = D + 2;
+    S.L = P.faceL[f];
+    S.R = P.faceR[f];
+    S.kind = S.R >= 0 ? 0 : (int)P.bc[(size_t)(-1 - S.R) * 6];
+    for (int d = 0; d < 3; ++d) {
+        S.An[d] = d < D ? P.An[(size_t)f * D + d] : T(0);
+        S.rL[d] = d < D ? P.rL[(size_t)f * D + d] : T(0);
+        S.rR[d] = d < D ? P.rR[(size_t)f * D + d] : T(0);
+        T v = T(0);
+        if (d < D) {
+            v = (T)P.Win[(size_t)S.L * NW + 1 + d] / (T)P.Win[(size_t)S.L * NW];
+            if (S.R >= 0) v = T(0.5) * (v + (T)P.Win[(size_t)S.R * NW + 1 + d] / (T)P.Win[(size_t)S.R * NW]);
+        }
+        S.V[d] = (double)v;
+        S.Vt[d] = v;
+    }
+    if (S.kind != 0) {
+        const double* B = P.bc + (size_t)(-1 - S.R) * 6;
+        const double Ub[3] = {B[2], B[3], B[4]};
+        S.eq = make_eq<D, T>(S.kind == 1 ? 1.0 : B[1], Ub, P.R * B[5], nullptr, P.Pr);
+    }
+}
+
+// number of pass-A sums per face: NM raw moments (interior) or 2 (D+2) flux
+// moments (boundary: outgoing, incoming)
+template <int D>
+struct FaceNR {
+    static constexpr int NM = NMom<D>::v, NW = D + 2;
+    static constexpr int v = (NM > 2 * NW) ? NM : 2 * NW;
+};
+
+template <int D, typename T, int NT, bool CACHE, int V>
+__device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T>& S, T* fc, int kb, int ke,
+                                            T* acc, int tid)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
-    constexpr int NR = (NM > 2 * NW) ? NM : 2 * NW;
-    constexpr int V = VF;
+    constexpr int NR = FaceNR<D>::v;
     constexpr bool PACK = sizeof(T) == 4 && V == 2;      // FP32 pairs in packed arithmetic
-    __shared__ FaceSt<T> S;
-    __shared__ double sw[(NT / 32) * NR];
-    __shared__ double red[NR];
-    extern __shared__ __align__(16) unsigned char face_dsm[];
-    T* fc = reinterpret_cast<T*>(face_dsm);     // [array][Nvp] foot values (CACHE)
-
-    const int tid = threadIdx.x;
-    const int f = P.order[blockIdx.x];
     const T h = P.h;
-    if (tid == 0) {
-        S.L = P.faceL[f];
-        S.R = P.faceR[f];
-        S.kind = S.R >= 0 ? 0 : (int)P.bc[(size_t)(-1 - S.R) * 6];
-        for (int d = 0; d < 3; ++d) {
-            S.An[d] = d < D ? P.An[(size_t)f * D + d] : T(0);
-            S.rL[d] = d < D ? P.rL[(size_t)f * D + d] : T(0);
-            S.rR[d] = d < D ? P.rR[(size_t)f * D + d] : T(0);
-            T v = T(0);
-            if (d < D) {
-                v = (T)P.Win[(size_t)S.L * NW + 1 + d] / (T)P.Win[(size_t)S.L * NW];
-                if (S.R >= 0) v = T(0.5) * (v + (T)P.Win[(size_t)S.R * NW + 1 + d] / (T)P.Win[(size_t)S.R * NW]);
-            }
-            S.V[d] = (double)v;
-            S.Vt[d] = v;
-        }
-        if (S.kind != 0) {
-            const double* B = P.bc + (size_t)(-1 - S.R) * 6;
-            const double Ub[3] = {B[2], B[3], B[4]};
-            S.eq = make_eq<D, T>(S.kind == 1 ? 1.0 : B[1], Ub, P.R * B[5], nullptr, P.Pr);
-        }
-    }
-    __syncthreads();
     const bool inter = S.kind == 0;
     const int L = S.L, R = inter ? S.R : S.L;
     T An[D], Vt[D], rl[D], rr[D];
@@ -417,145 +396,167 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF ==
     const T* fR = P.fin + (size_t)R * P.cstride;
     const T* gL = P.G ? P.G + (size_t)L * NA * D * Nvp : nullptr;
     const T* gR = P.G ? P.G + (size_t)R * NA * D * Nvp : nullptr;
-    T* Fo = P.F + (size_t)f * NA * Nvp;
-
-    // ---------------- pass A
-    {
-        T acc[NR];
 #pragma unroll
-        for (int m = 0; m < NR; ++m) acc[m] = T(0);
-        bool packed = false;
-        if constexpr (PACK) {
-          if (inter) {
-            packed = true;
-            // FP32 node pairs in packed two-lane arithmetic; per-lane partial sums
-            float2 acc2[NM];
+    for (int m = 0; m < NR; ++m) acc[m] = T(0);
+    bool packed = false;
+    if constexpr (PACK) {
+      if (inter) {
+        packed = true;
+        // FP32 node pairs in packed two-lane arithmetic; per-lane partial sums
+        float2 acc2[NM];
 #pragma unroll
-            for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
-            for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
-                T x[V][D], wv[V];
-                load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
-                float2 X[D];
+        for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
+        for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
+            T x[V][D], wv[V];
+            load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
+            float2 X[D];
 #pragma unroll
-                for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
-                float2 sn = mul2(X[0], bc2(An[0]));
+            for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
+            float2 sn = mul2(X[0], bc2(An[0]));
 #pragma unroll
-                for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
-                const bool up[2] = {sn.x >= 0.0f, sn.y >= 0.0f};
-                float2 F[NA];
-                foot_face2<D, NA>((const float*)fL, (const float*)fR, (const float*)gL, (const float*)gR, Nvp, up,
-                                  k0, X, (const float*)rl, (const float*)rr, (float)h, F);
-                if constexpr (CACHE) {
+            for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
+            const bool up[2] = {sn.x >= 0.0f, sn.y >= 0.0f};
+            float2 F[NA];
+            foot_face2<D, NA>((const float*)fL, (const float*)fR, (const float*)gL, (const float*)gR, Nvp, up,
+                              k0, X, (const float*)rl, (const float*)rr, (float)h, F);
+            if constexpr (CACHE) {
 #pragma unroll
-                    for (int a = 0; a < NA; ++a) *reinterpret_cast<float2*>((float*)fc + a * Nvp + k0) = F[a];
-                }
-                float2 xs[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-(float)Vt[d]));
-                const float2 W2 = make_float2(wv[0], wv[1]);
-                raw_acc2<D>(acc2, xs, mul2(W2, F[0]), NA == 2 ? mul2(W2, F[NA - 1]) : bc2(0.0f));
+                for (int a = 0; a < NA; ++a) *reinterpret_cast<float2*>((float*)fc + a * Nvp + k0) = F[a];
             }
+            float2 xs[D];
 #pragma unroll
-            for (int m = 0; m < NM; ++m) acc[m] = (T)(acc2[m].x + acc2[m].y);
-          }
+            for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-(float)Vt[d]));
+            const float2 W2 = make_float2(wv[0], wv[1]);
+            raw_acc2<D>(acc2, xs, mul2(W2, F[0]), NA == 2 ? mul2(W2, F[NA - 1]) : bc2(0.0f));
         }
-        if (packed) {
-        } else if (inter) {
-            for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
-                T x[V][D], wv[V];
-                load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
-                bool up[V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) up[v] = dot_rn<D>(x[v], An) >= T(0);
-                T fv[V][NA];
-                foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
-                if constexpr (CACHE) {
-#pragma unroll
-                    for (int a = 0; a < NA; ++a) {
-                        T t[V];
-#pragma unroll
-                        for (int v = 0; v < V; ++v) t[v] = fv[v][a];
-                        stv<T, V>(fc + a * Nvp + k0, t);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    T xs[D];
-#pragma unroll
-                    for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Vt[d];
-                    raw_acc<D>(acc, xs, wv[v] * fv[v][0], NA == 2 ? wv[v] * fv[v][NA - 1] : T(0));
-                }
-            }
-        } else {
-            for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
-                T x[V][D], wv[V], sn[V];
-                load_nodes<D, V>(P, k0, x, wv);
-                bool up[V], any_out = false;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    sn[v] = dot_rn<D>(x[v], An);
-                    up[v] = true;
-                    any_out = any_out || sn[v] >= T(0);
-                }
-                T fv[V][NA];
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-#pragma unroll
-                    for (int a = 0; a < NA; ++a) fv[v][a] = T(0);
-                if (any_out) foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const bool out = sn[v] >= T(0);
-                    T g0 = fv[v][0], g1 = NA == 2 ? fv[v][NA - 1] : T(0);
-                    if (!out) eq_eval<D>(S.eq, x[v], g0, g1);
-                    const T t = wv[v] * sn[v];
-                    T x2 = T(0);
-#pragma unroll
-                    for (int d = 0; d < D; ++d) x2 += x[v][d] * x[v][d];
-                    T mm[NW];
-                    mm[0] = t * g0;
-#pragma unroll
-                    for (int d = 0; d < D; ++d) mm[1 + d] = t * g0 * x[v][d];
-                    mm[D + 1] = t * T(0.5) * (x2 * g0 + g1);
-#pragma unroll
-                    for (int c = 0; c < NW; ++c) {
-                        acc[c] += out ? mm[c] : T(0);
-                        acc[NW + c] += out ? T(0) : mm[c];
-                    }
-                }
-            }
-        }
-        block_sum_t<NR, NT>(acc, sw, red);
+        for (int m = 0; m < NM; ++m) acc[m] = (T)(acc2[m].x + acc2[m].y);
+      }
     }
-
-    // ---------------- interface state / boundary flux
-    if (tid == 0) {
-        if (inter) {
-            T rho, U[3], RT, qb[3];
-            state_from_raw<D, T>(red, S.V, rho, U, RT, qb);
-            if (!(rho > T(0)) || !(RT > T(0))) atomicOr(P.err, 1);
-            const T tau = tau_vhs<T>(rho, RT, (T)P.R, (T)P.mu_ref, (T)P.T_ref, (T)P.omega);
-            const T hh = (T)P.hd;
-            T qf[3] = {T(0), T(0), T(0)};
-            const T qs = fdiv(tau, tau + hh * (T)P.Pr);
-            for (int d = 0; d < D; ++d) qf[d] = qs * qb[d];
-            S.eq = make_eq_a<D, T, T>(rho, U, RT, qf, (T)P.Pr);
-            S.wa = fdiv(tau, tau + hh);
-            S.wb = fdiv(hh, tau + hh);
-        } else if (S.kind == 1) {
-            const double Sin = -red[NW];          // incoming mass flux of the unit-density wall Maxwellian
-            const double rw = Sin > 0.0 ? red[0] / Sin : 0.0;
-            for (int m = 0; m < NW; ++m) P.AF[(size_t)f * NW + m] = red[m] + rw * red[NW + m];
-            const double* B = P.bc + (size_t)(-1 - S.R) * 6;
-            const double Ub[3] = {B[2], B[3], B[4]};
-            S.eq = make_eq<D, T>(rw, Ub, P.R * B[5], nullptr, P.Pr);
-        } else {
-            for (int m = 0; m < NW; ++m) P.AF[(size_t)f * NW + m] = red[m] + red[NW + m];
+    if (packed) {
+    } else if (inter) {
+        for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
+            T x[V][D], wv[V];
+            load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
+            bool up[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) up[v] = dot_rn<D>(x[v], An) >= T(0);
+            T fv[V][NA];
+            foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
+            if constexpr (CACHE) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    T t[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) t[v] = fv[v][a];
+                    stv<T, V>(fc + a * Nvp + k0, t);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                T xs[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Vt[d];
+                raw_acc<D>(acc, xs, wv[v] * fv[v][0], NA == 2 ? wv[v] * fv[v][NA - 1] : T(0));
+            }
+        }
+    } else {
+        for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
+            T x[V][D], wv[V], sn[V];
+            load_nodes<D, V>(P, k0, x, wv);
+            bool up[V], any_out = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                sn[v] = dot_rn<D>(x[v], An);
+                up[v] = true;
+                any_out = any_out || sn[v] >= T(0);
+            }
+            T fv[V][NA];
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+#pragma unroll
+                for (int a = 0; a < NA; ++a) fv[v][a] = T(0);
+            if (any_out) foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const bool out = sn[v] >= T(0);
+                T g0 = fv[v][0], g1 = NA == 2 ? fv[v][NA - 1] : T(0);
+                if (!out) eq_eval<D>(S.eq, x[v], g0, g1);
+                const T t = wv[v] * sn[v];
+                T x2 = T(0);
+#pragma unroll
+                for (int d = 0; d < D; ++d) x2 += x[v][d] * x[v][d];
+                T mm[NW];
+                mm[0] = t * g0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) mm[1 + d] = t * g0 * x[v][d];
+                mm[D + 1] = t * T(0.5) * (x2 * g0 + g1);
+#pragma unroll
+                for (int c = 0; c < NW; ++c) {
+                    acc[c] += out ? mm[c] : T(0);
+                    acc[NW + c] += out ? T(0) : mm[c];
+                }
+            }
         }
     }
-    __syncthreads();
+}
 
-    // ---------------- pass B: per-node flux of the interface distribution
+// Interface state from the summed pass-A moments red[]; writes S.eq, S.wa,
+// S.wb and, for a boundary face, its area-weighted flux AF[0..D+1].
+template <int D, typename T>
+__device__ __forceinline__ void face_state(const FaceP<D, T>& P, FaceSt<T>& S, const double* red, double* AF)
+{
+    constexpr int NW = D + 2;
+    if (S.kind == 0) {
+        T rho, U[3], RT, qb[3];
+        state_from_raw<D, T>(red, S.V, rho, U, RT, qb);
+        if (!(rho > T(0)) || !(RT > T(0))) atomicOr(P.err, 1);
+        const T tau = tau_vhs<T>(rho, RT, (T)P.R, (T)P.mu_ref, (T)P.T_ref, (T)P.omega);
+        const T hh = (T)P.hd;
+        T qf[3] = {T(0), T(0), T(0)};
+        const T qs = fdiv(tau, tau + hh * (T)P.Pr);
+        for (int d = 0; d < D; ++d) qf[d] = qs * qb[d];
+        S.eq = make_eq_a<D, T, T>(rho, U, RT, qf, (T)P.Pr);
+        S.wa = fdiv(tau, tau + hh);
+        S.wb = fdiv(hh, tau + hh);
+    } else if (S.kind == 1) {
+        const double Sin = -red[NW];          // incoming mass flux of the unit-density wall Maxwellian
+        const double rw = Sin > 0.0 ? red[0] / Sin : 0.0;
+        for (int m = 0; m < NW; ++m) AF[m] = red[m] + rw * red[NW + m];
+        const double* B = P.bc + (size_t)(-1 - S.R) * 6;
+        const double Ub[3] = {B[2], B[3], B[4]};
+        S.eq = make_eq<D, T>(rw, Ub, P.R * B[5], nullptr, P.Pr);
+    } else {
+        for (int m = 0; m < NW; ++m) AF[m] = red[m] + red[NW + m];
+    }
+}
+
+// Pass B over nodes [kb, ke): writes the per-node flux into Fo (the face's
+// rows) and, for an interior face, returns the per-thread flux-moment
+// partial sums in acc[D+2] (element type).
+template <int D, typename T, int NT, bool CACHE, int V>
+__device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T>& S, const T* fc, int kb, int ke,
+                                            T* Fo, T* acc, int tid)
+{
+    constexpr int NA = NArr<D>::v, NW = D + 2;
+    constexpr bool PACK = sizeof(T) == 4 && V == 2;
+    const T h = P.h;
+    const bool inter = S.kind == 0;
+    const int L = S.L, R = inter ? S.R : S.L;
+    T An[D], rl[D], rr[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        An[d] = S.An[d];
+        rl[d] = S.rL[d];
+        rr[d] = S.rR[d];
+    }
+    const int Nvp = P.Nvp;
+    const T* fL = P.fin + (size_t)L * P.cstride;
+    const T* fR = P.fin + (size_t)R * P.cstride;
+    const T* gL = P.G ? P.G + (size_t)L * NA * D * Nvp : nullptr;
+    const T* gR = P.G ? P.G + (size_t)R * NA * D * Nvp : nullptr;
+#pragma unroll
+    for (int m = 0; m < NW; ++m) acc[m] = T(0);
     bool packed = false;
     if constexpr (PACK) {
       if (inter) {
@@ -565,7 +566,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF ==
         float2 acc2[NW];
 #pragma unroll
         for (int m = 0; m < NW; ++m) acc2[m] = bc2(0.0f);
-        for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+        for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V];
             load_nodes<D, V>(P, k0, x, wv);
             float2 X[D];
@@ -599,20 +600,14 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF ==
             *reinterpret_cast<float2*>((float*)Fo + k0) = mul2(sn, pG);
             if (NA == 2) *reinterpret_cast<float2*>((float*)Fo + (size_t)(NA - 1) * Nvp + k0) = mul2(sn, pH);
         }
-        T acc[NW];
 #pragma unroll
         for (int m = 0; m < NW; ++m) acc[m] = (T)(acc2[m].x + acc2[m].y);
-        block_sum_t<NW, NT>(acc, sw, red);
-        if (tid < NW) P.AF[(size_t)f * NW + tid] = red[tid];
       }
     }
     if (packed) {
     } else if (inter) {
         const T wa = S.wa, wb = S.wb;
-        T acc[NW];
-#pragma unroll
-        for (int m = 0; m < NW; ++m) acc[m] = T(0);
-        for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+        for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
             bool up[V];
@@ -654,10 +649,8 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF ==
 #pragma unroll
             for (int a = 0; a < NA; ++a) stv<T, V>(Fo + (size_t)a * Nvp + k0, o[a]);
         }
-        block_sum_t<NW, NT>(acc, sw, red);
-        if (tid < NW) P.AF[(size_t)f * NW + tid] = red[tid];
     } else {
-        for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+        for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
             bool up[V], any_out = false;
@@ -684,6 +677,37 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF ==
 #pragma unroll
             for (int a = 0; a < NA; ++a) stv<T, V>(Fo + (size_t)a * Nvp + k0, o[a]);
         }
+    }
+}
+
+// One block per face, all nodes: setup, pass A, state, pass B.
+template <int D, typename T, int NT, bool CACHE, int VF>
+__global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4)) k_face(FaceP<D, T> P)
+{
+    constexpr int NA = NArr<D>::v, NW = D + 2;
+    constexpr int NR = FaceNR<D>::v;
+    __shared__ FaceSt<T> S;
+    __shared__ double sw[(NT / 32) * NR];
+    __shared__ double red[NR];
+    extern __shared__ __align__(16) unsigned char face_dsm[];
+    T* fc = reinterpret_cast<T*>(face_dsm);     // [array][Nvp] foot values (CACHE)
+
+    const int tid = threadIdx.x;
+    const int f = P.order[blockIdx.x];
+    if (tid == 0) face_setup<D, T>(P, f, S);
+    __syncthreads();
+    {
+        T acc[NR];
+        face_pass_a<D, T, NT, CACHE, VF>(P, S, fc, 0, P.Nv, acc, tid);
+        block_sum_t<NR, NT>(acc, sw, red);
+    }
+    if (tid == 0) face_state<D, T>(P, S, red, P.AF + (size_t)f * NW);
+    __syncthreads();
+    T acc[NW];
+    face_pass_b<D, T, NT, CACHE, VF>(P, S, fc, 0, P.Nv, P.F + (size_t)f * NA * P.Nvp, acc, tid);
+    if (S.kind == 0) {
+        block_sum_t<NW, NT>(acc, sw, red);
+        if (tid < NW) P.AF[(size_t)f * NW + tid] = red[tid];
     }
 }
 
@@ -720,25 +744,20 @@ struct CellP {
     int* err;
 };
 
-// Raw moments of the own f^n of every cell about its U(W^n) (one block per
-// cell); used when the previous step did not leave them (after init, set_f,
-// set_W or an adaptation).
+// Raw moments of the own f^n of cell i about its U(W^n) over nodes [kb, ke):
+// per-thread partial sums in acc[NM].
 template <int D, typename T, int NT, int VC>
-__global__ void __launch_bounds__(NT) k_raw_moments(CellP<D, T> P)
+__device__ __forceinline__ void cell_raw_moments(const CellP<D, T>& P, int i, int kb, int ke, T* acc)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
     constexpr int V = VC;
-    __shared__ double sw[(NT / 32) * NM];
-    __shared__ double red[NM];
-    const int i = blockIdx.x;
     T Vct[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) Vct[d] = (T)P.Win[(size_t)i * NW + 1 + d] / (T)P.Win[(size_t)i * NW];
     const T* fi = P.fin + (size_t)i * P.cstride;
-    T acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = T(0);
-    for (int k0 = threadIdx.x * V; k0 < P.Nv; k0 += NT * V) {
+    for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
         T x[V][D], wv[V], f0[V], f1[V];
         load_nodes<D, V>(P, k0, x, wv);
         ldv<T, V>(fi + k0, f0);
@@ -751,6 +770,20 @@ __global__ void __launch_bounds__(NT) k_raw_moments(CellP<D, T> P)
             raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
         }
     }
+}
+
+// Raw moments of the own f^n of every cell about its U(W^n) (one block per
+// cell); used when the previous step did not leave them (after init, set_f,
+// set_W or an adaptation).
+template <int D, typename T, int NT, int VC>
+__global__ void __launch_bounds__(NT) k_raw_moments(CellP<D, T> P)
+{
+    constexpr int NM = NMom<D>::v;
+    __shared__ double sw[(NT / 32) * NM];
+    __shared__ double red[NM];
+    const int i = blockIdx.x;
+    T acc[NM];
+    cell_raw_moments<D, T, NT, VC>(P, i, 0, P.Nv, acc);
     block_sum_t<NM, NT>(acc, sw, red);
     if (threadIdx.x < NM) P.mom[(size_t)i * NM + threadIdx.x] = red[threadIdx.x];
 }
@@ -800,41 +833,27 @@ __global__ void k_cell_state(CellP<D, T> P)
     P.par[i] = cp;
 }
 
-// One block per cell: net flux N = sum_j sgn_j F_j per node and the collision
-// update (diagonal of Eq. SGS_phi, R1); pad nodes are written as zero.  The
-// raw moments of the new f about U(W~) are summed on the way for the next
-// step (same nodes per thread and order as k_raw_moments).
+// Collision update of cell i over nodes [kb, ke): net flux N = sum_j sgn_j F_j
+// per node and the update (diagonal of Eq. SGS_phi, R1); pad nodes are written
+// as zero.  The raw moments of the new f about U(W~) are summed on the way
+// (per-thread partials in acc[NM], same nodes per thread and order as
+// cell_raw_moments).  fs, sg: the cell's face indices and signs; cp its
+// collision parameters (shared memory).
 template <int D, typename T, int NT, int VC>
-__global__ void __launch_bounds__(NT, NT == 32 ? 28 : ((sizeof(T) == 4) ? (VC == 4 ? 7 : 7) : 4)) k_cell(CellP<D, T> P)
+__device__ __forceinline__ void cell_update(const CellP<D, T>& P, int i, int ns, const int* fs, const T* sg,
+                                            const CellPar<T>& cp, int kb, int ke, T* acc)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v;
     constexpr int V = VC;
-    __shared__ int fs[AVS_MAXS];
-    __shared__ T sg[AVS_MAXS];
-    __shared__ double sw[(NT / 32) * NM];
-    __shared__ double red[NM];
-    __shared__ CellPar<T> cp;
-
-    const int tid = threadIdx.x;
-    const int i = blockIdx.x;
-    const int ns = P.nslot[i];
-    if (tid < ns) {
-        const int sl = P.slot[i * AVS_MAXS + tid];
-        fs[tid] = sl >> 1;
-        sg[tid] = (sl & 1) ? T(-1) : T(1);
-    }
-    if (tid == 32 % NT) cp = P.par[i];
-    __syncthreads();
     const T* fi = P.fin + (size_t)i * P.cstride;
     T* fo = P.fout + (size_t)i * P.cstride;
     const T u0 = cp.upd[0], u1 = cp.upd[1], u2 = cp.upd[2], u3 = cp.upd[3];
     T Vnt[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) Vnt[d] = cp.Vn[d];
-    T acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = T(0);
-    for (int k0 = tid * V; k0 < P.Nv; k0 += NT * V) {
+    for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
         T x[V][D], wv[V];
         load_nodes<D, V>(P, k0, x, wv);
         T Nn[NA][V], fv[NA][V], out[NA][V];
@@ -872,6 +891,31 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 28 : ((sizeof(T) == 4) ? (VC ==
 #pragma unroll
         for (int a = 0; a < NA; ++a) stv<T, V>(fo + (size_t)a * P.Nvp + k0, out[a]);
     }
+}
+
+// One block per cell, all nodes; the raw moments of f^{n+1} to P.mom.
+template <int D, typename T, int NT, int VC>
+__global__ void __launch_bounds__(NT, NT == 32 ? 28 : ((sizeof(T) == 4) ? (VC == 4 ? 7 : 7) : 4)) k_cell(CellP<D, T> P)
+{
+    constexpr int NM = NMom<D>::v;
+    __shared__ int fs[AVS_MAXS];
+    __shared__ T sg[AVS_MAXS];
+    __shared__ double sw[(NT / 32) * NM];
+    __shared__ double red[NM];
+    __shared__ CellPar<T> cp;
+
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x;
+    const int ns = P.nslot[i];
+    if (tid < ns) {
+        const int sl = P.slot[i * AVS_MAXS + tid];
+        fs[tid] = sl >> 1;
+        sg[tid] = (sl & 1) ? T(-1) : T(1);
+    }
+    if (tid == 32 % NT) cp = P.par[i];
+    __syncthreads();
+    T acc[NM];
+    cell_update<D, T, NT, VC>(P, i, ns, fs, sg, cp, 0, P.Nv, acc);
     block_sum_t<NM, NT>(acc, sw, red);
     if (tid < NM) P.mom[(size_t)i * NM + tid] = red[tid];
 }
