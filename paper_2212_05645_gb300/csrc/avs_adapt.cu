@@ -365,24 +365,19 @@ __device__ __forceinline__ void ref_velocity(int D, const double* Wref, int i, d
         for (int d = 0; d < D; ++d) Vr[d] = (double)(T)(Wref[(size_t)i * NW + 1 + d] / Wref[(size_t)i * NW]);
 }
 
+// Per-thread raw moments of the row fi about Vt (16-byte vectors of nodes per
+// thread, thread t owns nodes tV.., tV + NT V..), returned as doubles: FP64
+// sums in the FP64 form; compensated FP32 sums (about twice the FP32
+// precision) in the mixed form, whose products w f x.. are FP32 as stored.
 template <int D, typename T, int NT>
-__global__ void __launch_bounds__(NT) k_cell_moments(int Nv, int Nvp, const T* __restrict__ f,
-                                                     const T* __restrict__ xi, const T* __restrict__ w,
-                                                     const double* __restrict__ Wref, double* rmom)
+__device__ __forceinline__ void cell_raw_sums(int Nv, int Nvp, const T* __restrict__ fi, const T* __restrict__ xi,
+                                              const T* __restrict__ w, const T* Vt, double* out)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v;
     constexpr int V = 16 / sizeof(T);
-    __shared__ double sw[(NT / 32) * NM];
-    __shared__ double mom[NM];
-    const int i = blockIdx.x;
-    double Vr[3];
-    ref_velocity<T>(D, Wref, i, Vr);
-    T Vt[D];
-    for (int d = 0; d < D; ++d) Vt[d] = (T)Vr[d];
-    const T* fi = f + (size_t)i * NA * Nvp;
-    T acc[NM];
+    T acc[NM], cmp[NM];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) acc[m] = T(0);
+    for (int m = 0; m < NM; ++m) acc[m] = cmp[m] = T(0);
     for (int k0 = threadIdx.x * V; k0 < Nv; k0 += NT * V) {
         T x[V * D], wv[V], f0[V], f1[V];
         vload<T, V * D>(xi + (size_t)k0 * D, x);
@@ -394,10 +389,33 @@ __global__ void __launch_bounds__(NT) k_cell_moments(int Nv, int Nvp, const T* _
             T xs[D];
 #pragma unroll
             for (int d = 0; d < D; ++d) xs[d] = x[v * D + d] - Vt[d];
-            raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
+            if constexpr (sizeof(T) == 4)
+                raw_acc_c<D>(acc, cmp, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
+            else
+                raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
         }
     }
-    block_sum_t<NM, NT>(acc, sw, mom);
+#pragma unroll
+    for (int m = 0; m < NM; ++m) out[m] = to_double(acc[m]) + to_double(cmp[m]);
+}
+
+template <int D, typename T, int NT>
+__global__ void __launch_bounds__(NT) k_cell_moments(int Nv, int Nvp, const T* __restrict__ f,
+                                                     const T* __restrict__ xi, const T* __restrict__ w,
+                                                     const double* __restrict__ Wref, double* rmom)
+{
+    constexpr int NA = NArr<D>::v, NM = NMom<D>::v;
+    __shared__ double sw[(NT / 32) * NM];
+    __shared__ double mom[NM];
+    const int i = blockIdx.x;
+    double Vr[3];
+    ref_velocity<T>(D, Wref, i, Vr);
+    T Vt[D];
+    for (int d = 0; d < D; ++d) Vt[d] = (T)Vr[d];
+    const T* fi = f + (size_t)i * NA * Nvp;
+    double acc[NM];
+    cell_raw_sums<D, T, NT>(Nv, Nvp, fi, xi, w, Vt, acc);
+    block_sum<NM, NT>(acc, sw, mom);
     if (threadIdx.x < NM) rmom[(size_t)i * NM + threadIdx.x] = mom[threadIdx.x];
 }
 
@@ -825,6 +843,7 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
     __shared__ double sw[(NT / 32) * NM];
     __shared__ double mom[NM];
     __shared__ EqPar<T> ea, eb;
+    __shared__ float ce[7];                   // mixed form: coefficients of g(W) - g(W') (see below)
     const int i = blockIdx.x;
     T* fi = f + (size_t)i * NA * Nvp;
     const double* Wi = Wt + (size_t)i * NW;
@@ -837,24 +856,9 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
     if (threadIdx.x == 0) ea = make_eq<D, T>(rho, U, RT, nullptr, 0.0);
     for (int it = 0; it <= iters; ++it) {
         // moments of the current f' (nodes per thread as in the update below)
-        T acc[NM];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) acc[m] = T(0);
-        for (int k0 = threadIdx.x * V; k0 < Nv; k0 += NT * V) {
-            T x[V * D], wv[V], f0[V], f1[V];
-            vload<T, V * D>(xi + (size_t)k0 * D, x);
-            vload<T, V>(w + k0, wv);
-            vload<T, V>(fi + k0, f0);
-            if (NA == 2) vload<T, V>(fi + Nvp + k0, f1);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                T xs[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) xs[d] = x[v * D + d] - Vt[d];
-                raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
-            }
-        }
-        block_sum_t<NM, NT>(acc, sw, mom);
+        double acc[NM];
+        cell_raw_sums<D, T, NT>(Nv, Nvp, fi, xi, w, Vt, acc);
+        block_sum<NM, NT>(acc, sw, mom);
         if (it == iters) {
             if (threadIdx.x == 0) {
                 double Wp[5];
@@ -875,6 +879,28 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
             moments_from_raw<D>(mom, Vr, Wp, nullptr, nullptr, nullptr);
             prim<D>(Wp, rp, Up, RTp);
             eb = make_eq<D, T>(rp, Up, RTp, nullptr, 0.0);
+            if constexpr (sizeof(T) == 4) {
+                // g(W) - g(W') = g(W') expm1(E), E = log of the ratio of the two
+                // Maxwellians = e0 + e1 . xi + e2 |xi|^2, coefficients in FP64
+                // from the differences of the states (no cancellation), so the
+                // FP32 difference is accurate where W' is close to W; H: the
+                // same with (3 - D) R T (ratio and difference)
+                const double a = 0.5 / RT;
+                const double e2 = (RT - RTp) / (2.0 * RT * RTp);      // b - a
+                double dU[3], sU[3], Ub2 = 0.0, dUs = 0.0;
+                for (int d = 0; d < D; ++d) {
+                    dU[d] = U[d] - Up[d];
+                    sU[d] = U[d] + Up[d];
+                    Ub2 += Up[d] * Up[d];
+                    dUs += dU[d] * sU[d];
+                }
+                const double lnA = log1p((rho - rp) / rp) - 0.5 * D * log1p((RT - RTp) / RTp);
+                ce[0] = (float)(lnA - a * dUs + e2 * Ub2);
+                for (int d = 0; d < 3; ++d) ce[1 + d] = d < D ? (float)(2.0 * (a * dU[d] - e2 * Up[d])) : 0.0f;
+                ce[4] = (float)e2;
+                ce[5] = (float)((3 - D) * RT);
+                ce[6] = (float)((3 - D) * (RT - RTp));
+            }
         }
         __syncthreads();
         // f' <- f' + g(W) - g(W')  (Sec. 3.3)
@@ -885,12 +911,31 @@ __global__ void __launch_bounds__(NT) k_correct(int Nv, int Nvp, T* f, const T* 
             if (NA == 2) vload<T, V>(fi + Nvp + k0, f1);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                T ga, gah, gb, gbh;
-                eq_eval<D>(ea, x + v * D, ga, gah);
-                eq_eval<D>(eb, x + v * D, gb, gbh);
+                T dG, dH;
+                if constexpr (sizeof(T) == 4) {
+                    T gb, gbh;
+                    eq_eval<D>(eb, x + v * D, gb, gbh);
+                    const T* xv = x + v * D;
+                    T E = ce[0], x2 = T(0);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) {
+                        E += ce[1 + d] * xv[d];
+                        x2 += xv[d] * xv[d];
+                    }
+                    E += ce[4] * x2;
+                    const T em1 = expm1f(E);
+                    dG = gb * em1;
+                    dH = gb * (ce[5] * em1 + ce[6]);
+                } else {
+                    T ga, gah, gb, gbh;
+                    eq_eval<D>(ea, x + v * D, ga, gah);
+                    eq_eval<D>(eb, x + v * D, gb, gbh);
+                    dG = ga - gb;
+                    dH = gah - gbh;
+                }
                 const bool real = k0 + v < Nv;
-                f0[v] = real ? f0[v] + (ga - gb) : f0[v];
-                if (NA == 2) f1[v] = real ? f1[v] + (gah - gbh) : f1[v];
+                f0[v] = real ? f0[v] + dG : f0[v];
+                if (NA == 2) f1[v] = real ? f1[v] + dH : f1[v];
             }
             vstore<T, V>(fi + k0, f0);
             if (NA == 2) vstore<T, V>(fi + Nvp + k0, f1);

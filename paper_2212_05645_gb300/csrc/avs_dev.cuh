@@ -430,6 +430,55 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// Compensated FP32 accumulation: s + c carries the running sum, c the exact
+// rounding errors of the additions (TwoSum, no multiply so no contraction), so
+// a per-thread sum of FP32 terms keeps about twice the FP32 precision.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float y)
+{
+    const float t = s + y;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (y - bp);
+    s = t;
+    c += e;
+}
+
+// raw_acc with compensated per-thread sums (s, c) of the same terms.
+template <int D>
+__device__ __forceinline__ void raw_acc_c(float* s, float* c, const float* xs, float wg, float wh)
+{
+    if (D == 2) {
+        const float q = xs[0] * xs[0] + xs[1] * xs[1];
+        const float t0 = wg * xs[0], t1 = wg * xs[1];
+        two_sum_acc(s[0], c[0], wg);
+        two_sum_acc(s[1], c[1], t0);
+        two_sum_acc(s[2], c[2], t1);
+        two_sum_acc(s[3], c[3], t0 * xs[0]);
+        two_sum_acc(s[4], c[4], t0 * xs[1]);
+        two_sum_acc(s[5], c[5], t1 * xs[1]);
+        two_sum_acc(s[6], c[6], t0 * q);
+        two_sum_acc(s[7], c[7], t1 * q);
+        two_sum_acc(s[8], c[8], wh);
+        two_sum_acc(s[9], c[9], wh * xs[0]);
+        two_sum_acc(s[10], c[10], wh * xs[1]);
+    } else {
+        const float q = xs[0] * xs[0] + xs[1] * xs[1] + xs[2] * xs[2];
+        const float t0 = wg * xs[0], t1 = wg * xs[1], t2 = wg * xs[2];
+        two_sum_acc(s[0], c[0], wg);
+        two_sum_acc(s[1], c[1], t0);
+        two_sum_acc(s[2], c[2], t1);
+        two_sum_acc(s[3], c[3], t2);
+        two_sum_acc(s[4], c[4], t0 * xs[0]);
+        two_sum_acc(s[5], c[5], t0 * xs[1]);
+        two_sum_acc(s[6], c[6], t0 * xs[2]);
+        two_sum_acc(s[7], c[7], t1 * xs[1]);
+        two_sum_acc(s[8], c[8], t1 * xs[2]);
+        two_sum_acc(s[9], c[9], t2 * xs[2]);
+        two_sum_acc(s[10], c[10], t0 * q);
+        two_sum_acc(s[11], c[11], t1 * q);
+        two_sum_acc(s[12], c[12], t2 * q);
+    }
+}
+
 // raw_acc for a pair of nodes (per-lane partial sums), D = 2 or 3
 template <int D>
 __device__ __forceinline__ void raw_acc2(float2* m, const float2* xs, float2 wg, float2 wh)
