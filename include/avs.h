@@ -44,7 +44,9 @@ typedef enum {
     AVS_ETIMEOUT = -4,    /* a bounded device wait gave up                 */
     AVS_ENUMERIC = -5,    /* non-positive density or temperature met       */
     AVS_ENOTCONV = -6,    /* conservation correction gap grew              */
-    AVS_ECAPACITY = -7    /* adapted velocity mesh exceeds max_nodes       */
+    AVS_ECAPACITY = -7    /* adapted velocity mesh exceeds max_nodes, or a
+                             problem beyond the fixed scratch of
+                             avs_criterion_noalloc                          */
 } avs_status;
 
 enum { AVS_FP64 = 0, AVS_MIXED = 1 };
@@ -245,7 +247,9 @@ avs_status avs_get_f_cells(avs_ctx *ctx, const int *cells, int ncells, double *o
  * All calls share that scratch and it keeps the last call's contents (each call
  * resets what it needs); calls that overlap on the GPU race and must be
  * ordered.  The first call on each device looks up the scratch address
- * (cudaGetSymbolAddress) and should come before any stream capture.
+ * (cudaGetSymbolAddress) and should come before any stream capture; after a
+ * device reset the next call looks it up again.  The status covers this
+ * call's own launches (an error pending from earlier code is cleared first).
  * Errors: EINVAL (bad argument), ECAPACITY, ECUDA. */
 avs_status avs_criterion_noalloc(int dim, int Nc, int Nv, const double *f, const double *xi, const double *w,
                                  const double *Wc, double *M_out, void *cuda_stream);
@@ -282,6 +286,13 @@ avs_status avs_mlp_grad(avs_ctx *ctx, const float *X, const float *Y, int n, flo
 avs_status avs_features(avs_ctx *ctx, float *X_out, float *Y_out);
 /* iters SGD steps on the current state's features and labels; last loss out. */
 avs_status avs_mlp_train(avs_ctx *ctx, int iters, float lr, float *loss_out);
+/* The check set of the last avs_adapt call of the learned form: *n_out = its
+ * number of cells, or -1 when that call evaluated no check set (plain form,
+ * untrained network); cells_out (host, nullable, room for Nc ints) receives
+ * the cell indices in no particular order.  For tests and diagnostics: the
+ * criterion restricted to these cells gives the decisions of a learned
+ * adaptation and, on a full one, the misses it reports. */
+avs_status avs_mlp_check_set(avs_ctx *ctx, int *cells_out, int *n_out);
 
 /* The adaptive parameters of Sec. 3.5 for a flow.  With sigma = sqrt(R T):
  * T_0 = T_inf (1 + (gamma - 1)/2 Ma^2) (Eq. totaltemperature); R_dv =

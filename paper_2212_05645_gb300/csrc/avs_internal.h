@@ -13,7 +13,7 @@
 #define AVS_NT 256            // threads per block of the per-cell kernels
 #define AVS_CELLPAR_BYTES 256 // bytes per cell of the collision parameters (CellPar)
 #define AVS_CMOM_MAX 17       // carried raw moments per cell (monatomic 11 / 13, Rykov 14 / 17)
-#define AVS_SMALL_ROW_BYTES 8192 // f rows of a cell up to this size: one warp per face / cell in the mixed step
+#define AVS_SMALL_ROW_BYTES 8192 // f rows of a cell up to this size: one warp per face in the mixed step
 #define AVS_IMPSLOT_BYTES 96  // bytes per slot record of the implicit macroscopic sweep
 
 // Refinement caps of the velocity nodes (Sec. 3.5), passed to kernels by value.
@@ -128,6 +128,7 @@ struct avs_ctx {
     int mlp_train_iters = 50;
     float mlp_zthr = -1.0f;                          // logit threshold of the check set
     float mlp_budget = 0.25f;                        // fraction of cells in the check set
+    int mlp_checked_last = -1;                       // size of the last adaptation's check set, -1 none
 };
 
 namespace avs {

@@ -21,8 +21,16 @@
 // race on the scratch and give wrong results.
 //
 // Set-up: the first call on each device looks up the device address of the
-// scratch with cudaGetSymbolAddress (that device current) and caches it.
-// Make that first call before any stream capture begins.
+// scratch with cudaGetSymbolAddress (that device current) and caches it with
+// the identity of the device's current context.  Make that first call before
+// any stream capture begins.  A device reset (cudaDeviceReset) destroys the
+// context and the module with it; the next call sees a new context identity
+// and looks the address up again, so no kernel is ever given the old one.
+//
+// Errors: the call reports the launch status of its own kernels only; an
+// error left pending by earlier code on this thread is cleared first, not
+// reported as this call's failure.
+#include <cuda.h>
 #include <stdio.h>
 
 #include <mutex>
@@ -42,9 +50,39 @@ static __device__ __align__(256) unsigned long long g_node_keys[AVS_NOALLOC_MAX_
 struct ScratchAddr {
     double* cells = nullptr;
     unsigned long long* keys = nullptr;
+    unsigned long long ctx_id = 0;     // context the addresses belong to (0: unknown)
 };
 ScratchAddr g_addr[AVS_NOALLOC_MAX_DEVICES];
 std::mutex g_addr_mu;
+
+// Unique identity of the calling thread's current context, 0 when none is
+// current or the driver does not report one.  The two driver functions are
+// taken through the runtime's entry-point query, so the library needs no
+// link to the driver library.
+unsigned long long current_context_id()
+{
+    typedef CUresult (*get_current_t)(CUcontext*);
+    typedef CUresult (*get_id_t)(CUcontext, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (get_current_t)p;
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (get_id_t)p;
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Per-cell inputs of the criterion in the fixed order of its definition:
 // rho, U_d = m_d / rho, e_int = rho E - 0.5 (sum m_d m_d) / rho.
@@ -125,19 +163,23 @@ extern "C" avs_status avs_criterion_noalloc(int dim, int Nc, int Nv, const doubl
     ScratchAddr a;
     {
         std::lock_guard<std::mutex> lk(g_addr_mu);
-        if (!g_addr[dev].cells) {
+        const unsigned long long id = current_context_id();
+        if (!g_addr[dev].cells || id == 0 || id != g_addr[dev].ctx_id) {
             void* pc = nullptr;
             void* pk = nullptr;
             if (cudaGetSymbolAddress(&pc, g_cell_inputs) != cudaSuccess ||
                 cudaGetSymbolAddress(&pk, g_node_keys) != cudaSuccess) {
                 fprintf(stderr, "avs_criterion_noalloc: cudaGetSymbolAddress failed\n");
+                g_addr[dev] = ScratchAddr();
                 return AVS_ECUDA;
             }
             g_addr[dev].cells = (double*)pc;
             g_addr[dev].keys = (unsigned long long*)pk;
+            g_addr[dev].ctx_id = current_context_id();   // the lookup made the context current
         }
         a = g_addr[dev];
     }
+    (void)cudaGetLastError();          // report this call's launches only
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int NA = dim == 2 ? 2 : 1;
     const int cpb = 64;

@@ -1824,7 +1824,6 @@ template <int D, typename T>
 cudaError_t rk_face_stage(avs_ctx* c, const void* fin, const double* Win, double dt, RkP<T>& P)
 {
     constexpr int NA = RkNA<D>::v;
-    const bool f32 = sizeof(T) == 4;
     const size_t rows = (size_t)std::max(c->fcap, c->Nvp);
     const bool grad = c->cfg.limiter != 0;
     cudaError_t e;
