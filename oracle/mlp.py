@@ -139,3 +139,102 @@ def backward(p, X, Y):
 
 def sgd(p, g, lr):
     return {k: p[k] - lr * g[k] for k in p}
+
+
+def bf16_round(x):
+    """Nearest BF16 value (ties to even) of float32(x), as float64."""
+    a = np.ascontiguousarray(x, np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def gradient_error_bound(p, X, Y, u=2.0 ** -8, u32=2.0 ** -24):
+    """First-order elementwise bound on |g' - g| for every parameter gradient
+    g of `loss`, where g' is computed with BF16 operands in every product.
+
+    Model of g': the weights in p and the inputs X are already BF16 values
+    (the same in both); the activations A1, A2 are rounded to BF16 before the
+    next layer's product, and so are the backward signals dZ3, dZ2, dZ1 before
+    their products (unit roundoff u each); the products accumulate in FP32 (a
+    K-term sum errs by at most K u32 times the sum of the absolute terms); the
+    bias gradients sum the unrounded FP32 signals; the sigmoid is evaluated to
+    a few FP32 ulp.  Each error is carried through the layers with absolute
+    values (ReLU and the sum are 1-Lipschitz, the sigmoid 1/4-Lipschitz).  A
+    ReLU whose input lies within its own error bound of zero may switch, which
+    adds the whole derivative at that element.  Returns (bounds per parameter
+    like `backward`, bound on the logits)."""
+    Z3, (X, Z1, A1, Z2, A2) = forward(p, X)
+    n = X.shape[0]
+    nn = n * NO
+    aW1, aW2, aW3 = np.abs(p["W1"]), np.abs(p["W2"]), np.abs(p["W3"])
+    aX, aA1, aA2 = np.abs(X), np.abs(A1), np.abs(A2)
+    g8, g64, gn = NF * u32, H * u32, n * u32
+    # forward
+    eZ1 = g8 * (aX @ aW1.T + np.abs(p["b1"]))
+    eA1b = eZ1 + u * (aA1 + eZ1)
+    eZ2 = eA1b @ aW2.T + g64 * (aA1 @ aW2.T + np.abs(p["b2"]))
+    eA2b = eZ2 + u * (aA2 + eZ2)
+    eZ3 = eA2b @ aW3.T + g64 * (aA2 @ aW3.T + np.abs(p["b3"]))
+    # backward
+    S = 1.0 / (1.0 + np.exp(-Z3))
+    dZ3 = (S - Y) / nn
+    aD3 = np.abs(dZ3)
+    e3 = (0.25 * eZ3 + 2.0 ** -20 * S) / nn
+    e3b = e3 + u * (aD3 + e3)
+    dA2 = dZ3 @ p["W3"]
+    edA2 = e3b @ aW3 + NO * u32 * (aD3 @ aW3)
+    amb2 = np.abs(Z2) <= eZ2
+    dZ2 = dA2 * (Z2 > 0)
+    e2 = np.where(amb2, np.abs(dA2) + edA2, edA2 * (Z2 > 0))
+    aD2 = np.abs(dZ2)
+    e2b = e2 + u * (aD2 + e2)
+    dA1 = dZ2 @ p["W2"]
+    edA1 = e2b @ aW2 + g64 * (aD2 @ aW2)
+    amb1 = np.abs(Z1) <= eZ1
+    dZ1 = dA1 * (Z1 > 0)
+    e1 = np.where(amb1, np.abs(dA1) + edA1, edA1 * (Z1 > 0))
+    aD1 = np.abs(dZ1)
+    e1b = e1 + u * (aD1 + e1)
+    b = {}
+    b["W3"] = e3b.T @ aA2 + aD3.T @ eA2b + e3b.T @ eA2b + gn * (aD3.T @ aA2)
+    b["b3"] = e3.sum(0) + gn * aD3.sum(0)
+    b["W2"] = e2b.T @ aA1 + aD2.T @ eA1b + e2b.T @ eA1b + gn * (aD2.T @ aA1)
+    b["b2"] = e2.sum(0) + gn * aD2.sum(0)
+    b["W1"] = e1b.T @ aX + gn * (aD1.T @ aX)
+    b["b1"] = e1.sum(0) + gn * aD1.sum(0)
+    return b, eZ3
+
+
+def backward_bf16_emulated(p, X, Y):
+    """The gradients as a BF16-operand pipeline computes them (the model of
+    gradient_error_bound), emulated in numpy: float32 arithmetic, BF16
+    rounding of A1, A2, dZ3, dZ2, dZ1 before each product.  Used only to
+    check that the bound holds; the GPU kernels are checked against the bound
+    directly."""
+    f32 = np.float32
+    W1, W2, W3 = (p[k].astype(f32) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = (p[k].astype(f32) for k in ("b1", "b2", "b3"))
+    Xf = X.astype(f32)
+    Z1 = Xf @ W1.T + b1
+    A1 = np.maximum(Z1, f32(0))
+    A1b = bf16_round(A1).astype(f32)
+    Z2 = A1b @ W2.T + b2
+    A2 = np.maximum(Z2, f32(0))
+    A2b = bf16_round(A2).astype(f32)
+    Z3 = A2b @ W3.T + b3
+    nn = f32(X.shape[0] * NO)
+    dZ3 = ((f32(1) / (f32(1) + np.exp(-Z3))) - Y.astype(f32)) / nn
+    d3b = bf16_round(dZ3).astype(f32)
+    g = {}
+    g["W3"] = d3b.T @ A2b
+    g["b3"] = dZ3.sum(0)
+    dZ2 = (d3b @ W3) * (Z2 > 0)
+    d2b = bf16_round(dZ2).astype(f32)
+    g["W2"] = d2b.T @ A1b
+    g["b2"] = dZ2.sum(0)
+    dZ1 = (d2b @ W2) * (Z1 > 0)
+    d1b = bf16_round(dZ1).astype(f32)
+    g["W1"] = d1b.T @ Xf
+    g["b1"] = dZ1.sum(0)
+    return {k: v.astype(np.float64) for k, v in g.items()}, Z3.astype(np.float64)

@@ -28,7 +28,7 @@ EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs
             "avs_criterion", "avs_get_tree", "avs_get_f", "avs_get_f_cells", "avs_set_f", "avs_sync",
             "avs_kernel_launches",
             "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
-            "avs_mlp_train", "avs_measure_fma_peak", "avs_grid_barrier_check",
+            "avs_mlp_train", "avs_mlp_check_set", "avs_measure_fma_peak", "avs_grid_barrier_check",
             "avs_paper_parameters"]
 MLP_NPARAM = 4996
 
@@ -118,6 +118,7 @@ def load():
         "avs_mlp_grad": (C.c_int, [vp, dp, dp, C.c_int, C.c_float, dp, C.POINTER(C.c_float)]),
         "avs_features": (C.c_int, [vp, dp, dp]),
         "avs_mlp_train": (C.c_int, [vp, C.c_int, C.c_float, C.POINTER(C.c_float)]),
+        "avs_mlp_check_set": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "avs_measure_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
         "avs_grid_barrier_check": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
         "avs_paper_parameters": (C.c_int, [C.POINTER(FlowSpecS), C.POINTER(Config)]),
@@ -413,6 +414,17 @@ class AVS:
         loss = C.c_float()
         self._ck(self.L.avs_mlp_train(self.h, int(iters), float(lr), C.byref(loss)))
         return loss.value
+
+    def check_set(self):
+        """Cells of the last learned adaptation's check set (sorted), or None
+        when that call evaluated none."""
+        n = C.c_int()
+        self._ck(self.L.avs_mlp_check_set(self.h, None, C.byref(n)))
+        if n.value < 0:
+            return None
+        cells = np.zeros(max(1, n.value), np.int32)
+        self._ck(self.L.avs_mlp_check_set(self.h, cells.ctypes.data_as(C.POINTER(C.c_int)), C.byref(n)))
+        return np.sort(cells[:n.value])
 
 
 def _fill_paper_parameters(L, D, flow, cfg):

@@ -775,6 +775,7 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
                            o.W_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     }
     int checked = c->Nc, missed = 0, full = 1;
+    c->mlp_checked_last = -1;
     if (c->cfg.learned) {
         avs_status s2 = ensure_mlp(c, c->Nc);
         if (s2 != AVS_OK) return s2;
@@ -788,6 +789,7 @@ avs_status avs_adapt(avs_ctx* c, const avs_adapt_opts* opts, avs_adapt_stats* st
             CK(mlp_checkset(c, c->mlp_logits, c->mlp_zthr, c->mlp_list, c->mlp_count));
             CK(cudaMemcpyAsync(&checked, c->mlp_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
+            c->mlp_checked_last = checked;
             CK(launch_criterion(c, c->f[c->cur], 0, c->Nc, c->Nvp, c->Wf, c->mlp_list, checked, 1));
         }
         if (full) {
@@ -1075,6 +1077,18 @@ avs_status avs_mlp_train(avs_ctx* c, int iters, float lr, float* loss_out)
         CK(cudaMemcpyAsync(&g, c->mlp_grad + AVS_MLP_NPARAM, sizeof(float), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         *loss_out = g;
+    }
+    return AVS_OK;
+}
+
+avs_status avs_mlp_check_set(avs_ctx* c, int* cells_out, int* n_out)
+{
+    if (!c || !n_out) return AVS_EINVAL;
+    *n_out = c->mlp_checked_last;
+    if (c->mlp_checked_last > 0 && cells_out) {
+        CK(cudaMemcpyAsync(cells_out, c->mlp_list, sizeof(int) * c->mlp_checked_last, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
     }
     return AVS_OK;
 }

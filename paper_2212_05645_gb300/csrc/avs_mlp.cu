@@ -504,7 +504,7 @@ __global__ void k_labels(int D, int NA, int Nv, int Nvp, const T* __restrict__ f
         const double sm = __dmul_rn(s, mk), sM = __dmul_rn(s, Mk);
         const bool actd = sM >= C2;
         y0 |= (sm > C1 && lv < lcap);
-        y1 |= (actd && mk == Mk);
+        y1 |= (actd && sm == sM);
         y2 |= (actd && sm >= 0.5 * sM);
         y3 |= (sm >= C2 && lv >= 1);
     }

@@ -47,9 +47,11 @@ def rel_err(a, b):
     return float((np.abs(a - b) / scale).max())
 
 
-def field_err(Wg, Wo, D):
+def field_err(Wg, Wo, D, qg=None, qo=None):
     """Macroscopic error by field: rho and E relative to their values,
-    momentum relative to rho sqrt(2 R T) + |rho U| (the field's scale)."""
+    momentum relative to rho sqrt(2 R T) + |rho U| (the field's scale), and,
+    when given, the heat flux q (Eq. 8) relative to rho (2 R T)^(3/2) (the
+    scale of a third velocity moment)."""
     rho = Wo[:, 0]
     e_rho = np.abs(Wg[:, 0] - rho) / np.abs(rho)
     m = Wo[:, 1:1 + D]
@@ -57,7 +59,19 @@ def field_err(Wg, Wo, D):
     mscale = np.sqrt((m * m).sum(1)) + rho * np.sqrt(2 * RT)
     e_m = np.abs(Wg[:, 1:1 + D] - m).max(1) / mscale
     e_E = np.abs(Wg[:, D + 1] - Wo[:, D + 1]) / np.abs(Wo[:, D + 1])
-    return dict(rho=float(e_rho.max()), mom=float(e_m.max()), E=float(e_E.max()))
+    out = dict(rho=float(e_rho.max()), mom=float(e_m.max()), E=float(e_E.max()))
+    if qg is not None:
+        qscale = rho * (2.0 * RT) ** 1.5
+        out["q"] = float((np.abs(np.asarray(qg) - np.asarray(qo)).max(1) / qscale).max())
+    return out
+
+
+def q_err(g, r, D):
+    """Heat flux of the GPU's f against the oracle's, both about the mean
+    velocity of their own f (Eq. 8), relative to rho (2 R T)^(3/2)."""
+    _, qg = g.moments()
+    Wo, qo = O.moments(D, r.xi, r.w, r.f)
+    return field_err(Wo, Wo, D, qg, qo)["q"]
 
 
 def patch_mesh(mesh, targets, rings=2):

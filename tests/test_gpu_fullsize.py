@@ -45,6 +45,61 @@ def test_full_cylinder_mixed_fields_within_1e5():
     g.close()
 
 
+def test_full_cylinder_bench_step_mixed_against_oracle():
+    """One benchmark step of the cylinder at full size (128 x 96 cells, ~3.5k
+    nodes) in the mixed form, against the FP64 oracle from the same start:
+    the Maxwellian start from rest, 50 explicit steps, one adaptation with
+    the full criterion.
+    - After the 50 steps every cell's fields, heat flux included, are within
+      1e-5 of the oracle's (per-field errors printed).
+    - The adaptation: the mixed form's criterion (on its FP32 f) takes the
+      oracle's split and merge decision on every node, except nodes whose
+      scaled value s M_k lies within 1e-4 relative of C1 or C2, where the FP32
+      storage of f can decide (flips counted and printed); the adapted tree
+      is the oracle's tree built from the mixed form's own criterion values
+      (bit-exact given M), and the adapted fields stay within 1e-5 of the
+      oracle's when the two trees agree."""
+    avs = need_gpu()
+    w = wl.cylinder(precision="mixed")
+    w.learned = False
+    r = O.Run(w)
+    r.init_field()
+    g = avs.AVS(w, precision="mixed", learned=False)
+    g.init_field()
+    t = g.tree()
+    assert np.array_equal(t["level"], r.level) and np.array_equal(t["key"], r.key)
+    dt = r.dt()
+    assert g.dt() == dt
+    for _ in range(50):
+        r.step(dt)
+    g.step(50, dt=dt)
+    W, q = g.moments()
+    Wo, qo = O.moments(2, r.xi, r.w, r.f)
+    e = field_err(W, r.Wc, 2, q, qo)
+    print(f"\ncylinder bench step, 50 steps, per-field error against the FP64 oracle: {e}")
+    assert max(e.values()) < 1e-5, e
+    # criterion and decisions
+    s, C1, C2 = r.s, w.C1, w.C2
+    Mg = g.criterion()
+    Mo = O.criterion(2, r.xi, r.w, r.f, Wo)
+    band = (np.abs(s * Mo - C1) < 1e-4 * C1) | (np.abs(s * Mo - C2) < 1e-4 * C2)
+    flip = ((s * Mg > C1) != (s * Mo > C1)) | ((s * Mg < C2) != (s * Mo < C2))
+    print(f"decision flips: {int(flip.sum())} of {len(Mo)} nodes, all inside the band: {not (flip & ~band).any()}; "
+          f"nodes in the band: {int(band.sum())}")
+    assert not (flip & ~band).any()
+    lv, bs, ky, _, _ = O.adapt_tree(2, r.level, r.base, r.key, Mg, s, C1, C2, w.max_refine)
+    st = g.adapt()
+    assert st["full"] == 1
+    t = g.tree()
+    assert np.array_equal(t["level"], lv) and np.array_equal(t["base"], bs) and np.array_equal(t["key"], ky)
+    r.adapt()
+    if np.array_equal(r.level, lv) and np.array_equal(r.key, ky):
+        e = field_err(g.f_moments(), O.moments(2, r.xi, r.w, r.f)[0], 2)
+        print(f"after the adaptation (same tree), moments of f against the oracle's: {e}")
+        assert max(e.values()) < 1e-5, e
+    g.close()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
 def test_32k_node_velocity_mesh(precision, tol):
     """Top of the sweep range: a 168 x 168 base forest refined once near the

@@ -20,10 +20,7 @@ pytestmark = pytest.mark.gpu
 
 def bf16(x):
     """Round to the nearest BF16 value (ties to even), returned as float64."""
-    a = np.ascontiguousarray(x, np.float32)
-    b = a.view(np.uint32).astype(np.uint64)
-    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
-    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+    return mlp.bf16_round(x)
 
 
 def rounded_params(P32):
@@ -33,16 +30,16 @@ def rounded_params(P32):
     return p
 
 
-def relnorm(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def small_ctx(avs, learned=True):
     w = wl.sweep_box((6, 6), base=(8, 8), max_refine=1)
     return avs.AVS(w, learned=learned)
 
 
 def test_mlp_forward_and_gradients_match_oracle():
+    """Logits and every parameter gradient, element by element: within the
+    first-order BF16 rounding bound of the FP64 oracle (mlp.gradient_error_bound,
+    pinned on the CPU), and within 2 % of that bound of the same BF16 pipeline
+    emulated in numpy (the GPU differs from it only in the FP32 summation order)."""
     avs = need_gpu()
     g = small_ctx(avs)
     rng = np.random.default_rng(11)
@@ -55,17 +52,23 @@ def test_mlp_forward_and_gradients_match_oracle():
     Y = (rng.random((n, 4)) > 0.6).astype(np.float32)
     pr = rounded_params(P32)
     Xr = bf16(X)
+    Yd = Y.astype(np.float64)
     z_ref, _ = mlp.forward(pr, Xr)
+    bound, ez3 = mlp.gradient_error_bound(pr, Xr, Yd)
+    emu, z_emu = mlp.backward_bf16_emulated(pr, Xr, Yd)
     z = g.mlp_forward(X)
-    assert relnorm(z, z_ref) < 2e-2
+    assert np.all(np.abs(z - z_ref) <= ez3)
+    assert np.all(np.abs(z - z_emu) <= 0.02 * ez3 + 1e-6 * np.abs(z_ref))
     gr, loss = g.mlp_grad(X, Y, lr=0.0)
-    assert abs(loss - mlp.loss(pr, Xr, Y)) < 1e-2 * mlp.loss(pr, Xr, Y)
-    ref = mlp.backward(pr, Xr, Y)
+    assert abs(loss - mlp.loss(pr, Xr, Yd)) < 1e-2 * mlp.loss(pr, Xr, Yd)
+    ref = mlp.backward(pr, Xr, Yd)
     gd = unflatten(gr.astype(np.float64))
     for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
-        a, b = gd[k].reshape(-1), ref[k].reshape(-1)
-        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
-        assert relnorm(a, b) < 6e-2 and cos > 0.998, (k, relnorm(a, b), cos)
+        d = np.abs(gd[k] - ref[k])
+        assert np.all(d <= bound[k]), (k, float((d / np.maximum(bound[k], 1e-300)).max()))
+        de = np.abs(gd[k] - emu[k])
+        tol = 0.02 * bound[k] + 1e-6 * np.abs(ref[k]).max()
+        assert np.all(de <= tol), (k, float((de / tol).max()))
     g.close()
 
 
@@ -92,6 +95,10 @@ def test_mlp_sgd_tracks_oracle():
 
 
 def test_features_and_labels_match_oracle():
+    """Features within FP32 rounding of the oracle's; labels bit-exact against
+    the oracle's labels of the same f and the same W (the moments of f the
+    GPU uses, so that the equality test of the dominant label sees the same
+    values on both sides)."""
     avs = need_gpu()
     w = wl.sweep_box((8, 8), base=(10, 10), max_refine=1, C1=2.0)
     r, g = pair(w, avs, amp=1e-2)
@@ -100,29 +107,52 @@ def test_features_and_labels_match_oracle():
     Xo = mlp.features(2, Wf, q, w.mesh.vol, w.mesh.faceL, w.mesh.faceR,
                       mu_ref=O.mu_ref_from_Kn(w.Kn, w.omega), omega=w.omega)
     assert np.allclose(X, Xo, rtol=2e-5, atol=2e-6)
-    m = mlp.criterion_values(2, r.xi, r.w, r.f, Wf, float(np.prod(w.base)))
+    Wg = g.f_moments()
+    m = mlp.criterion_values(2, r.xi, r.w, r.f, Wg, float(np.prod(w.base)))
     Yo = mlp.labels(m, m.max(0), r.level, w.C1, w.C2, w.max_refine)
-    assert (Y == Yo).mean() > 0.995
-    assert Yo[:, 1].sum() >= 1
+    assert np.array_equal(Y, Yo)
+    assert Yo[:, 1].sum() >= 1 and Yo[:, 1].sum() < len(Yo)
 
 
 def test_learned_adaptation_check_set_and_misses():
-    """After training on the criterion's own labels the proposer's check set is
-    a strict subset of the cells; a full adaptation right after reports the
-    misses of the check set, and decisions with the full criterion stay exact."""
+    """A learned adaptation applies exactly the decisions of the criterion
+    restricted to its check set (a strict subset of the cells); a full one
+    right after applies the decisions of the whole criterion and reports as
+    misses exactly the nodes whose split or merge test the check set would
+    have decided differently.  Both judged against the oracle's criterion on
+    the same f and W, with the check set the library reports."""
     avs = need_gpu()
     w = wl.sweep_box((16, 16), base=(10, 10), max_refine=2, C1=2.0)
     w.learned = True
     r, g = pair(w, avs, amp=1e-3)
     loss = g.mlp_train(400, lr=0.2)
     assert np.isfinite(loss)
-    st_l = g.adapt()                          # learned step (trained network, not a full step)
-    assert st_l["full"] in (0, 1)
-    assert 0 < st_l["checked_cells"] <= g.Nc
-    # the plain oracle adaptation from the same state gives the same tree when no node was missed
-    o = r.adapt()
-    if st_l["full"] == 1 or st_l["missed_nodes"] == 0:
-        assert st_l["Nv"] == o["Nv"]
+    s, C1, C2 = r.s, w.C1, w.C2
+    kinds = []
+    for force_full in (False, False, True):
+        t0 = g.tree()
+        f = g.get_f()
+        Wg = g.f_moments()
+        st = g.adapt(force_full=force_full)
+        full = bool(st["full"])
+        kinds.append(full)
+        cells = g.check_set()
+        assert cells is not None and 0 < len(cells) < g.Nc
+        assert np.array_equal(np.unique(cells), cells)
+        M_full = O.criterion(2, t0["xi"], t0["w"], f, Wg)
+        M_chk = O.criterion(2, t0["xi"], t0["w"], f[cells], Wg[cells])
+        a, b = s * M_full, s * M_chk
+        flips = int((((a > C1) != (b > C1)) | ((a < C2) != (b < C2))).sum())
+        M_used = M_full if full else M_chk
+        lv, bs, ky, _, _ = O.adapt_tree(2, t0["level"], t0["base"], t0["key"], M_used, s, C1, C2, w.max_refine)
+        t1 = g.tree()
+        assert np.array_equal(t1["level"], lv) and np.array_equal(t1["base"], bs) and np.array_equal(t1["key"], ky)
+        if full:
+            assert st["missed_nodes"] == flips
+            assert st["checked_cells"] == g.Nc
+        else:
+            assert st["missed_nodes"] == 0 and st["checked_cells"] == len(cells)
+    assert kinds[-1] and not all(kinds), kinds          # at least one learned and the forced full one
     g.close()
 
 
@@ -145,11 +175,19 @@ def _wall_heat_flux(w, q):
 
 
 def test_learned_proposer_gain_over_plain_criterion():
-    """What the trained network gains: the criterion runs on a quarter of the
-    cells (the proposer's budget).  The plain criterion stays the judge: it
-    counts the nodes whose decision the check set got wrong, and the learned
-    run and the plain run (same start, same steps) are compared by the L1 gap
-    of their f-moments and wall heat flux."""
+    """What the trained network gains, and what it costs, over four
+    adaptations 10 steps apart.  The first adaptation of a context and the
+    forced last one run the full criterion (the fallback and judge); the two
+    between are learned.  Gain: the learned adaptations evaluate the criterion
+    on at most half of the cells (budget a quarter, doubled once when the first
+    full adaptation finds more than 1 % of the nodes decided wrongly by the
+    check set).  Cost, judged by the plain criterion and by a plain run from
+    the same start over the same steps: on the forced full adaptation the check
+    set would have decided at most 1 % of the nodes differently (the
+    fallback's own widening trigger), and the learned run's f-moments and wall
+    heat flux differ from the plain run's by less than 1e-4 and 1 % (L1,
+    relative), a fifth of the 5 % the paper takes as its accuracy standard
+    (Sec. 4.6)."""
     avs = need_gpu()
     import time
     w = _walled_box()
@@ -173,9 +211,11 @@ def test_learned_proposer_gain_over_plain_criterion():
     Wp, qp = gp.moments()
     l1_mom = np.abs(Wl - Wp).sum() / np.abs(Wp).sum()
     hf = np.abs(_wall_heat_flux(w, ql) - _wall_heat_flux(w, qp)).sum() / np.abs(_wall_heat_flux(w, qp)).sum()
-    print(f"\nlearned proposer: loss {loss:.4f}, checked fraction {np.mean(fracs):.3f}, misses {misses}, "
-          f"L1 f-moment gap {l1_mom:.2e}, wall heat-flux gap {hf:.2e}, adapt time learned {tl:.3f}s plain {tp:.3f}s")
-    assert np.mean(fracs) <= 0.6
-    assert misses[-1] < 0.5 * gl.Nv
-    assert l1_mom < 1e-2 and hf < 0.2
+    print(f"\nlearned proposer: loss {loss:.4f}, checked fraction {np.mean(fracs):.3f}, misses {misses} of "
+          f"{gl.Nv} nodes, L1 f-moment gap {l1_mom:.2e}, wall heat-flux gap {hf:.2e}, "
+          f"adapt time learned {tl:.3f}s plain {tp:.3f}s")
+    assert len(fracs) == 2 and len(misses) == 2
+    assert max(fracs) <= 0.5
+    assert misses[-1] <= 0.01 * gl.Nv
+    assert l1_mom < 1e-4 and hf < 1e-2
     gl.close(); gp.close()

@@ -4,6 +4,7 @@ features of a uniform state take their closed-form values."""
 import math
 
 import numpy as np
+import pytest
 
 import oracle as O
 from oracle import mlp
@@ -69,3 +70,54 @@ def test_labels_small_case_by_hand():
     assert y[:, 1].tolist() == [1, 1, 0]          # argmax of node 0 and node 1 (node 2 inactive)
     assert y[:, 2].tolist() == [1, 1, 0]          # 0.1 >= 0.2/2, 0.2; 0.05 < 0.1
     assert y[:, 3].tolist() == [1, 1, 1]          # level-1 nodes with m >= C2
+
+
+def _bf16_case(seed, n=301):
+    rng = np.random.default_rng(seed)
+    p = mlp.init_params(seed)
+    p["b1"] = 0.1 * rng.standard_normal(mlp.H)
+    for k in ("W1", "W2", "W3"):
+        p[k] = mlp.bf16_round(p[k])
+    X = mlp.bf16_round(rng.standard_normal((n, mlp.NF)))
+    Y = (rng.random((n, mlp.NO)) > 0.6).astype(np.float64)
+    return p, X, Y
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_bf16_gradient_bound_holds(seed):
+    """The elementwise bound of a BF16-operand forward/backward pass (the
+    tolerance of the GPU gradient test) contains the deviation of an emulated
+    BF16 pipeline from the FP64 gradients on every element.  It is a
+    worst-case bound (absolute values through the layers, no cancellation):
+    on the elements that matter (|g| above 1 % of the layer's largest) its
+    median stays below |g| for the last two layers and below 10 |g| for the
+    first, where two products of absolute values stack up; the GPU test
+    therefore also compares with the emulated pipeline."""
+    p, X, Y = _bf16_case(seed)
+    ref = mlp.backward(p, X, Y)
+    bound, ez3 = mlp.gradient_error_bound(p, X, Y)
+    emu, z3 = mlp.backward_bf16_emulated(p, X, Y)
+    z_ref, _ = mlp.forward(p, X)
+    assert np.all(np.abs(z3 - z_ref) <= ez3)
+    for k in ref:
+        d = np.abs(emu[k] - ref[k])
+        assert np.all(d <= bound[k]), (k, float((d / np.maximum(bound[k], 1e-300)).max()))
+        big = np.abs(ref[k]) > 0.01 * np.abs(ref[k]).max()
+        med = np.median(bound[k][big] / np.abs(ref[k][big]))
+        assert med < (10.0 if k in ("W1", "b1") else 1.0), (k, med)
+
+
+def test_bf16_emulation_matches_definition_without_rounding():
+    """The emulated pipeline with its BF16 roundings replaced by the identity
+    reproduces backward() to float32 accuracy: the emulation differs from the
+    definition only by those roundings."""
+    p, X, Y = _bf16_case(5, n=40)
+    saved = mlp.bf16_round
+    try:
+        mlp.bf16_round = lambda x: np.asarray(x, np.float64)
+        emu, z3 = mlp.backward_bf16_emulated(p, X, Y)
+    finally:
+        mlp.bf16_round = saved
+    ref = mlp.backward(p, X, Y)
+    for k in ref:
+        assert np.allclose(emu[k], ref[k], rtol=1e-5, atol=1e-7 * np.abs(ref[k]).max()), k
