@@ -1,16 +1,22 @@
 """Benchmark of the UGKS + adaptive-velocity-space hot path on GB300.
 
-Workload (default): supersonic cylinder, O-mesh 128 radial x 96
-circumferential cells, Ma 5, Kn 0.1, isothermal wall, global quadtree over
-[-15, 15]^2 sqrt(R T_inf) with base 24x24 and up to 4 levels, mixed precision
-(f in FP32, moment sums, wall balance and correction in FP64).
+Workload (default): supersonic flow around a sphere in the slip regime
+(paper Sec. 4.6 shape): spherical shell of 64 radial x 48 polar x 48
+azimuthal cells, Ma 4.25, Kn 0.031, isothermal wall, global octree over
+[-12, 12]^3 sqrt(R T_inf) with base 16^3 and up to 3 levels (~15-21k nodes),
+mixed precision (f in FP32; moment sums, wall balance and correction in
+FP64) with the learned adaptation proposer.  `--workload cylinder` runs the
+Ma 5 cylinder (O-mesh 128 x 96, quadtree base 24^2, 4 levels).
 
 One benchmark step = one pass of the whole hot path over one batch: the
 Maxwellian start of the flow from the device-resident initial field, `nu`
 (= 50, the adaptation interval) explicit UGKS steps and one adaptation of the
 velocity mesh (moments, criterion, marks + scan compaction, consanguinity
 remap, conservation correction).  Metric: cell-velocity-node updates per
-second, sum over the UGKS steps of Nc * Nv divided by the time.
+second, sum over the UGKS steps of Nc * Nv divided by the time.  The line
+also carries the same workload with the plain criterion (ablation of the
+proposer), the plain FP64 GPU form, the end-to-end rate through the C ABI
+with host buffers, the HBM roofline of the UGKS step and the CPU oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -49,8 +55,9 @@ def _args():
     ap.add_argument("--nu", type=int, default=NU)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
-    ap.add_argument("--workload", default="cylinder", choices=sorted(WORKLOADS),
-                    help="cylinder (the benchmark case) or another configuration")
+    ap.add_argument("--no-ablation", action="store_true", help="skip the plain-criterion ablation leg")
+    ap.add_argument("--workload", default="sphere", choices=sorted(WORKLOADS),
+                    help="sphere (the benchmark case) or another configuration")
     ap.add_argument("--oracle-threads", type=int, default=0,
                     help="host threads of the CPU oracle (default: all cores)")
     ap.add_argument("--implicit", type=float, default=0.0, metavar="CFL",
@@ -82,7 +89,7 @@ WORKLOADS = {
     # the same on the inner 64 radial rows (profiling case)
     "cylinder-rykov-r64": ("cylinder", dict(n_r=64, model="rykov")),
 }
-_WL = "cylinder"
+_WL = "sphere"
 
 
 def _build(fn, kw, precision):
@@ -189,10 +196,11 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic(kind, Nc, Nv):
-    """dram bytes per launch of the step kernel from the committed ncu
-    summary, scaled to this launch by cell-nodes; None when the kernel source
-    changed since the counters were taken."""
+def _traffic(family, Nc, Nv):
+    """DRAM bytes per UGKS step (the step kernels, one ncu pass) from the
+    committed record of this workload family, scaled to this step by
+    cell-nodes; None when the step's kernel sources changed since the
+    counters were taken or no record exists."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "step_kernel_dram.json")
     if not os.path.exists(p):
@@ -203,7 +211,7 @@ def _traffic(kind, Nc, Nv):
     for f in ("avs_step.cu", "avs_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2212_05645_gb300", "csrc", f), "rb").read())
     sha = h.hexdigest()[:16]
-    e = d.get(kind)
+    e = d.get(family)
     if not e or e.get("src_sha") != sha:
         return None
     return e["dram_bytes"] * (Nc * Nv) / (e["Nc"] * e["Nv"])
@@ -290,35 +298,47 @@ def run_gpu(args):
     w = _workload("mixed")
     # headline form: mixed precision with the learned proposer (full criterion every 4th adaptation)
     learned = w.model == "shakhov"           # the proposer is built for the monatomic gas
-    g = A.AVS(w, precision="mixed", stream=stream.cuda_stream, learned=learned, full_every=4)
-    Nc = g.Nc
     nu = args.nu
-    # every bench step is one batch: a flow started from the resident initial
-    # field W0, nu UGKS steps and one adaptation (the explicit hypersonic runs
-    # are not carried on from step to step; see the design notes on long runs)
     W0 = torch.from_numpy(np.ascontiguousarray(w.W_init)).to("cuda")
+    Nc = w.mesh.Nc
 
-    def advance(ctx):
+    def advance(ctx, n):
         if args.implicit > 0:
-            ctx.step_implicit(nu, cfl=args.implicit)
+            ctx.step_implicit(n, cfl=args.implicit)
         else:
-            ctx.step(nu)
+            ctx.step(n)
 
-    def bench_step(ctx, updates):
+    # Every bench step is one batch: a flow started from the resident initial
+    # field W0, nu UGKS steps and one adaptation.  The hypersonic flows are
+    # not carried from one bench step to the next: from the rest start, the
+    # explicit step as read here drives f negative next to the far field
+    # within a few hundred steps (about 670 on the cylinder), so a batch
+    # always starts again from W0.
+    def bench_step(ctx, updates, n=nu):
         ctx.init_field(W0)
-        advance(ctx)
-        updates.append(Nc * ctx.Nv * nu)
+        advance(ctx, n)
+        updates.append(Nc * ctx.Nv * n)
         return ctx.adapt()
-
-    upd = []
-    for _ in range(args.warmup):
-        bench_step(g, upd)
-    torch.cuda.synchronize()
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
+    # inputs below twice the L2 size: a 256 MB write between timed bench steps
+    # (outside their events) so that no step starts from a warm L2
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+
+    def make(precision, learned_, **kw):
+        return A.AVS(w, precision=precision, stream=stream.cuda_stream, learned=learned_, full_every=4, **kw)
+
+    # ---- headline: mixed + learned, device-timed
+    g = make("mixed", learned)
+    NA, NW = g.NA, g.NW
+    f_bytes = Nc * NA * g.Nv * 4
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if f_bytes < 2 * l2 else None
+    for _ in range(args.warmup):
+        bench_step(g, [])
+    torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
@@ -326,11 +346,6 @@ def run_gpu(args):
     ev = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_s, ev_e, wb_s, wb_e = ev(), ev(), ev(), ev()
     step_cells = []
-    # inputs below twice the L2 size: a 256 MB write between timed bench steps
-    # (outside their events) so that no step starts from a warm L2
-    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
-    f_bytes = Nc * g.NA * g.Nv * 4
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if f_bytes < 2 * l2 else None
     barrier()
     torch.cuda.synchronize()
     l0 = g.launches
@@ -341,7 +356,7 @@ def run_gpu(args):
         wb_s[j].record(stream)
         g.init_field(W0)
         ev_s[j].record(stream)
-        advance(g)
+        advance(g, nu)
         ev_e[j].record(stream)
         upd.append(Nc * g.Nv * nu)
         step_cells.append(Nc * g.Nv)
@@ -355,17 +370,20 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
     t_max, tot_updates = aggregate(ms, float(sum(upd)), ws, device="cuda")
     value = tot_updates / (t_max * 1e-3)
+    Nv_last = g.Nv
+    g.close()
+    del g
 
-    # roofline of the UGKS step (k_grad + k_face + k_cell, 90+ % of the time):
-    # algorithmic traffic = 1 read + 1 write of G and H in FP32 per cell-node
-    bytes_per_cn = 2 * g.NA * 4
+    # roofline of the UGKS step (the step kernels; 90+ % of a bench step):
+    # algorithmic traffic = 1 read + 1 write of f in FP32 per cell-node
+    bytes_per_cn = 2 * NA * 4
     kern_ms = sum(step_ms) / (args.steps * nu)
     cn_per_launch = statistics.mean(step_cells)
     achieved = bytes_per_cn * cn_per_launch / (kern_ms * 1e-3) / 1e9
     peak, peak_kind = _peaks()
-    # ncu traffic of the step, measured on the cylinder family (2D, mixed)
-    traffic = (_traffic("mixed", Nc, cn_per_launch / Nc)
-               if _WL in ("cylinder", "cylinder-r64") and args.implicit <= 0 else None)
+    family = "sphere" if _WL.startswith("sphere") else "cylinder" if _WL.startswith("cylinder") else None
+    traffic = (_traffic(family, Nc, cn_per_launch / Nc)
+               if family and args.implicit <= 0 and w.model == "shakhov" else None)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic,
             "kernel": (f"implicit Rykov UGKS step: k_grad + rk_face + rk_imp_setup + rk_imp_macro + rk_imp_res"
@@ -378,18 +396,17 @@ def run_gpu(args):
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
             "peak_spec_gbs": 8000.0, "frac_of_spec": achieved / 8000.0}
 
-    # end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: a fresh
+    # context through the same warm-up, so that its steps see the same
+    # sequence of velocity meshes and of full and learned adaptations
     e2e = None
     if rank == 0 or ws > 1:
         Wp = torch.from_numpy(np.ascontiguousarray(w.W_init)).pin_memory()
-        Wout = torch.zeros((Nc, g.NW), dtype=torch.float64).pin_memory()   # D + 2, or D + 3 (Rykov)
-        # a fresh context through the same warm-up, so that the timed steps see
-        # the same sequence of velocity meshes and of full and learned
-        # adaptations as the device-timed ones
-        ge = A.AVS(w, precision="mixed", stream=stream.cuda_stream, learned=learned, full_every=4)
+        Wout = torch.zeros((Nc, NW), dtype=torch.float64).pin_memory()   # D + 2, or D + 3 (Rykov)
+        ge = make("mixed", learned)
         for _ in range(args.warmup):
             bench_step(ge, [])
-        ke = args.steps
+        ke = min(args.steps, 6)
         torch.cuda.synchronize()
         e_upd = []
         te0 = time.perf_counter()
@@ -397,36 +414,71 @@ def run_gpu(args):
             if flush is not None:     # the same cold L2 as the device-timed steps
                 flush.fill_(j & 255)
             ge.init_field(Wp)         # h2d of the step's input W
-            advance(ge)
+            advance(ge, nu)
             e_upd.append(Nc * ge.Nv * nu)
             ge.adapt()
             ge.moments(out_W=Wout)    # d2h of the step's result
         torch.cuda.synchronize()
         te = time.perf_counter() - te0
         ge.close()
+        del ge
         e2e = {"value": sum(e_upd) / te, "unit": UNIT, "h2d_bytes_per_step": int(Wp.numel() * 8),
                "d2h_bytes_per_step": int(Wout.numel() * 8), "steps": ke,
                "velocity_nodes": [int(u // (Nc * nu)) for u in e_upd]}
 
-    # plain FP64 GPU form on the same workload (same definition of a step)
+    # ---- ablation: the same workload and bench steps with the plain
+    # criterion on every adaptation (no proposer)
+    ablation = None
+    if learned and not args.no_ablation:
+        ga = make("mixed", False)
+        for _ in range(min(args.warmup, 2)):
+            bench_step(ga, [])
+        ka = min(args.steps, 6)
+        ua = []
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        ta = 0.0
+        crit = []
+        for j in range(ka):
+            if flush is not None:
+                flush.fill_(j & 255)
+            a0.record(stream)
+            bench_step(ga, ua)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ta += a0.elapsed_time(a1)
+        ga.close()
+        del ga
+        ablation = {"form": "mixed, plain criterion on every adaptation", "value": sum(ua) / (ta * 1e-3),
+                    "unit": UNIT, "steps": ka,
+                    "learned_over_plain": value / ws / (sum(ua) / (ta * 1e-3))}
+
+    # ---- plain FP64 GPU form on the same workload: the same kind of bench
+    # step with fewer UGKS steps where the workload is large (about 20 s of
+    # FP64 work; the step count is in the line); device memory permitting
     fp64 = None
     if not args.no_fp64:
-        gd = A.AVS(w, precision="fp64", stream=stream.cuda_stream, learned=False)
-        u = []
-        bench_step(gd, u)
-        torch.cuda.synchronize()
-        u = []
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        kd = 2
-        for _ in range(kd):
-            bench_step(gd, u)
-        b.record(stream)
-        torch.cuda.synchronize()
-        fms = a.elapsed_time(b)
-        fp64 = {"value": sum(u) / (fms * 1e-3), "ms_per_step": fms / kd, "steps": kd}
-        gd.close()
+        n64 = int(max(1, min(nu, 2.6e10 / (2.0 * Nc * Nv_last))))
+        try:
+            gd = make("fp64", False)
+            bench_step(gd, [], n64)
+            torch.cuda.synchronize()
+            u = []
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            kd = 2 if n64 == nu else 1
+            a.record(stream)
+            for _ in range(kd):
+                bench_step(gd, u, n64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fms = a.elapsed_time(b)
+            fp64 = {"value": sum(u) / (fms * 1e-3), "ms_per_step": fms / kd, "steps": kd,
+                    "ugks_steps_per_step": n64}
+            gd.close()
+            del gd
+        except A.AVSError as exc:
+            fp64 = {"value": None, "unavailable": str(exc)}
 
     alu = {"fp32_fma_gflops": A.fma_peak_gflops(0), "fp64_fma_gflops": A.fma_peak_gflops(1, iters=2000),
            "fp32x2_fma_gflops": A.fma_peak_gflops(2),
@@ -436,30 +488,33 @@ def run_gpu(args):
         cpu = cpu_baseline()
 
     if rank == 0:
-        f_mb = Nc * g.NA * g.Nv * 4 / 1e6
+        f_mb = f_bytes / 1e6
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": w.name, "cells": Nc, "velocity_nodes": g.Nv,
+                "config": {"workload": w.name, "cells": Nc, "velocity_nodes": Nv_last,
                            "ugks_steps_per_step": nu, "precision": "mixed (f FP32, sums FP64)",
                            "time_step": (f"implicit IUGKS, CFL {args.implicit}, 60 macro + 2 micro SGS iterations"
                                          if args.implicit > 0 else "explicit, CFL 0.8"),
                            "adaptation": ("learned proposer, full criterion every 4th adaptation" if learned
                                           else "plain criterion every adaptation"),
-                           "gas": ("Rykov (diatomic: G, H, R)" if w.model == "rykov" else "Shakhov (monatomic: G, H)"),
+                           "gas": ("Rykov (diatomic: G, H, R)" if w.model == "rykov" else
+                                   "Shakhov (monatomic: G, H)" if w.D == 2 else "Shakhov (monatomic: G)"),
                            "l2": (f"L2 flushed before each timed step (f = {f_mb:.0f} MB per buffer)"
                                   if flush is not None else f"inputs larger than L2 (f = {f_mb:.0f} MB per buffer)"),
                            "parallelism": f"replicas x{ws}"},
                 "roofline": roof, "alu_peaks": alu, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "fp64_form": fp64,
+                "clocks": clocks, "fp64_form": fp64, "ablation": ablation,
                 "adaptation": {"full": sum(a["full"] for a in astats), "learned": sum(1 - a["full"] for a in astats),
                                "mean_checked_cells": statistics.mean(a["checked_cells"] for a in astats),
+                               "checked_fraction_learned": (statistics.mean(
+                                   a["checked_cells"] / Nc for a in astats if not a["full"])
+                                   if any(not a["full"] for a in astats) else None),
                                "missed_nodes_on_full_steps": [a["missed_nodes"] for a in astats if a["full"]],
                                "nodes": [a["Nv"] for a in astats],
                                "step_velocity_nodes": [int(c // Nc) for c in step_cells]},
-                "speedup_vs_fp64_form": (value / ws / fp64["value"]) if fp64 else None}
+                "speedup_vs_fp64_form": (value / ws / fp64["value"]) if fp64 and fp64.get("value") else None}
         print(json.dumps(line), flush=True)
-    g.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
