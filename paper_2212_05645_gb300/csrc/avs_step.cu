@@ -1,28 +1,32 @@
 // One explicit UGKS step on the global velocity mesh (paper Sec. 2.3, with
-// the explicit readings R1-R4), as three kernels.
+// the explicit readings R1-R4), as four kernels.
 //
-// k_grad: the limited least-squares gradient L grad phi of every cell, array
-//   and node (Sec. 2.3.3: least squares with weights 1/|d|^2, Venkatakrishnan
-//   limiter), computed once and stored next to f.  Elementwise stencil over
-//   the face neighbours.
+// k_foot: one thread block per (cell, node chunk).  The limited
+//   least-squares gradient L grad phi of the cell (Sec. 2.3.3: weights
+//   1/|d|^2, Venkatakrishnan limiter) at each node, kept in registers, and the
+//   foot values phi_C + (L grad phi)_C . (x_f - xi h - x_C) of every face of
+//   the cell at the nodes where the cell is upwind (sign of xi . An), written
+//   to the face's row: each face node gets its foot value exactly once.
 //
-// k_face: one thread block per face.  Foot values phi_C + (L grad phi)_C .
-//   (x_f - xi h - x_C) from the upwind cell, their raw velocity moments
-//   (interface W of Eq. w_interface and heat flux), the interface Shakhov
-//   state (Eqs. 3, equ28, R4), then the interface distribution
+// k_face: one thread block per face.  The raw velocity moments of the foot
+//   values (interface W of Eq. w_interface and heat flux), the interface
+//   Shakhov state (Eqs. 3, equ28, R4), then the interface distribution
 //   phi_ij = tau/(tau+h) phi_bar + h/(tau+h) g_ij per node.  Writes the
-//   per-node flux (xi . An) phi_ij and the face's area-weighted flux of W.
-//   Boundaries: diffuse wall with zero net mass flux, far-field Maxwellian (R8).
+//   per-node flux (xi . An) phi_ij over the foot values and the face's
+//   area-weighted flux of W.  Boundaries: diffuse wall with zero net mass
+//   flux, far-field Maxwellian (R8).
 //
-// k_cell: one thread block per cell.  Lagged heat flux from the moments of
-//   f^n (R3), W~ = W - dt/|V| sum_j A F_j (R2), the cell's Shakhov state and
-//   the collision update of every node from the net flux of its faces
-//   (diagonal of Eq. SGS_phi, R1).
+// k_cell_state / k_cell: one thread per cell, then one block per cell.
+//   Lagged heat flux from the moments of f^n (R3), W~ = W - dt/|V| sum_j A F_j
+//   (R2), the cell's Shakhov state and the collision update of every node
+//   from the net flux of its faces (diagonal of Eq. SGS_phi, R1).
 //
 // Every face is evaluated once, so the two cells of a face see the same flux
-// and W telescopes exactly.  f^n, its gradient and W^n are read-only during
-// the step; no block waits on another.  Sums: per-thread and warp sums in the
-// element type, FP64 across warps and in every per-cell / per-face formula.
+// and W telescopes exactly.  f^n and W^n are read-only during the step; no
+// block waits on another.  Sums: per-thread and warp sums in the element
+// type, FP64 across warps and in every per-cell / per-face formula.  The
+// limited-gradient kernel k_grad (gradients stored next to f) serves the
+// Rykov model's face kernels.
 #include <algorithm>
 #include <type_traits>
 
@@ -180,91 +184,138 @@ __global__ void __launch_bounds__(256) k_grad(int Nv, int Nvp, int limiter, cons
     }
 }
 
+// ------------------------------------------------------------------ k_foot
+// Cell-centric reconstruction (Sec. 2.3.3).  Thread block (cell i, 256 x VG
+// nodes): the limited gradient of every array of cell i (as k_grad, kept in
+// registers), then for every face slot s of the cell the foot values
+//   phi_bar = phi_i + (L grad phi)_i . (x_f - x_i - xi h)
+// at the nodes where i is that face's upwind cell (xi . An >= 0 for the face's
+// L cell, < 0 for its R cell; xi . An summed without contraction, the same
+// value the face kernel tests), written to the face's row of
+// FB [face][array][Nvp].  Every node of an interior face is written exactly
+// once, by its upwind cell; of a boundary face only the outgoing half.  The
+// gradient itself is never stored.
+template <int D, typename T, int VG, int NS, int NA>
+__global__ void __launch_bounds__(256) k_foot(int Nv, int Nvp, int limiter, T h, const T* __restrict__ f,
+                                              T* __restrict__ FB, CellGeo<T> geo, const int* __restrict__ slot,
+                                              const T* __restrict__ An, const T* __restrict__ xi)
+{
+    static_assert((VG * sizeof(T)) % 16 == 0, "whole 16-byte vectors per thread");
+    const int i = blockIdx.x;
+    const int k0 = (blockIdx.y * blockDim.x + threadIdx.x) * VG;
+    if (k0 >= Nv) return;
+    const size_t cstride = (size_t)NA * Nvp;
+    const int ns = geo.ns[i];
+    int nb[NS];
+    T cg[NS][D], rr[NS][D];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int n = s < ns ? geo.nbr[i * AVS_MAXS + s] : -1;
+        nb[s] = n >= 0 ? n : i;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            cg[s][d] = s < ns ? geo.cg[(size_t)(i * AVS_MAXS + s) * D + d] : T(0);
+            rr[s][d] = s < ns ? geo.r[(size_t)(i * AVS_MAXS + s) * D + d] : T(0);
+        }
+    }
+    const T e2 = geo.eps2[i];
+    T phi[NA][VG], G[NA][D][VG];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const T* fa = f + (size_t)a * Nvp + k0;
+        T nv[NS][VG];
+        ldvn<T, VG>(fa + (size_t)i * cstride, phi[a]);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) ldvn<T, VG>(fa + (size_t)nb[s] * cstride, nv[s]);
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            T g[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) g[d] = T(0);
+            T dmax = T(0), dmin = T(0);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const T dd = nv[s][v] - phi[a][v];
+#pragma unroll
+                for (int d = 0; d < D; ++d) g[d] += cg[s][d] * dd;
+                dmax = dd > dmax ? dd : dmax;
+                dmin = dd < dmin ? dd : dmin;
+            }
+            T L = T(1);
+            if (limiter == 1) {
+                T p = T(0), n = T(0);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    T d2 = g[0] * rr[s][0];
+#pragma unroll
+                    for (int d = 1; d < D; ++d) d2 += g[d] * rr[s][d];
+                    p = d2 > p ? d2 : p;
+                    n = d2 < n ? d2 : n;
+                }
+                if (p > T(0)) { const T t = venkat(dmax, p, e2); L = t < L ? t : L; }
+                if (n < T(0)) { const T t = venkat(dmin, n, e2); L = t < L ? t : L; }
+            }
+            if (limiter == 0) L = T(0);          // first order: phi_bar = phi_C
+#pragma unroll
+            for (int d = 0; d < D; ++d) G[a][d][v] = L * g[d];
+        }
+    }
+    // node coordinates of the thread's nodes
+    T x[VG][D];
+    {
+        T xx[VG * D];
+        ldvn<T, VG * D>(xi + (size_t)k0 * D, xx);
+#pragma unroll
+        for (int v = 0; v < VG; ++v)
+#pragma unroll
+            for (int d = 0; d < D; ++d) x[v][d] = xx[v * D + d];
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if (s >= ns) break;
+        const int sl = slot[i * AVS_MAXS + s];
+        const int fc = sl >> 1;
+        const bool isR = sl & 1;
+        T an[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) an[d] = An[(size_t)fc * D + d];
+        bool up[VG];
+        bool all = true, any = false;
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            const T sn = dot_rn<D>(x[v], an);
+            up[v] = isR ? (sn < T(0)) : (sn >= T(0));
+            all = all && up[v];
+            any = any || up[v];
+        }
+        if (!any) continue;
+        T* row = FB + (size_t)fc * NA * Nvp + k0;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            T out[VG];
+#pragma unroll
+            for (int v = 0; v < VG; ++v) {
+                T val = phi[a][v];
+#pragma unroll
+                for (int d = 0; d < D; ++d) val += G[a][d][v] * (rr[s][d] - x[v][d] * h);
+                out[v] = val;
+            }
+            if (all) {
+                stvn<T, VG>(row + (size_t)a * Nvp, out);
+            } else {
+#pragma unroll
+                for (int v = 0; v < VG; ++v)
+                    if (up[v]) row[(size_t)a * Nvp + v] = out[v];
+            }
+        }
+    }
+}
+
 template <typename A>
 __device__ __forceinline__ A tau_vhs(A rho, A RT, A R, A mu_ref, A T_ref, A omega)
 {
     const A T = fdiv(RT, R);
     return fdiv(mu_ref * powa(fdiv(T, T_ref), omega), rho * RT);
-}
-
-// Foot values of both arrays at the V nodes k0.. of one face: the f rows of
-// its cells start at fL, fR and their gradient rows at gL, gR (null for first
-// order); node v is upwind from L when upL[v].  Both cells' vectors are loaded
-// (independent of the upwind test, so the loads issue together with those of
-// the node coordinates) and each node takes its upwind cell's values;
-// face-centre offsets rL, rR are in registers.
-template <int D, int NA, int V, typename T>
-__device__ __forceinline__ void foot_face(const T* fL, const T* fR, const T* gL, const T* gR, int Nvp,
-                                          const bool* upL, int k0, const T (*x)[D], const T* rL, const T* rR, T h,
-                                          T (*out)[NA])
-{
-    T fa[NA][V], fb[NA][V], ga[NA][D][V], gb[NA][D][V];
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-        ldv<T, V>(fL + k0 + (size_t)a * Nvp, fa[a]);
-        ldv<T, V>(fR + k0 + (size_t)a * Nvp, fb[a]);
-        if (gL) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                ldv<T, V>(gL + k0 + (size_t)(a * D + d) * Nvp, ga[a][d]);
-                ldv<T, V>(gR + k0 + (size_t)(a * D + d) * Nvp, gb[a][d]);
-            }
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-        T o[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) o[d] = (upL[v] ? rL[d] : rR[d]) - x[v][d] * h;
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            T val = upL[v] ? fa[a][v] : fb[a][v];
-            if (gL) {
-#pragma unroll
-                for (int d = 0; d < D; ++d) val += (upL[v] ? ga[a][d][v] : gb[a][d][v]) * o[d];
-            }
-            out[v][a] = val;
-        }
-    }
-}
-
-// foot_face for a pair of FP32 nodes in packed two-lane arithmetic (same
-// operations and rounding per lane): out[a] = the pair's foot values of array
-// a.  Both cells' pairs are loaded as above, through L2 only (each value is
-// used once by this block), which leaves L1 to the node coordinates and
-// weights that every face block reads.
-template <int D, int NA>
-__device__ __forceinline__ void foot_face2(const float* fL, const float* fR, const float* gL, const float* gR,
-                                           int Nvp, const bool* upL, int k0, const float2* X, const float* rL,
-                                           const float* rR, float h, float2* out)
-{
-    float2 fa[NA], fb[NA], ga[NA][D], gb[NA][D];
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-        fa[a] = __ldcg(reinterpret_cast<const float2*>(fL + k0 + (size_t)a * Nvp));
-        fb[a] = __ldcg(reinterpret_cast<const float2*>(fR + k0 + (size_t)a * Nvp));
-        if (gL) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                ga[a][d] = __ldcg(reinterpret_cast<const float2*>(gL + k0 + (size_t)(a * D + d) * Nvp));
-                gb[a][d] = __ldcg(reinterpret_cast<const float2*>(gR + k0 + (size_t)(a * D + d) * Nvp));
-            }
-        }
-    }
-    float2 o[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        o[d] = fma2(X[d], bc2(-h), make_float2(upL[0] ? rL[d] : rR[d], upL[1] ? rL[d] : rR[d]));
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-        float2 val = make_float2(upL[0] ? fa[a].x : fb[a].x, upL[1] ? fa[a].y : fb[a].y);
-        if (gL) {
-#pragma unroll
-            for (int d = 0; d < D; ++d)
-                val = fma2(make_float2(upL[0] ? ga[a][d].x : gb[a][d].x, upL[1] ? ga[a][d].y : gb[a][d].y), o[d], val);
-        }
-        out[a] = val;
-    }
 }
 
 template <int D, int V, typename T, typename PP>
@@ -294,9 +345,8 @@ struct FaceP {
     T h;
     double hd;
     double R, Pr, omega, mu_ref, T_ref;
-    const T* __restrict__ fin;
-    const T* __restrict__ G;   // [cell][array][dim][Nvp], null for first order
-    T* __restrict__ F;         // [face][array][Nvp] per-node flux (xi . An) phi_ij
+    T* FB;                     // [face][array][Nvp]: foot values phi_bar (k_foot) in,
+                               // per-node flux (xi . An) phi_ij out (pass B overwrites in place)
     double* __restrict__ AF;   // [face][D+2] area-weighted flux of W
     const double* __restrict__ Win;
     const T* __restrict__ xi;
@@ -375,27 +425,20 @@ struct FaceNR {
 
 template <int D, typename T, int NT, bool CACHE, int V>
 __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T>& S, T* fc, int kb, int ke,
-                                            T* acc, int tid)
+                                            T* acc, int tid, int f)
 {
     constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
     constexpr int NR = FaceNR<D>::v;
     constexpr bool PACK = sizeof(T) == 4 && V == 2;      // FP32 pairs in packed arithmetic
-    const T h = P.h;
     const bool inter = S.kind == 0;
-    const int L = S.L, R = inter ? S.R : S.L;
-    T An[D], Vt[D], rl[D], rr[D];
+    T An[D], Vt[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         An[d] = S.An[d];
         Vt[d] = S.Vt[d];
-        rl[d] = S.rL[d];
-        rr[d] = S.rR[d];
     }
     const int Nvp = P.Nvp;
-    const T* fL = P.fin + (size_t)L * P.cstride;
-    const T* fR = P.fin + (size_t)R * P.cstride;
-    const T* gL = P.G ? P.G + (size_t)L * NA * D * Nvp : nullptr;
-    const T* gR = P.G ? P.G + (size_t)R * NA * D * Nvp : nullptr;
+    const T* fb = P.FB + (size_t)f * NA * Nvp;          // the face's foot values
 #pragma unroll
     for (int m = 0; m < NR; ++m) acc[m] = T(0);
     bool packed = false;
@@ -409,23 +452,16 @@ __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V];
             load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
-            float2 X[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
-            float2 sn = mul2(X[0], bc2(An[0]));
-#pragma unroll
-            for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
-            const bool up[2] = {sn.x >= 0.0f, sn.y >= 0.0f};
             float2 F[NA];
-            foot_face2<D, NA>((const float*)fL, (const float*)fR, (const float*)gL, (const float*)gR, Nvp, up,
-                              k0, X, (const float*)rl, (const float*)rr, (float)h, F);
+#pragma unroll
+            for (int a = 0; a < NA; ++a) F[a] = __ldcg(reinterpret_cast<const float2*>((const float*)fb + a * Nvp + k0));
             if constexpr (CACHE) {
 #pragma unroll
                 for (int a = 0; a < NA; ++a) *reinterpret_cast<float2*>((float*)fc + a * Nvp + k0) = F[a];
             }
             float2 xs[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-(float)Vt[d]));
+            for (int d = 0; d < D; ++d) xs[d] = add2(make_float2(x[0][d], x[1][d]), bc2(-(float)Vt[d]));
             const float2 W2 = make_float2(wv[0], wv[1]);
             raw_acc2<D>(acc2, xs, mul2(W2, F[0]), NA == 2 ? mul2(W2, F[NA - 1]) : bc2(0.0f));
         }
@@ -438,49 +474,32 @@ __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V];
             load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
-            bool up[V];
+            T fv[NA][V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) up[v] = dot_rn<D>(x[v], An) >= T(0);
-            T fv[V][NA];
-            foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
-            if constexpr (CACHE) {
-#pragma unroll
-                for (int a = 0; a < NA; ++a) {
-                    T t[V];
-#pragma unroll
-                    for (int v = 0; v < V; ++v) t[v] = fv[v][a];
-                    stv<T, V>(fc + a * Nvp + k0, t);
-                }
+            for (int a = 0; a < NA; ++a) {
+                ldv<T, V>(fb + (size_t)a * Nvp + k0, fv[a]);
+                if constexpr (CACHE) stv<T, V>(fc + a * Nvp + k0, fv[a]);
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 T xs[D];
 #pragma unroll
                 for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Vt[d];
-                raw_acc<D>(acc, xs, wv[v] * fv[v][0], NA == 2 ? wv[v] * fv[v][NA - 1] : T(0));
+                raw_acc<D>(acc, xs, wv[v] * fv[0][v], NA == 2 ? wv[v] * fv[NA - 1][v] : T(0));
             }
         }
     } else {
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
-            bool up[V], any_out = false;
+            T fv[NA][V];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) ldv<T, V>(fb + (size_t)a * Nvp + k0, fv[a]);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 sn[v] = dot_rn<D>(x[v], An);
-                up[v] = true;
-                any_out = any_out || sn[v] >= T(0);
-            }
-            T fv[V][NA];
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-#pragma unroll
-                for (int a = 0; a < NA; ++a) fv[v][a] = T(0);
-            if (any_out) foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
                 const bool out = sn[v] >= T(0);
-                T g0 = fv[v][0], g1 = NA == 2 ? fv[v][NA - 1] : T(0);
+                T g0 = fv[0][v], g1 = NA == 2 ? fv[NA - 1][v] : T(0);
                 if (!out) eq_eval<D>(S.eq, x[v], g0, g1);
                 const T t = wv[v] * sn[v];
                 T x2 = T(0);
@@ -531,30 +550,21 @@ __device__ __forceinline__ void face_state(const FaceP<D, T>& P, FaceSt<T>& S, c
     }
 }
 
-// Pass B over nodes [kb, ke): writes the per-node flux into Fo (the face's
-// rows) and, for an interior face, returns the per-thread flux-moment
-// partial sums in acc[D+2] (element type).
+// Pass B over nodes [kb, ke): writes the per-node flux over the face's foot
+// values in FB (in place) and, for an interior face, returns the per-thread
+// flux-moment partial sums in acc[D+2] (element type).
 template <int D, typename T, int NT, bool CACHE, int V>
 __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T>& S, const T* fc, int kb, int ke,
-                                            T* Fo, T* acc, int tid)
+                                            T* acc, int tid, int f)
 {
     constexpr int NA = NArr<D>::v, NW = D + 2;
     constexpr bool PACK = sizeof(T) == 4 && V == 2;
-    const T h = P.h;
     const bool inter = S.kind == 0;
-    const int L = S.L, R = inter ? S.R : S.L;
-    T An[D], rl[D], rr[D];
+    T An[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-        An[d] = S.An[d];
-        rl[d] = S.rL[d];
-        rr[d] = S.rR[d];
-    }
+    for (int d = 0; d < D; ++d) An[d] = S.An[d];
     const int Nvp = P.Nvp;
-    const T* fL = P.fin + (size_t)L * P.cstride;
-    const T* fR = P.fin + (size_t)R * P.cstride;
-    const T* gL = P.G ? P.G + (size_t)L * NA * D * Nvp : nullptr;
-    const T* gR = P.G ? P.G + (size_t)R * NA * D * Nvp : nullptr;
+    T* Fo = P.FB + (size_t)f * NA * Nvp;                // foot values in, flux out
 #pragma unroll
     for (int m = 0; m < NW; ++m) acc[m] = T(0);
     bool packed = false;
@@ -576,14 +586,10 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
 #pragma unroll
             for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
             float2 F[NA];
-            if constexpr (CACHE) {
 #pragma unroll
-                for (int a = 0; a < NA; ++a) F[a] = *reinterpret_cast<const float2*>((const float*)fc + a * Nvp + k0);
-            } else {
-                const bool up[2] = {sn.x >= 0.0f, sn.y >= 0.0f};
-                foot_face2<D, NA>((const float*)fL, (const float*)fR, (const float*)gL, (const float*)gR, Nvp, up,
-                                  k0, X, (const float*)rl, (const float*)rr, (float)h, F);
-            }
+            for (int a = 0; a < NA; ++a)
+                F[a] = CACHE ? *reinterpret_cast<const float2*>((const float*)fc + a * Nvp + k0)
+                             : __ldcg(reinterpret_cast<const float2*>((const float*)Fo + a * Nvp + k0));
             float2 gG, gH;
             eq_eval2<D>(eq, X, gG, gH);
             const float2 pG = fma2(wb, gG, mul2(wa, F[0]));
@@ -610,31 +616,21 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
-            bool up[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                sn[v] = dot_rn<D>(x[v], An);
-                up[v] = sn[v] >= T(0);
-            }
-            T fv[V][NA];
-            if constexpr (CACHE) {
+            for (int v = 0; v < V; ++v) sn[v] = dot_rn<D>(x[v], An);
+            T fv[NA][V];
 #pragma unroll
-                for (int a = 0; a < NA; ++a) {
-                    T t[V];
-                    ldv<T, V>(fc + a * Nvp + k0, t);
-#pragma unroll
-                    for (int v = 0; v < V; ++v) fv[v][a] = t[v];
-                }
-            } else {
-                foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
+            for (int a = 0; a < NA; ++a) {
+                if constexpr (CACHE) ldv<T, V>(fc + a * Nvp + k0, fv[a]);
+                else ldv<T, V>(Fo + (size_t)a * Nvp + k0, fv[a]);
             }
             T o[NA][V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 T gG, gH;
                 eq_eval<D>(S.eq, x[v], gG, gH);
-                const T pG = wa * fv[v][0] + wb * gG;
-                const T pH = NA == 2 ? wa * fv[v][NA - 1] + wb * gH : T(0);
+                const T pG = wa * fv[0][v] + wb * gG;
+                const T pH = NA == 2 ? wa * fv[NA - 1][v] + wb * gH : T(0);
                 const T t = wv[v] * sn[v];
                 T x2 = T(0);
 #pragma unroll
@@ -653,23 +649,14 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
-            bool up[V], any_out = false;
+            T fv[NA][V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                sn[v] = dot_rn<D>(x[v], An);
-                up[v] = true;
-                any_out = any_out || sn[v] >= T(0);
-            }
-            T fv[V][NA];
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-#pragma unroll
-                for (int a = 0; a < NA; ++a) fv[v][a] = T(0);
-            if (any_out) foot_face<D, NA, V>(fL, fR, gL, gR, Nvp, up, k0, x, rl, rr, h, fv);
+            for (int a = 0; a < NA; ++a) ldv<T, V>(Fo + (size_t)a * Nvp + k0, fv[a]);
             T o[NA][V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                T g0 = fv[v][0], g1 = NA == 2 ? fv[v][NA - 1] : T(0);
+                sn[v] = dot_rn<D>(x[v], An);
+                T g0 = fv[0][v], g1 = NA == 2 ? fv[NA - 1][v] : T(0);
                 if (sn[v] < T(0)) eq_eval<D>(S.eq, x[v], g0, g1);
                 o[0][v] = sn[v] * g0;
                 if (NA == 2) o[NA - 1][v] = sn[v] * g1;
@@ -684,7 +671,7 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
 template <int D, typename T, int NT, bool CACHE, int VF>
 __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF == 4 ? 5 : 7) : 4)) k_face(FaceP<D, T> P)
 {
-    constexpr int NA = NArr<D>::v, NW = D + 2;
+    constexpr int NW = D + 2;
     constexpr int NR = FaceNR<D>::v;
     __shared__ FaceSt<T> S;
     __shared__ double sw[(NT / 32) * NR];
@@ -698,13 +685,13 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF ==
     __syncthreads();
     {
         T acc[NR];
-        face_pass_a<D, T, NT, CACHE, VF>(P, S, fc, 0, P.Nv, acc, tid);
+        face_pass_a<D, T, NT, CACHE, VF>(P, S, fc, 0, P.Nv, acc, tid, f);
         block_sum_t<NR, NT>(acc, sw, red);
     }
     if (tid == 0) face_state<D, T>(P, S, red, P.AF + (size_t)f * NW);
     __syncthreads();
     T acc[NW];
-    face_pass_b<D, T, NT, CACHE, VF>(P, S, fc, 0, P.Nv, P.F + (size_t)f * NA * P.Nvp, acc, tid);
+    face_pass_b<D, T, NT, CACHE, VF>(P, S, fc, 0, P.Nv, acc, tid, f);
     if (S.kind == 0) {
         block_sum_t<NW, NT>(acc, sw, red);
         if (tid < NW) P.AF[(size_t)f * NW + tid] = red[tid];
@@ -941,30 +928,18 @@ static void grad_t(avs_ctx* c, const void* fin)
     c->launches += 1;
 }
 
-// Limited gradients and the face stage of a step: per-node face flux in
-// c->flux, area-weighted face flux of W in c->AFf (shared by the explicit and
-// the implicit step).
+// Foot values of every face (k_foot) and the face stage of a step: per-node
+// face flux in c->flux, area-weighted face flux of W in c->AFf (shared by
+// the explicit and the implicit step).
 template <int D, typename T>
 static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, double dt)
 {
     const bool f32 = sizeof(T) == 4;
     const int NA = NArr<D>::v;
-    const bool grad = c->cfg.limiter != 0;
     const size_t rows = (size_t)std::max(c->fcap, c->Nvp);   // sized for the f capacity: no reallocation
-    if (grad) {
-        const size_t need = (size_t)c->Nc * NA * D * rows * sizeof(T);
-        if (c->grad_bytes < need) {
-            if (c->grad) cudaFree(c->grad);
-            c->grad = nullptr;
-            c->grad_bytes = 0;
-            cudaError_t e = cudaMalloc(&c->grad, need);
-            if (e != cudaSuccess) return e;
-            c->grad_bytes = need;
-        }
-    }
     {
-        // room for the face flux, and for one f-sized array (the implicit step's
-        // increment) once the face flux has been used
+        // foot values, then (in place) the face flux; afterwards one f-sized
+        // array for the implicit step's increment
         const size_t need = (size_t)std::max(c->Nf, c->Nc) * NA * rows * sizeof(T);
         if (c->flux_bytes < need) {
             if (c->flux) cudaFree(c->flux);
@@ -975,23 +950,40 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
             c->flux_bytes = need;
         }
     }
-    if (grad) grad_t<D, T, NArr<D>::v>(c, fin);
     const T* xi = f32 ? (const T*)c->xi_f : (const T*)c->xi_d;
     const T* w = f32 ? (const T*)c->w_f : (const T*)c->w_d;
+    const T* An = f32 ? (const T*)c->An_f : (const T*)c->An_d;
+    const double hd = 0.5 * dt;
+    {
+        CellGeo<T> geo;
+        geo.nbr = c->nbr;
+        geo.cg = f32 ? (const T*)c->cg_f : (const T*)c->cg_d;
+        geo.r = f32 ? (const T*)c->r_f : (const T*)c->r_d;
+        geo.eps2 = f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d;
+        geo.ns = c->nslot;
+        constexpr int VG = 4;
+        const dim3 g(c->Nc, (c->Nv + 256 * VG - 1) / (256 * VG));
+        if (D == 2 && c->max_ns <= 4)
+            k_foot<D, T, VG, 4, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (T)hd,
+                                                                      (const T*)fin, (T*)c->flux, geo, c->slot, An, xi);
+        else
+            k_foot<D, T, VG, AVS_MAXS, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (T)hd,
+                                                                             (const T*)fin, (T*)c->flux, geo, c->slot,
+                                                                             An, xi);
+        c->launches += 1;
+    }
     FaceP<D, T> P;
     P.Nv = c->Nv;
     P.Nvp = c->Nvp;
     P.cstride = (size_t)NA * c->Nvp;
-    P.hd = 0.5 * dt;
+    P.hd = hd;
     P.h = (T)P.hd;
     P.R = c->cfg.R;
     P.Pr = c->cfg.Pr;
     P.omega = c->cfg.omega;
     P.mu_ref = c->mu_ref;
     P.T_ref = c->cfg.T_ref;
-    P.fin = (const T*)fin;
-    P.G = grad ? (const T*)c->grad : nullptr;
-    P.F = (T*)c->flux;
+    P.FB = (T*)c->flux;
     P.AF = c->AFf;
     P.Win = Win;
     P.xi = xi;
@@ -999,14 +991,15 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
     P.order = c->forder;
     P.faceL = c->faceL;
     P.faceR = c->faceR;
-    P.An = f32 ? (const T*)c->An_f : (const T*)c->An_d;
+    P.An = An;
     P.rL = f32 ? (const T*)c->rL_f : (const T*)c->rL_d;
     P.rR = f32 ? (const T*)c->rR_f : (const T*)c->rR_d;
     P.bc = c->bc;
     P.err = c->dev_err;
     constexpr int NT = 128;
     // foot values of pass A kept in shared memory for pass B when they fit in
-    // the default dynamic allowance (48 KB); otherwise pass B recomputes them
+    // the default dynamic allowance (48 KB); otherwise pass B re-reads the
+    // face's row
     const size_t cache_bytes = (size_t)NA * c->Nvp * sizeof(T);
     // two nodes per thread per iteration (8-byte FP32 / 16-byte FP64 vectors):
     // fewer registers and more resident warps than 16-byte FP32 vectors, which
