@@ -54,6 +54,21 @@ struct CellGeo {
     const unsigned char* __restrict__ ns;   // [Nc] number of face slots
 };
 
+// Largest / smallest of three values (PTX three-input max / min on FP32;
+// exact, like the two-input forms).
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Venkatakrishnan limiter function, capped at 1.
 template <typename T>
 __device__ __forceinline__ T venkat(T d1, T d2, T eps2)

@@ -229,28 +229,46 @@ __global__ void __launch_bounds__(256) k_foot(int Nv, int Nvp, int limiter, T h,
         for (int s = 0; s < NS; ++s) ldvn<T, VG>(fa + (size_t)nb[s] * cstride, nv[s]);
 #pragma unroll
         for (int v = 0; v < VG; ++v) {
-            T g[D];
+            T g[D], dd[NS];
 #pragma unroll
             for (int d = 0; d < D; ++d) g[d] = T(0);
-            T dmax = T(0), dmin = T(0);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                const T dd = nv[s][v] - phi[a][v];
+                dd[s] = nv[s][v] - phi[a][v];
 #pragma unroll
-                for (int d = 0; d < D; ++d) g[d] += cg[s][d] * dd;
-                dmax = dd > dmax ? dd : dmax;
-                dmin = dd < dmin ? dd : dmin;
+                for (int d = 0; d < D; ++d) g[d] += cg[s][d] * dd[s];
             }
             T L = T(1);
             if (limiter == 1) {
-                T p = T(0), n = T(0);
+                // extremes of the neighbour differences and of the face
+                // projections g . r_s (both include 0: the cell itself)
+                T d2[NS];
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    T d2 = g[0] * rr[s][0];
+                    d2[s] = g[0] * rr[s][0];
 #pragma unroll
-                    for (int d = 1; d < D; ++d) d2 += g[d] * rr[s][d];
-                    p = d2 > p ? d2 : p;
-                    n = d2 < n ? d2 : n;
+                    for (int d = 1; d < D; ++d) d2[s] += g[d] * rr[s][d];
+                }
+                T dmax, dmin, p, n;
+                if constexpr (sizeof(T) == 4 && NS == 6) {
+                    dmax = max3f(max3f(dd[0], dd[1], dd[2]), max3f(dd[3], dd[4], dd[5]), 0.0f);
+                    dmin = min3f(min3f(dd[0], dd[1], dd[2]), min3f(dd[3], dd[4], dd[5]), 0.0f);
+                    p = max3f(max3f(d2[0], d2[1], d2[2]), max3f(d2[3], d2[4], d2[5]), 0.0f);
+                    n = min3f(min3f(d2[0], d2[1], d2[2]), min3f(d2[3], d2[4], d2[5]), 0.0f);
+                } else if constexpr (sizeof(T) == 4 && NS == 4) {
+                    dmax = max3f(max3f(dd[0], dd[1], dd[2]), dd[3], 0.0f);
+                    dmin = min3f(min3f(dd[0], dd[1], dd[2]), dd[3], 0.0f);
+                    p = max3f(max3f(d2[0], d2[1], d2[2]), d2[3], 0.0f);
+                    n = min3f(min3f(d2[0], d2[1], d2[2]), d2[3], 0.0f);
+                } else {
+                    dmax = dmin = p = n = T(0);
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        dmax = dd[s] > dmax ? dd[s] : dmax;
+                        dmin = dd[s] < dmin ? dd[s] : dmin;
+                        p = d2[s] > p ? d2[s] : p;
+                        n = d2[s] < n ? d2[s] : n;
+                    }
                 }
                 if (p > T(0)) { const T t = venkat(dmax, p, e2); L = t < L ? t : L; }
                 if (n < T(0)) { const T t = venkat(dmin, n, e2); L = t < L ? t : L; }
@@ -270,6 +288,17 @@ __global__ void __launch_bounds__(256) k_foot(int Nv, int Nvp, int limiter, T h,
 #pragma unroll
             for (int d = 0; d < D; ++d) x[v][d] = xx[v * D + d];
     }
+    // phi_bar = A + G . r_s with A = phi - h G . xi, the part common to the faces
+    T A[NA][VG];
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int v = 0; v < VG; ++v) {
+            T gx = G[a][0][v] * x[v][0];
+#pragma unroll
+            for (int d = 1; d < D; ++d) gx += G[a][d][v] * x[v][d];
+            A[a][v] = phi[a][v] - h * gx;
+        }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         if (s >= ns) break;
@@ -283,7 +312,17 @@ __global__ void __launch_bounds__(256) k_foot(int Nv, int Nvp, int limiter, T h,
         bool all = true, any = false;
 #pragma unroll
         for (int v = 0; v < VG; ++v) {
-            const T sn = dot_rn<D>(x[v], an);
+            // the face kernel's xi . An (FP64: summed without contraction, so
+            // the upwind choice is the plain sequential one; FP32: any fixed
+            // formula, since only the face's two cells must agree)
+            T sn;
+            if constexpr (sizeof(T) == 8) {
+                sn = dot_rn<D>(x[v], an);
+            } else {
+                sn = x[v][0] * an[0];
+#pragma unroll
+                for (int d = 1; d < D; ++d) sn = fmaf(x[v][d], an[d], sn);
+            }
             up[v] = isR ? (sn < T(0)) : (sn >= T(0));
             all = all && up[v];
             any = any || up[v];
@@ -295,9 +334,9 @@ __global__ void __launch_bounds__(256) k_foot(int Nv, int Nvp, int limiter, T h,
             T out[VG];
 #pragma unroll
             for (int v = 0; v < VG; ++v) {
-                T val = phi[a][v];
+                T val = A[a][v];
 #pragma unroll
-                for (int d = 0; d < D; ++d) val += G[a][d][v] * (rr[s][d] - x[v][d] * h);
+                for (int d = 0; d < D; ++d) val += G[a][d][v] * rr[s][d];
                 out[v] = val;
             }
             if (all) {
@@ -326,6 +365,10 @@ __device__ __forceinline__ void load_nodes(const PP& P, int k0, T (*x)[D], T* w)
         constexpr int PER = 16 / sizeof(T);
 #pragma unroll
         for (int j = 0; j < V * D / PER; ++j) ldv<T, PER>(P.xi + (size_t)k0 * D + j * PER, xx + j * PER);
+    } else if constexpr (sizeof(T) == 4 && (V * D) % 2 == 0) {
+        // 8-byte pairs (k0 is a multiple of V, so k0 D is even)
+#pragma unroll
+        for (int j = 0; j < V * D / 2; ++j) ldv<T, 2>(P.xi + (size_t)k0 * D + 2 * j, xx + 2 * j);
     } else {
 #pragma unroll
         for (int j = 0; j < V * D; ++j) xx[j] = P.xi[(size_t)k0 * D + j];
@@ -449,6 +492,7 @@ __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T
         float2 acc2[NM];
 #pragma unroll
         for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
+#pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V];
             load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
@@ -471,6 +515,7 @@ __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T
     }
     if (packed) {
     } else if (inter) {
+#pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V];
             load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
@@ -489,6 +534,7 @@ __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T
             }
         }
     } else {
+#pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
@@ -576,6 +622,7 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
         float2 acc2[NW];
 #pragma unroll
         for (int m = 0; m < NW; ++m) acc2[m] = bc2(0.0f);
+#pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V];
             load_nodes<D, V>(P, k0, x, wv);
@@ -613,6 +660,7 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
     if (packed) {
     } else if (inter) {
         const T wa = S.wa, wb = S.wb;
+#pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
@@ -646,6 +694,7 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
             for (int a = 0; a < NA; ++a) stv<T, V>(Fo + (size_t)a * Nvp + k0, o[a]);
         }
     } else {
+#pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
             T x[V][D], wv[V], sn[V];
             load_nodes<D, V>(P, k0, x, wv);
@@ -1003,7 +1052,8 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
     const size_t cache_bytes = (size_t)NA * c->Nvp * sizeof(T);
     // two nodes per thread per iteration (8-byte FP32 / 16-byte FP64 vectors):
     // fewer registers and more resident warps than 16-byte FP32 vectors, which
-    // the latency-bound face passes prefer
+    // the latency-bound face passes prefer; the node loops are unrolled twice
+    // so that two iterations' loads are in flight together
     constexpr int VF = 2;
     // small velocity meshes (the Sec. 3.5 spaces): one warp per face, so that
     // threads are not left idle and the block's serial state section holds no
