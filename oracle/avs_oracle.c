@@ -493,11 +493,15 @@ static double venkat(double d1, double d2, double eps2)
 /* Step 1 of the step: least-squares gradient (weights 1/|d|^2) of every cell,
  * array and node, and its Venkatakrishnan limiter factor L (Sec. 2.3.3, R6):
  * grad [Nc][nA][Nv][D] unlimited gradient, lim [Nc][nA][Nv] the factor, so the
- * limited gradient is lim * grad.  epsilon^2 = (K dx)^3 with dx = |V|^(1/D);
- * the limiter is the least Venkatakrishnan value over the cell's faces, taken
- * with the largest (smallest) neighbour difference on faces where the
- * unlimited change grad . r is positive (negative).  A cell whose LSQ matrix
- * is singular gets a zero gradient. */
+ * limited gradient is lim * grad.  epsilon^2 = (K dx)^3 phi_C^2 with
+ * dx = |V|^(1/D) and phi_C the cell's own value of the array at the node:
+ * the (K dx)^3 of the limiter for a quantity of unit size, scaled to the size
+ * of the limited value, so that the factor is the same for f and any
+ * multiple of f (the distribution spans many orders of magnitude over the
+ * velocity nodes).  The limiter is the least Venkatakrishnan value over the
+ * cell's faces, taken with the largest (smallest) neighbour difference on
+ * faces where the unlimited change grad . r is positive (negative).  A cell
+ * whose LSQ matrix is singular gets a zero gradient. */
 static void limited_gradients(const om_mesh *m, const om_gas *g, int Nv, const double *f_in, const slots_t *S,
                               double *grad, double *lim)
 {
@@ -546,8 +550,9 @@ static void limited_gradients(const om_mesh *m, const om_gas *g, int Nv, const d
                             double d2 = 0.0;
                             for (int c = 0; c < D; ++c) d2 += gr[c] * r[c];
                             double psi = 1.0;
-                            if (d2 > 0.0) psi = venkat(dmax, d2, eps2[i]);
-                            else if (d2 < 0.0) psi = venkat(dmin, d2, eps2[i]);
+                            const double e2 = eps2[i] * phi_i * phi_i;
+                            if (d2 > 0.0) psi = venkat(dmax, d2, e2);
+                            else if (d2 < 0.0) psi = venkat(dmin, d2, e2);
                             if (psi < L) L = psi;
                         }
                     }

@@ -79,60 +79,6 @@ __device__ __forceinline__ T venkat(T d1, T d2, T eps2)
     return v < T(1) ? v : T(1);
 }
 
-// Limited least-squares gradient of array `fa` (pointer already offset to
-// array and node) at cell C.  Returns phi_C; gr and L receive the gradient
-// and the limiter value.  The limiter is the minimum over the faces of the
-// capped Venkatakrishnan function; because the capped function is
-// non-increasing in |Delta_2| on each side of zero, that minimum is reached
-// at the largest positive and the most negative face projection.
-template <int D, typename T>
-__device__ __forceinline__ T grad_lim(const CellGeo<T>& g, int limiter, const T* __restrict__ fa,
-                                      size_t cstride, int C, T* gr, T& L)
-{
-    const T phi = fa[(size_t)C * cstride];
-#pragma unroll
-    for (int d = 0; d < D; ++d) gr[d] = T(0);
-    L = T(1);
-    if (limiter == 0) return phi;
-    const int ns = g.ns[C];
-    T dmax = T(0), dmin = T(0);
-    for (int s = 0; s < ns; ++s) {
-        const int nb = g.nbr[C * AVS_MAXS + s];
-        if (nb < 0) continue;
-        const T d = fa[(size_t)nb * cstride] - phi;
-        const T* c = g.cg + (size_t)(C * AVS_MAXS + s) * D;
-#pragma unroll
-        for (int k = 0; k < D; ++k) gr[k] += c[k] * d;
-        dmax = d > dmax ? d : dmax;
-        dmin = d < dmin ? d : dmin;
-    }
-    if (limiter == 1) {
-        T p = T(0), n = T(0);
-        for (int s = 0; s < ns; ++s) {
-            const T* r = g.r + (size_t)(C * AVS_MAXS + s) * D;
-            T d2 = gr[0] * r[0];
-#pragma unroll
-            for (int k = 1; k < D; ++k) d2 += gr[k] * r[k];
-            p = d2 > p ? d2 : p;
-            n = d2 < n ? d2 : n;
-        }
-        const T e2 = g.eps2[C];
-        if (p > T(0)) { T v = venkat(dmax, p, e2); L = v < L ? v : L; }
-        if (n < T(0)) { T v = venkat(dmin, n, e2); L = v < L ? v : L; }
-    }
-    return phi;
-}
-
-// Foot value phi_C + L grad . (x_f - x_C - xi h)   (Sec. 2.3.3)
-template <int D, typename T>
-__device__ __forceinline__ T foot_value(T phi, const T* gr, T L, const T* rF, const T* x, T h)
-{
-    T dot = gr[0] * (rF[0] - x[0] * h);
-#pragma unroll
-    for (int k = 1; k < D; ++k) dot += gr[k] * (rF[k] - x[k] * h);
-    return phi + L * dot;
-}
-
 // ---------------------------------------------------------------- equilibria
 // Parameters of one equilibrium evaluated on the nodes:
 //   G = pref exp(-|c|^2 inv2RT) (1 + (c . alpha)(|c|^2 invRT - D - 2)),

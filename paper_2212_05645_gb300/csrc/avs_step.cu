@@ -3,7 +3,8 @@
 //
 // k_foot: one thread block per (cell, node chunk).  The limited
 //   least-squares gradient L grad phi of the cell (Sec. 2.3.3: weights
-//   1/|d|^2, Venkatakrishnan limiter) at each node, kept in registers, and the
+//   1/|d|^2, Venkatakrishnan limiter with epsilon^2 = (K dx)^3 phi_C^2) at
+//   each node, kept in registers, and the
 //   foot values phi_C + (L grad phi)_C . (x_f - xi h - x_C) of every face of
 //   the cell at the nodes where the cell is upwind (sign of xi . An), written
 //   to the face's row: each face node gets its foot value exactly once.
@@ -173,8 +174,10 @@ __global__ void __launch_bounds__(256) k_grad(int Nv, int Nvp, int limiter, cons
                     p = d2 > p ? d2 : p;
                     n = d2 < n ? d2 : n;
                 }
-                if (p > T(0)) { const T t = venkat(dmax, p, e2); L = t < L ? t : L; }
-                if (n < T(0)) { const T t = venkat(dmin, n, e2); L = t < L ? t : L; }
+                // epsilon^2 = (K dx)^3 phi_C^2: scaled to the limited value (R6)
+                const T e2p = e2 * phi[v] * phi[v];
+                if (p > T(0)) { const T t = venkat(dmax, p, e2p); L = t < L ? t : L; }
+                if (n < T(0)) { const T t = venkat(dmin, n, e2p); L = t < L ? t : L; }
             }
 #pragma unroll
             for (int d = 0; d < D; ++d) out[d][v] = L * g[d];
@@ -270,8 +273,10 @@ __global__ void __launch_bounds__(256) k_foot(int Nv, int Nvp, int limiter, T h,
                         n = d2[s] < n ? d2[s] : n;
                     }
                 }
-                if (p > T(0)) { const T t = venkat(dmax, p, e2); L = t < L ? t : L; }
-                if (n < T(0)) { const T t = venkat(dmin, n, e2); L = t < L ? t : L; }
+                // epsilon^2 = (K dx)^3 phi_C^2: scaled to the limited value (R6)
+                const T e2p = e2 * phi[a][v] * phi[a][v];
+                if (p > T(0)) { const T t = venkat(dmax, p, e2p); L = t < L ? t : L; }
+                if (n < T(0)) { const T t = venkat(dmin, n, e2p); L = t < L ? t : L; }
             }
             if (limiter == 0) L = T(0);          // first order: phi_bar = phi_C
 #pragma unroll
@@ -1067,8 +1072,13 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
             done = true;
         }
     }
+    // the default allowance covers static and dynamic shared memory together:
+    // the block's own arrays (state, reductions: under 2 KB) come first
+    constexpr size_t kStaticFace = 2048;
+    static_assert(sizeof(FaceSt<T>) + (NT / 32 + 1) * FaceNR<D>::v * sizeof(double) <= kStaticFace,
+                  "static shared memory of the face block");
     if (done) {
-    } else if (cache_bytes <= 48 * 1024)
+    } else if (cache_bytes + kStaticFace <= 48 * 1024)
         k_face<D, T, NT, true, VF><<<c->Nf, NT, cache_bytes, c->stream>>>(P);
     else
         k_face<D, T, NT, false, VF><<<c->Nf, NT, 0, c->stream>>>(P);

@@ -226,11 +226,12 @@ def test_limited_gradient_three_cell_ring_by_hand():
       middle cell: central difference (3 - 0)/(2h) = 4.5; face changes +-0.75;
         largest / smallest neighbour differences 2 and -1; the + side gives
         y = 8/3 (capped at 1), the - side y = 4/3, so L = 20/23 at epsilon = 0;
-        with epsilon^2 = (K dx)^3, K = 0.3, dx = |V|^(1/2) = (1/3)^(1/2):
-        L = (2.5 + eps^2) / (2.875 + eps^2);
+        with epsilon^2 = (K dx)^3 phi_C^2, K = 0.3, dx = |V|^(1/2) = (1/3)^(1/2),
+        phi_C = 1: L = (2.5 + eps^2) / (2.875 + eps^2);
       end cells: local minimum and maximum, L = 0.
+    The H array holds 2 phi: the same factor (epsilon scales with the value).
     Catches a wrong LSQ weight, a limiter over the wrong neighbour difference
-    or face offset, and a different epsilon (K, power or length scale)."""
+    or face offset, and a different epsilon (K, power, length or value scale)."""
     m = wl.cartesian_mesh((3, 1), (1.0, 1.0), periodic=(True, True))
     mh = O.MeshHandle(m)
     phi = np.array([0.0, 1.0, 3.0])
@@ -249,9 +250,28 @@ def test_limited_gradient_three_cell_ring_by_hand():
     _, lim = O.limited_gradients(mh, g, f)
     e2 = (0.3 * math.sqrt(1.0 / 3.0)) ** 3
     assert lim[1, 0, 0] == pytest.approx((2.5 + e2) / (2.875 + e2), rel=1e-14)
-    # H = 2 G: differences of 4 and -2, face changes +-1.5 (epsilon is not scaled)
-    assert lim[1, 1, 0] == pytest.approx((10.0 + e2) / (11.5 + e2), rel=1e-14)
+    # H = 2 G: differences of 4 and -2, face changes +-1.5, phi_C = 2: epsilon^2 4 e2
+    assert lim[1, 1, 0] == pytest.approx((10.0 + 4.0 * e2) / (11.5 + 4.0 * e2), rel=1e-14)
+    assert lim[1, 1, 0] == pytest.approx(lim[1, 0, 0], rel=1e-14)
 
     g2 = O.gas(Kn=1.0, limiter=2)                                      # unlimited
     _, lim = O.limited_gradients(mh, g2, f)
     assert np.all(lim == 1.0)
+
+
+def test_limiter_factor_is_scale_free():
+    """Reading R6: epsilon^2 = (K dx)^3 phi_C^2 scales with the limited value,
+    so the limiter factor of c f equals that of f at every cell and node, for
+    c over twelve orders of magnitude (f spans as many over the velocity
+    nodes); with the unscaled epsilon^2 = (K dx)^3 the factor of a small
+    multiple of f would be 1 (no limiting in the tails of the distribution)."""
+    m = wl.cartesian_mesh((6, 5), (1.0, 1.0), periodic=(True, True))
+    mh = O.MeshHandle(m)
+    rng = np.random.default_rng(17)
+    f = rng.uniform(0.2, 1.0, size=(m.Nc, 2, 7))
+    g = O.gas(Kn=1.0, limiter=1)
+    _, lim = O.limited_gradients(mh, g, f)
+    assert (lim < 1.0).mean() > 0.3                     # the limiter acts on this field
+    for c in (1e-9, 1e-3, 1e3):
+        _, lc = O.limited_gradients(mh, g, c * f)
+        assert np.allclose(lc, lim, rtol=1e-12, atol=0), c
