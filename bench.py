@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU (oracle) baseline leg")
     ap.add_argument("--no-ablation", action="store_true", help="skip the plain-criterion ablation leg")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="form of the timed leg: mixed (the benchmark) or the plain FP64 form (profiling)")
     ap.add_argument("--workload", default="sphere", choices=sorted(WORKLOADS),
                     help="sphere (the benchmark case) or another configuration")
     ap.add_argument("--oracle-threads", type=int, default=0,
@@ -308,12 +310,12 @@ def run_gpu(args):
         else:
             ctx.step(n)
 
-    # Every bench step is one batch: a flow started from the resident initial
-    # field W0, nu UGKS steps and one adaptation.  The hypersonic flows are
-    # not carried from one bench step to the next: from the rest start, the
-    # explicit step as read here drives f negative next to the far field
-    # within a few hundred steps (about 670 on the cylinder), so a batch
-    # always starts again from W0.
+    # Every bench step is one batch: a flow started from the initial field W0
+    # (device-resident here, uploaded from pinned host memory in the e2e
+    # leg), nu UGKS steps and one adaptation, so that every timed bench step
+    # is the same job; the velocity mesh carries over from the previous
+    # batch's adaptation (the flows themselves run stably for thousands of
+    # steps; tests/test_gpu_long_runs.py).
     def bench_step(ctx, updates, n=nu):
         ctx.init_field(W0)
         advance(ctx, n)
@@ -331,10 +333,15 @@ def run_gpu(args):
     def make(precision, learned_, **kw):
         return A.AVS(w, precision=precision, stream=stream.cuda_stream, learned=learned_, full_every=4, **kw)
 
-    # ---- headline: mixed + learned, device-timed
-    g = make("mixed", learned)
+    # ---- headline: mixed + learned, device-timed (--precision fp64: the plain
+    # FP64 form instead, for profiling)
+    main_fp64 = args.precision == "fp64"
+    if main_fp64:
+        learned = False
+    g = make("fp64" if main_fp64 else "mixed", learned)
     NA, NW = g.NA, g.NW
-    f_bytes = Nc * NA * g.Nv * 4
+    esize = 8 if main_fp64 else 4
+    f_bytes = Nc * NA * g.Nv * esize
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if f_bytes < 2 * l2 else None
     for _ in range(args.warmup):
         bench_step(g, [])
@@ -376,7 +383,7 @@ def run_gpu(args):
 
     # roofline of the UGKS step (the step kernels; 90+ % of a bench step):
     # algorithmic traffic = 1 read + 1 write of f in FP32 per cell-node
-    bytes_per_cn = 2 * NA * 4
+    bytes_per_cn = 2 * NA * esize
     kern_ms = sum(step_ms) / (args.steps * nu)
     cn_per_launch = statistics.mean(step_cells)
     achieved = bytes_per_cn * cn_per_launch / (kern_ms * 1e-3) / 1e9
@@ -491,9 +498,10 @@ def run_gpu(args):
         f_mb = f_bytes / 1e6
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if main_fp64 else "f32+f64", "data": "synthetic",
                 "config": {"workload": w.name, "cells": Nc, "velocity_nodes": Nv_last,
-                           "ugks_steps_per_step": nu, "precision": "mixed (f FP32, sums FP64)",
+                           "ugks_steps_per_step": nu,
+                           "precision": "FP64" if main_fp64 else "mixed (f FP32, sums FP64)",
                            "time_step": (f"implicit IUGKS, CFL {args.implicit}, 60 macro + 2 micro SGS iterations"
                                          if args.implicit > 0 else "explicit, CFL 0.8"),
                            "adaptation": ("learned proposer, full criterion every 4th adaptation" if learned
