@@ -84,6 +84,8 @@ WORKLOADS = {
     "sphere-r8": ("sphere", dict(n_r=8)),
     # the sphere's inner 4 radial shells (detailed ncu captures: f = 0.55 GB, a few GB on the device)
     "sphere-r4": ("sphere", dict(n_r=4)),
+    # the sphere's inner 2 radial shells (captures of the FP64 form: f = 0.8 GB in FP64)
+    "sphere-r2": ("sphere", dict(n_r=2)),
     # the cylinder with the velocity space of the adaptive-parameter rules (zones, C1(Ma))
     "cylinder-zones": ("cylinder_zones", dict()),
     # the cylinder with a diatomic gas (Rykov model: G, H, R; no learned proposer)
@@ -229,6 +231,7 @@ ORACLE_SAMPLES = {
     "sphere": ("sphere", dict(n_r=2, learned=False), "the first 2 radial shells (4608 cells)"),
     "sphere-r8": ("sphere", dict(n_r=2, learned=False), "the first 2 radial shells (4608 cells)"),
     "sphere-r4": ("sphere", dict(n_r=2, learned=False), "the first 2 radial shells (4608 cells)"),
+    "sphere-r2": ("sphere", dict(n_r=2, learned=False), "the first 2 radial shells (4608 cells)"),
     "cylinder-zones": ("cylinder_zones", dict(), "the whole 128 x 96 O-mesh (12288 cells)"),
     "cylinder-rykov": ("cylinder", dict(n_r=12, model="rykov"), "the first 12 radial rows (1152 cells)"),
     "cylinder-rykov-r64": ("cylinder", dict(n_r=12, model="rykov"), "the first 12 radial rows (1152 cells)"),
