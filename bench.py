@@ -398,10 +398,10 @@ def run_gpu(args):
             "traffic": traffic,
             "kernel": (f"implicit Rykov UGKS step: k_grad + rk_face + rk_imp_setup + rk_imp_macro + rk_imp_res"
                        f" + rk_imp_micro + rk_imp_finish <{w.D},float>" if args.implicit > 0 and w.model == "rykov" else
-                       f"implicit UGKS step: k_grad + k_face + k_imp_setup + k_imp_macro + k_imp_state + k_imp_res"
+                       f"implicit UGKS step: k_foot + k_face + k_imp_setup + k_imp_macro + k_imp_state + k_imp_res"
                        f" + k_imp_micro + k_imp_finish <{w.D},float>" if args.implicit > 0 else
                        f"Rykov UGKS step: k_grad + rk_face + rk_cell <{w.D},float>" if w.model == "rykov" else
-                       f"UGKS step: k_grad + k_face + k_cell_state + k_cell <{w.D},float>"),
+                       f"UGKS step: k_foot + k_face + k_cell_state + k_cell <{w.D},{'double' if main_fp64 else 'float'}>"),
             "peak_source": peak_kind,
             "algorithmic_bytes_per_cell_node": bytes_per_cn, "kernel_ms": kern_ms,
             "peak_spec_gbs": 8000.0, "frac_of_spec": achieved / 8000.0}
