@@ -177,7 +177,9 @@ avs_status avs_dt(avs_ctx *ctx, double cfl, double *dt_out);
  * multiscale flux (Eq. equ28), conservative W update, implicit-collision
  * update of f (diagonal of Eq. SGS_phi).  dt from cfl (avs_dt); dt_out
  * nullable.  Does not synchronise; numeric failures surface at the next
- * blocking call as AVS_ENUMERIC. */
+ * blocking call as AVS_ENUMERIC, and an asynchronous copy of the FP32 face
+ * kernel that did not complete within its bound (about a second) as
+ * AVS_ETIMEOUT. */
 avs_status ugks_step(avs_ctx *ctx, int nsteps, double cfl, double *dt_out);
 avs_status ugks_step_dt(avs_ctx *ctx, int nsteps, double dt);
 

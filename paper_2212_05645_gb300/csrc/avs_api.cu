@@ -111,6 +111,10 @@ avs_status read_err(avs_ctx* c)
     int e = 0;
     CK(cudaMemcpyAsync(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (e & 4) {
+        CK(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+        return fail(c, AVS_ETIMEOUT, "an asynchronous copy into the face kernel's shared memory did not complete");
+    }
     if (e & 2) {
         CK(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
         return fail(c, AVS_ETIMEOUT, "a grid barrier of the implicit macroscopic sweep gave up");

@@ -84,7 +84,7 @@ struct avs_ctx {
     float *Mthr = nullptr;                           // [cap][4] label thresholds per node
     double *stage = nullptr;                         // FP64 staging [Nc][NA][Nv] for get/set (lazy)
     size_t stage_elems = 0;
-    int *dev_err = nullptr;                          // device error word (bit 1: numeric)
+    int *dev_err = nullptr;                          // device error word (1: numeric, 2: grid barrier, 4: staged copy)
     unsigned long long *dt_key = nullptr;
     double *gap_d = nullptr;                         // correction gap (max over cells)
     double dt_unit = 0.0;

@@ -752,6 +752,218 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 32 : ((sizeof(T) == 4) ? (VF ==
     }
 }
 
+// ---- k_face_staged: the FP32 face kernel for rows beyond the shared-memory
+// cache.  Same passes, state and arithmetic as k_face's packed path; the
+// face's foot-value row (and, with SXI, the node coordinates and weights,
+// which otherwise come by direct loads) reach shared memory by asynchronous
+// 1D bulk copies in stages of CH nodes, double-buffered on two mbarriers, so
+// that the loads of stage g+1 (and the first stages of pass B, during the
+// state computation) overlap the work on stage g.  Offsets and sizes are multiples of 16 bytes by construction (rows
+// of Nvp = 32 m nodes, stages of CH = 32 n nodes, the last one cut at Nvp).  Every
+// wait is bounded (about a second); a wait that gives up sets bit 4 of the
+// error word (AVS_ETIMEOUT at the next blocking call) and the block drains its
+// copies, again with a bound, before it leaves.
+template <int D, int CH, bool SXI>
+struct StageFloats { static constexpr int v = (NArr<D>::v + (SXI ? D + 1 : 0)) * CH; };
+constexpr long long kWaitCycles = 2000000000ll;
+
+template <int D, int NT, int CH, bool SXI>
+__global__ void __launch_bounds__(NT, 7) k_face_staged(FaceP<D, float> P)
+{
+    constexpr int NA = NArr<D>::v, NM = NMom<D>::v, NW = D + 2;
+    constexpr int NR = FaceNR<D>::v;
+    static_assert(CH % 32 == 0 && CH % (2 * NT) == 0, "stage: whole node pairs per thread, 128-byte rows");
+    __shared__ FaceSt<float> S;
+    __shared__ double sw[(NT / 32) * NR];
+    __shared__ double red[NR];
+    extern __shared__ __align__(128) float stg[];   // two stages of SF floats
+    constexpr int SF = StageFloats<D, CH, SXI>::v;
+    __shared__ __align__(8) unsigned long long full[2];
+    __shared__ int bad, gbad, nissued;           // timeout flag, first stage given up, stages issued
+
+    const int tid = threadIdx.x;
+    const int f = P.order[blockIdx.x];
+    if (tid == 0) {
+        face_setup<D, float>(P, f, S);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init_fence();
+        bad = 0;
+        gbad = 1 << 30;
+        nissued = 0;
+    }
+    __syncthreads();
+    if (S.kind != 0) {
+        // boundary face: the direct-load passes
+        float acc[NR];
+        face_pass_a<D, float, NT, false, 2>(P, S, nullptr, 0, P.Nv, acc, tid, f);
+        block_sum_t<NR, NT>(acc, sw, red);
+        if (tid == 0) face_state<D, float>(P, S, red, P.AF + (size_t)f * NW);
+        __syncthreads();
+        float accb[NW];
+        face_pass_b<D, float, NT, false, 2>(P, S, nullptr, 0, P.Nv, accb, tid, f);
+        return;
+    }
+    const int Nv = P.Nv, Nvp = P.Nvp;
+    const int nst = (Nv + CH - 1) / CH;          // stages per pass
+    const int ng = 2 * nst;                      // pass A stages, then pass B stages
+    float* row = P.FB + (size_t)f * NA * Nvp;
+    auto issue = [&](int g) {                    // thread 0
+        const int b = g & 1;
+        const int k0 = (g < nst ? g : g - nst) * CH;
+        const int n = min(CH, Nvp - k0);         // a multiple of 32 nodes
+        const unsigned bytes = (unsigned)n * 4u;
+        float* dst = stg + b * SF;
+        nissued = g + 1;
+        mbar_arrive_expect_tx(&full[b], bytes * (unsigned)(NA + (SXI ? D + 1 : 0)));
+#pragma unroll
+        for (int a = 0; a < NA; ++a) bulk_g2s(dst + a * CH, row + (size_t)a * Nvp + k0, bytes, &full[b]);
+        if constexpr (SXI) {
+            bulk_g2s(dst + NA * CH, P.xi + (size_t)k0 * D, bytes * D, &full[b]);
+            bulk_g2s(dst + (NA + D) * CH, P.w + k0, bytes, &full[b]);
+        }
+    };
+    // node pair (k, k+1) = stage offsets (kk, kk+1): from the stage, or
+    // direct loads (the coordinates and weights are shared by all faces)
+    auto stage_nodes = [&](const float* st, int k, int kk, float2 (&X)[D], float2& W2) {
+        if constexpr (SXI) {
+            const float* xv = st + NA * CH + kk * D;
+            float xx[2 * D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const float2 t = *reinterpret_cast<const float2*>(xv + 2 * j);
+                xx[2 * j] = t.x;
+                xx[2 * j + 1] = t.y;
+            }
+#pragma unroll
+            for (int d = 0; d < D; ++d) X[d] = make_float2(xx[d], xx[D + d]);
+            W2 = *reinterpret_cast<const float2*>(st + (NA + D) * CH + kk);
+        } else {
+            float x[2][D], wv[2];
+            load_nodes<D, 2>(P, k, x, wv);
+#pragma unroll
+            for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
+            W2 = make_float2(wv[0], wv[1]);
+        }
+    };
+    auto wait = [&](int g) {
+        if (bad) return;                         // a wait gave up: no further waits
+        if (!mbar_wait_bounded(&full[g & 1], (unsigned)((g >> 1) & 1), kWaitCycles)) {
+            atomicOr(P.err, 4);
+            atomicMin(&gbad, g);
+            bad = 1;
+        }
+    };
+    if (tid == 0) {
+        // after a wait that gave up anywhere, later blocks issue no copies
+        if (*(volatile int*)P.err & 4) bad = 2;
+        if (!bad) {
+            issue(0);
+            if (ng > 1) issue(1);
+        }
+    }
+    __syncthreads();
+    if (bad) return;
+    float Vt[D], An[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        Vt[d] = S.Vt[d];
+        An[d] = S.An[d];
+    }
+    // ---------------- pass A: raw moments of the foot values about V
+    float2 acc2[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
+    for (int g = 0; g < nst; ++g) {
+        wait(g);
+        const float* st = stg + (g & 1) * SF;
+        const int k0 = g * CH;
+#pragma unroll 2
+        for (int kk = tid * 2; kk < CH; kk += NT * 2) {
+            if (k0 + kk >= Nv) break;
+            float2 X[D], W2;
+            stage_nodes(st, k0 + kk, kk, X, W2);
+            float2 F[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) F[a] = *reinterpret_cast<const float2*>(st + a * CH + kk);
+            float2 xs[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-Vt[d]));
+            raw_acc2<D>(acc2, xs, mul2(W2, F[0]), NA == 2 ? mul2(W2, F[NA - 1]) : bc2(0.0f));
+        }
+        __syncthreads();
+        if (tid == 0 && g + 2 < ng && !bad) {
+            fence_proxy_async_smem();
+            issue(g + 2);
+        }
+    }
+    {
+        float acc[NR];
+#pragma unroll
+        for (int m = 0; m < NR; ++m) acc[m] = m < NM ? acc2[m].x + acc2[m].y : 0.0f;
+        block_sum_t<NR, NT>(acc, sw, red);
+    }
+    if (tid == 0) face_state<D, float>(P, S, red, P.AF + (size_t)f * NW);
+    __syncthreads();
+    // ---------------- pass B: per-node flux of the interface distribution
+    const float2 wa = bc2(S.wa), wb = bc2(S.wb);
+    const EqPar<float> eq = S.eq;
+    float2 accB[NW];
+#pragma unroll
+    for (int m = 0; m < NW; ++m) accB[m] = bc2(0.0f);
+    for (int g = nst; g < ng; ++g) {
+        wait(g);
+        const float* st = stg + (g & 1) * SF;
+        const int k0 = (g - nst) * CH;
+#pragma unroll 2
+        for (int kk = tid * 2; kk < CH; kk += NT * 2) {
+            const int k = k0 + kk;
+            if (k >= Nv) break;
+            float2 X[D], W2;
+            stage_nodes(st, k0 + kk, kk, X, W2);
+            float2 F[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) F[a] = *reinterpret_cast<const float2*>(st + a * CH + kk);
+            float2 sn = mul2(X[0], bc2(An[0]));
+#pragma unroll
+            for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
+            float2 gG, gH;
+            eq_eval2<D>(eq, X, gG, gH);
+            const float2 pG = fma2(wb, gG, mul2(wa, F[0]));
+            const float2 pH = NA == 2 ? fma2(wb, gH, mul2(wa, F[NA - 1])) : bc2(0.0f);
+            const float2 t = mul2(W2, sn);
+            float2 x2 = mul2(X[0], X[0]);
+#pragma unroll
+            for (int d = 1; d < D; ++d) x2 = fma2(X[d], X[d], x2);
+            accB[0] = fma2(t, pG, accB[0]);
+            const float2 tp = mul2(t, pG);
+#pragma unroll
+            for (int d = 0; d < D; ++d) accB[1 + d] = fma2(tp, X[d], accB[1 + d]);
+            accB[D + 1] = fma2(mul2(t, bc2(0.5f)), fma2(x2, pG, pH), accB[D + 1]);
+            *reinterpret_cast<float2*>(row + k) = mul2(sn, pG);
+            if (NA == 2) *reinterpret_cast<float2*>(row + (size_t)(NA - 1) * Nvp + k) = mul2(sn, pH);
+        }
+        __syncthreads();
+        if (tid == 0 && g + 2 < ng && !bad) {
+            fence_proxy_async_smem();
+            issue(g + 2);
+        }
+    }
+    {
+        float acc[NW];
+#pragma unroll
+        for (int m = 0; m < NW; ++m) acc[m] = accB[m].x + accB[m].y;
+        block_sum_t<NW, NT>(acc, sw, red);
+        if (tid < NW) P.AF[(size_t)f * NW + tid] = red[tid];
+    }
+    // a wait that gave up leaves copies in flight: drain them (bounded) before
+    // the block's shared memory is released
+    if (bad && tid == 0) {
+        for (int g = gbad; g < nissued; ++g)
+            mbar_wait_bounded(&full[g & 1], (unsigned)((g >> 1) & 1), kWaitCycles);
+    }
+}
+
 // ------------------------------------------------------------------ k_cell
 // Per-cell parameters of the collision update, written by k_cell_state.
 template <typename T>
@@ -1078,10 +1290,26 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
     static_assert(sizeof(FaceSt<T>) + (NT / 32 + 1) * FaceNR<D>::v * sizeof(double) <= kStaticFace,
                   "static shared memory of the face block");
     if (done) {
-    } else if (cache_bytes + kStaticFace <= 48 * 1024)
+    } else if (cache_bytes + kStaticFace <= 48 * 1024) {
         k_face<D, T, NT, true, VF><<<c->Nf, NT, cache_bytes, c->stream>>>(P);
-    else
+    } else if constexpr (sizeof(T) == 4) {
+        // rows beyond the cache: bulk-copy stages in shared memory (rows of
+        // Nvp = 32 m FP32 values keep every copy 16-byte aligned)
+        // measured on GB300 (2D wedge, 12k nodes; 3D sphere, 21k nodes):
+        // 2D: stages of 1024 nodes with the node coordinates and weights;
+        // 3D: stages of 2048 nodes, coordinates and weights loaded directly
+        constexpr int CH = D == 2 ? 1024 : 2048;
+        constexpr bool SXI = D == 2;
+        constexpr size_t smem = 2 * sizeof(float) * StageFloats<D, CH, SXI>::v;
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(k_face_staged<D, NT, CH, SXI>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_face_staged<D, NT, CH, SXI><<<c->Nf, NT, smem, c->stream>>>(P);
+    } else {
         k_face<D, T, NT, false, VF><<<c->Nf, NT, 0, c->stream>>>(P);
+    }
     c->launches += 1;
 
     return cudaGetLastError();
