@@ -355,6 +355,191 @@ __global__ void __launch_bounds__(256) k_foot(int Nv, int Nvp, int limiter, T h,
     }
 }
 
+// k_foot for the FP32 form in packed two-lane arithmetic: four nodes per
+// thread as two pairs, each lane doing k_foot's operations (the same products
+// and fused multiply-adds in the same order, so the same foot values; the
+// limiter's two ratios are evaluated in both lanes and selected per lane).
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, bc2(-1.0f), a); }   // a - b, one rounding
+
+template <int NS>
+__device__ __forceinline__ void ext4(const float* v, float& mx, float& mn)
+{
+    if constexpr (NS == 6) {
+        mx = max3f(max3f(v[0], v[1], v[2]), max3f(v[3], v[4], v[5]), 0.0f);
+        mn = min3f(min3f(v[0], v[1], v[2]), min3f(v[3], v[4], v[5]), 0.0f);
+    } else if constexpr (NS == 4) {
+        mx = max3f(max3f(v[0], v[1], v[2]), v[3], 0.0f);
+        mn = min3f(min3f(v[0], v[1], v[2]), v[3], 0.0f);
+    } else {
+        mx = mn = 0.0f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            mx = fmaxf(mx, v[s]);
+            mn = fminf(mn, v[s]);
+        }
+    }
+}
+
+// Venkatakrishnan ratio of venkat() in two lanes (division as a reciprocal
+// and a product, like fdiv); capped at 1
+__device__ __forceinline__ float2 venkat2(float2 d1, float2 d2, float2 eps2)
+{
+    const float2 d11 = mul2(d1, d1);
+    const float2 num = fma2(mul2(bc2(2.0f), d1), d2, add2(d11, eps2));
+    const float2 den = add2(fma2(d1, d2, fma2(mul2(bc2(2.0f), d2), d2, d11)), eps2);
+    const float2 v = make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+    return make_float2(v.x < 1.0f ? v.x : 1.0f, v.y < 1.0f ? v.y : 1.0f);
+}
+
+template <int D, int NS, int NA>
+__global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter, float h, const float* __restrict__ f,
+                                                 float* __restrict__ FB, CellGeo<float> geo,
+                                                 const int* __restrict__ slot, const float* __restrict__ An,
+                                                 const float* __restrict__ xi)
+{
+    constexpr int VG = 4;
+    const int i = blockIdx.x;
+    const int k0 = (blockIdx.y * blockDim.x + threadIdx.x) * VG;
+    if (k0 >= Nv) return;
+    const size_t cstride = (size_t)NA * Nvp;
+    const int ns = geo.ns[i];
+    int nb[NS];
+    float cg[NS][D], rr[NS][D];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int n = s < ns ? geo.nbr[i * AVS_MAXS + s] : -1;
+        nb[s] = n >= 0 ? n : i;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            cg[s][d] = s < ns ? geo.cg[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
+            rr[s][d] = s < ns ? geo.r[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
+        }
+    }
+    const float e2 = geo.eps2[i];
+    float2 phi[NA][2], G[NA][D][2];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const float* fa = f + (size_t)a * Nvp + k0;
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(fa + (size_t)i * cstride));
+        phi[a][0] = lo2(c4);
+        phi[a][1] = hi2(c4);
+        float4 n4[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) n4[s] = __ldg(reinterpret_cast<const float4*>(fa + (size_t)nb[s] * cstride));
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            float2 g[D], dd[NS];
+#pragma unroll
+            for (int d = 0; d < D; ++d) g[d] = bc2(0.0f);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                dd[s] = sub2(p ? hi2(n4[s]) : lo2(n4[s]), phi[a][p]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) g[d] = fma2(bc2(cg[s][d]), dd[s], g[d]);
+            }
+            float2 L = bc2(1.0f);
+            if (limiter == 1) {
+                float2 d2[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    d2[s] = mul2(g[0], bc2(rr[s][0]));
+#pragma unroll
+                    for (int d = 1; d < D; ++d) d2[s] = fma2(g[d], bc2(rr[s][d]), d2[s]);
+                }
+                float dx[NS], dy[NS], ex[NS], ey[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    dx[s] = dd[s].x; dy[s] = dd[s].y;
+                    ex[s] = d2[s].x; ey[s] = d2[s].y;
+                }
+                float2 dmax, dmin, pp, nn;
+                ext4<NS>(dx, dmax.x, dmin.x);
+                ext4<NS>(dy, dmax.y, dmin.y);
+                ext4<NS>(ex, pp.x, nn.x);
+                ext4<NS>(ey, pp.y, nn.y);
+                // epsilon^2 = (K dx)^3 phi_C^2: scaled to the limited value (R6)
+                const float2 e2p = mul2(mul2(bc2(e2), phi[a][p]), phi[a][p]);
+                const float2 tp = venkat2(dmax, pp, e2p);
+                const float2 tn = venkat2(dmin, nn, e2p);
+                if (pp.x > 0.0f) L.x = tp.x;
+                if (pp.y > 0.0f) L.y = tp.y;
+                if (nn.x < 0.0f && tn.x < L.x) L.x = tn.x;
+                if (nn.y < 0.0f && tn.y < L.y) L.y = tn.y;
+            }
+            if (limiter == 0) L = bc2(0.0f);     // first order: phi_bar = phi_C
+#pragma unroll
+            for (int d = 0; d < D; ++d) G[a][d][p] = mul2(L, g[d]);
+        }
+    }
+    // node coordinates of the thread's nodes, as lane pairs
+    float2 X[2][D];
+    {
+        float xx[VG * D];
+        ldvn<float, VG * D>(xi + (size_t)k0 * D, xx);
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int d = 0; d < D; ++d) X[p][d] = make_float2(xx[(2 * p) * D + d], xx[(2 * p + 1) * D + d]);
+    }
+    // phi_bar = A + G . r_s with A = phi - h G . xi, the part common to the faces
+    float2 A[NA][2];
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            float2 gx = mul2(G[a][0][p], X[p][0]);
+#pragma unroll
+            for (int d = 1; d < D; ++d) gx = fma2(G[a][d][p], X[p][d], gx);
+            A[a][p] = fma2(bc2(-h), gx, phi[a][p]);
+        }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if (s >= ns) break;
+        const int sl = slot[i * AVS_MAXS + s];
+        const int fc = sl >> 1;
+        const bool isR = sl & 1;
+        float an[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) an[d] = An[(size_t)fc * D + d];
+        bool up[4];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            // xi . An as in k_foot: a product, then fused multiply-adds
+            float2 sn = mul2(X[p][0], bc2(an[0]));
+#pragma unroll
+            for (int d = 1; d < D; ++d) sn = fma2(X[p][d], bc2(an[d]), sn);
+            up[2 * p] = isR ? (sn.x < 0.0f) : (sn.x >= 0.0f);
+            up[2 * p + 1] = isR ? (sn.y < 0.0f) : (sn.y >= 0.0f);
+        }
+        const bool all = up[0] && up[1] && up[2] && up[3];
+        const bool any = up[0] || up[1] || up[2] || up[3];
+        if (!any) continue;
+        float* row = FB + (size_t)fc * NA * Nvp + k0;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            float2 o[2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float2 val = A[a][p];
+#pragma unroll
+                for (int d = 0; d < D; ++d) val = fma2(G[a][d][p], bc2(rr[s][d]), val);
+                o[p] = val;
+            }
+            float* ra = row + (size_t)a * Nvp;
+            if (all) {
+                *reinterpret_cast<float4*>(ra) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+            } else {
+                if (up[0]) ra[0] = o[0].x;
+                if (up[1]) ra[1] = o[0].y;
+                if (up[2]) ra[2] = o[1].x;
+                if (up[3]) ra[3] = o[1].y;
+            }
+        }
+    }
+}
+
 template <typename A>
 __device__ __forceinline__ A tau_vhs(A rho, A RT, A R, A mu_ref, A T_ref, A omega)
 {
@@ -1229,13 +1414,23 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
         geo.ns = c->nslot;
         constexpr int VG = 4;
         const dim3 g(c->Nc, (c->Nv + 256 * VG - 1) / (256 * VG));
-        if (D == 2 && c->max_ns <= 4)
+        if constexpr (sizeof(T) == 4) {
+            if (D == 2 && c->max_ns <= 4)
+                k_foot_f2<D, 4, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (float)hd,
+                                                                      (const float*)fin, (float*)c->flux, geo,
+                                                                      c->slot, An, xi);
+            else
+                k_foot_f2<D, AVS_MAXS, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter,
+                                                                             (float)hd, (const float*)fin,
+                                                                             (float*)c->flux, geo, c->slot, An, xi);
+        } else if (D == 2 && c->max_ns <= 4) {
             k_foot<D, T, VG, 4, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (T)hd,
                                                                       (const T*)fin, (T*)c->flux, geo, c->slot, An, xi);
-        else
+        } else {
             k_foot<D, T, VG, AVS_MAXS, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (T)hd,
                                                                              (const T*)fin, (T*)c->flux, geo, c->slot,
                                                                              An, xi);
+        }
         c->launches += 1;
     }
     FaceP<D, T> P;
