@@ -1193,19 +1193,44 @@ __device__ __forceinline__ void cell_raw_moments(const CellP<D, T>& P, int i, in
 #pragma unroll
     for (int d = 0; d < D; ++d) Vct[d] = (T)P.Win[(size_t)i * NW + 1 + d] / (T)P.Win[(size_t)i * NW];
     const T* fi = P.fin + (size_t)i * P.cstride;
+    if constexpr (sizeof(T) == 4 && V == 4) {
+        // FP32: the four nodes as two lane pairs in packed arithmetic (the
+        // same pairing and order as cell_update's carried sums)
+        float2 acc2[NM];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) acc[m] = T(0);
-    for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
-        T x[V][D], wv[V], f0[V], f1[V];
-        load_nodes<D, V>(P, k0, x, wv);
-        ldv<T, V>(fi + k0, f0);
-        if (NA == 2) ldv<T, V>(fi + P.Nvp + k0, f1);
+        for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
+        for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
+            float x[V][D], wv[V], f0[V], f1[V];
+            load_nodes<D, V>(P, k0, x, wv);
+            ldv<T, V>(fi + k0, f0);
+            if (NA == 2) ldv<T, V>(fi + P.Nvp + k0, f1);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            T xs[D];
+            for (int p = 0; p < 2; ++p) {
+                float2 xs[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Vct[d];
-            raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
+                for (int d = 0; d < D; ++d) xs[d] = add2(make_float2(x[2 * p][d], x[2 * p + 1][d]), bc2(-Vct[d]));
+                const float2 W2 = make_float2(wv[2 * p], wv[2 * p + 1]);
+                raw_acc2<D>(acc2, xs, mul2(W2, make_float2(f0[2 * p], f0[2 * p + 1])),
+                            NA == 2 ? mul2(W2, make_float2(f1[2 * p], f1[2 * p + 1])) : bc2(0.0f));
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[m] = acc2[m].x + acc2[m].y;
+    } else {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[m] = T(0);
+        for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
+            T x[V][D], wv[V], f0[V], f1[V];
+            load_nodes<D, V>(P, k0, x, wv);
+            ldv<T, V>(fi + k0, f0);
+            if (NA == 2) ldv<T, V>(fi + P.Nvp + k0, f1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                T xs[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Vct[d];
+                raw_acc<D>(acc, xs, wv[v] * f0[v], NA == 2 ? wv[v] * f1[v] : T(0));
+            }
         }
     }
 }
@@ -1289,45 +1314,112 @@ __device__ __forceinline__ void cell_update(const CellP<D, T>& P, int i, int ns,
     T Vnt[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) Vnt[d] = cp.Vn[d];
+    if constexpr (sizeof(T) == 4 && V == 4) {
+        // FP32: the four nodes as two lane pairs in packed arithmetic
+        float2 acc2[NM];
 #pragma unroll
-    for (int m = 0; m < NM; ++m) acc[m] = T(0);
-    for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
-        T x[V][D], wv[V];
-        load_nodes<D, V>(P, k0, x, wv);
-        T Nn[NA][V], fv[NA][V], out[NA][V];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            ldv_cg<T, V>(fi + (size_t)a * P.Nvp + k0, fv[a]);
-#pragma unroll
-            for (int v = 0; v < V; ++v) Nn[a][v] = T(0);
-        }
-#pragma unroll
-        for (int s = 0; s < AVS_MAXS; ++s) {
-            if (s >= ns) break;
-            const T* Fs = P.F + (size_t)fs[s] * NA * P.Nvp + k0;
-            const T g = sg[s];
+        for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
+        const float2 U0 = bc2(u0), U1 = bc2(u1), U2n = bc2(-u2), U3 = bc2(u3);
+        const EqPar<float> eq = cp.eq;
+        for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
+            float x[V][D], wv[V];
+            load_nodes<D, V>(P, k0, x, wv);
+            float fv[NA][V];
+            float2 Nn[NA][2];
 #pragma unroll
             for (int a = 0; a < NA; ++a) {
-                T t[V];
-                ldv_cg<T, V>(Fs + (size_t)a * P.Nvp, t);
-#pragma unroll
-                for (int v = 0; v < V; ++v) Nn[a][v] += g * t[v];
+                ldv_cg<T, V>(fi + (size_t)a * P.Nvp + k0, fv[a]);
+                Nn[a][0] = Nn[a][1] = bc2(0.0f);
             }
+#pragma unroll
+            for (int s = 0; s < AVS_MAXS; ++s) {
+                if (s >= ns) break;
+                const float* Fs = P.F + (size_t)fs[s] * NA * P.Nvp + k0;
+                const float2 g = bc2(sg[s]);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    float t[V];
+                    ldv_cg<T, V>(Fs + (size_t)a * P.Nvp, t);
+                    Nn[a][0] = fma2(g, make_float2(t[0], t[1]), Nn[a][0]);
+                    Nn[a][1] = fma2(g, make_float2(t[2], t[3]), Nn[a][1]);
+                }
+            }
+            float out[NA][V];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float2 X[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) X[d] = make_float2(x[2 * p][d], x[2 * p + 1][d]);
+                float2 gG, gH;
+                eq_eval2<D>(eq, X, gG, gH);
+                const bool r0 = k0 + 2 * p < P.Nv, r1 = k0 + 2 * p + 1 < P.Nv;
+                float2 o[NA];
+                o[0] = mul2(fma2(Nn[0][p], U2n, fma2(make_float2(fv[0][2 * p], fv[0][2 * p + 1]), U0, mul2(gG, U1))),
+                            U3);
+                if (NA == 2)
+                    o[NA - 1] = mul2(fma2(Nn[NA - 1][p], U2n,
+                                          fma2(make_float2(fv[NA - 1][2 * p], fv[NA - 1][2 * p + 1]), U0,
+                                               mul2(gH, U1))),
+                                     U3);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    out[a][2 * p] = r0 ? o[a].x : 0.0f;
+                    out[a][2 * p + 1] = r1 ? o[a].y : 0.0f;
+                }
+                float2 xs[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-Vnt[d]));
+                const float2 W2 = make_float2(wv[2 * p], wv[2 * p + 1]);
+                raw_acc2<D>(acc2, xs, mul2(W2, make_float2(out[0][2 * p], out[0][2 * p + 1])),
+                            NA == 2 ? mul2(W2, make_float2(out[NA - 1][2 * p], out[NA - 1][2 * p + 1])) : bc2(0.0f));
+            }
+#pragma unroll
+            for (int a = 0; a < NA; ++a) stv<T, V>(fo + (size_t)a * P.Nvp + k0, out[a]);
         }
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            T gG, gH;
-            eq_eval<D>(cp.eq, x[v], gG, gH);
-            const bool real = k0 + v < P.Nv;
-            out[0][v] = real ? (fv[0][v] * u0 + gG * u1 - Nn[0][v] * u2) * u3 : T(0);
-            if (NA == 2) out[NA - 1][v] = real ? (fv[NA - 1][v] * u0 + gH * u1 - Nn[NA - 1][v] * u2) * u3 : T(0);
-            T xs[D];
+        for (int m = 0; m < NM; ++m) acc[m] = acc2[m].x + acc2[m].y;
+    } else {
 #pragma unroll
-            for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Vnt[d];
-            raw_acc<D>(acc, xs, wv[v] * out[0][v], NA == 2 ? wv[v] * out[NA - 1][v] : T(0));
+        for (int m = 0; m < NM; ++m) acc[m] = T(0);
+        for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
+            T x[V][D], wv[V];
+            load_nodes<D, V>(P, k0, x, wv);
+            T Nn[NA][V], fv[NA][V], out[NA][V];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                ldv_cg<T, V>(fi + (size_t)a * P.Nvp + k0, fv[a]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) Nn[a][v] = T(0);
+            }
+#pragma unroll
+            for (int s = 0; s < AVS_MAXS; ++s) {
+                if (s >= ns) break;
+                const T* Fs = P.F + (size_t)fs[s] * NA * P.Nvp + k0;
+                const T g = sg[s];
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    T t[V];
+                    ldv_cg<T, V>(Fs + (size_t)a * P.Nvp, t);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) Nn[a][v] += g * t[v];
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                T gG, gH;
+                eq_eval<D>(cp.eq, x[v], gG, gH);
+                const bool real = k0 + v < P.Nv;
+                out[0][v] = real ? (fv[0][v] * u0 + gG * u1 - Nn[0][v] * u2) * u3 : T(0);
+                if (NA == 2)
+                    out[NA - 1][v] = real ? (fv[NA - 1][v] * u0 + gH * u1 - Nn[NA - 1][v] * u2) * u3 : T(0);
+                T xs[D];
+#pragma unroll
+                for (int d = 0; d < D; ++d) xs[d] = x[v][d] - Vnt[d];
+                raw_acc<D>(acc, xs, wv[v] * out[0][v], NA == 2 ? wv[v] * out[NA - 1][v] : T(0));
+            }
+#pragma unroll
+            for (int a = 0; a < NA; ++a) stv<T, V>(fo + (size_t)a * P.Nvp + k0, out[a]);
         }
-#pragma unroll
-        for (int a = 0; a < NA; ++a) stv<T, V>(fo + (size_t)a * P.Nvp + k0, out[a]);
     }
 }
 
