@@ -401,22 +401,37 @@ __global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter
 {
     constexpr int VG = 4;
     const int i = blockIdx.x;
-    const int k0 = (blockIdx.y * blockDim.x + threadIdx.x) * VG;
+    const int t = threadIdx.x;
+    const int k0 = (blockIdx.y * blockDim.x + t) * VG;
+    const int ns = geo.ns[i];
+    // the cell's geometry, once per block: least-squares weights, face
+    // offsets and face normals per slot (padded to four floats, read back as
+    // one 16-byte vector), neighbour cells and slot codes
+    __shared__ __align__(16) float gs[3][NS][4];
+    __shared__ int gn[2][NS];
+    if (t < NS * 4) {
+        const int s = t >> 2, d = t & 3;
+        const bool on = s < ns && d < D;
+        gs[0][s][d] = on ? geo.cg[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
+        gs[1][s][d] = on ? geo.r[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
+    } else if (t >= 32 && t < 32 + NS) {
+        const int s = t - 32;
+        const int n = s < ns ? geo.nbr[i * AVS_MAXS + s] : -1;
+        const int sl = s < ns ? slot[i * AVS_MAXS + s] : 0;
+        gn[0][s] = n >= 0 ? n : i;
+        gn[1][s] = sl;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) gs[2][s][d] = (s < ns && d < D) ? An[(size_t)(sl >> 1) * D + d] : 0.0f;
+    }
+    __syncthreads();
     if (k0 >= Nv) return;
     const size_t cstride = (size_t)NA * Nvp;
-    const int ns = geo.ns[i];
-    int nb[NS];
-    float cg[NS][D], rr[NS][D];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        const int n = s < ns ? geo.nbr[i * AVS_MAXS + s] : -1;
-        nb[s] = n >= 0 ? n : i;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            cg[s][d] = s < ns ? geo.cg[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
-            rr[s][d] = s < ns ? geo.r[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
-        }
-    }
+    auto vec = [&](int q, int s, float (&o)[D]) {
+        const float4 v = *reinterpret_cast<const float4*>(gs[q][s]);
+        o[0] = v.x;
+        o[1] = v.y;
+        if constexpr (D == 3) o[2] = v.z;
+    };
     const float e2 = geo.eps2[i];
     float2 phi[NA][2], G[NA][D][2];
 #pragma unroll
@@ -427,7 +442,7 @@ __global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter
         phi[a][1] = hi2(c4);
         float4 n4[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) n4[s] = __ldg(reinterpret_cast<const float4*>(fa + (size_t)nb[s] * cstride));
+        for (int s = 0; s < NS; ++s) n4[s] = __ldg(reinterpret_cast<const float4*>(fa + (size_t)gn[0][s] * cstride));
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             float2 g[D], dd[NS];
@@ -435,18 +450,22 @@ __global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter
             for (int d = 0; d < D; ++d) g[d] = bc2(0.0f);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
+                float cg[D];
+                vec(0, s, cg);
                 dd[s] = sub2(p ? hi2(n4[s]) : lo2(n4[s]), phi[a][p]);
 #pragma unroll
-                for (int d = 0; d < D; ++d) g[d] = fma2(bc2(cg[s][d]), dd[s], g[d]);
+                for (int d = 0; d < D; ++d) g[d] = fma2(bc2(cg[d]), dd[s], g[d]);
             }
             float2 L = bc2(1.0f);
             if (limiter == 1) {
                 float2 d2[NS];
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    d2[s] = mul2(g[0], bc2(rr[s][0]));
+                    float rr[D];
+                    vec(1, s, rr);
+                    d2[s] = mul2(g[0], bc2(rr[0]));
 #pragma unroll
-                    for (int d = 1; d < D; ++d) d2[s] = fma2(g[d], bc2(rr[s][d]), d2[s]);
+                    for (int d = 1; d < D; ++d) d2[s] = fma2(g[d], bc2(rr[d]), d2[s]);
                 }
                 float dx[NS], dy[NS], ex[NS], ey[NS];
 #pragma unroll
@@ -497,12 +516,12 @@ __global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         if (s >= ns) break;
-        const int sl = slot[i * AVS_MAXS + s];
+        const int sl = gn[1][s];
         const int fc = sl >> 1;
         const bool isR = sl & 1;
-        float an[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) an[d] = An[(size_t)fc * D + d];
+        float an[D], rr[D];
+        vec(2, s, an);
+        vec(1, s, rr);
         bool up[4];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
@@ -524,7 +543,7 @@ __global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter
             for (int p = 0; p < 2; ++p) {
                 float2 val = A[a][p];
 #pragma unroll
-                for (int d = 0; d < D; ++d) val = fma2(G[a][d][p], bc2(rr[s][d]), val);
+                for (int d = 0; d < D; ++d) val = fma2(G[a][d][p], bc2(rr[d]), val);
                 o[p] = val;
             }
             float* ra = row + (size_t)a * Nvp;
