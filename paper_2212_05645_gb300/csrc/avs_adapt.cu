@@ -38,14 +38,17 @@ __device__ int zone_cap(const ZoneSet& Z, int D, const double* x)
 __global__ void k_geom(int D, int Nv, int Nvp, const int* __restrict__ level, const int* __restrict__ base,
                        const uint32_t* __restrict__ key, int nb0, int nb1, int nb2, double vlo0, double vlo1,
                        double vlo2, double hb0, double hb1, double hb2, double* xi_d, double* w_d, float* xi_f,
-                       float* w_f, ZoneSet Z, int* ncap)
+                       float* w_f, float* xi_p, ZoneSet Z, int* ncap)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Nvp) return;
+    // pair layout: the d-th components of nodes 2j and 2j+1 side by side
+    float* xp = xi_p + ((size_t)(k >> 1) * D) * 2 + (k & 1);
     if (k >= Nv) {
         for (int d = 0; d < D; ++d) {
             xi_d[(size_t)k * D + d] = 0.0;
             xi_f[(size_t)k * D + d] = 0.0f;
+            xp[2 * d] = 0.0f;
         }
         w_d[k] = 0.0;
         w_f[k] = 0.0f;
@@ -73,6 +76,7 @@ __global__ void k_geom(int D, int Nv, int Nvp, const int* __restrict__ level, co
         xc[d] = x;
         xi_d[(size_t)k * D + d] = x;
         xi_f[(size_t)k * D + d] = (float)x;
+        xp[2 * d] = (float)x;
         wk = __dmul_rn(wk, hb[d]);
     }
     const double wv = ldexp(wk, -D * l);
@@ -87,7 +91,7 @@ cudaError_t launch_geom(avs_ctx* c)
     k_geom<<<(n + 255) / 256, 256, 0, c->stream>>>(c->D, c->Nv, c->Nvp, c->level, c->base, c->key, c->cfg.base[0],
                                                    c->cfg.base[1], c->cfg.base[2], c->cfg.vlo[0], c->cfg.vlo[1],
                                                    c->cfg.vlo[2], c->hb[0], c->hb[1], c->hb[2], c->xi_d, c->w_d,
-                                                   c->xi_f, c->w_f, c->zs, c->ncap);
+                                                   c->xi_f, c->w_f, c->xi_p, c->zs, c->ncap);
     c->launches += 1;
     return cudaGetLastError();
 }

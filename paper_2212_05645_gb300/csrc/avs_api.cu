@@ -53,7 +53,7 @@ void free_all(avs_ctx* c)
     void* ptrs[] = {c->faceL, c->faceR, c->An_d, c->rL_d, c->rR_d, c->An_f, c->rL_f, c->rR_f, c->vol, c->bc,
                     c->slot, c->nslot, c->nbr, c->cg_d, c->r_d, c->eps2_d, c->cg_f, c->r_f, c->eps2_f,
                     c->level, c->base, c->key, c->level2, c->base2, c->key2, c->src, c->kind, c->emit,
-                    c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->M, c->Mkey, c->f[0], c->f[1],
+                    c->newidx, c->d_count, c->xi_d, c->w_d, c->xi_f, c->w_f, c->xi_p, c->M, c->Mkey, c->f[0], c->f[1],
                     c->W[0], c->W[1], c->ncap, c->Wf, c->q, c->pseudo_f, c->pseudo_W, c->crit_cp, c->crit_cp32, c->Mlo, c->Mhi, c->Mthr, c->stage, c->dev_err,
                     c->dt_key, c->gap_d, c->grad, c->flux, c->AFf, c->forder, c->cmom, c->rmom, c->cpar, c->clist, c->cstart_d, c->imp_dW, c->imp_rhs0, c->imp_diag, c->imp_Wta,
                     c->imp_co, c->imp_nint, c->imp_bar, c->mlp_P, c->mlp_Wb, c->mlp_part, c->mlp_grad,
@@ -563,7 +563,7 @@ avs_status avs_create(const avs_config* cfg, const avs_mesh* mesh, void* cuda_st
     AL(c->src, capp); AL(c->kind, capp); AL(c->emit, capp);
     AL(c->newidx, 2 * (size_t)capp); AL(c->d_count, 4);
     AL(c->xi_d, (size_t)capp * c->D); AL(c->w_d, capp);
-    AL(c->xi_f, (size_t)capp * c->D); AL(c->w_f, capp);
+    AL(c->xi_f, (size_t)capp * c->D); AL(c->w_f, capp); AL(c->xi_p, (size_t)capp * c->D);
     AL(c->M, capp); AL(c->Mkey, capp); AL(c->ncap, capp);
     AL(c->pseudo_f, 2 * (size_t)c->NA * capp); AL(c->pseudo_W, 4 * NW);
     AL(c->crit_cp, 5 * (size_t)std::max(c->Nc, 2)); AL(c->crit_cp32, 8 * (size_t)std::max(c->Nc, 2));

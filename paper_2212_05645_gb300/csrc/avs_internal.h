@@ -64,6 +64,7 @@ struct avs_ctx {
     double *xi_d = nullptr, *w_d = nullptr;          // [cap][D], [cap]
     int *ncap = nullptr;                             // [cap] largest level a node may split to (zones)
     float *xi_f = nullptr, *w_f = nullptr;
+    float *xi_p = nullptr;                           // FP32 node coordinates by pairs: [cap/2][D][2]
     double *M = nullptr;                             // [cap]
     unsigned long long *Mkey = nullptr;              // [cap]
 

@@ -397,7 +397,7 @@ template <int D, int NS, int NA>
 __global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter, float h, const float* __restrict__ f,
                                                  float* __restrict__ FB, CellGeo<float> geo,
                                                  const int* __restrict__ slot, const float* __restrict__ An,
-                                                 const float* __restrict__ xi)
+                                                 const float* __restrict__ xp)
 {
     constexpr int VG = 4;
     const int i = blockIdx.x;
@@ -492,15 +492,15 @@ __global__ void __launch_bounds__(256, 4) k_foot_f2(int Nv, int Nvp, int limiter
             for (int d = 0; d < D; ++d) G[a][d][p] = mul2(L, g[d]);
         }
     }
-    // node coordinates of the thread's nodes, as lane pairs
+    // node coordinates of the thread's nodes, as lane pairs (xp: the pair layout)
     float2 X[2][D];
     {
         float xx[VG * D];
-        ldvn<float, VG * D>(xi + (size_t)k0 * D, xx);
+        ldvn<float, VG * D>(xp + (size_t)k0 * D, xx);
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int d = 0; d < D; ++d) X[p][d] = make_float2(xx[(2 * p) * D + d], xx[(2 * p + 1) * D + d]);
+            for (int d = 0; d < D; ++d) X[p][d] = make_float2(xx[(p * D + d) * 2], xx[(p * D + d) * 2 + 1]);
     }
     // phi_bar = A + G . r_s with A = phi - h G . xi, the part common to the faces
     float2 A[NA][2];
@@ -589,6 +589,40 @@ __device__ __forceinline__ void load_nodes(const PP& P, int k0, T (*x)[D], T* w)
     ldv<T, V>(P.w + k0, w);
 }
 
+// FP32 node pair (k, k+1), k even, from the pair layout: X[d] the pair's
+// d-th components (one 8- or 16-byte load each), W2 their weights.
+template <int D, typename PP>
+__device__ __forceinline__ void load_pair(const PP& P, int k, float2 (&X)[D], float2& W2)
+{
+    const float* p = P.xp + (size_t)k * D;
+    if constexpr (D == 2) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        X[0] = make_float2(v.x, v.y);
+        X[1] = make_float2(v.z, v.w);
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) X[d] = *reinterpret_cast<const float2*>(p + 2 * d);
+    }
+    W2 = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(P.w) + k);
+}
+
+// Four FP32 nodes k..k+3, k a multiple of 4, as two pairs from the pair
+// layout (16-byte loads): X[p][d], W2[p] for the pair (k + 2p, k + 2p + 1).
+template <int D>
+__device__ __forceinline__ void load_quad(const float* xp, const float* w, int k, float2 (&X)[2][D],
+                                          float2 (&W2)[2])
+{
+    float xx[4 * D];
+    ldvn<float, 4 * D>(xp + (size_t)k * D, xx);
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int d = 0; d < D; ++d) X[p][d] = make_float2(xx[(p * D + d) * 2], xx[(p * D + d) * 2 + 1]);
+    const float4 wv = *reinterpret_cast<const float4*>(w + k);
+    W2[0] = make_float2(wv.x, wv.y);
+    W2[1] = make_float2(wv.z, wv.w);
+}
+
 // ------------------------------------------------------------------ k_face
 template <int D, typename T>
 struct FaceP {
@@ -603,6 +637,7 @@ struct FaceP {
     const double* __restrict__ Win;
     const T* __restrict__ xi;
     const T* __restrict__ w;
+    const float* __restrict__ xp;            // FP32 node coordinates by pairs [Nvp/2][D][2]
     const int* __restrict__ order;
     const int* __restrict__ faceL;
     const int* __restrict__ faceR;
@@ -703,8 +738,8 @@ __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T
         for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
 #pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
-            T x[V][D], wv[V];
-            load_nodes<D, V>(P, k0, x, wv);      // pad nodes carry w = 0 and contribute nothing
+            float2 X[D], W2;
+            load_pair<D>(P, k0, X, W2);          // pad nodes carry w = 0 and contribute nothing
             float2 F[NA];
 #pragma unroll
             for (int a = 0; a < NA; ++a) F[a] = __ldcg(reinterpret_cast<const float2*>((const float*)fb + a * Nvp + k0));
@@ -714,8 +749,7 @@ __device__ __forceinline__ void face_pass_a(const FaceP<D, T>& P, const FaceSt<T
             }
             float2 xs[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) xs[d] = add2(make_float2(x[0][d], x[1][d]), bc2(-(float)Vt[d]));
-            const float2 W2 = make_float2(wv[0], wv[1]);
+            for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-(float)Vt[d]));
             raw_acc2<D>(acc2, xs, mul2(W2, F[0]), NA == 2 ? mul2(W2, F[NA - 1]) : bc2(0.0f));
         }
 #pragma unroll
@@ -833,11 +867,8 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
         for (int m = 0; m < NW; ++m) acc2[m] = bc2(0.0f);
 #pragma unroll 2
         for (int k0 = kb + tid * V; k0 < ke; k0 += NT * V) {
-            T x[V][D], wv[V];
-            load_nodes<D, V>(P, k0, x, wv);
-            float2 X[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
+            float2 X[D], W2;
+            load_pair<D>(P, k0, X, W2);
             float2 sn = mul2(X[0], bc2(An[0]));
 #pragma unroll
             for (int d = 1; d < D; ++d) sn = add2(sn, mul2(X[d], bc2(An[d])));
@@ -850,7 +881,7 @@ __device__ __forceinline__ void face_pass_b(const FaceP<D, T>& P, const FaceSt<T
             eq_eval2<D>(eq, X, gG, gH);
             const float2 pG = fma2(wb, gG, mul2(wa, F[0]));
             const float2 pH = NA == 2 ? fma2(wb, gH, mul2(wa, F[NA - 1])) : bc2(0.0f);
-            const float2 t = mul2(make_float2(wv[0], wv[1]), sn);
+            const float2 t = mul2(W2, sn);
             float2 x2 = mul2(X[0], X[0]);
 #pragma unroll
             for (int d = 1; d < D; ++d) x2 = fma2(X[d], X[d], x2);
@@ -1023,7 +1054,7 @@ __global__ void __launch_bounds__(NT, 7) k_face_staged(FaceP<D, float> P)
 #pragma unroll
         for (int a = 0; a < NA; ++a) bulk_g2s(dst + a * CH, row + (size_t)a * Nvp + k0, bytes, &full[b]);
         if constexpr (SXI) {
-            bulk_g2s(dst + NA * CH, P.xi + (size_t)k0 * D, bytes * D, &full[b]);
+            bulk_g2s(dst + NA * CH, P.xp + (size_t)k0 * D, bytes * D, &full[b]);
             bulk_g2s(dst + (NA + D) * CH, P.w + k0, bytes, &full[b]);
         }
     };
@@ -1031,23 +1062,12 @@ __global__ void __launch_bounds__(NT, 7) k_face_staged(FaceP<D, float> P)
     // direct loads (the coordinates and weights are shared by all faces)
     auto stage_nodes = [&](const float* st, int k, int kk, float2 (&X)[D], float2& W2) {
         if constexpr (SXI) {
-            const float* xv = st + NA * CH + kk * D;
-            float xx[2 * D];
+            const float* xv = st + NA * CH + kk * D;      // pair layout, as in P.xp
 #pragma unroll
-            for (int j = 0; j < D; ++j) {
-                const float2 t = *reinterpret_cast<const float2*>(xv + 2 * j);
-                xx[2 * j] = t.x;
-                xx[2 * j + 1] = t.y;
-            }
-#pragma unroll
-            for (int d = 0; d < D; ++d) X[d] = make_float2(xx[d], xx[D + d]);
+            for (int d = 0; d < D; ++d) X[d] = *reinterpret_cast<const float2*>(xv + 2 * d);
             W2 = *reinterpret_cast<const float2*>(st + (NA + D) * CH + kk);
         } else {
-            float x[2][D], wv[2];
-            load_nodes<D, 2>(P, k, x, wv);
-#pragma unroll
-            for (int d = 0; d < D; ++d) X[d] = make_float2(x[0][d], x[1][d]);
-            W2 = make_float2(wv[0], wv[1]);
+            load_pair<D>(P, k, X, W2);
         }
     };
     auto wait = [&](int g) {
@@ -1195,6 +1215,7 @@ struct CellP {
     CellPar<T>* par;         // [cell]
     const T* __restrict__ xi;
     const T* __restrict__ w;
+    const float* __restrict__ xp;            // FP32 node coordinates by pairs [Nvp/2][D][2]
     const int* __restrict__ slot;
     const unsigned char* __restrict__ nslot;
     const double* __restrict__ vol;
@@ -1219,18 +1240,18 @@ __device__ __forceinline__ void cell_raw_moments(const CellP<D, T>& P, int i, in
 #pragma unroll
         for (int m = 0; m < NM; ++m) acc2[m] = bc2(0.0f);
         for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
-            float x[V][D], wv[V], f0[V], f1[V];
-            load_nodes<D, V>(P, k0, x, wv);
+            float2 X[2][D], W2[2];
+            float f0[V], f1[V];
+            load_quad<D>(P.xp, P.w, k0, X, W2);
             ldv<T, V>(fi + k0, f0);
             if (NA == 2) ldv<T, V>(fi + P.Nvp + k0, f1);
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 float2 xs[D];
 #pragma unroll
-                for (int d = 0; d < D; ++d) xs[d] = add2(make_float2(x[2 * p][d], x[2 * p + 1][d]), bc2(-Vct[d]));
-                const float2 W2 = make_float2(wv[2 * p], wv[2 * p + 1]);
-                raw_acc2<D>(acc2, xs, mul2(W2, make_float2(f0[2 * p], f0[2 * p + 1])),
-                            NA == 2 ? mul2(W2, make_float2(f1[2 * p], f1[2 * p + 1])) : bc2(0.0f));
+                for (int d = 0; d < D; ++d) xs[d] = add2(X[p][d], bc2(-Vct[d]));
+                raw_acc2<D>(acc2, xs, mul2(W2[p], make_float2(f0[2 * p], f0[2 * p + 1])),
+                            NA == 2 ? mul2(W2[p], make_float2(f1[2 * p], f1[2 * p + 1])) : bc2(0.0f));
             }
         }
 #pragma unroll
@@ -1341,8 +1362,8 @@ __device__ __forceinline__ void cell_update(const CellP<D, T>& P, int i, int ns,
         const float2 U0 = bc2(u0), U1 = bc2(u1), U2n = bc2(-u2), U3 = bc2(u3);
         const EqPar<float> eq = cp.eq;
         for (int k0 = kb + threadIdx.x * V; k0 < ke; k0 += NT * V) {
-            float x[V][D], wv[V];
-            load_nodes<D, V>(P, k0, x, wv);
+            float2 XX[2][D], W2[2];
+            load_quad<D>(P.xp, P.w, k0, XX, W2);
             float fv[NA][V];
             float2 Nn[NA][2];
 #pragma unroll
@@ -1366,9 +1387,7 @@ __device__ __forceinline__ void cell_update(const CellP<D, T>& P, int i, int ns,
             float out[NA][V];
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
-                float2 X[D];
-#pragma unroll
-                for (int d = 0; d < D; ++d) X[d] = make_float2(x[2 * p][d], x[2 * p + 1][d]);
+                const float2* X = XX[p];
                 float2 gG, gH;
                 eq_eval2<D>(eq, X, gG, gH);
                 const bool r0 = k0 + 2 * p < P.Nv, r1 = k0 + 2 * p + 1 < P.Nv;
@@ -1388,9 +1407,9 @@ __device__ __forceinline__ void cell_update(const CellP<D, T>& P, int i, int ns,
                 float2 xs[D];
 #pragma unroll
                 for (int d = 0; d < D; ++d) xs[d] = add2(X[d], bc2(-Vnt[d]));
-                const float2 W2 = make_float2(wv[2 * p], wv[2 * p + 1]);
-                raw_acc2<D>(acc2, xs, mul2(W2, make_float2(out[0][2 * p], out[0][2 * p + 1])),
-                            NA == 2 ? mul2(W2, make_float2(out[NA - 1][2 * p], out[NA - 1][2 * p + 1])) : bc2(0.0f));
+                raw_acc2<D>(acc2, xs, mul2(W2[p], make_float2(out[0][2 * p], out[0][2 * p + 1])),
+                            NA == 2 ? mul2(W2[p], make_float2(out[NA - 1][2 * p], out[NA - 1][2 * p + 1]))
+                                    : bc2(0.0f));
             }
 #pragma unroll
             for (int a = 0; a < NA; ++a) stv<T, V>(fo + (size_t)a * P.Nvp + k0, out[a]);
@@ -1529,11 +1548,12 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
             if (D == 2 && c->max_ns <= 4)
                 k_foot_f2<D, 4, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (float)hd,
                                                                       (const float*)fin, (float*)c->flux, geo,
-                                                                      c->slot, An, xi);
+                                                                      c->slot, An, c->xi_p);
             else
                 k_foot_f2<D, AVS_MAXS, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter,
                                                                              (float)hd, (const float*)fin,
-                                                                             (float*)c->flux, geo, c->slot, An, xi);
+                                                                             (float*)c->flux, geo, c->slot, An,
+                                                                             c->xi_p);
         } else if (D == 2 && c->max_ns <= 4) {
             k_foot<D, T, VG, 4, NArr<D>::v><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (T)hd,
                                                                       (const T*)fin, (T*)c->flux, geo, c->slot, An, xi);
@@ -1560,6 +1580,7 @@ static cudaError_t face_stage_t(avs_ctx* c, const void* fin, const double* Win, 
     P.Win = Win;
     P.xi = xi;
     P.w = w;
+    P.xp = c->xi_p;
     P.order = c->forder;
     P.faceL = c->faceL;
     P.faceR = c->faceR;
@@ -1653,6 +1674,7 @@ static cudaError_t launch_step_t(avs_ctx* c, const void* fin, void* fout, const 
     Q.par = (CellPar<T>*)c->cpar;
     Q.xi = xi;
     Q.w = w;
+    Q.xp = c->xi_p;
     Q.slot = c->slot;
     Q.nslot = c->nslot;
     Q.vol = c->vol;
@@ -2170,6 +2192,7 @@ static cudaError_t launch_step_implicit_t(avs_ctx* c, const void* fin, void* fou
     Q.par = (CellPar<T>*)c->cpar;
     Q.xi = xi;
     Q.w = w;
+    Q.xp = c->xi_p;
     Q.slot = c->slot;
     Q.nslot = c->nslot;
     Q.vol = c->vol;
