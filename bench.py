@@ -563,8 +563,8 @@ def run_sweep(args):
         for precision in ("mixed", "fp64"):
             es = 4 if precision == "mixed" else 8
             NA = 2 if D == 2 else 1
-            # f twice, L grad f, face flux (D faces per cell)
-            state = Nc * Nv * NA * es * (2 + D + D)
+            # f twice and the face rows of foot values / fluxes (D faces per cell)
+            state = Nc * Nv * NA * es * (2 + D)
             if state > SWEEP_MAX_BYTES:
                 continue
             w = dataclasses.replace(meshes[n], base=(b,) * D, precision=precision)
