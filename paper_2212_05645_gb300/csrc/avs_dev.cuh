@@ -135,6 +135,18 @@ __device__ __forceinline__ T venkat(T d1, T d2, T eps2)
     return v < T(1) ? v : T(1);
 }
 
+// log2(e), and log2 in the argument's type
+constexpr double kLog2e = 1.4426950408889634;
+__device__ __forceinline__ double log2a(double x) { return log2(x); }
+__device__ __forceinline__ float log2a(float x) { return log2f(x); }
+// 2^x by the PTX ex2 instruction (approximate, subnormal results flushed to zero)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---------------------------------------------------------------- equilibria
 // Parameters of one equilibrium evaluated on the nodes:
 //   G = pref exp(-|c|^2 inv2RT) (1 + (c . alpha)(|c|^2 invRT - D - 2)),
@@ -144,6 +156,7 @@ __device__ __forceinline__ T venkat(T d1, T d2, T eps2)
 template <typename T>
 struct EqPar {
     T pref, U[3], inv2RT, invRT, RTH, alpha[3];
+    T l2pref, k2;            // log2(pref) and -log2(e) / (2 R T): the FP32 pair form's base-2 exponent
 };
 
 template <int D, typename T>
@@ -180,6 +193,8 @@ __device__ __forceinline__ EqPar<T> make_eq(double rho, const double* U, double 
     p.inv2RT = (T)(1.0 / (2.0 * RT));
     p.invRT = (T)(1.0 / RT);
     p.RTH = (T)((3.0 - D) * RT);
+    p.l2pref = (T)log2(pref);
+    p.k2 = (T)(-kLog2e / (2.0 * RT));
     return p;
 }
 
@@ -357,6 +372,8 @@ __device__ __forceinline__ EqPar<T> make_eq_a(A rho, const A* U, A RT, const A* 
     p.inv2RT = (T)fdiv(A(1), A(2) * RT);
     p.invRT = (T)fdiv(A(1), RT);
     p.RTH = (T)(A(3 - D) * RT);
+    p.l2pref = (T)log2a(fdiv(rho, D == 2 ? t : t * sqrt(t)));
+    p.k2 = (T)(-A(kLog2e) * fdiv(A(1), A(2) * RT));
     return p;
 }
 
@@ -546,8 +563,10 @@ __device__ __forceinline__ void eq_eval2(const EqPar<float>& p, const float2* X,
         c2 = fma2(c[d], c[d], c2);
         cq = fma2(c[d], bc2(p.alpha[d]), cq);
     }
-    const float2 a = mul2(c2, bc2(-p.inv2RT));
-    const float2 e = mul2(bc2(p.pref), make_float2(__expf(a.x), __expf(a.y)));
+    // pref exp(-c^2 / 2RT) as 2^(log2 pref - c^2 log2(e) / 2RT): one fused
+    // multiply-add for the exponent of both lanes
+    const float2 a = fma2(c2, bc2(p.k2), bc2(p.l2pref));
+    const float2 e = make_float2(ex2_approx(a.x), ex2_approx(a.y));
     const float2 s = mul2(c2, bc2(p.invRT));
     gG = mul2(e, fma2(cq, add2(s, bc2(-(float)(D + 2))), bc2(1.0f)));
     gH = (D == 2) ? mul2(mul2(bc2(p.RTH), e), fma2(cq, add2(s, bc2(-(float)D)), bc2(1.0f))) : bc2(0.0f);
