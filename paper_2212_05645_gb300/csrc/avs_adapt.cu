@@ -105,7 +105,8 @@ cudaError_t launch_geom(avs_ctx* c)
 // The largest FP64 sum is found without evaluating every node in FP64: an
 // FP32 pass gives each node's sum S32 and a bound B on |S32 - S| (inputs and
 // every operation rounded to FP32: |S32 - S| <= 11 u sum_j sum_d |xi_d A_jd|,
-// u = 2^-24, while the results stay normal; B takes 32 u plus 2^-100).  Only nodes with S32 + B >= max_k (S32 - B), which
+// u = 2^-24, while the results stay normal; B takes 32 u of that sum, formed as
+// sum_d |xi_d| sum_j |A_jd|, plus 2^-100).  Only nodes with S32 + B >= max_k (S32 - B), which
 // include the node of the exact maximum, are evaluated in FP64.
 template <int NS>
 __global__ void __launch_bounds__(128) k_dt_unit(int D, int Nv, const double* __restrict__ xi,
@@ -132,18 +133,24 @@ __global__ void __launch_bounds__(128) k_dt_unit(int D, int Nv, const double* __
             A[s][d] = isR[s] ? -a : a;
         }
     }
+    // sum_j sum_d |xi_d A_jd| = sum_d |xi_d| sum_j |A_jd|: the face sums once per cell
+    float As[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        As[d] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) As[d] += fabsf(A[s][d]);
+    }
     auto s32 = [&](int k, float& S, float& B) {
         float x[3] = {0.0f, 0.0f, 0.0f};
         for (int d = 0; d < D; ++d) x[d] = xi_f[(size_t)k * D + d];
         S = 0.0f;
-        B = 0.0f;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const float sn = x[0] * A[s][0] + x[1] * A[s][1] + x[2] * A[s][2];
             S += sn > 0.0f ? sn : 0.0f;
-            B += fabsf(x[0] * A[s][0]) + fabsf(x[1] * A[s][1]) + fabsf(x[2] * A[s][2]);
         }
-        B = B * 0x1p-19f + 0x1p-100f;
+        B = (fabsf(x[0]) * As[0] + fabsf(x[1]) * As[1] + fabsf(x[2]) * As[2]) * 0x1p-19f + 0x1p-100f;
     };
     float lo = 0.0f;
     for (int k = threadIdx.x; k < Nv; k += blockDim.x) {
