@@ -324,6 +324,16 @@ avs_status avs_paper_parameters(const avs_flow_spec *spec, avs_config *cfg);
  * blocks.  Blocking.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
 avs_status avs_grid_barrier_check(avs_ctx *ctx, int blocks, int rounds, int short_by, int *passed);
 
+/* Self-test of the bounded mbarrier wait that the staged face and cell
+ * kernels use for their asynchronous bulk copies: one block initialises an
+ * mbarrier; with arrive = 1 one thread issues a 128-byte bulk copy into
+ * shared memory that completes it, with arrive = 0 nothing ever does, so the
+ * wait gives up after its limit (about a second), sets the error bit of the
+ * staged copies and the call returns AVS_ETIMEOUT with the context still
+ * usable.  *completed (host) = 1 when the copy arrived and its 128 bytes
+ * equal the source's.  Blocking.  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+avs_status avs_stage_wait_check(avs_ctx *ctx, int arrive, int *completed);
+
 /* Measured FMA throughput of the current GPU (GFLOP/s, 2 flops per FMA):
  * kind 0 FP32, 1 FP64, 2 FP32 pairs with the packed two-lane FMA.  Independent
  * multiply-add chains, timed with events; AVS_EINVAL for another kind.  A

@@ -28,7 +28,7 @@ EXPORTED = ["avs_create", "avs_destroy", "avs_last_error", "avs_num_nodes", "avs
             "avs_criterion", "avs_get_tree", "avs_get_f", "avs_get_f_cells", "avs_set_f", "avs_sync",
             "avs_kernel_launches",
             "avs_mlp_set_params", "avs_mlp_get_params", "avs_mlp_forward", "avs_mlp_grad", "avs_features",
-            "avs_mlp_train", "avs_mlp_check_set", "avs_measure_fma_peak", "avs_grid_barrier_check",
+            "avs_mlp_train", "avs_mlp_check_set", "avs_measure_fma_peak", "avs_grid_barrier_check", "avs_stage_wait_check",
             "avs_paper_parameters"]
 MLP_NPARAM = 4996
 
@@ -121,6 +121,7 @@ def load():
         "avs_mlp_check_set": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "avs_measure_fma_peak": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
         "avs_grid_barrier_check": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+        "avs_stage_wait_check": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int)]),
         "avs_paper_parameters": (C.c_int, [C.POINTER(FlowSpecS), C.POINTER(Config)]),
     }
     for name, (rt, args) in sig.items():
@@ -278,6 +279,14 @@ class AVS:
         self-test; raises AVSError(AVS_ETIMEOUT) when short_by > 0."""
         out = C.c_int()
         self._ck(self.L.avs_grid_barrier_check(self.h, int(blocks), int(rounds), int(short_by), C.byref(out)))
+        return out.value
+
+    def stage_wait_check(self, arrive=True):
+        """1 when a bulk copy completed the staged kernels' bounded mbarrier
+        wait with the right bytes; raises AVSError(AVS_ETIMEOUT) when nothing
+        arrives (arrive=False)."""
+        out = C.c_int()
+        self._ck(self.L.avs_stage_wait_check(self.h, int(bool(arrive)), C.byref(out)))
         return out.value
 
     def step(self, nsteps=1, dt=None, cfl=None):

@@ -755,6 +755,28 @@ avs_status avs_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int short_
     return read_err(c);
 }
 
+avs_status avs_stage_wait_check(avs_ctx* c, int arrive, int* completed)
+{
+    if (!c || !completed) return AVS_EINVAL;
+    float src[32];
+    for (int j = 0; j < 32; ++j) src[j] = 0.5f + (float)j;
+    float* d = nullptr;
+    int* dc = nullptr;
+    if (dalloc(&d, 32) != cudaSuccess || dalloc(&dc, 1) != cudaSuccess) {
+        cudaFree(d);
+        return fail(c, AVS_ENOMEM, "staged-copy wait check");
+    }
+    cudaError_t e = cudaMemcpyAsync(d, src, sizeof(src), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_stage_wait_check(c, d, arrive != 0, dc);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(completed, dc, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    cudaFree(dc);
+    CK(e);
+    return read_err(c);
+}
+
 avs_status ugks_step(avs_ctx* c, int nsteps, double cfl, double* dt_out)
 {
     if (!c || !(cfl > 0)) return AVS_EINVAL;

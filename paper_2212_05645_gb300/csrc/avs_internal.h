@@ -149,6 +149,7 @@ cudaError_t rk_launch_moments(avs_ctx* c, const void* f, int f_is_double, int Nc
 cudaError_t rk_launch_correct(avs_ctx* c, void* f, const double* Wtarget, int iters);
 cudaError_t rk_launch_cons_to_prim(avs_ctx* c, const double* Wc, double* Wp);
 cudaError_t launch_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int short_by, int* passed_dev);
+cudaError_t launch_stage_wait_check(avs_ctx* c, const float* src, bool arrive, int* completed_dev);
 cudaError_t launch_step_implicit(avs_ctx* c, const void* fin, void* fout, const double* Win, double* Wout, double dt,
                                  int k_macro, int k_micro);
 

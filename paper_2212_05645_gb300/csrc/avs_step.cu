@@ -2119,6 +2119,46 @@ cudaError_t launch_grid_barrier_check(avs_ctx* c, int blocks, int rounds, int sh
     return e;
 }
 
+// Self-test of the bounded mbarrier wait of the staged kernels: with `arrive`
+// one 128-byte bulk copy completes the barrier and the copied bytes are
+// compared with the source; without, no arrival ever comes and every thread's
+// wait gives up after kWaitCycles, setting bit 4 of the error word.
+__global__ void k_stage_wait_check(const float* __restrict__ src, int arrive, int* err, int* completed)
+{
+    __shared__ __align__(128) float buf[32];
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && arrive) {
+        mbar_arrive_expect_tx(&bar, 128u);
+        bulk_g2s(buf, src, 128u, &bar);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0u, kWaitCycles);
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, 4);
+            // a copy that was issued may still land: wait for it (bounded)
+            if (arrive) mbar_wait_bounded(&bar, 0u, kWaitCycles);
+        }
+        return;
+    }
+    if (threadIdx.x == 0) {
+        int same = 1;
+        for (int j = 0; j < 32; ++j) same &= buf[j] == src[j];
+        *completed = same;
+    }
+}
+
+cudaError_t launch_stage_wait_check(avs_ctx* c, const float* src, bool arrive, int* completed_dev)
+{
+    k_stage_wait_check<<<1, 32, 0, c->stream>>>(src, arrive ? 1 : 0, c->dev_err, completed_dev);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
 // One cell of a macroscopic sweep: dW_i = (Res_i(W~) + 1/2 sum A r dW_j) / diag_i,
 // Res_i = -sum sgn A F - 1/2 sum A (G(W~_j) - G(W^n_j)) over the interior faces.
 // Arithmetic in A (FP32 in the mixed form, where dW is a small correction of

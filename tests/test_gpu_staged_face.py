@@ -69,3 +69,27 @@ def test_staged_face_2d_walls(base):
 def test_staged_face_3d_sphere_walls_and_far_field(base):
     """12167 nodes (odd, ragged last stage) and 12288 (6 full stages)."""
     _check(_small_sphere_3d(base), 3, int(np.prod(base)))
+
+
+def test_staged_copy_wait_is_bounded():
+    """The mbarrier wait of the staged kernels' bulk copies: a copy completes
+    it with the right bytes; a wait that nothing completes gives up within its
+    limit, the call reports AVS_ETIMEOUT, and the context then runs a staged
+    step that matches the oracle."""
+    import time
+    avs = need_gpu()
+    w = _walled_box_2d((79, 79))
+    r, g = pair(w, avs, precision="mixed", amp=1e-2)
+    assert g.stage_wait_check(True) == 1
+    t0 = time.perf_counter()
+    with pytest.raises(avs.AVSError) as ei:
+        g.stage_wait_check(False)
+    assert ei.value.status == -4                     # AVS_ETIMEOUT
+    assert time.perf_counter() - t0 < 60
+    assert g.stage_wait_check(True) == 1             # the error word was cleared
+    dt = r.dt()
+    r.step(dt)
+    g.step(1, dt=dt)
+    e = field_err(g.f_moments(), O.moments(2, r.xi, r.w, r.f)[0], 2)
+    assert max(e.values()) < 1e-5, e
+    g.close()
