@@ -1712,6 +1712,105 @@ __global__ void __launch_bounds__(NT) k_raw_moments_pairs(CellP<D, float> P)
     if (tid < NM) P.mom[(size_t)i * NM + tid] = red[tid];
 }
 
+// k_grad for the FP32 form in packed two-lane arithmetic: four nodes per
+// thread as two pairs; the cell's geometry staged once per block in shared
+// memory; the gradient and limiter of k_foot_f2, stored as k_grad stores
+// them ([cell][array][D][Nvp]).  128-thread blocks, eight per SM.
+template <int D, int NS, int NA>
+__global__ void __launch_bounds__(128, 8) k_grad_f2(int Nv, int Nvp, int limiter, const float* __restrict__ f,
+                                                    float* __restrict__ Gout, CellGeo<float> geo)
+{
+    constexpr int VG = 4;
+    const int i = blockIdx.x;
+    const int t = threadIdx.x;
+    const int k0 = (blockIdx.y * blockDim.x + t) * VG;
+    const int ns = geo.ns[i];
+    __shared__ __align__(16) float gs[2][NS][4];      // LSQ weights, face offsets per slot
+    __shared__ int gn[NS];                            // neighbour cells (the cell itself where none)
+    if (t < NS * 4) {
+        const int s = t >> 2, d = t & 3;
+        const bool on = s < ns && d < D;
+        gs[0][s][d] = on ? geo.cg[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
+        gs[1][s][d] = on ? geo.r[(size_t)(i * AVS_MAXS + s) * D + d] : 0.0f;
+    } else if (t >= 32 && t < 32 + NS) {
+        const int s = t - 32;
+        const int n = s < ns ? geo.nbr[i * AVS_MAXS + s] : -1;
+        gn[s] = n >= 0 ? n : i;
+    }
+    __syncthreads();
+    if (k0 >= Nv) return;
+    const size_t cstride = (size_t)NA * Nvp;
+    auto vec = [&](int q, int s, float (&o)[D]) {
+        const float4 v = *reinterpret_cast<const float4*>(gs[q][s]);
+        o[0] = v.x;
+        o[1] = v.y;
+        if constexpr (D == 3) o[2] = v.z;
+    };
+    const float e2 = geo.eps2[i];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const float* fa = f + (size_t)a * Nvp + k0;
+        const float4 c4 = __ldg(reinterpret_cast<const float4*>(fa + (size_t)i * cstride));
+        const float2 phi[2] = {lo2(c4), hi2(c4)};
+        float4 n4[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) n4[s] = __ldg(reinterpret_cast<const float4*>(fa + (size_t)gn[s] * cstride));
+        float2 G[D][2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            float2 g[D], dd[NS];
+#pragma unroll
+            for (int d = 0; d < D; ++d) g[d] = bc2(0.0f);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                float cg[D];
+                vec(0, s, cg);
+                dd[s] = sub2(p ? hi2(n4[s]) : lo2(n4[s]), phi[p]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) g[d] = fma2(bc2(cg[d]), dd[s], g[d]);
+            }
+            float2 L = bc2(1.0f);
+            if (limiter == 1) {
+                float2 d2[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    float rr[D];
+                    vec(1, s, rr);
+                    d2[s] = mul2(g[0], bc2(rr[0]));
+#pragma unroll
+                    for (int d = 1; d < D; ++d) d2[s] = fma2(g[d], bc2(rr[d]), d2[s]);
+                }
+                float dx[NS], dy[NS], ex[NS], ey[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    dx[s] = dd[s].x; dy[s] = dd[s].y;
+                    ex[s] = d2[s].x; ey[s] = d2[s].y;
+                }
+                float2 dmax, dmin, pp, nn;
+                ext4<NS>(dx, dmax.x, dmin.x);
+                ext4<NS>(dy, dmax.y, dmin.y);
+                ext4<NS>(ex, pp.x, nn.x);
+                ext4<NS>(ey, pp.y, nn.y);
+                // epsilon^2 = (K dx)^3 phi_C^2: scaled to the limited value (R6)
+                const float2 e2p = mul2(mul2(bc2(e2), phi[p]), phi[p]);
+                const float2 tp = venkat2(dmax, pp, e2p);
+                const float2 tn = venkat2(dmin, nn, e2p);
+                if (pp.x > 0.0f) L.x = tp.x;
+                if (pp.y > 0.0f) L.y = tp.y;
+                if (nn.x < 0.0f && tn.x < L.x) L.x = tn.x;
+                if (nn.y < 0.0f && tn.y < L.y) L.y = tn.y;
+            }
+            if (limiter == 0) L = bc2(0.0f);
+#pragma unroll
+            for (int d = 0; d < D; ++d) G[d][p] = mul2(L, g[d]);
+        }
+        float* o = Gout + ((size_t)i * NA + a) * D * Nvp + k0;
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            *reinterpret_cast<float4*>(o + (size_t)d * Nvp) = make_float4(G[d][0].x, G[d][0].y, G[d][1].x, G[d][1].y);
+    }
+}
+
 // Limited gradients of every array of every cell into c->grad (allocated by the caller).
 template <int D, typename T, int NA>
 static void grad_t(avs_ctx* c, const void* fin)
@@ -1724,6 +1823,17 @@ static void grad_t(avs_ctx* c, const void* fin)
     geo.eps2 = f32 ? (const T*)c->eps2_f : (const T*)c->eps2_d;
     geo.ns = c->nslot;
     constexpr int VG = 4;
+    if constexpr (sizeof(T) == 4) {
+        const dim3 g2(c->Nc, (c->Nv + 128 * VG - 1) / (128 * VG));
+        if (D == 2 && c->max_ns <= 4)
+            k_grad_f2<D, 4, NA><<<g2, 128, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const float*)fin,
+                                                          (float*)c->grad, geo);
+        else
+            k_grad_f2<D, AVS_MAXS, NA><<<g2, 128, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const float*)fin,
+                                                                 (float*)c->grad, geo);
+        c->launches += 1;
+        return;
+    }
     dim3 g(c->Nc, (c->Nv + 256 * VG - 1) / (256 * VG));
     if (D == 2 && c->max_ns <= 4)
         k_grad<D, T, VG, 4, NA><<<g, 256, 0, c->stream>>>(c->Nv, c->Nvp, c->cfg.limiter, (const T*)fin, (T*)c->grad, geo);
