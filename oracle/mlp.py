@@ -16,6 +16,10 @@ features (8 per cell i; rho, U, T from the moments of f, R = 1/2, T_ref = 1)
      dx_i = |V_i|^(1/D)
   6  max over face neighbours |rho_j - rho_i| / rho_i
   7  max over face neighbours |T_j - T_i| / T_i
+For the diatomic (Rykov) gas of Sec. 2.1, T is the translational temperature
+T_t, (3/2) rho R T_t = rho E - rho U^2 / 2 - rho E_rot: the temperature of the
+velocity distribution G the velocity mesh resolves, and the one the model's
+viscosity and relaxation time take; q is the total heat flux q_t + q_r.
 labels (4 per cell) from m_ik = s max(M1_ik, M2_ik) and M_k = max_i m_ik
   0  split witness:   some node k below the level cap has m_ik > C1
   1  dominant:        some node k with M_k >= C2 has m_ik == M_k
@@ -34,11 +38,15 @@ NF = 8
 NO = 4
 
 
-def features(D, Wc, q, vol, faceL, faceR, R=0.5, mu_ref=1.0, omega=0.81, T_ref=1.0):
-    """Per-cell features (see module docstring) from conserved W and heat flux q."""
+def features(D, Wc, q, vol, faceL, faceR, R=0.5, mu_ref=1.0, omega=0.81, T_ref=1.0, rykov=False):
+    """Per-cell features (see module docstring) from conserved W and heat flux q.
+    rykov: W carries rho E_rot in column D+2 and T is the translational T_t."""
     rho = Wc[:, 0]
     U = Wc[:, 1:1 + D] / rho[:, None]
-    RT = (Wc[:, D + 1] - 0.5 * (Wc[:, 1:1 + D] ** 2).sum(1) / rho) / (1.5 * rho)
+    eint = Wc[:, D + 1] - 0.5 * (Wc[:, 1:1 + D] ** 2).sum(1) / rho
+    if rykov:
+        eint = eint - Wc[:, D + 2]
+    RT = eint / (1.5 * rho)
     T = RT / R
     mu = mu_ref * (T / T_ref) ** omega
     lam = 2.0 * mu * (5 - 2 * omega) * (7 - 2 * omega) / (15.0 * rho * np.sqrt(2 * math.pi * RT))

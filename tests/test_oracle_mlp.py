@@ -61,6 +61,38 @@ def test_features_uniform_state_closed_form():
     assert np.all(X[:, 6:] == 0.0)
 
 
+@pytest.mark.parametrize("D", [2, 3])
+def test_features_rykov_take_the_translational_temperature(D):
+    """Diatomic gas (Sec. 2.1): the temperature features are those of T_t,
+    whatever the rotational temperature.  W written by hand for rho = 2,
+    U = (0.3, -0.2[, 0.1]), T_t = 1.2 and a T_r that differs from cell to cell:
+    rho E_rot = rho R T_r, rho E = rho U^2/2 + (3/2) rho R T_t + rho E_rot.
+    The mean free path of Eq. 4 scales as T^(omega - 1/2) / rho from its
+    reference value Kn at rho = T = 1."""
+    w = wl.sweep_box((4, 4)) if D == 2 else wl.sphere(n_r=2, n_theta=3, n_phi=4, max_refine=1)
+    m = w.mesh
+    R, rho, Tt, Kn, omega = 0.5, 2.0, 1.2, 0.05, 0.81
+    U = np.array([0.3, -0.2, 0.1][:D])
+    Tr = 0.4 + 0.05 * np.arange(m.Nc)
+    Wc = np.zeros((m.Nc, D + 3))
+    Wc[:, 0] = rho
+    Wc[:, 1:1 + D] = rho * U
+    Wc[:, D + 2] = rho * R * Tr
+    Wc[:, D + 1] = 0.5 * rho * (U * U).sum() + 1.5 * rho * R * Tt + Wc[:, D + 2]
+    q = np.zeros((m.Nc, D))
+    mu = O.mu_ref_from_Kn(Kn, omega)
+    X = mlp.features(D, Wc, q, m.vol, m.faceL, m.faceR, mu_ref=mu, omega=omega, rykov=True)
+    su = math.sqrt(R)
+    assert np.allclose(X[:, 0], math.log(rho), rtol=1e-14)
+    for d in range(D):
+        assert np.allclose(X[:, 1 + d], U[d] / su, rtol=1e-14)
+    assert np.allclose(X[:, 4], math.log(Tt), rtol=1e-12)
+    lam = Kn * Tt ** (omega - 0.5) / rho
+    assert np.allclose(X[:, 5], np.log(lam / m.vol ** (1.0 / D)), rtol=1e-12, atol=1e-13)
+    assert np.all(np.abs(X[:, 7]) < 1e-13)            # T_r varies, T_t does not
+    assert np.all(X[:, 6] == 0.0)
+
+
 def test_labels_small_case_by_hand():
     m = np.array([[5.0, 0.1, 0.0], [1.0, 0.2, 3e-4], [1.0, 0.05, 1e-5]])
     M = m.max(0)
