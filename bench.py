@@ -88,7 +88,7 @@ WORKLOADS = {
     "sphere-r2": ("sphere", dict(n_r=2)),
     # the cylinder with the velocity space of the adaptive-parameter rules (zones, C1(Ma))
     "cylinder-zones": ("cylinder_zones", dict()),
-    # the cylinder with a diatomic gas (Rykov model: G, H, R; no learned proposer)
+    # the cylinder with a diatomic gas (Rykov model: G, H, R)
     "cylinder-rykov": ("cylinder", dict(model="rykov")),
     # the same on the inner 64 radial rows (profiling case)
     "cylinder-rykov-r64": ("cylinder", dict(n_r=64, model="rykov")),
@@ -103,8 +103,6 @@ def _build(fn, kw, precision):
     model = kw.pop("model", "shakhov")
     w = getattr(wl, fn)(precision=precision, **kw)
     w.model = model
-    if model != "shakhov":
-        w.learned = False
     return w
 
 
@@ -302,7 +300,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     w = _workload("mixed")
     # headline form: mixed precision with the learned proposer (full criterion every 4th adaptation)
-    learned = w.model == "shakhov"           # the proposer is built for the monatomic gas
+    learned = True
     nu = args.nu
     W0 = torch.from_numpy(np.ascontiguousarray(w.W_init)).to("cuda")
     Nc = w.mesh.Nc

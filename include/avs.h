@@ -100,8 +100,8 @@ typedef struct {
                              (Sec. 3.5 step 2); 0..max_refine                                */
     int model;            /* AVS_SHAKHOV (monatomic, Eqs. 14-17) or AVS_RYKOV (diatomic,
                              Eqs. GHR_equ, 11-13).  Rykov: f has the arrays G, H, R in 2D and
-                             G, R in 3D; W adds rho E_rot (NW = D+3 values per cell); no
-                             learned proposer and no implicit step                          */
+                             G, R in 3D; W adds rho E_rot (NW = D+3 values per cell); the
+                             proposer's temperature features are those of T_t           */
     double Zrot;          /* rotational collision number Z_rot of the Rykov model (>= 1)     */
 } avs_config;
 
@@ -262,7 +262,8 @@ avs_status avs_criterion_noalloc(int dim, int Nc, int Nv, const double *f, const
  * per-cell features (log rho, the velocity components over sqrt(R T_ref) (in
  * 2D the third slot holds |q|/(rho (RT)^1.5)), log T, log of the mean free
  * path of Eq. 4 over the cell size, the largest relative jumps of rho and T to
- * the face neighbours) it predicts four per-cell labels of
+ * the face neighbours; for the Rykov model T is the translational temperature
+ * T_t and q the total heat flux q_t + q_r) it predicts four per-cell labels of
  * the Sec. 3.4 criterion (split witness, dominant, near-dominant, merge
  * blocker).  With cfg.learned = 1, avs_adapt evaluates the criterion only on
  * the cells whose dominant logit exceeds the threshold (the check set: the cell

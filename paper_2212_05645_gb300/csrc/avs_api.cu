@@ -209,7 +209,6 @@ void mlp_default_params(std::vector<float>& P)
 
 avs_status ensure_mlp(avs_ctx* c, int rows)
 {
-    if (c->model != AVS_SHAKHOV) return fail(c, AVS_EINVAL, "the learned proposer is built for the Shakhov model");
     if (c->mlp_P && rows <= c->mlp_rows) return AVS_OK;
     const int nrows = std::max(rows, std::max(c->Nc, 1024));
     if (!c->mlp_P) {
@@ -267,7 +266,6 @@ avs_status validate(const avs_config* cfg, const avs_mesh* m, std::string& why)
     if (cfg->init_refine < 0 || cfg->init_refine > cfg->max_refine) { why = "init_refine out of range"; return AVS_EINVAL; }
     if (cfg->model != AVS_SHAKHOV && cfg->model != AVS_RYKOV) { why = "bad model"; return AVS_EINVAL; }
     if (cfg->model == AVS_RYKOV && !(cfg->Zrot >= 1.0)) { why = "Zrot must be at least 1"; return AVS_EINVAL; }
-    if (cfg->model == AVS_RYKOV && cfg->learned) { why = "the learned proposer is built for the Shakhov model"; return AVS_EINVAL; }
     if (m->Nc <= 0 || m->Nf <= 0 || m->nbc < 0) { why = "empty mesh"; return AVS_EINVAL; }
     if (!m->faceL || !m->faceR || !m->An || !m->rL || !m->rR || !m->vol || (m->nbc > 0 && !m->bc)) {
         why = "null mesh array";

@@ -405,9 +405,26 @@ __global__ void k_mlp_reduce(int nblk, const float* __restrict__ part, float* gr
 // Per-cell features (rho, U, T, lambda from the cell's moments Wf and heat flux q):
 // log rho, U / sqrt(R T_ref) (components; in 2D the third slot is
 // |q| / (rho (RT)^1.5)), log T, log(lambda / dx), largest relative jumps of rho
-// and T to the face neighbours.  lambda from Eqs. (3)-(4).
+// and T to the face neighbours.  lambda from Eqs. (3)-(4).  W holds NW values
+// per cell; for the diatomic (Rykov) gas of Sec. 2.1 the last is rho E_rot and
+// T is the translational temperature, (3/2) rho R T_t = rho E - rho U^2/2 -
+// rho E_rot, the temperature of G and of the model's viscosity.
 template <int D>
-__global__ void k_features(int Nc, const double* __restrict__ Wc, const double* __restrict__ q,
+__device__ __forceinline__ void feat_prim(const double* W, bool rykov, double& rho, double* U, double& RT)
+{
+    rho = W[0];
+    double m2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        U[d] = W[1 + d] / rho;
+        m2 += W[1 + d] * W[1 + d];
+    }
+    double e = W[D + 1] - 0.5 * m2 / rho;
+    if (rykov) e -= W[D + 2];
+    RT = e / (1.5 * rho);
+}
+
+template <int D>
+__global__ void k_features(int Nc, int NW, int rykov, const double* __restrict__ Wc, const double* __restrict__ q,
                            const double* __restrict__ vol, const int* __restrict__ nbr,
                            const unsigned char* __restrict__ nslot, double R, double mu_ref, double omega,
                            double T_ref, float* X)
@@ -415,7 +432,7 @@ __global__ void k_features(int Nc, const double* __restrict__ Wc, const double* 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Nc) return;
     double rho, U[3], RT;
-    prim<D>(Wc + (size_t)i * (D + 2), rho, U, RT);
+    feat_prim<D>(Wc + (size_t)i * NW, rykov != 0, rho, U, RT);
     const double T = RT / R;
     const double mu = mu_ref * pow(T / T_ref, omega);
     const double lam = 2.0 * mu * (5 - 2 * omega) * (7 - 2 * omega) / (15.0 * rho * sqrt(2 * AVS_PI * RT));
@@ -427,7 +444,7 @@ __global__ void k_features(int Nc, const double* __restrict__ Wc, const double* 
         const int j = nbr[i * AVS_MAXS + s];
         if (j < 0) continue;
         double rj, Uj[3], RTj;
-        prim<D>(Wc + (size_t)j * (D + 2), rj, Uj, RTj);
+        feat_prim<D>(Wc + (size_t)j * NW, rykov != 0, rj, Uj, RTj);
         jr = fmax(jr, fabs(rj - rho) / rho);
         jt = fmax(jt, fabs(RTj / R - T) / T);
     }
@@ -614,12 +631,13 @@ cudaError_t mlp_grad_step(avs_ctx* c, int n, const float* X, const float* Y, flo
 
 cudaError_t mlp_features(avs_ctx* c, const double* Wc, const double* q, float* X)
 {
+    const int rk = c->model == AVS_RYKOV;
     if (c->D == 2)
-        k_features<2><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(c->Nc, Wc, q, c->vol, c->nbr, c->nslot, c->cfg.R,
-                                                                  c->mu_ref, c->cfg.omega, c->cfg.T_ref, X);
+        k_features<2><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(c->Nc, c->NW, rk, Wc, q, c->vol, c->nbr, c->nslot,
+                                                                  c->cfg.R, c->mu_ref, c->cfg.omega, c->cfg.T_ref, X);
     else
-        k_features<3><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(c->Nc, Wc, q, c->vol, c->nbr, c->nslot, c->cfg.R,
-                                                                  c->mu_ref, c->cfg.omega, c->cfg.T_ref, X);
+        k_features<3><<<(c->Nc + 127) / 128, 128, 0, c->stream>>>(c->Nc, c->NW, rk, Wc, q, c->vol, c->nbr, c->nslot,
+                                                                  c->cfg.R, c->mu_ref, c->cfg.omega, c->cfg.T_ref, X);
     c->launches += 1;
     return cudaGetLastError();
 }

@@ -38,6 +38,21 @@ def pair(w, avs, precision=None, amp=1e-3, seed=12345, limiter=None, corr_iters=
     return r, g
 
 
+def pair_rykov(w, avs, precision=None, amp=1e-2, seed=7):
+    """Oracle run and CUDA context of the diatomic gas (Rykov model), same
+    tree, same f with the rotational temperature T_r = 0.8 T_t."""
+    r = O.Run(w)
+    g = avs.AVS(w, precision=precision)
+    t = g.tree()
+    assert np.array_equal(t["level"], r.level) and np.array_equal(t["key"], r.key)
+    Wp = np.column_stack([w.W_init, 0.8 * w.W_init[:, w.D + 1]])
+    r.init_field(Wp, amp=amp, seed=seed)
+    g.set_f(r.f)
+    g.set_W(r.Wc)
+    assert r.f.shape[1] == g.NA and r.Wc.shape[1] == g.NW
+    return r, g
+
+
 def rel_err(a, b):
     """max |a - b| / max |b| per leading index, then max."""
     a = np.asarray(a); b = np.asarray(b)

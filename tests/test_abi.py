@@ -65,7 +65,7 @@ def test_bad_configs_rejected_on_host():
     # the options of the next rows are checked on the host too
     assert try_cfg(model=5) == -1
     assert try_cfg(model=1, Zrot=0.5) == -1              # Rykov: Z_rot >= 1
-    assert try_cfg(model=1, Zrot=3.5, learned=1) == -1   # no learned proposer for the diatomic gas
+    assert try_cfg(model=1, Zrot=3.5, learned=1) != -1   # the diatomic gas takes the learned proposer
     assert try_cfg(nzones=9) == -1
     assert try_cfg(init_refine=2) == -1                  # beyond max_refine
     z = avs.Zone()

@@ -13,7 +13,7 @@ from oracle import mlp
 from oracle.mlp_params import flatten, unflatten
 from paper_2212_05645_gb300 import workloads as wl
 
-from gpu_common import need_gpu, pair
+from gpu_common import need_gpu, pair, pair_rykov, small_sphere
 
 pytestmark = pytest.mark.gpu
 
@@ -114,17 +114,52 @@ def test_features_and_labels_match_oracle():
     assert Yo[:, 1].sum() >= 1 and Yo[:, 1].sum() < len(Yo)
 
 
-def test_learned_adaptation_check_set_and_misses():
+RYKOV_FEATURE_CASES = {
+    "box": lambda: wl.sweep_box((8, 8), base=(10, 10), max_refine=1, C1=2.0),
+    "sphere": lambda: small_sphere(),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RYKOV_FEATURE_CASES))
+def test_features_and_labels_match_oracle_rykov(case):
+    """Diatomic gas (Rykov model, T_r = 0.8 T_t): features of the
+    translational temperature and the total heat flux q_t + q_r within FP32
+    rounding of the oracle's; labels bit-exact against the oracle's labels of
+    the same f (G decides the criterion) and the same W, 2D (G, H, R) and 3D
+    (G, R)."""
+    avs = need_gpu()
+    w = RYKOV_FEATURE_CASES[case]()
+    w.model = "rykov"
+    D = w.D
+    r, g = pair_rykov(w, avs, amp=1e-2)
+    X, Y = g.features()
+    Wf, qt, qr = O.moments_rykov(D, r.xi, r.w, r.f)
+    Xo = mlp.features(D, Wf, qt + qr, w.mesh.vol, w.mesh.faceL, w.mesh.faceR,
+                      mu_ref=O.mu_ref_from_Kn(w.Kn, w.omega), omega=w.omega, rykov=True)
+    assert np.allclose(X, Xo, rtol=2e-5, atol=2e-6)
+    Wg = g.f_moments()
+    assert Wg.shape[1] == D + 3
+    m = mlp.criterion_values(D, r.xi, r.w, r.f, Wg, r.s)
+    Yo = mlp.labels(m, m.max(0), r.level, w.C1, w.C2, w.max_refine)
+    assert np.array_equal(Y, Yo)
+    assert Yo[:, 1].sum() >= 1 and Yo[:, 1].sum() < len(Yo)
+    g.close()
+
+
+@pytest.mark.parametrize("model", ["shakhov", "rykov"])
+def test_learned_adaptation_check_set_and_misses(model):
     """A learned adaptation applies exactly the decisions of the criterion
     restricted to its check set (a strict subset of the cells); a full one
     right after applies the decisions of the whole criterion and reports as
     misses exactly the nodes whose split or merge test the check set would
     have decided differently.  Both judged against the oracle's criterion on
-    the same f and W, with the check set the library reports."""
+    the same f and W, with the check set the library reports; for the
+    monatomic gas and for the diatomic one (Rykov model, W with rho E_rot)."""
     avs = need_gpu()
     w = wl.sweep_box((16, 16), base=(10, 10), max_refine=2, C1=2.0)
     w.learned = True
-    r, g = pair(w, avs, amp=1e-3)
+    w.model = model
+    r, g = pair_rykov(w, avs, amp=1e-3) if model == "rykov" else pair(w, avs, amp=1e-3)
     loss = g.mlp_train(400, lr=0.2)
     assert np.isfinite(loss)
     s, C1, C2 = r.s, w.C1, w.C2
@@ -174,7 +209,8 @@ def _wall_heat_flux(w, q):
     return (q[m.faceL[b]] * n).sum(1)
 
 
-def test_learned_proposer_gain_over_plain_criterion():
+@pytest.mark.parametrize("model", ["shakhov", "rykov"])
+def test_learned_proposer_gain_over_plain_criterion(model):
     """What the trained network gains, and what it costs, over four
     adaptations 10 steps apart.  The first adaptation of a context and the
     forced last one run the full criterion (the fallback and judge); the two
@@ -191,6 +227,7 @@ def test_learned_proposer_gain_over_plain_criterion():
     avs = need_gpu()
     import time
     w = _walled_box()
+    w.model = model
     gl = avs.AVS(w, learned=True, full_every=1000)
     gp = avs.AVS(w, learned=False)
     for g in (gl, gp):
@@ -211,7 +248,7 @@ def test_learned_proposer_gain_over_plain_criterion():
     Wp, qp = gp.moments()
     l1_mom = np.abs(Wl - Wp).sum() / np.abs(Wp).sum()
     hf = np.abs(_wall_heat_flux(w, ql) - _wall_heat_flux(w, qp)).sum() / np.abs(_wall_heat_flux(w, qp)).sum()
-    print(f"\nlearned proposer: loss {loss:.4f}, checked fraction {np.mean(fracs):.3f}, misses {misses} of "
+    print(f"\nlearned proposer ({model}): loss {loss:.4f}, checked fraction {np.mean(fracs):.3f}, misses {misses} of "
           f"{gl.Nv} nodes, L1 f-moment gap {l1_mom:.2e}, wall heat-flux gap {hf:.2e}, "
           f"adapt time learned {tl:.3f}s plain {tp:.3f}s")
     assert len(fracs) == 2 and len(misses) == 2

@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 from paper_2212_05645_gb300 import workloads as wl
 
-from gpu_common import field_err, need_gpu, rel_err, small_cylinder, small_sphere
+from gpu_common import field_err, need_gpu, pair_rykov, rel_err, small_cylinder, small_sphere
 
 pytestmark = pytest.mark.gpu
 
@@ -23,20 +23,6 @@ CASES = {
 def rykov(w):
     w.model = "rykov"
     return w
-
-
-def pair_rykov(w, avs, precision=None, amp=1e-2, seed=7):
-    """Oracle run and CUDA context, same tree, same f with T_r = 0.8 T_t."""
-    r = O.Run(w)
-    g = avs.AVS(w, precision=precision)
-    t = g.tree()
-    assert np.array_equal(t["level"], r.level) and np.array_equal(t["key"], r.key)
-    Wp = np.column_stack([w.W_init, 0.8 * w.W_init[:, w.D + 1]])
-    r.init_field(Wp, amp=amp, seed=seed)
-    g.set_f(r.f)
-    g.set_W(r.Wc)
-    assert r.f.shape[1] == g.NA and r.Wc.shape[1] == g.NW
-    return r, g
 
 
 def erot_err(Wg, Wo, D):
@@ -113,13 +99,6 @@ def test_rykov_adapt_topology_remap_and_correction(D):
     g.adapt(bypass=True)
     assert rel_err(g.get_f(), r.f) < 1e-12
     g.close()
-
-
-def test_rykov_rejects_the_learned_proposer():
-    avs = need_gpu()
-    w = rykov(CASES["box"]("fp64"))
-    with pytest.raises(avs.AVSError):
-        avs.AVS(w, learned=True)
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
