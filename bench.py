@@ -458,7 +458,7 @@ def run_gpu(args):
         ga.close()
         del ga
         ablation = {"form": "mixed, plain criterion on every adaptation", "value": sum(ua) / (ta * 1e-3),
-                    "unit": UNIT, "steps": ka,
+                    "unit": UNIT, "steps": ka, "mean_velocity_nodes": sum(ua) / (ka * nu * Nc),
                     "learned_over_plain": value / ws / (sum(ua) / (ta * 1e-3))}
 
     # ---- plain FP64 GPU form on the same workload: the same kind of bench
