@@ -66,6 +66,8 @@ def _args():
                     help="time the implicit IUGKS step (60 macro + 2 micro SGS iterations) at this CFL instead")
     ap.add_argument("--sweep", action="store_true",
                     help="kernel sweep over cell and node counts (FP32 and FP64 steps), one JSON line per case")
+    ap.add_argument("--sweep-precision", default="both", choices=["both", "mixed", "fp64"],
+                    help="forms the sweep runs")
     return ap.parse_args()
 
 
@@ -558,7 +560,8 @@ def run_sweep(args):
         Nv = b ** D
         if n not in meshes:
             meshes[n] = wl.sweep_box(n, base=(b,) * D, max_refine=0)     # mesh and field built once per size
-        for precision in ("mixed", "fp64"):
+        forms = ("mixed", "fp64") if args.sweep_precision == "both" else (args.sweep_precision,)
+        for precision in forms:
             es = 4 if precision == "mixed" else 8
             NA = 2 if D == 2 else 1
             # f twice and the face rows of foot values / fluxes (D faces per cell)
