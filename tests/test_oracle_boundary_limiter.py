@@ -16,6 +16,10 @@ what diffuse reflection means, not by the oracle's own formula:
   temperature, a channel between walls sliding at the gas velocity) is left
   unchanged by a collisional second-order step.
 
+The diatomic gas (Rykov model, reading R29) is pinned by the same solve: the
+incoming R distribution of a boundary face is the rotational equilibrium at
+the boundary temperature, R T_b times the emitted G.
+
 The limiter (Sec. 2.3.3, reading R6) is pinned by Venkatakrishnan's function
 in its ratio form phi(y) = (y^2 + 2y)/(y^2 + y + 2), y = d+/d-, by its limits,
 and by a limited gradient worked out by hand on a ring of three cells.
@@ -121,6 +125,72 @@ def test_far_field_emits_free_stream_maxwellian(D):
     sel, phi = _emitted(xi, f, fo, dt, -1)
     M = maxwellian(xi[sel], rho, U, T)
     assert np.allclose(phi[0], M, rtol=1e-10, atol=0)
+    if D == 2:
+        assert np.allclose(phi[1], R * T * M, rtol=1e-10, atol=0)
+
+
+def _one_cell_step_rykov(D, lo_bc, hi_bc, nb, vlo, vhi, seed=11):
+    """_one_cell_step for the diatomic gas: f holds G, [H,] R (the last array
+    the rotational energy distribution), each a perturbed Maxwellian."""
+    bcs = [(lo_bc, hi_bc)] + [((), ())] * (D - 1)
+    m = wl.cartesian_mesh((1,) * D, (1.0,) * D, bcs=bcs, periodic=(False,) + (True,) * (D - 1))
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=1e14, limiter=0, model="rykov")
+    xi, w = _forest(nb, vlo, vhi)
+    assert np.all(np.abs(xi[:, 0]) > 1e-3)
+    rng = np.random.default_rng(seed)
+    nA = 3 if D == 2 else 2
+    f = maxwellian(xi, 1.0, [0.2, -0.1, 0.05], 1.1)[None, None, :] * rng.uniform(0.5, 1.5, size=(1, nA, len(w)))
+    Wc = O.moments_rykov(D, xi, w, f)[0]
+    dt = 0.2 * O.dt_unit(mh, xi)
+    fo = O.step(mh, g, xi, w, dt, f, Wc)
+    return xi, w, f[0], fo[0], dt
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_rykov_wall_emits_rotational_equilibrium_at_wall_temperature(D):
+    """R29: a diffuse wall in the diatomic gas sends rho_w M(U_w, T_w) in G,
+    (3 - D) R T_w times it in H and R T_w times it in R (rotational
+    equilibrium at the wall temperature), with zero net mass flux.  Catches
+    R T_w -> T_w in R, R at the gas's own rotational temperature, and R left
+    as the cell's outgoing values."""
+    Uw = (0.0, 0.3, -0.2)[:D]
+    Tw = 1.4
+    wall = wl._bc_row(wl.BC_WALL, T=Tw, U=Uw)
+    far = wl._bc_row(wl.BC_FARFIELD, rho=0.7, U=(0.4, -0.2, 0.1)[:D], T=1.6)
+    nb = (6, 5, 4)[:D]
+    vlo = (-2.4, -2.0, -2.1)[:D]
+    vhi = (2.6, 2.2, 1.9)[:D]
+    xi, w, f, fo, dt = _one_cell_step_rykov(D, far, wall, nb, vlo, vhi)
+    sel, phi = _emitted(xi, f, fo, dt, +1)
+    M = maxwellian(xi[sel], 1.0, Uw, Tw)
+    rho_w = phi[0] / M
+    assert np.ptp(rho_w) <= 1e-10 * rho_w.mean(), rho_w
+    x = xi[:, 0]
+    out = (w[~sel] * x[~sel] * f[0, ~sel]).sum()
+    inc = (w[sel] * (-x[sel]) * phi[0]).sum()
+    assert inc == pytest.approx(out, rel=1e-11)
+    assert np.allclose(phi[-1], R * Tw * phi[0], rtol=1e-10, atol=0)
+    if D == 2:
+        assert np.allclose(phi[1], (3 - D) * R * Tw * phi[0], rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_rykov_far_field_emits_free_stream_equilibrium(D):
+    """R29 far field in the diatomic gas: G = g^eq(W_inf) with its density,
+    velocity and temperature, R = R T_inf G (rotational temperature equal to
+    the free stream's), H = (3 - D) R T_inf G."""
+    rho, U, T = 0.7, (0.4, -0.2, 0.1)[:D], 1.6
+    far = wl._bc_row(wl.BC_FARFIELD, rho=rho, U=U, T=T)
+    wall = wl._bc_row(wl.BC_WALL, T=0.9)
+    nb = (6, 5, 4)[:D]
+    vlo = (-2.4, -2.0, -2.1)[:D]
+    vhi = (2.6, 2.2, 1.9)[:D]
+    xi, w, f, fo, dt = _one_cell_step_rykov(D, far, wall, nb, vlo, vhi, seed=12)
+    sel, phi = _emitted(xi, f, fo, dt, -1)
+    M = maxwellian(xi[sel], rho, U, T)
+    assert np.allclose(phi[0], M, rtol=1e-10, atol=0)
+    assert np.allclose(phi[-1], R * T * M, rtol=1e-10, atol=0)
     if D == 2:
         assert np.allclose(phi[1], R * T * M, rtol=1e-10, atol=0)
 
