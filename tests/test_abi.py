@@ -118,3 +118,29 @@ def test_binding_rejects_short_or_mistyped_buffers():
                 torch.zeros((5, 8), dtype=torch.float64)[:, :4], [0.0] * 20):
         with pytest.raises(ValueError):
             _check_buf(bad, 20, "W")
+
+
+PARAM_FLOWS = [(2, dict(Ma=5.0)),
+               (2, dict(Ma=8.0, separated=True)),
+               (2, dict(Ma=20.2, gamma=1.4, T_w=290.0 / 13.32, dir=(0.9848, 0.1736, 0.0))),
+               (3, dict(Ma=5.45, gamma=1.4, rdv_sigma=7.0)),
+               (3, dict(Ma=4.25, gamma=1.4, dir=(1.0, 0.0, 1.0)))]
+
+
+@pytest.mark.parametrize("D,kw", PARAM_FLOWS)
+def test_library_paper_parameters_on_host(D, kw):
+    """avs_paper_parameters is host code of the library (Sec. 3.5 rules): it
+    runs without a GPU and gives the oracle's velocity space, zones and
+    thresholds bit for bit."""
+    import oracle as O
+    from paper_2212_05645_gb300 import avs
+    B.build()
+    flow = wl.FlowSpec(**kw)
+    g = avs.paper_parameters(D, flow)
+    o = O.paper_parameters(D, flow.Ma, flow.gamma, flow.T_inf, flow.T_w, flow.dir, flow.h_std, flow.rdv_sigma,
+                           flow.separated)
+    for k in ("base", "vlo", "vhi", "max_refine", "outside", "init_refine", "C1", "C2"):
+        assert g[k] == o[k], (k, g[k], o[k])
+    assert len(g["zones"]) == len(o["zones"])
+    for zg, zo in zip(g["zones"], o["zones"]):
+        assert zg == (tuple(zo[0]), zo[1], zo[2], zo[3])
