@@ -144,3 +144,57 @@ def test_library_paper_parameters_on_host(D, kw):
     assert len(g["zones"]) == len(o["zones"])
     for zg, zo in zip(g["zones"], o["zones"]):
         assert zg == (tuple(zo[0]), zo[1], zo[2], zo[3])
+
+
+def test_bad_meshes_rejected_on_host():
+    """The face list is checked on the host before any device work: cells out
+    of range, a face joining a cell to itself, more than six faces on a cell,
+    unknown boundary types, non-positive boundary temperatures and cell
+    volumes are AVS_EINVAL; the untouched mesh passes the checks (and then
+    fails only for want of a GPU here)."""
+    from paper_2212_05645_gb300 import avs
+    B.build()
+    L = avs.load()
+    w = wl.cavity(n=4)
+
+    def try_mesh(edit=None):
+        m = w.mesh
+        a = {k: np.array(getattr(m, k), copy=True) for k in ("faceL", "faceR", "An", "rL", "rR", "vol", "bc")}
+        if edit:
+            edit(a)
+        cfg = avs.Config()
+        cfg.dim = 2; cfg.base[0] = cfg.base[1] = 4; cfg.max_refine = 1
+        cfg.vlo[0] = cfg.vlo[1] = -2.0; cfg.vhi[0] = cfg.vhi[1] = 2.0
+        cfg.R = 0.5; cfg.Pr = 2 / 3; cfg.omega = 0.81; cfg.Kn = 0.1; cfg.T_ref = 1.0
+        cfg.C1 = 1.0; cfg.C2 = 1e-4; cfg.W_inf[0] = 1.0; cfg.W_inf[3] = 1.0; cfg.limiter = 1; cfg.lim_K = 0.3
+        cfg.corr_iters = 3
+        dp = C.POINTER(C.c_double); ip = C.POINTER(C.c_int)
+        ms = avs.MeshS(m.D, m.Nc, len(a["faceL"]), a["bc"].shape[0], a["faceL"].ctypes.data_as(ip),
+                       a["faceR"].ctypes.data_as(ip), a["An"].ctypes.data_as(dp), a["rL"].ctypes.data_as(dp),
+                       a["rR"].ctypes.data_as(dp), a["vol"].ctypes.data_as(dp), a["bc"].ctypes.data_as(dp))
+        h = C.c_void_p()
+        return L.avs_create(C.byref(cfg), C.byref(ms), None, C.byref(h))
+
+    def setv(key, idx, val):
+        def e(a):
+            a[key][idx] = val
+        return e
+
+    nc = w.mesh.Nc
+    inner = int(np.nonzero(w.mesh.faceR >= 0)[0][0])
+    assert try_mesh() != -1
+    assert try_mesh(setv("faceL", 0, nc)) == -1                     # cell index out of range
+    assert try_mesh(setv("faceL", 0, -1)) == -1
+    assert try_mesh(setv("faceR", inner, nc)) == -1
+    assert try_mesh(setv("faceR", 0, -1 - w.mesh.bc.shape[0])) == -1  # boundary row out of range
+    assert try_mesh(setv("faceR", inner, int(w.mesh.faceL[inner]))) == -1   # a cell joined to itself
+    assert try_mesh(setv("bc", (0, 0), 7.0)) == -1                  # unknown boundary type
+    assert try_mesh(setv("bc", (0, 5), 0.0)) == -1                  # boundary temperature must be positive
+    assert try_mesh(setv("vol", 3, 0.0)) == -1                      # non-positive cell volume
+
+    def seven_faces(a):
+        # three more faces between cells 0 and 1: cell 0 then has more than six
+        for k in ("faceL", "faceR", "An", "rL", "rR"):
+            extra = np.repeat(a[k][inner:inner + 1], 3, axis=0)
+            a[k] = np.ascontiguousarray(np.concatenate([a[k], extra]))
+    assert try_mesh(seven_faces) == -1
