@@ -97,3 +97,80 @@ def test_interface_flux_free_molecular_limit_is_the_flux_of_the_foot_distributio
     """tau >> h: the interface distribution is phi_bar itself."""
     F_int, FE, Fk = _interior_face_flux(1e14)
     assert np.all(np.abs(F_int - Fk) <= 1e-12 * np.abs(Fk).max()), (F_int, Fk)
+
+
+# ---- the diatomic gas (Rykov model; reading R27 of its interface state)
+
+def rk_moments(xi, w, G, H, Rr):
+    """rho, rho u, rho v, rho E (total: translational and rotational), rho E_rot."""
+    x2 = (xi ** 2).sum(1)
+    return np.array([(w * G).sum(), (w * xi[:, 0] * G).sum(), (w * xi[:, 1] * G).sum(),
+                     0.5 * (w * (x2 * G + H)).sum() + (w * Rr).sum(), (w * Rr).sum()])
+
+
+def rk_flux(xi, w, G, H, Rr, n):
+    sn = xi @ n
+    x2 = (xi ** 2).sum(1)
+    return np.array([(w * sn * G).sum(), (w * sn * xi[:, 0] * G).sum(), (w * sn * xi[:, 1] * G).sum(),
+                     (w * sn * (0.5 * (x2 * G + H) + Rr)).sum(), (w * sn * Rr).sum()])
+
+
+def rk_euler_flux_x(W):
+    """Euler flux of a diatomic gas in rotational equilibrium: rho E = rho |U|^2/2
+    + (5/2) rho R T, p = rho R T; the rotational energy rho R T moves with u."""
+    rho, mu, mv, E, _ = W
+    u, v = mu / rho, mv / rho
+    p = (E - 0.5 * rho * (u * u + v * v)) / 2.5
+    return np.array([mu, mu * u + p, mv * u, (E + p) * u, p * u])
+
+
+def _interior_face_flux_rykov(Kn):
+    """As _interior_face_flux for the diatomic gas; each cell's f is G, H, R of
+    a Maxwellian at T_t with a rotational temperature T_r = 0.7 T_t."""
+    st = [(1.0, (0.3, 0.1), 1.0), (0.6, (-0.2, 0.05), 1.4)]
+    far = [wl._bc_row(wl.BC_FARFIELD, rho=r, U=(*U, 0.0), T=T) for r, U, T in st]
+    m = wl.cartesian_mesh((2, 1), (2.0, 1.0), bcs=[(far[0], far[1]), ((), ())], periodic=(False, True))
+    mh = O.MeshHandle(m)
+    g = O.gas(Kn=Kn, limiter=0, model="rykov")
+    nb = np.array([48, 48], np.int32)
+    level, base, key = O.forest_base(2, nb)
+    xi, w = O.forest_geom(2, nb, (-7.0, -7.0), (7.0, 7.0), level, base, key)
+    f = np.zeros((2, 3, len(w)))
+    for i, (r, U, T) in enumerate(st):
+        f[i, 0] = maxwellian(xi, r, U, T)
+        f[i, 1] = R * T * f[i, 0]
+        f[i, 2] = R * 0.7 * T * f[i, 0]
+    W0 = np.stack([rk_moments(xi, w, *f[i]) for i in range(2)])
+    Wc = W0.copy()
+    dt = 0.5 * O.dt_unit(mh, xi)
+    O.step(mh, g, xi, w, dt, f, Wc)
+    x = xi[:, 0]
+    inc = x > 0.0
+    Mf = maxwellian(xi, *st[0])
+    Tf = st[0][2]
+    F_left = rk_flux(xi, w, np.where(inc, Mf, f[0, 0]), np.where(inc, R * Tf * Mf, f[0, 1]),
+                     np.where(inc, R * Tf * Mf, f[0, 2]), np.array([-1.0, 0.0]))
+    F_int = (W0[0] - Wc[0]) / dt - F_left
+    up = x >= 0.0
+    feet = [np.where(up, f[0, a], f[1, a]) for a in range(3)]
+    FE = rk_euler_flux_x(rk_moments(xi, w, *feet))
+    Fk = rk_flux(xi, w, *feet, np.array([1.0, 0.0]))
+    return F_int, FE, Fk
+
+
+def test_rykov_interface_flux_continuum_limit_is_the_diatomic_euler_flux():
+    """tau << h: the interface relaxes the rotational energy fully and carries
+    the Euler flux of a diatomic gas in equilibrium (mass, momentum and total
+    energy: the cell's own rotational source then relaxes E_rot as well, so
+    its flux cannot be read back)."""
+    F_int, FE, Fk = _interior_face_flux_rykov(1e-10)
+    scale = np.abs(FE).max()
+    assert np.all(np.abs(F_int[:4] - FE[:4]) <= 1e-6 * scale), (F_int, FE)
+    assert np.abs(Fk[:4] - FE[:4]).max() > 1e-2 * scale
+
+
+def test_rykov_interface_flux_free_molecular_limit_is_the_flux_of_the_feet():
+    """tau >> h: no relaxation anywhere; every component, E_rot included, is
+    the flux of the feet."""
+    F_int, FE, Fk = _interior_face_flux_rykov(1e14)
+    assert np.all(np.abs(F_int - Fk) <= 1e-12 * np.abs(Fk).max()), (F_int, Fk)
