@@ -269,6 +269,43 @@ def test_continuum_limit_gives_shakhov_of_predicted_state():
         assert np.allclose(fo[i, 1], gH, rtol=0, atol=1e-7 * gH.max())
 
 
+def test_uniform_gas_relaxes_by_backward_euler():
+    """A spatially uniform gas in a periodic box (no net transport: every
+    face flux leaves one cell and enters another with the same value) whose f
+    is out of equilibrium relaxes by one backward-Euler step of
+    df/dt = (g - f)/tau: f^{n+1} = (tau f + dt g)/(tau + dt), g the Shakhov
+    equilibrium of W with the heat flux of f (R3) and tau = mu(T)/p with the
+    power-law viscosity of Eqs. 3-4; W stays as it was.  At Kn = 0.05 the
+    weight dt/(tau + dt) is neither 0 nor 1, so a wrong tau, a wrong power of
+    T, an explicit instead of implicit step or a missing heat flux shows."""
+    m = _box(3)
+    mh = O.MeshHandle(m)
+    Kn, omega = 0.05, 0.81
+    g = O.gas(Kn=Kn, omega=omega, limiter=1)
+    _, _, _, _, xi, w = uniform_forest(2, 16, -4.0, 4.0)
+    rho, U, T = 1.3, np.array([0.2, -0.1]), 1.2
+    c = xi - U[None, :]
+    f1 = O.maxwell_init(2, xi, np.array([[rho, *U, T]]))[0]
+    skew = 1.0 + 0.05 * c[:, 0] * ((c * c).sum(1) - 2.0) + 0.03 * c[:, 1]
+    f1 = f1 * skew[None, :]
+    f = np.repeat(f1[None], m.Nc, axis=0)
+    Wc, q = O.moments(2, xi, w, f)
+    W0 = Wc.copy()
+    dt = 0.5 * O.dt_unit(mh, xi)
+    fo = O.step(mh, g, xi, w, dt, f, Wc)
+    assert np.allclose(Wc, W0, rtol=1e-14, atol=0)
+    r = W0[0, 0]
+    u = W0[0, 1:3] / r
+    RT = (W0[0, 3] - 0.5 * r * u @ u) / (1.5 * r)
+    mu = O.mu_ref_from_Kn(Kn, omega) * (RT / R) ** omega
+    tau = mu / (r * RT)
+    gG, gH = O.shakhov_field(2, xi, g.Pr, r, u, RT, q[0])
+    assert 0.05 < dt / (tau + dt) < 0.95
+    for i in range(m.Nc):
+        assert np.allclose(fo[i, 0], (tau * f[i, 0] + dt * gG) / (tau + dt), rtol=0, atol=1e-13 * gG.max())
+        assert np.allclose(fo[i, 1], (tau * f[i, 1] + dt * gH) / (tau + dt), rtol=0, atol=1e-13 * gH.max())
+
+
 # ---------------------------------------------------------------- conservation
 def test_uniform_stream_stays_uniform():
     """Periodic box, f = discrete Maxwellian on a symmetric uniform velocity
