@@ -1,5 +1,6 @@
-"""The multi-rank path of bench.py (replicas, weak scaling) on the CPU: two
-gloo ranks aggregate the slowest rank's time and the sum of the updates."""
+"""bench.py on the CPU: the multi-rank path (replicas, weak scaling), where
+two gloo ranks aggregate the slowest rank's time and the sum of the updates,
+and the reference arm's JSON line."""
 import os
 import socket
 
@@ -43,3 +44,24 @@ def test_two_rank_aggregation_gloo():
 def test_single_rank_is_identity():
     import bench
     assert bench.aggregate(7.0, 5.0, 1) == (7.0, 5.0)
+
+
+def test_reference_arm_prints_its_json_line():
+    """`bench.py --impl reference` (the CPU oracle, timed as it stands) prints
+    one JSON line with the contract's keys; the cavity keeps it to a second."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "cavity", "--steps", "1",
+                        "--warmup", "0"], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "cell-velocity-node updates/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("cavity")
